@@ -1,0 +1,329 @@
+"""Python access to the FP64 CPU oracle (``oracle/oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, ``__graft_entry__.smoke()`` and the CPU
+baseline leg of ``bench.py``.  The product package never imports it.
+
+Inputs are the arrays of ``scenes`` (grids, MLP weights, cameras, rays); outputs are numpy
+float64 arrays.  See ``oracle.c`` for the definitions and the paper passages they follow.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import sys
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile ``liboracle.so`` (gcc, -O2, no FP contraction, OpenMP)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC",
+               "-shared", "-o", tmp, _SRC, "-lm"]
+        subprocess.check_call(cmd)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class OrGrid(C.Structure):
+    _fields_ = [("n", C.c_int * 3), ("C", C.c_int), ("aabb_min", C.c_float * 3), ("aabb_max", C.c_float * 3),
+                ("act_shift", C.c_double), ("dtype", C.c_int), ("density", C.c_void_p),
+                ("features", C.c_void_p), ("occ", C.c_void_p), ("occ_res", C.c_int)]
+
+
+class OrMlp(C.Structure):
+    _fields_ = [("in_dim", C.c_int), ("hidden", C.c_int), ("n_freq", C.c_int), ("dtype", C.c_int),
+                ("w1", C.c_void_p), ("b1", C.c_void_p), ("w2", C.c_void_p), ("b2", C.c_void_p),
+                ("w3", C.c_void_p), ("b3", C.c_void_p)]
+
+
+class OrSampling(C.Structure):
+    _fields_ = [("near_t", C.c_float), ("far_t", C.c_float), ("n_samples", C.c_int), ("step", C.c_float),
+                ("t_stop", C.c_float), ("bg", C.c_float * 3), ("void_acc", C.c_float)]
+
+
+class OrRays(C.Structure):
+    _fields_ = [("kind", C.c_int), ("width", C.c_int), ("height", C.c_int), ("f", C.c_float),
+                ("cx", C.c_float), ("cy", C.c_float), ("c2w", C.c_float * 12), ("pix", C.c_void_p),
+                ("n_pix", C.c_int), ("o", C.c_void_p), ("d", C.c_void_p), ("n_rays", C.c_int)]
+
+
+class OrCam(C.Structure):
+    _fields_ = [("width", C.c_int), ("height", C.c_int), ("f", C.c_float), ("cx", C.c_float),
+                ("cy", C.c_float), ("c2w", C.c_float * 12)]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = C.CDLL(_LIB)
+        P = C.c_void_p
+        L.or_render.argtypes = [P] * 13 + [C.c_int]
+        L.or_render.restype = C.c_int
+        L.or_active_samples.argtypes = [P, P, P, C.c_int, P, P, P, C.c_long, P, P]
+        L.or_active_samples.restype = C.c_long
+        L.or_sample_grid.argtypes = [P, P, C.c_int, P, P]
+        L.or_mlp_eval.argtypes = [P, P, C.c_int, P]
+        L.or_encode.argtypes = [P, C.c_int, P, P, C.c_int, P]
+        L.or_warp.argtypes = [P, P, P, P, C.c_float, P, P, P, P, P, P, P, P]
+        L.or_warp.restype = C.c_int
+        L.or_warp_bruteforce.argtypes = [P, P, P, C.c_float, P]
+        L.or_rel_pose.argtypes = [P, P, P]
+        L.or_backward.argtypes = [P] * 8
+        L.or_backward.restype = C.c_int
+        L.or_relu_margin.argtypes = [P] * 5
+        L.or_max_threads.restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+class _Keep:
+    """Holds the numpy buffers a ctypes struct points into."""
+
+    def __init__(self):
+        self.refs = []
+
+    def __call__(self, a):
+        self.refs.append(a)
+        return a
+
+
+_DT = {np.dtype(np.float64): 0, np.dtype(np.float32): 1, np.dtype(np.float16): 2}
+
+
+def _grid(g, keep) -> OrGrid:
+    dens = keep(np.ascontiguousarray(g.density))
+    feat = keep(np.ascontiguousarray(g.features))
+    assert dens.dtype == feat.dtype
+    s = OrGrid()
+    s.n[:] = list(g.n)
+    s.C = g.C
+    s.aabb_min[:] = list(g.aabb_min)
+    s.aabb_max[:] = list(g.aabb_max)
+    s.act_shift = g.act_shift
+    s.dtype = _DT[dens.dtype]
+    s.density = dens.ctypes.data
+    s.features = feat.ctypes.data
+    if g.occ is not None:
+        occ = keep(np.ascontiguousarray(g.occ, dtype=np.uint8))
+        s.occ = occ.ctypes.data
+        s.occ_res = occ.shape[0]
+    return s
+
+
+def _mlp(m, keep) -> OrMlp:
+    s = OrMlp()
+    arrs = [keep(np.ascontiguousarray(a)) for a in (m.w1, m.b1, m.w2, m.b2, m.w3, m.b3)]
+    s.in_dim, s.hidden, s.n_freq = m.in_dim, m.hidden, m.n_freq
+    s.dtype = 0 if arrs[0].dtype == np.float64 else 1
+    s.w1, s.b1, s.w2, s.b2, s.w3, s.b3 = [a.ctypes.data for a in arrs]
+    return s
+
+
+def _sampling(sp) -> OrSampling:
+    s = OrSampling()
+    s.near_t, s.far_t, s.n_samples, s.step, s.t_stop = sp.near, sp.far, sp.n_samples, sp.step, sp.t_stop
+    s.bg[:] = list(sp.bg)
+    s.void_acc = sp.void_acc
+    return s
+
+
+def _cam(cam) -> OrCam:
+    s = OrCam()
+    s.width, s.height, s.f, s.cx, s.cy = cam.width, cam.height, cam.f, cam.cx, cam.cy
+    s.c2w[:] = [float(v) for v in np.asarray(cam.c2w, dtype=np.float32).ravel()]
+    return s
+
+
+def _camera_rays(cam, pix, keep) -> OrRays:
+    s = OrRays()
+    s.kind = 0
+    s.width, s.height, s.f, s.cx, s.cy = cam.width, cam.height, cam.f, cam.cx, cam.cy
+    s.c2w[:] = [float(v) for v in np.asarray(cam.c2w, dtype=np.float32).ravel()]
+    if pix is not None:
+        p = keep(np.ascontiguousarray(pix, dtype=np.int32))
+        s.pix = p.ctypes.data
+        s.n_pix = p.size
+    return s
+
+
+def _explicit_rays(o, d, keep) -> OrRays:
+    s = OrRays()
+    s.kind = 1
+    o = keep(np.ascontiguousarray(o, dtype=np.float32))
+    d = keep(np.ascontiguousarray(d, dtype=np.float32))
+    s.o, s.d, s.n_rays = o.ctypes.data, d.ctypes.data, o.shape[0]
+    return s
+
+
+def _rays(keep, cam=None, pix=None, rays=None):
+    if rays is not None:
+        return _explicit_rays(rays[0], rays[1], keep)
+    return _camera_rays(cam, pix, keep)
+
+
+def _nrays(cam=None, pix=None, rays=None):
+    if rays is not None:
+        return int(np.asarray(rays[0]).shape[0])
+    return int(len(pix)) if pix is not None else cam.width * cam.height
+
+
+def render(grid, mlp, sampling, cam=None, pix=None, rays=None, threads: int = 0) -> dict:
+    """Render the rays of ``cam`` (every pixel, or the pixels in ``pix``) or the explicit
+    ``rays=(o, d)``.  Returns rgb [R,3], depth, acc, n_steps, amb and the *_alt outcome."""
+    keep = _Keep()
+    g, m, s = _grid(grid, keep), _mlp(mlp, keep), _sampling(sampling)
+    r = _rays(keep, cam, pix, rays)
+    R = _nrays(cam, pix, rays)
+    out = {k: np.zeros((R, 3)) for k in ("rgb", "rgb_alt")}
+    for k in ("depth", "acc", "depth_alt", "acc_alt"):
+        out[k] = np.zeros(R)
+    for k in ("n_steps", "amb", "n_steps_alt"):
+        out[k] = np.zeros(R, dtype=np.int32)
+    rc = lib().or_render(C.byref(g), C.byref(m), C.byref(r), C.byref(s), _ptr(out["rgb"]), _ptr(out["depth"]),
+                         _ptr(out["acc"]), _ptr(out["n_steps"]), _ptr(out["amb"]), _ptr(out["rgb_alt"]),
+                         _ptr(out["depth_alt"]), _ptr(out["acc_alt"]), _ptr(out["n_steps_alt"]), threads)
+    if rc != 0:
+        raise ValueError(f"or_render failed ({rc})")
+    out["amb"] = out["amb"].astype(bool)
+    return out
+
+
+def active_samples(grid, sampling, brick: int, cam=None, pix=None, rays=None, cap: int | None = None) -> dict:
+    """The samples that reach Feature Gathering with their brick id (FP32 decisions)."""
+    keep = _Keep()
+    g, s = _grid(grid, keep), _sampling(sampling)
+    r = _rays(keep, cam, pix, rays)
+    R = _nrays(cam, pix, rays)
+    cap = cap or R * sampling.n_samples
+    ray_of = np.zeros(cap, dtype=np.int32)
+    slot_of = np.zeros(cap, dtype=np.int32)
+    brick_of = np.zeros(cap, dtype=np.int32)
+    n_steps = np.zeros(R, dtype=np.int32)
+    amb = np.zeros(R, dtype=np.int32)
+    n = lib().or_active_samples(C.byref(g), C.byref(r), C.byref(s), brick, _ptr(ray_of), _ptr(slot_of),
+                                _ptr(brick_of), cap, _ptr(n_steps), _ptr(amb))
+    if n < 0:
+        raise ValueError("capacity too small")
+    return {"ray": ray_of[:n], "slot": slot_of[:n], "brick": brick_of[:n], "n_steps": n_steps,
+            "amb": amb.astype(bool)}
+
+
+def sample_grid(grid, points):
+    keep = _Keep()
+    g = _grid(grid, keep)
+    p = np.ascontiguousarray(points, dtype=np.float64)
+    n = p.shape[0]
+    raw = np.zeros(n)
+    feat = np.zeros((n, grid.C))
+    lib().or_sample_grid(C.byref(g), _ptr(p), n, _ptr(raw), _ptr(feat))
+    return raw, feat
+
+
+def mlp_eval(mlp, x):
+    keep = _Keep()
+    m = _mlp(mlp, keep)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    out = np.zeros((x.shape[0], 3))
+    lib().or_mlp_eval(C.byref(m), _ptr(x), x.shape[0], _ptr(out))
+    return out
+
+
+def encode(mlp, feat, d):
+    keep = _Keep()
+    m = _mlp(mlp, keep)
+    feat = np.ascontiguousarray(feat, dtype=np.float64)
+    d = np.ascontiguousarray(d, dtype=np.float64)
+    M, Cn = feat.shape
+    x = np.zeros((M, mlp.in_dim))
+    lib().or_encode(C.byref(m), Cn, _ptr(feat), _ptr(d), M, _ptr(x))
+    return x
+
+
+def warp(ref_rgb, ref_depth, ref_cam, tgt_cam, max_angle_deg: float = 180.0, void_grid=None,
+         void_sampling=None) -> dict:
+    """SpaRW warp of a float32 reference frame into the target camera (FP32 decisions)."""
+    keep = _Keep()
+    rgb = keep(np.ascontiguousarray(ref_rgb, dtype=np.float32))
+    dep = keep(np.ascontiguousarray(ref_depth, dtype=np.float32))
+    rc, tc = _cam(ref_cam), _cam(tgt_cam)
+    NT = tgt_cam.width * tgt_cam.height
+    out = {"rgb": np.zeros((NT, 3), dtype=np.float32), "depth": np.zeros(NT, dtype=np.float32),
+           "mask": np.zeros(NT, dtype=np.uint8), "hole_idx": np.zeros(NT, dtype=np.int32),
+           "src": np.zeros(NT, dtype=np.int32)}
+    nh = C.c_int32(0)
+    vg = _grid(void_grid, keep) if void_grid is not None else None
+    vs = _sampling(void_sampling or tgt_cam.sampling)
+    r = lib().or_warp(_ptr(rgb), _ptr(dep), C.byref(rc), C.byref(tc), max_angle_deg,
+                      C.byref(vg) if vg is not None else None, C.byref(vs), _ptr(out["rgb"]),
+                      _ptr(out["depth"]), _ptr(out["mask"]), _ptr(out["hole_idx"]), C.byref(nh), _ptr(out["src"]))
+    if r != 0:
+        raise MemoryError("or_warp")
+    out["n_holes"] = int(nh.value)
+    out["hole_idx"] = out["hole_idx"][: out["n_holes"]]
+    return out
+
+
+def warp_bruteforce(ref_depth, ref_cam, tgt_cam, max_angle_deg: float = 180.0):
+    dep = np.ascontiguousarray(ref_depth, dtype=np.float32)
+    rc, tc = _cam(ref_cam), _cam(tgt_cam)
+    src = np.zeros(tgt_cam.width * tgt_cam.height, dtype=np.int32)
+    lib().or_warp_bruteforce(_ptr(dep), C.byref(rc), C.byref(tc), max_angle_deg, _ptr(src))
+    return src
+
+
+def rel_pose(ref_cam, tgt_cam):
+    rc, tc = _cam(ref_cam), _cam(tgt_cam)
+    out = np.zeros(12, dtype=np.float32)
+    lib().or_rel_pose(C.byref(rc), C.byref(tc), _ptr(out))
+    return out.reshape(3, 4)
+
+
+def backward(grid, mlp, sampling, d_rgb, cam=None, pix=None, rays=None, with_mlp: bool = False):
+    """FP64 gradient of a loss with dL/drgb = ``d_rgb`` w.r.t. density, features (and MLP)."""
+    keep = _Keep()
+    g, m, s = _grid(grid, keep), _mlp(mlp, keep), _sampling(sampling)
+    r = _rays(keep, cam, pix, rays)
+    dr = np.ascontiguousarray(d_rgb, dtype=np.float64)
+    dd = np.zeros(grid.density.size)
+    df = np.zeros(grid.features.size)
+    nm = mlp.flat().size
+    dm = np.zeros(nm) if with_mlp else None
+    rc = lib().or_backward(C.byref(g), C.byref(m), C.byref(r), C.byref(s), _ptr(dr), _ptr(dd), _ptr(df), _ptr(dm))
+    if rc != 0:
+        raise ValueError(f"or_backward failed ({rc})")
+    return dd.reshape(grid.density.shape), df.reshape(grid.features.shape), dm
+
+
+def relu_margin(grid, mlp, sampling, cam=None, pix=None, rays=None):
+    keep = _Keep()
+    g, m, s = _grid(grid, keep), _mlp(mlp, keep), _sampling(sampling)
+    r = _rays(keep, cam, pix, rays)
+    out = np.zeros(_nrays(cam, pix, rays))
+    lib().or_relu_margin(C.byref(g), C.byref(m), C.byref(r), C.byref(s), _ptr(out))
+    return out
+
+
+def max_threads() -> int:
+    return int(lib().or_max_threads())
+
+
+def psnr(a, b) -> float:
+    mse = float(np.mean((np.asarray(a, dtype=np.float64) - np.asarray(b, dtype=np.float64)) ** 2))
+    return float("inf") if mse == 0 else 10.0 * np.log10(1.0 / mse)
+
+
+if __name__ == "__main__":
+    print(build(force="--force" in sys.argv))
