@@ -1,0 +1,242 @@
+/*
+ * cicero.h - C ABI of the GB300 (sm_103a) voxel-grid NeRF renderer with sparse radiance
+ * warping (SpaRW), after "Cicero: Addressing Algorithmic and Architectural Bottlenecks in
+ * Neural Rendering by Radiance Warping and Memory Optimizations" (arXiv 2404.11852).
+ *
+ * Conventions shared by every call
+ *   - Every array pointer is a DEVICE pointer owned by the caller, unless the parameter says
+ *     otherwise.  Descriptor structs (cicero_grid, cicero_mlp, cicero_camera, cicero_sampling,
+ *     cicero_options) are read on the host during the call and may be freed afterwards.
+ *   - Calls are asynchronous on `stream` (a cudaStream_t, NULL = legacy default stream).  The
+ *     host validates the arguments and returns a status before anything is launched; no call
+ *     synchronises the stream or allocates device memory.
+ *   - Scratch memory is the caller's `workspace` of `ws_bytes` bytes (size it with the matching
+ *     cicero_*_workspace_size query; 256-byte aligned).  A workspace must not be shared by calls
+ *     that may run concurrently.  Errors found by a kernel (an internal invariant broken, a
+ *     bounded wait that ran out) are recorded in the workspace and reported by
+ *     cicero_workspace_status.
+ *   - Pixel p = j * width + i is the pixel of column i and row j; its centre is (i + 0.5, j + 0.5).
+ *   - Camera poses c2w are row-major 3x4 camera-to-world matrices with OpenCV axes (x right,
+ *     y down, z forward); f is the focal length in pixels and (cx, cy) the principal point, the
+ *     intrinsics of Eq. 1 and Eq. 3.
+ *   - On error the call returns a non-zero status and cicero_last_error() describes it.
+ */
+#ifndef CICERO_H
+#define CICERO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CICERO_OK = 0,
+    CICERO_ERR_INVALID_ARG = 1,        /* a NULL pointer, a bad size or an inconsistent descriptor */
+    CICERO_ERR_UNSUPPORTED = 2,        /* a shape or option this build does not implement */
+    CICERO_ERR_ALIGNMENT = 3,          /* a pointer or stride breaks the TMA 16-byte rules */
+    CICERO_ERR_WORKSPACE_TOO_SMALL = 4,
+    CICERO_ERR_CUDA = 5,               /* a CUDA runtime call failed (message in cicero_last_error) */
+    CICERO_ERR_TIMEOUT = 6,            /* a kernel's bounded wait ran out (reported by cicero_workspace_status) */
+    CICERO_ERR_INTERNAL = 7            /* a kernel found a broken invariant (reported by cicero_workspace_status) */
+} cicero_status;
+
+typedef enum { CICERO_F32 = 0, CICERO_F16 = 1 } cicero_dtype;
+
+/* Arithmetic of Feature Computation (the MLP):
+ * FP32: FP32 FFMA on CUDA cores.  BF16: tcgen05 tensor-core MMAs with BF16 operands (weights and
+ * activations rounded to BF16) and FP32 accumulation in tensor memory. */
+typedef enum { CICERO_MLP_FP32 = 0, CICERO_MLP_BF16 = 1 } cicero_precision;
+
+/* Dense voxel grid (Sec. II-B: "each vertex carries a high-dimensional feature vector").
+ * Vertices sit on the corners of the box [aabb_min, aabb_max]; n[a] vertices along axis a.
+ *   density  [n2][n1][n0]       raw density, sigma = softplus(raw + act_shift)
+ *   features [n2][n1][n0][C]    feature vectors
+ *   occ      [R][R][R] uint8 or NULL: occupancy of R^3 equal cells over the box; samples in
+ *            empty cells are skipped (alpha = 0, no gathering, no MLP).
+ * Requirements: n[a] >= 2, 1 <= C <= 21 (the MLP input is C + 3 + 6 n_freq <= 48 for BF16),
+ * features 16-byte aligned and n0 * C * sizeof(element) a multiple of 16 (TMA staging). */
+typedef struct {
+    int n[3];
+    int C;
+    float aabb_min[3], aabb_max[3];
+    float act_shift;
+    cicero_dtype dtype;
+    const void *density;
+    const void *features;
+    const uint8_t *occ;
+    int occ_res;
+} cicero_grid;
+
+/* Feature Computation MLP (Sec. II-B: "a lightweight MLP"), FP32 weights, row-major [out][in]:
+ *   x  = [features (C), d (3), sin(2^k d), cos(2^k d) for k = 0..n_freq-1 (6 n_freq)]
+ *   h1 = relu(w1 x + b1)  (hidden), h2 = relu(w2 h1 + b2)  (hidden), c = sigmoid(w3 h2 + b3)  (3)
+ * where d is the unit ray direction and each sin/cos block is (x, y, z) of sin then of cos.
+ * This build supports hidden == 128 and in_dim == C + 3 + 6 n_freq <= 48. */
+typedef struct {
+    int in_dim, hidden, n_freq;
+    const float *w1, *b1, *w2, *b2, *w3, *b3;
+} cicero_mlp;
+
+/* Sample placement and compositing (Sec. II-B Indexing and accumulation).
+ *   step == 0: n_samples slots at near + (k + 1/2)(far - near)/n_samples, delta = (far-near)/n_samples
+ *   step  > 0: slots at t_in + (k + 1/2) step, k < n_samples, while before the box exit t_out,
+ *              where [t_in, t_out] is the ray's span inside the box clipped to [near, far]
+ *   Before slot k the march stops if the transmittance T_k < t_stop (t_stop = 0: never).
+ *   rgb = sum_k T_k alpha_k c_k + T_end bg,  acc = sum_k T_k alpha_k,
+ *   depth = sum_k T_k alpha_k t_k / acc (ray distance), or +inf when acc < void_acc. */
+typedef struct {
+    float near_t, far_t;
+    int n_samples;
+    float step;
+    float t_stop;
+    float bg[3];
+    float void_acc;
+} cicero_sampling;
+
+typedef struct {
+    int width, height;
+    float f, cx, cy;
+    float c2w[12];
+} cicero_camera;
+
+/* Options of the rendering calls (NULL = defaults: FP32 MLP, bricks of 8^3 voxels). */
+typedef struct {
+    cicero_precision precision;
+    int brick;          /* voxels per brick edge ("MVoxel", Sec. IV-A): 4, 8 or 16; 0 = 8 */
+} cicero_options;
+
+/* ---------------------------------------------------------------------------------------------
+ * Rendering (Sec. II-B, run memory-centric as in Sec. IV-A).
+ *
+ * Every pixel of `cam` is rendered.  The samples that reach Feature Gathering are grouped by
+ * brick (the Ray Index Table of Sec. IV-A, built by a counting sort on the brick id); each
+ * brick is staged once into shared memory by TMA and all of its samples are interpolated from
+ * there and passed through the MLP; per-ray colours are then composited in slot order.
+ * Outputs (device): rgb [H*W][3], depth [H*W] (+inf = void), acc [H*W] or NULL,
+ * n_steps [H*W] or NULL (slots visited before the early stop).
+ */
+cicero_status cicero_render(const cicero_grid *grid, const cicero_mlp *mlp, const cicero_camera *cam,
+                            const cicero_sampling *sampling, const cicero_options *opt,
+                            float *rgb, float *depth, float *acc, int32_t *n_steps,
+                            void *workspace, size_t ws_bytes, void *stream);
+
+/* Same as cicero_render for n_rays explicit rays: ray_o, ray_d [n_rays][3] (device, unit d). */
+cicero_status cicero_render_rays(const cicero_grid *grid, const cicero_mlp *mlp,
+                                 const float *ray_o, const float *ray_d, int n_rays,
+                                 const cicero_sampling *sampling, const cicero_options *opt,
+                                 float *rgb, float *depth, float *acc, int32_t *n_steps,
+                                 void *workspace, size_t ws_bytes, void *stream);
+
+/* Sparse NeRF rendering of the disoccluded pixels, Gamma_sp of Eq. 4, combined in place (the
+ * circled-asterisk of Eq. 4): the pixels hole_idx[0 .. *n_holes) of `cam` are rendered and
+ * written into rgb_inout [H*W][3] and depth_inout [H*W] (may be NULL); other pixels are left
+ * untouched.  n_holes is a DEVICE scalar (as written by cicero_warp), so no host read-back is
+ * needed; max_holes bounds it and sizes the workspace. */
+cicero_status cicero_render_holes(const cicero_grid *grid, const cicero_mlp *mlp, const cicero_camera *cam,
+                                  const cicero_sampling *sampling, const cicero_options *opt,
+                                  const int32_t *hole_idx, const int32_t *n_holes, int max_holes,
+                                  float *rgb_inout, float *depth_inout,
+                                  void *workspace, size_t ws_bytes, void *stream);
+
+/* Workspace bytes for cicero_render / cicero_render_rays / cicero_render_holes with n_rays rays
+ * (H*W, n_rays or max_holes).  Host query, allocates nothing. */
+size_t cicero_render_workspace_size(const cicero_grid *grid, int n_rays, const cicero_sampling *sampling,
+                                    const cicero_options *opt);
+
+/* ---------------------------------------------------------------------------------------------
+ * SpaRW target frame, steps 1-3 (Eq. 1 point cloud, Eq. 2 transform, Eq. 3 re-projection) plus
+ * the depth test, the void depth test and hole listing of step 4 (Sec. III-B).
+ *
+ *   ref_rgb [Hr*Wr][3], ref_depth [Hr*Wr] (ray distance; +inf = void) of the reference camera.
+ *   Eq. 1: Z = D / |((u-cx)/f, (v-cy)/f, 1)|, P = Z ((u-cx)/f, (v-cy)/f, 1).
+ *   Eq. 2: P' = R P + t with [R|t] = inverse(c2w_tgt) c2w_ref, formed in FP64 on the host and
+ *          rounded once to FP32.
+ *   Eq. 3: u' = f' X'/Z' + cx', v' = f' Y'/Z' + cy'; the point lands on pixel (floor u', floor v').
+ *   Points with Z' <= 1e-6 or off the target image are dropped; void reference pixels are points
+ *   at infinity (rotated direction, depth key +inf).  Depth test: a 64-bit atomicMin of
+ *   (float bits of Z') << 32 | reference pixel index, so the nearest point wins and ties go to
+ *   the lower index.  max_angle_deg < 180 enables the warp-angle heuristic phi (Sec. III-C): a
+ *   point is kept only when the angle between its reference and target rays is below it.
+ * Outputs: warped_rgb [Ht*Wt][3]; warped_depth [Ht*Wt] or NULL (distance |P'| of the winning
+ * point, +inf for void, 0 for holes); hole_mask [Ht*Wt] (0 warped, 1 hole to render, 2 void);
+ * hole_idx [Ht*Wt] (holes with mask 1 in ascending pixel order) and *n_holes (device scalar).
+ * void_grid (may be NULL) enables the void depth test: a hole whose target ray has no sample
+ * inside the grid box (and in an occupied cell) gets void_sampling->bg, depth +inf, mask 2.
+ * Decisions are taken in FP32 with round-to-nearest and no contraction, so the mask and the
+ * list are reproducible bit for bit. */
+cicero_status cicero_warp(const float *ref_rgb, const float *ref_depth,
+                          const cicero_camera *ref_cam, const cicero_camera *tgt_cam,
+                          float max_angle_deg, const cicero_grid *void_grid,
+                          const cicero_sampling *void_sampling,
+                          float *warped_rgb, float *warped_depth, uint8_t *hole_mask,
+                          int32_t *hole_idx, int32_t *n_holes,
+                          void *workspace, size_t ws_bytes, void *stream);
+
+size_t cicero_warp_workspace_size(const cicero_camera *tgt_cam);
+
+/* ---------------------------------------------------------------------------------------------
+ * Backward of cicero_render_rays with the FP32 MLP (not in the paper, whose models are trained
+ * offline; the gradient of its rendering function).  Given d_rgb = dL/drgb [n_rays][3], the
+ * gradient is ACCUMULATED into d_density [n2][n1][n0], d_features [n2][n1][n0][C] (both FP32;
+ * zero them first) and, when d_mlp is not NULL, into the MLP gradient laid out as
+ * [w1, b1, w2, b2, w3, b3].  Each ray's forward pass is recomputed (nothing is stored by the
+ * forward); early stop is a fixed truncation.  For composited sample k:
+ *   dL/dc_k = w_k g;  dL/dsigma_k = delta (T_{k+1} g.c_k - g.R_k), R_k = sum_{j>k} w_j c_j + T_end bg;
+ *   dL/draw_k = dL/dsigma_k sigmoid(raw_k + shift); MLP chain rule; trilinear adjoint. */
+cicero_status cicero_render_backward(const cicero_grid *grid, const cicero_mlp *mlp,
+                                     const float *ray_o, const float *ray_d, int n_rays,
+                                     const cicero_sampling *sampling, const float *d_rgb,
+                                     float *d_density, float *d_features, float *d_mlp,
+                                     void *workspace, size_t ws_bytes, void *stream);
+
+size_t cicero_backward_workspace_size(const cicero_grid *grid, int n_rays, const cicero_sampling *sampling);
+
+/* ---------------------------------------------------------------------------------------------
+ * Pieces of the path, exposed for testing and for callers that drive the stages themselves.
+ */
+
+/* The Ray Index Table (Sec. IV-A) of a camera: the samples that reach Feature Gathering, grouped
+ * by brick of opt->brick^3 voxels, brick id (bz * nby + by) * nbx + bx with nb = ceil((n-1)/brick).
+ * brick_offsets [n_bricks + 1]: samples of brick b are samples[brick_offsets[b] .. brick_offsets[b+1]).
+ * samples [H*W*n_samples]: sample id = ray * n_samples + slot.  The order inside one brick is
+ * not specified.  n_bricks is returned through *n_bricks_out (host). */
+cicero_status cicero_build_rit(const cicero_grid *grid, const cicero_camera *cam, const cicero_sampling *sampling,
+                               const cicero_options *opt, int32_t *brick_offsets, int32_t *samples,
+                               int *n_bricks_out, void *workspace, size_t ws_bytes, void *stream);
+
+/* Feature Computation alone: c [M][3] = MLP(x [M][in_dim]) in the chosen precision. */
+cicero_status cicero_mlp_eval(const cicero_mlp *mlp, const float *x, int M, cicero_precision precision,
+                              float *c, void *workspace, size_t ws_bytes, void *stream);
+
+size_t cicero_mlp_eval_workspace_size(int M);
+
+/* Reads the error word of a workspace after the work queued on `stream` has finished (this call
+ * synchronises `stream`).  Returns CICERO_OK, CICERO_ERR_TIMEOUT or CICERO_ERR_INTERNAL; the
+ * word is cleared. */
+cicero_status cicero_workspace_status(void *workspace, void *stream);
+
+/* Stage timing for measurement tools.  Between cicero_profile_begin and cicero_profile_end the
+ * library records a pair of CUDA events on the caller's stream around each stage it launches;
+ * cicero_profile_end synchronises on them and writes, per stage, the summed elapsed time in ms and
+ * the number of timed launches.  Stages: 0 march (Indexing + density + transmittance),
+ * 1 brick bucketing (Ray Index Table), 2 brick gather + MLP, 3 compositing, 4 warp splat
+ * (Eq. 1-3 + depth test), 5 warp resolve + hole listing, 6 backward per ray, 7 backward per
+ * brick, 8 MLP alone.  Profiling state is process-wide; do not profile from several threads. */
+cicero_status cicero_profile_begin(void);
+cicero_status cicero_profile_end(double *total_ms, long long *launches, int n_stages);
+
+/* Number of CUDA kernels this library has launched since it was loaded (all devices). */
+long long cicero_launch_count(void);
+
+/* Thread-local description of the last error returned on this thread. */
+const char *cicero_last_error(void);
+
+/* Library version string. */
+const char *cicero_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CICERO_H */

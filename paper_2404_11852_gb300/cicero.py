@@ -1,0 +1,299 @@
+"""Python binding of libcicero (include/cicero.h): argument marshalling only.
+
+Every function named ``cicero_*`` here calls the C entry point of the same name with the raw
+device pointers of the torch tensors it is given and raises ``CiceroError`` when the status is
+not ``CICERO_OK``.  All computation happens in the CUDA kernels of the library; if the library
+is missing the import of this module fails.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcicero.so")
+
+OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_ALIGNMENT, ERR_WORKSPACE, ERR_CUDA, ERR_TIMEOUT, ERR_INTERNAL = range(8)
+F32, F16 = 0, 1
+MLP_FP32, MLP_BF16 = 0, 1
+
+
+class CiceroError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"cicero status {status}: {msg}")
+        self.status = status
+
+
+class Grid(C.Structure):
+    _fields_ = [("n", C.c_int * 3), ("C", C.c_int), ("aabb_min", C.c_float * 3), ("aabb_max", C.c_float * 3),
+                ("act_shift", C.c_float), ("dtype", C.c_int), ("density", C.c_void_p), ("features", C.c_void_p),
+                ("occ", C.c_void_p), ("occ_res", C.c_int)]
+
+
+class Mlp(C.Structure):
+    _fields_ = [("in_dim", C.c_int), ("hidden", C.c_int), ("n_freq", C.c_int), ("w1", C.c_void_p),
+                ("b1", C.c_void_p), ("w2", C.c_void_p), ("b2", C.c_void_p), ("w3", C.c_void_p), ("b3", C.c_void_p)]
+
+
+class Sampling(C.Structure):
+    _fields_ = [("near_t", C.c_float), ("far_t", C.c_float), ("n_samples", C.c_int), ("step", C.c_float),
+                ("t_stop", C.c_float), ("bg", C.c_float * 3), ("void_acc", C.c_float)]
+
+
+class Camera(C.Structure):
+    _fields_ = [("width", C.c_int), ("height", C.c_int), ("f", C.c_float), ("cx", C.c_float), ("cy", C.c_float),
+                ("c2w", C.c_float * 12)]
+
+
+class Options(C.Structure):
+    _fields_ = [("precision", C.c_int), ("brick", C.c_int)]
+
+
+_P = C.c_void_p
+_Z = C.c_size_t
+_SIGS = {
+    "cicero_render": ([_P] * 10 + [_Z, _P], C.c_int),
+    "cicero_render_rays": ([_P] * 4 + [C.c_int] + [_P] * 7 + [_Z, _P], C.c_int),
+    "cicero_render_holes": ([_P] * 7 + [C.c_int] + [_P] * 3 + [_Z, _P], C.c_int),
+    "cicero_render_workspace_size": ([_P, C.c_int, _P, _P], _Z),
+    "cicero_warp": ([_P] * 4 + [C.c_float] + [_P] * 8 + [_Z, _P], C.c_int),
+    "cicero_warp_workspace_size": ([_P], _Z),
+    "cicero_render_backward": ([_P] * 4 + [C.c_int] + [_P] * 6 + [_Z, _P], C.c_int),
+    "cicero_backward_workspace_size": ([_P, C.c_int, _P], _Z),
+    "cicero_build_rit": ([_P] * 8 + [_Z, _P], C.c_int),
+    "cicero_mlp_eval": ([_P, _P, C.c_int, C.c_int, _P, _P, _Z, _P], C.c_int),
+    "cicero_mlp_eval_workspace_size": ([C.c_int], _Z),
+    "cicero_workspace_status": ([_P, _P], C.c_int),
+    "cicero_profile_begin": ([], C.c_int),
+    "cicero_profile_end": ([_P, _P, C.c_int], C.c_int),
+    "cicero_launch_count": ([], C.c_longlong),
+    "cicero_last_error": ([], C.c_char_p),
+    "cicero_version": ([], C.c_char_p),
+}
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libcicero.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = C.CDLL(LIB_PATH)
+        for name, (args, res) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != OK:
+        raise CiceroError(status, lib().cicero_last_error().decode())
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    assert isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous(), "expected a contiguous CUDA tensor"
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ws(ws: torch.Tensor):
+    return _ptr(ws), C.c_size_t(ws.numel() * ws.element_size())
+
+
+def _ref(x):
+    return None if x is None else C.byref(x)
+
+
+# ---------------------------------------------------------------------------------------------
+# descriptors
+
+
+class DeviceGrid:
+    """A grid resident on the GPU: torch tensors plus the ``cicero_grid`` descriptor."""
+
+    def __init__(self, density: torch.Tensor, features: torch.Tensor, aabb_min=(-1.0, -1.0, -1.0),
+                 aabb_max=(1.0, 1.0, 1.0), act_shift: float = -4.0, occ: torch.Tensor | None = None):
+        assert density.dtype == features.dtype and density.dtype in (torch.float32, torch.float16)
+        self.density, self.features, self.occ = density.contiguous(), features.contiguous(), occ
+        nz, ny, nx, c = features.shape
+        d = Grid()
+        d.n[:] = [nx, ny, nz]
+        d.C = c
+        d.aabb_min[:] = list(aabb_min)
+        d.aabb_max[:] = list(aabb_max)
+        d.act_shift = act_shift
+        d.dtype = F16 if density.dtype == torch.float16 else F32
+        d.density = self.density.data_ptr()
+        d.features = self.features.data_ptr()
+        if occ is not None:
+            self.occ = occ.to(torch.uint8).contiguous()
+            d.occ = self.occ.data_ptr()
+            d.occ_res = self.occ.shape[0]
+        self.desc = d
+
+    @classmethod
+    def from_host(cls, g, device="cuda"):
+        """From a host grid object with numpy ``density``/``features``/``occ`` arrays."""
+        dens = torch.from_numpy(g.density).to(device)
+        feat = torch.from_numpy(g.features).to(device)
+        occ = None if g.occ is None else torch.from_numpy(g.occ).to(device)
+        return cls(dens, feat, g.aabb_min, g.aabb_max, g.act_shift, occ)
+
+
+class DeviceMlp:
+    def __init__(self, w1, b1, w2, b2, w3, b3, n_freq: int = 4):
+        self.t = [w.contiguous().float() for w in (w1, b1, w2, b2, w3, b3)]
+        m = Mlp()
+        m.hidden, m.in_dim = self.t[0].shape
+        m.n_freq = n_freq
+        m.w1, m.b1, m.w2, m.b2, m.w3, m.b3 = [w.data_ptr() for w in self.t]
+        self.desc = m
+
+    @classmethod
+    def from_host(cls, m, device="cuda"):
+        return cls(*[torch.from_numpy(a).to(device) for a in (m.w1, m.b1, m.w2, m.b2, m.w3, m.b3)], n_freq=m.n_freq)
+
+
+def sampling(near=0.5, far=2.5, n_samples=64, step=0.0, t_stop=1e-3, bg=(0.0, 0.0, 0.0), void_acc=0.5) -> Sampling:
+    s = Sampling()
+    s.near_t, s.far_t, s.n_samples, s.step, s.t_stop = near, far, n_samples, step, t_stop
+    s.bg[:] = list(bg)
+    s.void_acc = void_acc
+    return s
+
+
+def sampling_from(sp) -> Sampling:
+    return sampling(sp.near, sp.far, sp.n_samples, sp.step, sp.t_stop, sp.bg, sp.void_acc)
+
+
+def camera(width, height, f, cx, cy, c2w) -> Camera:
+    c = Camera()
+    c.width, c.height, c.f, c.cx, c.cy = width, height, f, cx, cy
+    c.c2w[:] = [float(v) for v in c2w.reshape(-1)]
+    return c
+
+
+def camera_from(cam) -> Camera:
+    return camera(cam.width, cam.height, cam.f, cam.cx, cam.cy, cam.c2w)
+
+
+def options(precision: int = MLP_FP32, brick: int = 8) -> Options:
+    o = Options()
+    o.precision, o.brick = precision, brick
+    return o
+
+
+def workspace(nbytes: int, device="cuda") -> torch.Tensor:
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+# ---------------------------------------------------------------------------------------------
+# entry points (same names as the C ABI)
+
+
+def cicero_render(grid: Grid, mlp: Mlp, cam: Camera, samp: Sampling, opt: Options | None, rgb, depth, acc, n_steps,
+                  ws, stream=None):
+    p, n = _ws(ws)
+    _check(lib().cicero_render(C.byref(grid), C.byref(mlp), C.byref(cam), C.byref(samp), _ref(opt), _ptr(rgb),
+                               _ptr(depth), _ptr(acc), _ptr(n_steps), p, n, _stream(stream)))
+
+
+def cicero_render_rays(grid: Grid, mlp: Mlp, ray_o, ray_d, samp: Sampling, opt: Options | None, rgb, depth, acc,
+                       n_steps, ws, stream=None):
+    p, n = _ws(ws)
+    _check(lib().cicero_render_rays(C.byref(grid), C.byref(mlp), _ptr(ray_o), _ptr(ray_d), ray_o.shape[0],
+                                    C.byref(samp), _ref(opt), _ptr(rgb), _ptr(depth), _ptr(acc), _ptr(n_steps), p, n,
+                                    _stream(stream)))
+
+
+def cicero_render_holes(grid: Grid, mlp: Mlp, cam: Camera, samp: Sampling, opt: Options | None, hole_idx, n_holes,
+                        max_holes: int, rgb_inout, depth_inout, ws, stream=None):
+    p, n = _ws(ws)
+    _check(lib().cicero_render_holes(C.byref(grid), C.byref(mlp), C.byref(cam), C.byref(samp), _ref(opt),
+                                     _ptr(hole_idx), _ptr(n_holes), int(max_holes), _ptr(rgb_inout),
+                                     _ptr(depth_inout), p, n, _stream(stream)))
+
+
+def cicero_render_workspace_size(grid: Grid, n_rays: int, samp: Sampling, opt: Options | None = None) -> int:
+    return int(lib().cicero_render_workspace_size(C.byref(grid), int(n_rays), C.byref(samp), _ref(opt)))
+
+
+def cicero_warp(ref_rgb, ref_depth, ref_cam: Camera, tgt_cam: Camera, max_angle_deg: float, void_grid: Grid | None,
+                void_samp: Sampling | None, warped_rgb, warped_depth, hole_mask, hole_idx, n_holes, ws, stream=None):
+    p, n = _ws(ws)
+    _check(lib().cicero_warp(_ptr(ref_rgb), _ptr(ref_depth), C.byref(ref_cam), C.byref(tgt_cam), float(max_angle_deg),
+                             _ref(void_grid), _ref(void_samp), _ptr(warped_rgb), _ptr(warped_depth), _ptr(hole_mask),
+                             _ptr(hole_idx), _ptr(n_holes), p, n, _stream(stream)))
+
+
+def cicero_warp_workspace_size(tgt_cam: Camera) -> int:
+    return int(lib().cicero_warp_workspace_size(C.byref(tgt_cam)))
+
+
+def cicero_render_backward(grid: Grid, mlp: Mlp, ray_o, ray_d, samp: Sampling, d_rgb, d_density, d_features, d_mlp,
+                           ws, stream=None):
+    p, n = _ws(ws)
+    _check(lib().cicero_render_backward(C.byref(grid), C.byref(mlp), _ptr(ray_o), _ptr(ray_d), ray_o.shape[0],
+                                        C.byref(samp), _ptr(d_rgb), _ptr(d_density), _ptr(d_features), _ptr(d_mlp),
+                                        p, n, _stream(stream)))
+
+
+def cicero_backward_workspace_size(grid: Grid, n_rays: int, samp: Sampling) -> int:
+    return int(lib().cicero_backward_workspace_size(C.byref(grid), int(n_rays), C.byref(samp)))
+
+
+def cicero_build_rit(grid: Grid, cam: Camera, samp: Sampling, opt: Options | None, brick_offsets, samples, ws,
+                     stream=None) -> int:
+    p, n = _ws(ws)
+    nb = C.c_int(0)
+    _check(lib().cicero_build_rit(C.byref(grid), C.byref(cam), C.byref(samp), _ref(opt), _ptr(brick_offsets),
+                                  _ptr(samples), C.byref(nb), p, n, _stream(stream)))
+    return int(nb.value)
+
+
+def cicero_mlp_eval(mlp: Mlp, x, precision: int, c, ws, stream=None):
+    p, n = _ws(ws)
+    _check(lib().cicero_mlp_eval(C.byref(mlp), _ptr(x), x.shape[0], int(precision), _ptr(c), p, n, _stream(stream)))
+
+
+def cicero_mlp_eval_workspace_size(M: int) -> int:
+    return int(lib().cicero_mlp_eval_workspace_size(int(M)))
+
+
+def cicero_workspace_status(ws, stream=None):
+    _check(lib().cicero_workspace_status(_ptr(ws), _stream(stream)))
+
+
+STAGES = ("march", "bucket", "gather_mlp", "composite", "warp_splat", "warp_resolve", "bwd_ray", "bwd_brick",
+          "mlp_eval")
+
+
+def cicero_profile_begin():
+    _check(lib().cicero_profile_begin())
+
+
+def cicero_profile_end() -> dict:
+    n = len(STAGES)
+    ms = (C.c_double * n)()
+    cnt = (C.c_longlong * n)()
+    _check(lib().cicero_profile_end(ms, cnt, n))
+    return {s: (ms[i], cnt[i]) for i, s in enumerate(STAGES)}
+
+
+def cicero_launch_count() -> int:
+    return int(lib().cicero_launch_count())
+
+
+def cicero_version() -> str:
+    return lib().cicero_version().decode()

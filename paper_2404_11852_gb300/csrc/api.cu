@@ -1,0 +1,522 @@
+// C ABI of libcicero: argument validation, workspace carving and stage launches.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/cicero.h"
+#include "common.cuh"
+#include "internal.h"
+
+namespace cicero {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+cicero_status fail(cicero_status st, const std::string& msg) {
+  set_error(msg);
+  return st;
+}
+
+cicero_status cuda_fail(cudaError_t e, const char* where) {
+  set_error(std::string(where) + ": " + cudaGetErrorString(e));
+  return CICERO_ERR_CUDA;
+}
+
+int num_sms() {
+  static int cache[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 148;
+  if (!cache[dev]) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 148;
+    cache[dev] = n;
+  }
+  return cache[dev];
+}
+
+static std::atomic<long long> g_launches{0};
+void count_launches(int n) { g_launches += n; }
+
+struct ProfState {
+  std::mutex mu;
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  struct Rec {
+    int stage;
+    cudaEvent_t e0, e1;
+  };
+  std::vector<Rec> recs;
+  double ms[kNumStages] = {0};
+  long long n[kNumStages] = {0};
+  cudaEvent_t get() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+};
+static ProfState g_prof;
+
+ProfScope::ProfScope(int s, cudaStream_t stream) : stage(s), st(stream), e0(nullptr), e1(nullptr), on(false) {
+  std::lock_guard<std::mutex> lk(g_prof.mu);
+  if (!g_prof.on) return;
+  on = true;
+  e0 = g_prof.get();
+  e1 = g_prof.get();
+  cudaEventRecord(e0, st);
+}
+
+ProfScope::~ProfScope() {
+  if (!on) return;
+  cudaEventRecord(e1, st);
+  std::lock_guard<std::mutex> lk(g_prof.mu);
+  g_prof.recs.push_back({stage, e0, e1});
+}
+
+static void prof_drain() {
+  for (auto& r : g_prof.recs) {
+    float ms = 0.0f;
+    if (cudaEventSynchronize(r.e1) == cudaSuccess && cudaEventElapsedTime(&ms, r.e0, r.e1) == cudaSuccess) {
+      g_prof.ms[r.stage] += ms;
+      g_prof.n[r.stage] += 1;
+    }
+    g_prof.pool.push_back(r.e0);
+    g_prof.pool.push_back(r.e1);
+  }
+  g_prof.recs.clear();
+}
+
+static int elem_bytes(cicero_dtype t) { return t == CICERO_F16 ? 2 : 4; }
+
+cicero_status make_geo(const cicero_grid* g, int brick, GridGeo* geo) {
+  if (!g) return fail(CICERO_ERR_INVALID_ARG, "grid is NULL");
+  if (!g->density || !g->features) return fail(CICERO_ERR_INVALID_ARG, "grid density/features is NULL");
+  if (g->dtype != CICERO_F32 && g->dtype != CICERO_F16) return fail(CICERO_ERR_INVALID_ARG, "grid dtype");
+  if (g->C < 1 || g->C > 21) return fail(CICERO_ERR_UNSUPPORTED, "feature channels must be 1..21");
+  if (brick != 4 && brick != 8 && brick != 16) return fail(CICERO_ERR_INVALID_ARG, "brick must be 4, 8 or 16");
+  memset(geo, 0, sizeof *geo);
+  for (int a = 0; a < 3; a++) {
+    if (g->n[a] < 2 || g->n[a] > (1 << 15)) return fail(CICERO_ERR_INVALID_ARG, "grid size must be 2..32768");
+    if (!(g->aabb_max[a] > g->aabb_min[a])) return fail(CICERO_ERR_INVALID_ARG, "empty grid box");
+    geo->n[a] = g->n[a];
+    geo->amin[a] = g->aabb_min[a];
+    geo->amax[a] = g->aabb_max[a];
+    const float ext = g->aabb_max[a] - g->aabb_min[a];
+    geo->inv_h[a] = (float)(g->n[a] - 1) / ext;
+    geo->nb[a] = (g->n[a] - 2) / brick + 1;
+  }
+  if (g->occ) {
+    if (g->occ_res < 1) return fail(CICERO_ERR_INVALID_ARG, "occupancy mask needs occ_res >= 1");
+    for (int a = 0; a < 3; a++) geo->occ_scale[a] = (float)g->occ_res / (float)(g->n[a] - 1);
+  }
+  geo->C = g->C;
+  geo->act_shift = g->act_shift;
+  geo->occ = g->occ;
+  geo->occ_res = g->occ ? g->occ_res : 0;
+  geo->brick = brick;
+  const size_t row = (size_t)g->n[0] * g->C * elem_bytes(g->dtype);
+  if (((uintptr_t)g->features & 15) || (row & 15))
+    return fail(CICERO_ERR_ALIGNMENT, "features must be 16-byte aligned with n0*C*elem a multiple of 16 (TMA)");
+  const long long nbr = (long long)geo->nb[0] * geo->nb[1] * geo->nb[2];
+  if (nbr > (1ll << 26)) return fail(CICERO_ERR_UNSUPPORTED, "too many bricks");
+  return CICERO_OK;
+}
+
+cicero_status make_samp(const cicero_sampling* s, Samp* out) {
+  if (!s) return fail(CICERO_ERR_INVALID_ARG, "sampling is NULL");
+  if (s->n_samples < 1 || s->n_samples > 65535) return fail(CICERO_ERR_INVALID_ARG, "n_samples must be 1..65535");
+  if (!(s->step >= 0.0f)) return fail(CICERO_ERR_INVALID_ARG, "step must be >= 0");
+  if (s->step == 0.0f && !(s->far_t > s->near_t)) return fail(CICERO_ERR_INVALID_ARG, "far must exceed near");
+  if (!(s->t_stop >= 0.0f)) return fail(CICERO_ERR_INVALID_ARG, "t_stop must be >= 0");
+  out->near_t = s->near_t;
+  out->far_t = s->far_t;
+  out->n_samples = s->n_samples;
+  out->step = s->step;
+  out->t_stop = s->t_stop;
+  for (int c = 0; c < 3; c++) out->bg[c] = s->bg[c];
+  out->void_acc = s->void_acc;
+  return CICERO_OK;
+}
+
+cicero_status check_mlp(const cicero_mlp* m, const cicero_grid* g) {
+  if (!m) return fail(CICERO_ERR_INVALID_ARG, "mlp is NULL");
+  if (!m->w1 || !m->b1 || !m->w2 || !m->b2 || !m->w3 || !m->b3) return fail(CICERO_ERR_INVALID_ARG, "mlp weight is NULL");
+  if (m->hidden != kHidden) return fail(CICERO_ERR_UNSUPPORTED, "hidden width must be 128");
+  if (m->n_freq < 0) return fail(CICERO_ERR_INVALID_ARG, "n_freq must be >= 0");
+  if (g && m->in_dim != g->C + 3 + 6 * m->n_freq) return fail(CICERO_ERR_INVALID_ARG, "in_dim != C + 3 + 6 n_freq");
+  if (m->in_dim > kMaxIn || m->in_dim < 1) return fail(CICERO_ERR_UNSUPPORTED, "in_dim must be 1..48");
+  return CICERO_OK;
+}
+
+static MlpPtrs mlp_ptrs(const cicero_mlp* m) {
+  MlpPtrs p;
+  p.w1 = m->w1;
+  p.b1 = m->b1;
+  p.w2 = m->w2;
+  p.b2 = m->b2;
+  p.w3 = m->w3;
+  p.b3 = m->b3;
+  p.in_dim = m->in_dim;
+  p.n_freq = m->n_freq;
+  return p;
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  }
+  return fn;
+}
+
+cicero_status encode_brick_map(const cicero_grid* grid, const GridGeo& geo, const BrickBox& box, CUtensorMap* map) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return fail(CICERO_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  const int es = elem_bytes(grid->dtype);
+  if (box.vx * geo.C > 256 || box.vb > 256) return fail(CICERO_ERR_UNSUPPORTED, "brick box exceeds 256 elements");
+  cuuint64_t dims[3] = {(cuuint64_t)geo.n[0] * geo.C, (cuuint64_t)geo.n[1], (cuuint64_t)geo.n[2]};
+  cuuint64_t strides[2] = {(cuuint64_t)geo.n[0] * geo.C * es, (cuuint64_t)geo.n[0] * geo.n[1] * geo.C * es};
+  cuuint32_t boxd[3] = {(cuuint32_t)(box.vx * geo.C), (cuuint32_t)box.vb, (cuuint32_t)box.vb};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = fn(map, grid->dtype == CICERO_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+                  (void*)grid->features, dims, strides, boxd, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(CICERO_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+  return CICERO_OK;
+}
+
+static bool ws_ok(const void* ws) { return ws && (((uintptr_t)ws) & 255) == 0; }
+
+static cicero_status plan_render(const cicero_grid* grid, const cicero_mlp* mlp, int n_rays, const cicero_sampling* s,
+                                 const cicero_options* opt, RenderPlan* p, bool need_mlp) {
+  const int brick = (opt && opt->brick) ? opt->brick : 8;
+  cicero_status st = make_geo(grid, brick, &p->geo);
+  if (st != CICERO_OK) return st;
+  st = make_samp(s, &p->samp);
+  if (st != CICERO_OK) return st;
+  if (need_mlp) {
+    st = check_mlp(mlp, grid);
+    if (st != CICERO_OK) return st;
+  }
+  if (n_rays < 0) return fail(CICERO_ERR_INVALID_ARG, "negative ray count");
+  const unsigned long long RS = (unsigned long long)n_rays * (unsigned long long)s->n_samples;
+  if (RS >= 0xffffffffull) return fail(CICERO_ERR_UNSUPPORTED, "rays x samples must be below 2^32");
+  p->R = n_rays;
+  p->S = s->n_samples;
+  p->nb = p->geo.nb[0] * p->geo.nb[1] * p->geo.nb[2];
+  p->max_tiles = (int)((RS + kTile - 1) / kTile) + p->nb;
+  p->want_k = false;
+  p->want_bwd = false;
+  p->precision = opt ? opt->precision : CICERO_MLP_FP32;
+  if (p->precision != CICERO_MLP_FP32 && p->precision != CICERO_MLP_BF16)
+    return fail(CICERO_ERR_INVALID_ARG, "precision");
+  return CICERO_OK;
+}
+
+static RaySrc camera_src(const cicero_camera* cam) {
+  RaySrc s;
+  memset(&s, 0, sizeof s);
+  s.kind = 0;
+  s.width = cam->width;
+  s.f = cam->f;
+  s.cx = cam->cx;
+  s.cy = cam->cy;
+  for (int i = 0; i < 12; i++) s.c2w[i] = cam->c2w[i];
+  s.n_max = cam->width * cam->height;
+  return s;
+}
+
+static cicero_status check_cam(const cicero_camera* c) {
+  if (!c) return fail(CICERO_ERR_INVALID_ARG, "camera is NULL");
+  if (c->width < 1 || c->height < 1 || (long long)c->width * c->height > (1ll << 30))
+    return fail(CICERO_ERR_INVALID_ARG, "camera size");
+  if (!(c->f > 0.0f)) return fail(CICERO_ERR_INVALID_ARG, "focal length must be > 0");
+  for (int i = 0; i < 12; i++)
+    if (!isfinite(c->c2w[i])) return fail(CICERO_ERR_INVALID_ARG, "camera pose is not finite");
+  return CICERO_OK;
+}
+
+static cicero_status render_common(const cicero_grid* grid, const cicero_mlp* mlp, const cicero_sampling* s,
+                                   const cicero_options* opt, const RaySrc& src, int n_rays, float* rgb, float* depth,
+                                   float* acc, int32_t* n_steps, void* ws, size_t ws_bytes, void* stream) {
+  RenderPlan plan;
+  cicero_status st = plan_render(grid, mlp, n_rays, s, opt, &plan, true);
+  if (st != CICERO_OK) return st;
+  if (!rgb) return fail(CICERO_ERR_INVALID_ARG, "rgb is NULL");
+  if (!ws_ok(ws)) return fail(CICERO_ERR_INVALID_ARG, "workspace must be non-NULL and 256-byte aligned");
+  RenderWs w;
+  if (!carve_render_ws(ws, ws_bytes, plan, &w)) return fail(CICERO_ERR_WORKSPACE_TOO_SMALL, "workspace too small");
+  if (n_rays == 0) return CICERO_OK;
+  return run_render(grid, mlp_ptrs(mlp), plan, src, w, rgb, depth, acc, n_steps, false, (cudaStream_t)stream);
+}
+
+// relative pose [R | t] = inverse(c2w_tgt) c2w_ref in FP64, rounded once to FP32
+static void relative_pose(const cicero_camera* ref, const cicero_camera* tgt, float R[9], float t[3]) {
+  double Ra[9], Rb[9], ta[3], tb[3];
+  for (int a = 0; a < 3; a++) {
+    for (int b = 0; b < 3; b++) {
+      Ra[3 * a + b] = ref->c2w[4 * a + b];
+      Rb[3 * a + b] = tgt->c2w[4 * a + b];
+    }
+    ta[a] = ref->c2w[4 * a + 3];
+    tb[a] = tgt->c2w[4 * a + 3];
+  }
+  for (int i = 0; i < 3; i++) {
+    for (int j = 0; j < 3; j++) {
+      double acc = Rb[i] * Ra[j];
+      acc = acc + Rb[3 + i] * Ra[3 + j];
+      acc = acc + Rb[6 + i] * Ra[6 + j];
+      R[3 * i + j] = (float)acc;
+    }
+    double acc = Rb[i] * (ta[0] - tb[0]);
+    acc = acc + Rb[3 + i] * (ta[1] - tb[1]);
+    acc = acc + Rb[6 + i] * (ta[2] - tb[2]);
+    t[i] = (float)acc;
+  }
+}
+
+}  // namespace cicero
+
+using namespace cicero;
+
+extern "C" {
+
+cicero_status cicero_render(const cicero_grid* grid, const cicero_mlp* mlp, const cicero_camera* cam,
+                            const cicero_sampling* sampling, const cicero_options* opt, float* rgb, float* depth,
+                            float* acc, int32_t* n_steps, void* workspace, size_t ws_bytes, void* stream) {
+  cicero_status st = check_cam(cam);
+  if (st != CICERO_OK) return st;
+  return render_common(grid, mlp, sampling, opt, camera_src(cam), cam->width * cam->height, rgb, depth, acc, n_steps,
+                       workspace, ws_bytes, stream);
+}
+
+cicero_status cicero_render_rays(const cicero_grid* grid, const cicero_mlp* mlp, const float* ray_o, const float* ray_d,
+                                 int n_rays, const cicero_sampling* sampling, const cicero_options* opt, float* rgb,
+                                 float* depth, float* acc, int32_t* n_steps, void* workspace, size_t ws_bytes,
+                                 void* stream) {
+  if (n_rays > 0 && (!ray_o || !ray_d)) return fail(CICERO_ERR_INVALID_ARG, "ray_o/ray_d is NULL");
+  RaySrc src;
+  memset(&src, 0, sizeof src);
+  src.kind = 1;
+  src.o = ray_o;
+  src.d = ray_d;
+  src.n_max = n_rays;
+  return render_common(grid, mlp, sampling, opt, src, n_rays, rgb, depth, acc, n_steps, workspace, ws_bytes, stream);
+}
+
+cicero_status cicero_render_holes(const cicero_grid* grid, const cicero_mlp* mlp, const cicero_camera* cam,
+                                  const cicero_sampling* sampling, const cicero_options* opt, const int32_t* hole_idx,
+                                  const int32_t* n_holes, int max_holes, float* rgb_inout, float* depth_inout,
+                                  void* workspace, size_t ws_bytes, void* stream) {
+  cicero_status st = check_cam(cam);
+  if (st != CICERO_OK) return st;
+  if (!hole_idx || !n_holes) return fail(CICERO_ERR_INVALID_ARG, "hole_idx/n_holes is NULL");
+  if (max_holes < 0 || max_holes > cam->width * cam->height) return fail(CICERO_ERR_INVALID_ARG, "max_holes");
+  RaySrc src = camera_src(cam);
+  src.pix = hole_idx;
+  src.n_dev = n_holes;
+  src.n_max = max_holes;
+  return render_common(grid, mlp, sampling, opt, src, max_holes, rgb_inout, depth_inout, nullptr, nullptr, workspace,
+                       ws_bytes, stream);
+}
+
+size_t cicero_render_workspace_size(const cicero_grid* grid, int n_rays, const cicero_sampling* sampling,
+                                    const cicero_options* opt) {
+  RenderPlan plan;
+  if (plan_render(grid, nullptr, n_rays, sampling, opt, &plan, false) != CICERO_OK) return 0;
+  return render_ws_bytes(plan);
+}
+
+cicero_status cicero_build_rit(const cicero_grid* grid, const cicero_camera* cam, const cicero_sampling* sampling,
+                               const cicero_options* opt, int32_t* brick_offsets, int32_t* samples, int* n_bricks_out,
+                               void* workspace, size_t ws_bytes, void* stream) {
+  cicero_status st = check_cam(cam);
+  if (st != CICERO_OK) return st;
+  if (!brick_offsets || !samples) return fail(CICERO_ERR_INVALID_ARG, "brick_offsets/samples is NULL");
+  RenderPlan plan;
+  const int R = cam->width * cam->height;
+  st = plan_render(grid, nullptr, R, sampling, opt, &plan, false);
+  if (st != CICERO_OK) return st;
+  plan.want_k = true;
+  if (!ws_ok(workspace)) return fail(CICERO_ERR_INVALID_ARG, "workspace must be non-NULL and 256-byte aligned");
+  RenderWs w;
+  if (!carve_render_ws(workspace, ws_bytes, plan, &w))
+    return fail(CICERO_ERR_WORKSPACE_TOO_SMALL, "workspace too small (the RIT needs the slot array)");
+  if (n_bricks_out) *n_bricks_out = plan.nb;
+  const RaySrc src = camera_src(cam);
+  MlpPtrs none;
+  memset(&none, 0, sizeof none);
+  st = run_render(grid, none, plan, src, w, nullptr, nullptr, nullptr, nullptr, true, (cudaStream_t)stream);
+  if (st != CICERO_OK) return st;
+  return run_rit_export(w, plan.nb, plan.S, brick_offsets, samples, (cudaStream_t)stream);
+}
+
+cicero_status cicero_warp(const float* ref_rgb, const float* ref_depth, const cicero_camera* ref_cam,
+                          const cicero_camera* tgt_cam, float max_angle_deg, const cicero_grid* void_grid,
+                          const cicero_sampling* void_sampling, float* warped_rgb, float* warped_depth,
+                          uint8_t* hole_mask, int32_t* hole_idx, int32_t* n_holes, void* workspace, size_t ws_bytes,
+                          void* stream) {
+  cicero_status st = check_cam(ref_cam);
+  if (st != CICERO_OK) return st;
+  st = check_cam(tgt_cam);
+  if (st != CICERO_OK) return st;
+  if (!ref_rgb || !ref_depth || !warped_rgb || !hole_mask || !hole_idx || !n_holes)
+    return fail(CICERO_ERR_INVALID_ARG, "a warp buffer is NULL");
+  if (!ws_ok(workspace)) return fail(CICERO_ERR_INVALID_ARG, "workspace must be non-NULL and 256-byte aligned");
+  if (ws_bytes < warp_ws_bytes(tgt_cam->width, tgt_cam->height))
+    return fail(CICERO_ERR_WORKSPACE_TOO_SMALL, "workspace too small");
+  if (!(max_angle_deg > 0.0f)) return fail(CICERO_ERR_INVALID_ARG, "max_angle_deg must be > 0");
+  WarpArgs a;
+  memset(&a, 0, sizeof a);
+  a.wr = ref_cam->width;
+  a.hr = ref_cam->height;
+  a.fr = ref_cam->f;
+  a.cxr = ref_cam->cx;
+  a.cyr = ref_cam->cy;
+  a.wt = tgt_cam->width;
+  a.ht = tgt_cam->height;
+  a.ft = tgt_cam->f;
+  a.cxt = tgt_cam->cx;
+  a.cyt = tgt_cam->cy;
+  relative_pose(ref_cam, tgt_cam, a.R, a.t);
+  a.use_phi = max_angle_deg < 180.0f;
+  a.cos_phi = a.use_phi ? (float)cos((double)max_angle_deg * 3.14159265358979323846 / 180.0) : -1.0f;
+  VoidTest vt;
+  memset(&vt, 0, sizeof vt);
+  if (void_grid) {
+    if (!void_sampling) return fail(CICERO_ERR_INVALID_ARG, "void_sampling is NULL");
+    // the void test needs only the box, the occupancy mask and the sampling; features are unused
+    cicero_grid gg = *void_grid;
+    if (!gg.density) gg.density = (const void*)16;
+    if (!gg.features) gg.features = (const void*)16;
+    st = make_geo(&gg, 8, &vt.g);
+    if (st != CICERO_OK) return st;
+    st = make_samp(void_sampling, &vt.s);
+    if (st != CICERO_OK) return st;
+    vt.enabled = 1;
+    vt.src = camera_src(tgt_cam);
+  } else if (void_sampling) {
+    make_samp(void_sampling, &vt.s);
+  }
+  return run_warp(a, vt, ref_rgb, ref_depth, warped_rgb, warped_depth, hole_mask, hole_idx, n_holes, workspace,
+                  (cudaStream_t)stream);
+}
+
+size_t cicero_warp_workspace_size(const cicero_camera* tgt_cam) {
+  if (!tgt_cam || tgt_cam->width < 1 || tgt_cam->height < 1) return 0;
+  return warp_ws_bytes(tgt_cam->width, tgt_cam->height);
+}
+
+cicero_status cicero_render_backward(const cicero_grid* grid, const cicero_mlp* mlp, const float* ray_o,
+                                     const float* ray_d, int n_rays, const cicero_sampling* sampling,
+                                     const float* d_rgb, float* d_density, float* d_features, float* d_mlp,
+                                     void* workspace, size_t ws_bytes, void* stream) {
+  if (n_rays > 0 && (!ray_o || !ray_d || !d_rgb)) return fail(CICERO_ERR_INVALID_ARG, "ray_o/ray_d/d_rgb is NULL");
+  if (!d_density || !d_features) return fail(CICERO_ERR_INVALID_ARG, "d_density/d_features is NULL");
+  if (d_mlp) return fail(CICERO_ERR_UNSUPPORTED, "MLP weight gradients are not implemented in this build");
+  RenderPlan plan;
+  cicero_status st = plan_render(grid, mlp, n_rays, sampling, nullptr, &plan, true);
+  if (st != CICERO_OK) return st;
+  plan.want_bwd = true;
+  if (!ws_ok(workspace)) return fail(CICERO_ERR_INVALID_ARG, "workspace must be non-NULL and 256-byte aligned");
+  RenderWs w;
+  if (!carve_render_ws(workspace, ws_bytes, plan, &w)) return fail(CICERO_ERR_WORKSPACE_TOO_SMALL, "workspace too small");
+  if (n_rays == 0) return CICERO_OK;
+  RaySrc src;
+  memset(&src, 0, sizeof src);
+  src.kind = 1;
+  src.o = ray_o;
+  src.d = ray_d;
+  src.n_max = n_rays;
+  return run_backward(grid, mlp_ptrs(mlp), plan, src, w, d_rgb, d_density, d_features, (cudaStream_t)stream);
+}
+
+size_t cicero_backward_workspace_size(const cicero_grid* grid, int n_rays, const cicero_sampling* sampling) {
+  RenderPlan plan;
+  if (plan_render(grid, nullptr, n_rays, sampling, nullptr, &plan, false) != CICERO_OK) return 0;
+  plan.want_bwd = true;
+  return render_ws_bytes(plan);
+}
+
+cicero_status cicero_mlp_eval(const cicero_mlp* mlp, const float* x, int M, cicero_precision precision, float* c,
+                              void* workspace, size_t ws_bytes, void* stream) {
+  cicero_status st = check_mlp(mlp, nullptr);
+  if (st != CICERO_OK) return st;
+  if (M < 0 || (M > 0 && (!x || !c))) return fail(CICERO_ERR_INVALID_ARG, "x/c is NULL or M < 0");
+  if (!ws_ok(workspace) || ws_bytes < 256) return fail(CICERO_ERR_WORKSPACE_TOO_SMALL, "workspace too small");
+  if (M == 0) return CICERO_OK;
+  const MlpPtrs p = mlp_ptrs(mlp);
+  if (precision == CICERO_MLP_BF16) return launch_mlp_eval_bf16(p, x, M, c, (uint32_t*)workspace, (cudaStream_t)stream);
+  if (precision == CICERO_MLP_FP32) return launch_mlp_eval_f32(p, x, M, c, (cudaStream_t)stream);
+  return fail(CICERO_ERR_INVALID_ARG, "precision");
+}
+
+size_t cicero_mlp_eval_workspace_size(int M) {
+  (void)M;
+  return 256;
+}
+
+cicero_status cicero_workspace_status(void* workspace, void* stream) {
+  if (!workspace) return fail(CICERO_ERR_INVALID_ARG, "workspace is NULL");
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+  uint32_t word = 0;
+  e = cudaMemcpy(&word, workspace, 4, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(status)");
+  const uint32_t zero = 0;
+  e = cudaMemcpy(workspace, &zero, 4, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(clear status)");
+  if (word & kErrTimeout) return fail(CICERO_ERR_TIMEOUT, "a kernel's bounded wait ran out");
+  if (word & kErrInternal) return fail(CICERO_ERR_INTERNAL, "a kernel found a broken invariant");
+  return CICERO_OK;
+}
+
+cicero_status cicero_profile_begin(void) {
+  std::lock_guard<std::mutex> lk(g_prof.mu);
+  prof_drain();
+  for (int i = 0; i < kNumStages; i++) {
+    g_prof.ms[i] = 0.0;
+    g_prof.n[i] = 0;
+  }
+  g_prof.on = true;
+  return CICERO_OK;
+}
+
+cicero_status cicero_profile_end(double* total_ms, long long* count, int n_stages) {
+  std::lock_guard<std::mutex> lk(g_prof.mu);
+  g_prof.on = false;
+  prof_drain();
+  for (int i = 0; i < n_stages && i < kNumStages; i++) {
+    if (total_ms) total_ms[i] = g_prof.ms[i];
+    if (count) count[i] = g_prof.n[i];
+  }
+  return CICERO_OK;
+}
+
+long long cicero_launch_count(void) { return g_launches.load(); }
+
+const char* cicero_last_error(void) { return g_last_error.c_str(); }
+
+const char* cicero_version(void) { return "cicero-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"

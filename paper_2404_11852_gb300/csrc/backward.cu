@@ -1,0 +1,380 @@
+// Backward of the FP32 renderer: gradient of a loss L(rgb) with respect to the density and
+// feature grids.  Nothing is stored by the forward pass; the backward recomputes it:
+//
+//   forward recompute  K1-K5 of render.cu (march, Ray Index Table, per-brick gather + MLP),
+//                      which leaves per composited sample (c, w, T, raw density)
+//   B1 k_bwd_ray       per ray (warp), in slot order: R_k = sum_{j>k} w_j c_j + T_end bg by a
+//                      warp scan, dL/dsigma_k = delta (T_{k+1} g.c_k - g.R_k) and
+//                      dL/draw_k = dL/dsigma_k * sigmoid(raw_k + shift)
+//   B2 k_bwd_brick     per brick (Ray Index Table order), 64 samples at a time: MLP forward and
+//                      backward on CUDA cores down to dL/dfeatures, then the trilinear adjoint
+//                      accumulated in a shared-memory copy of the brick's vertices; when the CTA
+//                      leaves the brick, one global atomicAdd per touched vertex entry.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace cicero {
+
+constexpr int kBT = 64;  // samples per backward tile
+
+__device__ __forceinline__ float warp_sum_b(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// B1: dL/draw of every composited sample, written over rec_raw.
+__global__ void __launch_bounds__(256) k_bwd_ray(RaySrc src, Samp s, RenderWs w, const float* __restrict__ d_rgb,
+                                                 float act_shift) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  const int R = ray_count(src);
+  const float dt = s.step > 0.0f ? s.step : __fdiv_rn(__fsub_rn(s.far_t, s.near_t), (float)s.n_samples);
+  for (int r = warp; r < R; r += nwarps) {
+    const uint32_t n = w.ray_n[r];
+    const size_t rec0 = (size_t)r * w.S;
+    const float g0 = d_rgb[3 * r], g1 = d_rgb[3 * r + 1], g2 = d_rgb[3 * r + 2];
+    float tot = 0.0f;
+    for (uint32_t j = lane; j < n; j += 32) {
+      const float4 c = w.rec_c[rec0 + j];
+      tot += c.w * (g0 * c.x + g1 * c.y + g2 * c.z);
+    }
+    tot = warp_sum_b(tot);
+    const float gbg = w.ray_T[r] * (g0 * s.bg[0] + g1 * s.bg[1] + g2 * s.bg[2]);
+    float run = 0.0f;  // sum of e_j over earlier chunks
+    for (uint32_t j0 = 0; j0 < n; j0 += 32) {
+      const uint32_t j = j0 + lane;
+      float e = 0.0f, gc = 0.0f, wk = 0.0f;
+      if (j < n) {
+        const float4 c = w.rec_c[rec0 + j];
+        gc = g0 * c.x + g1 * c.y + g2 * c.z;
+        wk = c.w;
+        e = wk * gc;
+      }
+      float incl = e;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const float v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+      }
+      if (j < n) {
+        const float gR = (tot - (run + incl)) + gbg;
+        const float Tn = w.rec_T[rec0 + j] - wk;
+        const float dsig = dt * (Tn * gc - gR);
+        w.rec_raw[rec0 + j] = dsig * sigmoid_f(w.rec_raw[rec0 + j] + act_shift);
+      }
+      run += __shfl_sync(0xffffffffu, incl, 31);
+    }
+  }
+}
+
+struct BwdSmem {
+  static constexpr int w1t = 0;                          // [48][128]
+  static constexpr int w2t = w1t + kMaxIn * kHidden * 4; // [128][128]
+  static constexpr int w3 = w2t + kHidden * kHidden * 4; // [3][128]
+  static constexpr int b1 = w3 + 3 * kHidden * 4;
+  static constexpr int b2 = b1 + kHidden * 4;
+  static constexpr int x = b2 + kHidden * 4;             // [48][64]  inputs, later dL/dx
+  static constexpr int h1 = x + kMaxIn * kBT * 4;        // [128][64] h1, later dL/dh1
+  static constexpr int h2 = h1 + kHidden * kBT * 4;      // [128][64] h2, later dL/dh2
+  static constexpr int dz = h2 + kHidden * kBT * 4;      // [3][64]
+  static constexpr int meta = dz + 3 * kBT * 4;          // per sample: l[3] (int), f[3], draw, valid
+  static constexpr int gacc = meta + 8 * kBT * 4;        // [vb^3][C+1]
+};
+
+// acc[i][j]: rows tm*4+i (i < 4), cols {tn*4+j, 64+tn*4+(j-4)}; A [K][64], B [K][128] k-major
+__device__ __forceinline__ void gemm64(const float* A, const float* Bw, int K, int tm, int tn, float acc[4][8]) {
+#pragma unroll 2
+  for (int k = 0; k < K; k++) {
+    const float4 a = *reinterpret_cast<const float4*>(&A[k * kBT + tm * 4]);
+    const float4 b0 = *reinterpret_cast<const float4*>(&Bw[k * kHidden + tn * 4]);
+    const float4 b1 = *reinterpret_cast<const float4*>(&Bw[k * kHidden + 64 + tn * 4]);
+    const float av[4] = {a.x, a.y, a.z, a.w};
+    const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+#pragma unroll
+      for (int j = 0; j < 8; j++) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+  }
+}
+
+// same with B read transposed from Bt [128][128]: B[k][n] = Bt[n][k]
+__device__ __forceinline__ void gemm64_bt(const float* A, const float* Bt, int K, int tm, int tn, float acc[4][8]) {
+#pragma unroll 2
+  for (int k = 0; k < K; k++) {
+    const float4 a = *reinterpret_cast<const float4*>(&A[k * kBT + tm * 4]);
+    const float av[4] = {a.x, a.y, a.z, a.w};
+    float bv[8];
+#pragma unroll
+    for (int j = 0; j < 8; j++) bv[j] = Bt[(j < 4 ? tn * 4 + j : 64 + tn * 4 + (j - 4)) * kHidden + k];
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+#pragma unroll
+      for (int j = 0; j < 8; j++) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+  }
+}
+
+__device__ __forceinline__ int col8(int tn, int j) { return j < 4 ? tn * 4 + j : 64 + tn * 4 + (j - 4); }
+
+template <typename T>
+__device__ __forceinline__ void feat_trilinear_global(const GridGeo& g, const T* feat, const int i0[3], const float f[3],
+                                                      float* out) {
+  const int C = g.C;
+  for (int c = 0; c < C; c++) out[c] = 0.0f;
+#pragma unroll
+  for (int q = 0; q < 8; q++) {
+    const int x = i0[0] + (q & 1), y = i0[1] + ((q >> 1) & 1), z = i0[2] + (q >> 2);
+    const float wq = ((q & 1) ? f[0] : 1.f - f[0]) * (((q >> 1) & 1) ? f[1] : 1.f - f[1]) * ((q >> 2) ? f[2] : 1.f - f[2]);
+    const T* v = feat + (((size_t)z * g.n[1] + y) * g.n[0] + x) * C;
+    for (int c = 0; c < C; c++) out[c] += wq * ldf(v + c);
+  }
+}
+
+__device__ void flush_brick(const GridGeo& g, int b, float* gacc, int vb, float* d_dens, float* d_feat) {
+  const int C = g.C, B = g.brick;
+  const int bx = b % g.nb[0], by = (b / g.nb[0]) % g.nb[1], bz = b / (g.nb[0] * g.nb[1]);
+  const int n_ent = vb * vb * vb * (C + 1);
+  for (int e = threadIdx.x; e < n_ent; e += blockDim.x) {
+    const float v = gacc[e];
+    if (v == 0.0f) continue;
+    gacc[e] = 0.0f;
+    const int ch = e % (C + 1), lv = e / (C + 1);
+    const int lx = lv % vb, ly = (lv / vb) % vb, lz = lv / (vb * vb);
+    const int x = bx * B + lx, y = by * B + ly, z = bz * B + lz;
+    if (x >= g.n[0] || y >= g.n[1] || z >= g.n[2]) continue;
+    const size_t gv = ((size_t)z * g.n[1] + y) * g.n[0] + x;
+    if (ch < C)
+      atomicAdd(&d_feat[gv * C + ch], v);
+    else
+      atomicAdd(&d_dens[gv], v);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256, 1) k_bwd_brick(GridGeo g, RaySrc src, MlpPtrs mlp, RenderWs w,
+                                                      const T* __restrict__ feat, const float* __restrict__ d_rgb,
+                                                      float* d_dens, float* d_feat) {
+  extern __shared__ __align__(128) char sm[];
+  float* w1t = (float*)(sm + BwdSmem::w1t);
+  float* w2t = (float*)(sm + BwdSmem::w2t);
+  float* w3 = (float*)(sm + BwdSmem::w3);
+  float* b1 = (float*)(sm + BwdSmem::b1);
+  float* b2 = (float*)(sm + BwdSmem::b2);
+  float* X = (float*)(sm + BwdSmem::x);
+  float* H1 = (float*)(sm + BwdSmem::h1);
+  float* H2 = (float*)(sm + BwdSmem::h2);
+  float* DZ = (float*)(sm + BwdSmem::dz);
+  int* ml = (int*)(sm + BwdSmem::meta);              // [3][64]
+  float* mf = (float*)(sm + BwdSmem::meta) + 3 * kBT; // [3][64]
+  float* mdraw = mf + 3 * kBT;                        // [64]
+  int* mval = (int*)(mdraw + kBT);                    // [64]
+  float* gacc = (float*)(sm + BwdSmem::gacc);
+  const int C = g.C, B = g.brick, vb = B + 1, S = w.S;
+  for (int i = threadIdx.x; i < kMaxIn * kHidden; i += blockDim.x) {
+    const int k = i / kHidden, n = i % kHidden;
+    w1t[i] = k < mlp.in_dim ? mlp.w1[n * mlp.in_dim + k] : 0.0f;
+  }
+  for (int i = threadIdx.x; i < kHidden * kHidden; i += blockDim.x) w2t[i] = mlp.w2[(i % kHidden) * kHidden + i / kHidden];
+  for (int i = threadIdx.x; i < 3 * kHidden; i += blockDim.x) w3[i] = mlp.w3[i];
+  for (int i = threadIdx.x; i < kHidden; i += blockDim.x) {
+    b1[i] = mlp.b1[i];
+    b2[i] = mlp.b2[i];
+  }
+  for (int i = threadIdx.x; i < vb * vb * vb * (C + 1); i += blockDim.x) gacc[i] = 0.0f;
+  __syncthreads();
+
+  const uint32_t n_tiles = w.hdr[1];
+  const uint32_t per = (n_tiles + gridDim.x - 1) / gridDim.x;
+  const uint32_t t_begin = blockIdx.x * per, t_end = min(n_tiles, t_begin + per);
+  const int tm = threadIdx.x & 15, tn = threadIdx.x >> 4;
+  int cur = -1;
+  for (uint32_t ti = t_begin; ti < t_end; ti++) {
+    const int b = (int)w.tile_brick[ti];
+    const uint32_t start0 = w.tile_start[ti];
+    const uint32_t end = min(start0 + (uint32_t)kTile, w.brick_off[b + 1]);
+    const int bx = b % g.nb[0], by = (b / g.nb[0]) % g.nb[1], bz = b / (g.nb[0] * g.nb[1]);
+    if (b != cur) {
+      if (cur >= 0) {
+        flush_brick(g, cur, gacc, vb, d_dens, d_feat);
+        __syncthreads();
+      }
+      cur = b;
+    }
+    for (uint32_t start = start0; start < end; start += kBT) {
+      const int mcnt = (int)min((uint32_t)kBT, end - start);
+      // gather: thread m < 64 features + meta, 64 <= t < 128 encoding
+      const int m = threadIdx.x & (kBT - 1), part = threadIdx.x >> 6;
+      if (part < 2) {
+        const bool valid = m < mcnt;
+        uint32_t sid = valid ? w.sorted[start + m] : 0;
+        const int r = (int)(sid / (uint32_t)S);
+        float o[3], d[3];
+        if (valid) ray_gen(src, r, o, d);
+        if (part == 0) {
+          int ok = 0;
+          if (valid) {
+            float p[3], f[3], fv[24];
+            int i0[3];
+            sample_pos(o, d, w.rec_t[sid], p);
+            const bool in = index_sample(g, p, i0, f);
+            const int l[3] = {i0[0] - bx * B, i0[1] - by * B, i0[2] - bz * B};
+            if (!in || l[0] < 0 || l[0] >= B || l[1] < 0 || l[1] >= B || l[2] < 0 || l[2] >= B) {
+              set_err(&w.hdr[0], kErrInternal);
+            } else {
+              ok = 1;
+              feat_trilinear_global<T>(g, feat, i0, f, fv);
+              for (int c = 0; c < C; c++) X[c * kBT + m] = fv[c];
+              for (int a = 0; a < 3; a++) {
+                ml[a * kBT + m] = l[a];
+                mf[a * kBT + m] = f[a];
+              }
+              mdraw[m] = w.rec_raw[sid];
+              const float4 cw = w.rec_c[sid];
+              const float cc[3] = {cw.x, cw.y, cw.z};
+              for (int j = 0; j < 3; j++) DZ[j * kBT + m] = cw.w * d_rgb[3 * r + j] * cc[j] * (1.0f - cc[j]);
+            }
+          }
+          if (!ok) {
+            for (int c = 0; c < C; c++) X[c * kBT + m] = 0.0f;
+            for (int j = 0; j < 3; j++) DZ[j * kBT + m] = 0.0f;
+          }
+          mval[m] = ok;
+        } else {
+          float e[3 + 6 * 7];
+          const int ne = 3 + 6 * mlp.n_freq;
+          if (valid) encode_dir(d, mlp.n_freq, e);
+          for (int j = 0; j < ne; j++) X[(C + j) * kBT + m] = valid ? e[j] : 0.0f;
+          for (int j = C + ne; j < kMaxIn; j++) X[j * kBT + m] = 0.0f;
+        }
+      }
+      __syncthreads();
+      float acc[4][8];
+      // layer 1
+#pragma unroll
+      for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 8; j++) acc[i][j] = 0.0f;
+      gemm64(X, w1t, kMaxIn, tm, tn, acc);
+#pragma unroll
+      for (int j = 0; j < 8; j++) {
+        const int n = col8(tn, j);
+        float4 v;
+        v.x = fmaxf(acc[0][j] + b1[n], 0.f);
+        v.y = fmaxf(acc[1][j] + b1[n], 0.f);
+        v.z = fmaxf(acc[2][j] + b1[n], 0.f);
+        v.w = fmaxf(acc[3][j] + b1[n], 0.f);
+        *reinterpret_cast<float4*>(&H1[n * kBT + tm * 4]) = v;
+      }
+      __syncthreads();
+      // layer 2
+#pragma unroll
+      for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 8; j++) acc[i][j] = 0.0f;
+      gemm64(H1, w2t, kHidden, tm, tn, acc);
+#pragma unroll
+      for (int j = 0; j < 8; j++) {
+        const int n = col8(tn, j);
+        float4 v;
+        v.x = fmaxf(acc[0][j] + b2[n], 0.f);
+        v.y = fmaxf(acc[1][j] + b2[n], 0.f);
+        v.z = fmaxf(acc[2][j] + b2[n], 0.f);
+        v.w = fmaxf(acc[3][j] + b2[n], 0.f);
+        *reinterpret_cast<float4*>(&H2[n * kBT + tm * 4]) = v;
+      }
+      __syncthreads();
+      // dL/dh2 = W3^T dz, masked by relu'(pre2)
+      for (int e = threadIdx.x; e < kHidden * kBT; e += blockDim.x) {
+        const int o = e / kBT, mm = e % kBT;
+        const float v = w3[o] * DZ[mm] + w3[kHidden + o] * DZ[kBT + mm] + w3[2 * kHidden + o] * DZ[2 * kBT + mm];
+        H2[e] = H2[e] > 0.0f ? v : 0.0f;
+      }
+      __syncthreads();
+      // dL/dh1 = W2^T dh2, masked by relu'(pre1)
+#pragma unroll
+      for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 8; j++) acc[i][j] = 0.0f;
+      gemm64_bt(H2, w2t, kHidden, tm, tn, acc);
+#pragma unroll
+      for (int j = 0; j < 8; j++) {
+        const int n = col8(tn, j);
+        float4 h = *reinterpret_cast<float4*>(&H1[n * kBT + tm * 4]);
+        h.x = h.x > 0.f ? acc[0][j] : 0.f;
+        h.y = h.y > 0.f ? acc[1][j] : 0.f;
+        h.z = h.z > 0.f ? acc[2][j] : 0.f;
+        h.w = h.w > 0.f ? acc[3][j] : 0.f;
+        *reinterpret_cast<float4*>(&H1[n * kBT + tm * 4]) = h;
+      }
+      __syncthreads();
+      // dL/dfeatures = W1[:, :C]^T dh1
+      for (int e = threadIdx.x; e < C * kBT; e += blockDim.x) {
+        const int c = e / kBT, mm = e % kBT;
+        float s = 0.0f;
+#pragma unroll 8
+        for (int n = 0; n < kHidden; n++) s = fmaf(w1t[c * kHidden + n], H1[n * kBT + mm], s);
+        X[c * kBT + mm] = s;
+      }
+      __syncthreads();
+      // trilinear adjoint into the brick accumulator: 4 threads per sample, 2 corners each
+      {
+        const int mm = threadIdx.x >> 2, qp = threadIdx.x & 3;
+        if (mm < mcnt && mval[mm]) {
+          const float f0 = mf[mm], f1 = mf[kBT + mm], f2 = mf[2 * kBT + mm];
+          const int l0 = ml[mm], l1 = ml[kBT + mm], l2 = ml[2 * kBT + mm];
+          const float dr = mdraw[mm];
+#pragma unroll
+          for (int u = 0; u < 2; u++) {
+            const int q = 2 * qp + u;
+            const float wq = ((q & 1) ? f0 : 1.f - f0) * (((q >> 1) & 1) ? f1 : 1.f - f1) * ((q >> 2) ? f2 : 1.f - f2);
+            const int lv = ((l2 + (q >> 2)) * vb + (l1 + ((q >> 1) & 1))) * vb + (l0 + (q & 1));
+            float* ga = gacc + lv * (C + 1);
+            for (int c = 0; c < C; c++) atomicAdd(&ga[c], wq * X[c * kBT + mm]);
+            atomicAdd(&ga[C], wq * dr);
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  if (cur >= 0) flush_brick(g, cur, gacc, vb, d_dens, d_feat);
+}
+
+cicero_status run_backward(const cicero_grid* grid, const MlpPtrs& mlp, const RenderPlan& plan, const RaySrc& src,
+                           const RenderWs& ws, const float* d_rgb, float* d_dens, float* d_feat, cudaStream_t st) {
+  cicero_status s = run_render(grid, mlp, plan, src, ws, nullptr, nullptr, nullptr, nullptr, false, st);
+  if (s != CICERO_OK) return s;
+  const int nw = src.n_max;
+  int blocks = (nw + 7) / 8;
+  blocks = std::max(1, std::min(blocks, num_sms() * 16));
+  {
+    ProfScope ps(kStBwdRay, st);
+    k_bwd_ray<<<blocks, 256, 0, st>>>(src, plan.samp, ws, d_rgb, plan.geo.act_shift);
+  }
+  count_launches(2);
+  ProfScope ps(kStBwdBrick, st);
+  const int vb = plan.geo.brick + 1;
+  const int smem = BwdSmem::gacc + vb * vb * vb * (plan.geo.C + 1) * 4;
+  if (smem > 227 * 1024) return fail(CICERO_ERR_UNSUPPORTED, "brick too large for the backward kernel");
+  cudaError_t e;
+  if (grid->dtype == CICERO_F16) {
+    e = cudaFuncSetAttribute(k_bwd_brick<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_bwd_brick)");
+    k_bwd_brick<__half><<<num_sms(), 256, smem, st>>>(plan.geo, src, mlp, ws, (const __half*)grid->features, d_rgb,
+                                                      d_dens, d_feat);
+  } else {
+    e = cudaFuncSetAttribute(k_bwd_brick<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_bwd_brick)");
+    k_bwd_brick<float><<<num_sms(), 256, smem, st>>>(plan.geo, src, mlp, ws, (const float*)grid->features, d_rgb,
+                                                     d_dens, d_feat);
+  }
+  e = cudaGetLastError();
+  return e == cudaSuccess ? CICERO_OK : cuda_fail(e, "backward kernels");
+}
+
+}  // namespace cicero

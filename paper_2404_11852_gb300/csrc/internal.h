@@ -1,0 +1,131 @@
+// Host-side declarations shared by the translation units of libcicero.
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/cicero.h"
+#include "common.cuh"
+
+namespace cicero {
+
+void set_error(const std::string& msg);
+cicero_status fail(cicero_status st, const std::string& msg);
+cicero_status cuda_fail(cudaError_t e, const char* where);
+
+int num_sms();
+
+// Stage timing with CUDA events on the launching stream (off unless cicero_profile_begin was
+// called) and a count of the kernels the library launches.
+enum Stage { kStMarch = 0, kStBucket, kStGatherMlp, kStComposite, kStWarpSplat, kStWarpResolve, kStBwdRay,
+             kStBwdBrick, kStMlpEval, kNumStages };
+void count_launches(int n);
+struct ProfScope {
+  ProfScope(int stage, cudaStream_t st);
+  ~ProfScope();
+  int stage;
+  cudaStream_t st;
+  cudaEvent_t e0, e1;
+  bool on;
+};
+
+// Workspace of one rendering call (all device pointers, carved from the caller's buffer).
+struct RenderWs {
+  uint32_t* hdr;        // [0] error bits, [1] tile count, [2] active samples, [3] spare
+  uint32_t* ray_n;      // [R] composited samples of each ray
+  float* ray_T;         // [R] transmittance after the last composited slot
+  uint32_t* rec_key;    // [R*S] brick id of record (ray r, rank j) at r*S + j
+  float* rec_t;         // [R*S] slot distance t (FP32, bit-identical to the march)
+  float* rec_w;         // [R*S] compositing weight T_k alpha_k
+  uint16_t* rec_k;      // [R*S] slot index (only for Ray Index Table export; may be null)
+  uint32_t* brick_cnt;  // [nb]
+  uint32_t* brick_off;  // [nb + 1]
+  uint32_t* brick_cur;  // [nb]
+  uint32_t* tile_brick; // [max_tiles]
+  uint32_t* tile_start; // [max_tiles]
+  uint32_t* sorted;     // [R*S] record ids grouped by brick
+  float4* rec_c;        // [R*S] (c_r, c_g, c_b, w) of each record
+  float* rec_T;         // [R*S] transmittance before the slot (backward only; may be null)
+  float* rec_raw;       // [R*S] interpolated raw density (backward only; may be null)
+  int R, S, nb, max_tiles;
+};
+
+struct RenderPlan {
+  GridGeo geo;
+  Samp samp;
+  int R, S, nb;
+  int max_tiles;
+  bool want_k;
+  bool want_bwd;
+  cicero_precision precision;
+};
+
+size_t render_ws_bytes(const RenderPlan& p);
+bool carve_render_ws(void* ws, size_t bytes, const RenderPlan& p, RenderWs* out);
+
+// grid/sampling validation and geometry (api.cu)
+cicero_status make_geo(const cicero_grid* g, int brick, GridGeo* geo);
+cicero_status make_samp(const cicero_sampling* s, Samp* out);
+cicero_status check_mlp(const cicero_mlp* m, const cicero_grid* g);
+
+// the stages (render.cu)
+struct MlpPtrs {
+  const float *w1, *b1, *w2, *b2, *w3, *b3;
+  int in_dim, n_freq;
+};
+
+cicero_status run_render(const cicero_grid* grid, const MlpPtrs& mlp, const RenderPlan& plan, const RaySrc& src,
+                         const RenderWs& ws, float* rgb, float* depth, float* acc, int32_t* n_steps,
+                         bool stop_after_bucketing, cudaStream_t st);
+
+cicero_status run_rit_export(const RenderWs& ws, int n_bricks, int S, int32_t* brick_offsets, int32_t* samples,
+                             cudaStream_t st);
+
+// tensor map of the feature grid viewed as [n2][n1][n0 * C] (box: brick + halo)
+struct BrickBox {
+  int vb;          // vertices per brick edge staged (brick + 1)
+  int vx;          // vertices along x in the box (>= vb, box row a multiple of 16 bytes)
+  int row_bytes;   // vx * C * elem
+  int box_bytes;   // vb * vb * row_bytes
+};
+BrickBox brick_box(const GridGeo& geo, int elem_bytes);
+cicero_status encode_brick_map(const cicero_grid* grid, const GridGeo& geo, const BrickBox& box, CUtensorMap* map);
+
+// BF16 tensor-core Feature Computation (mlp_tc.cu)
+cicero_status launch_gather_mlp_bf16(const cicero_grid* grid, const GridGeo& geo, const Samp& samp, const RaySrc& src,
+                                     const MlpPtrs& mlp, const RenderWs& ws, const CUtensorMap& map, const BrickBox& box,
+                                     cudaStream_t st);
+cicero_status launch_mlp_eval_bf16(const MlpPtrs& mlp, const float* x, int M, float* c, uint32_t* err,
+                                   cudaStream_t st);
+
+// SpaRW warp (warp.cu)
+struct WarpArgs {
+  int wr, hr;          // reference image
+  float fr, cxr, cyr;
+  int wt, ht;          // target image
+  float ft, cxt, cyt;
+  float R[9];          // [R_rel | t_rel] = inverse(c2w_tgt) c2w_ref, rounded to FP32
+  float t[3];
+  float cos_phi;
+  int use_phi;
+};
+
+struct VoidTest {
+  int enabled;
+  GridGeo g;
+  Samp s;
+  RaySrc src;  // target camera pixels
+};
+
+size_t warp_ws_bytes(int wt, int ht);
+cicero_status run_warp(const WarpArgs& a, const VoidTest& vt, const float* ref_rgb, const float* ref_depth,
+                       float* wrgb, float* wdepth, uint8_t* mask, int32_t* hole_idx, int32_t* n_holes, void* ws,
+                       cudaStream_t st);
+cicero_status run_backward(const cicero_grid* grid, const MlpPtrs& mlp, const RenderPlan& plan, const RaySrc& src,
+                           const RenderWs& ws, const float* d_rgb, float* d_dens, float* d_feat, cudaStream_t st);
+cicero_status launch_mlp_eval_f32(const MlpPtrs& mlp, const float* x, int M, float* c, cudaStream_t st);
+
+}  // namespace cicero

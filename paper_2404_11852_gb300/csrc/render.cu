@@ -1,0 +1,712 @@
+// Memory-centric voxel-grid NeRF rendering (Sec. II-B stages, reordered as in Sec. IV-A).
+//
+//   K1 k_march        one warp per ray, 32 slots per step: Indexing, density gathering,
+//                     alpha, transmittance by a warp scan of sigma*delta, early stop; emits one
+//                     record (t, w, brick) per composited sample and a brick histogram
+//   K2 k_brick_scan   brick offsets (exclusive scan of the histogram) and the tile list
+//   K3 k_scatter      counting sort of the records by brick: the Ray Index Table
+//   K5 k_gather_mlp_f32 / mlp_tc.cu
+//                     per brick: one TMA copy of the brick (+1 vertex halo) into shared memory,
+//                     trilinear feature gathering from there, view encoding and the MLP
+//   K6 k_composite    per ray, in slot order: rgb = sum w c + T_end bg
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace cicero {
+
+static size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
+
+size_t render_ws_bytes(const RenderPlan& p) {
+  size_t RS = (size_t)p.R * p.S;
+  size_t b = al256(64);
+  b += 2 * al256(4 * (size_t)p.R);
+  b += 3 * al256(4 * RS);
+  if (p.want_k) b += al256(2 * RS);
+  b += 2 * al256(4 * (size_t)p.nb) + al256(4 * ((size_t)p.nb + 1));
+  b += 2 * al256(4 * (size_t)p.max_tiles);
+  b += al256(4 * RS);
+  b += al256(16 * RS);
+  if (p.want_bwd) b += 2 * al256(4 * RS);
+  return b;
+}
+
+bool carve_render_ws(void* ws, size_t bytes, const RenderPlan& p, RenderWs* w) {
+  if (render_ws_bytes(p) > bytes) return false;
+  char* q = (char*)ws;
+  size_t RS = (size_t)p.R * p.S;
+  auto take = [&](size_t n) {
+    char* r = q;
+    q += al256(n);
+    return (void*)r;
+  };
+  w->hdr = (uint32_t*)take(64);
+  w->ray_n = (uint32_t*)take(4 * (size_t)p.R);
+  w->ray_T = (float*)take(4 * (size_t)p.R);
+  w->rec_key = (uint32_t*)take(4 * RS);
+  w->rec_t = (float*)take(4 * RS);
+  w->rec_w = (float*)take(4 * RS);
+  w->rec_k = p.want_k ? (uint16_t*)take(2 * RS) : nullptr;
+  w->brick_cnt = (uint32_t*)take(4 * (size_t)p.nb);
+  w->brick_cur = (uint32_t*)take(4 * (size_t)p.nb);
+  w->brick_off = (uint32_t*)take(4 * ((size_t)p.nb + 1));
+  w->tile_brick = (uint32_t*)take(4 * (size_t)p.max_tiles);
+  w->tile_start = (uint32_t*)take(4 * (size_t)p.max_tiles);
+  w->sorted = (uint32_t*)take(4 * RS);
+  w->rec_c = (float4*)take(16 * RS);
+  w->rec_T = p.want_bwd ? (float*)take(4 * RS) : nullptr;
+  w->rec_raw = p.want_bwd ? (float*)take(4 * RS) : nullptr;
+  w->R = p.R;
+  w->S = p.S;
+  w->nb = p.nb;
+  w->max_tiles = p.max_tiles;
+  return true;
+}
+
+// -------------------------------------------------------------------------------------------
+
+__global__ void k_clear(uint32_t* a, size_t na, uint32_t* b, size_t nb) {
+  size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x, s = (size_t)gridDim.x * blockDim.x;
+  for (size_t k = i; k < na; k += s) a[k] = 0;
+  for (size_t k = i; k < nb; k += s) b[k] = 0;
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ int out_index(const RaySrc& s, int r) {
+  return (s.kind == 0 && s.pix) ? s.pix[r] : r;
+}
+
+// K1: one warp per ray; lane = slot within a chunk of 32 slots.
+template <typename T>
+__global__ void __launch_bounds__(256) k_march(GridGeo g, Samp s, RaySrc src, const T* __restrict__ dens,
+                                               RenderWs w, float* depth, float* acc_out, int32_t* nsteps_out) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  const int R = ray_count(src);
+  const unsigned lt_mask = (1u << lane) - 1u;
+  for (int r = warp; r < R; r += nwarps) {
+    float o[3], d[3];
+    ray_gen(src, r, o, d);
+    Slots sl = place_slots(g, s, o, d);
+    float Ssum = 0.0f, acc = 0.0f, dsum = 0.0f;
+    uint32_t cnt = 0;
+    int steps = sl.n;
+    const size_t rec0 = (size_t)r * s.n_samples;
+    for (int k0 = 0; k0 < sl.n; k0 += 32) {
+      const int k = k0 + lane;
+      const float t = slot_t(sl, k);
+      const bool valid = slot_valid(sl, k, t);
+      const unsigned vmask = __ballot_sync(0xffffffffu, valid);
+      int i0[3] = {0, 0, 0};
+      float f[3];
+      bool act = false;
+      float sd = 0.0f, raw = 0.0f;
+      if (valid) {
+        float p[3];
+        sample_pos(o, d, t, p);
+        act = index_sample(g, p, i0, f);
+        if (act) {
+          raw = density_trilinear(g, dens, i0, f);
+          sd = softplus_f(raw + g.act_shift) * sl.dt;
+        }
+      }
+      float incl = sd;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        float v = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += v;
+      }
+      float excl = __shfl_up_sync(0xffffffffu, incl, 1);
+      if (lane == 0) excl = 0.0f;
+      const float Tk = expf(-(Ssum + excl));
+      const bool stop = valid && s.t_stop > 0.0f && Tk < s.t_stop;
+      const unsigned smask = __ballot_sync(0xffffffffu, stop);
+      const int first = smask ? __ffs(smask) - 1 : 32;
+      const bool contrib = act && lane < first;
+      const float wk = contrib ? Tk * -expm1f(-sd) : 0.0f;
+      const unsigned cmask = __ballot_sync(0xffffffffu, contrib);
+      const uint32_t key = contrib ? brick_id(g, i0) : 0xffffffffu;
+      if (contrib) {
+        size_t q = rec0 + cnt + __popc(cmask & lt_mask);
+        w.rec_t[q] = t;
+        w.rec_w[q] = wk;
+        w.rec_key[q] = key;
+        if (w.rec_k) w.rec_k[q] = (uint16_t)k;
+        if (w.rec_T) {
+          w.rec_T[q] = Tk;
+          w.rec_raw[q] = raw;
+        }
+      }
+      const unsigned peers = __match_any_sync(0xffffffffu, key);
+      if (contrib && (peers & lt_mask) == 0) atomicAdd(&w.brick_cnt[key], (uint32_t)__popc(peers));
+      acc += warp_sum(wk);
+      dsum += warp_sum(wk * t);
+      cnt += __popc(cmask);
+      const int last = first == 32 ? 31 : first - 1;
+      float tot = __shfl_sync(0xffffffffu, incl, last < 0 ? 0 : last);
+      if (first > 0) Ssum += tot;
+      if (first < 32) {
+        steps = k0 + first;
+        break;
+      }
+      if (vmask != 0xffffffffu) {
+        steps = k0 + __popc(vmask);
+        break;
+      }
+    }
+    if (lane == 0) {
+      w.ray_n[r] = cnt;
+      w.ray_T[r] = expf(-Ssum);
+      const int oi = out_index(src, r);
+      if (depth) depth[oi] = acc >= s.void_acc ? dsum / acc : __int_as_float(0x7f800000);
+      if (acc_out) acc_out[oi] = acc;
+      if (nsteps_out) nsteps_out[oi] = steps;
+    }
+  }
+}
+
+// K2: exclusive scan of the brick histogram and the list of tiles (<= kTile samples of one brick).
+__device__ __forceinline__ void block_exscan2(uint32_t a, uint32_t b, uint32_t* ea, uint32_t* eb, uint32_t* ta,
+                                              uint32_t* tb, uint32_t* sh /* 64 words */) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  uint32_t ia = a, ib = b;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t va = __shfl_up_sync(0xffffffffu, ia, o), vb = __shfl_up_sync(0xffffffffu, ib, o);
+    if (lane >= o) {
+      ia += va;
+      ib += vb;
+    }
+  }
+  if (lane == 31) {
+    sh[wid] = ia;
+    sh[32 + wid] = ib;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    uint32_t xa = lane < nw ? sh[lane] : 0, xb = lane < nw ? sh[32 + lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t va = __shfl_up_sync(0xffffffffu, xa, o), vb = __shfl_up_sync(0xffffffffu, xb, o);
+      if (lane >= o) {
+        xa += va;
+        xb += vb;
+      }
+    }
+    sh[lane] = xa;
+    sh[32 + lane] = xb;
+  }
+  __syncthreads();
+  const uint32_t pa = wid ? sh[wid - 1] : 0, pb = wid ? sh[32 + wid - 1] : 0;
+  *ea = pa + ia - a;
+  *eb = pb + ib - b;
+  *ta = sh[nw - 1];
+  *tb = sh[32 + nw - 1];
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(1024) k_brick_scan(RenderWs w) {
+  __shared__ uint32_t sh[64];
+  uint32_t run_s = 0, run_t = 0;
+  for (int base = 0; base < w.nb; base += blockDim.x) {
+    const int i = base + threadIdx.x;
+    const uint32_t c = i < w.nb ? w.brick_cnt[i] : 0;
+    const uint32_t nt = (c + kTile - 1) / kTile;
+    uint32_t es, et, ts, tt;
+    block_exscan2(c, nt, &es, &et, &ts, &tt, sh);
+    if (i < w.nb) {
+      const uint32_t off = run_s + es;
+      w.brick_off[i] = off;
+      w.brick_cur[i] = 0;
+      for (uint32_t q = 0; q < nt; q++) {
+        const uint32_t ti = run_t + et + q;
+        if (ti < (uint32_t)w.max_tiles) {
+          w.tile_brick[ti] = i;
+          w.tile_start[ti] = off + q * kTile;
+        }
+      }
+    }
+    run_s += ts;
+    run_t += tt;
+  }
+  if (threadIdx.x == 0) {
+    w.brick_off[w.nb] = run_s;
+    if (run_t > (uint32_t)w.max_tiles) {
+      set_err(&w.hdr[0], kErrInternal);
+      run_t = w.max_tiles;
+    }
+    w.hdr[1] = run_t;
+    w.hdr[2] = run_s;
+  }
+}
+
+// K3: counting sort of the records by brick (order inside a brick is unspecified).
+__global__ void __launch_bounds__(256) k_scatter(RaySrc src, RenderWs w) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  const int R = ray_count(src);
+  const unsigned lt_mask = (1u << lane) - 1u;
+  for (int r = warp; r < R; r += nwarps) {
+    const uint32_t n = w.ray_n[r];
+    const size_t rec0 = (size_t)r * w.S;
+    for (uint32_t j0 = 0; j0 < n; j0 += 32) {
+      const uint32_t j = j0 + lane;
+      const bool valid = j < n;
+      const uint32_t key = valid ? w.rec_key[rec0 + j] : 0xffffffffu;
+      const unsigned peers = __match_any_sync(0xffffffffu, key);
+      const int leader = __ffs(peers) - 1;
+      uint32_t base = 0;
+      if (valid && lane == leader) base = atomicAdd(&w.brick_cur[key], (uint32_t)__popc(peers));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if (valid) w.sorted[w.brick_off[key] + base + __popc(peers & lt_mask)] = (uint32_t)(rec0 + j);
+    }
+  }
+}
+
+// -------------------------------------------------------------------------------------------
+// K5 (FP32): Feature Gathering from the staged brick and an FP32 SIMT MLP over 128-sample tiles.
+
+template <typename T>
+__device__ __forceinline__ void tri_smem(const T* tile, int vb, int vx, int C, const int l[3], const float f[3],
+                                         float* out) {
+  const float fx = f[0], fy = f[1], fz = f[2];
+  float wc[8];
+  wc[0] = (1.f - fx) * (1.f - fy) * (1.f - fz);
+  wc[1] = fx * (1.f - fy) * (1.f - fz);
+  wc[2] = (1.f - fx) * fy * (1.f - fz);
+  wc[3] = fx * fy * (1.f - fz);
+  wc[4] = (1.f - fx) * (1.f - fy) * fz;
+  wc[5] = fx * (1.f - fy) * fz;
+  wc[6] = (1.f - fx) * fy * fz;
+  wc[7] = fx * fy * fz;
+  for (int c = 0; c < C; c++) out[c] = 0.0f;
+#pragma unroll
+  for (int q = 0; q < 8; q++) {
+    const int x = l[0] + (q & 1), y = l[1] + ((q >> 1) & 1), z = l[2] + (q >> 2);
+    const T* v = tile + ((size_t)(z * vb + y) * vx + x) * C;
+    if constexpr (sizeof(T) == 4) {
+      if (C == 12) {
+        const float4* v4 = reinterpret_cast<const float4*>(v);
+#pragma unroll
+        for (int u = 0; u < 3; u++) {
+          float4 a = v4[u];
+          out[4 * u + 0] += wc[q] * a.x;
+          out[4 * u + 1] += wc[q] * a.y;
+          out[4 * u + 2] += wc[q] * a.z;
+          out[4 * u + 3] += wc[q] * a.w;
+        }
+        continue;
+      }
+    } else {
+      if (C == 12) {
+        const uint2* v2 = reinterpret_cast<const uint2*>(v);
+#pragma unroll
+        for (int u = 0; u < 3; u++) {
+          uint2 a = v2[u];
+          float2 lo = __half22float2(*reinterpret_cast<__half2*>(&a.x));
+          float2 hi = __half22float2(*reinterpret_cast<__half2*>(&a.y));
+          out[4 * u + 0] += wc[q] * lo.x;
+          out[4 * u + 1] += wc[q] * lo.y;
+          out[4 * u + 2] += wc[q] * hi.x;
+          out[4 * u + 3] += wc[q] * hi.y;
+        }
+        continue;
+      }
+    }
+    for (int c = 0; c < C; c++) {
+      float vv;
+      if constexpr (sizeof(T) == 4) vv = v[c];
+      else vv = __half2float(v[c]);
+      out[c] += wc[q] * vv;
+    }
+  }
+}
+
+constexpr int kK1 = kMaxIn;  // padded input width of layer 1
+
+struct F32Smem {
+  // byte offsets inside dynamic shared memory
+  static constexpr int w1t = 0;                                  // [48][128]
+  static constexpr int w2t = w1t + kK1 * kHidden * 4;            // [128][128]
+  static constexpr int w3 = w2t + kHidden * kHidden * 4;         // [3][128]
+  static constexpr int b1 = w3 + 3 * kHidden * 4;                // [128]
+  static constexpr int b2 = b1 + kHidden * 4;                    // [128]
+  static constexpr int b3 = b2 + kHidden * 4;                    // [4]
+  static constexpr int x = b3 + 16;                              // [48][128]
+  static constexpr int h = x + kK1 * kTile * 4;                  // [128][128]
+  static constexpr int bar = ((h + kHidden * kTile * 4 + 127) / 128) * 128;  // mbarrier (8 B, pad 128)
+  static constexpr int tile = bar + 128;                         // brick tile (TMA destination, 128-B aligned)
+  static_assert(tile % 128 == 0, "TMA destination must be 128-byte aligned");
+};
+
+// acc[i][j]: rows {tm*4+i, 64+tm*4+(i-4)}, cols {tn*4+j, 64+tn*4+(j-4)}; A, B k-major [K][128]
+__device__ __forceinline__ void simt_gemm(const float* __restrict__ A, const float* __restrict__ Bw, int K, int tm,
+                                          int tn, float acc[8][8]) {
+#pragma unroll 2
+  for (int k = 0; k < K; k++) {
+    const float4 a0 = *reinterpret_cast<const float4*>(&A[k * kTile + tm * 4]);
+    const float4 a1 = *reinterpret_cast<const float4*>(&A[k * kTile + 64 + tm * 4]);
+    const float4 b0 = *reinterpret_cast<const float4*>(&Bw[k * kHidden + tn * 4]);
+    const float4 b1 = *reinterpret_cast<const float4*>(&Bw[k * kHidden + 64 + tn * 4]);
+    const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+    const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+    for (int i = 0; i < 8; i++)
+#pragma unroll
+      for (int j = 0; j < 8; j++) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+  }
+}
+
+__device__ __forceinline__ int gemm_row(int tm, int i) { return i < 4 ? tm * 4 + i : 64 + tm * 4 + (i - 4); }
+
+// bias + relu, then store transposed as the next layer's k-major input H[n][m]
+__device__ __forceinline__ void simt_epilogue(float acc[8][8], const float* bias, float* H, int tm, int tn) {
+#pragma unroll
+  for (int j = 0; j < 8; j++) {
+    const int n = gemm_row(tn, j);
+    const float bj = bias[n];
+    float4 lo, hi;
+    lo.x = fmaxf(acc[0][j] + bj, 0.f);
+    lo.y = fmaxf(acc[1][j] + bj, 0.f);
+    lo.z = fmaxf(acc[2][j] + bj, 0.f);
+    lo.w = fmaxf(acc[3][j] + bj, 0.f);
+    hi.x = fmaxf(acc[4][j] + bj, 0.f);
+    hi.y = fmaxf(acc[5][j] + bj, 0.f);
+    hi.z = fmaxf(acc[6][j] + bj, 0.f);
+    hi.w = fmaxf(acc[7][j] + bj, 0.f);
+    *reinterpret_cast<float4*>(&H[n * kTile + tm * 4]) = lo;
+    *reinterpret_cast<float4*>(&H[n * kTile + 64 + tm * 4]) = hi;
+  }
+}
+
+__device__ void load_mlp_f32_smem(char* sm, const MlpPtrs& m) {
+  float* w1t = (float*)(sm + F32Smem::w1t);
+  float* w2t = (float*)(sm + F32Smem::w2t);
+  float* w3 = (float*)(sm + F32Smem::w3);
+  float* b1 = (float*)(sm + F32Smem::b1);
+  float* b2 = (float*)(sm + F32Smem::b2);
+  float* b3 = (float*)(sm + F32Smem::b3);
+  for (int i = threadIdx.x; i < kK1 * kHidden; i += blockDim.x) {
+    const int k = i / kHidden, n = i % kHidden;
+    w1t[i] = k < m.in_dim ? m.w1[n * m.in_dim + k] : 0.0f;
+  }
+  for (int i = threadIdx.x; i < kHidden * kHidden; i += blockDim.x) {
+    const int k = i / kHidden, n = i % kHidden;
+    w2t[i] = m.w2[n * kHidden + k];
+  }
+  for (int i = threadIdx.x; i < 3 * kHidden; i += blockDim.x) w3[i] = m.w3[i];
+  for (int i = threadIdx.x; i < kHidden; i += blockDim.x) {
+    b1[i] = m.b1[i];
+    b2[i] = m.b2[i];
+  }
+  if (threadIdx.x < 4) b3[threadIdx.x] = threadIdx.x < 3 ? m.b3[threadIdx.x] : 0.0f;
+}
+
+// Three-layer MLP of the 128 samples whose inputs are in X [48][128]; threads < 128 return c of
+// sample m = threadIdx.x.  Needs 256 threads.
+__device__ __forceinline__ void mlp_f32_tile(char* sm, float c[3]) {
+  const float* w1t = (const float*)(sm + F32Smem::w1t);
+  const float* w2t = (const float*)(sm + F32Smem::w2t);
+  const float* w3 = (const float*)(sm + F32Smem::w3);
+  const float* b1 = (const float*)(sm + F32Smem::b1);
+  const float* b2 = (const float*)(sm + F32Smem::b2);
+  const float* b3 = (const float*)(sm + F32Smem::b3);
+  const float* X = (const float*)(sm + F32Smem::x);
+  float* H = (float*)(sm + F32Smem::h);
+  const int tm = threadIdx.x & 15, tn = threadIdx.x >> 4;
+  float acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; i++)
+#pragma unroll
+    for (int j = 0; j < 8; j++) acc[i][j] = 0.0f;
+  simt_gemm(X, w1t, kK1, tm, tn, acc);
+  simt_epilogue(acc, b1, H, tm, tn);
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < 8; i++)
+#pragma unroll
+    for (int j = 0; j < 8; j++) acc[i][j] = 0.0f;
+  simt_gemm(H, w2t, kHidden, tm, tn, acc);
+  __syncthreads();
+  simt_epilogue(acc, b2, H, tm, tn);
+  __syncthreads();
+  if (threadIdx.x < kTile) {
+    const int m = threadIdx.x;
+    float z0 = b3[0], z1 = b3[1], z2 = b3[2];
+#pragma unroll 8
+    for (int k = 0; k < kHidden; k++) {
+      const float h = H[k * kTile + m];
+      z0 = fmaf(w3[k], h, z0);
+      z1 = fmaf(w3[kHidden + k], h, z1);
+      z2 = fmaf(w3[2 * kHidden + k], h, z2);
+    }
+    c[0] = sigmoid_f(z0);
+    c[1] = sigmoid_f(z1);
+    c[2] = sigmoid_f(z2);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256, 1) k_gather_mlp_f32(GridGeo g, RaySrc src, int S, MlpPtrs mlp, RenderWs w,
+                                                           const __grid_constant__ CUtensorMap fmap, int vb, int vx,
+                                                           int box_bytes) {
+  extern __shared__ __align__(128) char sm[];
+  float* X = (float*)(sm + F32Smem::x);
+  uint64_t* bar = (uint64_t*)(sm + F32Smem::bar);
+  T* tile = (T*)(sm + F32Smem::tile);
+  load_mlp_f32_smem(sm, mlp);
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  const uint32_t n_tiles = w.hdr[1];
+  const uint32_t per = (n_tiles + gridDim.x - 1) / gridDim.x;
+  const uint32_t t_begin = blockIdx.x * per, t_end = min(n_tiles, t_begin + per);
+  const int B = g.brick, C = g.C;
+  const int m = threadIdx.x & (kTile - 1), part = threadIdx.x >> 7;
+  int loaded = -1;
+  uint32_t phase = 0;
+  bool alive = true;
+  for (uint32_t ti = t_begin; ti < t_end && alive; ti++) {
+    const int b = (int)w.tile_brick[ti];
+    const uint32_t start = w.tile_start[ti];
+    const uint32_t end = min(start + (uint32_t)kTile, w.brick_off[b + 1]);
+    const int mcnt = (int)(end - start);
+    const int bx = b % g.nb[0], by = (b / g.nb[0]) % g.nb[1], bz = b / (g.nb[0] * g.nb[1]);
+    if (b != loaded) {
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        mbar_expect_tx(bar, (uint32_t)box_bytes);
+        tma_load_3d(tile, &fmap, bx * B * C, by * B, bz * B, bar);
+      }
+      if (!mbar_wait(bar, phase, &w.hdr[0])) alive = false;
+      phase ^= 1u;
+      loaded = b;
+    }
+    if (!__syncthreads_and(alive)) break;
+    if (m < mcnt) {
+      const uint32_t sid = w.sorted[start + m];
+      const int r = (int)(sid / (uint32_t)S);
+      float o[3], d[3];
+      ray_gen(src, r, o, d);
+      if (part == 0) {
+        float p[3], f[3], feat[24];
+        int i0[3];
+        sample_pos(o, d, w.rec_t[sid], p);
+        const bool ok = index_sample(g, p, i0, f);
+        const int l[3] = {i0[0] - bx * B, i0[1] - by * B, i0[2] - bz * B};
+        if (!ok || l[0] < 0 || l[0] >= B || l[1] < 0 || l[1] >= B || l[2] < 0 || l[2] >= B) {
+          set_err(&w.hdr[0], kErrInternal);
+          for (int c = 0; c < C; c++) X[c * kTile + m] = 0.0f;
+        } else {
+          tri_smem<T>(tile, vb, vx, C, l, f, feat);
+          for (int c = 0; c < C; c++) X[c * kTile + m] = feat[c];
+        }
+      } else {
+        float e[3 + 6 * 7];
+        encode_dir(d, mlp.n_freq, e);
+        const int ne = 3 + 6 * mlp.n_freq;
+        for (int j = 0; j < ne; j++) X[(C + j) * kTile + m] = e[j];
+        for (int j = C + ne; j < kK1; j++) X[j * kTile + m] = 0.0f;
+      }
+    } else {
+      if (part == 0)
+        for (int c = 0; c < C; c++) X[c * kTile + m] = 0.0f;
+      else
+        for (int j = C; j < kK1; j++) X[j * kTile + m] = 0.0f;
+    }
+    __syncthreads();
+    float c[3];
+    mlp_f32_tile(sm, c);
+    if (threadIdx.x < kTile && m < mcnt) {
+      const uint32_t sid = w.sorted[start + m];
+      w.rec_c[sid] = make_float4(c[0], c[1], c[2], w.rec_w[sid]);
+    }
+  }
+}
+
+// K6: per ray, in slot order.
+__global__ void __launch_bounds__(256) k_composite(RaySrc src, Samp s, RenderWs w, float* rgb) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  const int R = ray_count(src);
+  for (int r = warp; r < R; r += nwarps) {
+    const uint32_t n = w.ray_n[r];
+    const size_t rec0 = (size_t)r * w.S;
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+    for (uint32_t j = lane; j < n; j += 32) {
+      const float4 v = w.rec_c[rec0 + j];
+      a0 += v.w * v.x;
+      a1 += v.w * v.y;
+      a2 += v.w * v.z;
+    }
+    a0 = warp_sum(a0);
+    a1 = warp_sum(a1);
+    a2 = warp_sum(a2);
+    if (lane == 0) {
+      const float T = w.ray_T[r];
+      const int oi = out_index(src, r);
+      rgb[3 * oi + 0] = a0 + T * s.bg[0];
+      rgb[3 * oi + 1] = a1 + T * s.bg[1];
+      rgb[3 * oi + 2] = a2 + T * s.bg[2];
+    }
+  }
+}
+
+// Ray Index Table export: sample id = ray * S + slot.
+__global__ void k_rit_export(RenderWs w, int n_bricks, int32_t* offs, int32_t* samples) {
+  const uint32_t total = w.hdr[2];
+  const size_t i0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x, st = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = i0; i <= (size_t)n_bricks; i += st) offs[i] = (int32_t)w.brick_off[i];
+  for (size_t i = i0; i < total; i += st) {
+    const uint32_t sid = w.sorted[i];
+    const uint32_t r = sid / (uint32_t)w.S;
+    samples[i] = (int32_t)(r * (uint32_t)w.S + w.rec_k[sid]);
+  }
+}
+
+// -------------------------------------------------------------------------------------------
+// host side
+
+BrickBox brick_box(const GridGeo& geo, int elem) {
+  BrickBox b;
+  b.vb = geo.brick + 1;
+  int vx = b.vb;
+  while ((vx * geo.C * elem) % 16) vx++;
+  b.vx = vx;
+  b.row_bytes = vx * geo.C * elem;
+  b.box_bytes = b.vb * b.vb * b.row_bytes;
+  return b;
+}
+
+static int blocks_for_warps(long long warps, int per_sm) {
+  long long blocks = (warps + 7) / 8;
+  long long cap = (long long)num_sms() * per_sm;
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  return (int)blocks;
+}
+
+template <typename T>
+static cicero_status launch_f32(const GridGeo& geo, const RaySrc& src, int S, const MlpPtrs& mlp, const RenderWs& ws,
+                                const CUtensorMap& map, const BrickBox& box, cudaStream_t st) {
+  const int smem = F32Smem::tile + box.box_bytes;
+  if (smem > 227 * 1024) return fail(CICERO_ERR_UNSUPPORTED, "brick too large for the FP32 feature-computation kernel");
+  auto kern = k_gather_mlp_f32<T>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_gather_mlp_f32)");
+  {
+    ProfScope ps(kStGatherMlp, st);
+    kern<<<num_sms(), 256, smem, st>>>(geo, src, S, mlp, ws, map, box.vb, box.vx, box.box_bytes);
+  }
+  count_launches(1);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? CICERO_OK : cuda_fail(e, "k_gather_mlp_f32");
+}
+
+cicero_status run_render(const cicero_grid* grid, const MlpPtrs& mlp, const RenderPlan& plan, const RaySrc& src,
+                         const RenderWs& ws, float* rgb, float* depth, float* acc, int32_t* n_steps,
+                         bool stop_after_bucketing, cudaStream_t st) {
+  const GridGeo& geo = plan.geo;
+  const bool f16 = grid->dtype == CICERO_F16;
+  const int mb = blocks_for_warps(src.n_max, 16);
+  {
+    ProfScope ps(kStMarch, st);
+    k_clear<<<std::min(num_sms() * 4, (plan.nb + 255) / 256 + 1), 256, 0, st>>>(ws.hdr, 16, ws.brick_cnt, plan.nb);
+    if (f16)
+      k_march<__half><<<mb, 256, 0, st>>>(geo, plan.samp, src, (const __half*)grid->density, ws, depth, acc, n_steps);
+    else
+      k_march<float><<<mb, 256, 0, st>>>(geo, plan.samp, src, (const float*)grid->density, ws, depth, acc, n_steps);
+  }
+  {
+    ProfScope ps(kStBucket, st);
+    k_brick_scan<<<1, 1024, 0, st>>>(ws);
+    k_scatter<<<mb, 256, 0, st>>>(src, ws);
+  }
+  count_launches(4);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "march/bucket kernels");
+  if (stop_after_bucketing) return CICERO_OK;
+
+  const BrickBox box = brick_box(geo, f16 ? 2 : 4);
+  CUtensorMap map;
+  cicero_status s = encode_brick_map(grid, geo, box, &map);
+  if (s != CICERO_OK) return s;
+  if (plan.precision == CICERO_MLP_BF16) {
+    s = launch_gather_mlp_bf16(grid, geo, plan.samp, src, mlp, ws, map, box, st);
+  } else {
+    s = f16 ? launch_f32<__half>(geo, src, plan.S, mlp, ws, map, box, st)
+            : launch_f32<float>(geo, src, plan.S, mlp, ws, map, box, st);
+  }
+  if (s != CICERO_OK) return s;
+  if (!rgb) return CICERO_OK;  // the backward only needs the per-sample records
+  {
+    ProfScope ps(kStComposite, st);
+    k_composite<<<mb, 256, 0, st>>>(src, plan.samp, ws, rgb);
+  }
+  count_launches(1);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? CICERO_OK : cuda_fail(e, "k_composite");
+}
+
+cicero_status run_rit_export(const RenderWs& ws, int n_bricks, int S, int32_t* brick_offsets, int32_t* samples,
+                             cudaStream_t st) {
+  (void)S;
+  k_rit_export<<<num_sms() * 4, 256, 0, st>>>(ws, n_bricks, brick_offsets, samples);
+  count_launches(1);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? CICERO_OK : cuda_fail(e, "k_rit_export");
+}
+
+// Feature Computation alone (FP32): c = MLP(x) for M inputs, 128 per tile.
+__global__ void __launch_bounds__(256, 1) k_mlp_eval_f32(MlpPtrs mlp, const float* x, int M, float* c) {
+  extern __shared__ __align__(128) char sm[];
+  float* X = (float*)(sm + F32Smem::x);
+  load_mlp_f32_smem(sm, mlp);
+  __syncthreads();
+  const int ntile = (M + kTile - 1) / kTile;
+  for (int t = blockIdx.x; t < ntile; t += gridDim.x) {
+    for (int i = threadIdx.x; i < kK1 * kTile; i += blockDim.x) {
+      const int k = i / kTile, m = i % kTile, row = t * kTile + m;
+      X[i] = (k < mlp.in_dim && row < M) ? x[(size_t)row * mlp.in_dim + k] : 0.0f;
+    }
+    __syncthreads();
+    float cc[3];
+    mlp_f32_tile(sm, cc);
+    const int row = t * kTile + threadIdx.x;
+    if (threadIdx.x < kTile && row < M) {
+      c[3 * row + 0] = cc[0];
+      c[3 * row + 1] = cc[1];
+      c[3 * row + 2] = cc[2];
+    }
+    __syncthreads();
+  }
+}
+
+cicero_status launch_mlp_eval_f32(const MlpPtrs& mlp, const float* x, int M, float* c, cudaStream_t st) {
+  const int smem = F32Smem::bar;
+  cudaError_t e = cudaFuncSetAttribute(k_mlp_eval_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_mlp_eval_f32)");
+  const int ntile = (M + kTile - 1) / kTile;
+  {
+    ProfScope ps(kStMlpEval, st);
+    k_mlp_eval_f32<<<std::max(1, std::min(ntile, num_sms())), 256, smem, st>>>(mlp, x, M, c);
+  }
+  count_launches(1);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? CICERO_OK : cuda_fail(e, "k_mlp_eval_f32");
+}
+
+}  // namespace cicero

@@ -1,0 +1,153 @@
+"""GPU parity of SpaRW (Sec. III-B): the warp (Eq. 1-3 + depth test) bit-exact against the
+oracle on identical float inputs, and sparse rendering of the holes (Eq. 4) within the
+rendering tolerances."""
+import numpy as np
+import pytest
+
+import scenes
+from helpers import check_render, psnr
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cc():
+    from paper_2404_11852_gb300 import cicero
+    cicero.lib()
+    return cicero
+
+
+@pytest.fixture(scope="module")
+def ref_frame(orc):
+    """A 64x64 reference frame rendered by the oracle (rgb, depth rounded to float32)."""
+    g, m = scenes.scene_small(), scenes.make_mlp(12)
+    cam = scenes.orbit_camera(64, 64, sampling=scenes.sampling_uniform(64))
+    out = orc.render(g, m, cam.sampling, cam=cam)
+    return g, m, cam, out["rgb"].astype(np.float32), out["depth"].astype(np.float32)
+
+
+def gpu_warp(cc, rgb, depth, ref_cam, tgt_cam, phi=180.0, void_grid=None, void_sp=None):
+    import torch
+    NT = tgt_cam.width * tgt_cam.height
+    rc, tc = cc.camera_from(ref_cam), cc.camera_from(tgt_cam)
+    r = torch.from_numpy(rgb).cuda()
+    d = torch.from_numpy(depth).cuda()
+    wr = torch.empty(NT, 3, device="cuda")
+    wd = torch.empty(NT, device="cuda")
+    mask = torch.empty(NT, dtype=torch.uint8, device="cuda")
+    hidx = torch.empty(NT, dtype=torch.int32, device="cuda")
+    nh = torch.empty(1, dtype=torch.int32, device="cuda")
+    ws = cc.workspace(cc.cicero_warp_workspace_size(tc))
+    vg = cc.DeviceGrid.from_host(void_grid) if void_grid is not None else None
+    vs = cc.sampling_from(void_sp) if void_sp is not None else None
+    cc.cicero_warp(r, d, rc, tc, phi, vg.desc if vg else None, vs, wr, wd, mask, hidx, nh, ws)
+    n = int(nh.item())
+    return {"rgb": wr.cpu().numpy(), "depth": wd.cpu().numpy(), "mask": mask.cpu().numpy(),
+            "hole_idx": hidx.cpu().numpy()[:n], "n_holes": n, "_dev": (wr, wd, hidx, nh)}
+
+
+def assert_warp_equal(got, want):
+    np.testing.assert_array_equal(got["mask"], want["mask"])
+    assert got["n_holes"] == want["n_holes"]
+    np.testing.assert_array_equal(got["hole_idx"], want["hole_idx"])
+    np.testing.assert_array_equal(got["rgb"], want["rgb"])
+    np.testing.assert_array_equal(got["depth"], want["depth"])
+
+
+@pytest.mark.parametrize("k", [-8, -3, 1, 5, 8])
+def test_warp_bit_exact(cc, orc, ref_frame, k):
+    g, m, cam, rgb, depth = ref_frame
+    tgt = scenes.offset_camera(cam, k)
+    want = orc.warp(rgb, depth, cam, tgt, void_grid=g, void_sampling=cam.sampling)
+    got = gpu_warp(cc, rgb, depth, cam, tgt, void_grid=g, void_sp=cam.sampling)
+    assert_warp_equal(got, want)
+    assert (want["mask"] == 0).mean() > 0.5
+
+
+def test_warp_identity(cc, ref_frame):
+    g, m, cam, rgb, depth = ref_frame
+    got = gpu_warp(cc, rgb, depth, cam, cam, void_grid=g, void_sp=cam.sampling)
+    assert got["n_holes"] == 0 and (got["mask"] == 0).all()
+    np.testing.assert_array_equal(got["rgb"], rgb)
+
+
+def test_warp_angle_threshold_and_ragged_target(cc, orc, ref_frame):
+    g, m, cam, rgb, depth = ref_frame
+    tgt = scenes.offset_camera(cam, 6, yaw_deg=2.0, shift=0.03)
+    tgt = scenes.Camera(50, 37, tgt.f * 0.8, 24.5, 19.0, tgt.c2w, tgt.sampling)
+    for phi in (180.0, 3.0, 0.5):
+        want = orc.warp(rgb, depth, cam, tgt, max_angle_deg=phi, void_grid=g, void_sampling=cam.sampling)
+        got = gpu_warp(cc, rgb, depth, cam, tgt, phi=phi, void_grid=g, void_sp=cam.sampling)
+        assert_warp_equal(got, want)
+
+
+def test_warp_occupancy_void_test(cc, orc):
+    g = scenes.make_grid(64, 12, 6, seed=9, dtype=np.float16, occ_res=16, occ_frac=0.2)
+    cam = scenes.orbit_camera(48, 48, sampling=scenes.sampling_march(64, 128))
+    rgb = scenes.uniform(5, 48 * 48 * 3).astype(np.float32).reshape(-1, 3)
+    depth = scenes.uniform(6, 48 * 48, 1.0, 2.0).astype(np.float32)
+    depth[scenes.uniform(7, 48 * 48) < 0.4] = np.inf
+    tgt = scenes.offset_camera(cam, 4, yaw_deg=2.0)
+    want = orc.warp(rgb, depth, cam, tgt, void_grid=g, void_sampling=cam.sampling)
+    got = gpu_warp(cc, rgb, depth, cam, tgt, void_grid=g, void_sp=cam.sampling)
+    assert_warp_equal(got, want)
+    assert (want["mask"] == 2).any() and (want["mask"] == 1).any()
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-4), (1, 2e-2)])
+def test_render_holes(cc, orc, ref_frame, precision, tol):
+    import torch
+    g, m, cam, rgb, depth = ref_frame
+    tgt = scenes.offset_camera(cam, 8, yaw_deg=3.0, shift=0.02)
+    want = orc.warp(rgb, depth, cam, tgt, void_grid=g, void_sampling=cam.sampling)
+    got = gpu_warp(cc, rgb, depth, cam, tgt, void_grid=g, void_sp=cam.sampling)
+    assert_warp_equal(got, want)
+    wr, wd, hidx, nh = got["_dev"]
+    gd, md = cc.DeviceGrid.from_host(g), cc.DeviceMlp.from_host(m)
+    NT = tgt.width * tgt.height
+    sd, cd, opt = cc.sampling_from(cam.sampling), cc.camera_from(tgt), cc.options(precision, 8)
+    ws = cc.workspace(cc.cicero_render_workspace_size(gd.desc, NT, sd, opt))
+    cc.cicero_render_holes(gd.desc, md.desc, cd, sd, opt, hidx, nh, NT, wr, wd, ws)
+    cc.cicero_workspace_status(ws)
+    out_rgb = wr.cpu().double().numpy()
+    out_d = wd.cpu().double().numpy()
+    holes = want["hole_idx"]
+    assert len(holes) > 0
+    ref = orc.render(g, m, cam.sampling, cam=tgt, pix=holes)
+    sub = {"rgb": out_rgb[holes], "depth": out_d[holes], "acc": ref["acc"]}
+    check_render(sub, ref, tol)
+    # pixels that were not holes are untouched
+    keep = np.ones(NT, bool)
+    keep[holes] = False
+    np.testing.assert_array_equal(out_rgb[keep], want["rgb"][keep].astype(np.float64))
+
+
+def test_sparw_chain_against_oracle_chain(cc, orc):
+    """Reference render -> warp -> hole render on the GPU (BF16) vs the same chain in the
+    oracle: the two chains agree to within the BF16 tolerance band (reported PSNR)."""
+    import torch
+    g, m = scenes.scene_small(), scenes.make_mlp(12)
+    cam = scenes.orbit_camera(96, 96, sampling=scenes.sampling_uniform(64))
+    from helpers import gpu_render
+    gref = gpu_render(cc, g, m, cam, cam.sampling, 1, 8)
+    oref = orc.render(g, m, cam.sampling, cam=cam)
+    tgt = scenes.offset_camera(cam, 4)
+    o_w = orc.warp(oref["rgb"].astype(np.float32), oref["depth"].astype(np.float32), cam, tgt, void_grid=g,
+                   void_sampling=cam.sampling)
+    o_rgb = o_w["rgb"].astype(np.float64)
+    if o_w["n_holes"]:
+        o_rgb[o_w["hole_idx"]] = orc.render(g, m, cam.sampling, cam=tgt, pix=o_w["hole_idx"])["rgb"]
+    got = gpu_warp(cc, gref["rgb"].astype(np.float32), gref["depth"].astype(np.float32), cam, tgt, void_grid=g,
+                   void_sp=cam.sampling)
+    wr, wd, hidx, nh = got["_dev"]
+    gd, md = cc.DeviceGrid.from_host(g), cc.DeviceMlp.from_host(m)
+    NT = tgt.width * tgt.height
+    sd, cd, opt = cc.sampling_from(cam.sampling), cc.camera_from(tgt), cc.options(1, 8)
+    ws = cc.workspace(cc.cicero_render_workspace_size(gd.desc, NT, sd, opt))
+    cc.cicero_render_holes(gd.desc, md.desc, cd, sd, opt, hidx, nh, NT, wr, wd, ws)
+    cc.cicero_workspace_status(ws)
+    p = psnr(wr.cpu().double().numpy(), o_rgb)
+    full = orc.render(g, m, cam.sampling, cam=tgt)["rgb"]
+    print(f"SpaRW chain GPU vs oracle chain: {p:.1f} dB; oracle SpaRW vs full render: {psnr(o_rgb, full):.1f} dB; "
+          f"holes {o_w['n_holes']} of {NT}")
+    assert p >= 40.0
