@@ -42,7 +42,40 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-res", type=int, default=100, help="oracle sample resolution (square)")
+    p.add_argument("--case", default="full", choices=["full", "small"],
+                   help="small: one 320x320 reference frame (BF16 and FP32) and two targets, for profilers")
     return p.parse_args()
+
+
+def small_case():
+    """A reduced run of the same kernels for profiler captures (the grid stays 416 MB > L2)."""
+    import torch
+    import scenes
+    from paper_2404_11852_gb300 import build, cicero as cc
+    build.build()
+    g_h, m_h = scenes.scene_large(), scenes.make_mlp(12)
+    grid, mlp = cc.DeviceGrid.from_host(g_h), cc.DeviceMlp.from_host(m_h)
+    n = 320
+    cam = scenes.orbit_camera(n, n, sampling=scenes.sampling_march(256, 256))
+    sd, cd = cc.sampling_from(cam.sampling), cc.camera_from(cam)
+    R = n * n
+    rgb, depth = torch.empty(R, 3, device="cuda"), torch.empty(R, device="cuda")
+    o16, o32 = cc.options(cc.MLP_BF16, 8), cc.options(cc.MLP_FP32, 8)
+    ws = cc.workspace(cc.cicero_render_workspace_size(grid.desc, R, sd, o16))
+    for opt in (o16, o16, o32):
+        cc.cicero_render(grid.desc, mlp.desc, cd, sd, opt, rgb, depth, None, None, ws)
+    wws = cc.workspace(cc.cicero_warp_workspace_size(cd))
+    for k in (-8, 8):
+        td = cc.camera_from(scenes.offset_camera(cam, k))
+        wr, wd = torch.empty(R, 3, device="cuda"), torch.empty(R, device="cuda")
+        mask = torch.empty(R, dtype=torch.uint8, device="cuda")
+        hidx = torch.empty(R, dtype=torch.int32, device="cuda")
+        nh = torch.empty(1, dtype=torch.int32, device="cuda")
+        cc.cicero_warp(rgb, depth, cd, td, 180.0, grid.desc, sd, wr, wd, mask, hidx, nh, wws)
+        cc.cicero_render_holes(grid.desc, mlp.desc, td, sd, o16, hidx, nh, R, wr, wd, ws)
+    cc.cicero_workspace_status(ws)
+    torch.cuda.synchronize()
+    print("small case ok")
 
 
 def peaks():
@@ -157,6 +190,8 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.case == "small":
+        return small_case()
 
     import torch
     import torch.distributed as dist

@@ -262,7 +262,7 @@ static cicero_status render_common(const cicero_grid* grid, const cicero_mlp* ml
   RenderPlan plan;
   cicero_status st = plan_render(grid, mlp, n_rays, s, opt, &plan, true);
   if (st != CICERO_OK) return st;
-  if (!rgb) return fail(CICERO_ERR_INVALID_ARG, "rgb is NULL");
+  if (!rgb && n_rays > 0) return fail(CICERO_ERR_INVALID_ARG, "rgb is NULL");
   if (!ws_ok(ws)) return fail(CICERO_ERR_INVALID_ARG, "workspace must be non-NULL and 256-byte aligned");
   RenderWs w;
   if (!carve_render_ws(ws, ws_bytes, plan, &w)) return fail(CICERO_ERR_WORKSPACE_TOO_SMALL, "workspace too small");
@@ -464,6 +464,8 @@ cicero_status cicero_mlp_eval(const cicero_mlp* mlp, const float* x, int M, cice
   if (st != CICERO_OK) return st;
   if (M < 0 || (M > 0 && (!x || !c))) return fail(CICERO_ERR_INVALID_ARG, "x/c is NULL or M < 0");
   if (!ws_ok(workspace) || ws_bytes < 256) return fail(CICERO_ERR_WORKSPACE_TOO_SMALL, "workspace too small");
+  cudaError_t e = cudaMemsetAsync(workspace, 0, 4, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(status word)");
   if (M == 0) return CICERO_OK;
   const MlpPtrs p = mlp_ptrs(mlp);
   if (precision == CICERO_MLP_BF16) return launch_mlp_eval_bf16(p, x, M, c, (uint32_t*)workspace, (cudaStream_t)stream);

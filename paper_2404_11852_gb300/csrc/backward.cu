@@ -213,14 +213,20 @@ __global__ void __launch_bounds__(256, 1) k_bwd_brick(GridGeo g, RaySrc src, Mlp
         const bool valid = m < mcnt;
         uint32_t sid = valid ? w.sorted[start + m] : 0;
         const int r = (int)(sid / (uint32_t)S);
-        float o[3], d[3];
-        if (valid) ray_gen(src, r, o, d);
+        float d[3] = {0.0f, 0.0f, 1.0f};
+        if (valid) {
+          const float4 dd = w.ray_dir[r];
+          d[0] = dd.x;
+          d[1] = dd.y;
+          d[2] = dd.z;
+        }
         if (part == 0) {
           int ok = 0;
           if (valid) {
-            float p[3], f[3], fv[24];
+            const float4 pw = w.rec_pw[sid];
+            const float p[3] = {pw.x, pw.y, pw.z};
+            float f[3], fv[24];
             int i0[3];
-            sample_pos(o, d, w.rec_t[sid], p);
             const bool in = index_sample(g, p, i0, f);
             const int l[3] = {i0[0] - bx * B, i0[1] - by * B, i0[2] - bz * B};
             if (!in || l[0] < 0 || l[0] >= B || l[1] < 0 || l[1] >= B || l[2] < 0 || l[2] >= B) {

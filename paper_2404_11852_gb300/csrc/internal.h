@@ -37,9 +37,9 @@ struct RenderWs {
   uint32_t* hdr;        // [0] error bits, [1] tile count, [2] active samples, [3] spare
   uint32_t* ray_n;      // [R] composited samples of each ray
   float* ray_T;         // [R] transmittance after the last composited slot
+  float4* ray_dir;      // [R] unit direction of each ray
   uint32_t* rec_key;    // [R*S] brick id of record (ray r, rank j) at r*S + j
-  float* rec_t;         // [R*S] slot distance t (FP32, bit-identical to the march)
-  float* rec_w;         // [R*S] compositing weight T_k alpha_k
+  float4* rec_pw;       // [R*S] sample position (FP32, bit-identical to the march) and weight T_k alpha_k
   uint16_t* rec_k;      // [R*S] slot index (only for Ray Index Table export; may be null)
   uint32_t* brick_cnt;  // [nb]
   uint32_t* brick_off;  // [nb + 1]

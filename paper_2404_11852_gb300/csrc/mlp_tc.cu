@@ -1,15 +1,20 @@
-// Feature Computation on the 5th-generation tensor cores (tcgen05, sm_103a).
+// Feature Gathering + Feature Computation on the 5th-generation tensor cores (tcgen05, sm_103a).
 //
-// One CTA of 128 threads owns a 128-sample tile at a time:
-//   A1 [128 x 48]  BF16  gathered features + view encoding (written by the threads)
-//   D1 = A1 W1^T   FP32 in tensor memory (columns 0..127)    -> bias, ReLU, BF16 -> A2
-//   D2 = A2 W2^T   FP32 in tensor memory (columns 128..255)  -> bias, ReLU, BF16 -> A2
-//   D3 = A2 W3^T   FP32 in tensor memory (columns 0..15, N padded 3 -> 16) -> bias, sigmoid
-// One elected thread issues tcgen05.mma (kind::f16, BF16 x BF16 -> FP32) and commits to an
-// mbarrier; the four warps read their 32 accumulator rows back with tcgen05.ld.
-// Operands use the canonical K-major, no-swizzle shared-memory layout: 8-row x 16-byte core
-// matrices stored contiguously (128 B), consecutive K core matrices 128 B apart (LBO) and
-// consecutive 8-row groups K*2*8 bytes apart (SBO).
+// One persistent CTA per SM holds the MLP weights in shared memory (BF16, ~48 KB) and runs G
+// independent tile pipelines ("groups" of 4 warps = 128 threads, one thread per sample row), so
+// that while one group gathers features or runs its epilogue on CUDA cores, another group's MMAs
+// keep the tensor pipe busy.  Per 128-sample tile a group runs
+//   gather   : staged brick (TMA, one copy per brick visit) -> trilinear -> BF16 row of A
+//   layer 1  : D = A[128x48] W1^T      (tcgen05.mma kind::f16, FP32 accumulators in TMEM)
+//   epilogue : +b1, ReLU, BF16 (cvt.rn.relu.bf16x2)  -> A[128x128]   (A reused in place)
+//   layer 2  : D = A W2^T  -> +b2, ReLU, BF16 -> A
+//   layer 3  : D = A W3^T  (N padded 3 -> 16) -> +b3, sigmoid -> (c, w) record
+// Each group owns 128 TMEM columns (D of the three layers reuses them: every accumulator is read
+// back before the next MMA is issued) and synchronises on its own named barrier.  The elected
+// thread of a group issues the MMAs and commits them to the group's mbarrier.
+// Operands use the canonical K-major, no-swizzle layout: 8-row x 16-byte core matrices stored as
+// 128 contiguous bytes, K-adjacent core matrices 128 B apart (leading byte offset) and 8-row groups
+// K*16 bytes apart (stride byte offset).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -21,23 +26,27 @@ namespace cicero {
 
 namespace tc {
 
-constexpr int kK1 = kMaxIn;           // 48
-constexpr int kN3 = 16;               // layer-3 N padded to the smallest M=128 MMA width
-constexpr uint32_t kTmemCols = 256;
+constexpr int kK1 = kMaxIn;            // 48: layer-1 K (input padded)
+constexpr int kN3 = 16;                // layer-3 N padded to the smallest M=128 MMA width
+constexpr int kGT = 128;               // threads per group
+constexpr int kMaxGroups = 3;
+constexpr uint32_t kTmemCols = 512;    // all of an SM's tensor memory; 128 columns per group
+constexpr int kActBytes = kTile * kHidden * 2;
 
 struct Smem {
   static constexpr int w1 = 0;                                 // [128][48]  bf16
   static constexpr int w2 = w1 + kHidden * kK1 * 2;            // [128][128] bf16
   static constexpr int w3 = w2 + kHidden * kHidden * 2;        // [16][128]  bf16
-  static constexpr int a1 = w3 + kN3 * kHidden * 2;            // [128][48]  bf16
-  static constexpr int a2 = a1 + kTile * kK1 * 2;              // [128][128] bf16
-  static constexpr int b1 = a2 + kTile * kHidden * 2;          // [128] f32
+  static constexpr int b1 = w3 + kN3 * kHidden * 2;            // [128] f32
   static constexpr int b2 = b1 + kHidden * 4;                  // [128] f32
   static constexpr int b3 = b2 + kHidden * 4;                  // [4] f32
-  static constexpr int bars = ((b3 + 16 + 127) / 128) * 128;   // 2 mbarriers + TMEM address
-  static constexpr int tile = bars + 128;                      // brick box
-  static_assert(tile % 128 == 0 && a1 % 16 == 0 && a2 % 16 == 0 && w2 % 16 == 0 && w3 % 16 == 0, "alignment");
+  static constexpr int bars = ((b3 + 16 + 127) / 128) * 128;   // per group 2 mbarriers; TMEM address at +64
+  static constexpr int groups = bars + 128;                    // per group: activations, then brick tile
+  static_assert(groups % 128 == 0 && w2 % 16 == 0 && w3 % 16 == 0, "alignment");
 };
+
+__host__ __device__ constexpr int align128(int x) { return (x + 127) / 128 * 128; }
+__host__ __device__ constexpr int group_bytes(int box_bytes) { return kActBytes + align128(box_bytes); }
 
 // byte offset of element (row, k) in a K-major no-swizzle operand with K columns
 __device__ __forceinline__ uint32_t kmaj_off(int row, int k, int K) {
@@ -75,7 +84,28 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
+// named barrier of one group (ids 1..3; id 0 is __syncthreads)
+__device__ __forceinline__ void gsync(int g) {
+  asm volatile("bar.sync %0, %1;" ::"r"(g + 1), "r"(kGT) : "memory");
+}
+__device__ __forceinline__ bool gsync_and(int g, bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 p, %1, 0;\n\t"
+      "bar.red.and.pred q, %2, %3, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"((uint32_t)v), "r"(g + 1), "r"(kGT)
+      : "memory");
+  return r != 0;
+}
+
+template <int N>
+__device__ __forceinline__ void tmem_ld(uint32_t taddr, float* v);
+
+template <>
+__device__ __forceinline__ void tmem_ld<16>(uint32_t taddr, float* v) {
   uint32_t r[16];
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
@@ -87,9 +117,31 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
   for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
 }
 
+template <>
+__device__ __forceinline__ void tmem_ld<32>(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; i++) v[i] = __uint_as_float(r[i]);
+}
+
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
   return *reinterpret_cast<uint32_t*>(&h);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16_relu(float lo, float hi) {
+  uint32_t r;
+  asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+  return r;
 }
 
 // 8 consecutive K values of one row -> one 16-byte chunk of a K-major operand
@@ -103,7 +155,6 @@ __device__ __forceinline__ void store_chunk(char* base, int row, int k0, int K, 
 }
 
 __device__ void load_weights(char* sm, const MlpPtrs& m) {
-  // W1: rows n, K padded to 48
   for (int i = threadIdx.x; i < kHidden * (kK1 / 8); i += blockDim.x) {
     const int n = i / (kK1 / 8), k0 = (i % (kK1 / 8)) * 8;
     float v[8];
@@ -135,64 +186,74 @@ __device__ void load_weights(char* sm, const MlpPtrs& m) {
   if (threadIdx.x < 4) b3[threadIdx.x] = threadIdx.x < 3 ? m.b3[threadIdx.x] : 0.0f;
 }
 
-struct TcState {
-  uint32_t tmem;
-  uint32_t phase;
+struct Group {
+  int g;            // group index
+  int m;            // row (thread) inside the group
+  char* act;        // activation operand (A), 32 KB
+  char* tile;       // staged brick
+  uint64_t* bar_tma;
   uint64_t* bar_mma;
+  uint32_t tmem;    // first of the group's 128 TMEM columns
+  uint32_t ph_tma, ph_mma;
 };
 
-// Issue layer `L` (single thread) and wait for it (all threads).  Returns false on timeout.
-__device__ __forceinline__ bool run_layer(char* sm, TcState& st, int layer, uint32_t* err) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
+// Issue one layer (elected thread) and wait for it (whole group).  False on timeout.
+__device__ __forceinline__ bool run_layer(char* sm, Group& G, int layer, uint32_t* err) {
+  gsync(G.g);
+  if (G.m == 0) {
     fence_after();
-    const uint32_t a_base = smem_u32(sm + (layer == 0 ? Smem::a1 : Smem::a2));
+    const uint32_t a_base = smem_u32(G.act);
     const uint32_t b_base = smem_u32(sm + (layer == 0 ? Smem::w1 : layer == 1 ? Smem::w2 : Smem::w3));
     const int K = layer == 0 ? kK1 : kHidden;
-    const uint32_t sbo_a = (uint32_t)K * 16, sbo_b = (uint32_t)K * 16;
+    const uint32_t sbo = (uint32_t)K * 16;
     const uint32_t idesc = idesc_bf16(layer == 2 ? kN3 : kHidden);
-    const uint32_t d = st.tmem + (layer == 1 ? 128u : 0u);
+#pragma unroll 1
     for (int s = 0; s < K / 16; s++) {
-      const uint64_t ad = smem_desc(a_base + 256u * s, 128u, sbo_a);
-      const uint64_t bd = smem_desc(b_base + 256u * s, 128u, sbo_b);
-      mma_bf16(d, ad, bd, idesc, s > 0 ? 1u : 0u);
+      const uint64_t ad = smem_desc(a_base + 256u * s, 128u, sbo);
+      const uint64_t bd = smem_desc(b_base + 256u * s, 128u, sbo);
+      mma_bf16(G.tmem, ad, bd, idesc, s > 0 ? 1u : 0u);
     }
-    mma_commit(st.bar_mma);
+    mma_commit(G.bar_mma);
   }
-  const bool ok = __syncthreads_and(mbar_wait(st.bar_mma, st.phase, err));
-  st.phase ^= 1u;
+  const bool ok = gsync_and(G.g, mbar_wait(G.bar_mma, G.ph_mma, err));
+  G.ph_mma ^= 1u;
   fence_after();
   return ok;
 }
 
-// bias + ReLU of accumulator columns [col0, col0 + 128) -> BF16 into A2 (row = this thread)
-__device__ __forceinline__ void epilogue_hidden(char* sm, const TcState& st, uint32_t col0, const float* bias) {
-  const int warp = threadIdx.x >> 5, row = threadIdx.x;
-  const uint32_t taddr = st.tmem + ((uint32_t)(warp * 32) << 16) + col0;
+// bias + ReLU of the 128 accumulator columns -> BF16 K-major rows of A (row = this thread)
+__device__ __forceinline__ void epilogue_hidden(const Group& G, const float* bias) {
+  const uint32_t taddr = G.tmem + ((uint32_t)((G.m >> 5) * 32) << 16);
 #pragma unroll 1
-  for (int cc = 0; cc < kHidden / 16; cc++) {
-    float v[16];
-    tmem_ld16(taddr + cc * 16, v);
+  for (int cc = 0; cc < kHidden / 32; cc++) {
+    float v[32];
+    tmem_ld<32>(taddr + cc * 32, v);
 #pragma unroll
-    for (int j = 0; j < 16; j++) v[j] = fmaxf(v[j] + bias[cc * 16 + j], 0.0f);
-    store_chunk(sm + Smem::a2, row, cc * 16, kHidden, v);
-    store_chunk(sm + Smem::a2, row, cc * 16 + 8, kHidden, v + 8);
+    for (int q = 0; q < 4; q++) {
+      uint4 o;
+      const float* b = bias + cc * 32 + q * 8;
+      const float* x = v + q * 8;
+      o.x = pack_bf16_relu(x[0] + b[0], x[1] + b[1]);
+      o.y = pack_bf16_relu(x[2] + b[2], x[3] + b[3]);
+      o.z = pack_bf16_relu(x[4] + b[4], x[5] + b[5]);
+      o.w = pack_bf16_relu(x[6] + b[6], x[7] + b[7]);
+      *reinterpret_cast<uint4*>(G.act + kmaj_off(G.m, cc * 32 + q * 8, kHidden)) = o;
+    }
   }
   fence_proxy_async();
   fence_before();
 }
 
-// The three layers of the tile whose A1 is already written (and fenced) by every thread.
-// Returns false on a timeout; c receives this thread's row.
-__device__ __forceinline__ bool mlp_tile(char* sm, TcState& st, uint32_t* err, float c[3]) {
-  if (!run_layer(sm, st, 0, err)) return false;
-  epilogue_hidden(sm, st, 0, (const float*)(sm + Smem::b1));
-  if (!run_layer(sm, st, 1, err)) return false;
-  epilogue_hidden(sm, st, 128, (const float*)(sm + Smem::b2));
-  if (!run_layer(sm, st, 2, err)) return false;
-  const int warp = threadIdx.x >> 5;
+// The three layers of a tile whose A (K = 48 layout) has been written and proxy-fenced by every
+// thread of the group.  c receives this thread's colour.  False on timeout.
+__device__ __forceinline__ bool mlp_tile(char* sm, Group& G, uint32_t* err, float c[3]) {
+  if (!run_layer(sm, G, 0, err)) return false;
+  epilogue_hidden(G, (const float*)(sm + Smem::b1));
+  if (!run_layer(sm, G, 1, err)) return false;
+  epilogue_hidden(G, (const float*)(sm + Smem::b2));
+  if (!run_layer(sm, G, 2, err)) return false;
   float v[16];
-  tmem_ld16(st.tmem + ((uint32_t)(warp * 32) << 16), v);
+  tmem_ld<16>(G.tmem + ((uint32_t)((G.m >> 5) * 32) << 16), v);
   const float* b3 = (const float*)(sm + Smem::b3);
   c[0] = sigmoid_f(v[0] + b3[0]);
   c[1] = sigmoid_f(v[1] + b3[1]);
@@ -201,7 +262,75 @@ __device__ __forceinline__ bool mlp_tile(char* sm, TcState& st, uint32_t* err, f
   return true;
 }
 
-__device__ __forceinline__ void tmem_alloc(uint32_t* slot) {
+// View-direction encoding with the fast hardware sine/cosine (|d| <= 1, error ~1e-6, far below
+// the BF16 rounding of the MLP input) and the double-angle recurrence.
+template <int NF>
+__device__ __forceinline__ void encode_dir_fast(const float d[3], int n_freq_rt, float* x) {
+  const int n_freq = NF ? NF : n_freq_rt;
+  float s[3], c[3];
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    x[a] = d[a];
+    __sincosf(d[a], &s[a], &c[a]);
+  }
+#pragma unroll
+  for (int k = 0; k < n_freq; k++) {
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+      x[3 + 6 * k + a] = s[a];
+      x[3 + 6 * k + 3 + a] = c[a];
+      const float s2 = 2.0f * s[a] * c[a];
+      c[a] = 1.0f - 2.0f * s[a] * s[a];
+      s[a] = s2;
+    }
+  }
+}
+
+template <typename T, int CC>
+__device__ __forceinline__ void tri_tile(const T* tile, int vb, int vx, int Cr, const int l[3], const float f[3],
+                                         float* out) {
+  const int C = CC ? CC : Cr;
+  const float fx = f[0], fy = f[1], fz = f[2];
+  for (int c = 0; c < C; c++) out[c] = 0.0f;
+#pragma unroll
+  for (int q = 0; q < 8; q++) {
+    const int x = l[0] + (q & 1), y = l[1] + ((q >> 1) & 1), z = l[2] + (q >> 2);
+    const float wq = ((q & 1) ? fx : 1.f - fx) * (((q >> 1) & 1) ? fy : 1.f - fy) * ((q >> 2) ? fz : 1.f - fz);
+    const T* v = tile + ((size_t)(z * vb + y) * vx + x) * C;
+    if constexpr (CC == 12 && sizeof(T) == 2) {
+      const uint2* v2 = reinterpret_cast<const uint2*>(v);
+#pragma unroll
+      for (int u = 0; u < 3; u++) {
+        uint2 a = v2[u];
+        float2 lo = __half22float2(*reinterpret_cast<__half2*>(&a.x));
+        float2 hi = __half22float2(*reinterpret_cast<__half2*>(&a.y));
+        out[4 * u + 0] += wq * lo.x;
+        out[4 * u + 1] += wq * lo.y;
+        out[4 * u + 2] += wq * hi.x;
+        out[4 * u + 3] += wq * hi.y;
+      }
+    } else if constexpr (CC == 12 && sizeof(T) == 4) {
+      const float4* v4 = reinterpret_cast<const float4*>(v);
+#pragma unroll
+      for (int u = 0; u < 3; u++) {
+        float4 a = v4[u];
+        out[4 * u + 0] += wq * a.x;
+        out[4 * u + 1] += wq * a.y;
+        out[4 * u + 2] += wq * a.z;
+        out[4 * u + 3] += wq * a.w;
+      }
+    } else {
+      for (int c = 0; c < C; c++) {
+        float vv;
+        if constexpr (sizeof(T) == 4) vv = v[c];
+        else vv = __half2float(v[c]);
+        out[c] += wq * vv;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void tmem_alloc_all(uint32_t* slot) {
   if ((threadIdx.x >> 5) == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
                  "r"(kTmemCols)
@@ -210,7 +339,7 @@ __device__ __forceinline__ void tmem_alloc(uint32_t* slot) {
   }
 }
 
-__device__ __forceinline__ void tmem_free(uint32_t tmem) {
+__device__ __forceinline__ void tmem_free_all(uint32_t tmem) {
   fence_before();
   __syncthreads();
   if ((threadIdx.x >> 5) == 0) {
@@ -219,207 +348,161 @@ __device__ __forceinline__ void tmem_free(uint32_t tmem) {
   }
 }
 
-template <typename T>
-__device__ __forceinline__ void tri_smem_tc(const T* tile, int vb, int vx, int C, const int l[3], const float f[3],
-                                            float* out) {
-  const float fx = f[0], fy = f[1], fz = f[2];
-  for (int c = 0; c < C; c++) out[c] = 0.0f;
-#pragma unroll
-  for (int q = 0; q < 8; q++) {
-    const int x = l[0] + (q & 1), y = l[1] + ((q >> 1) & 1), z = l[2] + (q >> 2);
-    const float wq = ((q & 1) ? fx : 1.f - fx) * (((q >> 1) & 1) ? fy : 1.f - fy) * ((q >> 2) ? fz : 1.f - fz);
-    const T* v = tile + ((size_t)(z * vb + y) * vx + x) * C;
-    if constexpr (sizeof(T) == 2) {
-      if (C == 12) {
-        const uint2* v2 = reinterpret_cast<const uint2*>(v);
-#pragma unroll
-        for (int u = 0; u < 3; u++) {
-          uint2 a = v2[u];
-          float2 lo = __half22float2(*reinterpret_cast<__half2*>(&a.x));
-          float2 hi = __half22float2(*reinterpret_cast<__half2*>(&a.y));
-          out[4 * u + 0] += wq * lo.x;
-          out[4 * u + 1] += wq * lo.y;
-          out[4 * u + 2] += wq * hi.x;
-          out[4 * u + 3] += wq * hi.y;
-        }
-        continue;
-      }
-    } else {
-      if (C == 12) {
-        const float4* v4 = reinterpret_cast<const float4*>(v);
-#pragma unroll
-        for (int u = 0; u < 3; u++) {
-          float4 a = v4[u];
-          out[4 * u + 0] += wq * a.x;
-          out[4 * u + 1] += wq * a.y;
-          out[4 * u + 2] += wq * a.z;
-          out[4 * u + 3] += wq * a.w;
-        }
-        continue;
-      }
-    }
-    for (int c = 0; c < C; c++) {
-      float vv;
-      if constexpr (sizeof(T) == 4) vv = v[c];
-      else vv = __half2float(v[c]);
-      out[c] += wq * vv;
-    }
+// CTA prologue shared by both kernels: weights, barriers, TMEM; returns the group handle.
+__device__ __forceinline__ Group setup(char* sm, const MlpPtrs& mlp, int groups, int box_bytes) {
+  uint64_t* bars = (uint64_t*)(sm + Smem::bars);
+  uint32_t* tslot = (uint32_t*)(sm + Smem::bars + 64);
+  load_weights(sm, mlp);
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < 2 * groups; i++) mbar_init(&bars[i], 1);
+    fence_mbar_init();
   }
+  fence_proxy_async();
+  tmem_alloc_all(tslot);
+  fence_before();
+  __syncthreads();
+  fence_after();
+  Group G;
+  G.g = threadIdx.x / kGT;
+  G.m = threadIdx.x % kGT;
+  G.act = sm + Smem::groups + G.g * group_bytes(box_bytes);
+  G.tile = G.act + kActBytes;
+  G.bar_tma = &bars[2 * G.g];
+  G.bar_mma = &bars[2 * G.g + 1];
+  G.tmem = *tslot + (uint32_t)(G.g * 128);
+  G.ph_tma = 0;
+  G.ph_mma = 0;
+  return G;
 }
 
 }  // namespace tc
 
-template <typename T>
-__global__ void __launch_bounds__(128) k_gather_mlp_bf16(GridGeo g, RaySrc src, int S, MlpPtrs mlp, RenderWs w,
-                                                         const __grid_constant__ CUtensorMap fmap, int vb, int vx,
-                                                         int box_bytes) {
+// The persistent gather + MLP kernel of the BF16 path (launched with 128 * groups threads).
+template <typename T, int CC, int NF>
+__global__ void __launch_bounds__(384, 1) k_gather_mlp_bf16(GridGeo g, int S, MlpPtrs mlp, RenderWs w,
+                                                            const __grid_constant__ CUtensorMap fmap, int vb, int vx,
+                                                            int box_bytes, int groups) {
   using namespace tc;
   extern __shared__ __align__(1024) char sm[];
-  uint64_t* bar_tma = (uint64_t*)(sm + Smem::bars);
-  uint64_t* bar_mma = bar_tma + 1;
-  uint32_t* tslot = (uint32_t*)(bar_tma + 2);
-  T* tile = (T*)(sm + Smem::tile);
-  load_weights(sm, mlp);
-  if (threadIdx.x == 0) {
-    mbar_init(bar_tma, 1);
-    mbar_init(bar_mma, 1);
-    fence_mbar_init();
-  }
-  fence_proxy_async();  // weights written by the threads are read by the tensor cores
-  tmem_alloc(tslot);
-  fence_before();
-  __syncthreads();
-  fence_after();
-  TcState st;
-  st.tmem = *tslot;
-  st.phase = 0;
-  st.bar_mma = bar_mma;
-
+  Group G = setup(sm, mlp, groups, box_bytes);
+  const uint32_t tmem_base = G.tmem - (uint32_t)(G.g * 128);
   const uint32_t n_tiles = w.hdr[1];
   const uint32_t per = (n_tiles + gridDim.x - 1) / gridDim.x;
-  const uint32_t t_begin = blockIdx.x * per, t_end = min(n_tiles, t_begin + per);
-  const int B = g.brick, C = g.C, m = threadIdx.x;
+  const uint32_t c_begin = blockIdx.x * per, c_end = min(n_tiles, c_begin + per);
+  const uint32_t span = c_end > c_begin ? c_end - c_begin : 0;
+  const uint32_t t_begin = c_begin + (span * G.g) / groups, t_end = c_begin + (span * (G.g + 1)) / groups;
+  const int B = g.brick, C = CC ? CC : g.C, m = G.m;
+  const T* tile = (const T*)G.tile;
   int loaded = -1;
-  uint32_t tphase = 0;
   bool alive = true;
-  for (uint32_t ti = t_begin; ti < t_end; ti++) {
+  for (uint32_t ti = t_begin; alive && ti < t_end; ti++) {
     const int b = (int)w.tile_brick[ti];
     const uint32_t start = w.tile_start[ti];
     const uint32_t end = min(start + (uint32_t)kTile, w.brick_off[b + 1]);
     const int mcnt = (int)(end - start);
     const int bx = b % g.nb[0], by = (b / g.nb[0]) % g.nb[1], bz = b / (g.nb[0] * g.nb[1]);
-    if (b != loaded) {
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        mbar_expect_tx(bar_tma, (uint32_t)box_bytes);
-        tma_load_3d(tile, &fmap, bx * B * C, by * B, bz * B, bar_tma);
-      }
-      alive = mbar_wait(bar_tma, tphase, &w.hdr[0]);
-      tphase ^= 1u;
-      loaded = b;
-    }
-    if (!__syncthreads_and(alive)) break;
     uint32_t sid = 0;
+    float4 pw = make_float4(0.f, 0.f, 0.f, 0.f), dir = make_float4(0.f, 0.f, 1.f, 0.f);
+    if (m < mcnt) {  // issue the record loads before waiting for the brick
+      sid = w.sorted[start + m];
+      pw = w.rec_pw[sid];
+      dir = w.ray_dir[sid / (uint32_t)S];
+    }
+    if (b != loaded) {
+      gsync(G.g);  // every thread of the group is done with the previous brick
+      if (m == 0) {
+        mbar_expect_tx(G.bar_tma, (uint32_t)box_bytes);
+        tma_load_3d(G.tile, &fmap, bx * B * C, by * B, bz * B, G.bar_tma);
+      }
+      alive = gsync_and(G.g, mbar_wait(G.bar_tma, G.ph_tma, &w.hdr[0]));
+      G.ph_tma ^= 1u;
+      loaded = b;
+      if (!alive) break;
+    }
     float x[kK1];
 #pragma unroll
     for (int j = 0; j < kK1; j++) x[j] = 0.0f;
     if (m < mcnt) {
-      sid = w.sorted[start + m];
-      const int r = (int)(sid / (uint32_t)S);
-      float o[3], d[3], p[3], f[3];
-      int i0[3];
-      ray_gen(src, r, o, d);
-      sample_pos(o, d, w.rec_t[sid], p);
-      const bool ok = index_sample(g, p, i0, f);
-      const int l[3] = {i0[0] - bx * B, i0[1] - by * B, i0[2] - bz * B};
-      if (!ok || l[0] < 0 || l[0] >= B || l[1] < 0 || l[1] >= B || l[2] < 0 || l[2] >= B)
+      const float p[3] = {pw.x, pw.y, pw.z};
+      int l[3];
+      float f[3];
+      bool ok = true;
+#pragma unroll
+      for (int a = 0; a < 3; a++) {
+        const float ga = __fmul_rn(__fsub_rn(p[a], g.amin[a]), g.inv_h[a]);
+        int i = (int)floorf(ga);
+        if (i > g.n[a] - 2) i = g.n[a] - 2;
+        f[a] = __fsub_rn(ga, (float)i);
+        l[a] = i - (a == 0 ? bx : a == 1 ? by : bz) * B;
+        ok = ok && l[a] >= 0 && l[a] < B;
+      }
+      if (!ok)
         set_err(&w.hdr[0], kErrInternal);
       else
-        tri_smem_tc<T>(tile, vb, vx, C, l, f, x);
-      encode_dir(d, mlp.n_freq, x + C);
+        tri_tile<T, CC>(tile, vb, vx, C, l, f, x);
+      const float d[3] = {dir.x, dir.y, dir.z};
+      encode_dir_fast<NF>(d, mlp.n_freq, x + C);
     }
 #pragma unroll
-    for (int k0 = 0; k0 < kK1; k0 += 8) store_chunk(sm + Smem::a1, m, k0, kK1, x + k0);
+    for (int k0 = 0; k0 < kK1; k0 += 8) store_chunk(G.act, m, k0, kK1, x + k0);
     fence_proxy_async();
     float c[3];
-    if (!mlp_tile(sm, st, &w.hdr[0], c)) {
-      alive = false;
-      break;
-    }
-    if (m < mcnt) {
-      w.rec_c[sid] = make_float4(c[0], c[1], c[2], w.rec_w[sid]);
-    }
+    alive = mlp_tile(sm, G, &w.hdr[0], c);
+    if (alive && m < mcnt) w.rec_c[sid] = make_float4(c[0], c[1], c[2], pw.w);
   }
   if (!alive) {
     // a bounded wait ran out: give in-flight copies and MMAs one more bounded wait
-    mbar_wait(bar_tma, tphase, &w.hdr[0]);
-    mbar_wait(bar_mma, st.phase, &w.hdr[0]);
+    mbar_wait(G.bar_tma, G.ph_tma, &w.hdr[0]);
+    mbar_wait(G.bar_mma, G.ph_mma, &w.hdr[0]);
   }
-  tmem_free(st.tmem);
+  tmem_free_all(tmem_base);
 }
 
 // Feature Computation alone on tensor cores: c = MLP(x), x [M][in_dim] FP32.
-__global__ void __launch_bounds__(128) k_mlp_eval_bf16(MlpPtrs mlp, const float* x, int M, float* c, uint32_t* err) {
+__global__ void __launch_bounds__(384, 1) k_mlp_eval_bf16(MlpPtrs mlp, const float* x, int M, float* c, uint32_t* err) {
   using namespace tc;
   extern __shared__ __align__(1024) char sm[];
-  uint64_t* bar_mma = (uint64_t*)(sm + Smem::bars) + 1;
-  uint32_t* tslot = (uint32_t*)(bar_mma + 1);
-  load_weights(sm, mlp);
-  if (threadIdx.x == 0) {
-    mbar_init(bar_mma, 1);
-    fence_mbar_init();
-  }
-  fence_proxy_async();
-  tmem_alloc(tslot);
-  fence_before();
-  __syncthreads();
-  fence_after();
-  TcState st;
-  st.tmem = *tslot;
-  st.phase = 0;
-  st.bar_mma = bar_mma;
+  Group G = setup(sm, mlp, kMaxGroups, 0);
+  const uint32_t tmem_base = G.tmem - (uint32_t)(G.g * 128);
   const int ntile = (M + kTile - 1) / kTile;
   bool alive = true;
-  for (int t = blockIdx.x; t < ntile; t += gridDim.x) {
-    const int row = t * kTile + threadIdx.x;
+  for (int t = blockIdx.x * kMaxGroups + G.g; alive && t < ntile; t += gridDim.x * kMaxGroups) {
+    const int row = t * kTile + G.m;
     float v[kK1];
 #pragma unroll
     for (int j = 0; j < kK1; j++) v[j] = (row < M && j < mlp.in_dim) ? x[(size_t)row * mlp.in_dim + j] : 0.0f;
 #pragma unroll
-    for (int k0 = 0; k0 < kK1; k0 += 8) store_chunk(sm + Smem::a1, threadIdx.x, k0, kK1, v + k0);
+    for (int k0 = 0; k0 < kK1; k0 += 8) store_chunk(G.act, G.m, k0, kK1, v + k0);
     fence_proxy_async();
     float cc[3];
-    if (!mlp_tile(sm, st, err, cc)) {
-      alive = false;
-      break;
-    }
-    if (row < M) {
+    alive = mlp_tile(sm, G, err, cc);
+    if (alive && row < M) {
       c[3 * row + 0] = cc[0];
       c[3 * row + 1] = cc[1];
       c[3 * row + 2] = cc[2];
     }
   }
-  if (!alive) mbar_wait(bar_mma, st.phase, err);
-  tmem_free(st.tmem);
+  if (!alive) mbar_wait(G.bar_mma, G.ph_mma, err);
+  tmem_free_all(tmem_base);
 }
 
 // -------------------------------------------------------------------------------------------
 
-template <typename T>
-static cicero_status launch_tc(const GridGeo& geo, const RaySrc& src, int S, const MlpPtrs& mlp, const RenderWs& ws,
+template <typename T, int CC, int NF>
+static cicero_status launch_tc(const GridGeo& geo, int S, const MlpPtrs& mlp, const RenderWs& ws,
                                const CUtensorMap& map, const BrickBox& box, cudaStream_t st) {
-  const int smem = tc::Smem::tile + box.box_bytes;
+  using namespace tc;
+  int groups = kMaxGroups;
+  while (groups > 1 && Smem::groups + groups * group_bytes(box.box_bytes) > 227 * 1024) groups--;
+  int smem = Smem::groups + groups * group_bytes(box.box_bytes);
   if (smem > 227 * 1024) return fail(CICERO_ERR_UNSUPPORTED, "brick too large for the tensor-core kernel");
-  auto kern = k_gather_mlp_bf16<T>;
+  smem = std::max(smem, 120 * 1024);  // one CTA per SM: it owns all 512 TMEM columns
+  auto kern = k_gather_mlp_bf16<T, CC, NF>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_gather_mlp_bf16)");
-  int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, smem);
-  if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
-  per_sm = std::max(1, std::min(per_sm, 2));  // 2 x 256 TMEM columns fit in one SM's 512
   {
     ProfScope ps(kStGatherMlp, st);
-    kern<<<num_sms() * per_sm, 128, smem, st>>>(geo, src, S, mlp, ws, map, box.vb, box.vx, box.box_bytes);
+    kern<<<num_sms(), 128 * groups, smem, st>>>(geo, S, mlp, ws, map, box.vb, box.vx, box.box_bytes, groups);
   }
   count_launches(1);
   e = cudaGetLastError();
@@ -430,19 +513,26 @@ cicero_status launch_gather_mlp_bf16(const cicero_grid* grid, const GridGeo& geo
                                      const MlpPtrs& mlp, const RenderWs& ws, const CUtensorMap& map,
                                      const BrickBox& box, cudaStream_t st) {
   (void)samp;
-  if (grid->dtype == CICERO_F16) return launch_tc<__half>(geo, src, ws.S, mlp, ws, map, box, st);
-  return launch_tc<float>(geo, src, ws.S, mlp, ws, map, box, st);
+  (void)src;
+  const bool f16 = grid->dtype == CICERO_F16;
+  if (geo.C == 12 && mlp.n_freq == 4)
+    return f16 ? launch_tc<__half, 12, 4>(geo, ws.S, mlp, ws, map, box, st)
+               : launch_tc<float, 12, 4>(geo, ws.S, mlp, ws, map, box, st);
+  return f16 ? launch_tc<__half, 0, 0>(geo, ws.S, mlp, ws, map, box, st)
+             : launch_tc<float, 0, 0>(geo, ws.S, mlp, ws, map, box, st);
 }
 
 cicero_status launch_mlp_eval_bf16(const MlpPtrs& mlp, const float* x, int M, float* c, uint32_t* err,
                                    cudaStream_t st) {
-  const int smem = tc::Smem::tile;
+  using namespace tc;
+  const int smem = std::max(Smem::groups + kMaxGroups * group_bytes(0), 120 * 1024);
   cudaError_t e = cudaFuncSetAttribute(k_mlp_eval_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_mlp_eval_bf16)");
   const int ntile = (M + kTile - 1) / kTile;
+  const int grid = std::max(1, std::min((ntile + kMaxGroups - 1) / kMaxGroups, num_sms()));
   {
     ProfScope ps(kStMlpEval, st);
-    k_mlp_eval_bf16<<<std::max(1, std::min(ntile, num_sms() * 2)), 128, smem, st>>>(mlp, x, M, c, err);
+    k_mlp_eval_bf16<<<grid, 384, smem, st>>>(mlp, x, M, c, err);
   }
   count_launches(1);
   e = cudaGetLastError();

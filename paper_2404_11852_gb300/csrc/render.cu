@@ -23,8 +23,8 @@ static size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 size_t render_ws_bytes(const RenderPlan& p) {
   size_t RS = (size_t)p.R * p.S;
   size_t b = al256(64);
-  b += 2 * al256(4 * (size_t)p.R);
-  b += 3 * al256(4 * RS);
+  b += 2 * al256(4 * (size_t)p.R) + al256(16 * (size_t)p.R);
+  b += al256(4 * RS) + al256(16 * RS);
   if (p.want_k) b += al256(2 * RS);
   b += 2 * al256(4 * (size_t)p.nb) + al256(4 * ((size_t)p.nb + 1));
   b += 2 * al256(4 * (size_t)p.max_tiles);
@@ -46,9 +46,9 @@ bool carve_render_ws(void* ws, size_t bytes, const RenderPlan& p, RenderWs* w) {
   w->hdr = (uint32_t*)take(64);
   w->ray_n = (uint32_t*)take(4 * (size_t)p.R);
   w->ray_T = (float*)take(4 * (size_t)p.R);
+  w->ray_dir = (float4*)take(16 * (size_t)p.R);
   w->rec_key = (uint32_t*)take(4 * RS);
-  w->rec_t = (float*)take(4 * RS);
-  w->rec_w = (float*)take(4 * RS);
+  w->rec_pw = (float4*)take(16 * RS);
   w->rec_k = p.want_k ? (uint16_t*)take(2 * RS) : nullptr;
   w->brick_cnt = (uint32_t*)take(4 * (size_t)p.nb);
   w->brick_cur = (uint32_t*)take(4 * (size_t)p.nb);
@@ -107,11 +107,10 @@ __global__ void __launch_bounds__(256) k_march(GridGeo g, Samp s, RaySrc src, co
       const bool valid = slot_valid(sl, k, t);
       const unsigned vmask = __ballot_sync(0xffffffffu, valid);
       int i0[3] = {0, 0, 0};
-      float f[3];
+      float f[3], p[3] = {0.0f, 0.0f, 0.0f};
       bool act = false;
       float sd = 0.0f, raw = 0.0f;
       if (valid) {
-        float p[3];
         sample_pos(o, d, t, p);
         act = index_sample(g, p, i0, f);
         if (act) {
@@ -137,8 +136,7 @@ __global__ void __launch_bounds__(256) k_march(GridGeo g, Samp s, RaySrc src, co
       const uint32_t key = contrib ? brick_id(g, i0) : 0xffffffffu;
       if (contrib) {
         size_t q = rec0 + cnt + __popc(cmask & lt_mask);
-        w.rec_t[q] = t;
-        w.rec_w[q] = wk;
+        w.rec_pw[q] = make_float4(p[0], p[1], p[2], wk);
         w.rec_key[q] = key;
         if (w.rec_k) w.rec_k[q] = (uint16_t)k;
         if (w.rec_T) {
@@ -166,6 +164,7 @@ __global__ void __launch_bounds__(256) k_march(GridGeo g, Samp s, RaySrc src, co
     if (lane == 0) {
       w.ray_n[r] = cnt;
       w.ray_T[r] = expf(-Ssum);
+      w.ray_dir[r] = make_float4(d[0], d[1], d[2], 0.0f);
       const int oi = out_index(src, r);
       if (depth) depth[oi] = acc >= s.void_acc ? dsum / acc : __int_as_float(0x7f800000);
       if (acc_out) acc_out[oi] = acc;
@@ -457,7 +456,7 @@ __device__ __forceinline__ void mlp_f32_tile(char* sm, float c[3]) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256, 1) k_gather_mlp_f32(GridGeo g, RaySrc src, int S, MlpPtrs mlp, RenderWs w,
+__global__ void __launch_bounds__(256, 1) k_gather_mlp_f32(GridGeo g, int S, MlpPtrs mlp, RenderWs w,
                                                            const __grid_constant__ CUtensorMap fmap, int vb, int vx,
                                                            int box_bytes) {
   extern __shared__ __align__(128) char sm[];
@@ -498,12 +497,11 @@ __global__ void __launch_bounds__(256, 1) k_gather_mlp_f32(GridGeo g, RaySrc src
     if (m < mcnt) {
       const uint32_t sid = w.sorted[start + m];
       const int r = (int)(sid / (uint32_t)S);
-      float o[3], d[3];
-      ray_gen(src, r, o, d);
       if (part == 0) {
-        float p[3], f[3], feat[24];
+        const float4 pw = w.rec_pw[sid];
+        const float p[3] = {pw.x, pw.y, pw.z};
+        float f[3], feat[24];
         int i0[3];
-        sample_pos(o, d, w.rec_t[sid], p);
         const bool ok = index_sample(g, p, i0, f);
         const int l[3] = {i0[0] - bx * B, i0[1] - by * B, i0[2] - bz * B};
         if (!ok || l[0] < 0 || l[0] >= B || l[1] < 0 || l[1] >= B || l[2] < 0 || l[2] >= B) {
@@ -514,6 +512,8 @@ __global__ void __launch_bounds__(256, 1) k_gather_mlp_f32(GridGeo g, RaySrc src
           for (int c = 0; c < C; c++) X[c * kTile + m] = feat[c];
         }
       } else {
+        const float4 dd = w.ray_dir[r];
+        const float d[3] = {dd.x, dd.y, dd.z};
         float e[3 + 6 * 7];
         encode_dir(d, mlp.n_freq, e);
         const int ne = 3 + 6 * mlp.n_freq;
@@ -531,7 +531,7 @@ __global__ void __launch_bounds__(256, 1) k_gather_mlp_f32(GridGeo g, RaySrc src
     mlp_f32_tile(sm, c);
     if (threadIdx.x < kTile && m < mcnt) {
       const uint32_t sid = w.sorted[start + m];
-      w.rec_c[sid] = make_float4(c[0], c[1], c[2], w.rec_w[sid]);
+      w.rec_c[sid] = make_float4(c[0], c[1], c[2], w.rec_pw[sid].w);
     }
   }
 }
@@ -609,7 +609,7 @@ static cicero_status launch_f32(const GridGeo& geo, const RaySrc& src, int S, co
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_gather_mlp_f32)");
   {
     ProfScope ps(kStGatherMlp, st);
-    kern<<<num_sms(), 256, smem, st>>>(geo, src, S, mlp, ws, map, box.vb, box.vx, box.box_bytes);
+    kern<<<num_sms(), 256, smem, st>>>(geo, S, mlp, ws, map, box.vb, box.vx, box.box_bytes);
   }
   count_launches(1);
   e = cudaGetLastError();
