@@ -290,6 +290,13 @@ def main():
     hdr = ws_r[:16].view(torch.int32).cpu().numpy()
     active = int(hdr[2])
     t_bf16 = timed(lambda: full(o16), n_fp, 1)
+    sweep = {}
+    for bsz in (4, 8, 16):
+        ob = cc.options(cc.MLP_BF16, bsz)
+        wsb = cc.workspace(cc.cicero_render_workspace_size(grid.desc, R, sd, ob), dev)
+        tb = timed(lambda: cc.cicero_render(grid.desc, mlp.desc, cd, sd, ob, ref_rgb, ref_depth, None, None, wsb), 2, 1)
+        sweep[str(bsz)] = 2 * world / tb
+        del wsb
 
     # per-stage device time (CUDA events on the launching stream) over two profiled windows
     cc.cicero_profile_begin()
@@ -348,6 +355,7 @@ def main():
             "msamples_per_s_bf16_full": active * n_fp * world / t_bf16 / 1e6,
             "msamples_per_s_fp32_full": active * n_fp * world / t_fp32 / 1e6,
             "active_samples_per_frame": active,
+            "bf16_full_fps_by_brick": sweep,
             "fraction_rays_marched_targets": holes / (N_TARGETS * R),
             "roofline": roof, "stages": stages, "quality": quality, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "frames/s", "h2d_bytes_per_step": int(pose_h.numel() * 4),

@@ -44,6 +44,8 @@ struct RenderWs {
   uint32_t* brick_cnt;  // [nb]
   uint32_t* brick_off;  // [nb + 1]
   uint32_t* brick_cur;  // [nb]
+  uint32_t* tile_off;   // [nb + 1] first tile of each brick
+  uint32_t* blk_sums;   // [2 * scan blocks] per-block sums of the brick scan
   uint32_t* tile_brick; // [max_tiles]
   uint32_t* tile_start; // [max_tiles]
   uint32_t* sorted;     // [R*S] record ids grouped by brick

@@ -29,7 +29,7 @@ namespace tc {
 constexpr int kK1 = kMaxIn;            // 48: layer-1 K (input padded)
 constexpr int kN3 = 16;                // layer-3 N padded to the smallest M=128 MMA width
 constexpr int kGT = 128;               // threads per group
-constexpr int kMaxGroups = 3;
+constexpr int kMaxGroups = 4;
 constexpr uint32_t kTmemCols = 512;    // all of an SM's tensor memory; 128 columns per group
 constexpr int kActBytes = kTile * kHidden * 2;
 
@@ -40,7 +40,7 @@ struct Smem {
   static constexpr int b1 = w3 + kN3 * kHidden * 2;            // [128] f32
   static constexpr int b2 = b1 + kHidden * 4;                  // [128] f32
   static constexpr int b3 = b2 + kHidden * 4;                  // [4] f32
-  static constexpr int bars = ((b3 + 16 + 127) / 128) * 128;   // per group 2 mbarriers; TMEM address at +64
+  static constexpr int bars = ((b3 + 16 + 127) / 128) * 128;   // per group 2 mbarriers; TMEM address at +96
   static constexpr int groups = bars + 128;                    // per group: activations, then brick tile
   static_assert(groups % 128 == 0 && w2 % 16 == 0 && w3 % 16 == 0, "alignment");
 };
@@ -84,7 +84,7 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// named barrier of one group (ids 1..3; id 0 is __syncthreads)
+// named barrier of one group (ids 1..4; id 0 is __syncthreads)
 __device__ __forceinline__ void gsync(int g) {
   asm volatile("bar.sync %0, %1;" ::"r"(g + 1), "r"(kGT) : "memory");
 }
@@ -144,6 +144,23 @@ __device__ __forceinline__ uint32_t pack_bf16_relu(float lo, float hi) {
   return r;
 }
 
+// y[0..3] = x[0..3] + b (two packed FP32 adds)
+__device__ __forceinline__ void add2(const float* x, float4 b, float* y) {
+  uint64_t r0, r1;
+  asm("add.rn.f32x2 %0, %1, %2;"
+      : "=l"(r0)
+      : "l"((uint64_t)__float_as_uint(x[0]) | ((uint64_t)__float_as_uint(x[1]) << 32)),
+        "l"((uint64_t)__float_as_uint(b.x) | ((uint64_t)__float_as_uint(b.y) << 32)));
+  asm("add.rn.f32x2 %0, %1, %2;"
+      : "=l"(r1)
+      : "l"((uint64_t)__float_as_uint(x[2]) | ((uint64_t)__float_as_uint(x[3]) << 32)),
+        "l"((uint64_t)__float_as_uint(b.z) | ((uint64_t)__float_as_uint(b.w) << 32)));
+  y[0] = __uint_as_float((uint32_t)r0);
+  y[1] = __uint_as_float((uint32_t)(r0 >> 32));
+  y[2] = __uint_as_float((uint32_t)r1);
+  y[3] = __uint_as_float((uint32_t)(r1 >> 32));
+}
+
 // 8 consecutive K values of one row -> one 16-byte chunk of a K-major operand
 __device__ __forceinline__ void store_chunk(char* base, int row, int k0, int K, const float* v) {
   uint4 q;
@@ -159,7 +176,10 @@ __device__ void load_weights(char* sm, const MlpPtrs& m) {
     const int n = i / (kK1 / 8), k0 = (i % (kK1 / 8)) * 8;
     float v[8];
 #pragma unroll
-    for (int j = 0; j < 8; j++) v[j] = (k0 + j < m.in_dim) ? m.w1[n * m.in_dim + k0 + j] : 0.0f;
+    for (int j = 0; j < 8; j++) {
+      const int k = k0 + j;
+      v[j] = k < m.in_dim ? m.w1[n * m.in_dim + k] : (k == m.in_dim ? m.b1[n] : 0.0f);  // b1 rides on x[in_dim] = 1
+    }
     store_chunk(sm + Smem::w1, n, k0, kK1, v);
   }
   for (int i = threadIdx.x; i < kHidden * (kHidden / 8); i += blockDim.x) {
@@ -180,7 +200,7 @@ __device__ void load_weights(char* sm, const MlpPtrs& m) {
   float* b2 = (float*)(sm + Smem::b2);
   float* b3 = (float*)(sm + Smem::b3);
   for (int i = threadIdx.x; i < kHidden; i += blockDim.x) {
-    b1[i] = m.b1[i];
+    b1[i] = m.in_dim < kK1 ? 0.0f : m.b1[i];  // folded into W1 unless the input fills all 48 columns
     b2[i] = m.b2[i];
   }
   if (threadIdx.x < 4) b3[threadIdx.x] = threadIdx.x < 3 ? m.b3[threadIdx.x] : 0.0f;
@@ -230,13 +250,15 @@ __device__ __forceinline__ void epilogue_hidden(const Group& G, const float* bia
     tmem_ld<32>(taddr + cc * 32, v);
 #pragma unroll
     for (int q = 0; q < 4; q++) {
+      const float4* b4 = reinterpret_cast<const float4*>(bias + cc * 32 + q * 8);
+      float y[8];
+      add2(v + q * 8, b4[0], y);
+      add2(v + q * 8 + 4, b4[1], y + 4);
       uint4 o;
-      const float* b = bias + cc * 32 + q * 8;
-      const float* x = v + q * 8;
-      o.x = pack_bf16_relu(x[0] + b[0], x[1] + b[1]);
-      o.y = pack_bf16_relu(x[2] + b[2], x[3] + b[3]);
-      o.z = pack_bf16_relu(x[4] + b[4], x[5] + b[5]);
-      o.w = pack_bf16_relu(x[6] + b[6], x[7] + b[7]);
+      o.x = pack_bf16_relu(y[0], y[1]);
+      o.y = pack_bf16_relu(y[2], y[3]);
+      o.z = pack_bf16_relu(y[4], y[5]);
+      o.w = pack_bf16_relu(y[6], y[7]);
       *reinterpret_cast<uint4*>(G.act + kmaj_off(G.m, cc * 32 + q * 8, kHidden)) = o;
     }
   }
@@ -351,7 +373,7 @@ __device__ __forceinline__ void tmem_free_all(uint32_t tmem) {
 // CTA prologue shared by both kernels: weights, barriers, TMEM; returns the group handle.
 __device__ __forceinline__ Group setup(char* sm, const MlpPtrs& mlp, int groups, int box_bytes) {
   uint64_t* bars = (uint64_t*)(sm + Smem::bars);
-  uint32_t* tslot = (uint32_t*)(sm + Smem::bars + 64);
+  uint32_t* tslot = (uint32_t*)(sm + Smem::bars + 96);
   load_weights(sm, mlp);
   if (threadIdx.x == 0) {
     for (int i = 0; i < 2 * groups; i++) mbar_init(&bars[i], 1);
@@ -379,7 +401,7 @@ __device__ __forceinline__ Group setup(char* sm, const MlpPtrs& mlp, int groups,
 
 // The persistent gather + MLP kernel of the BF16 path (launched with 128 * groups threads).
 template <typename T, int CC, int NF>
-__global__ void __launch_bounds__(384, 1) k_gather_mlp_bf16(GridGeo g, int S, MlpPtrs mlp, RenderWs w,
+__global__ void __launch_bounds__(512, 1) k_gather_mlp_bf16(GridGeo g, int S, MlpPtrs mlp, RenderWs w,
                                                             const __grid_constant__ CUtensorMap fmap, int vb, int vx,
                                                             int box_bytes, int groups) {
   using namespace tc;
@@ -391,32 +413,43 @@ __global__ void __launch_bounds__(384, 1) k_gather_mlp_bf16(GridGeo g, int S, Ml
   const uint32_t c_begin = blockIdx.x * per, c_end = min(n_tiles, c_begin + per);
   const uint32_t span = c_end > c_begin ? c_end - c_begin : 0;
   const uint32_t t_begin = c_begin + (span * G.g) / groups, t_end = c_begin + (span * (G.g + 1)) / groups;
-  const int B = g.brick, C = CC ? CC : g.C, m = G.m;
+  const int B = g.brick, C = CC ? CC : g.C, m = G.m, in_dim = mlp.in_dim;
   const T* tile = (const T*)G.tile;
   int loaded = -1;
-  bool alive = true;
-  for (uint32_t ti = t_begin; alive && ti < t_end; ti++) {
-    const int b = (int)w.tile_brick[ti];
-    const uint32_t start = w.tile_start[ti];
-    const uint32_t end = min(start + (uint32_t)kTile, w.brick_off[b + 1]);
-    const int mcnt = (int)(end - start);
-    const int bx = b % g.nb[0], by = (b / g.nb[0]) % g.nb[1], bz = b / (g.nb[0] * g.nb[1]);
-    uint32_t sid = 0;
-    float4 pw = make_float4(0.f, 0.f, 0.f, 0.f), dir = make_float4(0.f, 0.f, 1.f, 0.f);
-    if (m < mcnt) {  // issue the record loads before waiting for the brick
-      sid = w.sorted[start + m];
-      pw = w.rec_pw[sid];
-      dir = w.ray_dir[sid / (uint32_t)S];
+  bool alive = true, pending = false;
+  // records of the tile being gathered, loaded one tile ahead
+  int nb_ = 0, nmcnt = 0;
+  uint32_t nstart = 0, nsid = 0;
+  float4 npw = make_float4(0.f, 0.f, 0.f, 0.f), ndir = make_float4(0.f, 0.f, 1.f, 0.f);
+  auto fetch = [&](uint32_t ti) {
+    nb_ = (int)w.tile_brick[ti];
+    nstart = w.tile_start[ti];
+    nmcnt = (int)(min(nstart + (uint32_t)kTile, w.brick_off[nb_ + 1]) - nstart);
+    if (m < nmcnt) {
+      nsid = w.sorted[nstart + m];
+      npw = w.rec_pw[nsid];
+      ndir = w.ray_dir[nsid / (uint32_t)S];
     }
+  };
+  if (t_begin < t_end) fetch(t_begin);
+  for (uint32_t ti = t_begin; alive && ti < t_end; ti++) {
+    const int b = nb_, mcnt = nmcnt;
+    const uint32_t sid = nsid;
+    const float4 pw = npw, dir = ndir;
+    const int bx = b % g.nb[0], by = (b / g.nb[0]) % g.nb[1], bz = b / (g.nb[0] * g.nb[1]);
     if (b != loaded) {
       gsync(G.g);  // every thread of the group is done with the previous brick
       if (m == 0) {
         mbar_expect_tx(G.bar_tma, (uint32_t)box_bytes);
         tma_load_3d(G.tile, &fmap, bx * B * C, by * B, bz * B, G.bar_tma);
       }
+      loaded = b;
+      pending = true;
+    }
+    if (pending) {
       alive = gsync_and(G.g, mbar_wait(G.bar_tma, G.ph_tma, &w.hdr[0]));
       G.ph_tma ^= 1u;
-      loaded = b;
+      pending = false;
       if (!alive) break;
     }
     float x[kK1];
@@ -442,24 +475,57 @@ __global__ void __launch_bounds__(384, 1) k_gather_mlp_bf16(GridGeo g, int S, Ml
         tri_tile<T, CC>(tile, vb, vx, C, l, f, x);
       const float d[3] = {dir.x, dir.y, dir.z};
       encode_dir_fast<NF>(d, mlp.n_freq, x + C);
+      if (in_dim < kK1) x[CC && NF ? (CC + 3 + 6 * NF) % kK1 : in_dim % kK1] = 1.0f;  // folded layer-1 bias
     }
 #pragma unroll
     for (int k0 = 0; k0 < kK1; k0 += 8) store_chunk(G.act, m, k0, kK1, x + k0);
     fence_proxy_async();
-    float c[3];
-    alive = mlp_tile(sm, G, &w.hdr[0], c);
-    if (alive && m < mcnt) w.rec_c[sid] = make_float4(c[0], c[1], c[2], pw.w);
+    // load the next tile's records while this tile is on the tensor cores
+    if (ti + 1 < t_end) fetch(ti + 1);
+    // layer 1, plus the next brick's TMA copy once every thread has finished gathering
+    gsync(G.g);
+    if (m == 0) {
+      fence_after();
+      const uint32_t a_base = smem_u32(G.act), b_base = smem_u32(sm + Smem::w1);
+#pragma unroll 1
+      for (int s2 = 0; s2 < kK1 / 16; s2++)
+        mma_bf16(G.tmem, smem_desc(a_base + 256u * s2, 128u, kK1 * 16), smem_desc(b_base + 256u * s2, 128u, kK1 * 16),
+                 idesc_bf16(kHidden), s2 > 0 ? 1u : 0u);
+      mma_commit(G.bar_mma);
+    }
+    if (ti + 1 < t_end && nb_ != loaded) {
+      if (m == 0) {
+        const int nbx = nb_ % g.nb[0], nby = (nb_ / g.nb[0]) % g.nb[1], nbz = nb_ / (g.nb[0] * g.nb[1]);
+        mbar_expect_tx(G.bar_tma, (uint32_t)box_bytes);
+        tma_load_3d(G.tile, &fmap, nbx * B * C, nby * B, nbz * B, G.bar_tma);
+      }
+      loaded = nb_;
+      pending = true;
+    }
+    alive = gsync_and(G.g, mbar_wait(G.bar_mma, G.ph_mma, &w.hdr[0]));
+    G.ph_mma ^= 1u;
+    fence_after();
+    if (!alive) break;
+    epilogue_hidden(G, (const float*)(sm + Smem::b1));
+    if (!(alive = run_layer(sm, G, 1, &w.hdr[0]))) break;
+    epilogue_hidden(G, (const float*)(sm + Smem::b2));
+    if (!(alive = run_layer(sm, G, 2, &w.hdr[0]))) break;
+    float v[16];
+    tmem_ld<16>(G.tmem + ((uint32_t)((m >> 5) * 32) << 16), v);
+    const float* b3 = (const float*)(sm + Smem::b3);
+    fence_before();
+    if (m < mcnt) w.rec_c[sid] = make_float4(sigmoid_f(v[0] + b3[0]), sigmoid_f(v[1] + b3[1]), sigmoid_f(v[2] + b3[2]), pw.w);
   }
-  if (!alive) {
-    // a bounded wait ran out: give in-flight copies and MMAs one more bounded wait
+  if (!alive || pending) {
+    // a bounded wait ran out (or a prefetched copy is still landing): wait once more, bounded
     mbar_wait(G.bar_tma, G.ph_tma, &w.hdr[0]);
-    mbar_wait(G.bar_mma, G.ph_mma, &w.hdr[0]);
+    if (!alive) mbar_wait(G.bar_mma, G.ph_mma, &w.hdr[0]);
   }
   tmem_free_all(tmem_base);
 }
 
 // Feature Computation alone on tensor cores: c = MLP(x), x [M][in_dim] FP32.
-__global__ void __launch_bounds__(384, 1) k_mlp_eval_bf16(MlpPtrs mlp, const float* x, int M, float* c, uint32_t* err) {
+__global__ void __launch_bounds__(512, 1) k_mlp_eval_bf16(MlpPtrs mlp, const float* x, int M, float* c, uint32_t* err) {
   using namespace tc;
   extern __shared__ __align__(1024) char sm[];
   Group G = setup(sm, mlp, kMaxGroups, 0);
@@ -470,7 +536,8 @@ __global__ void __launch_bounds__(384, 1) k_mlp_eval_bf16(MlpPtrs mlp, const flo
     const int row = t * kTile + G.m;
     float v[kK1];
 #pragma unroll
-    for (int j = 0; j < kK1; j++) v[j] = (row < M && j < mlp.in_dim) ? x[(size_t)row * mlp.in_dim + j] : 0.0f;
+    for (int j = 0; j < kK1; j++)
+      v[j] = (row < M && j < mlp.in_dim) ? x[(size_t)row * mlp.in_dim + j] : (j == mlp.in_dim ? 1.0f : 0.0f);
 #pragma unroll
     for (int k0 = 0; k0 < kK1; k0 += 8) store_chunk(G.act, G.m, k0, kK1, v + k0);
     fence_proxy_async();
@@ -532,7 +599,7 @@ cicero_status launch_mlp_eval_bf16(const MlpPtrs& mlp, const float* x, int M, fl
   const int grid = std::max(1, std::min((ntile + kMaxGroups - 1) / kMaxGroups, num_sms()));
   {
     ProfScope ps(kStMlpEval, st);
-    k_mlp_eval_bf16<<<grid, 384, smem, st>>>(mlp, x, M, c, err);
+    k_mlp_eval_bf16<<<grid, 128 * kMaxGroups, smem, st>>>(mlp, x, M, c, err);
   }
   count_launches(1);
   e = cudaGetLastError();

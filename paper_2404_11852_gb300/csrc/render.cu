@@ -3,7 +3,7 @@
 //   K1 k_march        one warp per ray, 32 slots per step: Indexing, density gathering,
 //                     alpha, transmittance by a warp scan of sigma*delta, early stop; emits one
 //                     record (t, w, brick) per composited sample and a brick histogram
-//   K2 k_brick_scan   brick offsets (exclusive scan of the histogram) and the tile list
+//   K2 k_brick_*      brick offsets (3-phase exclusive scan of the histogram) and the tile list
 //   K3 k_scatter      counting sort of the records by brick: the Ray Index Table
 //   K5 k_gather_mlp_f32 / mlp_tc.cu
 //                     per brick: one TMA copy of the brick (+1 vertex halo) into shared memory,
@@ -26,7 +26,8 @@ size_t render_ws_bytes(const RenderPlan& p) {
   b += 2 * al256(4 * (size_t)p.R) + al256(16 * (size_t)p.R);
   b += al256(4 * RS) + al256(16 * RS);
   if (p.want_k) b += al256(2 * RS);
-  b += 2 * al256(4 * (size_t)p.nb) + al256(4 * ((size_t)p.nb + 1));
+  b += 2 * al256(4 * (size_t)p.nb) + 2 * al256(4 * ((size_t)p.nb + 1));
+  b += al256(8 * ((size_t)p.nb / 4096 + 2));
   b += 2 * al256(4 * (size_t)p.max_tiles);
   b += al256(4 * RS);
   b += al256(16 * RS);
@@ -53,6 +54,8 @@ bool carve_render_ws(void* ws, size_t bytes, const RenderPlan& p, RenderWs* w) {
   w->brick_cnt = (uint32_t*)take(4 * (size_t)p.nb);
   w->brick_cur = (uint32_t*)take(4 * (size_t)p.nb);
   w->brick_off = (uint32_t*)take(4 * ((size_t)p.nb + 1));
+  w->tile_off = (uint32_t*)take(4 * ((size_t)p.nb + 1));
+  w->blk_sums = (uint32_t*)take(8 * ((size_t)p.nb / 4096 + 2));
   w->tile_brick = (uint32_t*)take(4 * (size_t)p.max_tiles);
   w->tile_start = (uint32_t*)take(4 * (size_t)p.max_tiles);
   w->sorted = (uint32_t*)take(4 * RS);
@@ -213,38 +216,93 @@ __device__ __forceinline__ void block_exscan2(uint32_t a, uint32_t b, uint32_t* 
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(1024) k_brick_scan(RenderWs w) {
+// K2a: per block of kScanChunk bricks, the sums of sample counts and tile counts.
+constexpr int kScanChunk = 4096;  // bricks per scan block (1024 threads x 4)
+
+__global__ void __launch_bounds__(1024) k_brick_sums(RenderWs w) {
   __shared__ uint32_t sh[64];
-  uint32_t run_s = 0, run_t = 0;
-  for (int base = 0; base < w.nb; base += blockDim.x) {
-    const int i = base + threadIdx.x;
-    const uint32_t c = i < w.nb ? w.brick_cnt[i] : 0;
-    const uint32_t nt = (c + kTile - 1) / kTile;
-    uint32_t es, et, ts, tt;
-    block_exscan2(c, nt, &es, &et, &ts, &tt, sh);
-    if (i < w.nb) {
-      const uint32_t off = run_s + es;
-      w.brick_off[i] = off;
-      w.brick_cur[i] = 0;
-      for (uint32_t q = 0; q < nt; q++) {
-        const uint32_t ti = run_t + et + q;
-        if (ti < (uint32_t)w.max_tiles) {
-          w.tile_brick[ti] = i;
-          w.tile_start[ti] = off + q * kTile;
-        }
-      }
+  const int base = blockIdx.x * kScanChunk + threadIdx.x * 4;
+  uint32_t c = 0, t = 0;
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+    const uint32_t v = base + k < w.nb ? w.brick_cnt[base + k] : 0;
+    c += v;
+    t += (v + kTile - 1) / kTile;
+  }
+  uint32_t ec, et, tc, tt;
+  block_exscan2(c, t, &ec, &et, &tc, &tt, sh);
+  if (threadIdx.x == 0) {
+    w.blk_sums[2 * blockIdx.x] = tc;
+    w.blk_sums[2 * blockIdx.x + 1] = tt;
+  }
+}
+
+// K2b: exclusive scan of the block sums (one block); totals into the header.
+__global__ void __launch_bounds__(1024) k_brick_blocks(RenderWs w, int nblk) {
+  __shared__ uint32_t sh[64];
+  uint32_t run_c = 0, run_t = 0;
+  for (int b0 = 0; b0 < nblk; b0 += blockDim.x) {
+    const int i = b0 + threadIdx.x;
+    const uint32_t c = i < nblk ? w.blk_sums[2 * i] : 0, t = i < nblk ? w.blk_sums[2 * i + 1] : 0;
+    uint32_t ec, et, tc, tt;
+    block_exscan2(c, t, &ec, &et, &tc, &tt, sh);
+    if (i < nblk) {
+      w.blk_sums[2 * i] = run_c + ec;
+      w.blk_sums[2 * i + 1] = run_t + et;
     }
-    run_s += ts;
+    run_c += tc;
     run_t += tt;
   }
   if (threadIdx.x == 0) {
-    w.brick_off[w.nb] = run_s;
+    w.brick_off[w.nb] = run_c;
+    w.tile_off[w.nb] = run_t;
     if (run_t > (uint32_t)w.max_tiles) {
       set_err(&w.hdr[0], kErrInternal);
       run_t = w.max_tiles;
     }
     w.hdr[1] = run_t;
-    w.hdr[2] = run_s;
+    w.hdr[2] = run_c;
+  }
+}
+
+// K2c: brick and tile offsets of every brick; cursors reset for the scatter.
+__global__ void __launch_bounds__(1024) k_brick_offsets(RenderWs w) {
+  __shared__ uint32_t sh[64];
+  const int base = blockIdx.x * kScanChunk + threadIdx.x * 4;
+  uint32_t v[4], c = 0, t = 0;
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+    v[k] = base + k < w.nb ? w.brick_cnt[base + k] : 0;
+    c += v[k];
+    t += (v[k] + kTile - 1) / kTile;
+  }
+  uint32_t ec, et, tc, tt;
+  block_exscan2(c, t, &ec, &et, &tc, &tt, sh);
+  uint32_t oc = w.blk_sums[2 * blockIdx.x] + ec, ot = w.blk_sums[2 * blockIdx.x + 1] + et;
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+    if (base + k < w.nb) {
+      w.brick_off[base + k] = oc;
+      w.tile_off[base + k] = ot;
+      w.brick_cur[base + k] = 0;
+    }
+    oc += v[k];
+    ot += (v[k] + kTile - 1) / kTile;
+  }
+}
+
+// K2d: the tile list, one entry per tile: its brick (binary search over tile offsets) and start.
+__global__ void __launch_bounds__(256) k_tiles(RenderWs w) {
+  const uint32_t n = w.hdr[1];
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    int lo = 0, hi = w.nb;  // largest b with tile_off[b] <= t
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (w.tile_off[mid] <= t) lo = mid;
+      else hi = mid;
+    }
+    w.tile_brick[t] = (uint32_t)lo;
+    w.tile_start[t] = w.brick_off[lo] + (t - w.tile_off[lo]) * kTile;
   }
 }
 
@@ -632,10 +690,14 @@ cicero_status run_render(const cicero_grid* grid, const MlpPtrs& mlp, const Rend
   }
   {
     ProfScope ps(kStBucket, st);
-    k_brick_scan<<<1, 1024, 0, st>>>(ws);
+    const int nblk = (plan.nb + kScanChunk - 1) / kScanChunk;
+    k_brick_sums<<<nblk, 1024, 0, st>>>(ws);
+    k_brick_blocks<<<1, 1024, 0, st>>>(ws, nblk);
+    k_brick_offsets<<<nblk, 1024, 0, st>>>(ws);
+    k_tiles<<<num_sms() * 4, 256, 0, st>>>(ws);
     k_scatter<<<mb, 256, 0, st>>>(src, ws);
   }
-  count_launches(4);
+  count_launches(7);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "march/bucket kernels");
   if (stop_after_bucketing) return CICERO_OK;

@@ -89,28 +89,43 @@ __global__ void __launch_bounds__(256) k_splat(WarpArgs a, const float* __restri
   }
 }
 
-__device__ __forceinline__ bool ray_has_sample(const VoidTest& vt, int p) {
+// Void depth test of pixel p by a whole warp: 32 slots per step, stop at the first slot that
+// is inside the box (and in an occupied cell).  Same FP32 slot placement and indexing as rendering.
+__device__ __forceinline__ bool warp_ray_has_sample(const VoidTest& vt, int p) {
+  const int lane = threadIdx.x & 31;
   float o[3], d[3];
   ray_gen(vt.src, p, o, d);
   const Slots sl = place_slots(vt.g, vt.s, o, d);
-  for (int k = 0; k < sl.n; k++) {
+  for (int k0 = 0; k0 < sl.n; k0 += 32) {
+    const int k = k0 + lane;
     const float t = slot_t(sl, k);
-    if (!slot_valid(sl, k, t)) break;
-    float pp[3], f[3];
-    int i0[3];
-    sample_pos(o, d, t, pp);
-    if (index_sample(vt.g, pp, i0, f)) return true;
+    const bool valid = slot_valid(sl, k, t);
+    bool in = false;
+    if (valid) {
+      float pp[3], f[3];
+      int i0[3];
+      sample_pos(o, d, t, pp);
+      in = index_sample(vt.g, pp, i0, f);
+    }
+    if (__any_sync(0xffffffffu, in)) return true;
+    if (!__all_sync(0xffffffffu, valid)) return false;
   }
   return false;
 }
 
+// One warp per 32 consecutive target pixels.
 __global__ void __launch_bounds__(256) k_resolve(WarpArgs a, VoidTest vt, const float* __restrict__ ref_rgb,
                                                  const float* __restrict__ ref_depth, const unsigned long long* z,
                                                  float* wrgb, float* wdepth, uint8_t* mask) {
   const int n = a.wt * a.ht;
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
-    const unsigned long long key = z[p];
-    if (key != ~0ull) {
+  const int lane = threadIdx.x & 31;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int p0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; p0 < n; p0 += nwarps * 32) {
+    const int p = p0 + lane;
+    const bool px = p < n;
+    const unsigned long long key = px ? z[p] : 0ull;
+    const bool hole = px && key == ~0ull;
+    if (px && !hole) {
       const int q = (int)(key & 0xffffffffull);
       wrgb[3 * p + 0] = ref_rgb[3 * q + 0];
       wrgb[3 * p + 1] = ref_rgb[3 * q + 1];
@@ -121,18 +136,31 @@ __global__ void __launch_bounds__(256) k_resolve(WarpArgs a, VoidTest vt, const 
                           : __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(s.X, s.X), __fmul_rn(s.Y, s.Y)), __fmul_rn(s.Z, s.Z)));
       }
       mask[p] = 0;
-    } else if (vt.enabled && !ray_has_sample(vt, p)) {
-      wrgb[3 * p + 0] = vt.s.bg[0];
-      wrgb[3 * p + 1] = vt.s.bg[1];
-      wrgb[3 * p + 2] = vt.s.bg[2];
-      if (wdepth) wdepth[p] = __int_as_float(0x7f800000);
-      mask[p] = 2;
-    } else {
-      wrgb[3 * p + 0] = 0.0f;
-      wrgb[3 * p + 1] = 0.0f;
-      wrgb[3 * p + 2] = 0.0f;
-      if (wdepth) wdepth[p] = 0.0f;
-      mask[p] = 1;
+    }
+    bool is_void = false;
+    if (vt.enabled) {
+      unsigned hm = __ballot_sync(0xffffffffu, hole);
+      while (hm) {
+        const int b = __ffs(hm) - 1;
+        hm &= hm - 1;
+        const bool v = !warp_ray_has_sample(vt, p0 + b);
+        if (lane == b) is_void = v;
+      }
+    }
+    if (hole) {
+      if (is_void) {
+        wrgb[3 * p + 0] = vt.s.bg[0];
+        wrgb[3 * p + 1] = vt.s.bg[1];
+        wrgb[3 * p + 2] = vt.s.bg[2];
+        if (wdepth) wdepth[p] = __int_as_float(0x7f800000);
+        mask[p] = 2;
+      } else {
+        wrgb[3 * p + 0] = 0.0f;
+        wrgb[3 * p + 1] = 0.0f;
+        wrgb[3 * p + 2] = 0.0f;
+        if (wdepth) wdepth[p] = 0.0f;
+        mask[p] = 1;
+      }
     }
   }
 }
