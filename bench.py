@@ -211,12 +211,15 @@ def main():
     sd = cc.sampling_from(cam.sampling)
     cd = cc.camera_from(cam)
     tds = [cc.camera_from(t) for t in targets]
-    o16, o32 = cc.options(cc.MLP_BF16, 8), cc.options(cc.MLP_FP32, 8)
     dev = torch.device("cuda", local)
-    ws_r = cc.workspace(cc.cicero_render_workspace_size(grid.desc, R, sd, o16), dev)
-    ws_w = cc.workspace(cc.cicero_warp_workspace_size(tds[0]), dev)
+    # brick size per precision, picked by the library's autotuner (timed renders of this frame)
+    ws_r = cc.workspace(cc.cicero_render_workspace_size(grid.desc, R, sd, cc.options(cc.MLP_BF16, 4)), dev)
     ref_rgb = torch.empty(R, 3, device=dev)
     ref_depth = torch.empty(R, device=dev)
+    b16, tune16 = cc.cicero_autotune_brick(grid.desc, mlp.desc, cd, sd, cc.MLP_BF16, ref_rgb, ref_depth, ws_r)
+    b32, tune32 = cc.cicero_autotune_brick(grid.desc, mlp.desc, cd, sd, cc.MLP_FP32, ref_rgb, ref_depth, ws_r)
+    o16, o32 = cc.options(cc.MLP_BF16, b16), cc.options(cc.MLP_FP32, b32)
+    ws_w = cc.workspace(cc.cicero_warp_workspace_size(tds[0]), dev)
     t_rgb = torch.empty(N_TARGETS, R, 3, device=dev)
     t_depth = torch.empty(N_TARGETS, R, device=dev)
     mask = torch.empty(N_TARGETS, R, dtype=torch.uint8, device=dev)
@@ -290,13 +293,6 @@ def main():
     hdr = ws_r[:16].view(torch.int32).cpu().numpy()
     active = int(hdr[2])
     t_bf16 = timed(lambda: full(o16), n_fp, 1)
-    sweep = {}
-    for bsz in (4, 8, 16):
-        ob = cc.options(cc.MLP_BF16, bsz)
-        wsb = cc.workspace(cc.cicero_render_workspace_size(grid.desc, R, sd, ob), dev)
-        tb = timed(lambda: cc.cicero_render(grid.desc, mlp.desc, cd, sd, ob, ref_rgb, ref_depth, None, None, wsb), 2, 1)
-        sweep[str(bsz)] = 2 * world / tb
-        del wsb
 
     # per-stage device time (CUDA events on the launching stream) over two profiled windows
     cc.cicero_profile_begin()
@@ -349,13 +345,14 @@ def main():
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "image": f"{W}x{H}", "grid": "256^3 x 12 fp16 + 32^3 occupancy (15%)",
                        "targets_per_reference": N_TARGETS, "samples": "<=256 per ray, step 0.5 voxel",
+                       "brick": "autotuned per precision (cicero_autotune_brick)",
                        "l2": "flushed (256 MB write) between timed steps", "parallelism": f"replicas x{world}"},
             "plain_fp32_fps": n_fp * world / t_fp32,
             "bf16_full_fps": n_fp * world / t_bf16,
             "msamples_per_s_bf16_full": active * n_fp * world / t_bf16 / 1e6,
             "msamples_per_s_fp32_full": active * n_fp * world / t_fp32 / 1e6,
             "active_samples_per_frame": active,
-            "bf16_full_fps_by_brick": sweep,
+            "autotune_ms_by_brick": {"bf16": tune16, "fp32": tune32}, "brick": {"bf16": b16, "fp32": b32},
             "fraction_rays_marched_targets": holes / (N_TARGETS * R),
             "roofline": roof, "stages": stages, "quality": quality, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "frames/s", "h2d_bytes_per_step": int(pose_h.numel() * 4),

@@ -145,6 +145,16 @@ cicero_status cicero_render_holes(const cicero_grid *grid, const cicero_mlp *mlp
 size_t cicero_render_workspace_size(const cicero_grid *grid, int n_rays, const cicero_sampling *sampling,
                                     const cicero_options *opt);
 
+/* Brick-size autotuner: renders `cam` once untimed and once timed with bricks of 4, 8 and 16
+ * voxels (each size that fits `ws_bytes` and the kernels' shared memory) and returns the fastest in
+ * *best_brick; ms[3] (may be NULL) receives the timed milliseconds (-1 = not tried).  rgb and depth
+ * (device, [H*W][3] and [H*W]) are scratch.  Size the workspace with brick 4, the largest.
+ * Synchronises `stream` (it times with CUDA events), unlike every other call. */
+cicero_status cicero_autotune_brick(const cicero_grid *grid, const cicero_mlp *mlp, const cicero_camera *cam,
+                                    const cicero_sampling *sampling, cicero_precision precision,
+                                    float *rgb, float *depth, void *workspace, size_t ws_bytes, void *stream,
+                                    int *best_brick, float *ms);
+
 /* ---------------------------------------------------------------------------------------------
  * SpaRW target frame, steps 1-3 (Eq. 1 point cloud, Eq. 2 transform, Eq. 3 re-projection) plus
  * the depth test, the void depth test and hole listing of step 4 (Sec. III-B).
@@ -161,7 +171,8 @@ size_t cicero_render_workspace_size(const cicero_grid *grid, int n_rays, const c
  *   point is kept only when the angle between its reference and target rays is below it.
  * Outputs: warped_rgb [Ht*Wt][3]; warped_depth [Ht*Wt] or NULL (distance |P'| of the winning
  * point, +inf for void, 0 for holes); hole_mask [Ht*Wt] (0 warped, 1 hole to render, 2 void);
- * hole_idx [Ht*Wt] (holes with mask 1 in ascending pixel order) and *n_holes (device scalar).
+ * hole_idx [Ht*Wt] (holes with mask 1 in ascending pixel order; also used as scratch during the call)
+ * and *n_holes (device scalar).
  * void_grid (may be NULL) enables the void depth test: a hole whose target ray has no sample
  * inside the grid box (and in an occupied cell) gets void_sampling->bg, depth +inf, mask 2.
  * Decisions are taken in FP32 with round-to-nearest and no contraction, so the mask and the

@@ -66,6 +66,7 @@ _SIGS = {
     "cicero_mlp_eval": ([_P, _P, C.c_int, C.c_int, _P, _P, _Z, _P], C.c_int),
     "cicero_mlp_eval_workspace_size": ([C.c_int], _Z),
     "cicero_workspace_status": ([_P, _P], C.c_int),
+    "cicero_autotune_brick": ([_P] * 4 + [C.c_int] + [_P] * 3 + [_Z] + [_P] * 3, C.c_int),
     "cicero_profile_begin": ([], C.c_int),
     "cicero_profile_end": ([_P, _P, C.c_int], C.c_int),
     "cicero_launch_count": ([], C.c_longlong),
@@ -260,6 +261,17 @@ def cicero_build_rit(grid: Grid, cam: Camera, samp: Sampling, opt: Options | Non
     _check(lib().cicero_build_rit(C.byref(grid), C.byref(cam), C.byref(samp), _ref(opt), _ptr(brick_offsets),
                                   _ptr(samples), C.byref(nb), p, n, _stream(stream)))
     return int(nb.value)
+
+
+def cicero_autotune_brick(grid: Grid, mlp: Mlp, cam: Camera, samp: Sampling, precision: int, rgb, depth, ws,
+                          stream=None):
+    """Returns (best brick, {brick: ms})."""
+    p, n = _ws(ws)
+    best = C.c_int(0)
+    ms = (C.c_float * 3)()
+    _check(lib().cicero_autotune_brick(C.byref(grid), C.byref(mlp), C.byref(cam), C.byref(samp), int(precision),
+                                       _ptr(rgb), _ptr(depth), p, n, _stream(stream), C.byref(best), ms))
+    return int(best.value), {b: float(ms[i]) for i, b in enumerate((4, 8, 16))}
 
 
 def cicero_mlp_eval(mlp: Mlp, x, precision: int, c, ws, stream=None):

@@ -371,6 +371,47 @@ cicero_status cicero_build_rit(const cicero_grid* grid, const cicero_camera* cam
   return run_rit_export(w, plan.nb, plan.S, brick_offsets, samples, (cudaStream_t)stream);
 }
 
+cicero_status cicero_autotune_brick(const cicero_grid* grid, const cicero_mlp* mlp, const cicero_camera* cam,
+                                    const cicero_sampling* sampling, cicero_precision precision, float* rgb,
+                                    float* depth, void* workspace, size_t ws_bytes, void* stream, int* best_brick,
+                                    float* ms) {
+  if (!best_brick) return fail(CICERO_ERR_INVALID_ARG, "best_brick is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int cand[3] = {4, 8, 16};
+  float best = 1e30f;
+  *best_brick = 0;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+  for (int i = 0; i < 3; i++) {
+    if (ms) ms[i] = -1.0f;
+    cicero_options opt = {precision, cand[i]};
+    const size_t need = cicero_render_workspace_size(grid, cam ? cam->width * cam->height : 0, sampling, &opt);
+    if (need == 0 || need > ws_bytes) continue;
+    // one untimed render (first use of the kernel), then one timed render
+    if (cicero_render(grid, mlp, cam, sampling, &opt, rgb, depth, nullptr, nullptr, workspace, ws_bytes, stream) !=
+        CICERO_OK)
+      continue;  // this brick size is not supported for this grid
+    cudaEventRecord(e0, st);
+    cicero_render(grid, mlp, cam, sampling, &opt, rgb, depth, nullptr, nullptr, workspace, ws_bytes, stream);
+    cudaEventRecord(e1, st);
+    if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+    float t = 0.0f;
+    cudaEventElapsedTime(&t, e0, e1);
+    if (ms) ms[i] = t;
+    if (t < best) {
+      best = t;
+      *best_brick = cand[i];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return cuda_fail(e, "autotune render");
+  if (!*best_brick) return fail(CICERO_ERR_UNSUPPORTED, "no brick size could render this grid");
+  return cicero_workspace_status(workspace, stream);
+}
+
 cicero_status cicero_warp(const float* ref_rgb, const float* ref_depth, const cicero_camera* ref_cam,
                           const cicero_camera* tgt_cam, float max_angle_deg, const cicero_grid* void_grid,
                           const cicero_sampling* void_sampling, float* warped_rgb, float* warped_depth,

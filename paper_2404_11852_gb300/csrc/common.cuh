@@ -21,7 +21,7 @@ constexpr int kMaxIn = 48;          // MLP input padded to 48 (3 x K16 MMA steps
 // error bits recorded in the workspace header
 constexpr uint32_t kErrInternal = 1u;
 constexpr uint32_t kErrTimeout = 2u;
-constexpr long long kSpinLimit = 1ll << 26;   // bounded mbarrier waits (~0.1-1 s)
+constexpr long long kWaitCycles = 4ll << 30;  // bounded mbarrier waits: ~2 s of SM clock
 
 // -------------------------------------------------------------------------------------------
 // descriptors passed by value to kernels
@@ -257,22 +257,25 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
 
+// Waits for the phase with the given parity, letting the warp sleep for up to 10 us per try.
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
       "selp.u32 %0, 1, 0, p;\n\t}"
       : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(10000u)
       : "memory");
   return ok != 0;
 }
 
 // Bounded wait on an mbarrier phase: returns false (after recording a timeout) if the phase
-// did not complete within kSpinLimit polls.
+// did not complete within kWaitCycles SM clock cycles.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t* err) {
-  for (long long i = 0; i < kSpinLimit; i++)
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (clock64() - t0 < kWaitCycles)
     if (mbar_try_wait(bar, parity)) return true;
   set_err(err, kErrTimeout);
   return false;

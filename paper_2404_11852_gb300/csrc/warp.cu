@@ -137,28 +137,34 @@ __global__ void __launch_bounds__(256) k_resolve(WarpArgs a, VoidTest vt, const 
       }
       mask[p] = 0;
     }
-    bool is_void = false;
-    if (vt.enabled) {
-      unsigned hm = __ballot_sync(0xffffffffu, hole);
-      while (hm) {
-        const int b = __ffs(hm) - 1;
-        hm &= hm - 1;
-        const bool v = !warp_ray_has_sample(vt, p0 + b);
-        if (lane == b) is_void = v;
-      }
-    }
     if (hole) {
-      if (is_void) {
+      wrgb[3 * p + 0] = 0.0f;
+      wrgb[3 * p + 1] = 0.0f;
+      wrgb[3 * p + 2] = 0.0f;
+      if (wdepth) wdepth[p] = 0.0f;
+      mask[p] = vt.enabled ? 3 : 1;  // 3: hole still to be tested for void
+    }
+  }
+}
+
+// Void depth test of the listed candidates, one warp each (candidates cluster in the image, so
+// testing them where they lie would serialise a warp's worth of marches).
+__global__ void __launch_bounds__(256) k_void(VoidTest vt, const int32_t* cand, const int32_t* n_cand, float* wrgb,
+                                              float* wdepth, uint8_t* mask) {
+  const int lane = threadIdx.x & 31;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  const int n = *n_cand;
+  for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nwarps) {
+    const int p = cand[i];
+    const bool v = !warp_ray_has_sample(vt, p);
+    if (lane == 0) {
+      if (v) {
         wrgb[3 * p + 0] = vt.s.bg[0];
         wrgb[3 * p + 1] = vt.s.bg[1];
         wrgb[3 * p + 2] = vt.s.bg[2];
         if (wdepth) wdepth[p] = __int_as_float(0x7f800000);
         mask[p] = 2;
       } else {
-        wrgb[3 * p + 0] = 0.0f;
-        wrgb[3 * p + 1] = 0.0f;
-        wrgb[3 * p + 2] = 0.0f;
-        if (wdepth) wdepth[p] = 0.0f;
         mask[p] = 1;
       }
     }
@@ -194,12 +200,12 @@ __device__ __forceinline__ uint32_t block_exscan(uint32_t v, uint32_t* tot, uint
   return r;
 }
 
-__global__ void __launch_bounds__(1024) k_hole_count(const uint8_t* mask, int n, uint32_t* block_sums) {
+__global__ void __launch_bounds__(1024) k_hole_count(const uint8_t* mask, int n, uint8_t val, uint32_t* block_sums) {
   __shared__ uint32_t sh[32];
   const int base = blockIdx.x * kHoleChunk + threadIdx.x * 4;
   uint32_t c = 0;
 #pragma unroll
-  for (int k = 0; k < 4; k++) c += (base + k < n && mask[base + k] == 1) ? 1u : 0u;
+  for (int k = 0; k < 4; k++) c += (base + k < n && mask[base + k] == val) ? 1u : 0u;
   uint32_t tot;
   block_exscan(c, &tot, sh);
   if (threadIdx.x == 0) block_sums[blockIdx.x] = tot;
@@ -219,7 +225,7 @@ __global__ void __launch_bounds__(1024) k_hole_blocks(uint32_t* block_sums, int 
   if (threadIdx.x == 0) *n_holes = (int32_t)run;
 }
 
-__global__ void __launch_bounds__(1024) k_hole_write(const uint8_t* mask, int n, const uint32_t* block_off,
+__global__ void __launch_bounds__(1024) k_hole_write(const uint8_t* mask, int n, uint8_t val, const uint32_t* block_off,
                                                      int32_t* hole_idx) {
   __shared__ uint32_t sh[32];
   const int base = blockIdx.x * kHoleChunk + threadIdx.x * 4;
@@ -227,7 +233,7 @@ __global__ void __launch_bounds__(1024) k_hole_write(const uint8_t* mask, int n,
   bool h[4];
 #pragma unroll
   for (int k = 0; k < 4; k++) {
-    h[k] = base + k < n && mask[base + k] == 1;
+    h[k] = base + k < n && mask[base + k] == val;
     c += h[k] ? 1u : 0u;
   }
   uint32_t tot;
@@ -260,9 +266,16 @@ cicero_status run_warp(const WarpArgs& a, const VoidTest& vt, const float* ref_r
   {
     ProfScope ps(kStWarpResolve, st);
     k_resolve<<<std::min(g, (nt + 255) / 256), 256, 0, st>>>(a, vt, ref_rgb, ref_depth, z, wrgb, wdepth, mask);
-    k_hole_count<<<nblk, 1024, 0, st>>>(mask, nt, bsum);
+    if (vt.enabled) {  // list the candidates, test them, then list the holes that remain
+      k_hole_count<<<nblk, 1024, 0, st>>>(mask, nt, 3, bsum);
+      k_hole_blocks<<<1, 1024, 0, st>>>(bsum, nblk, n_holes);
+      k_hole_write<<<nblk, 1024, 0, st>>>(mask, nt, 3, bsum, hole_idx);
+      k_void<<<g, 256, 0, st>>>(vt, hole_idx, n_holes, wrgb, wdepth, mask);
+      count_launches(4);
+    }
+    k_hole_count<<<nblk, 1024, 0, st>>>(mask, nt, 1, bsum);
     k_hole_blocks<<<1, 1024, 0, st>>>(bsum, nblk, n_holes);
-    k_hole_write<<<nblk, 1024, 0, st>>>(mask, nt, bsum, hole_idx);
+    k_hole_write<<<nblk, 1024, 0, st>>>(mask, nt, 1, bsum, hole_idx);
   }
   count_launches(6);
   cudaError_t e = cudaGetLastError();
