@@ -187,6 +187,26 @@ cicero_status cicero_warp(const float *ref_rgb, const float *ref_depth,
 
 size_t cicero_warp_workspace_size(const cicero_camera *tgt_cam);
 
+/* cicero_warp without a workspace, for callers that cannot allocate device memory (for example
+ * code that runs while a stream is captured into a CUDA graph, where cudaMalloc is not allowed,
+ * or real-time loops that must not enter an allocator).  The paper has no counterpart: this is a
+ * packaging variant of the warp above, with the same arguments and outputs minus the workspace.
+ *   - Scratch (the depth buffer and scan sums, ~8 MiB) is a static array in the library's device
+ *     image, present on every device that loads the library until the process exits.  The target
+ *     image may have at most 1048576 pixels (width * height); larger targets return
+ *     CICERO_ERR_UNSUPPORTED.  The call allocates and frees nothing.
+ *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
+ *     that device current; make that first call before any stream capture.
+ *   - Every call shares the one array: calls that may overlap on the GPU (different streams, or
+ *     different host threads on one device) race and must be serialised by the caller.  The call
+ *     clears what must start empty (the depth buffer) itself. */
+cicero_status cicero_warp_noalloc(const float *ref_rgb, const float *ref_depth,
+                                  const cicero_camera *ref_cam, const cicero_camera *tgt_cam,
+                                  float max_angle_deg, const cicero_grid *void_grid,
+                                  const cicero_sampling *void_sampling,
+                                  float *warped_rgb, float *warped_depth, uint8_t *hole_mask,
+                                  int32_t *hole_idx, int32_t *n_holes, void *stream);
+
 /* ---------------------------------------------------------------------------------------------
  * Backward of cicero_render_rays with the FP32 MLP (not in the paper, whose models are trained
  * offline; the gradient of its rendering function).  Given d_rgb = dL/drgb [n_rays][3], the

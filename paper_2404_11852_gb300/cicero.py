@@ -60,6 +60,7 @@ _SIGS = {
     "cicero_render_workspace_size": ([_P, C.c_int, _P, _P], _Z),
     "cicero_warp": ([_P] * 4 + [C.c_float] + [_P] * 8 + [_Z, _P], C.c_int),
     "cicero_warp_workspace_size": ([_P], _Z),
+    "cicero_warp_noalloc": ([_P] * 4 + [C.c_float] + [_P] * 8, C.c_int),
     "cicero_render_backward": ([_P] * 4 + [C.c_int] + [_P] * 6 + [_Z, _P], C.c_int),
     "cicero_backward_workspace_size": ([_P, C.c_int, _P], _Z),
     "cicero_build_rit": ([_P] * 8 + [_Z, _P], C.c_int),
@@ -236,6 +237,15 @@ def cicero_warp(ref_rgb, ref_depth, ref_cam: Camera, tgt_cam: Camera, max_angle_
     _check(lib().cicero_warp(_ptr(ref_rgb), _ptr(ref_depth), C.byref(ref_cam), C.byref(tgt_cam), float(max_angle_deg),
                              _ref(void_grid), _ref(void_samp), _ptr(warped_rgb), _ptr(warped_depth), _ptr(hole_mask),
                              _ptr(hole_idx), _ptr(n_holes), p, n, _stream(stream)))
+
+
+def cicero_warp_noalloc(ref_rgb, ref_depth, ref_cam: Camera, tgt_cam: Camera, max_angle_deg: float,
+                        void_grid: Grid | None, void_samp: Sampling | None, warped_rgb, warped_depth, hole_mask,
+                        hole_idx, n_holes, stream=None):
+    _check(lib().cicero_warp_noalloc(_ptr(ref_rgb), _ptr(ref_depth), C.byref(ref_cam), C.byref(tgt_cam),
+                                     float(max_angle_deg), _ref(void_grid), _ref(void_samp), _ptr(warped_rgb),
+                                     _ptr(warped_depth), _ptr(hole_mask), _ptr(hole_idx), _ptr(n_holes),
+                                     _stream(stream)))
 
 
 def cicero_warp_workspace_size(tgt_cam: Camera) -> int:

@@ -282,4 +282,62 @@ cicero_status run_warp(const WarpArgs& a, const VoidTest& vt, const float* ref_r
   return e == cudaSuccess ? CICERO_OK : cuda_fail(e, "warp kernels");
 }
 
+// -------------------------------------------------------------------------------------------
+// Allocation-free warp.  Some callers cannot allocate device memory: code running while a stream
+// is being captured into a CUDA graph (cudaMalloc is not allowed there), real-time loops that must
+// not enter the allocator, or host programs linking this library without a device allocator of
+// their own.  For them cicero_warp_noalloc uses a scratch array that is part of the library's
+// device image instead of a caller-provided workspace.
+
+namespace {
+
+constexpr int kNoAllocMaxPixels = 1024 * 1024;  // largest target image (width * height)
+constexpr size_t kNoAllocBytes = 256 + ((8 * (size_t)kNoAllocMaxPixels + 255) & ~size_t(255)) +
+                                 ((4 * (size_t)((kNoAllocMaxPixels + kHoleChunk - 1) / kHoleChunk) + 255) & ~size_t(255));
+
+// Depth buffer and scan sums of the allocation-free warp (~8 MiB on every device that loads the
+// library, held until the process exits).  In host code this name is only a stand-in: the device
+// address comes from cudaGetSymbolAddress below.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kMaxDevices = 64;
+void* g_noalloc_ptr[kMaxDevices] = {nullptr};
+
+// Device address of the scratch array on the current device (looked up once per device).
+cicero_status noalloc_scratch(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev < 0 || dev >= kMaxDevices) return fail(CICERO_ERR_UNSUPPORTED, "device index out of range");
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(scratch)");
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return CICERO_OK;
+}
+
+}  // namespace
+
 }  // namespace cicero
+
+extern "C" cicero_status cicero_warp_noalloc(const float* ref_rgb, const float* ref_depth,
+                                             const cicero_camera* ref_cam, const cicero_camera* tgt_cam,
+                                             float max_angle_deg, const cicero_grid* void_grid,
+                                             const cicero_sampling* void_sampling, float* warped_rgb,
+                                             float* warped_depth, uint8_t* hole_mask, int32_t* hole_idx,
+                                             int32_t* n_holes, void* stream) {
+  using namespace cicero;
+  if (!tgt_cam) return fail(CICERO_ERR_INVALID_ARG, "tgt_cam is NULL");
+  if ((long long)tgt_cam->width * tgt_cam->height > kNoAllocMaxPixels)
+    return fail(CICERO_ERR_UNSUPPORTED, "cicero_warp_noalloc: the target image exceeds 1048576 pixels "
+                                        "(the size of its built-in scratch); use cicero_warp with a workspace");
+  void* scratch = nullptr;
+  cicero_status st = noalloc_scratch(&scratch);
+  if (st != CICERO_OK) return st;
+  return cicero_warp(ref_rgb, ref_depth, ref_cam, tgt_cam, max_angle_deg, void_grid, void_sampling, warped_rgb,
+                     warped_depth, hole_mask, hole_idx, n_holes, scratch, kNoAllocBytes, stream);
+}
+
