@@ -32,6 +32,7 @@ METRIC = "800x800 FPS & Msamples/s, BF16+SpaRW vs plain FP32, at PSNR>=45dB vs o
 N_TARGETS = 16
 W = H = 800
 FLOP_PER_SAMPLE = 2 * (39 * 128 + 128 * 128 + 128 * 3)  # 43,520 MLP FLOP per composited sample
+HOLE_RECORDS = 320_000_000  # record capacity of the batched hole render (19 GB)
 
 
 def parse():
@@ -227,12 +228,20 @@ def main():
     nh = torch.zeros(N_TARGETS, 1, dtype=torch.int32, device=dev)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
 
+    # all targets' holes are rendered in one batched pass; records are capped well above need
+    ob = cc.options(cc.MLP_BF16, b16, max_records=HOLE_RECORDS)
+    ws_h = cc.workspace(cc.cicero_render_workspace_size(grid.desc, N_TARGETS * R, sd, ob), dev)
+    hidx_l = [hidx[i] for i in range(N_TARGETS)]
+    trgb_l = [t_rgb[i] for i in range(N_TARGETS)]
+    tdep_l = [t_depth[i] for i in range(N_TARGETS)]
+
     def step():
         cc.cicero_render(grid.desc, mlp.desc, cd, sd, o16, ref_rgb, ref_depth, None, None, ws_r)
         for i, td in enumerate(tds):
             cc.cicero_warp(ref_rgb, ref_depth, cd, td, 180.0, grid.desc, sd, t_rgb[i], t_depth[i], mask[i], hidx[i],
                            nh[i], ws_w)
-            cc.cicero_render_holes(grid.desc, mlp.desc, td, sd, o16, hidx[i], nh[i], R, t_rgb[i], t_depth[i], ws_r)
+        cc.cicero_render_holes_batch(grid.desc, mlp.desc, tds, sd, ob, hidx_l, nh, N_TARGETS * R, trgb_l, tdep_l,
+                                     ws_h)
 
     def full(opt):
         cc.cicero_render(grid.desc, mlp.desc, cd, sd, opt, ref_rgb, ref_depth, None, None, ws_r)
@@ -267,6 +276,8 @@ def main():
         t_main = timed(step, args.steps, args.warmup)
     launches = (cc.cicero_launch_count() - launches0) / (args.steps + args.warmup)
     cc.cicero_workspace_status(ws_r)
+    cc.cicero_workspace_status(ws_h)
+    hole_hdr = ws_h[:16].view(torch.int32).cpu().numpy()
     value = N_TARGETS * args.steps * world / t_main
     holes = nh.sum().item()
 
@@ -354,6 +365,8 @@ def main():
             "active_samples_per_frame": active,
             "autotune_ms_by_brick": {"bf16": tune16, "fp32": tune32}, "brick": {"bf16": b16, "fp32": b32},
             "fraction_rays_marched_targets": holes / (N_TARGETS * R),
+            "hole_batch": {"rays": holes / 1, "composited_samples": int(hole_hdr[2]),
+                           "records_reserved": int(np.uint32(hole_hdr[3])), "record_capacity": HOLE_RECORDS},
             "roofline": roof, "stages": stages, "quality": quality, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "frames/s", "h2d_bytes_per_step": int(pose_h.numel() * 4),
                     "d2h_bytes_per_step": int(host_out.numel() * 4)},

@@ -101,10 +101,15 @@ typedef struct {
     float c2w[12];
 } cicero_camera;
 
-/* Options of the rendering calls (NULL = defaults: FP32 MLP, bricks of 8^3 voxels). */
+/* Options of the rendering calls (NULL = defaults: FP32 MLP, bricks of 8^3 voxels, full capacity).
+ * max_records caps the per-sample records the workspace holds (0 = n_rays * n_samples, which can
+ * never overflow).  Each ray reserves an upper bound of its samples (its slots within two slots of
+ * the grid box); if the reservations exceed max_records the rays that do not fit composite nothing
+ * and cicero_workspace_status returns CICERO_ERR_WORKSPACE_TOO_SMALL. */
 typedef struct {
     cicero_precision precision;
     int brick;          /* voxels per brick edge ("MVoxel", Sec. IV-A): 4, 8 or 16; 0 = 8 */
+    long long max_records;
 } cicero_options;
 
 /* ---------------------------------------------------------------------------------------------
@@ -139,6 +144,20 @@ cicero_status cicero_render_holes(const cicero_grid *grid, const cicero_mlp *mlp
                                   const int32_t *hole_idx, const int32_t *n_holes, int max_holes,
                                   float *rgb_inout, float *depth_inout,
                                   void *workspace, size_t ws_bytes, void *stream);
+
+/* Gamma_sp of Eq. 4 for several target frames in one pass: view v renders the pixels
+ * hole_idx[v][0 .. n_holes[v]) of cams[v] into rgb_inout[v] / depth_inout[v].
+ *   cams [n_views] (host), hole_idx / rgb_inout / depth_inout: host arrays of n_views device
+ *   pointers (depth_inout, or any entry of it, may be NULL), n_holes: DEVICE array [n_views]
+ *   (for example the n_holes scalars of n_views cicero_warp calls laid out contiguously),
+ *   max_rays >= sum of n_holes bounds the rays and sizes the workspace (query it with
+ *   n_rays = max_rays).  1 <= n_views <= 32.  The rays of all views share one march, one Ray
+ *   Index Table and one tensor-core pass, so each brick is staged once for every view. */
+cicero_status cicero_render_holes_batch(const cicero_grid *grid, const cicero_mlp *mlp, const cicero_camera *cams,
+                                        int n_views, const cicero_sampling *sampling, const cicero_options *opt,
+                                        const int32_t *const *hole_idx, const int32_t *n_holes, int max_rays,
+                                        float *const *rgb_inout, float *const *depth_inout,
+                                        void *workspace, size_t ws_bytes, void *stream);
 
 /* Workspace bytes for cicero_render / cicero_render_rays / cicero_render_holes with n_rays rays
  * (H*W, n_rays or max_holes).  Host query, allocates nothing. */

@@ -48,7 +48,7 @@ class Camera(C.Structure):
 
 
 class Options(C.Structure):
-    _fields_ = [("precision", C.c_int), ("brick", C.c_int)]
+    _fields_ = [("precision", C.c_int), ("brick", C.c_int), ("max_records", C.c_longlong)]
 
 
 _P = C.c_void_p
@@ -58,6 +58,7 @@ _SIGS = {
     "cicero_render_rays": ([_P] * 4 + [C.c_int] + [_P] * 7 + [_Z, _P], C.c_int),
     "cicero_render_holes": ([_P] * 7 + [C.c_int] + [_P] * 3 + [_Z, _P], C.c_int),
     "cicero_render_workspace_size": ([_P, C.c_int, _P, _P], _Z),
+    "cicero_render_holes_batch": ([_P, _P, _P, C.c_int, _P, _P, _P, _P, C.c_int, _P, _P, _P, _Z, _P], C.c_int),
     "cicero_warp": ([_P] * 4 + [C.c_float] + [_P] * 8 + [_Z, _P], C.c_int),
     "cicero_warp_workspace_size": ([_P], _Z),
     "cicero_warp_noalloc": ([_P] * 4 + [C.c_float] + [_P] * 8, C.c_int),
@@ -190,9 +191,9 @@ def camera_from(cam) -> Camera:
     return camera(cam.width, cam.height, cam.f, cam.cx, cam.cy, cam.c2w)
 
 
-def options(precision: int = MLP_FP32, brick: int = 8) -> Options:
+def options(precision: int = MLP_FP32, brick: int = 8, max_records: int = 0) -> Options:
     o = Options()
-    o.precision, o.brick = precision, brick
+    o.precision, o.brick, o.max_records = precision, brick, max_records
     return o
 
 
@@ -225,6 +226,22 @@ def cicero_render_holes(grid: Grid, mlp: Mlp, cam: Camera, samp: Sampling, opt: 
     _check(lib().cicero_render_holes(C.byref(grid), C.byref(mlp), C.byref(cam), C.byref(samp), _ref(opt),
                                      _ptr(hole_idx), _ptr(n_holes), int(max_holes), _ptr(rgb_inout),
                                      _ptr(depth_inout), p, n, _stream(stream)))
+
+
+def cicero_render_holes_batch(grid: Grid, mlp: Mlp, cams, samp: Sampling, opt: Options | None, hole_idx, n_holes,
+                              max_rays: int, rgb_inout, depth_inout, ws, stream=None):
+    """cams: list of Camera; hole_idx / rgb_inout / depth_inout: lists of CUDA tensors (depth may be
+    None); n_holes: one int32 CUDA tensor holding the per-view counts contiguously."""
+    V = len(cams)
+    cam_arr = (Camera * V)(*cams)
+    P = C.c_void_p * V
+    h = P(*[t.data_ptr() for t in hole_idx])
+    rgb = P(*[t.data_ptr() for t in rgb_inout])
+    dep = P(*[(t.data_ptr() if t is not None else None) for t in depth_inout]) if depth_inout is not None else None
+    assert n_holes.is_cuda and n_holes.is_contiguous() and n_holes.numel() == V
+    p, n = _ws(ws)
+    _check(lib().cicero_render_holes_batch(C.byref(grid), C.byref(mlp), cam_arr, V, C.byref(samp), _ref(opt), h,
+                                           _ptr(n_holes), int(max_rays), rgb, dep, p, n, _stream(stream)))
 
 
 def cicero_render_workspace_size(grid: Grid, n_rays: int, samp: Sampling, opt: Options | None = None) -> int:

@@ -221,10 +221,13 @@ static cicero_status plan_render(const cicero_grid* grid, const cicero_mlp* mlp,
   if (n_rays < 0) return fail(CICERO_ERR_INVALID_ARG, "negative ray count");
   const unsigned long long RS = (unsigned long long)n_rays * (unsigned long long)s->n_samples;
   if (RS >= 0xffffffffull) return fail(CICERO_ERR_UNSUPPORTED, "rays x samples must be below 2^32");
+  unsigned long long Q = RS;
+  if (opt && opt->max_records > 0 && (unsigned long long)opt->max_records < Q) Q = (unsigned long long)opt->max_records;
   p->R = n_rays;
   p->S = s->n_samples;
+  p->Q = (uint32_t)Q;
   p->nb = p->geo.nb[0] * p->geo.nb[1] * p->geo.nb[2];
-  p->max_tiles = (int)((RS + kTile - 1) / kTile) + p->nb;
+  p->max_tiles = (int)((Q + kTile - 1) / kTile) + p->nb;
   p->want_k = false;
   p->want_bwd = false;
   p->precision = opt ? opt->precision : CICERO_MLP_FP32;
@@ -233,17 +236,34 @@ static cicero_status plan_render(const cicero_grid* grid, const cicero_mlp* mlp,
   return CICERO_OK;
 }
 
+static ViewCam view_of(const cicero_camera* cam) {
+  ViewCam v;
+  for (int i = 0; i < 12; i++) v.c2w[i] = cam->c2w[i];
+  v.f = cam->f;
+  v.cx = cam->cx;
+  v.cy = cam->cy;
+  v.width = cam->width;
+  return v;
+}
+
 static RaySrc camera_src(const cicero_camera* cam) {
   RaySrc s;
   memset(&s, 0, sizeof s);
   s.kind = 0;
-  s.width = cam->width;
-  s.f = cam->f;
-  s.cx = cam->cx;
-  s.cy = cam->cy;
-  for (int i = 0; i < 12; i++) s.c2w[i] = cam->c2w[i];
+  s.n_views = 1;
+  s.cam[0] = view_of(cam);
   s.n_max = cam->width * cam->height;
   return s;
+}
+
+static OutBufs single_out(float* rgb, float* depth, float* acc, int32_t* n_steps) {
+  OutBufs o;
+  memset(&o, 0, sizeof o);
+  o.rgb[0] = rgb;
+  o.depth[0] = depth;
+  o.acc = acc;
+  o.n_steps = n_steps;
+  return o;
 }
 
 static cicero_status check_cam(const cicero_camera* c) {
@@ -267,7 +287,8 @@ static cicero_status render_common(const cicero_grid* grid, const cicero_mlp* ml
   RenderWs w;
   if (!carve_render_ws(ws, ws_bytes, plan, &w)) return fail(CICERO_ERR_WORKSPACE_TOO_SMALL, "workspace too small");
   if (n_rays == 0) return CICERO_OK;
-  return run_render(grid, mlp_ptrs(mlp), plan, src, w, rgb, depth, acc, n_steps, false, (cudaStream_t)stream);
+  return run_render(grid, mlp_ptrs(mlp), plan, src, w, single_out(rgb, depth, acc, n_steps), false,
+                    (cudaStream_t)stream);
 }
 
 // relative pose [R | t] = inverse(c2w_tgt) c2w_ref in FP64, rounded once to FP32
@@ -318,6 +339,7 @@ cicero_status cicero_render_rays(const cicero_grid* grid, const cicero_mlp* mlp,
   RaySrc src;
   memset(&src, 0, sizeof src);
   src.kind = 1;
+  src.n_views = 1;
   src.o = ray_o;
   src.d = ray_d;
   src.n_max = n_rays;
@@ -333,11 +355,48 @@ cicero_status cicero_render_holes(const cicero_grid* grid, const cicero_mlp* mlp
   if (!hole_idx || !n_holes) return fail(CICERO_ERR_INVALID_ARG, "hole_idx/n_holes is NULL");
   if (max_holes < 0 || max_holes > cam->width * cam->height) return fail(CICERO_ERR_INVALID_ARG, "max_holes");
   RaySrc src = camera_src(cam);
-  src.pix = hole_idx;
+  src.pix[0] = hole_idx;
   src.n_dev = n_holes;
   src.n_max = max_holes;
   return render_common(grid, mlp, sampling, opt, src, max_holes, rgb_inout, depth_inout, nullptr, nullptr, workspace,
                        ws_bytes, stream);
+}
+
+cicero_status cicero_render_holes_batch(const cicero_grid* grid, const cicero_mlp* mlp, const cicero_camera* cams,
+                                        int n_views, const cicero_sampling* sampling, const cicero_options* opt,
+                                        const int32_t* const* hole_idx, const int32_t* n_holes, int max_rays,
+                                        float* const* rgb_inout, float* const* depth_inout, void* workspace,
+                                        size_t ws_bytes, void* stream) {
+  if (n_views < 1 || n_views > kMaxViews) return fail(CICERO_ERR_INVALID_ARG, "n_views must be 1..32");
+  if (!cams || !hole_idx || !n_holes || !rgb_inout) return fail(CICERO_ERR_INVALID_ARG, "a batch argument is NULL");
+  RaySrc src;
+  memset(&src, 0, sizeof src);
+  src.kind = 2;
+  src.n_views = n_views;
+  src.n_dev = n_holes;
+  src.n_max = max_rays;
+  OutBufs out;
+  memset(&out, 0, sizeof out);
+  long long total = 0;
+  for (int v = 0; v < n_views; v++) {
+    cicero_status st = check_cam(&cams[v]);
+    if (st != CICERO_OK) return st;
+    if (!hole_idx[v] || !rgb_inout[v]) return fail(CICERO_ERR_INVALID_ARG, "hole_idx/rgb_inout entry is NULL");
+    src.cam[v] = view_of(&cams[v]);
+    src.pix[v] = hole_idx[v];
+    out.rgb[v] = rgb_inout[v];
+    out.depth[v] = depth_inout ? depth_inout[v] : nullptr;
+    total += (long long)cams[v].width * cams[v].height;
+  }
+  if (max_rays < 0 || max_rays > total) return fail(CICERO_ERR_INVALID_ARG, "max_rays must be 0..sum of pixels");
+  RenderPlan plan;
+  cicero_status st = plan_render(grid, mlp, max_rays, sampling, opt, &plan, true);
+  if (st != CICERO_OK) return st;
+  if (!ws_ok(workspace)) return fail(CICERO_ERR_INVALID_ARG, "workspace must be non-NULL and 256-byte aligned");
+  RenderWs w;
+  if (!carve_render_ws(workspace, ws_bytes, plan, &w)) return fail(CICERO_ERR_WORKSPACE_TOO_SMALL, "workspace too small");
+  if (max_rays == 0) return CICERO_OK;
+  return run_render(grid, mlp_ptrs(mlp), plan, src, w, out, false, (cudaStream_t)stream);
 }
 
 size_t cicero_render_workspace_size(const cicero_grid* grid, int n_rays, const cicero_sampling* sampling,
@@ -366,7 +425,7 @@ cicero_status cicero_build_rit(const cicero_grid* grid, const cicero_camera* cam
   const RaySrc src = camera_src(cam);
   MlpPtrs none;
   memset(&none, 0, sizeof none);
-  st = run_render(grid, none, plan, src, w, nullptr, nullptr, nullptr, nullptr, true, (cudaStream_t)stream);
+  st = run_render(grid, none, plan, src, w, single_out(nullptr, nullptr, nullptr, nullptr), true, (cudaStream_t)stream);
   if (st != CICERO_OK) return st;
   return run_rit_export(w, plan.nb, plan.S, brick_offsets, samples, (cudaStream_t)stream);
 }
@@ -386,7 +445,7 @@ cicero_status cicero_autotune_brick(const cicero_grid* grid, const cicero_mlp* m
   if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
   for (int i = 0; i < 3; i++) {
     if (ms) ms[i] = -1.0f;
-    cicero_options opt = {precision, cand[i]};
+    cicero_options opt = {precision, cand[i], 0};
     const size_t need = cicero_render_workspace_size(grid, cam ? cam->width * cam->height : 0, sampling, &opt);
     if (need == 0 || need > ws_bytes) continue;
     // one untimed render (first use of the kernel), then one timed render
@@ -486,6 +545,7 @@ cicero_status cicero_render_backward(const cicero_grid* grid, const cicero_mlp* 
   RaySrc src;
   memset(&src, 0, sizeof src);
   src.kind = 1;
+  src.n_views = 1;
   src.o = ray_o;
   src.d = ray_d;
   src.n_max = n_rays;
@@ -530,6 +590,8 @@ cicero_status cicero_workspace_status(void* workspace, void* stream) {
   e = cudaMemcpy(workspace, &zero, 4, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(clear status)");
   if (word & kErrTimeout) return fail(CICERO_ERR_TIMEOUT, "a kernel's bounded wait ran out");
+  if (word & kErrCapacity)
+    return fail(CICERO_ERR_WORKSPACE_TOO_SMALL, "the rays composited more samples than opt->max_records allows");
   if (word & kErrInternal) return fail(CICERO_ERR_INTERNAL, "a kernel found a broken invariant");
   return CICERO_OK;
 }

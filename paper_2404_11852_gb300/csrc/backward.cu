@@ -12,6 +12,8 @@
 //                      leaves the brick, one global atomicAdd per touched vertex entry.
 #include <cuda_runtime.h>
 
+#include <string.h>
+
 #include <algorithm>
 
 #include "common.cuh"
@@ -37,7 +39,7 @@ __global__ void __launch_bounds__(256) k_bwd_ray(RaySrc src, Samp s, RenderWs w,
   const float dt = s.step > 0.0f ? s.step : __fdiv_rn(__fsub_rn(s.far_t, s.near_t), (float)s.n_samples);
   for (int r = warp; r < R; r += nwarps) {
     const uint32_t n = w.ray_n[r];
-    const size_t rec0 = (size_t)r * w.S;
+    const size_t rec0 = w.ray_start[r];
     const float g0 = d_rgb[3 * r], g1 = d_rgb[3 * r + 1], g2 = d_rgb[3 * r + 2];
     float tot = 0.0f;
     for (uint32_t j = lane; j < n; j += 32) {
@@ -211,8 +213,9 @@ __global__ void __launch_bounds__(256, 1) k_bwd_brick(GridGeo g, RaySrc src, Mlp
       const int m = threadIdx.x & (kBT - 1), part = threadIdx.x >> 6;
       if (part < 2) {
         const bool valid = m < mcnt;
-        uint32_t sid = valid ? w.sorted[start + m] : 0;
-        const int r = (int)(sid / (uint32_t)S);
+        const uint2 rq = valid ? w.srt_rq[start + m] : make_uint2(0u, 0u);
+        const uint32_t sid = rq.y;
+        const int r = (int)rq.x;
         float d[3] = {0.0f, 0.0f, 1.0f};
         if (valid) {
           const float4 dd = w.ray_dir[r];
@@ -223,7 +226,7 @@ __global__ void __launch_bounds__(256, 1) k_bwd_brick(GridGeo g, RaySrc src, Mlp
         if (part == 0) {
           int ok = 0;
           if (valid) {
-            const float4 pw = w.rec_pw[sid];
+            const float4 pw = w.srt_pw[start + m];
             const float p[3] = {pw.x, pw.y, pw.z};
             float f[3], fv[24];
             int i0[3];
@@ -353,7 +356,9 @@ __global__ void __launch_bounds__(256, 1) k_bwd_brick(GridGeo g, RaySrc src, Mlp
 
 cicero_status run_backward(const cicero_grid* grid, const MlpPtrs& mlp, const RenderPlan& plan, const RaySrc& src,
                            const RenderWs& ws, const float* d_rgb, float* d_dens, float* d_feat, cudaStream_t st) {
-  cicero_status s = run_render(grid, mlp, plan, src, ws, nullptr, nullptr, nullptr, nullptr, false, st);
+  OutBufs none;
+  memset(&none, 0, sizeof none);
+  cicero_status s = run_render(grid, mlp, plan, src, ws, none, false, st);
   if (s != CICERO_OK) return s;
   const int nw = src.n_max;
   int blocks = (nw + 7) / 8;

@@ -21,6 +21,7 @@ constexpr int kMaxIn = 48;          // MLP input padded to 48 (3 x K16 MMA steps
 // error bits recorded in the workspace header
 constexpr uint32_t kErrInternal = 1u;
 constexpr uint32_t kErrTimeout = 2u;
+constexpr uint32_t kErrCapacity = 4u;   // the record capacity of the workspace was exceeded
 constexpr long long kWaitCycles = 4ll << 30;  // bounded mbarrier waits: ~2 s of SM clock
 
 // -------------------------------------------------------------------------------------------
@@ -48,50 +49,94 @@ struct Samp {
   float void_acc;
 };
 
-struct RaySrc {
-  int kind;            // 0: camera pixels, 1: explicit rays
-  int width;
-  float f, cx, cy;
+constexpr int kMaxViews = 32;
+
+struct ViewCam {
   float c2w[12];
-  const int32_t* pix;  // camera pixel list (NULL: ray r is pixel r)
+  float f, cx, cy;
+  int width;
+};
+
+// Where the rays of a call come from.
+//   kind 0: pixels of cam[0] (all of them, or the list pix[0] of *n_dev / n_max entries)
+//   kind 1: explicit rays o, d [n_max][3]
+//   kind 2: the pixel lists pix[v] of n_views cameras, n_dev[v] entries each (device counts)
+struct RaySrc {
+  int kind;
+  int n_views;
+  int n_max;              // host bound on the total ray count
+  const int32_t* n_dev;   // device ray count(s) or NULL
   const float* o;
   const float* d;
-  const int32_t* n_dev;  // device ray count (hole lists) or NULL
-  int n_max;             // host bound on the ray count
+  const int32_t* pix[kMaxViews];
+  ViewCam cam[kMaxViews];
 };
 
 __device__ __forceinline__ int ray_count(const RaySrc& s) {
-  if (s.n_dev) {
-    int n = *s.n_dev;
-    return n < s.n_max ? (n < 0 ? 0 : n) : s.n_max;
+  long long n = s.n_max;
+  if (s.kind == 2) {
+    long long t = 0;
+    for (int v = 0; v < s.n_views; v++) t += max(0, s.n_dev[v]);
+    n = t < n ? t : n;
+  } else if (s.n_dev) {
+    const int c = *s.n_dev;
+    n = c < n ? (c < 0 ? 0 : c) : n;
   }
-  return s.n_max;
+  return (int)n;
+}
+
+// Which view and which pixel (ray index for explicit rays) ray r is.
+struct RayRef {
+  int view;
+  int pix;
+};
+
+__device__ __forceinline__ RayRef ray_ref(const RaySrc& s, int r) {
+  RayRef q;
+  q.view = 0;
+  q.pix = r;
+  if (s.kind == 0) {
+    if (s.pix[0]) q.pix = s.pix[0][r];
+  } else if (s.kind == 2) {
+    int base = 0;
+    for (int v = 0; v < s.n_views; v++) {
+      const int n = max(0, s.n_dev[v]);
+      if (r < base + n) {
+        q.view = v;
+        q.pix = s.pix[v][r - base];
+        return q;
+      }
+      base += n;
+    }
+  }
+  return q;
 }
 
 // Ray of pixel/ray r: pinhole model of Eq. 1 / Eq. 3 (centre (i + 1/2, j + 1/2)).
-__device__ __forceinline__ void ray_gen(const RaySrc& s, int r, float o[3], float d[3]) {
+__device__ __forceinline__ void ray_gen(const RaySrc& s, const RayRef& q, float o[3], float d[3]) {
   if (s.kind == 1) {
 #pragma unroll
     for (int a = 0; a < 3; a++) {
-      o[a] = s.o[3 * r + a];
-      d[a] = s.d[3 * r + a];
+      o[a] = s.o[3 * q.pix + a];
+      d[a] = s.d[3 * q.pix + a];
     }
     return;
   }
-  int p = s.pix ? s.pix[r] : r;
-  int i = p % s.width, j = p / s.width;
-  float u = __fadd_rn((float)i, 0.5f), v = __fadd_rn((float)j, 0.5f);
-  float dx = __fdiv_rn(__fsub_rn(u, s.cx), s.f);
-  float dy = __fdiv_rn(__fsub_rn(v, s.cy), s.f);
+  const ViewCam& c = s.cam[q.view];
+  const int i = q.pix % c.width, j = q.pix / c.width;
+  const float u = __fadd_rn((float)i, 0.5f), v = __fadd_rn((float)j, 0.5f);
+  const float dx = __fdiv_rn(__fsub_rn(u, c.cx), c.f);
+  const float dy = __fdiv_rn(__fsub_rn(v, c.cy), c.f);
   float w[3];
 #pragma unroll
   for (int a = 0; a < 3; a++)
-    w[a] = __fadd_rn(__fadd_rn(__fmul_rn(s.c2w[4 * a], dx), __fmul_rn(s.c2w[4 * a + 1], dy)), s.c2w[4 * a + 2]);
-  float nn = __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(w[0], w[0]), __fmul_rn(w[1], w[1])), __fmul_rn(w[2], w[2])));
+    w[a] = __fadd_rn(__fadd_rn(__fmul_rn(c.c2w[4 * a], dx), __fmul_rn(c.c2w[4 * a + 1], dy)), c.c2w[4 * a + 2]);
+  const float nn =
+      __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(w[0], w[0]), __fmul_rn(w[1], w[1])), __fmul_rn(w[2], w[2])));
 #pragma unroll
   for (int a = 0; a < 3; a++) {
     d[a] = __fdiv_rn(w[a], nn);
-    o[a] = s.c2w[4 * a + 3];
+    o[a] = c.c2w[4 * a + 3];
   }
 }
 

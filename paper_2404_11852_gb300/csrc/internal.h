@@ -33,14 +33,20 @@ struct ProfScope {
 };
 
 // Workspace of one rendering call (all device pointers, carved from the caller's buffer).
+// Records (one per composited sample) are allocated per ray from a capacity of Q records: each ray
+// reserves an upper bound of its sample count (from the slab test) and fills a prefix of it.
 struct RenderWs {
-  uint32_t* hdr;        // [0] error bits, [1] tile count, [2] active samples, [3] spare
+  uint32_t* hdr;        // [0] error bits, [1] tile count, [2] composited samples, [3] records reserved
   uint32_t* ray_n;      // [R] composited samples of each ray
+  uint32_t* ray_start;  // [R] first record of each ray
   float* ray_T;         // [R] transmittance after the last composited slot
   float4* ray_dir;      // [R] unit direction of each ray
-  uint32_t* rec_key;    // [R*S] brick id of record (ray r, rank j) at r*S + j
-  float4* rec_pw;       // [R*S] sample position (FP32, bit-identical to the march) and weight T_k alpha_k
-  uint16_t* rec_k;      // [R*S] slot index (only for Ray Index Table export; may be null)
+  uint32_t* rec_key;    // [Q] brick id
+  float4* rec_pw;       // [Q] sample position (FP32, bit-identical to the march) and weight T_k alpha_k
+  uint16_t* rec_k;      // [Q] slot index (only for Ray Index Table export; may be null)
+  float4* rec_c;        // [Q] (c_r, c_g, c_b, w) of each record
+  float* rec_T;         // [Q] transmittance before the slot (backward only; may be null)
+  float* rec_raw;       // [Q] interpolated raw density, then dL/draw (backward only; may be null)
   uint32_t* brick_cnt;  // [nb]
   uint32_t* brick_off;  // [nb + 1]
   uint32_t* brick_cur;  // [nb]
@@ -48,11 +54,10 @@ struct RenderWs {
   uint32_t* blk_sums;   // [2 * scan blocks] per-block sums of the brick scan
   uint32_t* tile_brick; // [max_tiles]
   uint32_t* tile_start; // [max_tiles]
-  uint32_t* sorted;     // [R*S] record ids grouped by brick
-  float4* rec_c;        // [R*S] (c_r, c_g, c_b, w) of each record
-  float* rec_T;         // [R*S] transmittance before the slot (backward only; may be null)
-  float* rec_raw;       // [R*S] interpolated raw density (backward only; may be null)
+  float4* srt_pw;       // [Q] records' (position, weight) in brick order (the Ray Index Table payload)
+  uint2* srt_rq;        // [Q] records' (ray, record index) in brick order
   int R, S, nb, max_tiles;
+  uint32_t Q;
 };
 
 struct RenderPlan {
@@ -60,9 +65,19 @@ struct RenderPlan {
   Samp samp;
   int R, S, nb;
   int max_tiles;
+  uint32_t Q;
   bool want_k;
   bool want_bwd;
   cicero_precision precision;
+};
+
+// Output buffers of a rendering call, per view (rgb/depth indexed by pixel, or by ray for explicit
+// rays); acc and n_steps only for single-view calls.
+struct OutBufs {
+  float* rgb[kMaxViews];
+  float* depth[kMaxViews];
+  float* acc;
+  int32_t* n_steps;
 };
 
 size_t render_ws_bytes(const RenderPlan& p);
@@ -80,8 +95,7 @@ struct MlpPtrs {
 };
 
 cicero_status run_render(const cicero_grid* grid, const MlpPtrs& mlp, const RenderPlan& plan, const RaySrc& src,
-                         const RenderWs& ws, float* rgb, float* depth, float* acc, int32_t* n_steps,
-                         bool stop_after_bucketing, cudaStream_t st);
+                         const RenderWs& ws, const OutBufs& out, bool stop_after_bucketing, cudaStream_t st);
 
 cicero_status run_rit_export(const RenderWs& ws, int n_bricks, int S, int32_t* brick_offsets, int32_t* samples,
                              cudaStream_t st);

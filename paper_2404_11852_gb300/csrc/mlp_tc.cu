@@ -426,9 +426,10 @@ __global__ void __launch_bounds__(512, 1) k_gather_mlp_bf16(GridGeo g, int S, Ml
     nstart = w.tile_start[ti];
     nmcnt = (int)(min(nstart + (uint32_t)kTile, w.brick_off[nb_ + 1]) - nstart);
     if (m < nmcnt) {
-      nsid = w.sorted[nstart + m];
-      npw = w.rec_pw[nsid];
-      ndir = w.ray_dir[nsid / (uint32_t)S];
+      const uint2 rq = w.srt_rq[nstart + m];
+      nsid = rq.y;
+      npw = w.srt_pw[nstart + m];
+      ndir = w.ray_dir[rq.x];
     }
   };
   if (t_begin < t_end) fetch(t_begin);

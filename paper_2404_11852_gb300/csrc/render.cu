@@ -1,10 +1,12 @@
 // Memory-centric voxel-grid NeRF rendering (Sec. II-B stages, reordered as in Sec. IV-A).
 //
 //   K1 k_march        one warp per ray, 32 slots per step: Indexing, density gathering,
-//                     alpha, transmittance by a warp scan of sigma*delta, early stop; emits one
-//                     record (t, w, brick) per composited sample and a brick histogram
+//                     alpha, transmittance by a warp scan of sigma*delta, early stop; reserves an
+//                     upper bound of its records, emits one record (position, w, brick) per
+//                     composited sample and counts them into the brick histogram
 //   K2 k_brick_*      brick offsets (3-phase exclusive scan of the histogram) and the tile list
-//   K3 k_scatter      counting sort of the records by brick: the Ray Index Table
+//   K3 k_scatter      counting sort of the records by brick, moving their payload into brick
+//                     order: the Ray Index Table
 //   K5 k_gather_mlp_f32 / mlp_tc.cu
 //                     per brick: one TMA copy of the brick (+1 vertex halo) into shared memory,
 //                     trilinear feature gathering from there, view encoding and the MLP
@@ -21,36 +23,39 @@ namespace cicero {
 static size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 
 size_t render_ws_bytes(const RenderPlan& p) {
-  size_t RS = (size_t)p.R * p.S;
+  const size_t Q = p.Q, R = (size_t)p.R;
   size_t b = al256(64);
-  b += 2 * al256(4 * (size_t)p.R) + al256(16 * (size_t)p.R);
-  b += al256(4 * RS) + al256(16 * RS);
-  if (p.want_k) b += al256(2 * RS);
+  b += 3 * al256(4 * R) + al256(16 * R);
+  b += al256(4 * Q) + 2 * al256(16 * Q);
+  if (p.want_k) b += al256(2 * Q);
+  if (p.want_bwd) b += 2 * al256(4 * Q);
   b += 2 * al256(4 * (size_t)p.nb) + 2 * al256(4 * ((size_t)p.nb + 1));
   b += al256(8 * ((size_t)p.nb / 4096 + 2));
   b += 2 * al256(4 * (size_t)p.max_tiles);
-  b += al256(4 * RS);
-  b += al256(16 * RS);
-  if (p.want_bwd) b += 2 * al256(4 * RS);
+  b += al256(16 * Q) + al256(8 * Q);
   return b;
 }
 
 bool carve_render_ws(void* ws, size_t bytes, const RenderPlan& p, RenderWs* w) {
   if (render_ws_bytes(p) > bytes) return false;
   char* q = (char*)ws;
-  size_t RS = (size_t)p.R * p.S;
+  const size_t Q = p.Q, R = (size_t)p.R;
   auto take = [&](size_t n) {
     char* r = q;
     q += al256(n);
     return (void*)r;
   };
   w->hdr = (uint32_t*)take(64);
-  w->ray_n = (uint32_t*)take(4 * (size_t)p.R);
-  w->ray_T = (float*)take(4 * (size_t)p.R);
-  w->ray_dir = (float4*)take(16 * (size_t)p.R);
-  w->rec_key = (uint32_t*)take(4 * RS);
-  w->rec_pw = (float4*)take(16 * RS);
-  w->rec_k = p.want_k ? (uint16_t*)take(2 * RS) : nullptr;
+  w->ray_n = (uint32_t*)take(4 * R);
+  w->ray_start = (uint32_t*)take(4 * R);
+  w->ray_T = (float*)take(4 * R);
+  w->ray_dir = (float4*)take(16 * R);
+  w->rec_key = (uint32_t*)take(4 * Q);
+  w->rec_pw = (float4*)take(16 * Q);
+  w->rec_c = (float4*)take(16 * Q);
+  w->rec_k = p.want_k ? (uint16_t*)take(2 * Q) : nullptr;
+  w->rec_T = p.want_bwd ? (float*)take(4 * Q) : nullptr;
+  w->rec_raw = p.want_bwd ? (float*)take(4 * Q) : nullptr;
   w->brick_cnt = (uint32_t*)take(4 * (size_t)p.nb);
   w->brick_cur = (uint32_t*)take(4 * (size_t)p.nb);
   w->brick_off = (uint32_t*)take(4 * ((size_t)p.nb + 1));
@@ -58,14 +63,13 @@ bool carve_render_ws(void* ws, size_t bytes, const RenderPlan& p, RenderWs* w) {
   w->blk_sums = (uint32_t*)take(8 * ((size_t)p.nb / 4096 + 2));
   w->tile_brick = (uint32_t*)take(4 * (size_t)p.max_tiles);
   w->tile_start = (uint32_t*)take(4 * (size_t)p.max_tiles);
-  w->sorted = (uint32_t*)take(4 * RS);
-  w->rec_c = (float4*)take(16 * RS);
-  w->rec_T = p.want_bwd ? (float*)take(4 * RS) : nullptr;
-  w->rec_raw = p.want_bwd ? (float*)take(4 * RS) : nullptr;
+  w->srt_pw = (float4*)take(16 * Q);
+  w->srt_rq = (uint2*)take(8 * Q);
   w->R = p.R;
   w->S = p.S;
   w->nb = p.nb;
   w->max_tiles = p.max_tiles;
+  w->Q = p.Q;
   return true;
 }
 
@@ -83,62 +87,102 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
-__device__ __forceinline__ int out_index(const RaySrc& s, int r) {
-  return (s.kind == 0 && s.pix) ? s.pix[r] : r;
+// Upper bound of the samples a ray can composite: its slots within two slots of the box span
+// (the slab test in FP32; the inside test that decides may differ from it only by rounding).
+__device__ __forceinline__ int record_bound(const GridGeo& g, const Slots& sl, const float o[3], const float d[3]) {
+  if (sl.n <= 0) return 0;
+  float lo = -3.0e38f, hi = 3.0e38f;
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    if (d[a] == 0.0f) continue;
+    float t0 = __fdiv_rn(__fsub_rn(g.amin[a], o[a]), d[a]);
+    float t1 = __fdiv_rn(__fsub_rn(g.amax[a], o[a]), d[a]);
+    lo = fmaxf(lo, fminf(t0, t1));
+    hi = fminf(hi, fmaxf(t0, t1));
+  }
+  if (lo > hi + 2.0f * sl.dt) return 0;
+  const float a = fminf(lo, hi), b = fmaxf(lo, hi);
+  const float klo = (a - sl.t0) / sl.dt - 2.5f, khi = (b - sl.t0) / sl.dt + 1.5f;
+  const int kmin = (int)floorf(fminf(fmaxf(klo, 0.0f), (float)sl.n));
+  const int kmax = (int)ceilf(fminf(fmaxf(khi, -1.0f), (float)(sl.n - 1)));
+  return kmax >= kmin ? kmax - kmin + 1 : 0;
 }
 
 // K1: one warp per ray; lane = slot within a chunk of 32 slots.
 template <typename T>
 __global__ void __launch_bounds__(256) k_march(GridGeo g, Samp s, RaySrc src, const T* __restrict__ dens,
-                                               RenderWs w, float* depth, float* acc_out, int32_t* nsteps_out) {
+                                               RenderWs w, OutBufs out) {
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   const int R = ray_count(src);
+  const unsigned full = 0xffffffffu;
   const unsigned lt_mask = (1u << lane) - 1u;
+  const unsigned le_mask = (2u << lane) - 1u;  // lanes <= this one (all ones for lane 31)
   for (int r = warp; r < R; r += nwarps) {
+    const RayRef rr = ray_ref(src, r);
     float o[3], d[3];
-    ray_gen(src, r, o, d);
-    Slots sl = place_slots(g, s, o, d);
-    float Ssum = 0.0f, acc = 0.0f, dsum = 0.0f;
+    ray_gen(src, rr, o, d);
+    const Slots sl = place_slots(g, s, o, d);
+    const int bound = record_bound(g, sl, o, d);
+    uint32_t base = 0;
+    if (lane == 0 && bound > 0) base = atomicAdd(&w.hdr[3], (uint32_t)bound);
+    base = __shfl_sync(full, base, 0);
+    const bool room = (unsigned long long)base + (unsigned)bound <= (unsigned long long)w.Q;
+    if (!room && lane == 0) set_err(&w.hdr[0], kErrCapacity);
+    float Ssum = 0.0f, acc_l = 0.0f, dsum_l = 0.0f;
     uint32_t cnt = 0;
     int steps = sl.n;
-    const size_t rec0 = (size_t)r * s.n_samples;
     for (int k0 = 0; k0 < sl.n; k0 += 32) {
       const int k = k0 + lane;
       const float t = slot_t(sl, k);
       const bool valid = slot_valid(sl, k, t);
-      const unsigned vmask = __ballot_sync(0xffffffffu, valid);
+      const unsigned vmask = __ballot_sync(full, valid);
+      if (!vmask) {
+        steps = k0;
+        break;
+      }
       int i0[3] = {0, 0, 0};
       float f[3], p[3] = {0.0f, 0.0f, 0.0f};
       bool act = false;
-      float sd = 0.0f, raw = 0.0f;
       if (valid) {
         sample_pos(o, d, t, p);
         act = index_sample(g, p, i0, f);
-        if (act) {
-          raw = density_trilinear(g, dens, i0, f);
-          sd = softplus_f(raw + g.act_shift) * sl.dt;
+      }
+      if (!__any_sync(full, act)) {  // nothing to composite in these slots: only the stop test
+        if (s.t_stop > 0.0f && expf(-(Ssum + 0.0f)) < s.t_stop) {
+          steps = k0;
+          break;
         }
+        if (vmask != full) {
+          steps = k0 + __popc(vmask);
+          break;
+        }
+        continue;
+      }
+      float sd = 0.0f, raw = 0.0f;
+      if (act) {
+        raw = density_trilinear(g, dens, i0, f);
+        sd = softplus_f(raw + g.act_shift) * sl.dt;
       }
       float incl = sd;
 #pragma unroll
       for (int off = 1; off < 32; off <<= 1) {
-        float v = __shfl_up_sync(0xffffffffu, incl, off);
+        const float v = __shfl_up_sync(full, incl, off);
         if (lane >= off) incl += v;
       }
-      float excl = __shfl_up_sync(0xffffffffu, incl, 1);
+      float excl = __shfl_up_sync(full, incl, 1);
       if (lane == 0) excl = 0.0f;
       const float Tk = expf(-(Ssum + excl));
       const bool stop = valid && s.t_stop > 0.0f && Tk < s.t_stop;
-      const unsigned smask = __ballot_sync(0xffffffffu, stop);
+      const unsigned smask = __ballot_sync(full, stop);
       const int first = smask ? __ffs(smask) - 1 : 32;
-      const bool contrib = act && lane < first;
-      const float wk = contrib ? Tk * -expm1f(-sd) : 0.0f;
-      const unsigned cmask = __ballot_sync(0xffffffffu, contrib);
+      const bool contrib = act && lane < first && room;
+      const float wk = (act && lane < first) ? Tk * -expm1f(-sd) : 0.0f;
+      const unsigned cmask = __ballot_sync(full, contrib);
       const uint32_t key = contrib ? brick_id(g, i0) : 0xffffffffu;
       if (contrib) {
-        size_t q = rec0 + cnt + __popc(cmask & lt_mask);
+        const size_t q = (size_t)base + cnt + __popc(cmask & lt_mask);
         w.rec_pw[q] = make_float4(p[0], p[1], p[2], wk);
         w.rec_key[q] = key;
         if (w.rec_k) w.rec_k[q] = (uint16_t)k;
@@ -147,31 +191,41 @@ __global__ void __launch_bounds__(256) k_march(GridGeo g, Samp s, RaySrc src, co
           w.rec_raw[q] = raw;
         }
       }
-      const unsigned peers = __match_any_sync(0xffffffffu, key);
-      if (contrib && (peers & lt_mask) == 0) atomicAdd(&w.brick_cnt[key], (uint32_t)__popc(peers));
-      acc += warp_sum(wk);
-      dsum += warp_sum(wk * t);
+      // brick histogram: one atomic per run of consecutive lanes with the same brick
+      const uint32_t prev = __shfl_up_sync(full, key, 1);
+      const bool head = contrib && (lane == 0 || prev != key);
+      const unsigned heads = __ballot_sync(full, head);
+      if (head) {
+        const unsigned after = heads & ~le_mask;
+        const int end = after ? __ffs(after) - 1 : 32;
+        const unsigned run = cmask & ~lt_mask & (end == 32 ? full : ((1u << end) - 1u));
+        atomicAdd(&w.brick_cnt[key], (uint32_t)__popc(run));
+      }
+      acc_l += wk;
+      dsum_l += wk * t;
       cnt += __popc(cmask);
       const int last = first == 32 ? 31 : first - 1;
-      float tot = __shfl_sync(0xffffffffu, incl, last < 0 ? 0 : last);
+      const float tot = __shfl_sync(full, incl, last < 0 ? 0 : last);
       if (first > 0) Ssum += tot;
       if (first < 32) {
         steps = k0 + first;
         break;
       }
-      if (vmask != 0xffffffffu) {
+      if (vmask != full) {
         steps = k0 + __popc(vmask);
         break;
       }
     }
+    const float acc = warp_sum(acc_l), dsum = warp_sum(dsum_l);
     if (lane == 0) {
       w.ray_n[r] = cnt;
+      w.ray_start[r] = base;
       w.ray_T[r] = expf(-Ssum);
       w.ray_dir[r] = make_float4(d[0], d[1], d[2], 0.0f);
-      const int oi = out_index(src, r);
-      if (depth) depth[oi] = acc >= s.void_acc ? dsum / acc : __int_as_float(0x7f800000);
-      if (acc_out) acc_out[oi] = acc;
-      if (nsteps_out) nsteps_out[oi] = steps;
+      float* dep = out.depth[rr.view];
+      if (dep) dep[rr.pix] = acc >= s.void_acc ? dsum / acc : __int_as_float(0x7f800000);
+      if (out.acc) out.acc[rr.pix] = acc;
+      if (out.n_steps) out.n_steps[rr.pix] = steps;
     }
   }
 }
@@ -306,26 +360,43 @@ __global__ void __launch_bounds__(256) k_tiles(RenderWs w) {
   }
 }
 
-// K3: counting sort of the records by brick (order inside a brick is unspecified).
+// K3: counting sort of the records by brick; the payload moves into brick order so that the
+// gather kernels stream it (order inside a brick is unspecified).
 __global__ void __launch_bounds__(256) k_scatter(RaySrc src, RenderWs w) {
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   const int R = ray_count(src);
+  const unsigned full = 0xffffffffu;
   const unsigned lt_mask = (1u << lane) - 1u;
+  const unsigned le_mask = (2u << lane) - 1u;
   for (int r = warp; r < R; r += nwarps) {
-    const uint32_t n = w.ray_n[r];
-    const size_t rec0 = (size_t)r * w.S;
+    const uint32_t n = w.ray_n[r], start = w.ray_start[r];
     for (uint32_t j0 = 0; j0 < n; j0 += 32) {
       const uint32_t j = j0 + lane;
       const bool valid = j < n;
-      const uint32_t key = valid ? w.rec_key[rec0 + j] : 0xffffffffu;
-      const unsigned peers = __match_any_sync(0xffffffffu, key);
-      const int leader = __ffs(peers) - 1;
-      uint32_t base = 0;
-      if (valid && lane == leader) base = atomicAdd(&w.brick_cur[key], (uint32_t)__popc(peers));
-      base = __shfl_sync(0xffffffffu, base, leader);
-      if (valid) w.sorted[w.brick_off[key] + base + __popc(peers & lt_mask)] = (uint32_t)(rec0 + j);
+      const uint32_t q = start + j;
+      const uint32_t key = valid ? w.rec_key[q] : 0xffffffffu;
+      const float4 pw = valid ? w.rec_pw[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+      const unsigned vmask = __ballot_sync(full, valid);
+      const uint32_t prev = __shfl_up_sync(full, key, 1);
+      const bool head = valid && (lane == 0 || prev != key);
+      const unsigned heads = __ballot_sync(full, head);
+      uint32_t off = 0;
+      if (head) {
+        const unsigned after = heads & ~le_mask;
+        const int end = after ? __ffs(after) - 1 : 32;
+        const unsigned run = vmask & ~lt_mask & (end == 32 ? full : ((1u << end) - 1u));
+        off = atomicAdd(&w.brick_cur[key], (uint32_t)__popc(run));
+      }
+      // every lane takes the base of its run's head
+      const int hl = 31 - __clz(heads & le_mask);
+      off = __shfl_sync(full, off, hl < 0 ? 0 : hl);
+      if (valid) {
+        const uint32_t dst = w.brick_off[key] + off + (uint32_t)(lane - hl);
+        w.srt_pw[dst] = pw;
+        w.srt_rq[dst] = make_uint2((uint32_t)r, q);
+      }
     }
   }
 }
@@ -553,10 +624,10 @@ __global__ void __launch_bounds__(256, 1) k_gather_mlp_f32(GridGeo g, int S, Mlp
     }
     if (!__syncthreads_and(alive)) break;
     if (m < mcnt) {
-      const uint32_t sid = w.sorted[start + m];
-      const int r = (int)(sid / (uint32_t)S);
+      const uint2 rq = w.srt_rq[start + m];
+      const int r = (int)rq.x;
       if (part == 0) {
-        const float4 pw = w.rec_pw[sid];
+        const float4 pw = w.srt_pw[start + m];
         const float p[3] = {pw.x, pw.y, pw.z};
         float f[3], feat[24];
         int i0[3];
@@ -587,25 +658,22 @@ __global__ void __launch_bounds__(256, 1) k_gather_mlp_f32(GridGeo g, int S, Mlp
     __syncthreads();
     float c[3];
     mlp_f32_tile(sm, c);
-    if (threadIdx.x < kTile && m < mcnt) {
-      const uint32_t sid = w.sorted[start + m];
-      w.rec_c[sid] = make_float4(c[0], c[1], c[2], w.rec_pw[sid].w);
-    }
+    if (threadIdx.x < kTile && m < mcnt)
+      w.rec_c[w.srt_rq[start + m].y] = make_float4(c[0], c[1], c[2], w.srt_pw[start + m].w);
   }
 }
 
 // K6: per ray, in slot order.
-__global__ void __launch_bounds__(256) k_composite(RaySrc src, Samp s, RenderWs w, float* rgb) {
+__global__ void __launch_bounds__(256) k_composite(RaySrc src, Samp s, RenderWs w, OutBufs out) {
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   const int R = ray_count(src);
   for (int r = warp; r < R; r += nwarps) {
-    const uint32_t n = w.ray_n[r];
-    const size_t rec0 = (size_t)r * w.S;
+    const uint32_t n = w.ray_n[r], start = w.ray_start[r];
     float a0 = 0.f, a1 = 0.f, a2 = 0.f;
     for (uint32_t j = lane; j < n; j += 32) {
-      const float4 v = w.rec_c[rec0 + j];
+      const float4 v = w.rec_c[start + j];
       a0 += v.w * v.x;
       a1 += v.w * v.y;
       a2 += v.w * v.z;
@@ -615,10 +683,11 @@ __global__ void __launch_bounds__(256) k_composite(RaySrc src, Samp s, RenderWs 
     a2 = warp_sum(a2);
     if (lane == 0) {
       const float T = w.ray_T[r];
-      const int oi = out_index(src, r);
-      rgb[3 * oi + 0] = a0 + T * s.bg[0];
-      rgb[3 * oi + 1] = a1 + T * s.bg[1];
-      rgb[3 * oi + 2] = a2 + T * s.bg[2];
+      const RayRef rr = ray_ref(src, r);
+      float* rgb = out.rgb[rr.view];
+      rgb[3 * rr.pix + 0] = a0 + T * s.bg[0];
+      rgb[3 * rr.pix + 1] = a1 + T * s.bg[1];
+      rgb[3 * rr.pix + 2] = a2 + T * s.bg[2];
     }
   }
 }
@@ -629,9 +698,8 @@ __global__ void k_rit_export(RenderWs w, int n_bricks, int32_t* offs, int32_t* s
   const size_t i0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x, st = (size_t)gridDim.x * blockDim.x;
   for (size_t i = i0; i <= (size_t)n_bricks; i += st) offs[i] = (int32_t)w.brick_off[i];
   for (size_t i = i0; i < total; i += st) {
-    const uint32_t sid = w.sorted[i];
-    const uint32_t r = sid / (uint32_t)w.S;
-    samples[i] = (int32_t)(r * (uint32_t)w.S + w.rec_k[sid]);
+    const uint2 rq = w.srt_rq[i];
+    samples[i] = (int32_t)(rq.x * (uint32_t)w.S + w.rec_k[rq.y]);
   }
 }
 
@@ -675,8 +743,7 @@ static cicero_status launch_f32(const GridGeo& geo, const RaySrc& src, int S, co
 }
 
 cicero_status run_render(const cicero_grid* grid, const MlpPtrs& mlp, const RenderPlan& plan, const RaySrc& src,
-                         const RenderWs& ws, float* rgb, float* depth, float* acc, int32_t* n_steps,
-                         bool stop_after_bucketing, cudaStream_t st) {
+                         const RenderWs& ws, const OutBufs& out, bool stop_after_bucketing, cudaStream_t st) {
   const GridGeo& geo = plan.geo;
   const bool f16 = grid->dtype == CICERO_F16;
   const int mb = blocks_for_warps(src.n_max, 16);
@@ -684,9 +751,9 @@ cicero_status run_render(const cicero_grid* grid, const MlpPtrs& mlp, const Rend
     ProfScope ps(kStMarch, st);
     k_clear<<<std::min(num_sms() * 4, (plan.nb + 255) / 256 + 1), 256, 0, st>>>(ws.hdr, 16, ws.brick_cnt, plan.nb);
     if (f16)
-      k_march<__half><<<mb, 256, 0, st>>>(geo, plan.samp, src, (const __half*)grid->density, ws, depth, acc, n_steps);
+      k_march<__half><<<mb, 256, 0, st>>>(geo, plan.samp, src, (const __half*)grid->density, ws, out);
     else
-      k_march<float><<<mb, 256, 0, st>>>(geo, plan.samp, src, (const float*)grid->density, ws, depth, acc, n_steps);
+      k_march<float><<<mb, 256, 0, st>>>(geo, plan.samp, src, (const float*)grid->density, ws, out);
   }
   {
     ProfScope ps(kStBucket, st);
@@ -713,10 +780,10 @@ cicero_status run_render(const cicero_grid* grid, const MlpPtrs& mlp, const Rend
             : launch_f32<float>(geo, src, plan.S, mlp, ws, map, box, st);
   }
   if (s != CICERO_OK) return s;
-  if (!rgb) return CICERO_OK;  // the backward only needs the per-sample records
+  if (!out.rgb[0]) return CICERO_OK;  // the backward only needs the per-sample records
   {
     ProfScope ps(kStComposite, st);
-    k_composite<<<mb, 256, 0, st>>>(src, plan.samp, ws, rgb);
+    k_composite<<<mb, 256, 0, st>>>(src, plan.samp, ws, out);
   }
   count_launches(1);
   e = cudaGetLastError();

@@ -94,7 +94,10 @@ __global__ void __launch_bounds__(256) k_splat(WarpArgs a, const float* __restri
 __device__ __forceinline__ bool warp_ray_has_sample(const VoidTest& vt, int p) {
   const int lane = threadIdx.x & 31;
   float o[3], d[3];
-  ray_gen(vt.src, p, o, d);
+  RayRef rr;
+  rr.view = 0;
+  rr.pix = p;
+  ray_gen(vt.src, rr, o, d);
   const Slots sl = place_slots(vt.g, vt.s, o, d);
   for (int k0 = 0; k0 < sl.n; k0 += 32) {
     const int k = k0 + lane;

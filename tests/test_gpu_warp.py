@@ -151,3 +151,65 @@ def test_sparw_chain_against_oracle_chain(cc, orc):
     print(f"SpaRW chain GPU vs oracle chain: {p:.1f} dB; oracle SpaRW vs full render: {psnr(o_rgb, full):.1f} dB; "
           f"holes {o_w['n_holes']} of {NT}")
     assert p >= 40.0
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_render_holes_batch_matches_single(cc, orc, ref_frame, precision):
+    """All targets' holes in one pass give exactly the per-target results (same per-ray and
+    per-sample arithmetic), and match the oracle on the holes."""
+    import torch
+    g, m, cam, rgb, depth = ref_frame
+    gd, md = cc.DeviceGrid.from_host(g), cc.DeviceMlp.from_host(m)
+    sd = cc.sampling_from(cam.sampling)
+    tgts = [scenes.offset_camera(cam, k, yaw_deg=2.0, shift=0.01) for k in (-6, -1, 3, 7)]
+    tgts.append(scenes.Camera(40, 30, cam.f * 0.7, 20.0, 15.0, tgts[0].c2w, cam.sampling))  # another size
+    outs, n_tot = [], 0
+    nh = torch.zeros(len(tgts), dtype=torch.int32, device="cuda")
+    for i, t in enumerate(tgts):
+        got = gpu_warp(cc, rgb, depth, cam, t, void_grid=g, void_sp=cam.sampling)
+        wr, wd, hidx, n1 = got["_dev"]
+        nh[i] = n1[0]
+        outs.append((t, wr, wd, hidx, got))
+        n_tot += t.width * t.height
+    # per-target renders into copies
+    single = []
+    for t, wr, wd, hidx, got in outs:
+        r1, d1 = wr.clone(), wd.clone()
+        NT = t.width * t.height
+        opt = cc.options(precision, 4)
+        ws = cc.workspace(cc.cicero_render_workspace_size(gd.desc, NT, sd, opt))
+        cc.cicero_render_holes(gd.desc, md.desc, cc.camera_from(t), sd, opt, hidx, nh[len(single):len(single) + 1],
+                               NT, r1, d1, ws)
+        cc.cicero_workspace_status(ws)
+        single.append((r1, d1))
+    opt = cc.options(precision, 4, max_records=2_000_000)
+    ws = cc.workspace(cc.cicero_render_workspace_size(gd.desc, n_tot, sd, opt))
+    cc.cicero_render_holes_batch(gd.desc, md.desc, [cc.camera_from(t) for t, *_ in outs], sd, opt,
+                                 [o[3] for o in outs], nh, n_tot, [o[1] for o in outs], [o[2] for o in outs], ws)
+    cc.cicero_workspace_status(ws)
+    tol = 1e-4 if precision == 0 else 2e-2
+    for (t, wr, wd, hidx, got), (r1, d1) in zip(outs, single):
+        assert torch.equal(wr, r1) and torch.equal(wd, d1)
+        holes = got["hole_idx"]
+        if len(holes):
+            ref = orc.render(g, m, cam.sampling, cam=t, pix=holes)
+            sub = {"rgb": wr.cpu().double().numpy()[holes], "depth": wd.cpu().double().numpy()[holes],
+                   "acc": ref["acc"]}
+            check_render(sub, ref, tol)
+
+
+def test_record_capacity_overflow_is_reported(cc, ref_frame):
+    """A workspace with too few records reports CICERO_ERR_WORKSPACE_TOO_SMALL instead of
+    writing past its capacity."""
+    import torch
+    g, m, cam, rgb, depth = ref_frame
+    gd, md = cc.DeviceGrid.from_host(g), cc.DeviceMlp.from_host(m)
+    sd, cd = cc.sampling_from(cam.sampling), cc.camera_from(cam)
+    R = cam.width * cam.height
+    opt = cc.options(0, 8, max_records=1000)
+    ws = cc.workspace(cc.cicero_render_workspace_size(gd.desc, R, sd, opt))
+    out = torch.empty(R, 3, device="cuda")
+    cc.cicero_render(gd.desc, md.desc, cd, sd, opt, out, None, None, None, ws)
+    with pytest.raises(cc.CiceroError) as e:
+        cc.cicero_workspace_status(ws)
+    assert e.value.status == cc.ERR_WORKSPACE
