@@ -399,6 +399,308 @@ __device__ __forceinline__ Group setup(char* sm, const MlpPtrs& mlp, int groups,
 
 }  // namespace tc
 
+// -------------------------------------------------------------------------------------------
+// Warp-specialized gather + MLP kernel (preferred; the group kernel below is the fallback for
+// bricks too large for its shared-memory plan).  Roles inside one persistent CTA per SM:
+//   warps 0..7   epilogue: warp w reads TMEM lane quarter w % 4, columns 64 * (w / 4) .. +63
+//   warps 8..15  gather: two groups of 4 warps take alternate tiles; each group keeps two TMA
+//                brick buffers and prefetches the brick of its next tile
+//   warp 16      one thread issues every tcgen05.mma and commit
+// A ring of `ns` A-operand stages (12 KB each) decouples gathering from layer 1; two TMEM slots
+// of 128 columns (with two 32 KB activation buffers) let the epilogue warps work on one tile
+// while the tensor cores run the other.  mbarriers:
+//   a1_full[st] (4 gather-warp arrivals) -> MMA; a1_empty[st] (commit of layer 1) -> gather;
+//   d_full[s] (commit of each layer) -> epilogue; e_done[s] (8 epilogue-warp arrivals) -> MMA;
+//   brick[group][buffer] (TMA transaction count) -> gather group.
+// Every wait is bounded; a timeout sets a shared flag that all roles poll, and every decision
+// taken by a gather group is made uniform across it before any named barrier.
+namespace wsp {
+
+constexpr int kEW = 8, kGW = 8, kWarps = kEW + kGW + 1, kThreads = kWarps * 32;
+constexpr int kSlots = 2;
+constexpr int kA1Bytes = kTile * tc::kK1 * 2;
+enum { kA1Full = 0, kA1Empty = 4, kDFull = 8, kEDone = 10, kBrick = 12, kNumBars = 16 };
+
+struct Layout {
+  int bars, a1, a2, tiles, box, total;
+};
+
+__host__ __device__ inline Layout layout(int ns, int box_bytes) {
+  Layout L;
+  L.bars = tc::Smem::bars;  // after the weights and biases
+  L.a1 = L.bars + 256;      // 16 mbarriers, TMEM address at +128, abort flag at +136, final mbarrier at +144
+  L.a2 = L.a1 + ns * kA1Bytes;
+  L.box = tc::align128(box_bytes);
+  L.tiles = L.a2 + kSlots * tc::kActBytes;
+  L.total = L.tiles + 4 * L.box;
+  return L;
+}
+
+__device__ __forceinline__ void arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+}  // namespace wsp
+
+template <typename T, int CC, int NF>
+__global__ void __launch_bounds__(wsp::kThreads, 1) k_gather_mlp_ws(GridGeo g, MlpPtrs mlp, RenderWs w,
+                                                                   const __grid_constant__ CUtensorMap fmap, int vb,
+                                                                   int vx, int box_bytes, int ns) {
+  using namespace tc;
+  using namespace wsp;
+  extern __shared__ __align__(1024) char sm[];
+  const Layout L = layout(ns, box_bytes);
+  uint64_t* bars = (uint64_t*)(sm + L.bars);
+  uint32_t* tslot = (uint32_t*)(sm + L.bars + 128);
+  volatile int* dead = (volatile int*)(sm + L.bars + 136);
+  uint32_t* err = &w.hdr[0];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  load_weights(sm, mlp);
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < ns; i++) {
+      mbar_init(&bars[kA1Full + i], 4);
+      mbar_init(&bars[kA1Empty + i], 1);
+    }
+    for (int i = 0; i < kSlots; i++) {
+      mbar_init(&bars[kDFull + i], 1);
+      mbar_init(&bars[kEDone + i], kEW);
+    }
+    for (int i = 0; i < 4; i++) mbar_init(&bars[kBrick + i], 1);
+    mbar_init((uint64_t*)(sm + L.bars + 144), 1);
+    fence_mbar_init();
+    *dead = 0;
+  }
+  fence_proxy_async();
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(256)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tslot;
+  const uint32_t n_tiles = w.hdr[1];
+  const uint32_t per = (n_tiles + gridDim.x - 1) / gridDim.x;
+  const uint32_t t_begin = blockIdx.x * per, t_end = min(n_tiles, t_begin + per);
+  const int n = t_end > t_begin ? (int)(t_end - t_begin) : 0;
+
+  if (warp < kEW) {
+    // ---------------------------------------------------------------- epilogue warps
+    const int q4 = warp & 3, half = warp >> 2, row = q4 * 32 + lane;
+    const uint32_t lane_base = (uint32_t)(q4 * 32) << 16;
+    bool ok = true;
+    for (int p = 0; ok && 2 * p < n; p++) {
+      const int np = min(2, n - 2 * p);
+      uint32_t qrec[2] = {0u, 0u};
+      float wrec[2] = {0.f, 0.f};
+      bool has[2] = {false, false};
+      if (half == 0) {
+        for (int u = 0; u < np; u++) {
+          const uint32_t ti = t_begin + 2 * p + u;
+          const uint32_t start = w.tile_start[ti], b = w.tile_brick[ti];
+          const uint32_t end = min(start + (uint32_t)kTile, w.brick_off[b + 1]);
+          has[u] = (uint32_t)row < end - start;
+          if (has[u]) {
+            qrec[u] = w.srt_rq[start + row].y;
+            wrec[u] = w.srt_pw[start + row].w;
+          }
+        }
+      }
+      for (int lr = 0; ok && lr < 3; lr++) {
+        for (int u = 0; ok && u < np; u++) {
+          const int t = 2 * p + u, sl = t & 1, k = t >> 1;
+          ok = __all_sync(0xffffffffu, mbar_wait(&bars[kDFull + sl], (uint32_t)(3 * k + lr) & 1u, err) && !*dead);
+          if (!ok) break;
+          fence_after();
+          const uint32_t taddr = tmem + (uint32_t)(sl * 128) + lane_base;
+          if (lr < 2) {
+            char* A2 = sm + L.a2 + sl * kActBytes;
+            const float* bias = (const float*)(sm + (lr == 0 ? Smem::b1 : Smem::b2));
+#pragma unroll 1
+            for (int cc = 0; cc < 2; cc++) {
+              const int col = half * 64 + cc * 32;
+              float v[32];
+              tmem_ld<32>(taddr + col, v);
+#pragma unroll
+              for (int q = 0; q < 4; q++) {
+                const float4* b4 = reinterpret_cast<const float4*>(bias + col + q * 8);
+                float y[8];
+                add2(v + q * 8, b4[0], y);
+                add2(v + q * 8 + 4, b4[1], y + 4);
+                uint4 o;
+                o.x = pack_bf16_relu(y[0], y[1]);
+                o.y = pack_bf16_relu(y[2], y[3]);
+                o.z = pack_bf16_relu(y[4], y[5]);
+                o.w = pack_bf16_relu(y[6], y[7]);
+                *reinterpret_cast<uint4*>(A2 + kmaj_off(row, col + q * 8, kHidden)) = o;
+              }
+            }
+            fence_proxy_async();
+          } else if (half == 0) {
+            float v[16];
+            tmem_ld<16>(taddr, v);
+            const float* b3 = (const float*)(sm + Smem::b3);
+            if (has[u])
+              w.rec_c[qrec[u]] = make_float4(sigmoid_f(v[0] + b3[0]), sigmoid_f(v[1] + b3[1]),
+                                             sigmoid_f(v[2] + b3[2]), wrec[u]);
+          }
+          fence_before();
+          __syncwarp();
+          if (lane == 0) arrive(&bars[kEDone + sl]);
+        }
+      }
+    }
+    if (!ok) *dead = 1;
+  } else if (warp < kEW + kGW) {
+    // ---------------------------------------------------------------- gather warps
+    const int gw = warp - kEW, gg = gw >> 2, row = (gw & 3) * 32 + lane;
+    const int B = g.brick, C = CC ? CC : g.C, in_dim = mlp.in_dim;
+    int bufb[2] = {-1, -1};
+    uint32_t bph[2] = {0u, 0u};
+    bool pend[2] = {false, false};
+    int prev = 1;
+    auto issue = [&](int x, int b) {
+      if (row == 0) {
+        const int bx = b % g.nb[0], by = (b / g.nb[0]) % g.nb[1], bz = b / (g.nb[0] * g.nb[1]);
+        mbar_expect_tx(&bars[kBrick + 2 * gg + x], (uint32_t)box_bytes);
+        tma_load_3d(sm + L.tiles + (2 * gg + x) * L.box, &fmap, bx * B * C, by * B, bz * B, &bars[kBrick + 2 * gg + x]);
+      }
+      bufb[x] = b;
+      pend[x] = true;
+    };
+    for (int t = gg; t < n; t += 2) {
+      if (!gsync_and(gg, !*dead)) break;
+      const uint32_t ti = t_begin + t;
+      const int b = (int)w.tile_brick[ti];
+      const uint32_t start = w.tile_start[ti];
+      const int mcnt = (int)(min(start + (uint32_t)kTile, w.brick_off[b + 1]) - start);
+      int x = bufb[0] == b ? 0 : (bufb[1] == b ? 1 : -1);
+      if (x < 0) {
+        x = prev ^ 1;
+        gsync(gg);  // nobody still reads the buffer being replaced
+        issue(x, b);
+      }
+      uint32_t sid = 0;
+      float4 pw = make_float4(0.f, 0.f, 0.f, 0.f), dir = make_float4(0.f, 0.f, 1.f, 0.f);
+      if (row < mcnt) {
+        const uint2 rq = w.srt_rq[start + row];
+        sid = rq.y;
+        pw = w.srt_pw[start + row];
+        dir = w.ray_dir[rq.x];
+      }
+      (void)sid;
+      if (pend[x]) {
+        const bool okb = gsync_and(gg, mbar_wait(&bars[kBrick + 2 * gg + x], bph[x], err));
+        bph[x] ^= 1u;
+        pend[x] = false;
+        if (!okb) {
+          *dead = 1;
+          break;
+        }
+      }
+      const int st = t % ns, us = t / ns;
+      if (us > 0 && !gsync_and(gg, mbar_wait(&bars[kA1Empty + st], (uint32_t)(us - 1) & 1u, err))) {
+        *dead = 1;
+        break;
+      }
+      char* A1 = sm + L.a1 + st * kA1Bytes;
+      const T* tile = (const T*)(sm + L.tiles + (2 * gg + x) * L.box);
+      float xr[kK1];
+#pragma unroll
+      for (int j = 0; j < kK1; j++) xr[j] = 0.0f;
+      if (row < mcnt) {
+        const int bx = b % g.nb[0], by = (b / g.nb[0]) % g.nb[1], bz = b / (g.nb[0] * g.nb[1]);
+        const float pp[3] = {pw.x, pw.y, pw.z};
+        int l[3];
+        float f[3];
+        bool okc = true;
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+          const float ga = __fmul_rn(__fsub_rn(pp[a], g.amin[a]), g.inv_h[a]);
+          int i = (int)floorf(ga);
+          if (i > g.n[a] - 2) i = g.n[a] - 2;
+          f[a] = __fsub_rn(ga, (float)i);
+          l[a] = i - (a == 0 ? bx : a == 1 ? by : bz) * B;
+          okc = okc && l[a] >= 0 && l[a] < B;
+        }
+        if (!okc)
+          set_err(err, kErrInternal);
+        else
+          tri_tile<T, CC>(tile, vb, vx, C, l, f, xr);
+        const float d[3] = {dir.x, dir.y, dir.z};
+        encode_dir_fast<NF>(d, mlp.n_freq, xr + C);
+        if (in_dim < kK1) xr[CC && NF ? (CC + 3 + 6 * NF) % kK1 : in_dim % kK1] = 1.0f;  // folded layer-1 bias
+      }
+#pragma unroll
+      for (int k0 = 0; k0 < kK1; k0 += 8) store_chunk(A1, row, k0, kK1, xr + k0);
+      fence_proxy_async();
+      __syncwarp();
+      if (lane == 0) arrive(&bars[kA1Full + st]);
+      prev = x;
+      if (t + 2 < n) {  // prefetch the brick of this group's next tile
+        const int nb2 = (int)w.tile_brick[ti + 2];
+        if (nb2 != bufb[0] && nb2 != bufb[1]) {
+          gsync(gg);  // the other buffer is no longer read by anyone in the group
+          issue(x ^ 1, nb2);
+        }
+      }
+    }
+    // a prefetched copy that will not be consumed must land before the CTA exits
+    for (int x = 0; x < 2; x++)
+      if (pend[x]) mbar_wait(&bars[kBrick + 2 * gg + x], bph[x], err);
+  } else if (lane == 0) {
+    // ---------------------------------------------------------------- MMA issuer
+    const uint32_t id128 = idesc_bf16(kHidden), id16 = idesc_bf16(kN3);
+    const uint32_t w1a = smem_u32(sm + Smem::w1), w2a = smem_u32(sm + Smem::w2), w3a = smem_u32(sm + Smem::w3);
+    bool ok = true;
+    for (int p = 0; ok && 2 * p < n; p++) {
+      const int np = min(2, n - 2 * p);
+      for (int u = 0; ok && u < np; u++) {
+        const int t = 2 * p + u, sl = t & 1, k = t >> 1, st = t % ns, us = t / ns;
+        ok = mbar_wait(&bars[kA1Full + st], (uint32_t)us & 1u, err) && !*dead;
+        if (ok && k > 0) ok = mbar_wait(&bars[kEDone + sl], (uint32_t)(3 * (k - 1) + 2) & 1u, err) && !*dead;
+        if (!ok) break;
+        fence_after();
+        const uint32_t a = smem_u32(sm + L.a1 + st * kA1Bytes), d = tmem + (uint32_t)(sl * 128);
+#pragma unroll
+        for (int s2 = 0; s2 < kK1 / 16; s2++)
+          mma_bf16(d, smem_desc(a + 256u * s2, 128u, kK1 * 16), smem_desc(w1a + 256u * s2, 128u, kK1 * 16), id128,
+                   s2 > 0 ? 1u : 0u);
+        mma_commit(&bars[kA1Empty + st]);
+        mma_commit(&bars[kDFull + sl]);
+      }
+      for (int lr = 1; ok && lr <= 2; lr++) {
+        for (int u = 0; ok && u < np; u++) {
+          const int t = 2 * p + u, sl = t & 1, k = t >> 1;
+          ok = mbar_wait(&bars[kEDone + sl], (uint32_t)(3 * k + lr - 1) & 1u, err) && !*dead;
+          if (!ok) break;
+          fence_after();
+          const uint32_t a = smem_u32(sm + L.a2 + sl * kActBytes), d = tmem + (uint32_t)(sl * 128);
+          const uint32_t bw = lr == 1 ? w2a : w3a;
+#pragma unroll 1
+          for (int s2 = 0; s2 < kHidden / 16; s2++)
+            mma_bf16(d, smem_desc(a + 256u * s2, 128u, kHidden * 16), smem_desc(bw + 256u * s2, 128u, kHidden * 16),
+                     lr == 1 ? id128 : id16, s2 > 0 ? 1u : 0u);
+          mma_commit(&bars[kDFull + sl]);
+        }
+      }
+    }
+    if (!ok) *dead = 1;
+    // every MMA issued above has completed before TMEM is released
+    uint64_t* fin = (uint64_t*)(sm + L.bars + 144);
+    mma_commit(fin);
+    mbar_wait(fin, 0u, err);
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256) : "memory");
+  }
+}
+
 // The persistent gather + MLP kernel of the BF16 path (launched with 128 * groups threads).
 template <typename T, int CC, int NF>
 __global__ void __launch_bounds__(512, 1) k_gather_mlp_bf16(GridGeo g, int S, MlpPtrs mlp, RenderWs w,
@@ -560,6 +862,20 @@ template <typename T, int CC, int NF>
 static cicero_status launch_tc(const GridGeo& geo, int S, const MlpPtrs& mlp, const RenderWs& ws,
                                const CUtensorMap& map, const BrickBox& box, cudaStream_t st) {
   using namespace tc;
+  for (int ns = 4; ns >= 2; ns -= 2) {
+    const wsp::Layout L = wsp::layout(ns, box.box_bytes);
+    if (L.total > 227 * 1024) continue;
+    auto kern = k_gather_mlp_ws<T, CC, NF>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_gather_mlp_ws)");
+    {
+      ProfScope ps(kStGatherMlp, st);
+      kern<<<num_sms(), wsp::kThreads, L.total, st>>>(geo, mlp, ws, map, box.vb, box.vx, box.box_bytes, ns);
+    }
+    count_launches(1);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? CICERO_OK : cuda_fail(e, "k_gather_mlp_ws");
+  }
   int groups = kMaxGroups;
   while (groups > 1 && Smem::groups + groups * group_bytes(box.box_bytes) > 227 * 1024) groups--;
   int smem = Smem::groups + groups * group_bytes(box.box_bytes);
