@@ -26,17 +26,18 @@ namespace cicero {
 
 namespace tc {
 
-constexpr int kK1 = kMaxIn;            // 48: layer-1 K (input padded)
+constexpr int kK1 = kMaxIn;            // 48: layer-1 K (input padded; column in_dim carries a 1 for b1)
+constexpr int kK2 = kHidden + 16;      // 144: layer-2 K (column 128 carries a 1 for b2)
 constexpr int kN3 = 16;                // layer-3 N padded to the smallest M=128 MMA width
 constexpr int kGT = 128;               // threads per group
 constexpr int kMaxGroups = 4;
 constexpr uint32_t kTmemCols = 512;    // all of an SM's tensor memory; 128 columns per group
-constexpr int kActBytes = kTile * kHidden * 2;
+constexpr int kActBytes = kTile * kK2 * 2;
 
 struct Smem {
   static constexpr int w1 = 0;                                 // [128][48]  bf16
-  static constexpr int w2 = w1 + kHidden * kK1 * 2;            // [128][128] bf16
-  static constexpr int w3 = w2 + kHidden * kHidden * 2;        // [16][128]  bf16
+  static constexpr int w2 = w1 + kHidden * kK1 * 2;            // [128][144] bf16 (column 128 = b2)
+  static constexpr int w3 = w2 + kHidden * kK2 * 2;            // [16][128]  bf16
   static constexpr int b1 = w3 + kN3 * kHidden * 2;            // [128] f32
   static constexpr int b2 = b1 + kHidden * 4;                  // [128] f32
   static constexpr int b3 = b2 + kHidden * 4;                  // [4] f32
@@ -182,12 +183,15 @@ __device__ void load_weights(char* sm, const MlpPtrs& m) {
     }
     store_chunk(sm + Smem::w1, n, k0, kK1, v);
   }
-  for (int i = threadIdx.x; i < kHidden * (kHidden / 8); i += blockDim.x) {
-    const int n = i / (kHidden / 8), k0 = (i % (kHidden / 8)) * 8;
+  for (int i = threadIdx.x; i < kHidden * (kK2 / 8); i += blockDim.x) {
+    const int n = i / (kK2 / 8), k0 = (i % (kK2 / 8)) * 8;
     float v[8];
 #pragma unroll
-    for (int j = 0; j < 8; j++) v[j] = m.w2[n * kHidden + k0 + j];
-    store_chunk(sm + Smem::w2, n, k0, kHidden, v);
+    for (int j = 0; j < 8; j++) {
+      const int k = k0 + j;
+      v[j] = k < kHidden ? m.w2[n * kHidden + k] : (k == kHidden ? m.b2[n] : 0.0f);  // b2 rides on a 1 column
+    }
+    store_chunk(sm + Smem::w2, n, k0, kK2, v);
   }
   for (int i = threadIdx.x; i < kN3 * (kHidden / 8); i += blockDim.x) {
     const int n = i / (kHidden / 8), k0 = (i % (kHidden / 8)) * 8;
@@ -201,7 +205,7 @@ __device__ void load_weights(char* sm, const MlpPtrs& m) {
   float* b3 = (float*)(sm + Smem::b3);
   for (int i = threadIdx.x; i < kHidden; i += blockDim.x) {
     b1[i] = m.in_dim < kK1 ? 0.0f : m.b1[i];  // folded into W1 unless the input fills all 48 columns
-    b2[i] = m.b2[i];
+    b2[i] = 0.0f;                             // folded into W2 (column 128)
   }
   if (threadIdx.x < 4) b3[threadIdx.x] = threadIdx.x < 3 ? m.b3[threadIdx.x] : 0.0f;
 }
@@ -224,13 +228,14 @@ __device__ __forceinline__ bool run_layer(char* sm, Group& G, int layer, uint32_
     fence_after();
     const uint32_t a_base = smem_u32(G.act);
     const uint32_t b_base = smem_u32(sm + (layer == 0 ? Smem::w1 : layer == 1 ? Smem::w2 : Smem::w3));
-    const int K = layer == 0 ? kK1 : kHidden;
-    const uint32_t sbo = (uint32_t)K * 16;
+    const int steps = layer == 0 ? kK1 / 16 : layer == 1 ? kK2 / 16 : kHidden / 16;
+    const uint32_t sbo_a = (uint32_t)(layer == 0 ? kK1 : kK2) * 16;
+    const uint32_t sbo_b = (uint32_t)(layer == 0 ? kK1 : layer == 1 ? kK2 : kHidden) * 16;
     const uint32_t idesc = idesc_bf16(layer == 2 ? kN3 : kHidden);
 #pragma unroll 1
-    for (int s = 0; s < K / 16; s++) {
-      const uint64_t ad = smem_desc(a_base + 256u * s, 128u, sbo);
-      const uint64_t bd = smem_desc(b_base + 256u * s, 128u, sbo);
+    for (int s = 0; s < steps; s++) {
+      const uint64_t ad = smem_desc(a_base + 256u * s, 128u, sbo_a);
+      const uint64_t bd = smem_desc(b_base + 256u * s, 128u, sbo_b);
       mma_bf16(G.tmem, ad, bd, idesc, s > 0 ? 1u : 0u);
     }
     mma_commit(G.bar_mma);
@@ -241,7 +246,8 @@ __device__ __forceinline__ bool run_layer(char* sm, Group& G, int layer, uint32_
   return ok;
 }
 
-// bias + ReLU of the 128 accumulator columns -> BF16 K-major rows of A (row = this thread)
+// ReLU of the 128 accumulator columns (+ bias when it could not be folded into the MMA) -> BF16
+// K-major rows of A (K = 144: column 128 is the constant 1 that multiplies b2, 129..143 zero).
 __device__ __forceinline__ void epilogue_hidden(const Group& G, const float* bias) {
   const uint32_t taddr = G.tmem + ((uint32_t)((G.m >> 5) * 32) << 16);
 #pragma unroll 1
@@ -250,36 +256,46 @@ __device__ __forceinline__ void epilogue_hidden(const Group& G, const float* bia
     tmem_ld<32>(taddr + cc * 32, v);
 #pragma unroll
     for (int q = 0; q < 4; q++) {
-      const float4* b4 = reinterpret_cast<const float4*>(bias + cc * 32 + q * 8);
+      const float* x = v + q * 8;
       float y[8];
-      add2(v + q * 8, b4[0], y);
-      add2(v + q * 8 + 4, b4[1], y + 4);
+      if (bias) {
+        const float4* b4 = reinterpret_cast<const float4*>(bias + cc * 32 + q * 8);
+        add2(x, b4[0], y);
+        add2(x + 4, b4[1], y + 4);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 8; j++) y[j] = x[j];
+      }
       uint4 o;
       o.x = pack_bf16_relu(y[0], y[1]);
       o.y = pack_bf16_relu(y[2], y[3]);
       o.z = pack_bf16_relu(y[4], y[5]);
       o.w = pack_bf16_relu(y[6], y[7]);
-      *reinterpret_cast<uint4*>(G.act + kmaj_off(G.m, cc * 32 + q * 8, kHidden)) = o;
+      *reinterpret_cast<uint4*>(G.act + kmaj_off(G.m, cc * 32 + q * 8, kK2)) = o;
     }
   }
+  *reinterpret_cast<uint4*>(G.act + kmaj_off(G.m, kHidden, kK2)) = make_uint4(0x3f80u, 0u, 0u, 0u);  // bf16 1.0
+  *reinterpret_cast<uint4*>(G.act + kmaj_off(G.m, kHidden + 8, kK2)) = make_uint4(0u, 0u, 0u, 0u);
   fence_proxy_async();
   fence_before();
 }
 
 // The three layers of a tile whose A (K = 48 layout) has been written and proxy-fenced by every
 // thread of the group.  c receives this thread's colour.  False on timeout.
-__device__ __forceinline__ bool mlp_tile(char* sm, Group& G, uint32_t* err, float c[3]) {
+__device__ __forceinline__ float sigmoid_fast(float z) { return __frcp_rn(1.0f + __expf(-z)); }
+
+__device__ __forceinline__ bool mlp_tile(char* sm, Group& G, uint32_t* err, float c[3], bool folded_b1) {
   if (!run_layer(sm, G, 0, err)) return false;
-  epilogue_hidden(G, (const float*)(sm + Smem::b1));
+  epilogue_hidden(G, folded_b1 ? nullptr : (const float*)(sm + Smem::b1));
   if (!run_layer(sm, G, 1, err)) return false;
-  epilogue_hidden(G, (const float*)(sm + Smem::b2));
+  epilogue_hidden(G, nullptr);
   if (!run_layer(sm, G, 2, err)) return false;
   float v[16];
   tmem_ld<16>(G.tmem + ((uint32_t)((G.m >> 5) * 32) << 16), v);
   const float* b3 = (const float*)(sm + Smem::b3);
-  c[0] = sigmoid_f(v[0] + b3[0]);
-  c[1] = sigmoid_f(v[1] + b3[1]);
-  c[2] = sigmoid_f(v[2] + b3[2]);
+  c[0] = sigmoid_fast(v[0] + b3[0]);
+  c[1] = sigmoid_fast(v[1] + b3[1]);
+  c[2] = sigmoid_fast(v[2] + b3[2]);
   fence_before();
   return true;
 }
@@ -320,17 +336,7 @@ __device__ __forceinline__ void tri_tile(const T* tile, int vb, int vx, int Cr, 
     const float wq = ((q & 1) ? fx : 1.f - fx) * (((q >> 1) & 1) ? fy : 1.f - fy) * ((q >> 2) ? fz : 1.f - fz);
     const T* v = tile + ((size_t)(z * vb + y) * vx + x) * C;
     if constexpr (CC == 12 && sizeof(T) == 2) {
-      const uint2* v2 = reinterpret_cast<const uint2*>(v);
-#pragma unroll
-      for (int u = 0; u < 3; u++) {
-        uint2 a = v2[u];
-        float2 lo = __half22float2(*reinterpret_cast<__half2*>(&a.x));
-        float2 hi = __half22float2(*reinterpret_cast<__half2*>(&a.y));
-        out[4 * u + 0] += wq * lo.x;
-        out[4 * u + 1] += wq * lo.y;
-        out[4 * u + 2] += wq * hi.x;
-        out[4 * u + 3] += wq * hi.y;
-      }
+      continue;  // handled by tri_tile_h2
     } else if constexpr (CC == 12 && sizeof(T) == 4) {
       const float4* v4 = reinterpret_cast<const float4*>(v);
 #pragma unroll
@@ -349,6 +355,36 @@ __device__ __forceinline__ void tri_tile(const T* tile, int vb, int vx, int Cr, 
         out[c] += wq * vv;
       }
     }
+  }
+}
+
+// FP16 grids, 12 channels: the eight corners accumulated in half2 (6 HFMA2 per corner).  The
+// accumulation error (~1e-3 worst case, features |f| <= 1) stays below the BF16 rounding of the
+// MLP input that follows.
+__device__ __forceinline__ void tri_tile_h2(const __half* tile, int vb, int vx, const int l[3], const float f[3],
+                                            float* out) {
+  __half2 acc[6];
+#pragma unroll
+  for (int u = 0; u < 6; u++) acc[u] = __float2half2_rn(0.0f);
+  const float fx = f[0], fy = f[1], fz = f[2];
+#pragma unroll
+  for (int q = 0; q < 8; q++) {
+    const int x = l[0] + (q & 1), y = l[1] + ((q >> 1) & 1), z = l[2] + (q >> 2);
+    const float wq = ((q & 1) ? fx : 1.f - fx) * (((q >> 1) & 1) ? fy : 1.f - fy) * ((q >> 2) ? fz : 1.f - fz);
+    const __half2 w2 = __float2half2_rn(wq);
+    const uint2* v2 = reinterpret_cast<const uint2*>(tile + ((size_t)(z * vb + y) * vx + x) * 12);
+#pragma unroll
+    for (int u = 0; u < 3; u++) {
+      uint2 a = v2[u];
+      acc[2 * u] = __hfma2(w2, *reinterpret_cast<__half2*>(&a.x), acc[2 * u]);
+      acc[2 * u + 1] = __hfma2(w2, *reinterpret_cast<__half2*>(&a.y), acc[2 * u + 1]);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < 6; u++) {
+    const float2 fv = __half22float2(acc[u]);
+    out[2 * u] = fv.x;
+    out[2 * u + 1] = fv.y;
   }
 }
 
@@ -398,308 +434,6 @@ __device__ __forceinline__ Group setup(char* sm, const MlpPtrs& mlp, int groups,
 }
 
 }  // namespace tc
-
-// -------------------------------------------------------------------------------------------
-// Warp-specialized gather + MLP kernel (preferred; the group kernel below is the fallback for
-// bricks too large for its shared-memory plan).  Roles inside one persistent CTA per SM:
-//   warps 0..7   epilogue: warp w reads TMEM lane quarter w % 4, columns 64 * (w / 4) .. +63
-//   warps 8..15  gather: two groups of 4 warps take alternate tiles; each group keeps two TMA
-//                brick buffers and prefetches the brick of its next tile
-//   warp 16      one thread issues every tcgen05.mma and commit
-// A ring of `ns` A-operand stages (12 KB each) decouples gathering from layer 1; two TMEM slots
-// of 128 columns (with two 32 KB activation buffers) let the epilogue warps work on one tile
-// while the tensor cores run the other.  mbarriers:
-//   a1_full[st] (4 gather-warp arrivals) -> MMA; a1_empty[st] (commit of layer 1) -> gather;
-//   d_full[s] (commit of each layer) -> epilogue; e_done[s] (8 epilogue-warp arrivals) -> MMA;
-//   brick[group][buffer] (TMA transaction count) -> gather group.
-// Every wait is bounded; a timeout sets a shared flag that all roles poll, and every decision
-// taken by a gather group is made uniform across it before any named barrier.
-namespace wsp {
-
-constexpr int kEW = 8, kGW = 8, kWarps = kEW + kGW + 1, kThreads = kWarps * 32;
-constexpr int kSlots = 2;
-constexpr int kA1Bytes = kTile * tc::kK1 * 2;
-enum { kA1Full = 0, kA1Empty = 4, kDFull = 8, kEDone = 10, kBrick = 12, kNumBars = 16 };
-
-struct Layout {
-  int bars, a1, a2, tiles, box, total;
-};
-
-__host__ __device__ inline Layout layout(int ns, int box_bytes) {
-  Layout L;
-  L.bars = tc::Smem::bars;  // after the weights and biases
-  L.a1 = L.bars + 256;      // 16 mbarriers, TMEM address at +128, abort flag at +136, final mbarrier at +144
-  L.a2 = L.a1 + ns * kA1Bytes;
-  L.box = tc::align128(box_bytes);
-  L.tiles = L.a2 + kSlots * tc::kActBytes;
-  L.total = L.tiles + 4 * L.box;
-  return L;
-}
-
-__device__ __forceinline__ void arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-}  // namespace wsp
-
-template <typename T, int CC, int NF>
-__global__ void __launch_bounds__(wsp::kThreads, 1) k_gather_mlp_ws(GridGeo g, MlpPtrs mlp, RenderWs w,
-                                                                   const __grid_constant__ CUtensorMap fmap, int vb,
-                                                                   int vx, int box_bytes, int ns) {
-  using namespace tc;
-  using namespace wsp;
-  extern __shared__ __align__(1024) char sm[];
-  const Layout L = layout(ns, box_bytes);
-  uint64_t* bars = (uint64_t*)(sm + L.bars);
-  uint32_t* tslot = (uint32_t*)(sm + L.bars + 128);
-  volatile int* dead = (volatile int*)(sm + L.bars + 136);
-  uint32_t* err = &w.hdr[0];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  load_weights(sm, mlp);
-  if (threadIdx.x == 0) {
-    for (int i = 0; i < ns; i++) {
-      mbar_init(&bars[kA1Full + i], 4);
-      mbar_init(&bars[kA1Empty + i], 1);
-    }
-    for (int i = 0; i < kSlots; i++) {
-      mbar_init(&bars[kDFull + i], 1);
-      mbar_init(&bars[kEDone + i], kEW);
-    }
-    for (int i = 0; i < 4; i++) mbar_init(&bars[kBrick + i], 1);
-    mbar_init((uint64_t*)(sm + L.bars + 144), 1);
-    fence_mbar_init();
-    *dead = 0;
-  }
-  fence_proxy_async();
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
-                 "r"(256)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
-  fence_before();
-  __syncthreads();
-  fence_after();
-  const uint32_t tmem = *tslot;
-  const uint32_t n_tiles = w.hdr[1];
-  const uint32_t per = (n_tiles + gridDim.x - 1) / gridDim.x;
-  const uint32_t t_begin = blockIdx.x * per, t_end = min(n_tiles, t_begin + per);
-  const int n = t_end > t_begin ? (int)(t_end - t_begin) : 0;
-
-  if (warp < kEW) {
-    // ---------------------------------------------------------------- epilogue warps
-    const int q4 = warp & 3, half = warp >> 2, row = q4 * 32 + lane;
-    const uint32_t lane_base = (uint32_t)(q4 * 32) << 16;
-    bool ok = true;
-    for (int p = 0; ok && 2 * p < n; p++) {
-      const int np = min(2, n - 2 * p);
-      uint32_t qrec[2] = {0u, 0u};
-      float wrec[2] = {0.f, 0.f};
-      bool has[2] = {false, false};
-      if (half == 0) {
-        for (int u = 0; u < np; u++) {
-          const uint32_t ti = t_begin + 2 * p + u;
-          const uint32_t start = w.tile_start[ti], b = w.tile_brick[ti];
-          const uint32_t end = min(start + (uint32_t)kTile, w.brick_off[b + 1]);
-          has[u] = (uint32_t)row < end - start;
-          if (has[u]) {
-            qrec[u] = w.srt_rq[start + row].y;
-            wrec[u] = w.srt_pw[start + row].w;
-          }
-        }
-      }
-      for (int lr = 0; ok && lr < 3; lr++) {
-        for (int u = 0; ok && u < np; u++) {
-          const int t = 2 * p + u, sl = t & 1, k = t >> 1;
-          ok = __all_sync(0xffffffffu, mbar_wait(&bars[kDFull + sl], (uint32_t)(3 * k + lr) & 1u, err) && !*dead);
-          if (!ok) break;
-          fence_after();
-          const uint32_t taddr = tmem + (uint32_t)(sl * 128) + lane_base;
-          if (lr < 2) {
-            char* A2 = sm + L.a2 + sl * kActBytes;
-            const float* bias = (const float*)(sm + (lr == 0 ? Smem::b1 : Smem::b2));
-#pragma unroll 1
-            for (int cc = 0; cc < 2; cc++) {
-              const int col = half * 64 + cc * 32;
-              float v[32];
-              tmem_ld<32>(taddr + col, v);
-#pragma unroll
-              for (int q = 0; q < 4; q++) {
-                const float4* b4 = reinterpret_cast<const float4*>(bias + col + q * 8);
-                float y[8];
-                add2(v + q * 8, b4[0], y);
-                add2(v + q * 8 + 4, b4[1], y + 4);
-                uint4 o;
-                o.x = pack_bf16_relu(y[0], y[1]);
-                o.y = pack_bf16_relu(y[2], y[3]);
-                o.z = pack_bf16_relu(y[4], y[5]);
-                o.w = pack_bf16_relu(y[6], y[7]);
-                *reinterpret_cast<uint4*>(A2 + kmaj_off(row, col + q * 8, kHidden)) = o;
-              }
-            }
-            fence_proxy_async();
-          } else if (half == 0) {
-            float v[16];
-            tmem_ld<16>(taddr, v);
-            const float* b3 = (const float*)(sm + Smem::b3);
-            if (has[u])
-              w.rec_c[qrec[u]] = make_float4(sigmoid_f(v[0] + b3[0]), sigmoid_f(v[1] + b3[1]),
-                                             sigmoid_f(v[2] + b3[2]), wrec[u]);
-          }
-          fence_before();
-          __syncwarp();
-          if (lane == 0) arrive(&bars[kEDone + sl]);
-        }
-      }
-    }
-    if (!ok) *dead = 1;
-  } else if (warp < kEW + kGW) {
-    // ---------------------------------------------------------------- gather warps
-    const int gw = warp - kEW, gg = gw >> 2, row = (gw & 3) * 32 + lane;
-    const int B = g.brick, C = CC ? CC : g.C, in_dim = mlp.in_dim;
-    int bufb[2] = {-1, -1};
-    uint32_t bph[2] = {0u, 0u};
-    bool pend[2] = {false, false};
-    int prev = 1;
-    auto issue = [&](int x, int b) {
-      if (row == 0) {
-        const int bx = b % g.nb[0], by = (b / g.nb[0]) % g.nb[1], bz = b / (g.nb[0] * g.nb[1]);
-        mbar_expect_tx(&bars[kBrick + 2 * gg + x], (uint32_t)box_bytes);
-        tma_load_3d(sm + L.tiles + (2 * gg + x) * L.box, &fmap, bx * B * C, by * B, bz * B, &bars[kBrick + 2 * gg + x]);
-      }
-      bufb[x] = b;
-      pend[x] = true;
-    };
-    for (int t = gg; t < n; t += 2) {
-      if (!gsync_and(gg, !*dead)) break;
-      const uint32_t ti = t_begin + t;
-      const int b = (int)w.tile_brick[ti];
-      const uint32_t start = w.tile_start[ti];
-      const int mcnt = (int)(min(start + (uint32_t)kTile, w.brick_off[b + 1]) - start);
-      int x = bufb[0] == b ? 0 : (bufb[1] == b ? 1 : -1);
-      if (x < 0) {
-        x = prev ^ 1;
-        gsync(gg);  // nobody still reads the buffer being replaced
-        issue(x, b);
-      }
-      uint32_t sid = 0;
-      float4 pw = make_float4(0.f, 0.f, 0.f, 0.f), dir = make_float4(0.f, 0.f, 1.f, 0.f);
-      if (row < mcnt) {
-        const uint2 rq = w.srt_rq[start + row];
-        sid = rq.y;
-        pw = w.srt_pw[start + row];
-        dir = w.ray_dir[rq.x];
-      }
-      (void)sid;
-      if (pend[x]) {
-        const bool okb = gsync_and(gg, mbar_wait(&bars[kBrick + 2 * gg + x], bph[x], err));
-        bph[x] ^= 1u;
-        pend[x] = false;
-        if (!okb) {
-          *dead = 1;
-          break;
-        }
-      }
-      const int st = t % ns, us = t / ns;
-      if (us > 0 && !gsync_and(gg, mbar_wait(&bars[kA1Empty + st], (uint32_t)(us - 1) & 1u, err))) {
-        *dead = 1;
-        break;
-      }
-      char* A1 = sm + L.a1 + st * kA1Bytes;
-      const T* tile = (const T*)(sm + L.tiles + (2 * gg + x) * L.box);
-      float xr[kK1];
-#pragma unroll
-      for (int j = 0; j < kK1; j++) xr[j] = 0.0f;
-      if (row < mcnt) {
-        const int bx = b % g.nb[0], by = (b / g.nb[0]) % g.nb[1], bz = b / (g.nb[0] * g.nb[1]);
-        const float pp[3] = {pw.x, pw.y, pw.z};
-        int l[3];
-        float f[3];
-        bool okc = true;
-#pragma unroll
-        for (int a = 0; a < 3; a++) {
-          const float ga = __fmul_rn(__fsub_rn(pp[a], g.amin[a]), g.inv_h[a]);
-          int i = (int)floorf(ga);
-          if (i > g.n[a] - 2) i = g.n[a] - 2;
-          f[a] = __fsub_rn(ga, (float)i);
-          l[a] = i - (a == 0 ? bx : a == 1 ? by : bz) * B;
-          okc = okc && l[a] >= 0 && l[a] < B;
-        }
-        if (!okc)
-          set_err(err, kErrInternal);
-        else
-          tri_tile<T, CC>(tile, vb, vx, C, l, f, xr);
-        const float d[3] = {dir.x, dir.y, dir.z};
-        encode_dir_fast<NF>(d, mlp.n_freq, xr + C);
-        if (in_dim < kK1) xr[CC && NF ? (CC + 3 + 6 * NF) % kK1 : in_dim % kK1] = 1.0f;  // folded layer-1 bias
-      }
-#pragma unroll
-      for (int k0 = 0; k0 < kK1; k0 += 8) store_chunk(A1, row, k0, kK1, xr + k0);
-      fence_proxy_async();
-      __syncwarp();
-      if (lane == 0) arrive(&bars[kA1Full + st]);
-      prev = x;
-      if (t + 2 < n) {  // prefetch the brick of this group's next tile
-        const int nb2 = (int)w.tile_brick[ti + 2];
-        if (nb2 != bufb[0] && nb2 != bufb[1]) {
-          gsync(gg);  // the other buffer is no longer read by anyone in the group
-          issue(x ^ 1, nb2);
-        }
-      }
-    }
-    // a prefetched copy that will not be consumed must land before the CTA exits
-    for (int x = 0; x < 2; x++)
-      if (pend[x]) mbar_wait(&bars[kBrick + 2 * gg + x], bph[x], err);
-  } else if (lane == 0) {
-    // ---------------------------------------------------------------- MMA issuer
-    const uint32_t id128 = idesc_bf16(kHidden), id16 = idesc_bf16(kN3);
-    const uint32_t w1a = smem_u32(sm + Smem::w1), w2a = smem_u32(sm + Smem::w2), w3a = smem_u32(sm + Smem::w3);
-    bool ok = true;
-    for (int p = 0; ok && 2 * p < n; p++) {
-      const int np = min(2, n - 2 * p);
-      for (int u = 0; ok && u < np; u++) {
-        const int t = 2 * p + u, sl = t & 1, k = t >> 1, st = t % ns, us = t / ns;
-        ok = mbar_wait(&bars[kA1Full + st], (uint32_t)us & 1u, err) && !*dead;
-        if (ok && k > 0) ok = mbar_wait(&bars[kEDone + sl], (uint32_t)(3 * (k - 1) + 2) & 1u, err) && !*dead;
-        if (!ok) break;
-        fence_after();
-        const uint32_t a = smem_u32(sm + L.a1 + st * kA1Bytes), d = tmem + (uint32_t)(sl * 128);
-#pragma unroll
-        for (int s2 = 0; s2 < kK1 / 16; s2++)
-          mma_bf16(d, smem_desc(a + 256u * s2, 128u, kK1 * 16), smem_desc(w1a + 256u * s2, 128u, kK1 * 16), id128,
-                   s2 > 0 ? 1u : 0u);
-        mma_commit(&bars[kA1Empty + st]);
-        mma_commit(&bars[kDFull + sl]);
-      }
-      for (int lr = 1; ok && lr <= 2; lr++) {
-        for (int u = 0; ok && u < np; u++) {
-          const int t = 2 * p + u, sl = t & 1, k = t >> 1;
-          ok = mbar_wait(&bars[kEDone + sl], (uint32_t)(3 * k + lr - 1) & 1u, err) && !*dead;
-          if (!ok) break;
-          fence_after();
-          const uint32_t a = smem_u32(sm + L.a2 + sl * kActBytes), d = tmem + (uint32_t)(sl * 128);
-          const uint32_t bw = lr == 1 ? w2a : w3a;
-#pragma unroll 1
-          for (int s2 = 0; s2 < kHidden / 16; s2++)
-            mma_bf16(d, smem_desc(a + 256u * s2, 128u, kHidden * 16), smem_desc(bw + 256u * s2, 128u, kHidden * 16),
-                     lr == 1 ? id128 : id16, s2 > 0 ? 1u : 0u);
-          mma_commit(&bars[kDFull + sl]);
-        }
-      }
-    }
-    if (!ok) *dead = 1;
-    // every MMA issued above has completed before TMEM is released
-    uint64_t* fin = (uint64_t*)(sm + L.bars + 144);
-    mma_commit(fin);
-    mbar_wait(fin, 0u, err);
-  }
-  fence_before();
-  __syncthreads();
-  if (warp == 0) {
-    fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256) : "memory");
-  }
-}
 
 // The persistent gather + MLP kernel of the BF16 path (launched with 128 * groups threads).
 template <typename T, int CC, int NF>
@@ -774,6 +508,8 @@ __global__ void __launch_bounds__(512, 1) k_gather_mlp_bf16(GridGeo g, int S, Ml
       }
       if (!ok)
         set_err(&w.hdr[0], kErrInternal);
+      else if constexpr (CC == 12 && sizeof(T) == 2)
+        tri_tile_h2((const __half*)tile, vb, vx, l, f, x);
       else
         tri_tile<T, CC>(tile, vb, vx, C, l, f, x);
       const float d[3] = {dir.x, dir.y, dir.z};
@@ -809,15 +545,16 @@ __global__ void __launch_bounds__(512, 1) k_gather_mlp_bf16(GridGeo g, int S, Ml
     G.ph_mma ^= 1u;
     fence_after();
     if (!alive) break;
-    epilogue_hidden(G, (const float*)(sm + Smem::b1));
+    epilogue_hidden(G, in_dim < kK1 ? nullptr : (const float*)(sm + Smem::b1));
     if (!(alive = run_layer(sm, G, 1, &w.hdr[0]))) break;
-    epilogue_hidden(G, (const float*)(sm + Smem::b2));
+    epilogue_hidden(G, nullptr);
     if (!(alive = run_layer(sm, G, 2, &w.hdr[0]))) break;
     float v[16];
     tmem_ld<16>(G.tmem + ((uint32_t)((m >> 5) * 32) << 16), v);
     const float* b3 = (const float*)(sm + Smem::b3);
     fence_before();
-    if (m < mcnt) w.rec_c[sid] = make_float4(sigmoid_f(v[0] + b3[0]), sigmoid_f(v[1] + b3[1]), sigmoid_f(v[2] + b3[2]), pw.w);
+    if (m < mcnt)
+      w.rec_c[sid] = make_float4(sigmoid_fast(v[0] + b3[0]), sigmoid_fast(v[1] + b3[1]), sigmoid_fast(v[2] + b3[2]), pw.w);
   }
   if (!alive || pending) {
     // a bounded wait ran out (or a prefetched copy is still landing): wait once more, bounded
@@ -845,7 +582,7 @@ __global__ void __launch_bounds__(512, 1) k_mlp_eval_bf16(MlpPtrs mlp, const flo
     for (int k0 = 0; k0 < kK1; k0 += 8) store_chunk(G.act, G.m, k0, kK1, v + k0);
     fence_proxy_async();
     float cc[3];
-    alive = mlp_tile(sm, G, err, cc);
+    alive = mlp_tile(sm, G, err, cc, mlp.in_dim < kK1);
     if (alive && row < M) {
       c[3 * row + 0] = cc[0];
       c[3 * row + 1] = cc[1];
@@ -862,20 +599,6 @@ template <typename T, int CC, int NF>
 static cicero_status launch_tc(const GridGeo& geo, int S, const MlpPtrs& mlp, const RenderWs& ws,
                                const CUtensorMap& map, const BrickBox& box, cudaStream_t st) {
   using namespace tc;
-  for (int ns = 4; ns >= 2; ns -= 2) {
-    const wsp::Layout L = wsp::layout(ns, box.box_bytes);
-    if (L.total > 227 * 1024) continue;
-    auto kern = k_gather_mlp_ws<T, CC, NF>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_gather_mlp_ws)");
-    {
-      ProfScope ps(kStGatherMlp, st);
-      kern<<<num_sms(), wsp::kThreads, L.total, st>>>(geo, mlp, ws, map, box.vb, box.vx, box.box_bytes, ns);
-    }
-    count_launches(1);
-    e = cudaGetLastError();
-    return e == cudaSuccess ? CICERO_OK : cuda_fail(e, "k_gather_mlp_ws");
-  }
   int groups = kMaxGroups;
   while (groups > 1 && Smem::groups + groups * group_bytes(box.box_bytes) > 227 * 1024) groups--;
   int smem = Smem::groups + groups * group_bytes(box.box_bytes);
