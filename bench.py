@@ -61,8 +61,10 @@ def small_case():
     sd, cd = cc.sampling_from(cam.sampling), cc.camera_from(cam)
     R = n * n
     rgb, depth = torch.empty(R, 3, device="cuda"), torch.empty(R, device="cuda")
-    o16, o32 = cc.options(cc.MLP_BF16, 8), cc.options(cc.MLP_FP32, 8)
-    ws = cc.workspace(cc.cicero_render_workspace_size(grid.desc, R, sd, o16))
+    ws = cc.workspace(cc.cicero_render_workspace_size(grid.desc, R, sd, cc.options(cc.MLP_BF16, 4)))
+    b16, _ = cc.cicero_autotune_brick(grid.desc, mlp.desc, cd, sd, cc.MLP_BF16, rgb, depth, ws)
+    b32, _ = cc.cicero_autotune_brick(grid.desc, mlp.desc, cd, sd, cc.MLP_FP32, rgb, depth, ws)
+    o16, o32 = cc.options(cc.MLP_BF16, b16), cc.options(cc.MLP_FP32, b32)
     for opt in (o16, o16, o32):
         cc.cicero_render(grid.desc, mlp.desc, cd, sd, opt, rgb, depth, None, None, ws)
     wws = cc.workspace(cc.cicero_warp_workspace_size(cd))

@@ -126,6 +126,7 @@ cicero_status make_geo(const cicero_grid* g, int brick, GridGeo* geo) {
   geo->occ = g->occ;
   geo->occ_res = g->occ ? g->occ_res : 0;
   geo->brick = brick;
+  geo->brick_shift = brick == 4 ? 2 : brick == 8 ? 3 : 4;
   const size_t row = (size_t)g->n[0] * g->C * elem_bytes(g->dtype);
   if (((uintptr_t)g->features & 15) || (row & 15))
     return fail(CICERO_ERR_ALIGNMENT, "features must be 16-byte aligned with n0*C*elem a multiple of 16 (TMA)");

@@ -36,7 +36,8 @@ struct GridGeo {
   float act_shift;
   int occ_res;
   const uint8_t* occ;
-  int brick;           // voxels per brick edge
+  int brick;           // voxels per brick edge (a power of two)
+  int brick_shift;     // log2(brick)
   int nb[3];           // bricks per axis
 };
 
@@ -224,8 +225,8 @@ __device__ __forceinline__ bool index_sample(const GridGeo& g, const float p[3],
 }
 
 __device__ __forceinline__ uint32_t brick_id(const GridGeo& g, const int i0[3]) {
-  int B = g.brick;
-  return (uint32_t)(((i0[2] / B) * g.nb[1] + i0[1] / B) * g.nb[0] + i0[0] / B);
+  const int sh = g.brick_shift;
+  return (uint32_t)(((i0[2] >> sh) * g.nb[1] + (i0[1] >> sh)) * g.nb[0] + (i0[0] >> sh));
 }
 
 template <typename T>

@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(256) k_march(GridGeo g, Samp s, RaySrc src, co
         act = index_sample(g, p, i0, f);
       }
       if (!__any_sync(full, act)) {  // nothing to composite in these slots: only the stop test
-        if (s.t_stop > 0.0f && expf(-(Ssum + 0.0f)) < s.t_stop) {
+        if (s.t_stop > 0.0f && __expf(-(Ssum + 0.0f)) < s.t_stop) {
           steps = k0;
           break;
         }
@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(256) k_march(GridGeo g, Samp s, RaySrc src, co
       }
       float excl = __shfl_up_sync(full, incl, 1);
       if (lane == 0) excl = 0.0f;
-      const float Tk = expf(-(Ssum + excl));
+      const float Tk = __expf(-(Ssum + excl));
       const bool stop = valid && s.t_stop > 0.0f && Tk < s.t_stop;
       const unsigned smask = __ballot_sync(full, stop);
       const int first = smask ? __ffs(smask) - 1 : 32;
@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(256) k_march(GridGeo g, Samp s, RaySrc src, co
     if (lane == 0) {
       w.ray_n[r] = cnt;
       w.ray_start[r] = base;
-      w.ray_T[r] = expf(-Ssum);
+      w.ray_T[r] = __expf(-Ssum);
       w.ray_dir[r] = make_float4(d[0], d[1], d[2], 0.0f);
       float* dep = out.depth[rr.view];
       if (dep) dep[rr.pix] = acc >= s.void_acc ? dsum / acc : __int_as_float(0x7f800000);
