@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(256, 1) k_bwd_brick(GridGeo g, RaySrc src, Mlp
         const int r = (int)rq.x;
         float d[3] = {0.0f, 0.0f, 1.0f};
         if (valid) {
-          const float4 dd = w.ray_dir[r];
+          const float4 dd = w.srt_d[start + m];
           d[0] = dd.x;
           d[1] = dd.y;
           d[2] = dd.z;

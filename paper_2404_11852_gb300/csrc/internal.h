@@ -56,6 +56,7 @@ struct RenderWs {
   uint32_t* tile_start; // [max_tiles]
   float4* srt_pw;       // [Q] records' (position, weight) in brick order (the Ray Index Table payload)
   uint2* srt_rq;        // [Q] records' (ray, record index) in brick order
+  float4* srt_d;        // [Q] records' ray direction in brick order
   int R, S, nb, max_tiles;
   uint32_t Q;
 };

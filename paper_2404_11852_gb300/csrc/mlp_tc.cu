@@ -462,10 +462,9 @@ __global__ void __launch_bounds__(512, 1) k_gather_mlp_bf16(GridGeo g, int S, Ml
     nstart = w.tile_start[ti];
     nmcnt = (int)(min(nstart + (uint32_t)kTile, w.brick_off[nb_ + 1]) - nstart);
     if (m < nmcnt) {
-      const uint2 rq = w.srt_rq[nstart + m];
-      nsid = rq.y;
+      nsid = w.srt_rq[nstart + m].y;
       npw = w.srt_pw[nstart + m];
-      ndir = w.ray_dir[rq.x];
+      ndir = w.srt_d[nstart + m];
     }
   };
   if (t_begin < t_end) fetch(t_begin);

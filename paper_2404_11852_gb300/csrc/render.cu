@@ -32,7 +32,7 @@ size_t render_ws_bytes(const RenderPlan& p) {
   b += 2 * al256(4 * (size_t)p.nb) + 2 * al256(4 * ((size_t)p.nb + 1));
   b += al256(8 * ((size_t)p.nb / 4096 + 2));
   b += 2 * al256(4 * (size_t)p.max_tiles);
-  b += al256(16 * Q) + al256(8 * Q);
+  b += 2 * al256(16 * Q) + al256(8 * Q);
   return b;
 }
 
@@ -65,6 +65,7 @@ bool carve_render_ws(void* ws, size_t bytes, const RenderPlan& p, RenderWs* w) {
   w->tile_start = (uint32_t*)take(4 * (size_t)p.max_tiles);
   w->srt_pw = (float4*)take(16 * Q);
   w->srt_rq = (uint2*)take(8 * Q);
+  w->srt_d = (float4*)take(16 * Q);
   w->R = p.R;
   w->S = p.S;
   w->nb = p.nb;
@@ -372,6 +373,7 @@ __global__ void __launch_bounds__(256) k_scatter(RaySrc src, RenderWs w) {
   const unsigned le_mask = (2u << lane) - 1u;
   for (int r = warp; r < R; r += nwarps) {
     const uint32_t n = w.ray_n[r], start = w.ray_start[r];
+    const float4 dir = n ? w.ray_dir[r] : make_float4(0.f, 0.f, 0.f, 0.f);
     for (uint32_t j0 = 0; j0 < n; j0 += 32) {
       const uint32_t j = j0 + lane;
       const bool valid = j < n;
@@ -396,6 +398,7 @@ __global__ void __launch_bounds__(256) k_scatter(RaySrc src, RenderWs w) {
         const uint32_t dst = w.brick_off[key] + off + (uint32_t)(lane - hl);
         w.srt_pw[dst] = pw;
         w.srt_rq[dst] = make_uint2((uint32_t)r, q);
+        w.srt_d[dst] = dir;
       }
     }
   }
@@ -624,8 +627,6 @@ __global__ void __launch_bounds__(256, 1) k_gather_mlp_f32(GridGeo g, int S, Mlp
     }
     if (!__syncthreads_and(alive)) break;
     if (m < mcnt) {
-      const uint2 rq = w.srt_rq[start + m];
-      const int r = (int)rq.x;
       if (part == 0) {
         const float4 pw = w.srt_pw[start + m];
         const float p[3] = {pw.x, pw.y, pw.z};
@@ -641,7 +642,7 @@ __global__ void __launch_bounds__(256, 1) k_gather_mlp_f32(GridGeo g, int S, Mlp
           for (int c = 0; c < C; c++) X[c * kTile + m] = feat[c];
         }
       } else {
-        const float4 dd = w.ray_dir[r];
+        const float4 dd = w.srt_d[start + m];
         const float d[3] = {dd.x, dd.y, dd.z};
         float e[3 + 6 * 7];
         encode_dir(d, mlp.n_freq, e);
