@@ -213,16 +213,10 @@ __global__ void __launch_bounds__(256, 1) k_bwd_brick(GridGeo g, RaySrc src, Mlp
       const int m = threadIdx.x & (kBT - 1), part = threadIdx.x >> 6;
       if (part < 2) {
         const bool valid = m < mcnt;
-        const uint2 rq = valid ? w.srt_rq[start + m] : make_uint2(0u, 0u);
-        const uint32_t sid = rq.y;
-        const int r = (int)rq.x;
-        float d[3] = {0.0f, 0.0f, 1.0f};
-        if (valid) {
-          const float4 dd = w.srt_d[start + m];
-          d[0] = dd.x;
-          d[1] = dd.y;
-          d[2] = dd.z;
-        }
+        const float4 qd = valid ? w.srt_qd[start + m] : make_float4(0.f, 0.f, 0.f, 1.f);
+        const uint32_t sid = __float_as_uint(qd.x);
+        const int r = valid ? (int)w.rec_ray[sid] : 0;
+        const float d[3] = {qd.y, qd.z, qd.w};
         if (part == 0) {
           int ok = 0;
           if (valid) {

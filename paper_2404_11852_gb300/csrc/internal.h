@@ -55,8 +55,8 @@ struct RenderWs {
   uint32_t* tile_brick; // [max_tiles]
   uint32_t* tile_start; // [max_tiles]
   float4* srt_pw;       // [Q] records' (position, weight) in brick order (the Ray Index Table payload)
-  uint2* srt_rq;        // [Q] records' (ray, record index) in brick order
-  float4* srt_d;        // [Q] records' ray direction in brick order
+  float4* srt_qd;       // [Q] records' (record index as bits, ray direction) in brick order
+  uint32_t* rec_ray;    // [Q] ray of each record (backward and RIT export only; may be null)
   int R, S, nb, max_tiles;
   uint32_t Q;
 };

@@ -456,15 +456,15 @@ __global__ void __launch_bounds__(512, 1) k_gather_mlp_bf16(GridGeo g, int S, Ml
   // records of the tile being gathered, loaded one tile ahead
   int nb_ = 0, nmcnt = 0;
   uint32_t nstart = 0, nsid = 0;
-  float4 npw = make_float4(0.f, 0.f, 0.f, 0.f), ndir = make_float4(0.f, 0.f, 1.f, 0.f);
+  float4 npw = make_float4(0.f, 0.f, 0.f, 0.f), ndir = make_float4(0.f, 0.f, 0.f, 1.f);
   auto fetch = [&](uint32_t ti) {
     nb_ = (int)w.tile_brick[ti];
     nstart = w.tile_start[ti];
     nmcnt = (int)(min(nstart + (uint32_t)kTile, w.brick_off[nb_ + 1]) - nstart);
     if (m < nmcnt) {
-      nsid = w.srt_rq[nstart + m].y;
       npw = w.srt_pw[nstart + m];
-      ndir = w.srt_d[nstart + m];
+      ndir = w.srt_qd[nstart + m];
+      nsid = __float_as_uint(ndir.x);
     }
   };
   if (t_begin < t_end) fetch(t_begin);
@@ -511,7 +511,7 @@ __global__ void __launch_bounds__(512, 1) k_gather_mlp_bf16(GridGeo g, int S, Ml
         tri_tile_h2((const __half*)tile, vb, vx, l, f, x);
       else
         tri_tile<T, CC>(tile, vb, vx, C, l, f, x);
-      const float d[3] = {dir.x, dir.y, dir.z};
+      const float d[3] = {dir.y, dir.z, dir.w};
       encode_dir_fast<NF>(d, mlp.n_freq, x + C);
       if (in_dim < kK1) x[CC && NF ? (CC + 3 + 6 * NF) % kK1 : in_dim % kK1] = 1.0f;  // folded layer-1 bias
     }

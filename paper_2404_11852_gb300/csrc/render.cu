@@ -29,10 +29,11 @@ size_t render_ws_bytes(const RenderPlan& p) {
   b += al256(4 * Q) + 2 * al256(16 * Q);
   if (p.want_k) b += al256(2 * Q);
   if (p.want_bwd) b += 2 * al256(4 * Q);
+  if (p.want_k || p.want_bwd) b += al256(4 * Q);
   b += 2 * al256(4 * (size_t)p.nb) + 2 * al256(4 * ((size_t)p.nb + 1));
   b += al256(8 * ((size_t)p.nb / 4096 + 2));
   b += 2 * al256(4 * (size_t)p.max_tiles);
-  b += 2 * al256(16 * Q) + al256(8 * Q);
+  b += 2 * al256(16 * Q);
   return b;
 }
 
@@ -56,6 +57,7 @@ bool carve_render_ws(void* ws, size_t bytes, const RenderPlan& p, RenderWs* w) {
   w->rec_k = p.want_k ? (uint16_t*)take(2 * Q) : nullptr;
   w->rec_T = p.want_bwd ? (float*)take(4 * Q) : nullptr;
   w->rec_raw = p.want_bwd ? (float*)take(4 * Q) : nullptr;
+  w->rec_ray = (p.want_k || p.want_bwd) ? (uint32_t*)take(4 * Q) : nullptr;
   w->brick_cnt = (uint32_t*)take(4 * (size_t)p.nb);
   w->brick_cur = (uint32_t*)take(4 * (size_t)p.nb);
   w->brick_off = (uint32_t*)take(4 * ((size_t)p.nb + 1));
@@ -64,8 +66,7 @@ bool carve_render_ws(void* ws, size_t bytes, const RenderPlan& p, RenderWs* w) {
   w->tile_brick = (uint32_t*)take(4 * (size_t)p.max_tiles);
   w->tile_start = (uint32_t*)take(4 * (size_t)p.max_tiles);
   w->srt_pw = (float4*)take(16 * Q);
-  w->srt_rq = (uint2*)take(8 * Q);
-  w->srt_d = (float4*)take(16 * Q);
+  w->srt_qd = (float4*)take(16 * Q);
   w->R = p.R;
   w->S = p.S;
   w->nb = p.nb;
@@ -187,6 +188,7 @@ __global__ void __launch_bounds__(256) k_march(GridGeo g, Samp s, RaySrc src, co
         w.rec_pw[q] = make_float4(p[0], p[1], p[2], wk);
         w.rec_key[q] = key;
         if (w.rec_k) w.rec_k[q] = (uint16_t)k;
+        if (w.rec_ray) w.rec_ray[q] = (uint32_t)r;
         if (w.rec_T) {
           w.rec_T[q] = Tk;
           w.rec_raw[q] = raw;
@@ -397,8 +399,7 @@ __global__ void __launch_bounds__(256) k_scatter(RaySrc src, RenderWs w) {
       if (valid) {
         const uint32_t dst = w.brick_off[key] + off + (uint32_t)(lane - hl);
         w.srt_pw[dst] = pw;
-        w.srt_rq[dst] = make_uint2((uint32_t)r, q);
-        w.srt_d[dst] = dir;
+        w.srt_qd[dst] = make_float4(__uint_as_float(q), dir.x, dir.y, dir.z);
       }
     }
   }
@@ -642,8 +643,8 @@ __global__ void __launch_bounds__(256, 1) k_gather_mlp_f32(GridGeo g, int S, Mlp
           for (int c = 0; c < C; c++) X[c * kTile + m] = feat[c];
         }
       } else {
-        const float4 dd = w.srt_d[start + m];
-        const float d[3] = {dd.x, dd.y, dd.z};
+        const float4 dd = w.srt_qd[start + m];
+        const float d[3] = {dd.y, dd.z, dd.w};
         float e[3 + 6 * 7];
         encode_dir(d, mlp.n_freq, e);
         const int ne = 3 + 6 * mlp.n_freq;
@@ -660,7 +661,7 @@ __global__ void __launch_bounds__(256, 1) k_gather_mlp_f32(GridGeo g, int S, Mlp
     float c[3];
     mlp_f32_tile(sm, c);
     if (threadIdx.x < kTile && m < mcnt)
-      w.rec_c[w.srt_rq[start + m].y] = make_float4(c[0], c[1], c[2], w.srt_pw[start + m].w);
+      w.rec_c[__float_as_uint(w.srt_qd[start + m].x)] = make_float4(c[0], c[1], c[2], w.srt_pw[start + m].w);
   }
 }
 
@@ -699,8 +700,8 @@ __global__ void k_rit_export(RenderWs w, int n_bricks, int32_t* offs, int32_t* s
   const size_t i0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x, st = (size_t)gridDim.x * blockDim.x;
   for (size_t i = i0; i <= (size_t)n_bricks; i += st) offs[i] = (int32_t)w.brick_off[i];
   for (size_t i = i0; i < total; i += st) {
-    const uint2 rq = w.srt_rq[i];
-    samples[i] = (int32_t)(rq.x * (uint32_t)w.S + w.rec_k[rq.y]);
+    const uint32_t q = __float_as_uint(w.srt_qd[i].x);
+    samples[i] = (int32_t)(w.rec_ray[q] * (uint32_t)w.S + w.rec_k[q]);
   }
 }
 
