@@ -251,10 +251,14 @@ size_t cicero_backward_workspace_size(const cicero_grid *grid, int n_rays, const
  * by brick of opt->brick^3 voxels, brick id (bz * nby + by) * nbx + bx with nb = ceil((n-1)/brick).
  * brick_offsets [n_bricks + 1]: samples of brick b are samples[brick_offsets[b] .. brick_offsets[b+1]).
  * samples [H*W*n_samples]: sample id = ray * n_samples + slot.  The order inside one brick is
- * not specified.  n_bricks is returned through *n_bricks_out (host). */
+ * not specified.  n_bricks is returned through *n_bricks_out (host).  Size the workspace with
+ * cicero_build_rit_workspace_size. */
 cicero_status cicero_build_rit(const cicero_grid *grid, const cicero_camera *cam, const cicero_sampling *sampling,
                                const cicero_options *opt, int32_t *brick_offsets, int32_t *samples,
                                int *n_bricks_out, void *workspace, size_t ws_bytes, void *stream);
+
+size_t cicero_build_rit_workspace_size(const cicero_grid *grid, const cicero_camera *cam,
+                                       const cicero_sampling *sampling, const cicero_options *opt);
 
 /* Feature Computation alone: c [M][3] = MLP(x [M][in_dim]) in the chosen precision. */
 cicero_status cicero_mlp_eval(const cicero_mlp *mlp, const float *x, int M, cicero_precision precision,

@@ -65,6 +65,7 @@ _SIGS = {
     "cicero_render_backward": ([_P] * 4 + [C.c_int] + [_P] * 6 + [_Z, _P], C.c_int),
     "cicero_backward_workspace_size": ([_P, C.c_int, _P], _Z),
     "cicero_build_rit": ([_P] * 8 + [_Z, _P], C.c_int),
+    "cicero_build_rit_workspace_size": ([_P] * 4, _Z),
     "cicero_mlp_eval": ([_P, _P, C.c_int, C.c_int, _P, _P, _Z, _P], C.c_int),
     "cicero_mlp_eval_workspace_size": ([C.c_int], _Z),
     "cicero_workspace_status": ([_P, _P], C.c_int),
@@ -299,6 +300,10 @@ def cicero_autotune_brick(grid: Grid, mlp: Mlp, cam: Camera, samp: Sampling, pre
     _check(lib().cicero_autotune_brick(C.byref(grid), C.byref(mlp), C.byref(cam), C.byref(samp), int(precision),
                                        _ptr(rgb), _ptr(depth), p, n, _stream(stream), C.byref(best), ms))
     return int(best.value), {b: float(ms[i]) for i, b in enumerate((4, 8, 16))}
+
+
+def cicero_build_rit_workspace_size(grid: Grid, cam: Camera, samp: Sampling, opt: Options | None = None) -> int:
+    return int(lib().cicero_build_rit_workspace_size(C.byref(grid), C.byref(cam), C.byref(samp), _ref(opt)))
 
 
 def cicero_mlp_eval(mlp: Mlp, x, precision: int, c, ws, stream=None):

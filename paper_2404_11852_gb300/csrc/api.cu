@@ -407,6 +407,15 @@ size_t cicero_render_workspace_size(const cicero_grid* grid, int n_rays, const c
   return render_ws_bytes(plan);
 }
 
+size_t cicero_build_rit_workspace_size(const cicero_grid* grid, const cicero_camera* cam,
+                                       const cicero_sampling* sampling, const cicero_options* opt) {
+  if (!cam) return 0;
+  RenderPlan plan;
+  if (plan_render(grid, nullptr, cam->width * cam->height, sampling, opt, &plan, false) != CICERO_OK) return 0;
+  plan.want_k = true;
+  return render_ws_bytes(plan);
+}
+
 cicero_status cicero_build_rit(const cicero_grid* grid, const cicero_camera* cam, const cicero_sampling* sampling,
                                const cicero_options* opt, int32_t* brick_offsets, int32_t* samples, int* n_bricks_out,
                                void* workspace, size_t ws_bytes, void* stream) {

@@ -148,7 +148,7 @@ def test_ray_index_table_bit_exact(cc, orc, small, occ_scene, which, brick):
     nb = int(np.prod([(n - 2) // brick + 1 for n in g.n]))
     offs = torch.empty(nb + 1, dtype=torch.int32, device="cuda")
     samples = torch.empty(R * S, dtype=torch.int32, device="cuda")
-    ws = cc.workspace(cc.cicero_render_workspace_size(gd.desc, R, sd, opt) + 2 * R * S + 256)
+    ws = cc.workspace(cc.cicero_build_rit_workspace_size(gd.desc, cd, sd, opt))
     n_b = cc.cicero_build_rit(gd.desc, cd, sd, opt, offs, samples, ws)
     cc.cicero_workspace_status(ws)
     assert n_b == nb
