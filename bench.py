@@ -237,11 +237,14 @@ def main():
     trgb_l = [t_rgb[i] for i in range(N_TARGETS)]
     tdep_l = [t_depth[i] for i in range(N_TARGETS)]
 
+    ws_wb = cc.workspace(cc.cicero_warp_batch_workspace_size(tds), dev)
+    mask_l = [mask[i] for i in range(N_TARGETS)]
+    nh_flat = nh.view(-1)
+
     def step():
         cc.cicero_render(grid.desc, mlp.desc, cd, sd, o16, ref_rgb, ref_depth, None, None, ws_r)
-        for i, td in enumerate(tds):
-            cc.cicero_warp(ref_rgb, ref_depth, cd, td, 180.0, grid.desc, sd, t_rgb[i], t_depth[i], mask[i], hidx[i],
-                           nh[i], ws_w)
+        cc.cicero_warp_batch(ref_rgb, ref_depth, cd, tds, 180.0, grid.desc, sd, trgb_l, tdep_l, mask_l, hidx_l, nh_flat,
+                             ws_wb)
         cc.cicero_render_holes_batch(grid.desc, mlp.desc, tds, sd, ob, hidx_l, nh, N_TARGETS * R, trgb_l, tdep_l,
                                      ws_h)
 

@@ -206,6 +206,19 @@ cicero_status cicero_warp(const float *ref_rgb, const float *ref_depth,
 
 size_t cicero_warp_workspace_size(const cicero_camera *tgt_cam);
 
+/* cicero_warp from one reference into n_views targets in one set of launches (the targets of a
+ * SpaRW window, Sec. III-C).  tgt_cams [n_views] (host); warped_rgb, warped_depth (may be NULL, or
+ * have NULL entries), hole_mask, hole_idx: host arrays of n_views device pointers; n_holes: DEVICE
+ * array [n_views].  1 <= n_views <= 32.  Results are identical to n_views cicero_warp calls. */
+cicero_status cicero_warp_batch(const float *ref_rgb, const float *ref_depth, const cicero_camera *ref_cam,
+                                const cicero_camera *tgt_cams, int n_views, float max_angle_deg,
+                                const cicero_grid *void_grid, const cicero_sampling *void_sampling,
+                                float *const *warped_rgb, float *const *warped_depth, uint8_t *const *hole_mask,
+                                int32_t *const *hole_idx, int32_t *n_holes,
+                                void *workspace, size_t ws_bytes, void *stream);
+
+size_t cicero_warp_batch_workspace_size(const cicero_camera *tgt_cams, int n_views);
+
 /* cicero_warp without a workspace, for callers that cannot allocate device memory (for example
  * code that runs while a stream is captured into a CUDA graph, where cudaMalloc is not allowed,
  * or real-time loops that must not enter an allocator).  The paper has no counterpart: this is a

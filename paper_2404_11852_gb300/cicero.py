@@ -61,6 +61,8 @@ _SIGS = {
     "cicero_render_holes_batch": ([_P, _P, _P, C.c_int, _P, _P, _P, _P, C.c_int, _P, _P, _P, _Z, _P], C.c_int),
     "cicero_warp": ([_P] * 4 + [C.c_float] + [_P] * 8 + [_Z, _P], C.c_int),
     "cicero_warp_workspace_size": ([_P], _Z),
+    "cicero_warp_batch": ([_P] * 3 + [_P, C.c_int, C.c_float] + [_P] * 7 + [_P, _Z, _P], C.c_int),
+    "cicero_warp_batch_workspace_size": ([_P, C.c_int], _Z),
     "cicero_warp_noalloc": ([_P] * 4 + [C.c_float] + [_P] * 8, C.c_int),
     "cicero_render_backward": ([_P] * 4 + [C.c_int] + [_P] * 6 + [_Z, _P], C.c_int),
     "cicero_backward_workspace_size": ([_P, C.c_int, _P], _Z),
@@ -264,6 +266,27 @@ def cicero_warp_noalloc(ref_rgb, ref_depth, ref_cam: Camera, tgt_cam: Camera, ma
                                      float(max_angle_deg), _ref(void_grid), _ref(void_samp), _ptr(warped_rgb),
                                      _ptr(warped_depth), _ptr(hole_mask), _ptr(hole_idx), _ptr(n_holes),
                                      _stream(stream)))
+
+
+def cicero_warp_batch(ref_rgb, ref_depth, ref_cam: Camera, tgt_cams, max_angle_deg: float, void_grid: Grid | None,
+                      void_samp: Sampling | None, warped_rgb, warped_depth, hole_mask, hole_idx, n_holes, ws,
+                      stream=None):
+    """tgt_cams: list of Camera; warped_* / hole_*: lists of CUDA tensors (warped_depth may be None);
+    n_holes: one int32 CUDA tensor with len(tgt_cams) entries."""
+    V = len(tgt_cams)
+    P = C.c_void_p * V
+    arr = lambda ts: P(*[(t.data_ptr() if t is not None else None) for t in ts])
+    p, n = _ws(ws)
+    assert n_holes.is_cuda and n_holes.is_contiguous() and n_holes.numel() == V
+    _check(lib().cicero_warp_batch(_ptr(ref_rgb), _ptr(ref_depth), C.byref(ref_cam), (Camera * V)(*tgt_cams), V,
+                                   float(max_angle_deg), _ref(void_grid), _ref(void_samp), arr(warped_rgb),
+                                   arr(warped_depth) if warped_depth is not None else None, arr(hole_mask),
+                                   arr(hole_idx), _ptr(n_holes), p, n, _stream(stream)))
+
+
+def cicero_warp_batch_workspace_size(tgt_cams) -> int:
+    V = len(tgt_cams)
+    return int(lib().cicero_warp_batch_workspace_size((Camera * V)(*tgt_cams), V))
 
 
 def cicero_warp_workspace_size(tgt_cam: Camera) -> int:

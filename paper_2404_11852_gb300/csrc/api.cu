@@ -317,6 +317,74 @@ static void relative_pose(const cicero_camera* ref, const cicero_camera* tgt, fl
   }
 }
 
+static cicero_status warp_common(const float* ref_rgb, const float* ref_depth, const cicero_camera* ref_cam,
+                                 const cicero_camera* tgt_cams, int n_views, float max_angle_deg,
+                                 const cicero_grid* void_grid, const cicero_sampling* void_sampling,
+                                 float* const* warped_rgb, float* const* warped_depth, uint8_t* const* hole_mask,
+                                 int32_t* const* hole_idx, int32_t* n_holes, void* workspace, size_t ws_bytes,
+                                 void* stream) {
+  cicero_status st = check_cam(ref_cam);
+  if (st != CICERO_OK) return st;
+  if (n_views < 1 || n_views > kMaxWarpViews) return fail(CICERO_ERR_INVALID_ARG, "n_views must be 1..32");
+  if (!ref_rgb || !ref_depth || !tgt_cams || !warped_rgb || !hole_mask || !hole_idx || !n_holes)
+    return fail(CICERO_ERR_INVALID_ARG, "a warp buffer is NULL");
+  if (!ws_ok(workspace)) return fail(CICERO_ERR_INVALID_ARG, "workspace must be non-NULL and 256-byte aligned");
+  if (!(max_angle_deg > 0.0f)) return fail(CICERO_ERR_INVALID_ARG, "max_angle_deg must be > 0");
+  static thread_local WarpBatch B;
+  memset(&B, 0, sizeof B);
+  B.n_views = n_views;
+  int wt[kMaxWarpViews], ht[kMaxWarpViews];
+  VoidTest vt;
+  memset(&vt, 0, sizeof vt);
+  for (int v = 0; v < n_views; v++) {
+    const cicero_camera* tgt = &tgt_cams[v];
+    st = check_cam(tgt);
+    if (st != CICERO_OK) return st;
+    if (!warped_rgb[v] || !hole_mask[v] || !hole_idx[v]) return fail(CICERO_ERR_INVALID_ARG, "a warp output is NULL");
+    WarpArgs& a = B.v[v].a;
+    a.wr = ref_cam->width;
+    a.hr = ref_cam->height;
+    a.fr = ref_cam->f;
+    a.cxr = ref_cam->cx;
+    a.cyr = ref_cam->cy;
+    a.wt = tgt->width;
+    a.ht = tgt->height;
+    a.ft = tgt->f;
+    a.cxt = tgt->cx;
+    a.cyt = tgt->cy;
+    relative_pose(ref_cam, tgt, a.R, a.t);
+    a.use_phi = max_angle_deg < 180.0f;
+    a.cos_phi = a.use_phi ? (float)cos((double)max_angle_deg * 3.14159265358979323846 / 180.0) : -1.0f;
+    B.v[v].wrgb = warped_rgb[v];
+    B.v[v].wdepth = warped_depth ? warped_depth[v] : nullptr;
+    B.v[v].mask = hole_mask[v];
+    B.v[v].hole_idx = hole_idx[v];
+    B.v[v].n_holes = n_holes + v;
+    wt[v] = tgt->width;
+    ht[v] = tgt->height;
+    vt.src.cam[v] = view_of(tgt);
+  }
+  if (ws_bytes < warp_batch_ws_bytes(wt, ht, n_views)) return fail(CICERO_ERR_WORKSPACE_TOO_SMALL, "workspace too small");
+  carve_warp_ws(B, workspace);
+  if (void_grid) {
+    if (!void_sampling) return fail(CICERO_ERR_INVALID_ARG, "void_sampling is NULL");
+    // the void test needs only the box, the occupancy mask and the sampling; features are unused
+    cicero_grid gg = *void_grid;
+    if (!gg.density) gg.density = (const void*)16;
+    if (!gg.features) gg.features = (const void*)16;
+    st = make_geo(&gg, 8, &vt.g);
+    if (st != CICERO_OK) return st;
+    st = make_samp(void_sampling, &vt.s);
+    if (st != CICERO_OK) return st;
+    vt.enabled = 1;
+    vt.src.kind = 0;
+    vt.src.n_views = n_views;
+  } else if (void_sampling) {
+    make_samp(void_sampling, &vt.s);
+  }
+  return run_warp(B, vt, ref_rgb, ref_depth, (cudaStream_t)stream);
+}
+
 }  // namespace cicero
 
 using namespace cicero;
@@ -486,50 +554,30 @@ cicero_status cicero_warp(const float* ref_rgb, const float* ref_depth, const ci
                           const cicero_sampling* void_sampling, float* warped_rgb, float* warped_depth,
                           uint8_t* hole_mask, int32_t* hole_idx, int32_t* n_holes, void* workspace, size_t ws_bytes,
                           void* stream) {
-  cicero_status st = check_cam(ref_cam);
-  if (st != CICERO_OK) return st;
-  st = check_cam(tgt_cam);
-  if (st != CICERO_OK) return st;
-  if (!ref_rgb || !ref_depth || !warped_rgb || !hole_mask || !hole_idx || !n_holes)
-    return fail(CICERO_ERR_INVALID_ARG, "a warp buffer is NULL");
-  if (!ws_ok(workspace)) return fail(CICERO_ERR_INVALID_ARG, "workspace must be non-NULL and 256-byte aligned");
-  if (ws_bytes < warp_ws_bytes(tgt_cam->width, tgt_cam->height))
-    return fail(CICERO_ERR_WORKSPACE_TOO_SMALL, "workspace too small");
-  if (!(max_angle_deg > 0.0f)) return fail(CICERO_ERR_INVALID_ARG, "max_angle_deg must be > 0");
-  WarpArgs a;
-  memset(&a, 0, sizeof a);
-  a.wr = ref_cam->width;
-  a.hr = ref_cam->height;
-  a.fr = ref_cam->f;
-  a.cxr = ref_cam->cx;
-  a.cyr = ref_cam->cy;
-  a.wt = tgt_cam->width;
-  a.ht = tgt_cam->height;
-  a.ft = tgt_cam->f;
-  a.cxt = tgt_cam->cx;
-  a.cyt = tgt_cam->cy;
-  relative_pose(ref_cam, tgt_cam, a.R, a.t);
-  a.use_phi = max_angle_deg < 180.0f;
-  a.cos_phi = a.use_phi ? (float)cos((double)max_angle_deg * 3.14159265358979323846 / 180.0) : -1.0f;
-  VoidTest vt;
-  memset(&vt, 0, sizeof vt);
-  if (void_grid) {
-    if (!void_sampling) return fail(CICERO_ERR_INVALID_ARG, "void_sampling is NULL");
-    // the void test needs only the box, the occupancy mask and the sampling; features are unused
-    cicero_grid gg = *void_grid;
-    if (!gg.density) gg.density = (const void*)16;
-    if (!gg.features) gg.features = (const void*)16;
-    st = make_geo(&gg, 8, &vt.g);
-    if (st != CICERO_OK) return st;
-    st = make_samp(void_sampling, &vt.s);
-    if (st != CICERO_OK) return st;
-    vt.enabled = 1;
-    vt.src = camera_src(tgt_cam);
-  } else if (void_sampling) {
-    make_samp(void_sampling, &vt.s);
+  if (!tgt_cam) return fail(CICERO_ERR_INVALID_ARG, "tgt_cam is NULL");
+  return warp_common(ref_rgb, ref_depth, ref_cam, tgt_cam, 1, max_angle_deg, void_grid, void_sampling, &warped_rgb,
+                     &warped_depth, &hole_mask, &hole_idx, n_holes, workspace, ws_bytes, stream);
+}
+
+cicero_status cicero_warp_batch(const float* ref_rgb, const float* ref_depth, const cicero_camera* ref_cam,
+                                const cicero_camera* tgt_cams, int n_views, float max_angle_deg,
+                                const cicero_grid* void_grid, const cicero_sampling* void_sampling,
+                                float* const* warped_rgb, float* const* warped_depth, uint8_t* const* hole_mask,
+                                int32_t* const* hole_idx, int32_t* n_holes, void* workspace, size_t ws_bytes,
+                                void* stream) {
+  return warp_common(ref_rgb, ref_depth, ref_cam, tgt_cams, n_views, max_angle_deg, void_grid, void_sampling,
+                     warped_rgb, warped_depth, hole_mask, hole_idx, n_holes, workspace, ws_bytes, stream);
+}
+
+size_t cicero_warp_batch_workspace_size(const cicero_camera* tgt_cams, int n_views) {
+  if (!tgt_cams || n_views < 1 || n_views > kMaxWarpViews) return 0;
+  int wt[kMaxWarpViews], ht[kMaxWarpViews];
+  for (int v = 0; v < n_views; v++) {
+    if (tgt_cams[v].width < 1 || tgt_cams[v].height < 1) return 0;
+    wt[v] = tgt_cams[v].width;
+    ht[v] = tgt_cams[v].height;
   }
-  return run_warp(a, vt, ref_rgb, ref_depth, warped_rgb, warped_depth, hole_mask, hole_idx, n_holes, workspace,
-                  (cudaStream_t)stream);
+  return warp_batch_ws_bytes(wt, ht, n_views);
 }
 
 size_t cicero_warp_workspace_size(const cicero_camera* tgt_cam) {

@@ -253,6 +253,8 @@ __device__ __forceinline__ float density_trilinear(const GridGeo& g, const T* de
 }
 
 __device__ __forceinline__ float softplus_f(float x) { return x > 20.0f ? x : log1pf(expf(x)); }
+// softplus with the hardware exp/log (relative error ~1e-6; for x < -16 it returns 0 instead of ~e^x)
+__device__ __forceinline__ float softplus_fast(float x) { return x > 15.0f ? x : __logf(1.0f + __expf(x)); }
 __device__ __forceinline__ float sigmoid_f(float x) { return 1.0f / (1.0f + expf(-x)); }
 
 // View-direction encoding: d, then sin/cos(2^k d) by the double-angle recurrence

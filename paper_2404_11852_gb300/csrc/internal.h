@@ -137,9 +137,29 @@ struct VoidTest {
   RaySrc src;  // target camera pixels
 };
 
+constexpr int kMaxWarpViews = kMaxViews;
+
+struct WarpView {
+  WarpArgs a;
+  float* wrgb;
+  float* wdepth;
+  uint8_t* mask;
+  int32_t* hole_idx;
+  int32_t* n_holes;
+  unsigned long long* z;  // depth buffer (workspace)
+  uint32_t* bsum;         // scan block sums (workspace)
+  int nblk;
+};
+
+struct WarpBatch {
+  int n_views;
+  WarpView v[kMaxWarpViews];
+};
+
 size_t warp_ws_bytes(int wt, int ht);
-cicero_status run_warp(const WarpArgs& a, const VoidTest& vt, const float* ref_rgb, const float* ref_depth,
-                       float* wrgb, float* wdepth, uint8_t* mask, int32_t* hole_idx, int32_t* n_holes, void* ws,
+size_t warp_batch_ws_bytes(const int* wt, const int* ht, int n_views);
+void carve_warp_ws(WarpBatch& B, void* ws);
+cicero_status run_warp(const WarpBatch& B, const VoidTest& vt, const float* ref_rgb, const float* ref_depth,
                        cudaStream_t st);
 cicero_status run_backward(const cicero_grid* grid, const MlpPtrs& mlp, const RenderPlan& plan, const RaySrc& src,
                            const RenderWs& ws, const float* d_rgb, float* d_dens, float* d_feat, cudaStream_t st);

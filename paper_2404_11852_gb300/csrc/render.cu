@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(256) k_march(GridGeo g, Samp s, RaySrc src, co
       float sd = 0.0f, raw = 0.0f;
       if (act) {
         raw = density_trilinear(g, dens, i0, f);
-        sd = softplus_f(raw + g.act_shift) * sl.dt;
+        sd = softplus_fast(raw + g.act_shift) * sl.dt;
       }
       float incl = sd;
 #pragma unroll

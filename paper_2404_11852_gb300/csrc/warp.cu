@@ -74,28 +74,34 @@ __device__ __forceinline__ Splat splat_point(const WarpArgs& a, const float* ref
   return s;
 }
 
-__global__ void k_zclear(unsigned long long* z, int n) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) z[i] = ~0ull;
+// Kernels take the whole batch of target views as a __grid_constant__ parameter; blockIdx.y is
+// the view.
+__global__ void k_zclear(const __grid_constant__ WarpBatch B) {
+  const WarpView& V = B.v[blockIdx.y];
+  const int n = V.a.wt * V.a.ht;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) V.z[i] = ~0ull;
 }
 
-__global__ void __launch_bounds__(256) k_splat(WarpArgs a, const float* __restrict__ ref_depth, unsigned long long* z) {
-  const int n = a.wr * a.hr;
+__global__ void __launch_bounds__(256) k_splat(const __grid_constant__ WarpBatch B, const float* __restrict__ ref_depth) {
+  const WarpView& V = B.v[blockIdx.y];
+  const int n = V.a.wr * V.a.hr;
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
-    const Splat s = splat_point(a, ref_depth, q);
+    const Splat s = splat_point(V.a, ref_depth, q);
     if (!s.ok) continue;
     const float zk = s.inf ? __int_as_float(0x7f800000) : s.Z;
     const unsigned long long key = ((unsigned long long)__float_as_uint(zk) << 32) | (unsigned int)q;
-    atomicMin(&z[s.py * a.wt + s.px], key);
+    atomicMin(&V.z[s.py * V.a.wt + s.px], key);
   }
 }
 
-// Void depth test of pixel p by a whole warp: 32 slots per step, stop at the first slot that
-// is inside the box (and in an occupied cell).  Same FP32 slot placement and indexing as rendering.
-__device__ __forceinline__ bool warp_ray_has_sample(const VoidTest& vt, int p) {
+// Void depth test of pixel p of view v by a whole warp: 32 slots per step, stop at the first slot
+// that is inside the box (and in an occupied cell).  Same FP32 slot placement and indexing as
+// rendering.
+__device__ __forceinline__ bool warp_ray_has_sample(const VoidTest& vt, int v, int p) {
   const int lane = threadIdx.x & 31;
   float o[3], d[3];
   RayRef rr;
-  rr.view = 0;
+  rr.view = v;
   rr.pix = p;
   ray_gen(vt.src, rr, o, d);
   const Slots sl = place_slots(vt.g, vt.s, o, d);
@@ -116,65 +122,65 @@ __device__ __forceinline__ bool warp_ray_has_sample(const VoidTest& vt, int p) {
   return false;
 }
 
-// One warp per 32 consecutive target pixels.
-__global__ void __launch_bounds__(256) k_resolve(WarpArgs a, VoidTest vt, const float* __restrict__ ref_rgb,
-                                                 const float* __restrict__ ref_depth, const unsigned long long* z,
-                                                 float* wrgb, float* wdepth, uint8_t* mask) {
-  const int n = a.wt * a.ht;
+// One warp per 32 consecutive target pixels: copy the winners, mark the holes (3 = still to be
+// tested for void when the void test is on, else 1).
+__global__ void __launch_bounds__(256) k_resolve(const __grid_constant__ WarpBatch B, int void_on,
+                                                 const float* __restrict__ ref_rgb, const float* __restrict__ ref_depth) {
+  const WarpView& V = B.v[blockIdx.y];
+  const int n = V.a.wt * V.a.ht;
   const int lane = threadIdx.x & 31;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   for (int p0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; p0 < n; p0 += nwarps * 32) {
     const int p = p0 + lane;
-    const bool px = p < n;
-    const unsigned long long key = px ? z[p] : 0ull;
-    const bool hole = px && key == ~0ull;
-    if (px && !hole) {
+    if (p >= n) continue;
+    const unsigned long long key = V.z[p];
+    if (key != ~0ull) {
       const int q = (int)(key & 0xffffffffull);
-      wrgb[3 * p + 0] = ref_rgb[3 * q + 0];
-      wrgb[3 * p + 1] = ref_rgb[3 * q + 1];
-      wrgb[3 * p + 2] = ref_rgb[3 * q + 2];
-      if (wdepth) {
-        const Splat s = splat_point(a, ref_depth, q);
-        wdepth[p] = s.inf ? __int_as_float(0x7f800000)
-                          : __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(s.X, s.X), __fmul_rn(s.Y, s.Y)), __fmul_rn(s.Z, s.Z)));
+      V.wrgb[3 * p + 0] = ref_rgb[3 * q + 0];
+      V.wrgb[3 * p + 1] = ref_rgb[3 * q + 1];
+      V.wrgb[3 * p + 2] = ref_rgb[3 * q + 2];
+      if (V.wdepth) {
+        const Splat s = splat_point(V.a, ref_depth, q);
+        V.wdepth[p] = s.inf ? __int_as_float(0x7f800000)
+                            : __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(s.X, s.X), __fmul_rn(s.Y, s.Y)), __fmul_rn(s.Z, s.Z)));
       }
-      mask[p] = 0;
-    }
-    if (hole) {
-      wrgb[3 * p + 0] = 0.0f;
-      wrgb[3 * p + 1] = 0.0f;
-      wrgb[3 * p + 2] = 0.0f;
-      if (wdepth) wdepth[p] = 0.0f;
-      mask[p] = vt.enabled ? 3 : 1;  // 3: hole still to be tested for void
+      V.mask[p] = 0;
+    } else {
+      V.wrgb[3 * p + 0] = 0.0f;
+      V.wrgb[3 * p + 1] = 0.0f;
+      V.wrgb[3 * p + 2] = 0.0f;
+      if (V.wdepth) V.wdepth[p] = 0.0f;
+      V.mask[p] = void_on ? 3 : 1;
     }
   }
 }
 
 // Void depth test of the listed candidates, one warp each (candidates cluster in the image, so
 // testing them where they lie would serialise a warp's worth of marches).
-__global__ void __launch_bounds__(256) k_void(VoidTest vt, const int32_t* cand, const int32_t* n_cand, float* wrgb,
-                                              float* wdepth, uint8_t* mask) {
+__global__ void __launch_bounds__(256) k_void(const __grid_constant__ WarpBatch B, const __grid_constant__ VoidTest vt) {
+  const int v = blockIdx.y;
+  const WarpView& V = B.v[v];
   const int lane = threadIdx.x & 31;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  const int n = *n_cand;
+  const int n = *V.n_holes;
   for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nwarps) {
-    const int p = cand[i];
-    const bool v = !warp_ray_has_sample(vt, p);
+    const int p = V.hole_idx[i];
+    const bool is_void = !warp_ray_has_sample(vt, v, p);
     if (lane == 0) {
-      if (v) {
-        wrgb[3 * p + 0] = vt.s.bg[0];
-        wrgb[3 * p + 1] = vt.s.bg[1];
-        wrgb[3 * p + 2] = vt.s.bg[2];
-        if (wdepth) wdepth[p] = __int_as_float(0x7f800000);
-        mask[p] = 2;
+      if (is_void) {
+        V.wrgb[3 * p + 0] = vt.s.bg[0];
+        V.wrgb[3 * p + 1] = vt.s.bg[1];
+        V.wrgb[3 * p + 2] = vt.s.bg[2];
+        if (V.wdepth) V.wdepth[p] = __int_as_float(0x7f800000);
+        V.mask[p] = 2;
       } else {
-        mask[p] = 1;
+        V.mask[p] = 1;
       }
     }
   }
 }
 
-// Hole compaction: each block of 1024 threads owns kHoleChunk consecutive pixels.
+// Hole compaction: each block of 1024 threads owns kHoleChunk consecutive pixels of its view.
 constexpr int kHoleChunk = 4096;
 
 __device__ __forceinline__ uint32_t block_exscan(uint32_t v, uint32_t* tot, uint32_t* sh) {
@@ -203,82 +209,111 @@ __device__ __forceinline__ uint32_t block_exscan(uint32_t v, uint32_t* tot, uint
   return r;
 }
 
-__global__ void __launch_bounds__(1024) k_hole_count(const uint8_t* mask, int n, uint8_t val, uint32_t* block_sums) {
+__global__ void __launch_bounds__(1024) k_hole_count(const __grid_constant__ WarpBatch B, uint8_t val) {
   __shared__ uint32_t sh[32];
+  const WarpView& V = B.v[blockIdx.y];
+  if ((int)blockIdx.x >= V.nblk) return;  // uniform per block
+  const int n = V.a.wt * V.a.ht;
   const int base = blockIdx.x * kHoleChunk + threadIdx.x * 4;
   uint32_t c = 0;
 #pragma unroll
-  for (int k = 0; k < 4; k++) c += (base + k < n && mask[base + k] == val) ? 1u : 0u;
+  for (int k = 0; k < 4; k++) c += (base + k < n && V.mask[base + k] == val) ? 1u : 0u;
   uint32_t tot;
   block_exscan(c, &tot, sh);
-  if (threadIdx.x == 0) block_sums[blockIdx.x] = tot;
+  if (threadIdx.x == 0) V.bsum[blockIdx.x] = tot;
 }
 
-__global__ void __launch_bounds__(1024) k_hole_blocks(uint32_t* block_sums, int nblocks, int32_t* n_holes) {
+__global__ void __launch_bounds__(1024) k_hole_blocks(const __grid_constant__ WarpBatch B) {
   __shared__ uint32_t sh[32];
+  const WarpView& V = B.v[blockIdx.y];
   uint32_t run = 0;
-  for (int b0 = 0; b0 < nblocks; b0 += blockDim.x) {
+  for (int b0 = 0; b0 < V.nblk; b0 += blockDim.x) {
     const int i = b0 + threadIdx.x;
-    const uint32_t v = i < nblocks ? block_sums[i] : 0;
+    const uint32_t x = i < V.nblk ? V.bsum[i] : 0;
     uint32_t tot;
-    const uint32_t e = block_exscan(v, &tot, sh);
-    if (i < nblocks) block_sums[i] = run + e;
+    const uint32_t e = block_exscan(x, &tot, sh);
+    if (i < V.nblk) V.bsum[i] = run + e;
     run += tot;
   }
-  if (threadIdx.x == 0) *n_holes = (int32_t)run;
+  if (threadIdx.x == 0) *V.n_holes = (int32_t)run;
 }
 
-__global__ void __launch_bounds__(1024) k_hole_write(const uint8_t* mask, int n, uint8_t val, const uint32_t* block_off,
-                                                     int32_t* hole_idx) {
+__global__ void __launch_bounds__(1024) k_hole_write(const __grid_constant__ WarpBatch B, uint8_t val) {
   __shared__ uint32_t sh[32];
+  const WarpView& V = B.v[blockIdx.y];
+  if ((int)blockIdx.x >= V.nblk) return;
+  const int n = V.a.wt * V.a.ht;
   const int base = blockIdx.x * kHoleChunk + threadIdx.x * 4;
   uint32_t c = 0;
   bool h[4];
 #pragma unroll
   for (int k = 0; k < 4; k++) {
-    h[k] = base + k < n && mask[base + k] == val;
+    h[k] = base + k < n && V.mask[base + k] == val;
     c += h[k] ? 1u : 0u;
   }
   uint32_t tot;
-  uint32_t pos = block_off[blockIdx.x] + block_exscan(c, &tot, sh);
+  uint32_t pos = V.bsum[blockIdx.x] + block_exscan(c, &tot, sh);
 #pragma unroll
   for (int k = 0; k < 4; k++)
-    if (h[k]) hole_idx[pos++] = base + k;
+    if (h[k]) V.hole_idx[pos++] = base + k;
 }
 
-// workspace: [256-byte header (error word)] [depth buffer, 8 B per target pixel] [block sums]
+static size_t al256w(size_t x) { return (x + 255) & ~size_t(255); }
+
+// workspace: [256-byte header] then per view [depth buffer, 8 B per target pixel] [block sums]
 size_t warp_ws_bytes(int wt, int ht) {
   const size_t n = (size_t)wt * ht;
   const size_t nb = (n + kHoleChunk - 1) / kHoleChunk;
-  return 256 + ((8 * n + 255) & ~size_t(255)) + ((4 * nb + 255) & ~size_t(255));
+  return 256 + al256w(8 * n) + al256w(4 * nb);
 }
 
-cicero_status run_warp(const WarpArgs& a, const VoidTest& vt, const float* ref_rgb, const float* ref_depth,
-                       float* wrgb, float* wdepth, uint8_t* mask, int32_t* hole_idx, int32_t* n_holes, void* ws,
+size_t warp_batch_ws_bytes(const int* wt, const int* ht, int n_views) {
+  size_t b = 256;
+  for (int v = 0; v < n_views; v++) b += warp_ws_bytes(wt[v], ht[v]) - 256;
+  return b;
+}
+
+void carve_warp_ws(WarpBatch& B, void* ws) {
+  char* q = (char*)ws + 256;
+  for (int v = 0; v < B.n_views; v++) {
+    const size_t n = (size_t)B.v[v].a.wt * B.v[v].a.ht;
+    B.v[v].nblk = (int)((n + kHoleChunk - 1) / kHoleChunk);
+    B.v[v].z = (unsigned long long*)q;
+    q += al256w(8 * n);
+    B.v[v].bsum = (uint32_t*)q;
+    q += al256w(4 * (size_t)B.v[v].nblk);
+  }
+}
+
+cicero_status run_warp(const WarpBatch& B, const VoidTest& vt, const float* ref_rgb, const float* ref_depth,
                        cudaStream_t st) {
-  const int nt = a.wt * a.ht, nr = a.wr * a.hr;
-  unsigned long long* z = (unsigned long long*)((char*)ws + 256);
-  uint32_t* bsum = (uint32_t*)((char*)ws + 256 + ((8 * (size_t)nt + 255) & ~size_t(255)));
-  const int nblk = (nt + kHoleChunk - 1) / kHoleChunk;
-  const int g = num_sms() * 8;
+  int max_nt = 1, max_blk = 1;
+  for (int v = 0; v < B.n_views; v++) {
+    max_nt = std::max(max_nt, B.v[v].a.wt * B.v[v].a.ht);
+    max_blk = std::max(max_blk, B.v[v].nblk);
+  }
+  const int nr = B.v[0].a.wr * B.v[0].a.hr;
+  const int g = std::max(1, num_sms() * 8 / B.n_views);
+  const dim3 gz(std::min(g, (max_nt + 255) / 256), B.n_views), gs(std::min(g, (nr + 255) / 256), B.n_views);
+  const dim3 gb(max_blk, B.n_views), g1(1, B.n_views), gv(g, B.n_views);
   {
     ProfScope ps(kStWarpSplat, st);
-    k_zclear<<<std::min(g, (nt + 255) / 256), 256, 0, st>>>(z, nt);
-    k_splat<<<std::min(g, (nr + 255) / 256), 256, 0, st>>>(a, ref_depth, z);
+    k_zclear<<<gz, 256, 0, st>>>(B);
+    k_splat<<<gs, 256, 0, st>>>(B, ref_depth);
   }
   {
     ProfScope ps(kStWarpResolve, st);
-    k_resolve<<<std::min(g, (nt + 255) / 256), 256, 0, st>>>(a, vt, ref_rgb, ref_depth, z, wrgb, wdepth, mask);
+    k_resolve<<<gz, 256, 0, st>>>(B, vt.enabled, ref_rgb, ref_depth);
     if (vt.enabled) {  // list the candidates, test them, then list the holes that remain
-      k_hole_count<<<nblk, 1024, 0, st>>>(mask, nt, 3, bsum);
-      k_hole_blocks<<<1, 1024, 0, st>>>(bsum, nblk, n_holes);
-      k_hole_write<<<nblk, 1024, 0, st>>>(mask, nt, 3, bsum, hole_idx);
-      k_void<<<g, 256, 0, st>>>(vt, hole_idx, n_holes, wrgb, wdepth, mask);
+      k_hole_count<<<gb, 1024, 0, st>>>(B, 3);
+      k_hole_blocks<<<g1, 1024, 0, st>>>(B);
+      k_hole_write<<<gb, 1024, 0, st>>>(B, 3);
+      k_void<<<gv, 256, 0, st>>>(B, vt);
       count_launches(4);
     }
-    k_hole_count<<<nblk, 1024, 0, st>>>(mask, nt, 1, bsum);
-    k_hole_blocks<<<1, 1024, 0, st>>>(bsum, nblk, n_holes);
-    k_hole_write<<<nblk, 1024, 0, st>>>(mask, nt, 1, bsum, hole_idx);
+    k_hole_count<<<gb, 1024, 0, st>>>(B, 1);
+    k_hole_blocks<<<g1, 1024, 0, st>>>(B);
+    k_hole_write<<<gb, 1024, 0, st>>>(B, 1);
   }
   count_launches(6);
   cudaError_t e = cudaGetLastError();

@@ -213,3 +213,31 @@ def test_record_capacity_overflow_is_reported(cc, ref_frame):
     with pytest.raises(cc.CiceroError) as e:
         cc.cicero_workspace_status(ws)
     assert e.value.status == cc.ERR_WORKSPACE
+
+
+def test_warp_batch_matches_single_warps(cc, orc, ref_frame):
+    """One batched warp into several targets (different sizes, with the void test and phi) gives
+    exactly what the single-target warps give, and what the oracle gives."""
+    import torch
+    g, m, cam, rgb, depth = ref_frame
+    tg = [scenes.offset_camera(cam, k, yaw_deg=1.5, shift=0.01) for k in (-7, -2, 4, 8)]
+    tg.append(scenes.Camera(50, 37, cam.f * 0.8, 24.5, 19.0, tg[1].c2w, cam.sampling))
+    for phi in (180.0, 2.0):
+        want = [orc.warp(rgb, depth, cam, t, max_angle_deg=phi, void_grid=g, void_sampling=cam.sampling) for t in tg]
+        gd = cc.DeviceGrid.from_host(g)
+        r, d = torch.from_numpy(rgb).cuda(), torch.from_numpy(depth).cuda()
+        n = [t.width * t.height for t in tg]
+        wr = [torch.empty(k, 3, device="cuda") for k in n]
+        wd = [torch.empty(k, device="cuda") for k in n]
+        mk = [torch.empty(k, dtype=torch.uint8, device="cuda") for k in n]
+        hi = [torch.empty(k, dtype=torch.int32, device="cuda") for k in n]
+        nh = torch.empty(len(tg), dtype=torch.int32, device="cuda")
+        cams = [cc.camera_from(t) for t in tg]
+        ws = cc.workspace(cc.cicero_warp_batch_workspace_size(cams))
+        cc.cicero_warp_batch(r, d, cc.camera_from(cam), cams, phi, gd.desc, cc.sampling_from(cam.sampling), wr, wd, mk,
+                             hi, nh, ws)
+        nhh = nh.cpu().numpy()
+        for i, w in enumerate(want):
+            got = {"rgb": wr[i].cpu().numpy(), "depth": wd[i].cpu().numpy(), "mask": mk[i].cpu().numpy(),
+                   "n_holes": int(nhh[i]), "hole_idx": hi[i].cpu().numpy()[:nhh[i]]}
+            assert_warp_equal(got, w)
