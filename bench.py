@@ -33,23 +33,33 @@ N_TARGETS = 16
 W = H = 800
 FLOP_PER_SAMPLE = 2 * (39 * 128 + 128 * 128 + 128 * 3)  # 43,520 MLP FLOP per composited sample
 HOLE_RECORDS = 320_000_000  # record capacity of the batched hole render (19 GB)
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_gather_mlp_bf16 launch on the
+# 800x800 reference frame, from a one-pass ncu capture of this benchmark, and the SHA-1 of the
+# kernel sources it was taken on; the roofline reports it only while those sources are unchanged.
+GATHER_TRAFFIC = {"bytes": 2499950080 + 1201474304, "sources_sha1": "6879172ada0c195223960e350463f4a7892a192e"}
+GATHER_SOURCES = ("mlp_tc.cu", "common.cuh", "internal.h")
 
 
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--steps", type=int, default=50)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-res", type=int, default=100, help="oracle sample resolution (square)")
     p.add_argument("--case", default="full", choices=["full", "small"],
                    help="small: one 320x320 reference frame (BF16 and FP32) and two targets, for profilers")
+    p.add_argument("--brick", type=int, default=4, help="brick size of the small case")
     return p.parse_args()
 
 
-def small_case():
-    """A reduced run of the same kernels for profiler captures (the grid stays 416 MB > L2)."""
+def small_case(brick: int = 4):
+    """A reduced run of the same kernels for profiler captures (the grid stays 416 MB > L2).
+
+    Kernel launch order: reference frame BF16 twice, FP32 once (one k_march, bucketing, gather
+    and composite each), then per target one warp and one hole render.  No autotuning, so a
+    capture's launch index (-s) does not depend on timing."""
     import torch
     import scenes
     from paper_2404_11852_gb300 import build, cicero as cc
@@ -61,12 +71,12 @@ def small_case():
     sd, cd = cc.sampling_from(cam.sampling), cc.camera_from(cam)
     R = n * n
     rgb, depth = torch.empty(R, 3, device="cuda"), torch.empty(R, device="cuda")
-    ws = cc.workspace(cc.cicero_render_workspace_size(grid.desc, R, sd, cc.options(cc.MLP_BF16, 4)))
-    b16, _ = cc.cicero_autotune_brick(grid.desc, mlp.desc, cd, sd, cc.MLP_BF16, rgb, depth, ws)
-    b32, _ = cc.cicero_autotune_brick(grid.desc, mlp.desc, cd, sd, cc.MLP_FP32, rgb, depth, ws)
-    o16, o32 = cc.options(cc.MLP_BF16, b16), cc.options(cc.MLP_FP32, b32)
+    o16, o32 = cc.options(cc.MLP_BF16, brick), cc.options(cc.MLP_FP32, brick)
+    ws = cc.workspace(cc.cicero_render_workspace_size(grid.desc, R, sd, o16))
     for opt in (o16, o16, o32):
         cc.cicero_render(grid.desc, mlp.desc, cd, sd, opt, rgb, depth, None, None, ws)
+    cc.cicero_workspace_status(ws)
+    active = int(ws[:16].view(torch.int32).cpu().numpy()[2])
     wws = cc.workspace(cc.cicero_warp_workspace_size(cd))
     for k in (-8, 8):
         td = cc.camera_from(scenes.offset_camera(cam, k))
@@ -78,7 +88,17 @@ def small_case():
         cc.cicero_render_holes(grid.desc, mlp.desc, td, sd, o16, hidx, nh, R, wr, wd, ws)
     cc.cicero_workspace_status(ws)
     torch.cuda.synchronize()
-    print("small case ok")
+    print(json.dumps({"case": "small", "image": f"{n}x{n}", "brick": brick, "active_samples_reference": active}))
+
+
+def gather_traffic():
+    import hashlib
+    h = hashlib.sha1()
+    for f in GATHER_SOURCES:
+        with open(os.path.join(ROOT, "paper_2404_11852_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    ok = GATHER_TRAFFIC["bytes"] is not None and GATHER_TRAFFIC["sources_sha1"] == h.hexdigest()
+    return GATHER_TRAFFIC["bytes"] if ok else None
 
 
 def peaks():
@@ -194,7 +214,7 @@ def main():
     if args.impl == "reference":
         return run_reference(args, rank, world)
     if args.case == "small":
-        return small_case()
+        return small_case(args.brick)
 
     import torch
     import torch.distributed as dist
@@ -328,7 +348,7 @@ def main():
     achieved = FLOP_PER_SAMPLE * active / t_launch / 1e12
     roof = {"kernel": "k_gather_mlp_bf16 (reference frame)", "bound": "tensor", "achieved": achieved,
             "peak": pk["bf16_tflops_sustained"], "unit": "TFLOP/s", "frac": achieved / pk["bf16_tflops_sustained"],
-            "traffic": None, "peak_src": f"{pk['src']} (sustained bf16)",
+            "traffic": gather_traffic(), "peak_src": f"{pk['src']} (sustained bf16)",
             "flop_per_launch": FLOP_PER_SAMPLE * active}
     stages = {k: {"ms_per_step": v[0] / 2, "launches_per_step": v[1] / 2} for k, v in prof.items() if v[1]}
 

@@ -196,10 +196,11 @@ __global__ void __launch_bounds__(256, 1) k_bwd_brick(GridGeo g, RaySrc src, Mlp
   const int tm = threadIdx.x & 15, tn = threadIdx.x >> 4;
   int cur = -1;
   for (uint32_t ti = t_begin; ti < t_end; ti++) {
-    const int b = (int)w.tile_brick[ti];
-    const uint32_t start0 = w.tile_start[ti];
-    const uint32_t end = min(start0 + (uint32_t)kTile, w.brick_off[b + 1]);
-    const int bx = b % g.nb[0], by = (b / g.nb[0]) % g.nb[1], bz = b / (g.nb[0] * g.nb[1]);
+    const uint4 td = w.tile[ti];
+    const int b = (int)td.z;
+    const uint32_t start0 = td.x;
+    const uint32_t end = start0 + (td.y & 0xFFu);
+    const int bx = (int)(td.w & 0xFFFFu), by = (int)(td.w >> 16), bz = (int)(td.y >> 8);
     if (b != cur) {
       if (cur >= 0) {
         flush_brick(g, cur, gacc, vb, d_dens, d_feat);

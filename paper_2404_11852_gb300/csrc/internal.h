@@ -52,8 +52,7 @@ struct RenderWs {
   uint32_t* brick_cur;  // [nb]
   uint32_t* tile_off;   // [nb + 1] first tile of each brick
   uint32_t* blk_sums;   // [2 * scan blocks] per-block sums of the brick scan
-  uint32_t* tile_brick; // [max_tiles]
-  uint32_t* tile_start; // [max_tiles]
+  uint4* tile;          // [max_tiles] (first record, count | bz << 8, brick id, bx | by << 16)
   float4* srt_pw;       // [Q] records' (position, weight) in brick order (the Ray Index Table payload)
   float4* srt_qd;       // [Q] records' (record index as bits, ray direction) in brick order
   uint32_t* rec_ray;    // [Q] ray of each record (backward and RIT export only; may be null)

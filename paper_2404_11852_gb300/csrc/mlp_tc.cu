@@ -7,10 +7,12 @@
 //   gather   : staged brick (TMA, one copy per brick visit) -> trilinear -> BF16 row of A
 //   layer 1  : D = A[128x48] W1^T      (tcgen05.mma kind::f16, FP32 accumulators in TMEM)
 //   epilogue : +b1, ReLU, BF16 (cvt.rn.relu.bf16x2)  -> A[128x128]   (A reused in place)
-//   layer 2  : D = A W2^T  -> +b2, ReLU, BF16 -> A
-//   layer 3  : D = A W3^T  (N padded 3 -> 16) -> +b3, sigmoid -> (c, w) record
-// Each group owns 128 TMEM columns (D of the three layers reuses them: every accumulator is read
-// back before the next MMA is issued) and synchronises on its own named barrier.  The elected
+//   layer 2  : D = A W2^T  -> +b2, ReLU, BF16 -> A3 in TMEM (tcgen05.st)
+//   layer 3  : D = A3 W3^T (A from TMEM, N padded 3 -> 16) -> +b3, sigmoid -> (c, w) record
+// Each group owns 128 TMEM columns (D of layers 1 and 2 reuses them: every accumulator is read
+// back before the next MMA is issued; the layer-2 epilogue writes its BF16 output back into the
+// first 64 of them, where layer 3 reads its A operand, so that activation never touches shared
+// memory) and synchronises on its own named barrier.  The elected
 // thread of a group issues the MMAs and commits them to the group's mbarrier.
 // Operands use the canonical K-major, no-swizzle layout: 8-row x 16-byte core matrices stored as
 // 128 contiguous bytes, K-adjacent core matrices 128 B apart (leading byte offset) and 8-row groups
@@ -32,6 +34,7 @@ constexpr int kN3 = 16;                // layer-3 N padded to the smallest M=128
 constexpr int kGT = 128;               // threads per group
 constexpr int kMaxGroups = 4;
 constexpr uint32_t kTmemCols = 512;    // all of an SM's tensor memory; 128 columns per group
+constexpr uint32_t kL3Col = 64;        // layer-3 accumulator columns [64, 80) of a group (A sits in [0, 64))
 constexpr int kActBytes = kTile * kK2 * 2;
 
 struct Smem {
@@ -74,6 +77,17 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b
       "setp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
       "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+// the same with A read from tensor memory (row m = lane m, two BF16 K values per 32-bit column)
+__device__ __forceinline__ void mma_bf16_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc,
+                                            uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc)
       : "memory");
 }
 
@@ -133,6 +147,43 @@ __device__ __forceinline__ void tmem_ld<32>(uint32_t taddr, float* v) {
 #pragma unroll
   for (int i = 0; i < 32; i++) v[i] = __uint_as_float(r[i]);
 }
+
+template <>
+__device__ __forceinline__ void tmem_ld<64>(uint32_t taddr, float* v) {
+  uint32_t r[64];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x64.b32 {"
+      "%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,"
+      "%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,"
+      "%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]),
+        "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]),
+        "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]),
+        "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]),
+        "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 64; i++) v[i] = __uint_as_float(r[i]);
+}
+
+// 32 consecutive columns of this thread's lane
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t* r) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+      "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+      "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]),
+      "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]),
+      "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
@@ -222,26 +273,33 @@ struct Group {
 };
 
 // Issue one layer (elected thread) and wait for it (whole group).  False on timeout.
+// Layers 0 and 1 read A from shared memory and accumulate into the group's columns [0, 128);
+// layer 2 reads A from the group's TMEM columns [0, 64) and accumulates into [64, 80).
 __device__ __forceinline__ bool run_layer(char* sm, Group& G, int layer, uint32_t* err) {
   gsync(G.g);
   if (G.m == 0) {
     fence_after();
-    const uint32_t a_base = smem_u32(G.act);
-    const uint32_t b_base = smem_u32(sm + (layer == 0 ? Smem::w1 : layer == 1 ? Smem::w2 : Smem::w3));
-    const int steps = layer == 0 ? kK1 / 16 : layer == 1 ? kK2 / 16 : kHidden / 16;
-    const uint32_t sbo_a = (uint32_t)(layer == 0 ? kK1 : kK2) * 16;
-    const uint32_t sbo_b = (uint32_t)(layer == 0 ? kK1 : layer == 1 ? kK2 : kHidden) * 16;
-    const uint32_t idesc = idesc_bf16(layer == 2 ? kN3 : kHidden);
+    if (layer < 2) {
+      const uint32_t a_base = smem_u32(G.act);
+      const uint32_t b_base = smem_u32(sm + (layer == 0 ? Smem::w1 : Smem::w2));
+      const int steps = layer == 0 ? kK1 / 16 : kK2 / 16;
+      const uint32_t sbo = (uint32_t)(layer == 0 ? kK1 : kK2) * 16;
+      const uint32_t idesc = idesc_bf16(kHidden);
 #pragma unroll 1
-    for (int s = 0; s < steps; s++) {
-      const uint64_t ad = smem_desc(a_base + 256u * s, 128u, sbo_a);
-      const uint64_t bd = smem_desc(b_base + 256u * s, 128u, sbo_b);
-      mma_bf16(G.tmem, ad, bd, idesc, s > 0 ? 1u : 0u);
+      for (int s = 0; s < steps; s++)
+        mma_bf16(G.tmem, smem_desc(a_base + 256u * s, 128u, sbo), smem_desc(b_base + 256u * s, 128u, sbo), idesc,
+                 s > 0 ? 1u : 0u);
+    } else {
+      const uint32_t b_base = smem_u32(sm + Smem::w3);
+#pragma unroll 1
+      for (int s = 0; s < kHidden / 16; s++)
+        mma_bf16_ta(G.tmem + kL3Col, G.tmem + 8u * s, smem_desc(b_base + 256u * s, 128u, kHidden * 16),
+                    idesc_bf16(kN3), s > 0 ? 1u : 0u);
     }
     mma_commit(G.bar_mma);
   }
   const bool ok = gsync_and(G.g, mbar_wait(G.bar_mma, G.ph_mma, err));
-  G.ph_mma ^= 1u;
+  if (ok) G.ph_mma ^= 1u;  // on a timeout the phase stays, so a final bounded wait watches the right one
   fence_after();
   return ok;
 }
@@ -251,15 +309,15 @@ __device__ __forceinline__ bool run_layer(char* sm, Group& G, int layer, uint32_
 __device__ __forceinline__ void epilogue_hidden(const Group& G, const float* bias) {
   const uint32_t taddr = G.tmem + ((uint32_t)((G.m >> 5) * 32) << 16);
 #pragma unroll 1
-  for (int cc = 0; cc < kHidden / 32; cc++) {
-    float v[32];
-    tmem_ld<32>(taddr + cc * 32, v);
+  for (int cc = 0; cc < kHidden / 64; cc++) {
+    float v[64];
+    tmem_ld<64>(taddr + cc * 64, v);  // one TMEM round trip per 64 columns
 #pragma unroll
-    for (int q = 0; q < 4; q++) {
+    for (int q = 0; q < 8; q++) {
       const float* x = v + q * 8;
       float y[8];
       if (bias) {
-        const float4* b4 = reinterpret_cast<const float4*>(bias + cc * 32 + q * 8);
+        const float4* b4 = reinterpret_cast<const float4*>(bias + cc * 64 + q * 8);
         add2(x, b4[0], y);
         add2(x + 4, b4[1], y + 4);
       } else {
@@ -271,7 +329,7 @@ __device__ __forceinline__ void epilogue_hidden(const Group& G, const float* bia
       o.y = pack_bf16_relu(y[2], y[3]);
       o.z = pack_bf16_relu(y[4], y[5]);
       o.w = pack_bf16_relu(y[6], y[7]);
-      *reinterpret_cast<uint4*>(G.act + kmaj_off(G.m, cc * 32 + q * 8, kK2)) = o;
+      *reinterpret_cast<uint4*>(G.act + kmaj_off(G.m, cc * 64 + q * 8, kK2)) = o;
     }
   }
   *reinterpret_cast<uint4*>(G.act + kmaj_off(G.m, kHidden, kK2)) = make_uint4(0x3f80u, 0u, 0u, 0u);  // bf16 1.0
@@ -280,18 +338,36 @@ __device__ __forceinline__ void epilogue_hidden(const Group& G, const float* bia
   fence_before();
 }
 
+// Layer-2 epilogue: ReLU of the 128 accumulator columns -> BF16, written back into the group's
+// TMEM columns [0, 64) as the A operand of layer 3 (b2 rides on the MMA).  Chunk c of 64 FP32
+// columns becomes BF16 columns [32c, 32c + 32), which chunk 0 has already read.
+__device__ __forceinline__ void epilogue_to_tmem(const Group& G) {
+  const uint32_t taddr = G.tmem + ((uint32_t)((G.m >> 5) * 32) << 16);
+#pragma unroll 1
+  for (int cc = 0; cc < kHidden / 64; cc++) {
+    float v[64];
+    tmem_ld<64>(taddr + cc * 64, v);
+    uint32_t o[32];
+#pragma unroll
+    for (int j = 0; j < 32; j++) o[j] = pack_bf16_relu(v[2 * j], v[2 * j + 1]);
+    tmem_st32(taddr + cc * 32, o);
+  }
+  tmem_wait_st();
+  fence_before();
+}
+
 // The three layers of a tile whose A (K = 48 layout) has been written and proxy-fenced by every
 // thread of the group.  c receives this thread's colour.  False on timeout.
-__device__ __forceinline__ float sigmoid_fast(float z) { return __frcp_rn(1.0f + __expf(-z)); }
+__device__ __forceinline__ float sigmoid_fast(float z) { return __fdividef(1.0f, 1.0f + __expf(-z)); }
 
 __device__ __forceinline__ bool mlp_tile(char* sm, Group& G, uint32_t* err, float c[3], bool folded_b1) {
   if (!run_layer(sm, G, 0, err)) return false;
   epilogue_hidden(G, folded_b1 ? nullptr : (const float*)(sm + Smem::b1));
   if (!run_layer(sm, G, 1, err)) return false;
-  epilogue_hidden(G, nullptr);
+  epilogue_to_tmem(G);
   if (!run_layer(sm, G, 2, err)) return false;
   float v[16];
-  tmem_ld<16>(G.tmem + ((uint32_t)((G.m >> 5) * 32) << 16), v);
+  tmem_ld<16>(G.tmem + kL3Col + ((uint32_t)((G.m >> 5) * 32) << 16), v);
   const float* b3 = (const float*)(sm + Smem::b3);
   c[0] = sigmoid_fast(v[0] + b3[0]);
   c[1] = sigmoid_fast(v[1] + b3[1]);
@@ -436,6 +512,8 @@ __device__ __forceinline__ Group setup(char* sm, const MlpPtrs& mlp, int groups,
 }  // namespace tc
 
 // The persistent gather + MLP kernel of the BF16 path (launched with 128 * groups threads).
+// Each group software-pipelines its tiles: while layer 3 of tile t runs on the tensor cores (its A
+// operand is in TMEM, so shared memory is free), the group gathers tile t + 1 into its A buffer.
 template <typename T, int CC, int NF>
 __global__ void __launch_bounds__(512, 1) k_gather_mlp_bf16(GridGeo g, int S, MlpPtrs mlp, RenderWs w,
                                                             const __grid_constant__ CUtensorMap fmap, int vb, int vx,
@@ -448,118 +526,164 @@ __global__ void __launch_bounds__(512, 1) k_gather_mlp_bf16(GridGeo g, int S, Ml
   const uint32_t per = (n_tiles + gridDim.x - 1) / gridDim.x;
   const uint32_t c_begin = blockIdx.x * per, c_end = min(n_tiles, c_begin + per);
   const uint32_t span = c_end > c_begin ? c_end - c_begin : 0;
-  const uint32_t t_begin = c_begin + (span * G.g) / groups, t_end = c_begin + (span * (G.g + 1)) / groups;
+  const long long t_begin = c_begin + (span * G.g) / groups, t_end = c_begin + (span * (G.g + 1)) / groups;
   const int B = g.brick, C = CC ? CC : g.C, m = G.m, in_dim = mlp.in_dim;
   const T* tile = (const T*)G.tile;
-  int loaded = -1;
-  bool alive = true, pending = false;
-  // records of the tile being gathered, loaded one tile ahead
-  int nb_ = 0, nmcnt = 0;
-  uint32_t nstart = 0, nsid = 0;
-  float4 npw = make_float4(0.f, 0.f, 0.f, 0.f), ndir = make_float4(0.f, 0.f, 0.f, 1.f);
-  auto fetch = [&](uint32_t ti) {
-    nb_ = (int)w.tile_brick[ti];
-    nstart = w.tile_start[ti];
-    nmcnt = (int)(min(nstart + (uint32_t)kTile, w.brick_off[nb_ + 1]) - nstart);
-    if (m < nmcnt) {
-      npw = w.srt_pw[nstart + m];
-      ndir = w.srt_qd[nstart + m];
-      nsid = __float_as_uint(ndir.x);
-    }
+  // Tile descriptors run two tiles ahead of the gather and record payloads one tile ahead, and a
+  // payload load is never conditional on loaded data (rows past a tile's count re-read its last
+  // record), so no load of this pipeline waits on another.
+  const uint4 none = make_uint4(0u, 0u, 0u, 0u);
+  auto payload = [&](const uint4& d, float4& a, float4& q) {
+    const uint32_t row = d.x + min((uint32_t)m, (d.y & 0xFFu) - 1u);  // every listed tile has >= 1 record
+    a = w.srt_pw[row];
+    q = w.srt_qd[row];
   };
-  if (t_begin < t_end) fetch(t_begin);
-  for (uint32_t ti = t_begin; alive && ti < t_end; ti++) {
-    const int b = nb_, mcnt = nmcnt;
-    const uint32_t sid = nsid;
-    const float4 pw = npw, dir = ndir;
-    const int bx = b % g.nb[0], by = (b / g.nb[0]) % g.nb[1], bz = b / (g.nb[0] * g.nb[1]);
-    if (b != loaded) {
-      gsync(G.g);  // every thread of the group is done with the previous brick
+  auto tma_brick = [&](const uint4& d) {
+    mbar_expect_tx(G.bar_tma, (uint32_t)box_bytes);
+    tma_load_3d(G.tile, &fmap, (int)(d.w & 0xFFFFu) * B * C, (int)(d.w >> 16) * B, (int)(d.y >> 8) * B, G.bar_tma);
+  };
+  // tg: the tile gathered in iteration ti (= tile ti + 1), tg1 the one after it
+  uint4 tg = t_begin < t_end ? w.tile[t_begin] : none;
+  uint4 tg1 = t_begin + 1 < t_end ? w.tile[t_begin + 1] : none;
+  float4 gpw = make_float4(0.f, 0.f, 0.f, 0.f), gdir = make_float4(0.f, 0.f, 0.f, 1.f);
+  if (t_begin < t_end) payload(tg, gpw, gdir);
+  // the tile whose MLP runs in iteration ti: this row's record (kNoRecord past the tile's count)
+  // and weight; then the same for the previous tile with its layer-3 output, written out once the
+  // next tile's layer 1 is issued
+  constexpr uint32_t kNoRecord = 0xFFFFFFFFu;
+  uint32_t csid = kNoRecord, osid = kNoRecord;
+  float cw = 0.0f, ow = 0.0f;
+  float o3[3] = {0.f, 0.f, 0.f};
+  const float* b3 = (const float*)(sm + Smem::b3);
+  auto write_out = [&]() {
+    if (osid != kNoRecord)
+      w.rec_c[osid] = make_float4(sigmoid_fast(o3[0] + b3[0]), sigmoid_fast(o3[1] + b3[1]),
+                                  sigmoid_fast(o3[2] + b3[2]), ow);
+    osid = kNoRecord;
+  };
+  int loaded = -1;
+  bool alive = true, tma_pending = false, mma_pending = false;
+  if (t_begin < t_end) {
+    if (m == 0) tma_brick(tg);
+    loaded = (int)tg.z;
+    tma_pending = true;
+  }
+  for (long long ti = t_begin - 1; ti < t_end; ti++) {
+    const bool run = ti >= t_begin, gather = ti + 1 < t_end;
+    if (run) {
+      // layer 1 of tile ti (its A was gathered in the previous iteration)
+      gsync(G.g);
       if (m == 0) {
-        mbar_expect_tx(G.bar_tma, (uint32_t)box_bytes);
-        tma_load_3d(G.tile, &fmap, bx * B * C, by * B, bz * B, G.bar_tma);
-      }
-      loaded = b;
-      pending = true;
-    }
-    if (pending) {
-      alive = gsync_and(G.g, mbar_wait(G.bar_tma, G.ph_tma, &w.hdr[0]));
-      G.ph_tma ^= 1u;
-      pending = false;
-      if (!alive) break;
-    }
-    float x[kK1];
-#pragma unroll
-    for (int j = 0; j < kK1; j++) x[j] = 0.0f;
-    if (m < mcnt) {
-      const float p[3] = {pw.x, pw.y, pw.z};
-      int l[3];
-      float f[3];
-      bool ok = true;
-#pragma unroll
-      for (int a = 0; a < 3; a++) {
-        const float ga = __fmul_rn(__fsub_rn(p[a], g.amin[a]), g.inv_h[a]);
-        int i = (int)floorf(ga);
-        if (i > g.n[a] - 2) i = g.n[a] - 2;
-        f[a] = __fsub_rn(ga, (float)i);
-        l[a] = i - (a == 0 ? bx : a == 1 ? by : bz) * B;
-        ok = ok && l[a] >= 0 && l[a] < B;
-      }
-      if (!ok)
-        set_err(&w.hdr[0], kErrInternal);
-      else if constexpr (CC == 12 && sizeof(T) == 2)
-        tri_tile_h2((const __half*)tile, vb, vx, l, f, x);
-      else
-        tri_tile<T, CC>(tile, vb, vx, C, l, f, x);
-      const float d[3] = {dir.y, dir.z, dir.w};
-      encode_dir_fast<NF>(d, mlp.n_freq, x + C);
-      if (in_dim < kK1) x[CC && NF ? (CC + 3 + 6 * NF) % kK1 : in_dim % kK1] = 1.0f;  // folded layer-1 bias
-    }
-#pragma unroll
-    for (int k0 = 0; k0 < kK1; k0 += 8) store_chunk(G.act, m, k0, kK1, x + k0);
-    fence_proxy_async();
-    // load the next tile's records while this tile is on the tensor cores
-    if (ti + 1 < t_end) fetch(ti + 1);
-    // layer 1, plus the next brick's TMA copy once every thread has finished gathering
-    gsync(G.g);
-    if (m == 0) {
-      fence_after();
-      const uint32_t a_base = smem_u32(G.act), b_base = smem_u32(sm + Smem::w1);
+        fence_after();
+        const uint32_t a_base = smem_u32(G.act), b_base = smem_u32(sm + Smem::w1);
 #pragma unroll 1
-      for (int s2 = 0; s2 < kK1 / 16; s2++)
-        mma_bf16(G.tmem, smem_desc(a_base + 256u * s2, 128u, kK1 * 16), smem_desc(b_base + 256u * s2, 128u, kK1 * 16),
-                 idesc_bf16(kHidden), s2 > 0 ? 1u : 0u);
-      mma_commit(G.bar_mma);
-    }
-    if (ti + 1 < t_end && nb_ != loaded) {
-      if (m == 0) {
-        const int nbx = nb_ % g.nb[0], nby = (nb_ / g.nb[0]) % g.nb[1], nbz = nb_ / (g.nb[0] * g.nb[1]);
-        mbar_expect_tx(G.bar_tma, (uint32_t)box_bytes);
-        tma_load_3d(G.tile, &fmap, nbx * B * C, nby * B, nbz * B, G.bar_tma);
+        for (int s2 = 0; s2 < kK1 / 16; s2++)
+          mma_bf16(G.tmem, smem_desc(a_base + 256u * s2, 128u, kK1 * 16),
+                   smem_desc(b_base + 256u * s2, 128u, kK1 * 16), idesc_bf16(kHidden), s2 > 0 ? 1u : 0u);
+        mma_commit(G.bar_mma);
       }
-      loaded = nb_;
-      pending = true;
+      mma_pending = true;
+      // every thread is done with the staged brick: copy the next tile's brick if it differs
+      if (gather && (int)tg.z != loaded) {
+        if (m == 0) tma_brick(tg);
+        loaded = (int)tg.z;
+        tma_pending = true;
+      }
+      write_out();  // the previous tile's colours, while layer 1 runs
+      alive = gsync_and(G.g, mbar_wait(G.bar_mma, G.ph_mma, &w.hdr[0]));
+      fence_after();
+      if (!alive) break;
+      G.ph_mma ^= 1u;
+      mma_pending = false;
+      epilogue_hidden(G, in_dim < kK1 ? nullptr : (const float*)(sm + Smem::b1));
+      mma_pending = true;
+      if (!(alive = run_layer(sm, G, 1, &w.hdr[0]))) break;
+      mma_pending = false;
+      epilogue_to_tmem(G);
+      // layer 3 of tile ti, not waited for yet
+      gsync(G.g);
+      if (m == 0) {
+        fence_after();
+        const uint32_t b_base = smem_u32(sm + Smem::w3);
+#pragma unroll 1
+        for (int s2 = 0; s2 < kHidden / 16; s2++)
+          mma_bf16_ta(G.tmem + kL3Col, G.tmem + 8u * s2, smem_desc(b_base + 256u * s2, 128u, kHidden * 16),
+                      idesc_bf16(kN3), s2 > 0 ? 1u : 0u);
+        mma_commit(G.bar_mma);
+      }
+      mma_pending = true;
     }
-    alive = gsync_and(G.g, mbar_wait(G.bar_mma, G.ph_mma, &w.hdr[0]));
-    G.ph_mma ^= 1u;
-    fence_after();
-    if (!alive) break;
-    epilogue_hidden(G, in_dim < kK1 ? nullptr : (const float*)(sm + Smem::b1));
-    if (!(alive = run_layer(sm, G, 1, &w.hdr[0]))) break;
-    epilogue_hidden(G, nullptr);
-    if (!(alive = run_layer(sm, G, 2, &w.hdr[0]))) break;
-    float v[16];
-    tmem_ld<16>(G.tmem + ((uint32_t)((m >> 5) * 32) << 16), v);
-    const float* b3 = (const float*)(sm + Smem::b3);
-    fence_before();
-    if (m < mcnt)
-      w.rec_c[sid] = make_float4(sigmoid_fast(v[0] + b3[0]), sigmoid_fast(v[1] + b3[1]), sigmoid_fast(v[2] + b3[2]), pw.w);
+    // payload of the tile after the one gathered now, and the descriptor after that
+    float4 npw = gpw, ndir = gdir;
+    uint4 tg2 = none;
+    if (ti + 2 < t_end) payload(tg1, npw, ndir);
+    if (ti + 3 < t_end) tg2 = w.tile[ti + 3];
+    if (gather) {
+      if (tma_pending) {
+        alive = gsync_and(G.g, mbar_wait(G.bar_tma, G.ph_tma, &w.hdr[0]));
+        if (!alive) break;
+        G.ph_tma ^= 1u;
+        tma_pending = false;
+      }
+      const int mcnt = (int)(tg.y & 0xFFu);
+      const int bx = (int)(tg.w & 0xFFFFu), by = (int)(tg.w >> 16), bz = (int)(tg.y >> 8);
+      float x[kK1];
+#pragma unroll
+      for (int j = 0; j < kK1; j++) x[j] = 0.0f;
+      if (m < mcnt) {
+        const float p[3] = {gpw.x, gpw.y, gpw.z};
+        int l[3];
+        float f[3];
+        bool ok = true;
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+          const float ga = __fmul_rn(__fsub_rn(p[a], g.amin[a]), g.inv_h[a]);
+          int i = (int)floorf(ga);
+          if (i > g.n[a] - 2) i = g.n[a] - 2;
+          f[a] = __fsub_rn(ga, (float)i);
+          l[a] = i - (a == 0 ? bx : a == 1 ? by : bz) * B;
+          ok = ok && l[a] >= 0 && l[a] < B;
+        }
+        if (!ok)
+          set_err(&w.hdr[0], kErrInternal);
+        else if constexpr (CC == 12 && sizeof(T) == 2)
+          tri_tile_h2((const __half*)tile, vb, vx, l, f, x);
+        else
+          tri_tile<T, CC>(tile, vb, vx, C, l, f, x);
+        const float d[3] = {gdir.y, gdir.z, gdir.w};
+        encode_dir_fast<NF>(d, mlp.n_freq, x + C);
+        if (in_dim < kK1) x[CC && NF ? (CC + 3 + 6 * NF) % kK1 : in_dim % kK1] = 1.0f;  // folded layer-1 bias
+      }
+#pragma unroll
+      for (int k0 = 0; k0 < kK1; k0 += 8) store_chunk(G.act, m, k0, kK1, x + k0);
+      fence_proxy_async();
+    }
+    if (run) {
+      alive = gsync_and(G.g, mbar_wait(G.bar_mma, G.ph_mma, &w.hdr[0]));
+      fence_after();
+      if (!alive) break;
+      G.ph_mma ^= 1u;
+      mma_pending = false;
+      float v[16];
+      tmem_ld<16>(G.tmem + kL3Col + ((uint32_t)((m >> 5) * 32) << 16), v);
+      fence_before();
+      o3[0] = v[0];
+      o3[1] = v[1];
+      o3[2] = v[2];
+      osid = csid;
+      ow = cw;
+    }
+    // the gathered tile is the next one through the MLP
+    csid = m < (int)(tg.y & 0xFFu) ? __float_as_uint(gdir.x) : kNoRecord;
+    cw = gpw.w;
+    tg = tg1;
+    tg1 = tg2;
+    gpw = npw;
+    gdir = ndir;
   }
-  if (!alive || pending) {
-    // a bounded wait ran out (or a prefetched copy is still landing): wait once more, bounded
-    mbar_wait(G.bar_tma, G.ph_tma, &w.hdr[0]);
-    if (!alive) mbar_wait(G.bar_mma, G.ph_mma, &w.hdr[0]);
-  }
+  if (alive) write_out();
+  if (tma_pending) mbar_wait(G.bar_tma, G.ph_tma, &w.hdr[0]);  // a copy may still be landing (bounded)
+  if (mma_pending) mbar_wait(G.bar_mma, G.ph_mma, &w.hdr[0]);  // MMAs may still be running (bounded)
   tmem_free_all(tmem_base);
 }
 

@@ -32,7 +32,7 @@ size_t render_ws_bytes(const RenderPlan& p) {
   if (p.want_k || p.want_bwd) b += al256(4 * Q);
   b += 2 * al256(4 * (size_t)p.nb) + 2 * al256(4 * ((size_t)p.nb + 1));
   b += al256(8 * ((size_t)p.nb / 4096 + 2));
-  b += 2 * al256(4 * (size_t)p.max_tiles);
+  b += al256(16 * (size_t)p.max_tiles);
   b += 2 * al256(16 * Q);
   return b;
 }
@@ -63,8 +63,7 @@ bool carve_render_ws(void* ws, size_t bytes, const RenderPlan& p, RenderWs* w) {
   w->brick_off = (uint32_t*)take(4 * ((size_t)p.nb + 1));
   w->tile_off = (uint32_t*)take(4 * ((size_t)p.nb + 1));
   w->blk_sums = (uint32_t*)take(8 * ((size_t)p.nb / 4096 + 2));
-  w->tile_brick = (uint32_t*)take(4 * (size_t)p.max_tiles);
-  w->tile_start = (uint32_t*)take(4 * (size_t)p.max_tiles);
+  w->tile = (uint4*)take(16 * (size_t)p.max_tiles);
   w->srt_pw = (float4*)take(16 * Q);
   w->srt_qd = (float4*)take(16 * Q);
   w->R = p.R;
@@ -108,6 +107,14 @@ __device__ __forceinline__ int record_bound(const GridGeo& g, const Slots& sl, c
   const int kmin = (int)floorf(fminf(fmaxf(klo, 0.0f), (float)sl.n));
   const int kmax = (int)ceilf(fminf(fmaxf(khi, -1.0f), (float)(sl.n - 1)));
   return kmax >= kmin ? kmax - kmin + 1 : 0;
+}
+
+// 1 - e^{-x} for x >= 0 without cancellation: the Taylor series x (1 - x/2 (1 - x/3 (1 - x/4 (1 - x/5))))
+// below 1/32 (truncation < x^6/720, ~1e-12 relative), the hardware exponential above it (absolute
+// error ~1e-7, relative < 4e-6 there).
+__device__ __forceinline__ float one_minus_exp_neg(float x) {
+  const float series = x * (1.0f - 0.5f * x * (1.0f - (1.0f / 3.0f) * x * (1.0f - 0.25f * x * (1.0f - 0.2f * x))));
+  return x < 0.03125f ? series : 1.0f - __expf(-x);
 }
 
 // K1: one warp per ray; lane = slot within a chunk of 32 slots.
@@ -180,7 +187,7 @@ __global__ void __launch_bounds__(256) k_march(GridGeo g, Samp s, RaySrc src, co
       const unsigned smask = __ballot_sync(full, stop);
       const int first = smask ? __ffs(smask) - 1 : 32;
       const bool contrib = act && lane < first && room;
-      const float wk = (act && lane < first) ? Tk * -expm1f(-sd) : 0.0f;
+      const float wk = (act && lane < first) ? Tk * one_minus_exp_neg(sd) : 0.0f;
       const unsigned cmask = __ballot_sync(full, contrib);
       const uint32_t key = contrib ? brick_id(g, i0) : 0xffffffffu;
       if (contrib) {
@@ -349,7 +356,7 @@ __global__ void __launch_bounds__(1024) k_brick_offsets(RenderWs w) {
 }
 
 // K2d: the tile list, one entry per tile: its brick (binary search over tile offsets) and start.
-__global__ void __launch_bounds__(256) k_tiles(RenderWs w) {
+__global__ void __launch_bounds__(256) k_tiles(GridGeo g, RenderWs w) {
   const uint32_t n = w.hdr[1];
   for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
     int lo = 0, hi = w.nb;  // largest b with tile_off[b] <= t
@@ -358,8 +365,10 @@ __global__ void __launch_bounds__(256) k_tiles(RenderWs w) {
       if (w.tile_off[mid] <= t) lo = mid;
       else hi = mid;
     }
-    w.tile_brick[t] = (uint32_t)lo;
-    w.tile_start[t] = w.brick_off[lo] + (t - w.tile_off[lo]) * kTile;
+    const uint32_t start = w.brick_off[lo] + (t - w.tile_off[lo]) * kTile;
+    const uint32_t cnt = min(start + (uint32_t)kTile, w.brick_off[lo + 1]) - start;
+    const uint32_t bx = lo % g.nb[0], by = (lo / g.nb[0]) % g.nb[1], bz = lo / (g.nb[0] * g.nb[1]);
+    w.tile[t] = make_uint4(start, cnt | (bz << 8), (uint32_t)lo, bx | (by << 16));
   }
 }
 
@@ -611,11 +620,11 @@ __global__ void __launch_bounds__(256, 1) k_gather_mlp_f32(GridGeo g, int S, Mlp
   uint32_t phase = 0;
   bool alive = true;
   for (uint32_t ti = t_begin; ti < t_end && alive; ti++) {
-    const int b = (int)w.tile_brick[ti];
-    const uint32_t start = w.tile_start[ti];
-    const uint32_t end = min(start + (uint32_t)kTile, w.brick_off[b + 1]);
-    const int mcnt = (int)(end - start);
-    const int bx = b % g.nb[0], by = (b / g.nb[0]) % g.nb[1], bz = b / (g.nb[0] * g.nb[1]);
+    const uint4 td = w.tile[ti];
+    const int b = (int)td.z;
+    const uint32_t start = td.x;
+    const int mcnt = (int)(td.y & 0xFFu);
+    const int bx = (int)(td.w & 0xFFFFu), by = (int)(td.w >> 16), bz = (int)(td.y >> 8);
     if (b != loaded) {
       __syncthreads();
       if (threadIdx.x == 0) {
@@ -763,7 +772,7 @@ cicero_status run_render(const cicero_grid* grid, const MlpPtrs& mlp, const Rend
     k_brick_sums<<<nblk, 1024, 0, st>>>(ws);
     k_brick_blocks<<<1, 1024, 0, st>>>(ws, nblk);
     k_brick_offsets<<<nblk, 1024, 0, st>>>(ws);
-    k_tiles<<<num_sms() * 4, 256, 0, st>>>(ws);
+    k_tiles<<<num_sms() * 4, 256, 0, st>>>(geo, ws);
     k_scatter<<<mb, 256, 0, st>>>(src, ws);
   }
   count_launches(7);
