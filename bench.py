@@ -91,6 +91,31 @@ def small_case(brick: int = 4):
     print(json.dumps({"case": "small", "image": f"{n}x{n}", "brick": brick, "active_samples_reference": active}))
 
 
+# ---------------------------------------------------------------------------------------------
+# multi-rank host logic (one process per GPU, replicas: no collective on the data path)
+
+
+def rank_azimuth(rank: int) -> float:
+    """Each rank renders its own SpaRW window, from its own orbit azimuth."""
+    return 30.0 + 20.0 * rank
+
+
+def max_over_ranks(seconds: float, device=None) -> float:
+    """The slowest rank's time: the job ends when it does (a no-op without a process group)."""
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return seconds
+    import torch
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_step: int, steps: int, world: int, seconds: float) -> float:
+    """Whole-job throughput: the units every rank processed over the slowest rank's time."""
+    return units_per_step * steps * world / seconds
+
+
 def gather_traffic():
     import hashlib
     h = hashlib.sha1()
@@ -166,7 +191,7 @@ def oracle_window(res: int, rank: int = 0):
     import scenes
     g, m = scenes.scene_large(), scenes.make_mlp(12)
     oracle.build()
-    cam = scenes.orbit_camera(res, res, az_deg=30.0 + 20.0 * rank, sampling=scenes.sampling_march(256, 256))
+    cam = scenes.orbit_camera(res, res, az_deg=rank_azimuth(rank), sampling=scenes.sampling_march(256, 256))
     t0 = time.perf_counter()
     ref = oracle.render(g, m, cam.sampling, cam=cam)
     holes = 0
@@ -181,12 +206,14 @@ def oracle_window(res: int, rank: int = 0):
     return dt, oracle.max_threads(), holes / (N_TARGETS * res * res)
 
 
-def run_reference(args, rank, world):
+def run_reference(args, rank, world, window=None):
+    """The oracle arm: rank 0 alone times the oracle; the other ranks exit without work."""
     if rank != 0:
-        return
+        return None
+    window = window or oracle_window
     dts = []
     for _ in range(max(1, args.steps)):
-        dt, cores, _ = oracle_window(args.cpu_res)
+        dt, cores, _ = window(args.cpu_res)
         dts.append(dt)
     scale = (W * H) / (args.cpu_res * args.cpu_res)
     t_step = float(np.mean(dts)) * scale
@@ -200,6 +227,7 @@ def run_reference(args, rank, world):
                                        f"({args.cpu_res**2} of {W*H} pixels per frame), time x {scale:.0f}"},
             "e2e": {"value": fps, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+    return line
 
 
 # ---------------------------------------------------------------------------------------------
@@ -228,7 +256,7 @@ def main():
     g_h, m_h = scenes.scene_large(), scenes.make_mlp(12)
     grid = cc.DeviceGrid.from_host(g_h)
     mlp = cc.DeviceMlp.from_host(m_h)
-    cam = scenes.orbit_camera(W, H, az_deg=30.0 + 20.0 * rank, sampling=scenes.sampling_march(256, 256))
+    cam = scenes.orbit_camera(W, H, az_deg=rank_azimuth(rank), sampling=scenes.sampling_march(256, 256))
     targets = [scenes.offset_camera(cam, k) for k in scenes.SPARW_OFFSETS]
     R = W * H
     sd = cc.sampling_from(cam.sampling)
@@ -289,11 +317,7 @@ def main():
             e1.record()
             torch.cuda.synchronize()
             total += e0.elapsed_time(e1) / 1e3
-        if world > 1:
-            t = torch.tensor([total], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total = float(t.item())
-        return total
+        return max_over_ranks(total, dev)
 
     # headline: SpaRW windows, device-resident inputs
     launches0 = cc.cicero_launch_count()
@@ -303,7 +327,7 @@ def main():
     cc.cicero_workspace_status(ws_r)
     cc.cicero_workspace_status(ws_h)
     hole_hdr = ws_h[:16].view(torch.int32).cpu().numpy()
-    value = N_TARGETS * args.steps * world / t_main
+    value = job_value(N_TARGETS, args.steps, world, t_main)
     holes = nh.sum().item()
 
     # end to end: the same step with its result (16 target frames) read back to pinned host memory
@@ -321,7 +345,7 @@ def main():
         step()
 
     t_e2e = timed(step_e2e, args.steps, 1, host_io=d2h)
-    e2e_value = N_TARGETS * args.steps * world / t_e2e
+    e2e_value = job_value(N_TARGETS, args.steps, world, t_e2e)
 
     # the plain FP32 full render and the BF16 full render of the same frame
     n_fp = max(2, args.steps)
