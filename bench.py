@@ -47,6 +47,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-extra", action="store_true", help="skip the backward and small-scene SpaRW reports")
     p.add_argument("--cpu-res", type=int, default=100, help="oracle sample resolution (square)")
     p.add_argument("--case", default="full", choices=["full", "small"],
                    help="small: one 320x320 reference frame (BF16 and FP32) and two targets, for profilers")
@@ -114,6 +115,41 @@ def max_over_ranks(seconds: float, device=None) -> float:
 def job_value(units_per_step: int, steps: int, world: int, seconds: float) -> float:
     """Whole-job throughput: the units every rank processed over the slowest rank's time."""
     return units_per_step * steps * world / seconds
+
+
+def stage_roofline(stages, pk, R, n_holes, ref_samples, hole_samples):
+    """Per stage of one SpaRW window: algorithmic bytes (or FLOP), achieved rate over the stage's
+    device time, and the fraction of the measured peak of the resource that bounds it.
+
+    Bytes counted: march, per composited sample its record (brick id 4 B + position/weight 16 B)
+    and per ray its header and depth (36 B); bucket, per record 20 B read + 32 B written (the Ray
+    Index Table payload) + 24 B of ray header per ray; gather + MLP, 43,520 FLOP per sample;
+    composite, per sample 16 B read + per ray 28 B; warp splat, per reference pixel 16 B read +
+    8 B of depth-key atomic per target; warp resolve, ~29 B per target pixel."""
+    rays = R + n_holes
+    samples = ref_samples + hole_samples
+    work = {
+        "march": ("issue", 20.0 * samples + 36.0 * rays),
+        "bucket": ("hbm", 52.0 * samples + 24.0 * rays),
+        "gather_mlp": ("tensor", float(FLOP_PER_SAMPLE) * samples),
+        "composite": ("hbm", 16.0 * samples + 28.0 * rays),
+        "warp_splat": ("hbm", (16.0 + 8.0 * N_TARGETS) * R),
+        "warp_resolve": ("hbm", 29.0 * N_TARGETS * R),
+    }
+    out = {}
+    for k, (bound, amount) in work.items():
+        if k not in stages or stages[k]["ms_per_step"] <= 0:
+            continue
+        t = stages[k]["ms_per_step"] / 1e3
+        if bound == "tensor":
+            ach = amount / t / 1e12
+            out[k] = {"bound": bound, "algorithmic_tflop": amount / 1e12, "achieved": ach, "unit": "TFLOP/s",
+                      "frac": ach / pk["bf16_tflops_sustained"]}
+        else:
+            ach = amount / t / 1e9
+            out[k] = {"bound": bound, "algorithmic_gb": amount / 1e9, "achieved": ach, "unit": "GB/s",
+                      "frac_of_hbm": ach / pk["hbm_gbs"]}
+    return out
 
 
 def gather_traffic():
@@ -184,9 +220,9 @@ class ClockSampler:
 # CPU oracle leg (the reference arm and the cpu_baseline object)
 
 
-def oracle_window(res: int, rank: int = 0):
+def oracle_window(res: int, rank: int = 0, frames: list | None = None):
     """The oracle's SpaRW window at res x res on the same scene, FOV, poses and sampling; returns
-    (seconds, cores, hole fraction)."""
+    (seconds, cores, hole fraction).  With ``frames``, the 16 target frames are appended to it."""
     import oracle
     import scenes
     g, m = scenes.scene_large(), scenes.make_mlp(12)
@@ -199,8 +235,11 @@ def oracle_window(res: int, rank: int = 0):
         tgt = scenes.offset_camera(cam, k)
         w = oracle.warp(ref["rgb"].astype(np.float32), ref["depth"].astype(np.float32), cam, tgt, void_grid=g,
                         void_sampling=cam.sampling)
+        frame = w["rgb"].astype(np.float64)
         if w["n_holes"]:
-            oracle.render(g, m, cam.sampling, cam=tgt, pix=w["hole_idx"])
+            frame[w["hole_idx"]] = oracle.render(g, m, cam.sampling, cam=tgt, pix=w["hole_idx"])["rgb"]
+        if frames is not None:
+            frames.append(frame)
         holes += w["n_holes"]
     dt = time.perf_counter() - t0
     return dt, oracle.max_threads(), holes / (N_TARGETS * res * res)
@@ -228,6 +267,162 @@ def run_reference(args, rank, world, window=None):
             "e2e": {"value": fps, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return line
+
+
+# ---------------------------------------------------------------------------------------------
+# one SpaRW window on the device
+
+
+class SparwWindow:
+    """Device buffers and the call sequence of one SpaRW window (Sec. III-B/C): the reference frame
+    rendered in full, every target warped from it in one batch, then all targets' holes rendered in
+    one batch, written into the warped frames (Eq. 4)."""
+
+    def __init__(self, cc, torch, dev, grid, mlp, cam, targets, opt_ref, opt_holes, ref_ws_bytes=0):
+        self.cc, self.grid, self.mlp = cc, grid, mlp
+        self.R, self.n = cam.width * cam.height, len(targets)
+        R, n = self.R, self.n
+        self.sd, self.cd = cc.sampling_from(cam.sampling), cc.camera_from(cam)
+        self.tds = [cc.camera_from(t) for t in targets]
+        self.opt_ref, self.opt_holes = opt_ref, opt_holes
+        self.ref_rgb, self.ref_depth = torch.empty(R, 3, device=dev), torch.empty(R, device=dev)
+        self.t_rgb, self.t_depth = torch.empty(n, R, 3, device=dev), torch.empty(n, R, device=dev)
+        self.mask = torch.empty(n, R, dtype=torch.uint8, device=dev)
+        self.hidx = torch.empty(n, R, dtype=torch.int32, device=dev)
+        self.nh = torch.zeros(n, 1, dtype=torch.int32, device=dev)
+        ref_bytes = max(ref_ws_bytes, cc.cicero_render_workspace_size(grid.desc, R, self.sd, opt_ref))
+        self.ws_r = cc.workspace(ref_bytes, dev)
+        self.ws_w = cc.workspace(cc.cicero_warp_batch_workspace_size(self.tds), dev)
+        self.ws_h = cc.workspace(cc.cicero_render_workspace_size(grid.desc, n * R, self.sd, opt_holes), dev)
+        self.lists = [[x[i] for i in range(n)] for x in (self.t_rgb, self.t_depth, self.mask, self.hidx)]
+
+    def render_reference(self, opt=None):
+        self.cc.cicero_render(self.grid.desc, self.mlp.desc, self.cd, self.sd, opt or self.opt_ref, self.ref_rgb,
+                              self.ref_depth, None, None, self.ws_r)
+
+    def run(self):
+        cc, L = self.cc, self.lists
+        self.render_reference()
+        cc.cicero_warp_batch(self.ref_rgb, self.ref_depth, self.cd, self.tds, 180.0, self.grid.desc, self.sd, L[0],
+                             L[1], L[2], L[3], self.nh.view(-1), self.ws_w)
+        cc.cicero_render_holes_batch(self.grid.desc, self.mlp.desc, self.tds, self.sd, self.opt_holes, L[3], self.nh,
+                                     self.n * self.R, L[0], L[1], self.ws_h)
+
+    def check(self):
+        """Raise if a kernel reported an error (capacity, timeout, broken invariant)."""
+        self.cc.cicero_workspace_status(self.ws_r)
+        self.cc.cicero_workspace_status(self.ws_h)
+
+    def header(self, ws):
+        return ws[:16].view(self.nh.dtype).cpu().numpy()
+
+
+def frame_psnr(got, want):
+    mse = float(np.mean((np.asarray(got, np.float64) - np.asarray(want, np.float64)) ** 2))
+    return 10 * math.log10(1.0 / max(mse, 1e-30))
+
+
+# ---------------------------------------------------------------------------------------------
+# the other measured workloads (rank 0, outside the headline timing)
+
+
+def event_ms(torch, fn, reps):
+    """Average device time of fn() over reps, CUDA events on the current stream."""
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def sparw_parity(cc, torch, dev, grid, mlp, res, rank, frames, opt):
+    """The device SpaRW window (BF16 MLP) at res x res against the oracle's SpaRW window on the same
+    scene and cameras: PSNR and max |rgb error| of every pixel of every target frame."""
+    import scenes
+    cam = scenes.orbit_camera(res, res, az_deg=rank_azimuth(rank), sampling=scenes.sampling_march(256, 256))
+    targets = [scenes.offset_camera(cam, k) for k in scenes.SPARW_OFFSETS]
+    win = SparwWindow(cc, torch, dev, grid, mlp, cam, targets, opt, opt)
+    win.run()
+    win.check()
+    got = win.t_rgb.cpu().double().numpy()
+    ps = [frame_psnr(got[i], frames[i]) for i in range(len(frames))]
+    err = max(float(np.abs(got[i] - frames[i]).max()) for i in range(len(frames)))
+    return {"image": f"{res}x{res}", "targets": len(frames), "psnr_db_min": min(ps),
+            "psnr_db_mean": float(np.mean(ps)), "max_err": err}
+
+
+def backward_workload(cc, torch, dev):
+    """Forward + backward over 8192 random rays x 256 samples on the 160^3 x 12 FP32 scene, MSE
+    loss against seeded target colours (the differentiation workload)."""
+    import scenes
+    g, m = scenes.scene_backward(), scenes.make_mlp(12)
+    R = 8192
+    o, d = scenes.random_rays(R)
+    sp = scenes.Sampling(near=0.5, far=2.5, n_samples=256, t_stop=1e-3)
+    gd, md, sd = cc.DeviceGrid.from_host(g, dev), cc.DeviceMlp.from_host(m, dev), cc.sampling_from(sp)
+    ot, dt = torch.from_numpy(o).to(dev), torch.from_numpy(d).to(dev)
+    tgt = torch.from_numpy(scenes.random_targets(R)).to(dev)
+    rgb, depth = torch.empty(R, 3, device=dev), torch.empty(R, device=dev)
+    d_rgb = torch.empty(R, 3, device=dev)
+    dd, df = torch.zeros(g.density.shape, device=dev), torch.zeros(g.features.shape, device=dev)
+    opt = cc.options(cc.MLP_FP32, 8)
+    ws_f = cc.workspace(cc.cicero_render_workspace_size(gd.desc, R, sd, opt), dev)
+    ws_b = cc.workspace(cc.cicero_backward_workspace_size(gd.desc, R, sd), dev)
+
+    def fwd():
+        cc.cicero_render_rays(gd.desc, md.desc, ot, dt, sd, opt, rgb, depth, None, None, ws_f)
+
+    def bwd():
+        torch.sub(rgb, tgt, out=d_rgb).mul_(2.0 / rgb.numel())  # dL/drgb of the MSE loss
+        cc.cicero_render_backward(gd.desc, md.desc, ot, dt, sd, d_rgb, dd, df, None, ws_b)
+
+    fwd()
+    t_f = event_ms(torch, fwd, 5)
+    t_b = event_ms(torch, bwd, 5)
+    cc.cicero_workspace_status(ws_f)
+    cc.cicero_workspace_status(ws_b)
+    return {"workload": "8192 rays x 256 samples, 160^3 x 12 FP32 grid, MSE loss", "forward_ms": t_f,
+            "backward_ms": t_b, "rays_per_s_fwd_bwd": R / ((t_f + t_b) / 1e3),
+            "grad_bytes": int(dd.numel() * 4 + df.numel() * 4)}
+
+
+def sparw_small_scene(cc, torch, dev, n_pix=1024):
+    """SpaRW on the 64^3 scene: reference 800x800 at the orbit pose (64 uniform samples), 16 targets
+    warped and hole-rendered (BF16 MLP).  Per target: fraction of rays marched and PSNR against
+    the FP64 oracle on n_pix sampled pixels; the window's device time."""
+    import oracle
+    import scenes
+    g, m = scenes.scene_small(), scenes.make_mlp(12)
+    cam = scenes.orbit_camera(W, H, sampling=scenes.sampling_uniform(64))
+    targets = [scenes.offset_camera(cam, k) for k in scenes.SPARW_OFFSETS]
+    R, n_t = W * H, len(targets)
+    gd, md = cc.DeviceGrid.from_host(g, dev), cc.DeviceMlp.from_host(m, dev)
+    opt = cc.options(cc.MLP_BF16, 8)
+    opt_h = cc.options(cc.MLP_BF16, 8, max_records=120_000_000)  # holes are ~10% of the pixels
+    win = SparwWindow(cc, torch, dev, gd, md, cam, targets, opt, opt_h)
+    t_win = event_ms(torch, win.run, 5)
+    win.check()
+    t_rgb, nh = win.t_rgb, win.nh
+    oracle.build()
+    holes = nh.view(-1).cpu().numpy()
+    per = []
+    for i, tgt in enumerate(targets):
+        pix = (scenes.splitmix64(5000 + i, n_pix) % np.uint64(R)).astype(np.int32)
+        ref = oracle.render(g, m, cam.sampling, cam=tgt, pix=pix)
+        got = t_rgb[i].cpu().double().numpy()[pix]
+        e = np.where(ref["amb"][:, None], np.minimum(np.abs(got - ref["rgb"]), np.abs(got - ref["rgb_alt"])),
+                     np.abs(got - ref["rgb"]))
+        mse = float(np.mean(e ** 2))
+        per.append({"k": scenes.SPARW_OFFSETS[i], "fraction_marched": float(holes[i]) / R,
+                    "psnr_db": 10 * math.log10(1.0 / max(mse, 1e-30)), "max_err": float(e.max())})
+    return {"workload": "64^3 x 12 FP32 scene, 800x800, 64 samples, 16 targets (1 deg yaw + 5 mm apart)",
+            "window_ms": t_win, "target_fps": n_t / (t_win / 1e3), "psnr_pixels_per_target": n_pix,
+            "psnr_db_min": min(p["psnr_db"] for p in per), "fraction_marched_mean": float(holes.sum()) / (n_t * R),
+            "targets": per}
 
 
 # ---------------------------------------------------------------------------------------------
@@ -261,43 +456,25 @@ def main():
     R = W * H
     sd = cc.sampling_from(cam.sampling)
     cd = cc.camera_from(cam)
-    tds = [cc.camera_from(t) for t in targets]
     dev = torch.device("cuda", local)
     # brick size per precision, picked by the library's autotuner (timed renders of this frame)
-    ws_r = cc.workspace(cc.cicero_render_workspace_size(grid.desc, R, sd, cc.options(cc.MLP_BF16, 4)), dev)
-    ref_rgb = torch.empty(R, 3, device=dev)
-    ref_depth = torch.empty(R, device=dev)
-    b16, tune16 = cc.cicero_autotune_brick(grid.desc, mlp.desc, cd, sd, cc.MLP_BF16, ref_rgb, ref_depth, ws_r)
-    b32, tune32 = cc.cicero_autotune_brick(grid.desc, mlp.desc, cd, sd, cc.MLP_FP32, ref_rgb, ref_depth, ws_r)
+    tune_bytes = cc.cicero_render_workspace_size(grid.desc, R, sd, cc.options(cc.MLP_BF16, 4))
+    ws_t = cc.workspace(tune_bytes, dev)
+    ref_rgb, ref_depth = torch.empty(R, 3, device=dev), torch.empty(R, device=dev)
+    b16, tune16 = cc.cicero_autotune_brick(grid.desc, mlp.desc, cd, sd, cc.MLP_BF16, ref_rgb, ref_depth, ws_t)
+    b32, tune32 = cc.cicero_autotune_brick(grid.desc, mlp.desc, cd, sd, cc.MLP_FP32, ref_rgb, ref_depth, ws_t)
+    del ws_t, ref_rgb, ref_depth
     o16, o32 = cc.options(cc.MLP_BF16, b16), cc.options(cc.MLP_FP32, b32)
-    ws_w = cc.workspace(cc.cicero_warp_workspace_size(tds[0]), dev)
-    t_rgb = torch.empty(N_TARGETS, R, 3, device=dev)
-    t_depth = torch.empty(N_TARGETS, R, device=dev)
-    mask = torch.empty(N_TARGETS, R, dtype=torch.uint8, device=dev)
-    hidx = torch.empty(N_TARGETS, R, dtype=torch.int32, device=dev)
-    nh = torch.zeros(N_TARGETS, 1, dtype=torch.int32, device=dev)
-    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
-
     # all targets' holes are rendered in one batched pass; records are capped well above need
     ob = cc.options(cc.MLP_BF16, b16, max_records=HOLE_RECORDS)
-    ws_h = cc.workspace(cc.cicero_render_workspace_size(grid.desc, N_TARGETS * R, sd, ob), dev)
-    hidx_l = [hidx[i] for i in range(N_TARGETS)]
-    trgb_l = [t_rgb[i] for i in range(N_TARGETS)]
-    tdep_l = [t_depth[i] for i in range(N_TARGETS)]
-
-    ws_wb = cc.workspace(cc.cicero_warp_batch_workspace_size(tds), dev)
-    mask_l = [mask[i] for i in range(N_TARGETS)]
-    nh_flat = nh.view(-1)
-
-    def step():
-        cc.cicero_render(grid.desc, mlp.desc, cd, sd, o16, ref_rgb, ref_depth, None, None, ws_r)
-        cc.cicero_warp_batch(ref_rgb, ref_depth, cd, tds, 180.0, grid.desc, sd, trgb_l, tdep_l, mask_l, hidx_l, nh_flat,
-                             ws_wb)
-        cc.cicero_render_holes_batch(grid.desc, mlp.desc, tds, sd, ob, hidx_l, nh, N_TARGETS * R, trgb_l, tdep_l,
-                                     ws_h)
+    win = SparwWindow(cc, torch, dev, grid, mlp, cam, targets, o16, ob,
+                      ref_ws_bytes=cc.cicero_render_workspace_size(grid.desc, R, sd, o32))
+    t_rgb, nh = win.t_rgb, win.nh
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
+    step = win.run
 
     def full(opt):
-        cc.cicero_render(grid.desc, mlp.desc, cd, sd, opt, ref_rgb, ref_depth, None, None, ws_r)
+        win.render_reference(opt)
 
     def timed(fn, steps, warmup, host_io=None):
         for _ in range(warmup):
@@ -324,9 +501,8 @@ def main():
     with ClockSampler(local) as clk:
         t_main = timed(step, args.steps, args.warmup)
     launches = (cc.cicero_launch_count() - launches0) / (args.steps + args.warmup)
-    cc.cicero_workspace_status(ws_r)
-    cc.cicero_workspace_status(ws_h)
-    hole_hdr = ws_h[:16].view(torch.int32).cpu().numpy()
+    win.check()
+    hole_hdr = win.header(win.ws_h)
     value = job_value(N_TARGETS, args.steps, world, t_main)
     holes = nh.sum().item()
 
@@ -340,7 +516,7 @@ def main():
     def step_e2e():
         # poses come from pinned host memory (they are passed to the kernels by value)
         p = pose_h.numpy()
-        for i, td in enumerate(tds):
+        for i, td in enumerate(win.tds):
             td.c2w[:] = [float(v) for v in p[i].reshape(-1)]
         step()
 
@@ -350,7 +526,7 @@ def main():
     # the plain FP32 full render and the BF16 full render of the same frame
     n_fp = max(2, args.steps)
     t_fp32 = timed(lambda: full(o32), n_fp, 1)
-    hdr = ws_r[:16].view(torch.int32).cpu().numpy()
+    hdr = win.header(win.ws_r)
     active = int(hdr[2])
     t_bf16 = timed(lambda: full(o16), n_fp, 1)
 
@@ -375,6 +551,7 @@ def main():
             "traffic": gather_traffic(), "peak_src": f"{pk['src']} (sustained bf16)",
             "flop_per_launch": FLOP_PER_SAMPLE * active}
     stages = {k: {"ms_per_step": v[0] / 2, "launches_per_step": v[1] / 2} for k, v in prof.items() if v[1]}
+    stage_roof = stage_roofline(stages, pk, R, int(holes), active, int(hole_hdr[2]))
 
     # quality: reference frame (BF16) vs the FP64 oracle on sampled pixels, and the cpu baseline
     cpu = None
@@ -384,18 +561,26 @@ def main():
         oracle.build()
         pix = (scenes.splitmix64(777, 256) % np.uint64(R)).astype(np.int32)
         full(o16)
-        got = ref_rgb.cpu().double().numpy()[pix]
+        got = win.ref_rgb.cpu().double().numpy()[pix]
         ref = oracle.render(g_h, m_h, cam.sampling, cam=cam, pix=pix)
         e = np.where(ref["amb"][:, None], np.minimum(np.abs(got - ref["rgb"]), np.abs(got - ref["rgb_alt"])),
                      np.abs(got - ref["rgb"]))
         quality = {"ref_bf16_max_err": float(e.max()),
                    "ref_bf16_psnr_db": float(10 * math.log10(1.0 / max(float(np.mean(e ** 2)), 1e-30))),
                    "sample_pixels": int(len(pix))}
-        dt, cores, _ = oracle_window(args.cpu_res, rank)
+        frames = []
+        dt, cores, _ = oracle_window(args.cpu_res, rank, frames)
+        quality["sparw_bf16_vs_oracle_sparw"] = sparw_parity(cc, torch, dev, grid, mlp, args.cpu_res, rank, frames,
+                                                             o16)
         scale = R / (args.cpu_res ** 2)
         cpu = {"value": N_TARGETS / (dt * scale), "unit": "frames/s", "cores": cores, "kind": "oracle",
                "sample": f"whole SpaRW window at {args.cpu_res}x{args.cpu_res} ({args.cpu_res**2} of {R} pixels "
                          f"per frame, FP64), time x {scale:.0f}"}
+
+    others = {}
+    if rank == 0 and not args.no_extra:
+        others["config_backward"] = backward_workload(cc, torch, dev)
+        others["config_sparw_small_scene"] = sparw_small_scene(cc, torch, dev)
 
     if rank == 0:
         line = {
@@ -416,11 +601,12 @@ def main():
             "fraction_rays_marched_targets": holes / (N_TARGETS * R),
             "hole_batch": {"rays": holes / 1, "composited_samples": int(hole_hdr[2]),
                            "records_reserved": int(np.uint32(hole_hdr[3])), "record_capacity": HOLE_RECORDS},
-            "roofline": roof, "stages": stages, "quality": quality, "cpu_baseline": cpu,
+            "roofline": roof, "stages": stages, "stage_roofline": stage_roof, "quality": quality, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "frames/s", "h2d_bytes_per_step": int(pose_h.numel() * 4),
                     "d2h_bytes_per_step": int(host_out.numel() * 4)},
             "gpu_launches": int(round(launches)) * args.steps,
             "clocks": clk.summary(),
+            **others,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
