@@ -32,7 +32,7 @@ METRIC = "800x800 FPS & Msamples/s, BF16+SpaRW vs plain FP32, at PSNR>=45dB vs o
 N_TARGETS = 16
 W = H = 800
 FLOP_PER_SAMPLE = 2 * (39 * 128 + 128 * 128 + 128 * 3)  # 43,520 MLP FLOP per composited sample
-HOLE_RECORDS = 320_000_000  # record capacity of the batched hole render (19 GB)
+HOLE_RECORDS = 128_000_000  # record capacity of the batched hole render (6.7 GB; ~84 M are used)
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_gather_mlp_bf16 launch on the
 # 800x800 reference frame, from a one-pass ncu capture of this benchmark, and the SHA-1 of the
 # kernel sources it was taken on; the roofline reports it only while those sources are unchanged.
@@ -355,6 +355,106 @@ def sparw_parity(cc, torch, dev, grid, mlp, res, rank, frames, opt):
             "psnr_db_mean": float(np.mean(ps)), "max_err": err}
 
 
+BATCH_GRIDS = (96, 128, 160, 192, 224, 256)
+BATCH_SIDES = (256, 384, 512, 640, 768, 896, 1024)
+BATCH_SAMPLES = (64, 128, 192, 256)
+BATCH_JOBS = 48
+
+
+def batched_workload(cc, torch, dev, n_check=8, reps=5):
+    """48 scene/view pairs of uneven size rendered as one batch (cicero_batch_*), replayed from a
+    CUDA graph, against the same jobs rendered one cicero_render call at a time.  Six scenes
+    (96^3 .. 256^3 x 12 FP16, 24 blobs, 32^3 occupancy at 15%), each with its own MLP, 8 views
+    each; image side (256 .. 1024) and samples per ray (64 .. 256, slots every half voxel) drawn
+    per job from a seeded stream.  n_check pixels per job are checked against the FP64 oracle."""
+    import oracle
+    import scenes
+    u = scenes.splitmix64(4321, 2 * BATCH_JOBS)
+    sc = []
+    for i, N in enumerate(BATCH_GRIDS):
+        g = scenes.make_grid(N, 12, 24, seed=700 + i, dtype=np.float16, occ_res=32, occ_frac=0.15)
+        m = scenes.make_mlp(12, seed=800 + i)
+        sc.append((g, m, cc.DeviceGrid.from_host(g, dev), cc.DeviceMlp.from_host(m, dev)))
+    specs, keep, rows, outs = [], [], [], []
+    for j in range(BATCH_JOBS):
+        si = j % len(BATCH_GRIDS)
+        side = BATCH_SIDES[int(u[2 * j] % np.uint64(len(BATCH_SIDES)))]
+        S = BATCH_SAMPLES[int(u[2 * j + 1] % np.uint64(len(BATCH_SAMPLES)))]
+        cam = scenes.orbit_camera(side, side, az_deg=360.0 * j / BATCH_JOBS, el_deg=10.0 + 20.0 * (j % 3),
+                                  sampling=scenes.sampling_march(BATCH_GRIDS[si], S))
+        cd, sd = cc.camera_from(cam), cc.sampling_from(cam.sampling)
+        R = side * side
+        rgb, dep = torch.empty(R, 3, device=dev), torch.empty(R, device=dev)
+        specs.append((si, cam, S))
+        keep.append((cd, sd))
+        outs.append((rgb, dep))
+        rows.append((sc[si][2].desc, sc[si][3].desc, cd, sd, rgb, dep))
+    jobs = cc.jobs_array(rows)
+    rays = sum(c.width * c.height for _, c, _ in specs)
+    rs = sum(c.width * c.height * S for _, c, S in specs)
+    cap = int(0.45 * rs)  # composited samples are ~35% of the slots here; a shortfall is reported
+    opt4 = cc.options(cc.MLP_BF16, 4, max_records=cap)
+    ws = cc.workspace(cc.cicero_batch_workspace_size(jobs, opt4), dev)
+    brick, tune = cc.cicero_batch_autotune_brick(jobs, opt4, ws)
+    opt = cc.options(cc.MLP_BF16, brick, max_records=cap)
+    b = cc.Batch(jobs, opt, ws)
+    b.launch()  # outside the capture: kernel attributes
+    torch.cuda.synchronize()
+    b.status()
+    samples = int(b.header()[2])
+    stream = torch.cuda.Stream(dev)
+    stream.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        b.launch()
+    t_batch = event_ms(torch, graph.replay, reps)
+    b.status()
+    # the same jobs one cicero_render at a time (one workspace, sized for the largest job)
+    o1 = cc.options(cc.MLP_BF16, brick)
+    big = max(cc.cicero_render_workspace_size(sc[si][2].desc, c.width * c.height, keep[j][1], o1)
+              for j, (si, c, _) in enumerate(specs))
+    ws1 = cc.workspace(big, dev)
+
+    def one_by_one():
+        for j, (si, c, _) in enumerate(specs):
+            cd, sd = keep[j]
+            cc.cicero_render(sc[si][2].desc, sc[si][3].desc, cd, sd, o1, outs[j][0], outs[j][1], None, None, ws1)
+
+    t_single = event_ms(torch, one_by_one, 2)
+    cc.cicero_workspace_status(ws1)
+    # where the time goes: per-stage device time of one batch launch and of the 48 single renders
+    stage_ms = {}
+    for name, fn in (("batch", b.launch), ("one_call_per_job", one_by_one)):
+        cc.cicero_profile_begin()
+        fn()
+        torch.cuda.synchronize()
+        stage_ms[name] = {k: round(v[0], 3) for k, v in cc.cicero_profile_end().items() if v[1]}
+    # oracle check on sampled pixels of every job (outputs of the last batch replay)
+    graph.replay()
+    torch.cuda.synchronize()
+    oracle.build()
+    worst, sq, n = 0.0, 0.0, 0
+    for j, (si, c, _) in enumerate(specs):
+        R = c.width * c.height
+        pix = (scenes.splitmix64(9000 + j, n_check) % np.uint64(R)).astype(np.int32)
+        ref = oracle.render(sc[si][0], sc[si][1], c.sampling, cam=c, pix=pix)
+        got = outs[j][0].cpu().double().numpy()[pix]
+        e = np.where(ref["amb"][:, None], np.minimum(np.abs(got - ref["rgb"]), np.abs(got - ref["rgb_alt"])),
+                     np.abs(got - ref["rgb"]))
+        worst = max(worst, float(e.max()))
+        sq += float((e ** 2).sum())
+        n += e.size
+    del graph
+    b.close()
+    return {"workload": f"{BATCH_JOBS} jobs: grids 96^3..256^3 x 12 FP16 (6 scenes, own MLPs), images 256^2..1024^2, "
+                        "64..256 samples per ray", "rays": rays, "composited_samples": samples,
+            "brick": brick, "autotune_ms_by_brick": tune, "batch_ms": t_batch,
+            "jobs_per_s": BATCH_JOBS / (t_batch / 1e3), "msamples_per_s": samples / (t_batch / 1e3) / 1e6,
+            "one_call_per_job_ms": t_single, "speedup_vs_one_call_per_job": t_single / t_batch,
+            "launch": "one CUDA graph (9 kernels for all jobs)", "record_capacity": cap, "stage_ms": stage_ms,
+            "oracle_check": {"pixels": n // 3, "max_err": worst, "psnr_db": 10 * math.log10(1.0 / max(sq / n, 1e-30))}}
+
+
 def backward_workload(cc, torch, dev):
     """Forward + backward over 8192 random rays x 256 samples on the 160^3 x 12 FP32 scene, MSE
     loss against seeded target colours (the differentiation workload)."""
@@ -581,6 +681,7 @@ def main():
     if rank == 0 and not args.no_extra:
         others["config_backward"] = backward_workload(cc, torch, dev)
         others["config_sparw_small_scene"] = sparw_small_scene(cc, torch, dev)
+        others["config_batched"] = batched_workload(cc, torch, dev)
 
     if rank == 0:
         line = {

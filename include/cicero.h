@@ -103,9 +103,11 @@ typedef struct {
 
 /* Options of the rendering calls (NULL = defaults: FP32 MLP, bricks of 8^3 voxels, full capacity).
  * max_records caps the per-sample records the workspace holds (0 = n_rays * n_samples, which can
- * never overflow).  Each ray reserves an upper bound of its samples (its slots within two slots of
- * the grid box); if the reservations exceed max_records the rays that do not fit composite nothing
- * and cicero_workspace_status returns CICERO_ERR_WORKSPACE_TOO_SMALL. */
+ * never overflow; 52 bytes per record).  With a capacity below n_rays * n_samples, a ray that can
+ * composite at most 256 samples reserves exactly the samples it composites (it stages them on chip
+ * first); with the full capacity, and for every ray of cicero_render_backward and cicero_build_rit,
+ * rays reserve an upper bound of their samples (their slots within two slots of the grid box).  If the reservations exceed max_records the rays that do not
+ * fit composite nothing and cicero_workspace_status returns CICERO_ERR_WORKSPACE_TOO_SMALL. */
 typedef struct {
     cicero_precision precision;
     int brick;          /* voxels per brick edge ("MVoxel", Sec. IV-A): 4, 8 or 16; 0 = 8 */
@@ -173,6 +175,55 @@ cicero_status cicero_autotune_brick(const cicero_grid *grid, const cicero_mlp *m
                                     const cicero_sampling *sampling, cicero_precision precision,
                                     float *rgb, float *depth, void *workspace, size_t ws_bytes, void *stream,
                                     int *best_brick, float *ms);
+
+/* ---------------------------------------------------------------------------------------------
+ * Batched rendering: many scene/view pairs of uneven size through one set of launches.
+ *
+ * The paper renders one frame at a time; it has no counterpart for this.  Each job is a full
+ * cicero_render of its own grid, MLP, camera and sampling: the rays of all jobs share one march,
+ * one Ray Index Table (brick ids numbered job after job) and one persistent tensor-core pass
+ * whose CTAs each take a contiguous range of the brick-ordered work, loading a job's MLP weights
+ * only where the range crosses into a job with other weights.  The BF16 tensor-core MLP only
+ * (opt->precision must be CICERO_MLP_BF16); all jobs must share the grid dtype, the channel
+ * count and the view encoding; at most 2048 jobs.  opt->brick applies to every job;
+ * opt->max_records caps the records of the whole batch (0 = the sum of H*W*n_samples, which
+ * must stay below 2^32).
+ *
+ * cicero_batch_create validates the jobs, encodes each grid's TMA descriptor and uploads the job
+ * table into the workspace (a synchronous host-to-device copy; the host arrays, including the
+ * grid/mlp/camera/sampling structs, may be freed afterwards, but the device buffers they point
+ * to must outlive the handle).  cicero_batch_launch then issues kernels only (no host-device
+ * copy, allocation or synchronisation), so it can be captured into a CUDA graph and replayed;
+ * every launch renders every job again into its rgb [H*W][3] and depth [H*W] (or NULL) device
+ * buffers.  Errors inside the kernels are read with cicero_workspace_status on
+ * (char *)workspace + cicero_batch_table_bytes(n_jobs).  The handle is host memory owned by the
+ * caller: cicero_batch_destroy frees it.  A workspace serves one handle at a time.
+ */
+typedef struct {
+    const cicero_grid *grid;          /* the job's scene */
+    const cicero_mlp *mlp;            /* its colour MLP */
+    const cicero_camera *cam;         /* its view; every pixel is rendered */
+    const cicero_sampling *sampling;
+    float *rgb;                       /* device [H*W][3] */
+    float *depth;                     /* device [H*W] (+inf = void) or NULL */
+} cicero_job;
+
+typedef struct cicero_batch cicero_batch;
+
+size_t cicero_batch_workspace_size(const cicero_job *jobs, int n_jobs, const cicero_options *opt);
+size_t cicero_batch_table_bytes(int n_jobs);
+cicero_status cicero_batch_create(const cicero_job *jobs, int n_jobs, const cicero_options *opt,
+                                  void *workspace, size_t ws_bytes, cicero_batch **out);
+cicero_status cicero_batch_launch(const cicero_batch *batch, void *stream);
+cicero_status cicero_batch_destroy(cicero_batch *batch);
+
+/* Brick-size autotuner of a batch: creates, launches once untimed and once timed with bricks of
+ * 4, 8 and 16 voxels (each that fits ws_bytes) and returns the fastest in *best_brick; ms[3]
+ * (may be NULL) the timed milliseconds (-1 = not tried).  Size the workspace with brick 4.
+ * Synchronises `stream`; leaves no handle behind (create one with the chosen brick). */
+cicero_status cicero_batch_autotune_brick(const cicero_job *jobs, int n_jobs, const cicero_options *opt,
+                                          void *workspace, size_t ws_bytes, void *stream,
+                                          int *best_brick, float *ms);
 
 /* ---------------------------------------------------------------------------------------------
  * SpaRW target frame, steps 1-3 (Eq. 1 point cloud, Eq. 2 transform, Eq. 3 re-projection) plus

@@ -51,6 +51,11 @@ class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("brick", C.c_int), ("max_records", C.c_longlong)]
 
 
+class Job(C.Structure):
+    _fields_ = [("grid", C.c_void_p), ("mlp", C.c_void_p), ("cam", C.c_void_p), ("sampling", C.c_void_p),
+                ("rgb", C.c_void_p), ("depth", C.c_void_p)]
+
+
 _P = C.c_void_p
 _Z = C.c_size_t
 _SIGS = {
@@ -72,6 +77,12 @@ _SIGS = {
     "cicero_mlp_eval_workspace_size": ([C.c_int], _Z),
     "cicero_workspace_status": ([_P, _P], C.c_int),
     "cicero_autotune_brick": ([_P] * 4 + [C.c_int] + [_P] * 3 + [_Z] + [_P] * 3, C.c_int),
+    "cicero_batch_workspace_size": ([_P, C.c_int, _P], _Z),
+    "cicero_batch_table_bytes": ([C.c_int], _Z),
+    "cicero_batch_create": ([_P, C.c_int, _P, _P, _Z, _P], C.c_int),
+    "cicero_batch_launch": ([_P, _P], C.c_int),
+    "cicero_batch_destroy": ([_P], C.c_int),
+    "cicero_batch_autotune_brick": ([_P, C.c_int, _P, _P, _Z, _P, _P, _P], C.c_int),
     "cicero_profile_begin": ([], C.c_int),
     "cicero_profile_end": ([_P, _P, C.c_int], C.c_int),
     "cicero_launch_count": ([], C.c_longlong),
@@ -364,3 +375,70 @@ def cicero_launch_count() -> int:
 
 def cicero_version() -> str:
     return lib().cicero_version().decode()
+
+
+# ---------------------------------------------------------------------------------------------
+# batched rendering
+
+
+def jobs_array(jobs) -> C.Array:
+    """A ``cicero_job`` array from (grid desc, mlp desc, camera, sampling, rgb tensor, depth tensor or
+    None) tuples; the descriptor structs must stay referenced while the array is used."""
+    arr = (Job * len(jobs))()
+    for i, (g, m, cam, samp, rgb, depth) in enumerate(jobs):
+        arr[i].grid = C.addressof(g)
+        arr[i].mlp = C.addressof(m)
+        arr[i].cam = C.addressof(cam)
+        arr[i].sampling = C.addressof(samp)
+        arr[i].rgb = _ptr(rgb).value
+        arr[i].depth = _ptr(depth).value if depth is not None else None
+    return arr
+
+
+def cicero_batch_workspace_size(jobs, opt: Options) -> int:
+    return int(lib().cicero_batch_workspace_size(jobs, len(jobs), C.byref(opt)))
+
+
+def cicero_batch_table_bytes(n_jobs: int) -> int:
+    return int(lib().cicero_batch_table_bytes(int(n_jobs)))
+
+
+class Batch:
+    """A planned batch (``cicero_batch`` handle); ``launch`` renders every job again."""
+
+    def __init__(self, jobs, opt: Options, ws: torch.Tensor):
+        p, n = _ws(ws)
+        h = C.c_void_p()
+        _check(lib().cicero_batch_create(jobs, len(jobs), C.byref(opt), p, n, C.byref(h)))
+        self.handle, self.ws, self.n_jobs = h, ws, len(jobs)
+
+    def launch(self, stream=None):
+        _check(lib().cicero_batch_launch(self.handle, _stream(stream)))
+
+    def status(self, stream=None):
+        """Raise if a kernel of the last launches reported an error."""
+        off = cicero_batch_table_bytes(self.n_jobs)
+        _check(lib().cicero_workspace_status(C.c_void_p(self.ws.data_ptr() + off), _stream(stream)))
+
+    def header(self):
+        off = cicero_batch_table_bytes(self.n_jobs)
+        return self.ws[off:off + 64].view(torch.int32).cpu()
+
+    def close(self):
+        if self.handle:
+            lib().cicero_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def cicero_batch_autotune_brick(jobs, opt: Options, ws: torch.Tensor, stream=None):
+    p, n = _ws(ws)
+    best = C.c_int(0)
+    ms = (C.c_float * 3)()
+    _check(lib().cicero_batch_autotune_brick(jobs, len(jobs), C.byref(opt), p, n, _stream(stream), C.byref(best), ms))
+    return int(best.value), {b: float(ms[i]) for i, b in enumerate((4, 8, 16))}

@@ -385,6 +385,95 @@ static cicero_status warp_common(const float* ref_rgb, const float* ref_depth, c
   return run_warp(B, vt, ref_rgb, ref_depth, (cudaStream_t)stream);
 }
 
+// -------------------------------------------------------------------------------------------
+// batched render: validation, totals and the job table
+
+static size_t al256h(size_t x) { return (x + 255) & ~size_t(255); }
+
+// job descriptors, then the jobs' first rays and first bricks as two contiguous int arrays
+size_t batch_table_bytes(int n_jobs) {
+  return al256h(sizeof(JobDesc) * (size_t)n_jobs) + al256h(sizeof(int) * 2 * (size_t)n_jobs);
+}
+
+// Validates the jobs and fills the totals of the batch; with `table`, also each job's descriptor.
+static cicero_status plan_batch(const cicero_job* jobs, int n_jobs, const cicero_options* opt, BatchPlan* b,
+                                JobDesc* table) {
+  if (!jobs || n_jobs < 1 || n_jobs > kMaxBatchJobs) return fail(CICERO_ERR_INVALID_ARG, "n_jobs must be 1..2048");
+  if (!opt || opt->precision != CICERO_MLP_BF16)
+    return fail(CICERO_ERR_UNSUPPORTED, "batched rendering runs the BF16 tensor-core MLP only");
+  const int brick = opt->brick ? opt->brick : 8;
+  memset(b, 0, sizeof *b);
+  unsigned long long R = 0, Q = 0, nb = 0;
+  int S = 0;
+  for (int j = 0; j < n_jobs; j++) {
+    const cicero_job& J = jobs[j];
+    if (!J.grid || !J.mlp || !J.cam || !J.sampling || !J.rgb) return fail(CICERO_ERR_INVALID_ARG, "a job field is NULL");
+    GridGeo geo;
+    Samp samp;
+    cicero_status st = make_geo(J.grid, brick, &geo);
+    if (st == CICERO_OK) st = make_samp(J.sampling, &samp);
+    if (st == CICERO_OK) st = check_cam(J.cam);
+    if (st == CICERO_OK) st = check_mlp(J.mlp, J.grid);
+    if (st != CICERO_OK) return st;
+    if (j == 0) {
+      b->f16 = J.grid->dtype == CICERO_F16;
+      b->C = J.grid->C;
+      b->n_freq = J.mlp->n_freq;
+    } else if ((J.grid->dtype == CICERO_F16) != b->f16 || J.grid->C != b->C || J.mlp->n_freq != b->n_freq) {
+      return fail(CICERO_ERR_UNSUPPORTED, "all jobs of a batch need the same grid dtype, channels and encoding");
+    }
+    const unsigned long long rj = (unsigned long long)J.cam->width * J.cam->height;
+    const unsigned long long nbj = (unsigned long long)geo.nb[0] * geo.nb[1] * geo.nb[2];
+    if (table) {
+      JobDesc& D = table[j];
+      memset(&D, 0, sizeof D);
+      D.geo = geo;
+      D.samp = samp;
+      D.cam = view_of(J.cam);
+      D.mlp = mlp_ptrs(J.mlp);
+      D.density = J.grid->density;
+      D.rgb = J.rgb;
+      D.depth = J.depth;
+      D.ray_base = (int)R;
+      D.brick_base = (int)nb;
+      D.n_rays = (int)rj;
+      D.nb = (int)nbj;
+      st = encode_brick_map(J.grid, geo, brick_box(geo, elem_bytes(J.grid->dtype)), &D.map);
+      if (st != CICERO_OK) return st;
+    }
+    R += rj;
+    Q += rj * (unsigned long long)J.sampling->n_samples;
+    nb += nbj;
+    S = std::max(S, J.sampling->n_samples);
+    if (j == 0) b->box = brick_box(geo, elem_bytes(J.grid->dtype));
+    if (j == 0) b->plan.geo = geo;
+  }
+  if (R >= (1ull << 31) || nb >= (1ull << 31)) return fail(CICERO_ERR_UNSUPPORTED, "batch has too many rays or bricks");
+  if (opt->max_records > 0 && (unsigned long long)opt->max_records < Q) Q = (unsigned long long)opt->max_records;
+  if (Q >= 0xffffffffull) return fail(CICERO_ERR_UNSUPPORTED, "batch records must stay below 2^32 (set max_records)");
+  b->n_jobs = n_jobs;
+  RenderPlan& p = b->plan;
+  p.R = (int)R;
+  p.S = S;
+  p.Q = (uint32_t)Q;
+  p.nb = (int)nb;
+  p.max_tiles = (int)((Q + kTile - 1) / kTile) + p.nb;
+  p.want_k = false;
+  p.want_bwd = false;
+  p.precision = CICERO_MLP_BF16;
+  return CICERO_OK;
+}
+
+}  // namespace cicero
+
+struct cicero_batch {
+  cicero::BatchPlan plan;
+};
+
+namespace cicero {
+
+static size_t batch_ws_bytes(const BatchPlan& b) { return batch_table_bytes(b.n_jobs) + render_ws_bytes(b.plan); }
+
 }  // namespace cicero
 
 using namespace cicero;
@@ -681,5 +770,105 @@ long long cicero_launch_count(void) { return g_launches.load(); }
 const char* cicero_last_error(void) { return g_last_error.c_str(); }
 
 const char* cicero_version(void) { return "cicero-gb300 0.1 (sm_103a)"; }
+
+size_t cicero_batch_table_bytes(int n_jobs) {
+  return n_jobs >= 1 && n_jobs <= kMaxBatchJobs ? batch_table_bytes(n_jobs) : 0;
+}
+
+size_t cicero_batch_workspace_size(const cicero_job* jobs, int n_jobs, const cicero_options* opt) {
+  BatchPlan b;
+  if (plan_batch(jobs, n_jobs, opt, &b, nullptr) != CICERO_OK) return 0;
+  return batch_ws_bytes(b);
+}
+
+cicero_status cicero_batch_create(const cicero_job* jobs, int n_jobs, const cicero_options* opt, void* workspace,
+                                  size_t ws_bytes, cicero_batch** out) {
+  if (!out) return fail(CICERO_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!ws_ok(workspace)) return fail(CICERO_ERR_INVALID_ARG, "workspace must be non-NULL and 256-byte aligned");
+  std::vector<JobDesc> table(n_jobs > 0 && n_jobs <= kMaxBatchJobs ? n_jobs : 1);
+  BatchPlan b;
+  cicero_status st = plan_batch(jobs, n_jobs, opt, &b, table.data());
+  if (st != CICERO_OK) return st;
+  if (batch_ws_bytes(b) > ws_bytes) return fail(CICERO_ERR_WORKSPACE_TOO_SMALL, "workspace too small for the batch");
+  char* base = (char*)workspace;
+  const size_t tb = batch_table_bytes(n_jobs);
+  if (!carve_render_ws(base + tb, ws_bytes - tb, b.plan, &b.ws))
+    return fail(CICERO_ERR_WORKSPACE_TOO_SMALL, "workspace too small for the batch");
+  const size_t jb = al256h(sizeof(JobDesc) * (size_t)n_jobs);
+  std::vector<int> bases(2 * (size_t)n_jobs);
+  for (int j = 0; j < n_jobs; j++) {
+    bases[j] = table[j].ray_base;
+    bases[n_jobs + j] = table[j].brick_base;
+  }
+  cudaError_t e = cudaMemcpy(base, table.data(), sizeof(JobDesc) * (size_t)n_jobs, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(base + jb, bases.data(), sizeof(int) * bases.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "job table upload");
+  b.jobs = (const JobDesc*)base;
+  b.bases = (const int*)(base + jb);
+  b.workspace = workspace;
+  b.ws_bytes = ws_bytes;
+  cicero_batch* h = new (std::nothrow) cicero_batch;
+  if (!h) return fail(CICERO_ERR_INTERNAL, "out of host memory");
+  h->plan = b;
+  *out = h;
+  return CICERO_OK;
+}
+
+cicero_status cicero_batch_launch(const cicero_batch* batch, void* stream) {
+  if (!batch) return fail(CICERO_ERR_INVALID_ARG, "batch is NULL");
+  return run_render_batch(batch->plan, (cudaStream_t)stream);
+}
+
+cicero_status cicero_batch_destroy(cicero_batch* batch) {
+  delete batch;
+  return CICERO_OK;
+}
+
+cicero_status cicero_batch_autotune_brick(const cicero_job* jobs, int n_jobs, const cicero_options* opt,
+                                          void* workspace, size_t ws_bytes, void* stream, int* best_brick,
+                                          float* ms) {
+  if (!best_brick || !opt) return fail(CICERO_ERR_INVALID_ARG, "best_brick/opt is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int cand[3] = {4, 8, 16};
+  float best = 1e30f;
+  *best_brick = 0;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+  for (int i = 0; i < 3; i++) {
+    if (ms) ms[i] = -1.0f;
+    cicero_options o = *opt;
+    o.brick = cand[i];
+    cicero_batch* b = nullptr;
+    if (cicero_batch_create(jobs, n_jobs, &o, workspace, ws_bytes, &b) != CICERO_OK) continue;
+    // one untimed launch (first use of the kernels), then one timed launch
+    if (cicero_batch_launch(b, stream) != CICERO_OK) {
+      cicero_batch_destroy(b);
+      continue;  // this brick size is not supported for these grids
+    }
+    cudaEventRecord(e0, st);
+    cicero_batch_launch(b, stream);
+    cudaEventRecord(e1, st);
+    e = cudaEventSynchronize(e1);
+    const cicero_status ws_st = cicero_workspace_status((char*)workspace + batch_table_bytes(n_jobs), stream);
+    cicero_batch_destroy(b);
+    if (e != cudaSuccess) break;
+    if (ws_st != CICERO_OK) continue;
+    float t = 0.0f;
+    cudaEventElapsedTime(&t, e0, e1);
+    if (ms) ms[i] = t;
+    if (t < best) {
+      best = t;
+      *best_brick = cand[i];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return cuda_fail(e, "batch autotune");
+  if (!*best_brick) return fail(CICERO_ERR_UNSUPPORTED, "no brick size could render this batch");
+  return CICERO_OK;
+}
 
 }  // extern "C"

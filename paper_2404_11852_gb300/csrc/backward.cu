@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(256, 1) k_bwd_brick(GridGeo g, RaySrc src, Mlp
     const int b = (int)td.z;
     const uint32_t start0 = td.x;
     const uint32_t end = start0 + (td.y & 0xFFu);
-    const int bx = (int)(td.w & 0xFFFFu), by = (int)(td.w >> 16), bz = (int)(td.y >> 8);
+    const int bx = (int)(td.w & 0xFFFFu), by = (int)(td.w >> 16), bz = (int)((td.y >> 8) & 0x1FFFu);
     if (b != cur) {
       if (cur >= 0) {
         flush_brick(g, cur, gacc, vb, d_dens, d_feat);

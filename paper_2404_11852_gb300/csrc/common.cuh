@@ -113,18 +113,9 @@ __device__ __forceinline__ RayRef ray_ref(const RaySrc& s, int r) {
   return q;
 }
 
-// Ray of pixel/ray r: pinhole model of Eq. 1 / Eq. 3 (centre (i + 1/2, j + 1/2)).
-__device__ __forceinline__ void ray_gen(const RaySrc& s, const RayRef& q, float o[3], float d[3]) {
-  if (s.kind == 1) {
-#pragma unroll
-    for (int a = 0; a < 3; a++) {
-      o[a] = s.o[3 * q.pix + a];
-      d[a] = s.d[3 * q.pix + a];
-    }
-    return;
-  }
-  const ViewCam& c = s.cam[q.view];
-  const int i = q.pix % c.width, j = q.pix / c.width;
+// Ray through pixel `pix` of camera c: pinhole model of Eq. 1 / Eq. 3 (centre (i + 1/2, j + 1/2)).
+__device__ __forceinline__ void ray_gen_cam(const ViewCam& c, int pix, float o[3], float d[3]) {
+  const int i = pix % c.width, j = pix / c.width;
   const float u = __fadd_rn((float)i, 0.5f), v = __fadd_rn((float)j, 0.5f);
   const float dx = __fdiv_rn(__fsub_rn(u, c.cx), c.f);
   const float dy = __fdiv_rn(__fsub_rn(v, c.cy), c.f);
@@ -139,6 +130,19 @@ __device__ __forceinline__ void ray_gen(const RaySrc& s, const RayRef& q, float 
     d[a] = __fdiv_rn(w[a], nn);
     o[a] = c.c2w[4 * a + 3];
   }
+}
+
+// Ray of pixel/ray r of a ray source.
+__device__ __forceinline__ void ray_gen(const RaySrc& s, const RayRef& q, float o[3], float d[3]) {
+  if (s.kind == 1) {
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+      o[a] = s.o[3 * q.pix + a];
+      d[a] = s.d[3 * q.pix + a];
+    }
+    return;
+  }
+  ray_gen_cam(s.cam[q.view], q.pix, o, d);
 }
 
 // Slot placement: t_k = t0 + (k + 1/2) dt for k < n (and t_k < t_out in box-march mode).

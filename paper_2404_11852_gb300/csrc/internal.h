@@ -52,7 +52,7 @@ struct RenderWs {
   uint32_t* brick_cur;  // [nb]
   uint32_t* tile_off;   // [nb + 1] first tile of each brick
   uint32_t* blk_sums;   // [2 * scan blocks] per-block sums of the brick scan
-  uint4* tile;          // [max_tiles] (first record, count | bz << 8, brick id, bx | by << 16)
+  uint4* tile;          // [max_tiles] (first record, count | bz << 8 | job << 21, brick id, bx | by << 16)
   float4* srt_pw;       // [Q] records' (position, weight) in brick order (the Ray Index Table payload)
   float4* srt_qd;       // [Q] records' (record index as bits, ray direction) in brick order
   uint32_t* rec_ray;    // [Q] ray of each record (backward and RIT export only; may be null)
@@ -109,6 +109,40 @@ struct BrickBox {
 };
 BrickBox brick_box(const GridGeo& geo, int elem_bytes);
 cicero_status encode_brick_map(const cicero_grid* grid, const GridGeo& geo, const BrickBox& box, CUtensorMap* map);
+
+// One job of a batched render as the kernels read it from the workspace.  Aligned like its first
+// member, so the tensor map at its start is a valid TMA descriptor in global memory.
+struct JobDesc {  // aligned as CUtensorMap (64 bytes or more)
+  CUtensorMap map;   // the job's feature grid, viewed as for a single render
+  GridGeo geo;
+  Samp samp;
+  ViewCam cam;
+  MlpPtrs mlp;
+  const void* density;
+  float* rgb;        // [H*W][3]
+  float* depth;      // [H*W] or NULL
+  int ray_base;      // first ray of the job in the batch's ray numbering
+  int brick_base;    // first brick of the job in the batch's brick numbering
+  int n_rays, nb;
+};
+constexpr int kMaxBatchJobs = 2048;  // the job index rides in 11 bits of a tile descriptor
+
+// Host side of a planned batch (the public cicero_batch handle wraps it).
+struct BatchPlan {
+  int n_jobs;
+  const JobDesc* jobs;  // device copy, in the workspace
+  const int* bases;     // device: first ray of each job [n_jobs], then first brick of each job [n_jobs]
+  RenderPlan plan;      // totals: rays, records, bricks, tiles
+  RenderWs ws;
+  BrickBox box;
+  bool f16;
+  int C, n_freq;
+  void* workspace;
+  size_t ws_bytes;
+};
+size_t batch_table_bytes(int n_jobs);
+cicero_status run_render_batch(const BatchPlan& b, cudaStream_t st);
+cicero_status launch_gather_mlp_bf16_batch(const BatchPlan& b, cudaStream_t st);
 
 // BF16 tensor-core Feature Computation (mlp_tc.cu)
 cicero_status launch_gather_mlp_bf16(const cicero_grid* grid, const GridGeo& geo, const Samp& samp, const RaySrc& src,

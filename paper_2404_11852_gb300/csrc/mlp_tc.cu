@@ -20,6 +20,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 
 #include "common.cuh"
 #include "internal.h"
@@ -45,7 +46,9 @@ struct Smem {
   static constexpr int b2 = b1 + kHidden * 4;                  // [128] f32
   static constexpr int b3 = b2 + kHidden * 4;                  // [4] f32
   static constexpr int bars = ((b3 + 16 + 127) / 128) * 128;   // per group 2 mbarriers; TMEM address at +96
-  static constexpr int groups = bars + 128;                    // per group: activations, then brick tile
+  static constexpr int geo = bars + 128;                       // batch: geometry of the current job
+  static constexpr int groups = geo + 128;                     // per group: activations, then brick tile
+  static_assert(sizeof(GridGeo) <= 128, "job geometry slot");
   static_assert(groups % 128 == 0 && w2 % 16 == 0 && w3 % 16 == 0, "alignment");
 };
 
@@ -482,11 +485,11 @@ __device__ __forceinline__ void tmem_free_all(uint32_t tmem) {
   }
 }
 
-// CTA prologue shared by both kernels: weights, barriers, TMEM; returns the group handle.
-__device__ __forceinline__ Group setup(char* sm, const MlpPtrs& mlp, int groups, int box_bytes) {
+// CTA prologue shared by the kernels: weights (unless NULL), barriers, TMEM; returns the group handle.
+__device__ __forceinline__ Group setup(char* sm, const MlpPtrs* mlp, int groups, int box_bytes) {
   uint64_t* bars = (uint64_t*)(sm + Smem::bars);
   uint32_t* tslot = (uint32_t*)(sm + Smem::bars + 96);
-  load_weights(sm, mlp);
+  if (mlp) load_weights(sm, *mlp);
   if (threadIdx.x == 0) {
     for (int i = 0; i < 2 * groups; i++) mbar_init(&bars[i], 1);
     fence_mbar_init();
@@ -511,23 +514,20 @@ __device__ __forceinline__ Group setup(char* sm, const MlpPtrs& mlp, int groups,
 
 }  // namespace tc
 
-// The persistent gather + MLP kernel of the BF16 path (launched with 128 * groups threads).
-// Each group software-pipelines its tiles: while layer 3 of tile t runs on the tensor cores (its A
-// operand is in TMEM, so shared memory is free), the group gathers tile t + 1 into its A buffer.
+// One group's tiles [t_begin, t_end) through gather + MLP, software-pipelined: while layer 3 of
+// tile t runs on the tensor cores (its A operand is in TMEM, so shared memory is free), the group
+// gathers tile t + 1 into its A buffer.  `loaded` is the brick held in the group's tile buffer
+// (global brick ids, so it stays valid across calls).  Returns false if a bounded wait ran out;
+// with alive false on entry it does nothing.
+// The grid's geometry `g` and the MLP dimensions are read where they live (kernel parameters for
+// one grid, the job table for a batch); `map` is the generic address of the feature grid's tensor map.
 template <typename T, int CC, int NF>
-__global__ void __launch_bounds__(512, 1) k_gather_mlp_bf16(GridGeo g, int S, MlpPtrs mlp, RenderWs w,
-                                                            const __grid_constant__ CUtensorMap fmap, int vb, int vx,
-                                                            int box_bytes, int groups) {
+__device__ __forceinline__ bool gather_tiles(char* sm, tc::Group& G, const GridGeo& g, const CUtensorMap* map,
+                                             int in_dim, int n_freq, int vb, int vx, int box_bytes, const RenderWs& w,
+                                             long long t_begin, long long t_end, int& loaded, bool alive) {
   using namespace tc;
-  extern __shared__ __align__(1024) char sm[];
-  Group G = setup(sm, mlp, groups, box_bytes);
-  const uint32_t tmem_base = G.tmem - (uint32_t)(G.g * 128);
-  const uint32_t n_tiles = w.hdr[1];
-  const uint32_t per = (n_tiles + gridDim.x - 1) / gridDim.x;
-  const uint32_t c_begin = blockIdx.x * per, c_end = min(n_tiles, c_begin + per);
-  const uint32_t span = c_end > c_begin ? c_end - c_begin : 0;
-  const long long t_begin = c_begin + (span * G.g) / groups, t_end = c_begin + (span * (G.g + 1)) / groups;
-  const int B = g.brick, C = CC ? CC : g.C, m = G.m, in_dim = mlp.in_dim;
+  if (!alive) return false;
+  const int B = g.brick, C = CC ? CC : g.C, m = G.m;
   const T* tile = (const T*)G.tile;
   // Tile descriptors run two tiles ahead of the gather and record payloads one tile ahead, and a
   // payload load is never conditional on loaded data (rows past a tile's count re-read its last
@@ -540,7 +540,8 @@ __global__ void __launch_bounds__(512, 1) k_gather_mlp_bf16(GridGeo g, int S, Ml
   };
   auto tma_brick = [&](const uint4& d) {
     mbar_expect_tx(G.bar_tma, (uint32_t)box_bytes);
-    tma_load_3d(G.tile, &fmap, (int)(d.w & 0xFFFFu) * B * C, (int)(d.w >> 16) * B, (int)(d.y >> 8) * B, G.bar_tma);
+    tma_load_3d(G.tile, map, (int)(d.w & 0xFFFFu) * B * C, (int)(d.w >> 16) * B, (int)((d.y >> 8) & 0x1FFFu) * B,
+                G.bar_tma);
   };
   // tg: the tile gathered in iteration ti (= tile ti + 1), tg1 the one after it
   uint4 tg = t_begin < t_end ? w.tile[t_begin] : none;
@@ -561,8 +562,7 @@ __global__ void __launch_bounds__(512, 1) k_gather_mlp_bf16(GridGeo g, int S, Ml
                                   sigmoid_fast(o3[2] + b3[2]), ow);
     osid = kNoRecord;
   };
-  int loaded = -1;
-  bool alive = true, tma_pending = false, mma_pending = false;
+  bool tma_pending = false, mma_pending = false;
   if (t_begin < t_end) {
     if (m == 0) tma_brick(tg);
     loaded = (int)tg.z;
@@ -626,7 +626,7 @@ __global__ void __launch_bounds__(512, 1) k_gather_mlp_bf16(GridGeo g, int S, Ml
         tma_pending = false;
       }
       const int mcnt = (int)(tg.y & 0xFFu);
-      const int bx = (int)(tg.w & 0xFFFFu), by = (int)(tg.w >> 16), bz = (int)(tg.y >> 8);
+      const int bx = (int)(tg.w & 0xFFFFu), by = (int)(tg.w >> 16), bz = (int)((tg.y >> 8) & 0x1FFFu);
       float x[kK1];
 #pragma unroll
       for (int j = 0; j < kK1; j++) x[j] = 0.0f;
@@ -651,7 +651,7 @@ __global__ void __launch_bounds__(512, 1) k_gather_mlp_bf16(GridGeo g, int S, Ml
         else
           tri_tile<T, CC>(tile, vb, vx, C, l, f, x);
         const float d[3] = {gdir.y, gdir.z, gdir.w};
-        encode_dir_fast<NF>(d, mlp.n_freq, x + C);
+        encode_dir_fast<NF>(d, n_freq, x + C);
         if (in_dim < kK1) x[CC && NF ? (CC + 3 + 6 * NF) % kK1 : in_dim % kK1] = 1.0f;  // folded layer-1 bias
       }
 #pragma unroll
@@ -684,6 +684,65 @@ __global__ void __launch_bounds__(512, 1) k_gather_mlp_bf16(GridGeo g, int S, Ml
   if (alive) write_out();
   if (tma_pending) mbar_wait(G.bar_tma, G.ph_tma, &w.hdr[0]);  // a copy may still be landing (bounded)
   if (mma_pending) mbar_wait(G.bar_mma, G.ph_mma, &w.hdr[0]);  // MMAs may still be running (bounded)
+  return alive;
+}
+
+// The persistent gather + MLP kernel of the BF16 path for one grid (launched with 128 * groups
+// threads): each CTA takes a contiguous range of tiles, split evenly among its groups.
+template <typename T, int CC, int NF>
+__global__ void __launch_bounds__(512, 1) k_gather_mlp_bf16(GridGeo g, int S, MlpPtrs mlp, RenderWs w,
+                                                            const __grid_constant__ CUtensorMap fmap, int vb, int vx,
+                                                            int box_bytes, int groups) {
+  using namespace tc;
+  extern __shared__ __align__(1024) char sm[];
+  Group G = setup(sm, &mlp, groups, box_bytes);
+  const uint32_t tmem_base = G.tmem - (uint32_t)(G.g * 128);
+  const uint32_t n_tiles = w.hdr[1];
+  const uint32_t per = (n_tiles + gridDim.x - 1) / gridDim.x;
+  const uint32_t c_begin = blockIdx.x * per, c_end = min(n_tiles, c_begin + per);
+  const uint32_t span = c_end > c_begin ? c_end - c_begin : 0;
+  const long long t_begin = c_begin + (span * G.g) / groups, t_end = c_begin + (span * (G.g + 1)) / groups;
+  int loaded = -1;
+  gather_tiles<T, CC, NF>(sm, G, g, &fmap, mlp.in_dim, mlp.n_freq, vb, vx, box_bytes, w, t_begin, t_end, loaded, true);
+  tmem_free_all(tmem_base);
+}
+
+// The batched version: like the kernel above, each CTA takes a contiguous range of the tile list
+// (ordered job after job), split into pieces at job boundaries; at the start of each piece the
+// CTA stages the job's geometry in shared memory and loads its MLP weights if they differ from
+// the ones there, and the piece is split evenly among the groups.
+template <typename T, int CC, int NF>
+__global__ void __launch_bounds__(512, 1) k_gather_mlp_bf16_batch(const JobDesc* __restrict__ jobs, int n_jobs,
+                                                                  RenderWs w, int vb, int vx, int box_bytes,
+                                                                  int groups) {
+  using namespace tc;
+  extern __shared__ __align__(1024) char sm[];
+  Group G = setup(sm, nullptr, groups, box_bytes);
+  const uint32_t tmem_base = G.tmem - (uint32_t)(G.g * 128);
+  const uint32_t n_tiles = w.hdr[1];
+  const uint32_t per = (n_tiles + gridDim.x - 1) / gridDim.x;
+  const long long c0 = (long long)blockIdx.x * per, c1 = min((long long)n_tiles, c0 + per);
+  GridGeo& geo = *(GridGeo*)(sm + Smem::geo);  // the current job's geometry, read by every group
+  const float* cur_w1 = nullptr;
+  int loaded = -1;
+  bool alive = true;
+  for (long long a = c0; a < c1;) {
+    const JobDesc& J = jobs[(w.tile[a].y >> 21) & 0x7FFu];
+    const long long b = min(c1, (long long)w.tile_off[J.brick_base + J.nb]);
+    __syncthreads();  // every group is done with the previous job's geometry (and weights)
+    if (threadIdx.x == 0) geo = J.geo;
+    if (J.mlp.w1 != cur_w1) {
+      load_weights(sm, J.mlp);
+      fence_proxy_async();
+      cur_w1 = J.mlp.w1;
+    }
+    __syncthreads();
+    const long long span = b - a;
+    const long long t0 = a + (span * G.g) / groups, t1 = a + (span * (G.g + 1)) / groups;
+    alive = gather_tiles<T, CC, NF>(sm, G, geo, &J.map, J.mlp.in_dim, J.mlp.n_freq, vb, vx, box_bytes, w, t0, t1,
+                                    loaded, alive);
+    a = b;
+  }
   tmem_free_all(tmem_base);
 }
 
@@ -691,7 +750,7 @@ __global__ void __launch_bounds__(512, 1) k_gather_mlp_bf16(GridGeo g, int S, Ml
 __global__ void __launch_bounds__(512, 1) k_mlp_eval_bf16(MlpPtrs mlp, const float* x, int M, float* c, uint32_t* err) {
   using namespace tc;
   extern __shared__ __align__(1024) char sm[];
-  Group G = setup(sm, mlp, kMaxGroups, 0);
+  Group G = setup(sm, &mlp, kMaxGroups, 0);
   const uint32_t tmem_base = G.tmem - (uint32_t)(G.g * 128);
   const int ntile = (M + kTile - 1) / kTile;
   bool alive = true;
@@ -750,6 +809,38 @@ cicero_status launch_gather_mlp_bf16(const cicero_grid* grid, const GridGeo& geo
                : launch_tc<float, 12, 4>(geo, ws.S, mlp, ws, map, box, st);
   return f16 ? launch_tc<__half, 0, 0>(geo, ws.S, mlp, ws, map, box, st)
              : launch_tc<float, 0, 0>(geo, ws.S, mlp, ws, map, box, st);
+}
+
+template <typename T, int CC, int NF>
+static cicero_status launch_tc_batch(const BatchPlan& b, cudaStream_t st) {
+  using namespace tc;
+  int groups = kMaxGroups;
+  while (groups > 1 && Smem::groups + groups * group_bytes(b.box.box_bytes) > 227 * 1024) groups--;
+  int smem = Smem::groups + groups * group_bytes(b.box.box_bytes);
+  if (smem > 227 * 1024) return fail(CICERO_ERR_UNSUPPORTED, "brick too large for the tensor-core kernel");
+  smem = std::max(smem, 120 * 1024);  // one CTA per SM: it owns all 512 TMEM columns
+  auto kern = k_gather_mlp_bf16_batch<T, CC, NF>;
+  // set once per size, so that a launch after the first one is pure kernel launches (graph capture)
+  static std::atomic<int> smem_set{0};
+  cudaError_t e = cudaSuccess;
+  if (smem > smem_set.load()) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_gather_mlp_bf16_batch)");
+    smem_set.store(smem);
+  }
+  {
+    ProfScope ps(kStGatherMlp, st);
+    kern<<<num_sms(), 128 * groups, smem, st>>>(b.jobs, b.n_jobs, b.ws, b.box.vb, b.box.vx, b.box.box_bytes, groups);
+  }
+  count_launches(1);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? CICERO_OK : cuda_fail(e, "k_gather_mlp_bf16_batch");
+}
+
+cicero_status launch_gather_mlp_bf16_batch(const BatchPlan& b, cudaStream_t st) {
+  if (b.C == 12 && b.n_freq == 4)
+    return b.f16 ? launch_tc_batch<__half, 12, 4>(b, st) : launch_tc_batch<float, 12, 4>(b, st);
+  return b.f16 ? launch_tc_batch<__half, 0, 0>(b, st) : launch_tc_batch<float, 0, 0>(b, st);
 }
 
 cicero_status launch_mlp_eval_bf16(const MlpPtrs& mlp, const float* x, int M, float* c, uint32_t* err,

@@ -14,6 +14,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstddef>
+#include <cstring>
 
 #include "common.cuh"
 #include "internal.h"
@@ -26,7 +28,7 @@ size_t render_ws_bytes(const RenderPlan& p) {
   const size_t Q = p.Q, R = (size_t)p.R;
   size_t b = al256(64);
   b += 3 * al256(4 * R) + al256(16 * R);
-  b += al256(4 * Q) + 2 * al256(16 * Q);
+  b += al256(4 * Q) + al256(16 * Q);  // rec_c shares rec_pw's storage (rec_pw is dead after the sort)
   if (p.want_k) b += al256(2 * Q);
   if (p.want_bwd) b += 2 * al256(4 * Q);
   if (p.want_k || p.want_bwd) b += al256(4 * Q);
@@ -53,7 +55,7 @@ bool carve_render_ws(void* ws, size_t bytes, const RenderPlan& p, RenderWs* w) {
   w->ray_dir = (float4*)take(16 * R);
   w->rec_key = (uint32_t*)take(4 * Q);
   w->rec_pw = (float4*)take(16 * Q);
-  w->rec_c = (float4*)take(16 * Q);
+  w->rec_c = w->rec_pw;
   w->rec_k = p.want_k ? (uint16_t*)take(2 * Q) : nullptr;
   w->rec_T = p.want_bwd ? (float*)take(4 * Q) : nullptr;
   w->rec_raw = p.want_bwd ? (float*)take(4 * Q) : nullptr;
@@ -117,126 +119,201 @@ __device__ __forceinline__ float one_minus_exp_neg(float x) {
   return x < 0.03125f ? series : 1.0f - __expf(-x);
 }
 
-// K1: one warp per ray; lane = slot within a chunk of 32 slots.
-template <typename T>
-__global__ void __launch_bounds__(256) k_march(GridGeo g, Samp s, RaySrc src, const T* __restrict__ dens,
-                                               RenderWs w, OutBufs out) {
+constexpr int kStage = 256;  // records a warp stages in shared memory before reserving them
+
+// Brick histogram of n consecutive records with keys key(j), one atomic per run of equal keys,
+// adding `sign` per record (-1 takes back the counts of records that found no room).
+template <typename KeyAt>
+__device__ __forceinline__ void count_bricks(const RenderWs& w, uint32_t n, KeyAt key_at, int sign) {
   const int lane = threadIdx.x & 31;
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  const int R = ray_count(src);
+  const unsigned full = 0xffffffffu;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  const unsigned le_mask = (2u << lane) - 1u;
+  for (uint32_t j0 = 0; j0 < n; j0 += 32) {
+    const uint32_t j = j0 + lane;
+    const bool v = j < n;
+    const uint32_t key = v ? key_at(j) : 0xffffffffu;
+    const unsigned vmask = __ballot_sync(full, v);
+    const uint32_t prev = __shfl_up_sync(full, key, 1);
+    const bool head = v && (lane == 0 || prev != key);
+    const unsigned heads = __ballot_sync(full, head);
+    if (head) {
+      const unsigned after = heads & ~le_mask;
+      const int end = after ? __ffs(after) - 1 : 32;
+      const unsigned run = vmask & ~lt_mask & (end == 32 ? full : ((1u << end) - 1u));
+      atomicAdd(&w.brick_cnt[key], (uint32_t)(sign * __popc(run)));
+    }
+  }
+}
+
+// K1 per ray (one warp; lane = slot within a chunk of 32 slots).  Records carry the brick id
+// offset by key_base (the job's first brick in a batch); dep/acc/steps point at the ray's outputs
+// (or are NULL).  When the caller capped the record capacity below rays x samples, a ray that can
+// emit at most kStage records (and no backward / RIT extras) stages them in the warp's shared
+// buffers st_pw/st_key and reserves exactly its count at the end, so the capacity follows the
+// samples actually composited; otherwise rays reserve their upper bound up front (faster).
+template <typename T>
+__device__ __forceinline__ void march_ray(const GridGeo& g, const Samp& s, const T* __restrict__ dens,
+                                          const RenderWs& w, int r, const float o[3], const float d[3],
+                                          uint32_t key_base, float* dep, float* acc_out, int32_t* steps_out,
+                                          float4* st_pw, uint32_t* st_key, int tag = 0) {
+  const int lane = threadIdx.x & 31;
   const unsigned full = 0xffffffffu;
   const unsigned lt_mask = (1u << lane) - 1u;
   const unsigned le_mask = (2u << lane) - 1u;  // lanes <= this one (all ones for lane 31)
-  for (int r = warp; r < R; r += nwarps) {
-    const RayRef rr = ray_ref(src, r);
-    float o[3], d[3];
-    ray_gen(src, rr, o, d);
-    const Slots sl = place_slots(g, s, o, d);
-    const int bound = record_bound(g, sl, o, d);
-    uint32_t base = 0;
+  const Slots sl = place_slots(g, s, o, d);
+  const int bound = record_bound(g, sl, o, d);
+  // exact reservation pays only when the caller capped the capacity below the worst case
+  const bool capped = (unsigned long long)w.Q < (unsigned long long)w.R * (unsigned long long)w.S;
+  const bool staged = capped && bound <= kStage && !w.rec_k && !w.rec_ray && !w.rec_T;
+  uint32_t base = 0;
+  if (!staged) {
     if (lane == 0 && bound > 0) base = atomicAdd(&w.hdr[3], (uint32_t)bound);
     base = __shfl_sync(full, base, 0);
-    const bool room = (unsigned long long)base + (unsigned)bound <= (unsigned long long)w.Q;
-    if (!room && lane == 0) set_err(&w.hdr[0], kErrCapacity);
-    float Ssum = 0.0f, acc_l = 0.0f, dsum_l = 0.0f;
-    uint32_t cnt = 0;
-    int steps = sl.n;
-    for (int k0 = 0; k0 < sl.n; k0 += 32) {
-      const int k = k0 + lane;
-      const float t = slot_t(sl, k);
-      const bool valid = slot_valid(sl, k, t);
-      const unsigned vmask = __ballot_sync(full, valid);
-      if (!vmask) {
+  }
+  const bool room = staged || (unsigned long long)base + (unsigned)bound <= (unsigned long long)w.Q;
+  if (!room && lane == 0) set_err(&w.hdr[0], kErrCapacity);
+  float Ssum = 0.0f, acc_l = 0.0f, dsum_l = 0.0f;
+  uint32_t cnt = 0;
+  int steps = sl.n;
+  for (int k0 = 0; k0 < sl.n; k0 += 32) {
+    const int k = k0 + lane;
+    const float t = slot_t(sl, k);
+    const bool valid = slot_valid(sl, k, t);
+    const unsigned vmask = __ballot_sync(full, valid);
+    if (!vmask) {
+      steps = k0;
+      break;
+    }
+    int i0[3] = {0, 0, 0};
+    float f[3], p[3] = {0.0f, 0.0f, 0.0f};
+    bool act = false;
+    if (valid) {
+      sample_pos(o, d, t, p);
+      act = index_sample(g, p, i0, f);
+    }
+    if (!__any_sync(full, act)) {  // nothing to composite in these slots: only the stop test
+      if (s.t_stop > 0.0f && __expf(-(Ssum + 0.0f)) < s.t_stop) {
         steps = k0;
-        break;
-      }
-      int i0[3] = {0, 0, 0};
-      float f[3], p[3] = {0.0f, 0.0f, 0.0f};
-      bool act = false;
-      if (valid) {
-        sample_pos(o, d, t, p);
-        act = index_sample(g, p, i0, f);
-      }
-      if (!__any_sync(full, act)) {  // nothing to composite in these slots: only the stop test
-        if (s.t_stop > 0.0f && __expf(-(Ssum + 0.0f)) < s.t_stop) {
-          steps = k0;
-          break;
-        }
-        if (vmask != full) {
-          steps = k0 + __popc(vmask);
-          break;
-        }
-        continue;
-      }
-      float sd = 0.0f, raw = 0.0f;
-      if (act) {
-        raw = density_trilinear(g, dens, i0, f);
-        sd = softplus_fast(raw + g.act_shift) * sl.dt;
-      }
-      float incl = sd;
-#pragma unroll
-      for (int off = 1; off < 32; off <<= 1) {
-        const float v = __shfl_up_sync(full, incl, off);
-        if (lane >= off) incl += v;
-      }
-      float excl = __shfl_up_sync(full, incl, 1);
-      if (lane == 0) excl = 0.0f;
-      const float Tk = __expf(-(Ssum + excl));
-      const bool stop = valid && s.t_stop > 0.0f && Tk < s.t_stop;
-      const unsigned smask = __ballot_sync(full, stop);
-      const int first = smask ? __ffs(smask) - 1 : 32;
-      const bool contrib = act && lane < first && room;
-      const float wk = (act && lane < first) ? Tk * one_minus_exp_neg(sd) : 0.0f;
-      const unsigned cmask = __ballot_sync(full, contrib);
-      const uint32_t key = contrib ? brick_id(g, i0) : 0xffffffffu;
-      if (contrib) {
-        const size_t q = (size_t)base + cnt + __popc(cmask & lt_mask);
-        w.rec_pw[q] = make_float4(p[0], p[1], p[2], wk);
-        w.rec_key[q] = key;
-        if (w.rec_k) w.rec_k[q] = (uint16_t)k;
-        if (w.rec_ray) w.rec_ray[q] = (uint32_t)r;
-        if (w.rec_T) {
-          w.rec_T[q] = Tk;
-          w.rec_raw[q] = raw;
-        }
-      }
-      // brick histogram: one atomic per run of consecutive lanes with the same brick
-      const uint32_t prev = __shfl_up_sync(full, key, 1);
-      const bool head = contrib && (lane == 0 || prev != key);
-      const unsigned heads = __ballot_sync(full, head);
-      if (head) {
-        const unsigned after = heads & ~le_mask;
-        const int end = after ? __ffs(after) - 1 : 32;
-        const unsigned run = cmask & ~lt_mask & (end == 32 ? full : ((1u << end) - 1u));
-        atomicAdd(&w.brick_cnt[key], (uint32_t)__popc(run));
-      }
-      acc_l += wk;
-      dsum_l += wk * t;
-      cnt += __popc(cmask);
-      const int last = first == 32 ? 31 : first - 1;
-      const float tot = __shfl_sync(full, incl, last < 0 ? 0 : last);
-      if (first > 0) Ssum += tot;
-      if (first < 32) {
-        steps = k0 + first;
         break;
       }
       if (vmask != full) {
         steps = k0 + __popc(vmask);
         break;
       }
+      continue;
     }
-    const float acc = warp_sum(acc_l), dsum = warp_sum(dsum_l);
-    if (lane == 0) {
-      w.ray_n[r] = cnt;
-      w.ray_start[r] = base;
-      w.ray_T[r] = __expf(-Ssum);
-      w.ray_dir[r] = make_float4(d[0], d[1], d[2], 0.0f);
-      float* dep = out.depth[rr.view];
-      if (dep) dep[rr.pix] = acc >= s.void_acc ? dsum / acc : __int_as_float(0x7f800000);
-      if (out.acc) out.acc[rr.pix] = acc;
-      if (out.n_steps) out.n_steps[rr.pix] = steps;
+    float sd = 0.0f, raw = 0.0f;
+    if (act) {
+      raw = density_trilinear(g, dens, i0, f);
+      sd = softplus_fast(raw + g.act_shift) * sl.dt;
     }
+    float incl = sd;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const float v = __shfl_up_sync(full, incl, off);
+      if (lane >= off) incl += v;
+    }
+    float excl = __shfl_up_sync(full, incl, 1);
+    if (lane == 0) excl = 0.0f;
+    const float Tk = __expf(-(Ssum + excl));
+    const bool stop = valid && s.t_stop > 0.0f && Tk < s.t_stop;
+    const unsigned smask = __ballot_sync(full, stop);
+    const int first = smask ? __ffs(smask) - 1 : 32;
+    const bool contrib = act && lane < first && room;
+    const float wk = (act && lane < first) ? Tk * one_minus_exp_neg(sd) : 0.0f;
+    const unsigned cmask = __ballot_sync(full, contrib);
+    const uint32_t key = contrib ? key_base + brick_id(g, i0) : 0xffffffffu;
+    if (staged) {
+      if (contrib) {
+        const uint32_t j = cnt + __popc(cmask & lt_mask);
+        st_pw[j] = make_float4(p[0], p[1], p[2], wk);
+        st_key[j] = key;
+      }
+    } else if (contrib) {
+      const size_t q = (size_t)base + cnt + __popc(cmask & lt_mask);
+      w.rec_pw[q] = make_float4(p[0], p[1], p[2], wk);
+      w.rec_key[q] = key;
+      if (w.rec_k) w.rec_k[q] = (uint16_t)k;
+      if (w.rec_ray) w.rec_ray[q] = (uint32_t)r;
+      if (w.rec_T) {
+        w.rec_T[q] = Tk;
+        w.rec_raw[q] = raw;
+      }
+    }
+    // brick histogram: one atomic per run of consecutive lanes with the same brick
+    const uint32_t prev = __shfl_up_sync(full, key, 1);
+    const bool head = contrib && (lane == 0 || prev != key);
+    const unsigned heads = __ballot_sync(full, head);
+    if (head) {
+      const unsigned after = heads & ~le_mask;
+      const int end = after ? __ffs(after) - 1 : 32;
+      const unsigned run = cmask & ~lt_mask & (end == 32 ? full : ((1u << end) - 1u));
+      atomicAdd(&w.brick_cnt[key], (uint32_t)__popc(run));
+    }
+    acc_l += wk;
+    dsum_l += wk * t;
+    cnt += __popc(cmask);
+    const int last = first == 32 ? 31 : first - 1;
+    const float tot = __shfl_sync(full, incl, last < 0 ? 0 : last);
+    if (first > 0) Ssum += tot;
+    if (first < 32) {
+      steps = k0 + first;
+      break;
+    }
+    if (vmask != full) {
+      steps = k0 + __popc(vmask);
+      break;
+    }
+  }
+  if (staged) {
+    // reserve exactly the composited records and copy them out
+    __syncwarp();
+    if (lane == 0 && cnt) base = atomicAdd(&w.hdr[3], cnt);
+    base = __shfl_sync(full, base, 0);
+    if ((unsigned long long)base + cnt <= (unsigned long long)w.Q) {
+      for (uint32_t j = lane; j < cnt; j += 32) {
+        w.rec_pw[(size_t)base + j] = st_pw[j];
+        w.rec_key[(size_t)base + j] = st_key[j];
+      }
+    } else {
+      // no room: take the records back out of the histogram; the ray composites nothing and the
+      // error is reported
+      if (lane == 0) set_err(&w.hdr[0], kErrCapacity);
+      count_bricks(w, cnt, [&](uint32_t j) { return st_key[j]; }, -1);
+      cnt = 0;
+    }
+    __syncwarp();  // the staging buffers are free for the warp's next ray
+  }
+  const float acc = warp_sum(acc_l), dsum = warp_sum(dsum_l);
+  if (lane == 0) {
+    w.ray_n[r] = cnt;
+    w.ray_start[r] = base;
+    w.ray_T[r] = __expf(-Ssum);
+    w.ray_dir[r] = make_float4(d[0], d[1], d[2], __int_as_float(tag));  // tag: the ray's job in a batch
+    if (dep) *dep = acc >= s.void_acc ? dsum / acc : __int_as_float(0x7f800000);
+    if (acc_out) *acc_out = acc;
+    if (steps_out) *steps_out = steps;
+  }
+}
+
+// K1: one warp per ray.
+template <typename T>
+__global__ void __launch_bounds__(256) k_march(GridGeo g, Samp s, RaySrc src, const T* __restrict__ dens,
+                                               RenderWs w, OutBufs out) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  const int R = ray_count(src);
+  __shared__ float4 st_pw[8][kStage];
+  __shared__ uint32_t st_key[8][kStage];
+  const int wb = threadIdx.x >> 5;
+  for (int r = warp; r < R; r += nwarps) {
+    const RayRef rr = ray_ref(src, r);
+    float o[3], d[3];
+    ray_gen(src, rr, o, d);
+    float* dep = out.depth[rr.view];
+    march_ray<T>(g, s, dens, w, r, o, d, 0u, dep ? dep + rr.pix : nullptr, out.acc ? out.acc + rr.pix : nullptr,
+                 out.n_steps ? out.n_steps + rr.pix : nullptr, st_pw[wb], st_key[wb]);
   }
 }
 
@@ -624,7 +701,7 @@ __global__ void __launch_bounds__(256, 1) k_gather_mlp_f32(GridGeo g, int S, Mlp
     const int b = (int)td.z;
     const uint32_t start = td.x;
     const int mcnt = (int)(td.y & 0xFFu);
-    const int bx = (int)(td.w & 0xFFFFu), by = (int)(td.w >> 16), bz = (int)(td.y >> 8);
+    const int bx = (int)(td.w & 0xFFFFu), by = (int)(td.w >> 16), bz = (int)((td.y >> 8) & 0x1FFFu);
     if (b != loaded) {
       __syncthreads();
       if (threadIdx.x == 0) {
@@ -699,6 +776,113 @@ __global__ void __launch_bounds__(256) k_composite(RaySrc src, Samp s, RenderWs 
       rgb[3 * rr.pix + 0] = a0 + T * s.bg[0];
       rgb[3 * rr.pix + 1] = a1 + T * s.bg[1];
       rgb[3 * rr.pix + 2] = a2 + T * s.bg[2];
+    }
+  }
+}
+
+// -------------------------------------------------------------------------------------------
+// Batched render: every ray of every job in one launch per stage.  Rays are numbered job after
+// job, and so are bricks, so bucketing, scan and scatter run unchanged on the batch.
+
+// The job whose first ray (or first brick) is the largest one <= x, from the contiguous array of
+// the jobs' first rays (or bricks).
+__device__ __forceinline__ int job_of(const int* __restrict__ base, int n_jobs, int x) {
+  int lo = 0, hi = n_jobs;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(&base[mid]) <= x) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// Per-warp copy of the current job's geometry and sampling in shared memory, refreshed when the
+// warp's ray belongs to another job (the march reads them there, not from registers).
+struct JobCache {
+  GridGeo g;
+  Samp s;
+  int job;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_march_batch(const JobDesc* __restrict__ jobs, const int* __restrict__ bases,
+                                                     int n_jobs, int R, RenderWs w) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  __shared__ float4 st_pw[8][kStage];
+  __shared__ uint32_t st_key[8][kStage];
+  __shared__ JobCache cache[8];
+  const int wb = threadIdx.x >> 5;
+  JobCache& C = cache[wb];
+  if (lane == 0) C.job = -1;
+  __syncwarp();
+  for (int r = warp; r < R; r += nwarps) {
+    const int j = job_of(bases, n_jobs, r);
+    const JobDesc& J = jobs[j];
+    if (C.job != j) {
+      __syncwarp();
+      constexpr int kWords = (int)((sizeof(GridGeo) + sizeof(Samp)) / 4);
+      static_assert(offsetof(JobCache, s) == sizeof(GridGeo), "cache layout");
+      static_assert(offsetof(JobDesc, samp) == offsetof(JobDesc, geo) + sizeof(GridGeo), "job layout");
+      const uint32_t* src = (const uint32_t*)&J.geo;
+      uint32_t* dst = (uint32_t*)&C.g;
+      for (int k = lane; k < kWords; k += 32) dst[k] = src[k];
+      if (lane == 0) C.job = j;
+      __syncwarp();
+    }
+    const int pix = r - J.ray_base;
+    float o[3], d[3];
+    ray_gen_cam(J.cam, pix, o, d);
+    march_ray<T>(C.g, C.s, (const T*)J.density, w, r, o, d, (uint32_t)J.brick_base, J.depth ? J.depth + pix : nullptr,
+                 nullptr, nullptr, st_pw[wb], st_key[wb], j);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_tiles_batch(const JobDesc* __restrict__ jobs, const int* __restrict__ bases,
+                                                     int n_jobs, RenderWs w) {
+  const uint32_t n = w.hdr[1];
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    int lo = 0, hi = w.nb;  // largest b with tile_off[b] <= t
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (w.tile_off[mid] <= t) lo = mid;
+      else hi = mid;
+    }
+    const uint32_t start = w.brick_off[lo] + (t - w.tile_off[lo]) * kTile;
+    const uint32_t cnt = min(start + (uint32_t)kTile, w.brick_off[lo + 1]) - start;
+    const int j = job_of(bases + n_jobs, n_jobs, lo);
+    const int* nb = jobs[j].geo.nb;
+    const uint32_t b = (uint32_t)(lo - jobs[j].brick_base);
+    const uint32_t bx = b % nb[0], by = (b / nb[0]) % nb[1], bz = b / (nb[0] * nb[1]);
+    w.tile[t] = make_uint4(start, cnt | (bz << 8) | ((uint32_t)j << 21), (uint32_t)lo, bx | (by << 16));
+  }
+}
+
+__global__ void __launch_bounds__(256) k_composite_batch(const JobDesc* __restrict__ jobs, int n_jobs, int R,
+                                                         RenderWs w) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int r = warp; r < R; r += nwarps) {
+    const uint32_t n = w.ray_n[r], start = w.ray_start[r];
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+    for (uint32_t j = lane; j < n; j += 32) {
+      const float4 v = w.rec_c[start + j];
+      a0 += v.w * v.x;
+      a1 += v.w * v.y;
+      a2 += v.w * v.z;
+    }
+    a0 = warp_sum(a0);
+    a1 = warp_sum(a1);
+    a2 = warp_sum(a2);
+    if (lane == 0) {
+      const JobDesc& J = jobs[__float_as_int(w.ray_dir[r].w)];  // the job the march tagged the ray with
+      const int pix = r - J.ray_base;
+      const float T = w.ray_T[r];
+      J.rgb[3 * pix + 0] = a0 + T * J.samp.bg[0];
+      J.rgb[3 * pix + 1] = a1 + T * J.samp.bg[1];
+      J.rgb[3 * pix + 2] = a2 + T * J.samp.bg[2];
     }
   }
 }
@@ -799,6 +983,46 @@ cicero_status run_render(const cicero_grid* grid, const MlpPtrs& mlp, const Rend
   count_launches(1);
   e = cudaGetLastError();
   return e == cudaSuccess ? CICERO_OK : cuda_fail(e, "k_composite");
+}
+
+cicero_status run_render_batch(const BatchPlan& b, cudaStream_t st) {
+  const RenderPlan& plan = b.plan;
+  const RenderWs& ws = b.ws;
+  const int R = plan.R;
+  if (R == 0) return CICERO_OK;
+  RaySrc src;
+  memset(&src, 0, sizeof src);
+  src.n_max = R;
+  const int mb = blocks_for_warps(R, 16);
+  {
+    ProfScope ps(kStMarch, st);
+    k_clear<<<std::min(num_sms() * 4, (plan.nb + 255) / 256 + 1), 256, 0, st>>>(ws.hdr, 16, ws.brick_cnt, plan.nb);
+    if (b.f16)
+      k_march_batch<__half><<<mb, 256, 0, st>>>(b.jobs, b.bases, b.n_jobs, R, ws);
+    else
+      k_march_batch<float><<<mb, 256, 0, st>>>(b.jobs, b.bases, b.n_jobs, R, ws);
+  }
+  {
+    ProfScope ps(kStBucket, st);
+    const int nblk = (plan.nb + kScanChunk - 1) / kScanChunk;
+    k_brick_sums<<<nblk, 1024, 0, st>>>(ws);
+    k_brick_blocks<<<1, 1024, 0, st>>>(ws, nblk);
+    k_brick_offsets<<<nblk, 1024, 0, st>>>(ws);
+    k_tiles_batch<<<num_sms() * 4, 256, 0, st>>>(b.jobs, b.bases, b.n_jobs, ws);
+    k_scatter<<<mb, 256, 0, st>>>(src, ws);
+  }
+  count_launches(7);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "batched march/bucket kernels");
+  cicero_status s = launch_gather_mlp_bf16_batch(b, st);
+  if (s != CICERO_OK) return s;
+  {
+    ProfScope ps(kStComposite, st);
+    k_composite_batch<<<mb, 256, 0, st>>>(b.jobs, b.n_jobs, R, ws);
+  }
+  count_launches(1);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? CICERO_OK : cuda_fail(e, "k_composite_batch");
 }
 
 cicero_status run_rit_export(const RenderWs& ws, int n_bricks, int S, int32_t* brick_offsets, int32_t* samples,

@@ -94,3 +94,48 @@ def test_invalid_arguments_rejected_on_host(cc):
     # unsupported brick size
     st = L.cicero_render_workspace_size(C.byref(_grid()), 64, C.byref(sp), C.byref(cc.options(0, 5)))
     assert st == 0
+
+
+def _mlp_desc(cc, in_dim=39, n_freq=4):
+    m = cc.Mlp()
+    m.in_dim, m.hidden, m.n_freq = in_dim, 128, n_freq
+    m.w1 = m.b1 = m.w2 = m.b2 = m.w3 = m.b3 = 256
+    return m
+
+
+def test_batch_plan_validated_on_host(cc):
+    L = cc.lib()
+    keep = []
+
+    def job(grid, n_samples=64, w=32, h=24):
+        sp, cam, m = cc.sampling(n_samples=n_samples), cc.camera(w, h, 30.0, w / 2, h / 2, np.eye(3, 4)), _mlp_desc(cc)
+        keep.extend([grid, sp, cam, m])
+        j = cc.Job()
+        j.grid, j.mlp, j.cam, j.sampling = C.addressof(grid), C.addressof(m), C.addressof(cam), C.addressof(sp)
+        j.rgb, j.depth = 256, None
+        return j
+
+    arr = (cc.Job * 3)(job(_grid(dtype=1)), job(_grid(n=(96, 96, 96), dtype=1), 128, 40, 40),
+                       job(_grid(n=(48, 48, 48), dtype=1), 32))
+    bf16 = cc.options(cc.MLP_BF16, 8)
+    size = L.cicero_batch_workspace_size(arr, 3, C.byref(bf16))
+    table = L.cicero_batch_table_bytes(3)
+    assert table >= 3 * 128 and table % 256 == 0
+    rays = 32 * 24 * 2 + 40 * 40
+    records = 32 * 24 * (64 + 32) + 40 * 40 * 128
+    assert size > table + records * 52 + rays * 28  # table + per-record payload + per-ray headers
+    # only the BF16 tensor-core path is batched
+    assert L.cicero_batch_workspace_size(arr, 3, C.byref(cc.options(cc.MLP_FP32, 8))) == 0
+    # jobs must share the grid dtype
+    mixed = (cc.Job * 2)(job(_grid(dtype=1)), job(_grid(dtype=0)))
+    assert L.cicero_batch_workspace_size(mixed, 2, C.byref(bf16)) == 0
+    # job counts
+    assert L.cicero_batch_workspace_size(arr, 0, C.byref(bf16)) == 0
+    assert L.cicero_batch_table_bytes(0) == 0 and L.cicero_batch_table_bytes(2049) == 0
+    # create rejects before touching the GPU
+    h = C.c_void_p()
+    st = L.cicero_batch_create(arr, 3, C.byref(cc.options(cc.MLP_FP32, 8)), C.c_void_p(1 << 20), size, C.byref(h))
+    assert st == cc.ERR_UNSUPPORTED and not h.value
+    st = L.cicero_batch_create(arr, 3, C.byref(bf16), C.c_void_p((1 << 20) + 8), size, C.byref(h))
+    assert st == cc.ERR_INVALID_ARG  # workspace not 256-byte aligned
+    assert L.cicero_batch_launch(None, None) == cc.ERR_INVALID_ARG
