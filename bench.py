@@ -455,6 +455,61 @@ def batched_workload(cc, torch, dev, n_check=8, reps=5):
             "oracle_check": {"pixels": n // 3, "max_err": worst, "psnr_db": 10 * math.log10(1.0 / max(sq / n, 1e-30))}}
 
 
+SWEEP_WINDOWS = (6, 16, 21, 26, 30)
+SWEEP_FRAMES = 120
+
+
+def window_sweep(cc, torch, dev, grid, mlp, o16):
+    """SpaRW over a 120-frame trajectory on the 800x800 scene (the camera orbits the object at
+    0.5 deg of azimuth per frame, looking at it: a 60 deg arc) with the reference of each window
+    rendered on a second stream (cicero_pipeline, Sec. III-C), for windows of 6 .. 30 targets (the
+    paper's window sizes).  Per window size: frames/s overlapped and serialised, speedup over
+    rendering every frame in full (BF16), and PSNR of the frames against those full renders (every
+    pixel; a frame identical to its full render counts as 100 dB in the mean)."""
+    import scenes
+    cam = scenes.orbit_camera(W, H, sampling=scenes.sampling_march(256, 256))
+    traj = [scenes.orbit_camera(W, H, az_deg=30.0 + 0.5 * k, sampling=cam.sampling) for k in range(SWEEP_FRAMES)]
+    targets = [cc.camera_from(t) for t in traj]
+    R = W * H
+    cd, sd = cc.camera_from(cam), cc.sampling_from(cam.sampling)
+    # every frame rendered in full: the speed and the image the warped frames are compared with
+    full = [torch.empty(R, 3, device=dev) for _ in traj]
+    fd = torch.empty(R, device=dev)
+    ws_f = cc.workspace(cc.cicero_render_workspace_size(grid.desc, R, sd, o16), dev)
+
+    def render_all():
+        for t, out in zip(targets, full):
+            cc.cicero_render(grid.desc, mlp.desc, t, sd, o16, out, fd, None, None, ws_f)
+
+    t_full = event_ms(torch, render_all, 1)
+    del ws_f
+    frames = [torch.empty(R, 3, device=dev) for _ in traj]
+    s_ref = torch.cuda.Stream(dev)
+    res = {"frames": SWEEP_FRAMES, "full_render_fps": SWEEP_FRAMES / (t_full / 1e3), "windows": []}
+    for N, lead in [(n, "centred") for n in SWEEP_WINDOWS] + [(16, "paper")]:
+        hole_records = N * R * 40  # ~16% of the window's slots
+        ws = cc.workspace(cc.cicero_pipeline_workspace_size(grid.desc, cd, sd, o16, N, hole_records), dev)
+        p = cc.Pipeline(grid.desc, mlp.desc, cd, sd, o16, N, hole_records, 180.0, ws)
+        refs = cc.reference_poses(targets, N, lead)
+
+        def run(overlap):
+            cur = torch.cuda.current_stream(dev)
+            s_ref.wait_stream(cur)
+            p.run(targets, refs, frames, None, stream_tgt=cur, stream_ref=s_ref if overlap else cur)
+
+        t_ov = event_ms(torch, lambda: run(True), 2)
+        t_se = event_ms(torch, lambda: run(False), 2)
+        p.status()
+        ps = np.minimum([frame_psnr(a.cpu().numpy(), b.cpu().numpy()) for a, b in zip(frames, full)], 100.0)
+        res["windows"].append({"window": N, "lead": lead, "fps_overlapped": SWEEP_FRAMES / (t_ov / 1e3),
+                               "fps_serialised": SWEEP_FRAMES / (t_se / 1e3),
+                               "speedup_vs_full": t_full / t_ov, "psnr_db_mean": float(np.mean(ps)),
+                               "psnr_db_median": float(np.median(ps)), "psnr_db_min": float(np.min(ps))})
+        p.close()
+        del ws
+    return res
+
+
 def backward_workload(cc, torch, dev):
     """Forward + backward over 8192 random rays x 256 samples on the 160^3 x 12 FP32 scene, MSE
     loss against seeded target colours (the differentiation workload)."""
@@ -682,6 +737,7 @@ def main():
         others["config_backward"] = backward_workload(cc, torch, dev)
         others["config_sparw_small_scene"] = sparw_small_scene(cc, torch, dev)
         others["config_batched"] = batched_workload(cc, torch, dev)
+        others["sparw_window_sweep"] = window_sweep(cc, torch, dev, grid, mlp, o16)
 
     if rank == 0:
         line = {

@@ -226,6 +226,48 @@ cicero_status cicero_batch_autotune_brick(const cicero_job *jobs, int n_jobs, co
                                           int *best_brick, float *ms);
 
 /* ---------------------------------------------------------------------------------------------
+ * Reference pose by extrapolation (Sec. III-C, Eq. 5-6): from the two latest camera poses `prev`
+ * and `cur`, one frame interval apart, the velocity v = (cur - prev) / dt (Eq. 5) is applied for
+ * t_r = lead * dt (Eq. 6, where the paper takes lead = N / 2 for N targets per reference):
+ * position = p_cur + lead (p_cur - p_prev).  The paper states the velocity of the position only;
+ * the orientation follows the same rule with the angular velocity: the rotation taken from prev to
+ * cur is applied `lead` more times (shortest arc; FP64, rounded once to FP32).  Intrinsics are
+ * copied from `cur`.  Host only. */
+cicero_status cicero_extrapolate_pose(const cicero_camera *prev, const cicero_camera *cur, float lead,
+                                      cicero_camera *out);
+
+/* ---------------------------------------------------------------------------------------------
+ * SpaRW over a trajectory with reference rendering overlapped (Sec. III-C, "Reference Frame
+ * Rendering"): frames are taken in windows of `window` targets; window w is warped from
+ * reference frame refs[w] (cicero_warp_batch, void test on the pipeline's grid) and its holes
+ * rendered (cicero_render_holes_batch), while reference w + 1 is rendered on `stream_ref`.  With
+ * stream_ref == stream_tgt the same work runs serialised (same results).  Reference poses are the
+ * caller's (for example from cicero_extrapolate_pose); every frame, reference or target, has the
+ * size and intrinsics of `cam`.
+ *
+ * The workspace holds two reference frames and their render workspaces (opt applies to them),
+ * scratch for one window's hole masks and lists, and the hole-batch workspace of `hole_records`
+ * records (opt's max_records for the hole batch).  The handle is host memory owned by the
+ * caller; one run at a time per pipeline (the previous run's work is waited for on the streams,
+ * not on the host).  targets [n_frames] and refs [ceil(n_frames / window)] are host arrays;
+ * rgb / depth are host arrays of n_frames device pointers ([H*W][3] / [H*W]; depth may be NULL).
+ * cicero_pipeline_status reads the error bits of the kernels (synchronises `stream`). */
+typedef struct cicero_pipeline cicero_pipeline;
+
+size_t cicero_pipeline_workspace_size(const cicero_grid *grid, const cicero_camera *cam,
+                                      const cicero_sampling *sampling, const cicero_options *opt, int window,
+                                      long long hole_records);
+cicero_status cicero_pipeline_create(const cicero_grid *grid, const cicero_mlp *mlp, const cicero_camera *cam,
+                                     const cicero_sampling *sampling, const cicero_options *opt, int window,
+                                     long long hole_records, float max_angle_deg, void *workspace, size_t ws_bytes,
+                                     cicero_pipeline **out);
+cicero_status cicero_pipeline_run(cicero_pipeline *pipeline, const cicero_camera *targets, int n_frames,
+                                  const cicero_camera *refs, float *const *rgb, float *const *depth,
+                                  void *stream_tgt, void *stream_ref);
+cicero_status cicero_pipeline_status(const cicero_pipeline *pipeline, void *stream);
+cicero_status cicero_pipeline_destroy(cicero_pipeline *pipeline);
+
+/* ---------------------------------------------------------------------------------------------
  * SpaRW target frame, steps 1-3 (Eq. 1 point cloud, Eq. 2 transform, Eq. 3 re-projection) plus
  * the depth test, the void depth test and hole listing of step 4 (Sec. III-B).
  *

@@ -9,6 +9,7 @@ float64 arrays.  See ``oracle.c`` for the definitions and the paper passages the
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 import subprocess
 import sys
@@ -314,6 +315,30 @@ def relu_margin(grid, mlp, sampling, cam=None, pix=None, rays=None):
     out = np.zeros(_nrays(cam, pix, rays))
     lib().or_relu_margin(C.byref(g), C.byref(m), C.byref(r), C.byref(s), _ptr(out))
     return out
+
+
+def extrapolate_pose(c2w_prev, c2w_cur, lead: float) -> np.ndarray:
+    """Pose of a reference frame extrapolated from the two latest camera poses (Sec. III-C, Eq. 5-6),
+    in FP64.  c2w are 3x4 [R | position] camera-to-world matrices one frame interval apart.
+
+    Eq. 5: v = (T_cur - T_prev) / dt.  Eq. 6: T_ref = T_cur + v t_r with t_r = lead * dt (the paper
+    takes lead = N / 2).  The paper writes the velocity of the position only; the orientation is
+    extrapolated the same way with the angular velocity: the rotation dR = R_cur R_prev^T taken from
+    prev to cur is applied `lead` more times (its axis-angle form, angle scaled by lead):
+    R_ref = rot(axis, lead * angle) R_cur."""
+    P = np.asarray(c2w_prev, dtype=np.float64).reshape(3, 4)
+    Cm = np.asarray(c2w_cur, dtype=np.float64).reshape(3, 4)
+    pos = Cm[:, 3] + lead * (Cm[:, 3] - P[:, 3])
+    dR = Cm[:, :3] @ P[:, :3].T
+    angle = math.acos(min(1.0, max(-1.0, (np.trace(dR) - 1.0) / 2.0)))
+    if angle < 1e-12:
+        Rl = np.eye(3)
+    else:
+        axis = np.array([dR[2, 1] - dR[1, 2], dR[0, 2] - dR[2, 0], dR[1, 0] - dR[0, 1]]) / (2.0 * math.sin(angle))
+        a = lead * angle
+        K = np.array([[0.0, -axis[2], axis[1]], [axis[2], 0.0, -axis[0]], [-axis[1], axis[0], 0.0]])
+        Rl = np.eye(3) + math.sin(a) * K + (1.0 - math.cos(a)) * (K @ K)  # Rodrigues
+    return np.concatenate([Rl @ Cm[:, :3], pos[:, None]], axis=1)
 
 
 def max_threads() -> int:

@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libcicero.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["api.cu", "render.cu", "mlp_tc.cu", "warp.cu", "backward.cu"]
+SOURCES = ["api.cu", "render.cu", "mlp_tc.cu", "warp.cu", "backward.cu", "pipeline.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

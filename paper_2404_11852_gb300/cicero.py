@@ -83,6 +83,12 @@ _SIGS = {
     "cicero_batch_launch": ([_P, _P], C.c_int),
     "cicero_batch_destroy": ([_P], C.c_int),
     "cicero_batch_autotune_brick": ([_P, C.c_int, _P, _P, _Z, _P, _P, _P], C.c_int),
+    "cicero_extrapolate_pose": ([_P, _P, C.c_float, _P], C.c_int),
+    "cicero_pipeline_workspace_size": ([_P, _P, _P, _P, C.c_int, C.c_longlong], _Z),
+    "cicero_pipeline_create": ([_P] * 5 + [C.c_int, C.c_longlong, C.c_float, _P, _Z, _P], C.c_int),
+    "cicero_pipeline_run": ([_P, _P, C.c_int, _P, _P, _P, _P, _P], C.c_int),
+    "cicero_pipeline_status": ([_P, _P], C.c_int),
+    "cicero_pipeline_destroy": ([_P], C.c_int),
     "cicero_profile_begin": ([], C.c_int),
     "cicero_profile_end": ([_P, _P, C.c_int], C.c_int),
     "cicero_launch_count": ([], C.c_longlong),
@@ -442,3 +448,69 @@ def cicero_batch_autotune_brick(jobs, opt: Options, ws: torch.Tensor, stream=Non
     ms = (C.c_float * 3)()
     _check(lib().cicero_batch_autotune_brick(jobs, len(jobs), C.byref(opt), p, n, _stream(stream), C.byref(best), ms))
     return int(best.value), {b: float(ms[i]) for i, b in enumerate((4, 8, 16))}
+
+
+def cicero_extrapolate_pose(prev: Camera, cur: Camera, lead: float) -> Camera:
+    out = Camera()
+    _check(lib().cicero_extrapolate_pose(C.byref(prev), C.byref(cur), float(lead), C.byref(out)))
+    return out
+
+
+# ---------------------------------------------------------------------------------------------
+# SpaRW over a trajectory
+
+
+def cicero_pipeline_workspace_size(grid: Grid, cam: Camera, samp: Sampling, opt: Options, window: int,
+                                   hole_records: int) -> int:
+    return int(lib().cicero_pipeline_workspace_size(C.byref(grid), C.byref(cam), C.byref(samp), C.byref(opt),
+                                                    int(window), int(hole_records)))
+
+
+class Pipeline:
+    """A ``cicero_pipeline`` handle: SpaRW windows with the next reference rendered on a second stream."""
+
+    def __init__(self, grid: Grid, mlp: Mlp, cam: Camera, samp: Sampling, opt: Options, window: int,
+                 hole_records: int, max_angle_deg: float, ws: torch.Tensor):
+        p, n = _ws(ws)
+        h = C.c_void_p()
+        _check(lib().cicero_pipeline_create(C.byref(grid), C.byref(mlp), C.byref(cam), C.byref(samp), C.byref(opt),
+                                            int(window), int(hole_records), float(max_angle_deg), p, n, C.byref(h)))
+        self.handle, self.ws, self.window = h, ws, window
+
+    def run(self, targets, refs, rgb, depth=None, stream_tgt=None, stream_ref=None):
+        """targets / refs: lists of Camera; rgb / depth: lists of device tensors (one per target)."""
+        tg = (Camera * len(targets))(*targets)
+        rf = (Camera * len(refs))(*refs)
+        pr = (C.c_void_p * len(rgb))(*[_ptr(t).value for t in rgb])
+        pd = (C.c_void_p * len(depth))(*[_ptr(t).value for t in depth]) if depth is not None else None
+        _check(lib().cicero_pipeline_run(self.handle, tg, len(targets), rf, pr, pd, _stream(stream_tgt),
+                                         _stream(stream_ref)))
+
+    def status(self, stream=None):
+        _check(lib().cicero_pipeline_status(self.handle, _stream(stream)))
+
+    def close(self):
+        if self.handle:
+            lib().cicero_pipeline_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def reference_poses(targets, window: int, lead: str = "centred"):
+    """Reference cameras of a trajectory for Pipeline.run (Sec. III-C, Eq. 5-6), causal for the
+    overlapped schedule: reference w is rendered while window w - 1 runs, so it is extrapolated
+    from the two poses known at the first frame s of window w - 1.  lead="centred" carries it to
+    frame w * window + window / 2 (the paper's centre of the window it serves); lead="paper"
+    applies Eq. 6 literally (window / 2 frame intervals from frame s).  Reference 0 is frame 0."""
+    refs = [targets[0]]
+    n_win = (len(targets) + window - 1) // window
+    for w in range(1, n_win):
+        s = max(1, (w - 1) * window)
+        frames = (w * window + window / 2.0 - s) if lead == "centred" else window / 2.0
+        refs.append(cicero_extrapolate_pose(targets[s - 1], targets[s], frames))
+    return refs

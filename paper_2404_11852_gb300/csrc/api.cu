@@ -221,9 +221,9 @@ static cicero_status plan_render(const cicero_grid* grid, const cicero_mlp* mlp,
   }
   if (n_rays < 0) return fail(CICERO_ERR_INVALID_ARG, "negative ray count");
   const unsigned long long RS = (unsigned long long)n_rays * (unsigned long long)s->n_samples;
-  if (RS >= 0xffffffffull) return fail(CICERO_ERR_UNSUPPORTED, "rays x samples must be below 2^32");
   unsigned long long Q = RS;
   if (opt && opt->max_records > 0 && (unsigned long long)opt->max_records < Q) Q = (unsigned long long)opt->max_records;
+  if (Q >= 0xffffffffull) return fail(CICERO_ERR_UNSUPPORTED, "record capacity must be below 2^32 (set max_records)");
   p->R = n_rays;
   p->S = s->n_samples;
   p->Q = (uint32_t)Q;
@@ -583,6 +583,8 @@ cicero_status cicero_build_rit(const cicero_grid* grid, const cicero_camera* cam
   const int R = cam->width * cam->height;
   st = plan_render(grid, nullptr, R, sampling, opt, &plan, false);
   if (st != CICERO_OK) return st;
+  if ((long long)R * plan.S > 0x7fffffffll)
+    return fail(CICERO_ERR_UNSUPPORTED, "the RIT's sample ids (ray x n_samples + slot) must fit in 31 bits");
   plan.want_k = true;
   if (!ws_ok(workspace)) return fail(CICERO_ERR_INVALID_ARG, "workspace must be non-NULL and 256-byte aligned");
   RenderWs w;

@@ -139,3 +139,19 @@ def test_batch_plan_validated_on_host(cc):
     st = L.cicero_batch_create(arr, 3, C.byref(bf16), C.c_void_p((1 << 20) + 8), size, C.byref(h))
     assert st == cc.ERR_INVALID_ARG  # workspace not 256-byte aligned
     assert L.cicero_batch_launch(None, None) == cc.ERR_INVALID_ARG
+
+
+def test_extrapolate_pose_matches_oracle(cc):
+    """Eq. 5-6 on the host side of the library (quaternions) against the oracle's axis-angle form."""
+    import oracle
+    import scenes
+    cam = scenes.orbit_camera(64, 48)
+    for (ka, kb, yaw, shift) in ((0, 1, 1.0, 0.005), (3, 4, -2.5, 0.02), (5, 6, 0.0, 0.01), (2, 3, 7.0, 0.0)):
+        a, b = scenes.offset_camera(cam, ka, yaw, shift), scenes.offset_camera(cam, kb, yaw, shift)
+        for lead in (0.0, 3.0, 10.5, 15.0, -1.0):
+            got = cc.cicero_extrapolate_pose(cc.camera_from(a), cc.camera_from(b), lead)
+            want = oracle.extrapolate_pose(a.c2w, b.c2w, lead)
+            np.testing.assert_allclose(np.array(got.c2w[:]).reshape(3, 4), want, atol=3e-6)
+            assert (got.width, got.height, got.f) == (b.width, b.height, np.float32(b.f))
+    with pytest.raises(cc.CiceroError):
+        cc.cicero_extrapolate_pose(cc.camera_from(cam), cc.camera_from(cam), float("nan"))

@@ -528,3 +528,50 @@ def test_mlp_gradient_matches_central_differences(orc):
     assert off == dm.size
     assert skipped <= 0.2 * n, (skipped, n)
     assert worst <= 1e-6, worst
+
+
+# ---------------------------------------------------------------------------------------------
+# reference-pose extrapolation (Sec. III-C, Eq. 5-6)
+
+
+def _rz(a):
+    c, s = np.cos(a), np.sin(a)
+    return np.array([[c, -s, 0.0], [s, c, 0.0], [0.0, 0.0, 1.0]])
+
+
+def test_extrapolate_translation_closed_form(orc):
+    p1, p2 = np.array([0.1, -0.2, 1.5]), np.array([0.13, -0.18, 1.49])
+    prev = np.concatenate([np.eye(3), p1[:, None]], 1)
+    cur = np.concatenate([np.eye(3), p2[:, None]], 1)
+    for lead in (0.5, 3.0, 10.5, 15.0):
+        r = orc.extrapolate_pose(prev, cur, lead)
+        np.testing.assert_allclose(r[:, 3], p2 + lead * (p2 - p1), atol=1e-15)  # Eq. 5-6
+        np.testing.assert_allclose(r[:, :3], np.eye(3), atol=1e-15)
+
+
+def test_extrapolate_rotation_about_fixed_axis(orc):
+    th0, a = 0.3, np.radians(1.0)
+    R1 = _rz(th0) @ _rz(0.1)  # any orientation, then turning about world z by a per frame
+    R2 = _rz(a) @ R1
+    prev = np.concatenate([R1, np.zeros((3, 1))], 1)
+    cur = np.concatenate([R2, np.zeros((3, 1))], 1)
+    for lead in (1.0, 8.0, 10.5):
+        r = orc.extrapolate_pose(prev, cur, lead)
+        np.testing.assert_allclose(r[:, :3], _rz(lead * a) @ R2, atol=1e-13)
+
+
+def test_extrapolate_special_leads(orc):
+    cam = scenes.orbit_camera(64, 64)
+    t0, t1 = scenes.offset_camera(cam, 0).c2w, scenes.offset_camera(cam, 1, yaw_deg=2.0, shift=0.02).c2w
+    np.testing.assert_allclose(orc.extrapolate_pose(t0, t1, 0.0), t1, atol=1e-12)   # no lead: the latest pose
+    np.testing.assert_allclose(orc.extrapolate_pose(t0, t1, -1.0), t0, atol=1e-6)   # one frame back
+    np.testing.assert_allclose(orc.extrapolate_pose(t1, t1, 7.0), t1, atol=1e-12)   # standing still
+
+
+def test_extrapolate_trajectory_generator(orc):
+    """The trajectory generator turns about a fixed axis and moves along a fixed direction at a
+    constant rate, so extrapolating k frames ahead lands on frame k ahead (to float rounding)."""
+    cam = scenes.orbit_camera(64, 64)
+    t = [scenes.offset_camera(cam, k).c2w.astype(np.float64) for k in range(20)]
+    for a, lead in ((1, 3), (4, 8), (9, 10)):
+        np.testing.assert_allclose(orc.extrapolate_pose(t[a - 1], t[a], lead), t[a + lead], atol=2e-6)
