@@ -278,8 +278,9 @@ class SparwWindow:
     rendered in full, every target warped from it in one batch, then all targets' holes rendered in
     one batch, written into the warped frames (Eq. 4)."""
 
-    def __init__(self, cc, torch, dev, grid, mlp, cam, targets, opt_ref, opt_holes, ref_ws_bytes=0):
-        self.cc, self.grid, self.mlp = cc, grid, mlp
+    def __init__(self, cc, torch, dev, grid, mlp, cam, targets, opt_ref, opt_holes, ref_ws_bytes=0,
+                 max_angle_deg=180.0):
+        self.cc, self.grid, self.mlp, self.max_angle = cc, grid, mlp, max_angle_deg
         self.R, self.n = cam.width * cam.height, len(targets)
         R, n = self.R, self.n
         self.sd, self.cd = cc.sampling_from(cam.sampling), cc.camera_from(cam)
@@ -303,8 +304,8 @@ class SparwWindow:
     def run(self):
         cc, L = self.cc, self.lists
         self.render_reference()
-        cc.cicero_warp_batch(self.ref_rgb, self.ref_depth, self.cd, self.tds, 180.0, self.grid.desc, self.sd, L[0],
-                             L[1], L[2], L[3], self.nh.view(-1), self.ws_w)
+        cc.cicero_warp_batch(self.ref_rgb, self.ref_depth, self.cd, self.tds, self.max_angle, self.grid.desc,
+                             self.sd, L[0], L[1], L[2], L[3], self.nh.view(-1), self.ws_w)
         cc.cicero_render_holes_batch(self.grid.desc, self.mlp.desc, self.tds, self.sd, self.opt_holes, L[3], self.nh,
                                      self.n * self.R, L[0], L[1], self.ws_h)
 
@@ -483,9 +484,29 @@ def window_sweep(cc, torch, dev, grid, mlp, o16):
 
     t_full = event_ms(torch, render_all, 1)
     del ws_f
+    # DS-2: every frame rendered at half resolution (f, cx, cy halved), then upsampled bilinearly
+    w2, h2 = W // 2, H // 2
+    half = [cc.camera(w2, h2, t.f / 2, t.cx / 2, t.cy / 2, np.array(t.c2w[:], np.float32).reshape(3, 4))
+            for t in targets]
+    lo_rgb, lo_d = torch.empty(w2 * h2, 3, device=dev), torch.empty(w2 * h2, device=dev)
+    ds2 = [torch.empty(R, 3, device=dev) for _ in traj]
+    ws_h2 = cc.workspace(cc.cicero_render_workspace_size(grid.desc, w2 * h2, sd, o16), dev)
+
+    def ds2_all():
+        for t, out in zip(half, ds2):
+            cc.cicero_render(grid.desc, mlp.desc, t, sd, o16, lo_rgb, lo_d, None, None, ws_h2)
+            cc.cicero_upsample_bilinear(lo_rgb, w2, h2, out, W, H)
+
+    t_ds2 = event_ms(torch, ds2_all, 1)
+    del ws_h2
+    p2 = np.minimum([frame_psnr(a.cpu().numpy(), b.cpu().numpy()) for a, b in zip(ds2, full)], 100.0)
+    ds2_res = {"fps": SWEEP_FRAMES / (t_ds2 / 1e3), "speedup_vs_full": t_full / t_ds2,
+               "psnr_db_mean": float(np.mean(p2)), "psnr_db_median": float(np.median(p2)),
+               "psnr_db_min": float(np.min(p2))}
+    del ds2
     frames = [torch.empty(R, 3, device=dev) for _ in traj]
     s_ref = torch.cuda.Stream(dev)
-    res = {"frames": SWEEP_FRAMES, "full_render_fps": SWEEP_FRAMES / (t_full / 1e3), "windows": []}
+    res = {"frames": SWEEP_FRAMES, "full_render_fps": SWEEP_FRAMES / (t_full / 1e3), "ds2": ds2_res, "windows": []}
     for N, lead in [(n, "centred") for n in SWEEP_WINDOWS] + [(16, "paper")]:
         hole_records = N * R * 40  # ~16% of the window's slots
         ws = cc.workspace(cc.cicero_pipeline_workspace_size(grid.desc, cd, sd, o16, N, hole_records), dev)
@@ -508,6 +529,44 @@ def window_sweep(cc, torch, dev, grid, mlp, o16):
         p.close()
         del ws
     return res
+
+
+PHI_SWEEP = (180.0, 8.0, 4.0, 2.0, 1.0)
+
+
+def phi_sweep(cc, torch, dev, grid, o16, ref_samples):
+    """The warp-angle heuristic (Sec. III-C "Deciding When to Warp"): a point is warped only when
+    the angle between its reference and target rays is below phi.  On the headline window (16
+    targets around the reference) with a strongly view-dependent MLP (the weights of the direction
+    encoding scaled by 6), per phi: fraction of target rays marched, target frames/s and PSNR of
+    the targets against their full renders (every pixel)."""
+    import scenes
+    m = scenes.make_mlp(12, seed=4242)
+    m.w1[:, 12:] *= 6.0
+    mlp = cc.DeviceMlp.from_host(m, dev)
+    cam = scenes.orbit_camera(W, H, sampling=scenes.sampling_march(256, 256))
+    targets = [scenes.offset_camera(cam, k) for k in scenes.SPARW_OFFSETS]
+    R, sd = W * H, cc.sampling_from(cam.sampling)
+    full = torch.empty(len(targets), R, 3, device=dev)
+    fd = torch.empty(R, device=dev)
+    ws_f = cc.workspace(cc.cicero_render_workspace_size(grid.desc, R, sd, o16), dev)
+    for i, t in enumerate(targets):
+        cc.cicero_render(grid.desc, mlp.desc, cc.camera_from(t), sd, o16, full[i], fd, None, None, ws_f)
+    del ws_f
+    # a small phi turns almost every target pixel into a hole: room for all of them
+    ob = cc.options(cc.MLP_BF16, o16.brick, max_records=min(int(1.3 * len(targets) * ref_samples), 4_000_000_000))
+    out = []
+    for phi in PHI_SWEEP:
+        win = SparwWindow(cc, torch, dev, grid, mlp, cam, targets, o16, ob, max_angle_deg=phi)
+        t = event_ms(torch, win.run, 3)
+        win.check()
+        ps = np.minimum([frame_psnr(win.t_rgb[i].cpu().numpy(), full[i].cpu().numpy()) for i in range(len(targets))],
+                        100.0)
+        out.append({"phi_deg": phi, "fraction_marched": float(win.nh.sum().item()) / (len(targets) * R),
+                    "target_fps": len(targets) / (t / 1e3), "psnr_db_mean": float(np.mean(ps)),
+                    "psnr_db_min": float(np.min(ps))})
+        del win
+    return {"mlp": "direction-encoding weights x 6", "window": "16 targets, 1..8 deg yaw + 5 mm steps", "phi": out}
 
 
 def backward_workload(cc, torch, dev):
@@ -738,6 +797,7 @@ def main():
         others["config_sparw_small_scene"] = sparw_small_scene(cc, torch, dev)
         others["config_batched"] = batched_workload(cc, torch, dev)
         others["sparw_window_sweep"] = window_sweep(cc, torch, dev, grid, mlp, o16)
+        others["sparw_phi_sweep"] = phi_sweep(cc, torch, dev, grid, o16, active)
 
     if rank == 0:
         line = {

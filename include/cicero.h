@@ -226,6 +226,16 @@ cicero_status cicero_batch_autotune_brick(const cicero_job *jobs, int n_jobs, co
                                           int *best_brick, float *ms);
 
 /* ---------------------------------------------------------------------------------------------
+ * Bilinear resampling, for the DS-2 comparator of the evaluation (render the frame at half
+ * resolution, then upsample it to the original resolution by bilinear interpolation).  Pixel
+ * centres align: output pixel (i, j) samples src at ((i + 1/2) w / W - 1/2, (j + 1/2) h / H - 1/2)
+ * from the nearest two source pixel centres per axis, clamped to the image (a half-resolution
+ * render is the frame rendered with f, cx, cy halved).  src [h][w][channels], dst [H][W][channels],
+ * device FP32; 1 <= channels <= 16. */
+cicero_status cicero_upsample_bilinear(const float *src, int w, int h, int channels, float *dst, int W, int H,
+                                       void *stream);
+
+/* ---------------------------------------------------------------------------------------------
  * Reference pose by extrapolation (Sec. III-C, Eq. 5-6): from the two latest camera poses `prev`
  * and `cur`, one frame interval apart, the velocity v = (cur - prev) / dt (Eq. 5) is applied for
  * t_r = lead * dt (Eq. 6, where the paper takes lead = N / 2 for N targets per reference):

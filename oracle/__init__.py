@@ -341,6 +341,23 @@ def extrapolate_pose(c2w_prev, c2w_cur, lead: float) -> np.ndarray:
     return np.concatenate([Rl @ Cm[:, :3], pos[:, None]], axis=1)
 
 
+def upsample_bilinear(img, W: int, H: int) -> np.ndarray:
+    """Bilinear resampling of img [h, w, C] to [H, W, C] in FP64 (the DS-2 comparator: the frame is
+    rendered at half resolution, then upsampled by bilinear interpolation).  Reading: pixel
+    centres align, so output pixel (i, j) samples the source at ((i + 1/2) w / W - 1/2,
+    (j + 1/2) h / H - 1/2); coordinates are clamped to the image."""
+    img = np.asarray(img, dtype=np.float64)
+    h, w = img.shape[:2]
+    u = np.clip((np.arange(W) + 0.5) * w / W - 0.5, 0.0, w - 1)
+    v = np.clip((np.arange(H) + 0.5) * h / H - 0.5, 0.0, h - 1)
+    x0, y0 = np.floor(u).astype(int), np.floor(v).astype(int)
+    x1, y1 = np.minimum(x0 + 1, w - 1), np.minimum(y0 + 1, h - 1)
+    fx, fy = (u - x0)[None, :, None], (v - y0)[:, None, None]
+    top = img[y0][:, x0] * (1 - fx) + img[y0][:, x1] * fx
+    bot = img[y1][:, x0] * (1 - fx) + img[y1][:, x1] * fx
+    return top * (1 - fy) + bot * fy
+
+
 def max_threads() -> int:
     return int(lib().or_max_threads())
 

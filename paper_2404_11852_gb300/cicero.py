@@ -84,6 +84,7 @@ _SIGS = {
     "cicero_batch_destroy": ([_P], C.c_int),
     "cicero_batch_autotune_brick": ([_P, C.c_int, _P, _P, _Z, _P, _P, _P], C.c_int),
     "cicero_extrapolate_pose": ([_P, _P, C.c_float, _P], C.c_int),
+    "cicero_upsample_bilinear": ([_P, C.c_int, C.c_int, C.c_int, _P, C.c_int, C.c_int, _P], C.c_int),
     "cicero_pipeline_workspace_size": ([_P, _P, _P, _P, C.c_int, C.c_longlong], _Z),
     "cicero_pipeline_create": ([_P] * 5 + [C.c_int, C.c_longlong, C.c_float, _P, _Z, _P], C.c_int),
     "cicero_pipeline_run": ([_P, _P, C.c_int, _P, _P, _P, _P, _P], C.c_int),
@@ -514,3 +515,10 @@ def reference_poses(targets, window: int, lead: str = "centred"):
         frames = (w * window + window / 2.0 - s) if lead == "centred" else window / 2.0
         refs.append(cicero_extrapolate_pose(targets[s - 1], targets[s], frames))
     return refs
+
+
+def cicero_upsample_bilinear(src, w: int, h: int, dst, W: int, H: int, stream=None):
+    """src [h*w][C] -> dst [H*W][C] (device FP32 tensors)."""
+    ch = src.numel() // (w * h)
+    _check(lib().cicero_upsample_bilinear(_ptr(src), int(w), int(h), int(ch), _ptr(dst), int(W), int(H),
+                                          _stream(stream)))

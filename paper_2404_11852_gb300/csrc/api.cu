@@ -773,6 +773,15 @@ const char* cicero_last_error(void) { return g_last_error.c_str(); }
 
 const char* cicero_version(void) { return "cicero-gb300 0.1 (sm_103a)"; }
 
+cicero_status cicero_upsample_bilinear(const float* src, int w, int h, int channels, float* dst, int W, int H,
+                                       void* stream) {
+  if (!src || !dst) return fail(CICERO_ERR_INVALID_ARG, "src/dst is NULL");
+  if (w < 1 || h < 1 || W < 1 || H < 1 || channels < 1 || channels > 16)
+    return fail(CICERO_ERR_INVALID_ARG, "sizes must be >= 1 and channels 1..16");
+  if ((long long)W * H > (1ll << 30) || (long long)w * h > (1ll << 30)) return fail(CICERO_ERR_UNSUPPORTED, "image too large");
+  return run_upsample(src, w, h, channels, dst, W, H, (cudaStream_t)stream);
+}
+
 size_t cicero_batch_table_bytes(int n_jobs) {
   return n_jobs >= 1 && n_jobs <= kMaxBatchJobs ? batch_table_bytes(n_jobs) : 0;
 }

@@ -144,6 +144,8 @@ size_t batch_table_bytes(int n_jobs);
 cicero_status run_render_batch(const BatchPlan& b, cudaStream_t st);
 cicero_status launch_gather_mlp_bf16_batch(const BatchPlan& b, cudaStream_t st);
 
+cicero_status run_upsample(const float* src, int w, int h, int C, float* dst, int W, int H, cudaStream_t st);
+
 // BF16 tensor-core Feature Computation (mlp_tc.cu)
 cicero_status launch_gather_mlp_bf16(const cicero_grid* grid, const GridGeo& geo, const Samp& samp, const RaySrc& src,
                                      const MlpPtrs& mlp, const RenderWs& ws, const CUtensorMap& map, const BrickBox& box,

@@ -258,6 +258,40 @@ __global__ void __launch_bounds__(1024) k_hole_write(const __grid_constant__ War
     if (h[k]) V.hole_idx[pos++] = base + k;
 }
 
+// Bilinear resampling of an image (the DS-2 comparator of the evaluation: render at half resolution,
+// then upsample).  Pixel centres align: output pixel i samples the source at u = (i + 1/2) w / W - 1/2,
+// interpolating the two nearest source pixel centres per axis, clamped to the image.
+__global__ void __launch_bounds__(256) k_upsample(const float* __restrict__ src, int w, int h, int C,
+                                                  float* __restrict__ dst, int W, int H) {
+  const long long n = (long long)W * H;
+  const float sx = (float)w / (float)W, sy = (float)h / (float)H;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(q % W), j = (int)(q / W);
+    const float u = fmaxf(((float)i + 0.5f) * sx - 0.5f, 0.0f), v = fmaxf(((float)j + 0.5f) * sy - 0.5f, 0.0f);
+    const int x0 = min((int)u, w - 1), y0 = min((int)v, h - 1);
+    const int x1 = min(x0 + 1, w - 1), y1 = min(y0 + 1, h - 1);
+    const float fx = fminf(u - (float)x0, 1.0f), fy = fminf(v - (float)y0, 1.0f);
+    const float* a = src + ((size_t)y0 * w + x0) * C;
+    const float* b = src + ((size_t)y0 * w + x1) * C;
+    const float* c = src + ((size_t)y1 * w + x0) * C;
+    const float* d = src + ((size_t)y1 * w + x1) * C;
+    float* o = dst + (size_t)q * C;
+    for (int k = 0; k < C; k++) {
+      const float top = a[k] + fx * (b[k] - a[k]), bot = c[k] + fx * (d[k] - c[k]);
+      o[k] = top + fy * (bot - top);
+    }
+  }
+}
+
+cicero_status run_upsample(const float* src, int w, int h, int C, float* dst, int W, int H, cudaStream_t st) {
+  const long long n = (long long)W * H;
+  const int blocks = (int)std::min<long long>((n + 255) / 256, (long long)num_sms() * 8);
+  k_upsample<<<blocks, 256, 0, st>>>(src, w, h, C, dst, W, H);
+  count_launches(1);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? CICERO_OK : cuda_fail(e, "k_upsample");
+}
+
 static size_t al256w(size_t x) { return (x + 255) & ~size_t(255); }
 
 // workspace: [256-byte header] then per view [depth buffer, 8 B per target pixel] [block sums]

@@ -575,3 +575,21 @@ def test_extrapolate_trajectory_generator(orc):
     t = [scenes.offset_camera(cam, k).c2w.astype(np.float64) for k in range(20)]
     for a, lead in ((1, 3), (4, 8), (9, 10)):
         np.testing.assert_allclose(orc.extrapolate_pose(t[a - 1], t[a], lead), t[a + lead], atol=2e-6)
+
+
+# ---------------------------------------------------------------------------------------------
+# bilinear resampling of the DS-2 comparator
+
+
+def test_upsample_constant_identity_and_ramp(orc):
+    img = np.full((5, 7, 3), 0.37)
+    np.testing.assert_allclose(orc.upsample_bilinear(img, 14, 10), 0.37, atol=1e-15)
+    rnd = np.random.default_rng(3).random((6, 9, 2))
+    np.testing.assert_allclose(orc.upsample_bilinear(rnd, 9, 6), rnd, atol=1e-15)  # same size: identity
+    # a ramp a + b x along x is reproduced at every output centre, clamped at the image edges
+    w, W, a, b = 8, 20, 0.25, 0.1
+    ramp = np.broadcast_to((a + b * np.arange(w))[None, :, None], (3, w, 1))
+    out = orc.upsample_bilinear(ramp, W, 3)[0, :, 0]
+    u = np.clip((np.arange(W) + 0.5) * w / W - 0.5, 0, w - 1)
+    np.testing.assert_allclose(out, a + b * u, atol=1e-14)
+    assert out[0] == a and out[-1] == a + b * (w - 1)
