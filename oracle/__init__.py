@@ -36,7 +36,12 @@ def build(force: bool = False) -> str:
 class OrGrid(C.Structure):
     _fields_ = [("n", C.c_int * 3), ("C", C.c_int), ("aabb_min", C.c_float * 3), ("aabb_max", C.c_float * 3),
                 ("act_shift", C.c_double), ("dtype", C.c_int), ("density", C.c_void_p),
-                ("features", C.c_void_p), ("occ", C.c_void_p), ("occ_res", C.c_int)]
+                ("features", C.c_void_p), ("occ", C.c_void_p), ("occ_res", C.c_int), ("hash", C.c_void_p)]
+
+
+class OrHash(C.Structure):
+    _fields_ = [("levels", C.c_int), ("feat", C.c_int), ("log2_size", C.c_int), ("res", C.c_int * 16),
+                ("dtype", C.c_int), ("table", C.c_void_p)]
 
 
 class OrMlp(C.Structure):
@@ -72,6 +77,7 @@ def lib():
         L.or_active_samples.argtypes = [P, P, P, C.c_int, P, P, P, C.c_long, P, P]
         L.or_active_samples.restype = C.c_long
         L.or_sample_grid.argtypes = [P, P, C.c_int, P, P]
+        L.or_hash_features.argtypes = [P, P, C.c_int, P]
         L.or_mlp_eval.argtypes = [P, P, C.c_int, P]
         L.or_encode.argtypes = [P, C.c_int, P, P, C.c_int, P]
         L.or_warp.argtypes = [P, P, P, P, C.c_float, P, P, P, P, P, P, P, P]
@@ -106,7 +112,7 @@ _DT = {np.dtype(np.float64): 0, np.dtype(np.float32): 1, np.dtype(np.float16): 2
 
 def _grid(g, keep) -> OrGrid:
     dens = keep(np.ascontiguousarray(g.density))
-    feat = keep(np.ascontiguousarray(g.features))
+    feat = keep(np.ascontiguousarray(g.features if g.features is not None else np.zeros(1, dens.dtype)))
     assert dens.dtype == feat.dtype
     s = OrGrid()
     s.n[:] = list(g.n)
@@ -121,6 +127,16 @@ def _grid(g, keep) -> OrGrid:
         occ = keep(np.ascontiguousarray(g.occ, dtype=np.uint8))
         s.occ = occ.ctypes.data
         s.occ_res = occ.shape[0]
+    h = getattr(g, "hash", None)
+    if h is not None:
+        hs = OrHash()
+        hs.levels, hs.feat, hs.log2_size = h.levels, h.feat, h.log2_size
+        hs.res[: h.levels] = list(h.res)
+        tab = keep(np.ascontiguousarray(h.table))
+        hs.dtype = 1 if tab.dtype == np.float32 else 2
+        hs.table = tab.ctypes.data
+        keep(hs)
+        s.hash = C.addressof(hs)
     return s
 
 
@@ -356,6 +372,16 @@ def upsample_bilinear(img, W: int, H: int) -> np.ndarray:
     top = img[y0][:, x0] * (1 - fx) + img[y0][:, x1] * fx
     bot = img[y1][:, x0] * (1 - fx) + img[y1][:, x1] * fx
     return top * (1 - fy) + bot * fy
+
+
+def hash_features(grid, points):
+    """Hash-encoding features of a grid with ``hash`` at world points [n, 3] -> [n, levels * feat]."""
+    keep = _Keep()
+    g = _grid(grid, keep)
+    p = keep(np.ascontiguousarray(points, dtype=np.float64))
+    out = np.zeros((p.shape[0], grid.C))
+    lib().or_hash_features(C.byref(g), _ptr(p), p.shape[0], _ptr(out))
+    return out
 
 
 def max_threads() -> int:

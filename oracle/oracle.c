@@ -35,9 +35,22 @@
 #define OR_MAX_HIDDEN 256
 #define OR_MAX_IN 96
 
+/* Multiresolution hash encoding (the hash-grid workload, Instant-NGP-like): `levels` levels of
+ * `feat` features.  Level l divides the grid box into res[l] cells per axis; its (res+1)^3
+ * vertices are stored densely, at x + (res+1) (y + (res+1) z), when they fit the level's table of
+ * T = 2^log2_size entries, otherwise at the spatial hash (x * 1) xor (y * 2654435761) xor
+ * (z * 805459861) mod T of 32-bit unsigned integers.  A level's features are the trilinear
+ * interpolation of its 8 corner entries; the levels are concatenated (feature l * feat + c). */
+typedef struct {
+    int levels, feat, log2_size;
+    int res[16];
+    int dtype;             /* storage of the table: 1 f32, 2 f16 bits */
+    const void *table;     /* [levels][T][feat] */
+} or_hash;
+
 typedef struct {
     int n[3];              /* vertices along x, y, z */
-    int C;                 /* feature channels */
+    int C;                 /* feature channels (levels * feat with a hash encoding) */
     float aabb_min[3], aabb_max[3];
     double act_shift;      /* density activation shift (-4) */
     int dtype;             /* storage of density/features: 0 f64, 1 f32, 2 f16 bits */
@@ -45,6 +58,7 @@ typedef struct {
     const void *features;  /* [z][y][x][C] */
     const uint8_t *occ;    /* [R][R][R] or NULL */
     int occ_res;
+    const or_hash *hash;   /* NULL: features from the dense grid; else from the hash encoding */
 } or_grid;
 
 typedef struct {
@@ -245,6 +259,48 @@ static void trilinear(const or_grid *g, const int i0[3], const double f[3], doub
             }
 }
 
+static uint32_t hash_index(const or_hash *h, int l, uint32_t x, uint32_t y, uint32_t z) {
+    const uint32_t n = (uint32_t)h->res[l] + 1u;
+    const uint64_t T = 1ull << h->log2_size;
+    if ((uint64_t)n * n * n <= T) return x + n * (y + n * z);
+    return (x * 1u ^ y * 2654435761u ^ z * 805459861u) & (uint32_t)(T - 1);
+}
+
+/* Features of the hash encoding at world position p (FP64). */
+static void hash_features(const or_grid *g, const double p[3], double *feat) {
+    const or_hash *h = g->hash;
+    const size_t T = (size_t)1 << h->log2_size;
+    double pn[3];
+    for (int a = 0; a < 3; a++) {
+        double u = (p[a] - (double)g->aabb_min[a]) / ((double)g->aabb_max[a] - (double)g->aabb_min[a]);
+        pn[a] = u < 0.0 ? 0.0 : (u > 1.0 ? 1.0 : u);
+    }
+    for (int l = 0; l < h->levels; l++) {
+        const int N = h->res[l];
+        int i0[3];
+        double f[3];
+        for (int a = 0; a < 3; a++) {
+            double gx = pn[a] * N;
+            int i = (int)floor(gx);
+            if (i > N - 1) i = N - 1;
+            i0[a] = i;
+            f[a] = gx - i;
+        }
+        for (int c = 0; c < h->feat; c++) feat[l * h->feat + c] = 0.0;
+        for (int dz = 0; dz < 2; dz++)
+            for (int dy = 0; dy < 2; dy++)
+                for (int dx = 0; dx < 2; dx++) {
+                    double w = (dx ? f[0] : 1.0 - f[0]) * (dy ? f[1] : 1.0 - f[1]) * (dz ? f[2] : 1.0 - f[2]);
+                    size_t e = ((size_t)l * T + hash_index(h, l, i0[0] + dx, i0[1] + dy, i0[2] + dz)) * h->feat;
+                    for (int c = 0; c < h->feat; c++) {
+                        double v = h->dtype == 1 ? (double)((const float *)h->table)[e + c]
+                                                 : f16_to_f64(((const uint16_t *)h->table)[e + c]);
+                        feat[l * h->feat + c] += w * v;
+                    }
+                }
+    }
+}
+
 static double softplus(double x) { return x > 30.0 ? x + log1p(exp(-x)) : log1p(exp(x)); }
 static double sigm(double x) { return 1.0 / (1.0 + exp(-x)); }
 
@@ -343,7 +399,12 @@ static void march_ray(const or_grid *g, const or_mlp *m, const or_rays *rays, co
             f[a] = ga - ix.i0[a];
         }
         double raw;
-        trilinear(g, ix.i0, f, &raw, feat);
+        trilinear(g, ix.i0, f, &raw, g->hash ? NULL : feat);
+        if (g->hash) {
+            double p[3];
+            for (int a = 0; a < 3; a++) p[a] = o[a] + t * d[a];
+            hash_features(g, p, feat);
+        }
         double sigma = softplus(raw + g->act_shift);
         double alpha = -expm1(-sigma * dt);
         double w = T * alpha;
@@ -707,6 +768,7 @@ int or_backward(const or_grid *g, const or_mlp *m, const or_rays *rays, const or
                 const double *d_rgb, double *d_density, double *d_features, double *d_mlp) {
     int R = n_rays_of(rays), C = g->C, I = m->in_dim, H = m->hidden;
     if (m->in_dim != C + 3 + 6 * m->n_freq || H > OR_MAX_HIDDEN || I > OR_MAX_IN) return -1;
+    if (g->hash) return -3;  /* the gradient of the hash encoding is not defined here */
     int maxs = s->n_samples;
     sample_rec *recs = (sample_rec *)malloc(sizeof(sample_rec) * (size_t)(maxs > 0 ? maxs : 1));
     if (!recs) return -2;
@@ -798,6 +860,11 @@ void or_relu_margin(const or_grid *g, const or_mlp *m, const or_rays *rays, cons
         kink[r] = mn;
     }
     free(recs);
+}
+
+/* Features of the hash encoding at n world positions p [n][3] -> feat [n][levels * feat]. */
+void or_hash_features(const or_grid *g, const double *p, int n, double *feat) {
+    for (int i = 0; i < n; i++) hash_features(g, p + 3 * i, feat + (size_t)i * g->C);
 }
 
 int or_max_threads(void) {

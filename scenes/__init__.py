@@ -65,11 +65,24 @@ def uniform(seed: int, n: int, lo: float = 0.0, hi: float = 1.0, offset: int = 0
 
 
 @dataclass
+class HashGrid:
+    """Multiresolution hash encoding: ``table`` is [levels][2^log2_size][feat]; level l divides the
+    box into ``res[l]`` cells per axis."""
+
+    levels: int
+    feat: int
+    log2_size: int
+    res: tuple
+    table: np.ndarray
+
+
+@dataclass
 class Grid:
     """Dense voxel grid: ``density`` is [Nz][Ny][Nx], ``features`` is [Nz][Ny][Nx][C].
 
     Vertices sit on the corners of the axis-aligned box ``aabb_min .. aabb_max``.
-    ``occ`` is an optional [R][R][R] uint8 occupancy mask over the same box.
+    ``occ`` is an optional [R][R][R] uint8 occupancy mask over the same box.  With ``hash`` set,
+    the colour features come from that encoding (C = levels * feat) and ``features`` is unused.
     """
 
     n: tuple
@@ -80,6 +93,7 @@ class Grid:
     aabb_max: tuple = (1.0, 1.0, 1.0)
     act_shift: float = -4.0
     occ: np.ndarray | None = None
+    hash: HashGrid | None = None
 
     @property
     def occ_res(self) -> int:
@@ -87,7 +101,7 @@ class Grid:
 
     def astype(self, dtype) -> "Grid":
         return Grid(self.n, self.C, self.density.astype(dtype), self.features.astype(dtype),
-                    self.aabb_min, self.aabb_max, self.act_shift, self.occ)
+                    self.aabb_min, self.aabb_max, self.act_shift, self.occ, self.hash)
 
 
 @dataclass
@@ -317,6 +331,25 @@ def random_targets(R: int, seed: int = SEED_RAYS) -> np.ndarray:
 
 # --------------------------------------------------------------------------------------------
 # the standard workloads
+
+
+def hash_levels(levels: int, base_res: int, max_res: int) -> tuple:
+    """Cells per axis of each level: floor(base * b^l) with b = (max / base)^(1 / (levels - 1))."""
+    b = math.exp((math.log(max_res) - math.log(base_res)) / max(levels - 1, 1))
+    return tuple(int(math.floor(base_res * b ** l)) for l in range(levels))
+
+
+def make_hash_grid(levels: int = 8, feat: int = 2, log2_size: int = 19, base_res: int = 16, max_res: int = 512,
+                   seed: int = SEED_SCENE, dtype=np.float16) -> HashGrid:
+    """Table entries U[-1, 1] (a seeded stand-in for trained features)."""
+    T = 1 << log2_size
+    table = uniform(stream_seed(seed, 40), levels * T * feat, -1.0, 1.0).astype(dtype).reshape(levels, T, feat)
+    return HashGrid(levels, feat, log2_size, hash_levels(levels, base_res, max_res), table)
+
+
+def with_hash(g: Grid, h: HashGrid) -> Grid:
+    """The scene g (density, occupancy, box) with its colour features from the hash encoding h."""
+    return Grid(g.n, h.levels * h.feat, g.density, None, g.aabb_min, g.aabb_max, g.act_shift, g.occ, h)
 
 
 def scene_small(dtype=np.float32) -> Grid:

@@ -593,3 +593,54 @@ def test_upsample_constant_identity_and_ramp(orc):
     u = np.clip((np.arange(W) + 0.5) * w / W - 0.5, 0, w - 1)
     np.testing.assert_allclose(out, a + b * u, atol=1e-14)
     assert out[0] == a and out[-1] == a + b * (w - 1)
+
+
+# ---------------------------------------------------------------------------------------------
+# multiresolution hash encoding (the hash-grid workload)
+
+
+def _hash_scene(levels=3, log2_size=10, res=(4, 8, 40), table=None):
+    h = scenes.HashGrid(levels, 2, log2_size, tuple(res),
+                        table if table is not None else np.zeros((levels, 1 << log2_size, 2), np.float32))
+    return scenes.with_hash(scenes.scene_fd().astype(np.float32), h)
+
+
+def test_hash_constant_table(orc):
+    g = _hash_scene(table=np.full((3, 1024, 2), 0.625, np.float32))
+    p = scenes.uniform(7, 60, -1.0, 1.0).reshape(20, 3)
+    np.testing.assert_allclose(orc.hash_features(g, p), 0.625, atol=1e-15)
+
+
+def test_hash_dense_level_is_exact_on_linear_fields(orc):
+    """Level 0 (4 cells, 125 vertices <= 1024 entries) is stored densely at x + 5 (y + 5 z): a
+    linear field written at its vertices is reproduced exactly anywhere in the box."""
+    N, T = 4, 1024
+    tab = np.zeros((3, T, 2), np.float32)
+    for z in range(N + 1):
+        for y in range(N + 1):
+            for x in range(N + 1):
+                tab[0, x + (N + 1) * (y + (N + 1) * z)] = [0.25 * x - 0.5 * y + 0.125 * z, 0.5 + 0.25 * z]
+    g = _hash_scene(table=tab)
+    p = scenes.uniform(8, 90, -1.0, 1.0).reshape(30, 3)
+    v = (p + 1.0) / 2.0 * N  # vertex coordinates of level 0
+    got = orc.hash_features(g, p)[:, :2]
+    np.testing.assert_allclose(got[:, 0], 0.25 * v[:, 0] - 0.5 * v[:, 1] + 0.125 * v[:, 2], atol=1e-12)
+    np.testing.assert_allclose(got[:, 1], 0.5 + 0.25 * v[:, 2], atol=1e-12)
+
+
+def test_hash_vertices_on_the_x_axis(orc):
+    """Level 2 (40 cells: 68921 vertices > 1024 entries) is hashed; on the x axis (y = z = 0) the
+    spatial hash reduces to x mod T, and at a vertex the interpolation returns that one entry."""
+    tab = (np.arange(3 * 1024 * 2, dtype=np.float32).reshape(3, 1024, 2) * 1e-3).astype(np.float32)
+    g = _hash_scene(table=tab)
+    for x in (0, 1, 17, 39):
+        p = np.array([[-1.0 + 2.0 * x / 40.0, -1.0, -1.0]])
+        np.testing.assert_allclose(orc.hash_features(g, p)[0, 4:6], tab[2, x % 1024], atol=1e-9)
+
+
+def test_hash_continuous_across_cell_faces(orc):
+    g = _hash_scene(table=scenes.uniform(9, 3 * 1024 * 2, -1.0, 1.0).astype(np.float32).reshape(3, 1024, 2))
+    x_face = -1.0 + 2.0 * 7.0 / 40.0  # a face of level 2 (and of no coarser level)
+    p = np.array([[x_face - 1e-9, 0.13, -0.41], [x_face + 1e-9, 0.13, -0.41]])
+    f = orc.hash_features(g, p)
+    np.testing.assert_allclose(f[0], f[1], atol=1e-7)
