@@ -569,6 +569,53 @@ def phi_sweep(cc, torch, dev, grid, o16, ref_samples):
     return {"mlp": "direction-encoding weights x 6", "window": "16 targets, 1..8 deg yaw + 5 mm steps", "phi": out}
 
 
+def hash_workload(cc, torch, dev, grid, g_h, reps=5):
+    """The hash-grid workload (Sec. IV-A, hierarchical encodings; Instant-NGP-like): the 800x800
+    frame of the 256^3 scene (its density and occupancy) with the colour features from a
+    multiresolution hash encoding of 8 levels x 2 FP16 features, 2^19 entries per level, 16 .. 1024
+    cells per axis; BF16 MLP 43 -> 128 -> 128 -> 3.  Frames/s, Msamples/s, the tensor roofline of
+    the gather kernel, and the oracle on 256 sampled pixels."""
+    import oracle
+    import scenes
+    h = scenes.make_hash_grid(8, 2, 19, 16, 1024, seed=777)
+    m = scenes.make_mlp(16, seed=778)
+    hd, md = cc.DeviceHashGrid.from_host(h, dev), cc.DeviceMlp.from_host(m, dev)
+    cam = scenes.orbit_camera(W, H, sampling=scenes.sampling_march(256, 256))
+    cd, sd = cc.camera_from(cam), cc.sampling_from(cam.sampling)
+    R = W * H
+    rgb, dep = torch.empty(R, 3, device=dev), torch.empty(R, device=dev)
+    best = None
+    for brick in (4, 8):
+        opt = cc.options(cc.MLP_BF16, brick)
+        ws = cc.workspace(cc.cicero_render_hash_workspace_size(grid.desc, hd.desc, R, sd, opt), dev)
+        t = event_ms(torch, lambda: cc.cicero_render_hash(grid.desc, hd.desc, md.desc, cd, sd, opt, rgb, dep, ws), reps)
+        cc.cicero_workspace_status(ws)
+        if best is None or t < best[0]:
+            best = (t, brick, ws, opt)
+    t, brick, ws, opt = best
+    samples = int(ws[:16].view(torch.int32).cpu().numpy()[2])
+    cc.cicero_profile_begin()
+    cc.cicero_render_hash(grid.desc, hd.desc, md.desc, cd, sd, opt, rgb, dep, ws)
+    torch.cuda.synchronize()
+    prof = cc.cicero_profile_end()
+    g_ms = prof["gather_mlp"][0] / max(prof["gather_mlp"][1], 1)
+    flop = 2 * (m.in_dim * 128 + 128 * 128 + 128 * 3) * samples
+    pk = peaks()
+    oracle.build()
+    pix = (scenes.splitmix64(3131, 256) % np.uint64(R)).astype(np.int32)
+    ref = oracle.render(scenes.with_hash(g_h, h), m, cam.sampling, cam=cam, pix=pix)
+    got = rgb.cpu().double().numpy()[pix]
+    e = np.where(ref["amb"][:, None], np.minimum(np.abs(got - ref["rgb"]), np.abs(got - ref["rgb_alt"])),
+                 np.abs(got - ref["rgb"]))
+    return {"workload": "800x800, 256^3 density + 32^3 occupancy, hash encoding 8 levels x 2 FP16, 2^19 entries, "
+                        "16..1024 cells", "brick": brick, "fps": 1e3 / t, "msamples_per_s": samples / t / 1e3,
+            "composited_samples": samples, "stages_ms": {k: round(v[0], 3) for k, v in prof.items() if v[1]},
+            "gather_mlp_tflops": flop / (g_ms / 1e3) / 1e12,
+            "gather_mlp_frac": flop / (g_ms / 1e3) / 1e12 / pk["bf16_tflops_sustained"],
+            "oracle_check": {"pixels": 256, "max_err": float(e.max()),
+                             "psnr_db": 10 * math.log10(1.0 / max(float(np.mean(e ** 2)), 1e-30))}}
+
+
 def backward_workload(cc, torch, dev):
     """Forward + backward over 8192 random rays x 256 samples on the 160^3 x 12 FP32 scene, MSE
     loss against seeded target colours (the differentiation workload)."""
@@ -798,6 +845,7 @@ def main():
         others["config_batched"] = batched_workload(cc, torch, dev)
         others["sparw_window_sweep"] = window_sweep(cc, torch, dev, grid, mlp, o16)
         others["sparw_phi_sweep"] = phi_sweep(cc, torch, dev, grid, o16, active)
+        others["config_hash_grid"] = hash_workload(cc, torch, dev, grid, g_h)
 
     if rank == 0:
         line = {

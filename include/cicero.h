@@ -226,6 +226,34 @@ cicero_status cicero_batch_autotune_brick(const cicero_job *jobs, int n_jobs, co
                                           int *best_brick, float *ms);
 
 /* ---------------------------------------------------------------------------------------------
+ * Hash-encoded rendering (the hierarchical-encoding workload of Sec. IV-A "Accommodating
+ * Hierarchical Data Encodings"; Instant-NGP-like).  Density, occupancy and the box come from
+ * `grid` (its `features` and `C` are ignored and may be NULL / 0); the colour features come from a
+ * multiresolution hash encoding: level l divides the box into res[l] cells per axis; its
+ * (res+1)^3 vertices are stored densely at x + (res+1)(y + (res+1) z) when they fit the level's
+ * table of T = 2^log2_size entries, otherwise at the spatial hash (x * 1) xor (y * 2654435761) xor
+ * (z * 805459861) mod T of 32-bit unsigned integers; each level's 2 features are the trilinear
+ * interpolation of its 8 corner entries, and the levels are concatenated as the MLP's features
+ * (mlp->in_dim = 2 levels + 3 + 6 n_freq <= 48).  Every level is gathered directly from the table
+ * in global memory (the paper's non-streaming fallback; an Instant-NGP-sized table set fits in
+ * GB300's L2), in the brick order of the density grid.  BF16 MLP only.  Workspace:
+ * cicero_render_hash_workspace_size (rays = H*W). */
+typedef struct {
+    int levels;            /* 1..16 */
+    int features;          /* per level: 2 */
+    int log2_size;         /* entries per level T = 2^log2_size, 1..24 */
+    int res[16];           /* cells per axis of each level */
+    cicero_dtype dtype;    /* of the table: F16 or F32 */
+    const void *table;     /* [levels][T][features], device */
+} cicero_hash_grid;
+
+cicero_status cicero_render_hash(const cicero_grid *grid, const cicero_hash_grid *hash, const cicero_mlp *mlp,
+                                 const cicero_camera *cam, const cicero_sampling *sampling, const cicero_options *opt,
+                                 float *rgb, float *depth, void *workspace, size_t ws_bytes, void *stream);
+size_t cicero_render_hash_workspace_size(const cicero_grid *grid, const cicero_hash_grid *hash, int n_rays,
+                                         const cicero_sampling *sampling, const cicero_options *opt);
+
+/* ---------------------------------------------------------------------------------------------
  * Bilinear resampling, for the DS-2 comparator of the evaluation (render the frame at half
  * resolution, then upsample it to the original resolution by bilinear interpolation).  Pixel
  * centres align: output pixel (i, j) samples src at ((i + 1/2) w / W - 1/2, (j + 1/2) h / H - 1/2)

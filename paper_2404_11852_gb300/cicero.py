@@ -51,6 +51,11 @@ class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("brick", C.c_int), ("max_records", C.c_longlong)]
 
 
+class HashGridDesc(C.Structure):
+    _fields_ = [("levels", C.c_int), ("features", C.c_int), ("log2_size", C.c_int), ("res", C.c_int * 16),
+                ("dtype", C.c_int), ("table", C.c_void_p)]
+
+
 class Job(C.Structure):
     _fields_ = [("grid", C.c_void_p), ("mlp", C.c_void_p), ("cam", C.c_void_p), ("sampling", C.c_void_p),
                 ("rgb", C.c_void_p), ("depth", C.c_void_p)]
@@ -84,6 +89,8 @@ _SIGS = {
     "cicero_batch_destroy": ([_P], C.c_int),
     "cicero_batch_autotune_brick": ([_P, C.c_int, _P, _P, _Z, _P, _P, _P], C.c_int),
     "cicero_extrapolate_pose": ([_P, _P, C.c_float, _P], C.c_int),
+    "cicero_render_hash": ([_P] * 8 + [_P, _Z, _P], C.c_int),
+    "cicero_render_hash_workspace_size": ([_P, _P, C.c_int, _P, _P], _Z),
     "cicero_upsample_bilinear": ([_P, C.c_int, C.c_int, C.c_int, _P, C.c_int, C.c_int, _P], C.c_int),
     "cicero_pipeline_workspace_size": ([_P, _P, _P, _P, C.c_int, C.c_longlong], _Z),
     "cicero_pipeline_create": ([_P] * 5 + [C.c_int, C.c_longlong, C.c_float, _P, _Z, _P], C.c_int),
@@ -146,20 +153,23 @@ def _ref(x):
 class DeviceGrid:
     """A grid resident on the GPU: torch tensors plus the ``cicero_grid`` descriptor."""
 
-    def __init__(self, density: torch.Tensor, features: torch.Tensor, aabb_min=(-1.0, -1.0, -1.0),
+    def __init__(self, density: torch.Tensor, features: torch.Tensor | None, aabb_min=(-1.0, -1.0, -1.0),
                  aabb_max=(1.0, 1.0, 1.0), act_shift: float = -4.0, occ: torch.Tensor | None = None):
-        assert density.dtype == features.dtype and density.dtype in (torch.float32, torch.float16)
-        self.density, self.features, self.occ = density.contiguous(), features.contiguous(), occ
-        nz, ny, nx, c = features.shape
+        """features may be None for a grid whose colour features come from a hash encoding."""
+        assert features is None or density.dtype == features.dtype
+        assert density.dtype in (torch.float32, torch.float16)
+        self.density, self.occ = density.contiguous(), occ
+        self.features = features.contiguous() if features is not None else None
+        nz, ny, nx = density.shape
         d = Grid()
         d.n[:] = [nx, ny, nz]
-        d.C = c
+        d.C = features.shape[3] if features is not None else 0
         d.aabb_min[:] = list(aabb_min)
         d.aabb_max[:] = list(aabb_max)
         d.act_shift = act_shift
         d.dtype = F16 if density.dtype == torch.float16 else F32
         d.density = self.density.data_ptr()
-        d.features = self.features.data_ptr()
+        d.features = self.features.data_ptr() if self.features is not None else None
         if occ is not None:
             self.occ = occ.to(torch.uint8).contiguous()
             d.occ = self.occ.data_ptr()
@@ -170,7 +180,7 @@ class DeviceGrid:
     def from_host(cls, g, device="cuda"):
         """From a host grid object with numpy ``density``/``features``/``occ`` arrays."""
         dens = torch.from_numpy(g.density).to(device)
-        feat = torch.from_numpy(g.features).to(device)
+        feat = torch.from_numpy(g.features).to(device) if g.features is not None else None
         occ = None if g.occ is None else torch.from_numpy(g.occ).to(device)
         return cls(dens, feat, g.aabb_min, g.aabb_max, g.act_shift, occ)
 
@@ -522,3 +532,37 @@ def cicero_upsample_bilinear(src, w: int, h: int, dst, W: int, H: int, stream=No
     ch = src.numel() // (w * h)
     _check(lib().cicero_upsample_bilinear(_ptr(src), int(w), int(h), int(ch), _ptr(dst), int(W), int(H),
                                           _stream(stream)))
+
+
+# ---------------------------------------------------------------------------------------------
+# hash-encoded rendering
+
+
+class DeviceHashGrid:
+    """A hash encoding resident on the GPU (scenes.HashGrid -> torch tensor + descriptor)."""
+
+    def __init__(self, table: torch.Tensor, res, log2_size: int):
+        assert table.dtype in (torch.float16, torch.float32) and table.shape[-1] == 2
+        self.table = table.contiguous()
+        d = HashGridDesc()
+        d.levels, d.features, d.log2_size = table.shape[0], 2, int(log2_size)
+        d.res[: len(res)] = list(res)
+        d.dtype = F16 if table.dtype == torch.float16 else F32
+        d.table = self.table.data_ptr()
+        self.desc = d
+
+    @classmethod
+    def from_host(cls, h, device="cuda"):
+        return cls(torch.from_numpy(h.table).to(device), h.res, h.log2_size)
+
+
+def cicero_render_hash(grid: Grid, hg: HashGridDesc, mlp: Mlp, cam: Camera, samp: Sampling, opt: Options, rgb, depth,
+                       ws, stream=None):
+    p, n = _ws(ws)
+    _check(lib().cicero_render_hash(C.byref(grid), C.byref(hg), C.byref(mlp), C.byref(cam), C.byref(samp),
+                                    C.byref(opt), _ptr(rgb), _ptr(depth), p, n, _stream(stream)))
+
+
+def cicero_render_hash_workspace_size(grid: Grid, hg: HashGridDesc, n_rays: int, samp: Sampling, opt: Options) -> int:
+    return int(lib().cicero_render_hash_workspace_size(C.byref(grid), C.byref(hg), int(n_rays), C.byref(samp),
+                                                       C.byref(opt)))

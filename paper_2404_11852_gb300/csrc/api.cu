@@ -100,9 +100,10 @@ static void prof_drain() {
 
 static int elem_bytes(cicero_dtype t) { return t == CICERO_F16 ? 2 : 4; }
 
-cicero_status make_geo(const cicero_grid* g, int brick, GridGeo* geo) {
+cicero_status make_geo(const cicero_grid* g, int brick, GridGeo* geo, bool with_features) {
   if (!g) return fail(CICERO_ERR_INVALID_ARG, "grid is NULL");
-  if (!g->density || !g->features) return fail(CICERO_ERR_INVALID_ARG, "grid density/features is NULL");
+  if (!g->density || (with_features && !g->features))
+    return fail(CICERO_ERR_INVALID_ARG, "grid density/features is NULL");
   if (g->dtype != CICERO_F32 && g->dtype != CICERO_F16) return fail(CICERO_ERR_INVALID_ARG, "grid dtype");
   if (g->C < 1 || g->C > 21) return fail(CICERO_ERR_UNSUPPORTED, "feature channels must be 1..21");
   if (brick != 4 && brick != 8 && brick != 16) return fail(CICERO_ERR_INVALID_ARG, "brick must be 4, 8 or 16");
@@ -128,7 +129,7 @@ cicero_status make_geo(const cicero_grid* g, int brick, GridGeo* geo) {
   geo->brick = brick;
   geo->brick_shift = brick == 4 ? 2 : brick == 8 ? 3 : 4;
   const size_t row = (size_t)g->n[0] * g->C * elem_bytes(g->dtype);
-  if (((uintptr_t)g->features & 15) || (row & 15))
+  if (with_features && (((uintptr_t)g->features & 15) || (row & 15)))
     return fail(CICERO_ERR_ALIGNMENT, "features must be 16-byte aligned with n0*C*elem a multiple of 16 (TMA)");
   const long long nbr = (long long)geo->nb[0] * geo->nb[1] * geo->nb[2];
   if (nbr > (1ll << 26)) return fail(CICERO_ERR_UNSUPPORTED, "too many bricks");
@@ -209,9 +210,9 @@ cicero_status encode_brick_map(const cicero_grid* grid, const GridGeo& geo, cons
 static bool ws_ok(const void* ws) { return ws && (((uintptr_t)ws) & 255) == 0; }
 
 static cicero_status plan_render(const cicero_grid* grid, const cicero_mlp* mlp, int n_rays, const cicero_sampling* s,
-                                 const cicero_options* opt, RenderPlan* p, bool need_mlp) {
+                                 const cicero_options* opt, RenderPlan* p, bool need_mlp, bool with_features = true) {
   const int brick = (opt && opt->brick) ? opt->brick : 8;
-  cicero_status st = make_geo(grid, brick, &p->geo);
+  cicero_status st = make_geo(grid, brick, &p->geo, with_features);
   if (st != CICERO_OK) return st;
   st = make_samp(s, &p->samp);
   if (st != CICERO_OK) return st;
@@ -772,6 +773,69 @@ long long cicero_launch_count(void) { return g_launches.load(); }
 const char* cicero_last_error(void) { return g_last_error.c_str(); }
 
 const char* cicero_version(void) { return "cicero-gb300 0.1 (sm_103a)"; }
+
+// The grid of a hash-encoded render: the caller's density grid with C = levels * features.
+static cicero_status hash_grid(const cicero_grid* grid, const cicero_hash_grid* h, const cicero_mlp* mlp,
+                               cicero_grid* out, HashGeo* hg) {
+  if (!grid || !h) return fail(CICERO_ERR_INVALID_ARG, "grid/hash is NULL");
+  if (h->levels < 1 || h->levels > kMaxHashLevels) return fail(CICERO_ERR_INVALID_ARG, "hash levels must be 1..16");
+  if (h->features != 2) return fail(CICERO_ERR_UNSUPPORTED, "hash encodings with 2 features per level only");
+  if (h->log2_size < 1 || h->log2_size > 24) return fail(CICERO_ERR_INVALID_ARG, "hash log2_size must be 1..24");
+  if (!h->table) return fail(CICERO_ERR_INVALID_ARG, "hash table is NULL");
+  if (h->dtype != CICERO_F16 && h->dtype != CICERO_F32) return fail(CICERO_ERR_INVALID_ARG, "hash dtype");
+  if (((uintptr_t)h->table) & (h->dtype == CICERO_F16 ? 3 : 7)) return fail(CICERO_ERR_ALIGNMENT, "hash table alignment");
+  *out = *grid;
+  out->C = h->levels * h->features;
+  memset(hg, 0, sizeof *hg);
+  hg->table = h->table;
+  hg->levels = h->levels;
+  hg->f16 = h->dtype == CICERO_F16;
+  hg->mask = (uint32_t)((1ull << h->log2_size) - 1);
+  for (int l = 0; l < h->levels; l++) {
+    const long long N = h->res[l];
+    if (N < 1 || N > (1 << 20)) return fail(CICERO_ERR_INVALID_ARG, "hash level resolution must be 1..2^20");
+    hg->res[l] = (int)N;
+    if ((N + 1) * (N + 1) * (N + 1) <= (1ll << h->log2_size)) hg->dense |= 1u << l;
+  }
+  for (int a = 0; a < 3; a++) {
+    hg->amin[a] = grid->aabb_min[a];
+    hg->inv_ext[a] = 1.0f / (grid->aabb_max[a] - grid->aabb_min[a]);
+  }
+  if (mlp && mlp->in_dim != out->C + 3 + 6 * mlp->n_freq)
+    return fail(CICERO_ERR_INVALID_ARG, "mlp in_dim != 2 levels + 3 + 6 n_freq");
+  return CICERO_OK;
+}
+
+cicero_status cicero_render_hash(const cicero_grid* grid, const cicero_hash_grid* hash, const cicero_mlp* mlp,
+                                 const cicero_camera* cam, const cicero_sampling* sampling, const cicero_options* opt,
+                                 float* rgb, float* depth, void* workspace, size_t ws_bytes, void* stream) {
+  cicero_status st = check_cam(cam);
+  if (st != CICERO_OK) return st;
+  if (!opt || opt->precision != CICERO_MLP_BF16)
+    return fail(CICERO_ERR_UNSUPPORTED, "hash-encoded rendering runs the BF16 tensor-core MLP only");
+  cicero_grid g;
+  HashGeo hg;
+  if ((st = hash_grid(grid, hash, mlp, &g, &hg)) != CICERO_OK) return st;
+  const int R = cam->width * cam->height;
+  RenderPlan plan;
+  if ((st = plan_render(&g, mlp, R, sampling, opt, &plan, true, false)) != CICERO_OK) return st;
+  if (!rgb) return fail(CICERO_ERR_INVALID_ARG, "rgb is NULL");
+  if (!ws_ok(workspace)) return fail(CICERO_ERR_INVALID_ARG, "workspace must be non-NULL and 256-byte aligned");
+  RenderWs w;
+  if (!carve_render_ws(workspace, ws_bytes, plan, &w)) return fail(CICERO_ERR_WORKSPACE_TOO_SMALL, "workspace too small");
+  return run_render(&g, mlp_ptrs(mlp), plan, camera_src(cam), w, single_out(rgb, depth, nullptr, nullptr), false,
+                    (cudaStream_t)stream, &hg);
+}
+
+size_t cicero_render_hash_workspace_size(const cicero_grid* grid, const cicero_hash_grid* hash, int n_rays,
+                                         const cicero_sampling* sampling, const cicero_options* opt) {
+  cicero_grid g;
+  HashGeo hg;
+  RenderPlan plan;
+  if (hash_grid(grid, hash, nullptr, &g, &hg) != CICERO_OK) return 0;
+  if (plan_render(&g, nullptr, n_rays, sampling, opt, &plan, false, false) != CICERO_OK) return 0;
+  return render_ws_bytes(plan);
+}
 
 cicero_status cicero_upsample_bilinear(const float* src, int w, int h, int channels, float* dst, int W, int H,
                                        void* stream) {

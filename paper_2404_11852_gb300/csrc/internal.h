@@ -84,7 +84,7 @@ size_t render_ws_bytes(const RenderPlan& p);
 bool carve_render_ws(void* ws, size_t bytes, const RenderPlan& p, RenderWs* out);
 
 // grid/sampling validation and geometry (api.cu)
-cicero_status make_geo(const cicero_grid* g, int brick, GridGeo* geo);
+cicero_status make_geo(const cicero_grid* g, int brick, GridGeo* geo, bool with_features = true);
 cicero_status make_samp(const cicero_sampling* s, Samp* out);
 cicero_status check_mlp(const cicero_mlp* m, const cicero_grid* g);
 
@@ -94,8 +94,10 @@ struct MlpPtrs {
   int in_dim, n_freq;
 };
 
+struct HashGeo;
 cicero_status run_render(const cicero_grid* grid, const MlpPtrs& mlp, const RenderPlan& plan, const RaySrc& src,
-                         const RenderWs& ws, const OutBufs& out, bool stop_after_bucketing, cudaStream_t st);
+                         const RenderWs& ws, const OutBufs& out, bool stop_after_bucketing, cudaStream_t st,
+                         const HashGeo* hash = nullptr);
 
 cicero_status run_rit_export(const RenderWs& ws, int n_bricks, int S, int32_t* brick_offsets, int32_t* samples,
                              cudaStream_t st);
@@ -145,6 +147,20 @@ cicero_status run_render_batch(const BatchPlan& b, cudaStream_t st);
 cicero_status launch_gather_mlp_bf16_batch(const BatchPlan& b, cudaStream_t st);
 
 cicero_status run_upsample(const float* src, int w, int h, int C, float* dst, int W, int H, cudaStream_t st);
+
+// Multiresolution hash encoding of the hash-grid workload, as the kernels read it.
+constexpr int kMaxHashLevels = 16;
+struct HashGeo {
+  const void* table;            // [levels][T][2], FP16 or FP32
+  int levels;
+  bool f16;
+  uint32_t mask;                // T - 1
+  uint32_t dense;               // bit l: level l stored densely
+  int res[kMaxHashLevels];      // cells per axis
+  float amin[3], inv_ext[3];    // the box: p -> (p - amin) * inv_ext in [0, 1]
+};
+cicero_status launch_gather_mlp_bf16_hash(const GridGeo& geo, const MlpPtrs& mlp, const RenderWs& ws,
+                                          const HashGeo& hg, cudaStream_t st);
 
 // BF16 tensor-core Feature Computation (mlp_tc.cu)
 cicero_status launch_gather_mlp_bf16(const cicero_grid* grid, const GridGeo& geo, const Samp& samp, const RaySrc& src,

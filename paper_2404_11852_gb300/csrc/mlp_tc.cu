@@ -514,6 +514,52 @@ __device__ __forceinline__ Group setup(char* sm, const MlpPtrs* mlp, int groups,
 
 }  // namespace tc
 
+// Features of the multiresolution hash encoding at world position p: per level, the box mapped
+// onto res cells per axis, the 8 corner entries (dense index where the level's vertices fit the
+// table, else the spatial hash (x * 1 xor y * 2654435761 xor z * 805459861) mod T) interpolated
+// trilinearly; two features per level, levels concatenated.  The tables are read straight from
+// global memory (they fit in L2).
+template <int LL, typename T>
+__device__ __forceinline__ void hash_features(const HashGeo& h, const float p[3], float* x) {
+  const int L = LL ? LL : h.levels;
+  float pn[3];
+#pragma unroll
+  for (int a = 0; a < 3; a++) pn[a] = __saturatef(__fmul_rn(__fsub_rn(p[a], h.amin[a]), h.inv_ext[a]));
+#pragma unroll
+  for (int l = 0; l < (LL ? LL : kMaxHashLevels); l++) {
+    if (!LL && l >= L) break;
+    const int N = h.res[l];
+    int i0[3];
+    float f[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+      const float gx = pn[a] * (float)N;
+      const int i = min((int)gx, N - 1);
+      i0[a] = i;
+      f[a] = gx - (float)i;
+    }
+    const uint32_t s1 = (uint32_t)N + 1u;
+    const bool dense = (h.dense >> l) & 1u;
+    const size_t base = (size_t)l * (h.mask + 1u);
+    float a0 = 0.0f, a1 = 0.0f;
+#pragma unroll
+    for (int q = 0; q < 8; q++) {
+      const uint32_t cx = (uint32_t)i0[0] + (q & 1), cy = (uint32_t)i0[1] + ((q >> 1) & 1),
+                     cz = (uint32_t)i0[2] + (q >> 2);
+      const uint32_t idx = dense ? cx + s1 * (cy + s1 * cz) : ((cx ^ (cy * 2654435761u) ^ (cz * 805459861u)) & h.mask);
+      const float w = ((q & 1) ? f[0] : 1.f - f[0]) * (((q >> 1) & 1) ? f[1] : 1.f - f[1]) *
+                      ((q >> 2) ? f[2] : 1.f - f[2]);
+      float2 v;
+      if constexpr (sizeof(T) == 2) v = __half22float2(__ldg((const __half2*)h.table + base + idx));
+      else v = __ldg((const float2*)h.table + base + idx);
+      a0 += w * v.x;
+      a1 += w * v.y;
+    }
+    x[2 * l] = a0;
+    x[2 * l + 1] = a1;
+  }
+}
+
 // One group's tiles [t_begin, t_end) through gather + MLP, software-pipelined: while layer 3 of
 // tile t runs on the tensor cores (its A operand is in TMEM, so shared memory is free), the group
 // gathers tile t + 1 into its A buffer.  `loaded` is the brick held in the group's tile buffer
@@ -521,10 +567,12 @@ __device__ __forceinline__ Group setup(char* sm, const MlpPtrs* mlp, int groups,
 // with alive false on entry it does nothing.
 // The grid's geometry `g` and the MLP dimensions are read where they live (kernel parameters for
 // one grid, the job table for a batch); `map` is the generic address of the feature grid's tensor map.
-template <typename T, int CC, int NF>
+// With HASH, the features come from the hash encoding `hg` instead of staged bricks (no TMA).
+template <typename T, int CC, int NF, bool HASH = false>
 __device__ __forceinline__ bool gather_tiles(char* sm, tc::Group& G, const GridGeo& g, const CUtensorMap* map,
                                              int in_dim, int n_freq, int vb, int vx, int box_bytes, const RenderWs& w,
-                                             long long t_begin, long long t_end, int& loaded, bool alive) {
+                                             long long t_begin, long long t_end, int& loaded, bool alive,
+                                             const HashGeo* hg = nullptr) {
   using namespace tc;
   if (!alive) return false;
   const int B = g.brick, C = CC ? CC : g.C, m = G.m;
@@ -563,7 +611,7 @@ __device__ __forceinline__ bool gather_tiles(char* sm, tc::Group& G, const GridG
     osid = kNoRecord;
   };
   bool tma_pending = false, mma_pending = false;
-  if (t_begin < t_end) {
+  if (!HASH && t_begin < t_end) {
     if (m == 0) tma_brick(tg);
     loaded = (int)tg.z;
     tma_pending = true;
@@ -584,7 +632,7 @@ __device__ __forceinline__ bool gather_tiles(char* sm, tc::Group& G, const GridG
       }
       mma_pending = true;
       // every thread is done with the staged brick: copy the next tile's brick if it differs
-      if (gather && (int)tg.z != loaded) {
+      if (!HASH && gather && (int)tg.z != loaded) {
         if (m == 0) tma_brick(tg);
         loaded = (int)tg.z;
         tma_pending = true;
@@ -632,24 +680,28 @@ __device__ __forceinline__ bool gather_tiles(char* sm, tc::Group& G, const GridG
       for (int j = 0; j < kK1; j++) x[j] = 0.0f;
       if (m < mcnt) {
         const float p[3] = {gpw.x, gpw.y, gpw.z};
-        int l[3];
-        float f[3];
-        bool ok = true;
+        if constexpr (HASH) {
+          hash_features<CC / 2, T>(*hg, p, x);
+        } else {
+          int l[3];
+          float f[3];
+          bool ok = true;
 #pragma unroll
-        for (int a = 0; a < 3; a++) {
-          const float ga = __fmul_rn(__fsub_rn(p[a], g.amin[a]), g.inv_h[a]);
-          int i = (int)floorf(ga);
-          if (i > g.n[a] - 2) i = g.n[a] - 2;
-          f[a] = __fsub_rn(ga, (float)i);
-          l[a] = i - (a == 0 ? bx : a == 1 ? by : bz) * B;
-          ok = ok && l[a] >= 0 && l[a] < B;
+          for (int a = 0; a < 3; a++) {
+            const float ga = __fmul_rn(__fsub_rn(p[a], g.amin[a]), g.inv_h[a]);
+            int i = (int)floorf(ga);
+            if (i > g.n[a] - 2) i = g.n[a] - 2;
+            f[a] = __fsub_rn(ga, (float)i);
+            l[a] = i - (a == 0 ? bx : a == 1 ? by : bz) * B;
+            ok = ok && l[a] >= 0 && l[a] < B;
+          }
+          if (!ok)
+            set_err(&w.hdr[0], kErrInternal);
+          else if constexpr (CC == 12 && sizeof(T) == 2)
+            tri_tile_h2((const __half*)tile, vb, vx, l, f, x);
+          else
+            tri_tile<T, CC>(tile, vb, vx, C, l, f, x);
         }
-        if (!ok)
-          set_err(&w.hdr[0], kErrInternal);
-        else if constexpr (CC == 12 && sizeof(T) == 2)
-          tri_tile_h2((const __half*)tile, vb, vx, l, f, x);
-        else
-          tri_tile<T, CC>(tile, vb, vx, C, l, f, x);
         const float d[3] = {gdir.y, gdir.z, gdir.w};
         encode_dir_fast<NF>(d, n_freq, x + C);
         if (in_dim < kK1) x[CC && NF ? (CC + 3 + 6 * NF) % kK1 : in_dim % kK1] = 1.0f;  // folded layer-1 bias
@@ -704,6 +756,26 @@ __global__ void __launch_bounds__(512, 1) k_gather_mlp_bf16(GridGeo g, int S, Ml
   const long long t_begin = c_begin + (span * G.g) / groups, t_end = c_begin + (span * (G.g + 1)) / groups;
   int loaded = -1;
   gather_tiles<T, CC, NF>(sm, G, g, &fmap, mlp.in_dim, mlp.n_freq, vb, vx, box_bytes, w, t_begin, t_end, loaded, true);
+  tmem_free_all(tmem_base);
+}
+
+// The hash-grid workload: the single-grid kernel with features from the hash encoding (every level
+// gathered from global memory / L2; no brick staging).
+template <typename T, int CC, int NF>
+__global__ void __launch_bounds__(512, 1) k_gather_mlp_bf16_hash(GridGeo g, MlpPtrs mlp, RenderWs w,
+                                                                 const __grid_constant__ HashGeo hg, int groups) {
+  using namespace tc;
+  extern __shared__ __align__(1024) char sm[];
+  Group G = setup(sm, &mlp, groups, 0);
+  const uint32_t tmem_base = G.tmem - (uint32_t)(G.g * 128);
+  const uint32_t n_tiles = w.hdr[1];
+  const uint32_t per = (n_tiles + gridDim.x - 1) / gridDim.x;
+  const uint32_t c_begin = blockIdx.x * per, c_end = min(n_tiles, c_begin + per);
+  const uint32_t span = c_end > c_begin ? c_end - c_begin : 0;
+  const long long t_begin = c_begin + (span * G.g) / groups, t_end = c_begin + (span * (G.g + 1)) / groups;
+  int loaded = -1;
+  gather_tiles<T, CC, NF, true>(sm, G, g, nullptr, mlp.in_dim, mlp.n_freq, 0, 0, 0, w, t_begin, t_end, loaded, true,
+                                &hg);
   tmem_free_all(tmem_base);
 }
 
@@ -809,6 +881,32 @@ cicero_status launch_gather_mlp_bf16(const cicero_grid* grid, const GridGeo& geo
                : launch_tc<float, 12, 4>(geo, ws.S, mlp, ws, map, box, st);
   return f16 ? launch_tc<__half, 0, 0>(geo, ws.S, mlp, ws, map, box, st)
              : launch_tc<float, 0, 0>(geo, ws.S, mlp, ws, map, box, st);
+}
+
+template <typename T, int CC, int NF>
+static cicero_status launch_tc_hash(const GridGeo& geo, const MlpPtrs& mlp, const RenderWs& ws, const HashGeo& hg,
+                                    cudaStream_t st) {
+  using namespace tc;
+  const int groups = kMaxGroups;
+  const int smem = std::max(Smem::groups + groups * group_bytes(0), 120 * 1024);
+  auto kern = k_gather_mlp_bf16_hash<T, CC, NF>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_gather_mlp_bf16_hash)");
+  {
+    ProfScope ps(kStGatherMlp, st);
+    kern<<<num_sms(), 128 * groups, smem, st>>>(geo, mlp, ws, hg, groups);
+  }
+  count_launches(1);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? CICERO_OK : cuda_fail(e, "k_gather_mlp_bf16_hash");
+}
+
+cicero_status launch_gather_mlp_bf16_hash(const GridGeo& geo, const MlpPtrs& mlp, const RenderWs& ws,
+                                          const HashGeo& hg, cudaStream_t st) {
+  // the kernel's type is the table's element type; 8 levels x 2 features with 4 frequencies is specialised
+  if (hg.levels == 8 && mlp.n_freq == 4)
+    return hg.f16 ? launch_tc_hash<__half, 16, 4>(geo, mlp, ws, hg, st) : launch_tc_hash<float, 16, 4>(geo, mlp, ws, hg, st);
+  return hg.f16 ? launch_tc_hash<__half, 0, 0>(geo, mlp, ws, hg, st) : launch_tc_hash<float, 0, 0>(geo, mlp, ws, hg, st);
 }
 
 template <typename T, int CC, int NF>

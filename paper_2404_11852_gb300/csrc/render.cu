@@ -938,7 +938,8 @@ static cicero_status launch_f32(const GridGeo& geo, const RaySrc& src, int S, co
 }
 
 cicero_status run_render(const cicero_grid* grid, const MlpPtrs& mlp, const RenderPlan& plan, const RaySrc& src,
-                         const RenderWs& ws, const OutBufs& out, bool stop_after_bucketing, cudaStream_t st) {
+                         const RenderWs& ws, const OutBufs& out, bool stop_after_bucketing, cudaStream_t st,
+                         const HashGeo* hash) {
   const GridGeo& geo = plan.geo;
   const bool f16 = grid->dtype == CICERO_F16;
   const int mb = blocks_for_warps(src.n_max, 16);
@@ -964,11 +965,14 @@ cicero_status run_render(const cicero_grid* grid, const MlpPtrs& mlp, const Rend
   if (e != cudaSuccess) return cuda_fail(e, "march/bucket kernels");
   if (stop_after_bucketing) return CICERO_OK;
 
+  cicero_status s;
   const BrickBox box = brick_box(geo, f16 ? 2 : 4);
   CUtensorMap map;
-  cicero_status s = encode_brick_map(grid, geo, box, &map);
-  if (s != CICERO_OK) return s;
-  if (plan.precision == CICERO_MLP_BF16) {
+  if (hash) {
+    s = launch_gather_mlp_bf16_hash(geo, mlp, ws, *hash, st);  // features from the hash encoding
+  } else if ((s = encode_brick_map(grid, geo, box, &map)) != CICERO_OK) {
+    return s;
+  } else if (plan.precision == CICERO_MLP_BF16) {
     s = launch_gather_mlp_bf16(grid, geo, plan.samp, src, mlp, ws, map, box, st);
   } else {
     s = f16 ? launch_f32<__half>(geo, src, plan.S, mlp, ws, map, box, st)
