@@ -450,7 +450,9 @@ __global__ void __launch_bounds__(256) k_tiles(GridGeo g, RenderWs w) {
 }
 
 // K3: counting sort of the records by brick; the payload moves into brick order so that the
-// gather kernels stream it (order inside a brick is unspecified).
+// gather kernels stream it (order inside a brick is unspecified).  A warp takes one ray at a time
+// in chunks of 32 records; each chunk's records and their bricks' offsets load together, and the
+// next ray's header and first chunk are loaded while the current ray's atomics are in flight.
 __global__ void __launch_bounds__(256) k_scatter(RaySrc src, RenderWs w) {
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -459,35 +461,72 @@ __global__ void __launch_bounds__(256) k_scatter(RaySrc src, RenderWs w) {
   const unsigned full = 0xffffffffu;
   const unsigned lt_mask = (1u << lane) - 1u;
   const unsigned le_mask = (2u << lane) - 1u;
-  for (int r = warp; r < R; r += nwarps) {
-    const uint32_t n = w.ray_n[r], start = w.ray_start[r];
-    const float4 dir = n ? w.ray_dir[r] : make_float4(0.f, 0.f, 0.f, 0.f);
+  struct Chunk {
+    uint32_t key, boff;
+    float4 pw;
+  };
+  auto load_chunk = [&](uint32_t start, uint32_t n, uint32_t j0, Chunk& c) {
+    const uint32_t j = j0 + lane;
+    const bool valid = j < n;
+    c.key = valid ? w.rec_key[start + j] : 0xffffffffu;
+    c.pw = valid ? w.rec_pw[start + j] : make_float4(0.f, 0.f, 0.f, 0.f);
+    c.boff = valid ? w.brick_off[c.key] : 0u;
+  };
+  // the warp's current ray and its first chunk
+  int r = warp;
+  uint32_t n = 0, start = 0;
+  float4 dir = make_float4(0.f, 0.f, 0.f, 0.f);
+  Chunk cur;
+  if (r < R) {
+    n = w.ray_n[r];
+    start = w.ray_start[r];
+    dir = w.ray_dir[r];
+    load_chunk(start, n, 0, cur);
+  }
+  for (; r < R; r += nwarps) {
+    // the next ray's header and first chunk
+    const int rn = r + nwarps;
+    uint32_t nn = 0, nstart = 0;
+    float4 ndir = make_float4(0.f, 0.f, 0.f, 0.f);
+    Chunk nxt;
+    nxt.key = 0xffffffffu;
+    if (rn < R) {
+      nn = w.ray_n[rn];
+      nstart = w.ray_start[rn];
+      ndir = w.ray_dir[rn];
+    }
     for (uint32_t j0 = 0; j0 < n; j0 += 32) {
+      Chunk c = cur;
+      if (j0 + 32 < n) load_chunk(start, n, j0 + 32, cur);  // this ray's next chunk
+      else if (rn < R) load_chunk(nstart, nn, 0, nxt);        // or the next ray's first
       const uint32_t j = j0 + lane;
       const bool valid = j < n;
       const uint32_t q = start + j;
-      const uint32_t key = valid ? w.rec_key[q] : 0xffffffffu;
-      const float4 pw = valid ? w.rec_pw[q] : make_float4(0.f, 0.f, 0.f, 0.f);
       const unsigned vmask = __ballot_sync(full, valid);
-      const uint32_t prev = __shfl_up_sync(full, key, 1);
-      const bool head = valid && (lane == 0 || prev != key);
+      const uint32_t prev = __shfl_up_sync(full, c.key, 1);
+      const bool head = valid && (lane == 0 || prev != c.key);
       const unsigned heads = __ballot_sync(full, head);
       uint32_t off = 0;
       if (head) {
         const unsigned after = heads & ~le_mask;
         const int end = after ? __ffs(after) - 1 : 32;
         const unsigned run = vmask & ~lt_mask & (end == 32 ? full : ((1u << end) - 1u));
-        off = atomicAdd(&w.brick_cur[key], (uint32_t)__popc(run));
+        off = atomicAdd(&w.brick_cur[c.key], (uint32_t)__popc(run));
       }
       // every lane takes the base of its run's head
       const int hl = 31 - __clz(heads & le_mask);
       off = __shfl_sync(full, off, hl < 0 ? 0 : hl);
       if (valid) {
-        const uint32_t dst = w.brick_off[key] + off + (uint32_t)(lane - hl);
-        w.srt_pw[dst] = pw;
+        const uint32_t dst = c.boff + off + (uint32_t)(lane - hl);
+        w.srt_pw[dst] = c.pw;
         w.srt_qd[dst] = make_float4(__uint_as_float(q), dir.x, dir.y, dir.z);
       }
     }
+    if (n == 0 && rn < R) load_chunk(nstart, nn, 0, nxt);
+    n = nn;
+    start = nstart;
+    dir = ndir;
+    cur = nxt;
   }
 }
 
