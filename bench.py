@@ -36,7 +36,7 @@ HOLE_RECORDS = 128_000_000  # record capacity of the batched hole render (6.7 GB
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_gather_mlp_bf16 launch on the
 # 800x800 reference frame, from a one-pass ncu capture of this benchmark, and the SHA-1 of the
 # kernel sources it was taken on; the roofline reports it only while those sources are unchanged.
-GATHER_TRAFFIC = {"bytes": 2499950080 + 1201474304, "sources_sha1": "6879172ada0c195223960e350463f4a7892a192e"}
+GATHER_TRAFFIC = {"bytes": 2500065536 + 1201630976, "sources_sha1": "a0c846425698818bee1092f0098bf033f85447ef"}
 GATHER_SOURCES = ("mlp_tc.cu", "common.cuh", "internal.h")
 
 
@@ -59,8 +59,8 @@ def small_case(brick: int = 4):
     """A reduced run of the same kernels for profiler captures (the grid stays 416 MB > L2).
 
     Kernel launch order: reference frame BF16 twice, FP32 once (one k_march, bucketing, gather
-    and composite each), then per target one warp and one hole render.  No autotuning, so a
-    capture's launch index (-s) does not depend on timing."""
+    and composite each), then per target one warp and one hole render, then the frame with a hash
+    encoding twice.  No autotuning, so a capture's launch index (-s) does not depend on timing."""
     import torch
     import scenes
     from paper_2404_11852_gb300 import build, cicero as cc
@@ -88,6 +88,13 @@ def small_case(brick: int = 4):
         cc.cicero_warp(rgb, depth, cd, td, 180.0, grid.desc, sd, wr, wd, mask, hidx, nh, wws)
         cc.cicero_render_holes(grid.desc, mlp.desc, td, sd, o16, hidx, nh, R, wr, wd, ws)
     cc.cicero_workspace_status(ws)
+    # the hash-encoded frame (8 levels x 2 FP16, 2^19 entries), twice
+    h = scenes.make_hash_grid(8, 2, 19, 16, 1024, seed=777)
+    hd, md = cc.DeviceHashGrid.from_host(h), cc.DeviceMlp.from_host(scenes.make_mlp(16, seed=778))
+    wsh = cc.workspace(cc.cicero_render_hash_workspace_size(grid.desc, hd.desc, R, sd, o16))
+    for _ in range(2):
+        cc.cicero_render_hash(grid.desc, hd.desc, md.desc, cd, sd, o16, rgb, depth, wsh)
+    cc.cicero_workspace_status(wsh)
     torch.cuda.synchronize()
     print(json.dumps({"case": "small", "image": f"{n}x{n}", "brick": brick, "active_samples_reference": active}))
 
