@@ -644,17 +644,21 @@ def backward_workload(cc, torch, dev):
     def fwd():
         cc.cicero_render_rays(gd.desc, md.desc, ot, dt, sd, opt, rgb, depth, None, None, ws_f)
 
-    def bwd():
+    dm = torch.zeros(m.flat().size, device=dev)
+
+    def bwd(d_mlp=None):
         torch.sub(rgb, tgt, out=d_rgb).mul_(2.0 / rgb.numel())  # dL/drgb of the MSE loss
-        cc.cicero_render_backward(gd.desc, md.desc, ot, dt, sd, d_rgb, dd, df, None, ws_b)
+        cc.cicero_render_backward(gd.desc, md.desc, ot, dt, sd, d_rgb, dd, df, d_mlp, ws_b)
 
     fwd()
     t_f = event_ms(torch, fwd, 5)
     t_b = event_ms(torch, bwd, 5)
+    t_bm = event_ms(torch, lambda: bwd(dm), 5)
     cc.cicero_workspace_status(ws_f)
     cc.cicero_workspace_status(ws_b)
     return {"workload": "8192 rays x 256 samples, 160^3 x 12 FP32 grid, MSE loss", "forward_ms": t_f,
-            "backward_ms": t_b, "rays_per_s_fwd_bwd": R / ((t_f + t_b) / 1e3),
+            "backward_ms": t_b, "backward_with_mlp_weights_ms": t_bm,
+            "rays_per_s_fwd_bwd": R / ((t_f + t_b) / 1e3),
             "grad_bytes": int(dd.numel() * 4 + df.numel() * 4)}
 
 

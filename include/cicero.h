@@ -375,7 +375,10 @@ cicero_status cicero_warp_noalloc(const float *ref_rgb, const float *ref_depth,
  * offline; the gradient of its rendering function).  Given d_rgb = dL/drgb [n_rays][3], the
  * gradient is ACCUMULATED into d_density [n2][n1][n0], d_features [n2][n1][n0][C] (both FP32;
  * zero them first) and, when d_mlp is not NULL, into the MLP gradient laid out as
- * [w1, b1, w2, b2, w3, b3].  Each ray's forward pass is recomputed (nothing is stored by the
+ * [w1 [hidden][in_dim], b1 [hidden], w2 [hidden][hidden], b2 [hidden], w3 [3][hidden], b3 [3]]
+ * (FP32, the layout of cicero_mlp's tensors back to back).  Gradients are summed with atomic adds,
+ * so the order of the sums, and the last bits of the result, vary between calls.  Each ray's
+ * forward pass is recomputed (nothing is stored by the
  * forward); early stop is a fixed truncation.  For composited sample k:
  *   dL/dc_k = w_k g;  dL/dsigma_k = delta (T_{k+1} g.c_k - g.R_k), R_k = sum_{j>k} w_j c_j + T_end bg;
  *   dL/draw_k = dL/dsigma_k sigmoid(raw_k + shift); MLP chain rule; trilinear adjoint. */

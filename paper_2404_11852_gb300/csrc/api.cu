@@ -683,7 +683,6 @@ cicero_status cicero_render_backward(const cicero_grid* grid, const cicero_mlp* 
                                      void* workspace, size_t ws_bytes, void* stream) {
   if (n_rays > 0 && (!ray_o || !ray_d || !d_rgb)) return fail(CICERO_ERR_INVALID_ARG, "ray_o/ray_d/d_rgb is NULL");
   if (!d_density || !d_features) return fail(CICERO_ERR_INVALID_ARG, "d_density/d_features is NULL");
-  if (d_mlp) return fail(CICERO_ERR_UNSUPPORTED, "MLP weight gradients are not implemented in this build");
   RenderPlan plan;
   cicero_status st = plan_render(grid, mlp, n_rays, sampling, nullptr, &plan, true);
   if (st != CICERO_OK) return st;
@@ -699,7 +698,7 @@ cicero_status cicero_render_backward(const cicero_grid* grid, const cicero_mlp* 
   src.o = ray_o;
   src.d = ray_d;
   src.n_max = n_rays;
-  return run_backward(grid, mlp_ptrs(mlp), plan, src, w, d_rgb, d_density, d_features, (cudaStream_t)stream);
+  return run_backward(grid, mlp_ptrs(mlp), plan, src, w, d_rgb, d_density, d_features, d_mlp, (cudaStream_t)stream);
 }
 
 size_t cicero_backward_workspace_size(const cicero_grid* grid, int n_rays, const cicero_sampling* sampling) {

@@ -9,7 +9,9 @@
 //   B2 k_bwd_brick     per brick (Ray Index Table order), 64 samples at a time: MLP forward and
 //                      backward on CUDA cores down to dL/dfeatures, then the trilinear adjoint
 //                      accumulated in a shared-memory copy of the brick's vertices; when the CTA
-//                      leaves the brick, one global atomicAdd per touched vertex entry.
+//                      leaves the brick, one global atomicAdd per touched vertex entry.  With
+//                      d_mlp, the weight gradients are summed over the CTA's tiles in registers
+//                      and added to d_mlp once per CTA.
 #include <cuda_runtime.h>
 
 #include <string.h>
@@ -75,25 +77,30 @@ __global__ void __launch_bounds__(256) k_bwd_ray(RaySrc src, Samp s, RenderWs w,
   }
 }
 
+// Tiles are stored feature-major, [feature][sample], with a row stride of kLD = 68 floats: 64
+// samples plus 4 of padding, so that 8 threads reading one float4 each from 8 consecutive
+// feature rows at the same samples hit 8 different bank quads (68 = 4 mod 32).
+constexpr int kLD = 68;
+
 struct BwdSmem {
   static constexpr int w1t = 0;                          // [48][128]
   static constexpr int w2t = w1t + kMaxIn * kHidden * 4; // [128][128]
   static constexpr int w3 = w2t + kHidden * kHidden * 4; // [3][128]
   static constexpr int b1 = w3 + 3 * kHidden * 4;
   static constexpr int b2 = b1 + kHidden * 4;
-  static constexpr int x = b2 + kHidden * 4;             // [48][64]  inputs, later dL/dx
-  static constexpr int h1 = x + kMaxIn * kBT * 4;        // [128][64] h1, later dL/dh1
-  static constexpr int h2 = h1 + kHidden * kBT * 4;      // [128][64] h2, later dL/dh2
-  static constexpr int dz = h2 + kHidden * kBT * 4;      // [3][64]
-  static constexpr int meta = dz + 3 * kBT * 4;          // per sample: l[3] (int), f[3], draw, valid
+  static constexpr int x = b2 + kHidden * 4;             // [48][kLD]  inputs
+  static constexpr int h1 = x + kMaxIn * kLD * 4;        // [128][kLD] h1, later dL/dh1
+  static constexpr int h2 = h1 + kHidden * kLD * 4;      // [128][kLD] h2, later dL/dh2, then dL/dfeatures
+  static constexpr int dz = h2 + kHidden * kLD * 4;      // [3][kLD]
+  static constexpr int meta = dz + 3 * kLD * 4;          // per sample: l[3] (int), f[3], draw, valid
   static constexpr int gacc = meta + 8 * kBT * 4;        // [vb^3][C+1]
 };
 
-// acc[i][j]: rows tm*4+i (i < 4), cols {tn*4+j, 64+tn*4+(j-4)}; A [K][64], B [K][128] k-major
+// acc[i][j]: rows tm*4+i (i < 4), cols {tn*4+j, 64+tn*4+(j-4)}; A [K][kLD], B [K][128] k-major
 __device__ __forceinline__ void gemm64(const float* A, const float* Bw, int K, int tm, int tn, float acc[4][8]) {
 #pragma unroll 2
   for (int k = 0; k < K; k++) {
-    const float4 a = *reinterpret_cast<const float4*>(&A[k * kBT + tm * 4]);
+    const float4 a = *reinterpret_cast<const float4*>(&A[k * kLD + tm * 4]);
     const float4 b0 = *reinterpret_cast<const float4*>(&Bw[k * kHidden + tn * 4]);
     const float4 b1 = *reinterpret_cast<const float4*>(&Bw[k * kHidden + 64 + tn * 4]);
     const float av[4] = {a.x, a.y, a.z, a.w};
@@ -109,7 +116,7 @@ __device__ __forceinline__ void gemm64(const float* A, const float* Bw, int K, i
 __device__ __forceinline__ void gemm64_bt(const float* A, const float* Bt, int K, int tm, int tn, float acc[4][8]) {
 #pragma unroll 2
   for (int k = 0; k < K; k++) {
-    const float4 a = *reinterpret_cast<const float4*>(&A[k * kBT + tm * 4]);
+    const float4 a = *reinterpret_cast<const float4*>(&A[k * kLD + tm * 4]);
     const float av[4] = {a.x, a.y, a.z, a.w};
     float bv[8];
 #pragma unroll
@@ -119,6 +126,10 @@ __device__ __forceinline__ void gemm64_bt(const float* A, const float* Bt, int K
 #pragma unroll
       for (int j = 0; j < 8; j++) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
   }
+}
+
+__device__ __forceinline__ float dot4(float4 a, float4 b) {
+  return fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, a.w * b.w)));
 }
 
 __device__ __forceinline__ int col8(int tn, int j) { return j < 4 ? tn * 4 + j : 64 + tn * 4 + (j - 4); }
@@ -157,10 +168,14 @@ __device__ void flush_brick(const GridGeo& g, int b, float* gacc, int vb, float*
   }
 }
 
-template <typename T>
+// WG: also accumulate the MLP weight gradients.  Each thread keeps its share in registers for the
+// whole launch and adds it to d_mlp once at the end:
+//   dW2[o][i] (o = tn + 16a, i = tm + 16b, a, b < 8)   dW1[o][k] (k = tm + 16b, b < 3)   db1[o]
+//   dW3[j][o], db2[o] (o = tid mod 128, one half of the tile's samples each)   db3[j]
+template <typename T, bool WG>
 __global__ void __launch_bounds__(256, 1) k_bwd_brick(GridGeo g, RaySrc src, MlpPtrs mlp, RenderWs w,
                                                       const T* __restrict__ feat, const float* __restrict__ d_rgb,
-                                                      float* d_dens, float* d_feat) {
+                                                      float* d_dens, float* d_feat, float* d_mlp) {
   extern __shared__ __align__(128) char sm[];
   float* w1t = (float*)(sm + BwdSmem::w1t);
   float* w2t = (float*)(sm + BwdSmem::w2t);
@@ -194,6 +209,20 @@ __global__ void __launch_bounds__(256, 1) k_bwd_brick(GridGeo g, RaySrc src, Mlp
   const uint32_t per = (n_tiles + gridDim.x - 1) / gridDim.x;
   const uint32_t t_begin = blockIdx.x * per, t_end = min(n_tiles, t_begin + per);
   const int tm = threadIdx.x & 15, tn = threadIdx.x >> 4;
+  const int ro = threadIdx.x & (kHidden - 1), rs0 = (threadIdx.x >> 7) * (kBT / 2);  // dh2 phase: row, samples
+  float gw2[8][8], gw1[8][3], gb1[8], gw3[3], gb3[3], gb2 = 0.0f;
+  if constexpr (WG) {
+#pragma unroll
+    for (int a = 0; a < 8; a++) {
+#pragma unroll
+      for (int b = 0; b < 8; b++) gw2[a][b] = 0.0f;
+#pragma unroll
+      for (int b = 0; b < 3; b++) gw1[a][b] = 0.0f;
+      gb1[a] = 0.0f;
+    }
+#pragma unroll
+    for (int j = 0; j < 3; j++) gw3[j] = gb3[j] = 0.0f;
+  }
   int cur = -1;
   for (uint32_t ti = t_begin; ti < t_end; ti++) {
     const uint4 td = w.tile[ti];
@@ -210,7 +239,8 @@ __global__ void __launch_bounds__(256, 1) k_bwd_brick(GridGeo g, RaySrc src, Mlp
     }
     for (uint32_t start = start0; start < end; start += kBT) {
       const int mcnt = (int)min((uint32_t)kBT, end - start);
-      // gather: thread m < 64 features + meta, 64 <= t < 128 encoding
+      // gather: thread m < 64 features + meta, 64 <= t < 128 encoding.  Samples past mcnt and
+      // rejected samples get x = 0 and dL/dz = 0, so they add nothing to any gradient.
       const int m = threadIdx.x & (kBT - 1), part = threadIdx.x >> 6;
       if (part < 2) {
         const bool valid = m < mcnt;
@@ -232,7 +262,7 @@ __global__ void __launch_bounds__(256, 1) k_bwd_brick(GridGeo g, RaySrc src, Mlp
             } else {
               ok = 1;
               feat_trilinear_global<T>(g, feat, i0, f, fv);
-              for (int c = 0; c < C; c++) X[c * kBT + m] = fv[c];
+              for (int c = 0; c < C; c++) X[c * kLD + m] = fv[c];
               for (int a = 0; a < 3; a++) {
                 ml[a * kBT + m] = l[a];
                 mf[a * kBT + m] = f[a];
@@ -240,20 +270,20 @@ __global__ void __launch_bounds__(256, 1) k_bwd_brick(GridGeo g, RaySrc src, Mlp
               mdraw[m] = w.rec_raw[sid];
               const float4 cw = w.rec_c[sid];
               const float cc[3] = {cw.x, cw.y, cw.z};
-              for (int j = 0; j < 3; j++) DZ[j * kBT + m] = cw.w * d_rgb[3 * r + j] * cc[j] * (1.0f - cc[j]);
+              for (int j = 0; j < 3; j++) DZ[j * kLD + m] = cw.w * d_rgb[3 * r + j] * cc[j] * (1.0f - cc[j]);
             }
           }
           if (!ok) {
-            for (int c = 0; c < C; c++) X[c * kBT + m] = 0.0f;
-            for (int j = 0; j < 3; j++) DZ[j * kBT + m] = 0.0f;
+            for (int c = 0; c < C; c++) X[c * kLD + m] = 0.0f;
+            for (int j = 0; j < 3; j++) DZ[j * kLD + m] = 0.0f;
           }
           mval[m] = ok;
         } else {
           float e[3 + 6 * 7];
           const int ne = 3 + 6 * mlp.n_freq;
           if (valid) encode_dir(d, mlp.n_freq, e);
-          for (int j = 0; j < ne; j++) X[(C + j) * kBT + m] = valid ? e[j] : 0.0f;
-          for (int j = C + ne; j < kMaxIn; j++) X[j * kBT + m] = 0.0f;
+          for (int j = 0; j < ne; j++) X[(C + j) * kLD + m] = valid ? e[j] : 0.0f;
+          for (int j = C + ne; j < kMaxIn; j++) X[j * kLD + m] = 0.0f;
         }
       }
       __syncthreads();
@@ -272,7 +302,7 @@ __global__ void __launch_bounds__(256, 1) k_bwd_brick(GridGeo g, RaySrc src, Mlp
         v.y = fmaxf(acc[1][j] + b1[n], 0.f);
         v.z = fmaxf(acc[2][j] + b1[n], 0.f);
         v.w = fmaxf(acc[3][j] + b1[n], 0.f);
-        *reinterpret_cast<float4*>(&H1[n * kBT + tm * 4]) = v;
+        *reinterpret_cast<float4*>(&H1[n * kLD + tm * 4]) = v;
       }
       __syncthreads();
       // layer 2
@@ -289,40 +319,94 @@ __global__ void __launch_bounds__(256, 1) k_bwd_brick(GridGeo g, RaySrc src, Mlp
         v.y = fmaxf(acc[1][j] + b2[n], 0.f);
         v.z = fmaxf(acc[2][j] + b2[n], 0.f);
         v.w = fmaxf(acc[3][j] + b2[n], 0.f);
-        *reinterpret_cast<float4*>(&H2[n * kBT + tm * 4]) = v;
+        *reinterpret_cast<float4*>(&H2[n * kLD + tm * 4]) = v;
       }
       __syncthreads();
-      // dL/dh2 = W3^T dz, masked by relu'(pre2)
-      for (int e = threadIdx.x; e < kHidden * kBT; e += blockDim.x) {
-        const int o = e / kBT, mm = e % kBT;
-        const float v = w3[o] * DZ[mm] + w3[kHidden + o] * DZ[kBT + mm] + w3[2 * kHidden + o] * DZ[2 * kBT + mm];
-        H2[e] = H2[e] > 0.0f ? v : 0.0f;
+      // dL/dh2 = W3^T dz masked by relu'(pre2), in place over h2 (each element read and written by
+      // the same thread); dW3 += dz h2^T, db3 += dz, db2 += dL/dh2 on the way
+      {
+        const float wa = w3[ro], wb = w3[kHidden + ro], wc = w3[2 * kHidden + ro];
+        float* hr = H2 + ro * kLD;
+#pragma unroll 2
+        for (int s = rs0; s < rs0 + kBT / 2; s += 4) {
+          const float4 h = *reinterpret_cast<const float4*>(&hr[s]);
+          const float4 z0 = *reinterpret_cast<const float4*>(&DZ[s]);
+          const float4 z1 = *reinterpret_cast<const float4*>(&DZ[kLD + s]);
+          const float4 z2 = *reinterpret_cast<const float4*>(&DZ[2 * kLD + s]);
+          float4 v;
+          v.x = h.x > 0.0f ? wa * z0.x + wb * z1.x + wc * z2.x : 0.0f;
+          v.y = h.y > 0.0f ? wa * z0.y + wb * z1.y + wc * z2.y : 0.0f;
+          v.z = h.z > 0.0f ? wa * z0.z + wb * z1.z + wc * z2.z : 0.0f;
+          v.w = h.w > 0.0f ? wa * z0.w + wb * z1.w + wc * z2.w : 0.0f;
+          if constexpr (WG) {
+            gw3[0] += dot4(z0, h);
+            gw3[1] += dot4(z1, h);
+            gw3[2] += dot4(z2, h);
+            gb3[0] += (z0.x + z0.y) + (z0.z + z0.w);
+            gb3[1] += (z1.x + z1.y) + (z1.z + z1.w);
+            gb3[2] += (z2.x + z2.y) + (z2.z + z2.w);
+            gb2 += (v.x + v.y) + (v.z + v.w);
+          }
+          *reinterpret_cast<float4*>(&hr[s]) = v;
+        }
       }
       __syncthreads();
+      // dW2 += dL/dh2 h1^T, while H1 still holds h1
+      if constexpr (WG) {
+#pragma unroll 1
+        for (int s = 0; s < kBT; s += 4) {
+          float4 hv[8];
+#pragma unroll
+          for (int bb = 0; bb < 8; bb++) hv[bb] = *reinterpret_cast<const float4*>(&H1[(tm + 16 * bb) * kLD + s]);
+#pragma unroll
+          for (int a = 0; a < 8; a++) {
+            const float4 dv = *reinterpret_cast<const float4*>(&H2[(tn + 16 * a) * kLD + s]);
+#pragma unroll
+            for (int bb = 0; bb < 8; bb++) gw2[a][bb] += dot4(dv, hv[bb]);
+          }
+        }
+      }
       // dL/dh1 = W2^T dh2, masked by relu'(pre1)
 #pragma unroll
       for (int i = 0; i < 4; i++)
 #pragma unroll
         for (int j = 0; j < 8; j++) acc[i][j] = 0.0f;
       gemm64_bt(H2, w2t, kHidden, tm, tn, acc);
+      if constexpr (WG) __syncthreads();  // every thread's dW2 reads of h1 are done
 #pragma unroll
       for (int j = 0; j < 8; j++) {
         const int n = col8(tn, j);
-        float4 h = *reinterpret_cast<float4*>(&H1[n * kBT + tm * 4]);
+        float4 h = *reinterpret_cast<float4*>(&H1[n * kLD + tm * 4]);
         h.x = h.x > 0.f ? acc[0][j] : 0.f;
         h.y = h.y > 0.f ? acc[1][j] : 0.f;
         h.z = h.z > 0.f ? acc[2][j] : 0.f;
         h.w = h.w > 0.f ? acc[3][j] : 0.f;
-        *reinterpret_cast<float4*>(&H1[n * kBT + tm * 4]) = h;
+        *reinterpret_cast<float4*>(&H1[n * kLD + tm * 4]) = h;
       }
       __syncthreads();
-      // dL/dfeatures = W1[:, :C]^T dh1
+      // dW1 += dL/dh1 x^T, db1 += dL/dh1
+      if constexpr (WG) {
+#pragma unroll 1
+        for (int s = 0; s < kBT; s += 4) {
+          float4 xv[3];
+#pragma unroll
+          for (int bb = 0; bb < 3; bb++) xv[bb] = *reinterpret_cast<const float4*>(&X[(tm + 16 * bb) * kLD + s]);
+#pragma unroll
+          for (int a = 0; a < 8; a++) {
+            const float4 dv = *reinterpret_cast<const float4*>(&H1[(tn + 16 * a) * kLD + s]);
+            gb1[a] += (dv.x + dv.y) + (dv.z + dv.w);
+#pragma unroll
+            for (int bb = 0; bb < 3; bb++) gw1[a][bb] += dot4(dv, xv[bb]);
+          }
+        }
+      }
+      // dL/dfeatures = W1[:, :C]^T dh1, into H2 (dL/dh2 is no longer read)
       for (int e = threadIdx.x; e < C * kBT; e += blockDim.x) {
         const int c = e / kBT, mm = e % kBT;
         float s = 0.0f;
 #pragma unroll 8
-        for (int n = 0; n < kHidden; n++) s = fmaf(w1t[c * kHidden + n], H1[n * kBT + mm], s);
-        X[c * kBT + mm] = s;
+        for (int n = 0; n < kHidden; n++) s = fmaf(w1t[c * kHidden + n], H1[n * kLD + mm], s);
+        H2[c * kLD + mm] = s;
       }
       __syncthreads();
       // trilinear adjoint into the brick accumulator: 4 threads per sample, 2 corners each
@@ -338,7 +422,7 @@ __global__ void __launch_bounds__(256, 1) k_bwd_brick(GridGeo g, RaySrc src, Mlp
             const float wq = ((q & 1) ? f0 : 1.f - f0) * (((q >> 1) & 1) ? f1 : 1.f - f1) * ((q >> 2) ? f2 : 1.f - f2);
             const int lv = ((l2 + (q >> 2)) * vb + (l1 + ((q >> 1) & 1))) * vb + (l0 + (q & 1));
             float* ga = gacc + lv * (C + 1);
-            for (int c = 0; c < C; c++) atomicAdd(&ga[c], wq * X[c * kBT + mm]);
+            for (int c = 0; c < C; c++) atomicAdd(&ga[c], wq * H2[c * kLD + mm]);
             atomicAdd(&ga[C], wq * dr);
           }
         }
@@ -347,10 +431,48 @@ __global__ void __launch_bounds__(256, 1) k_bwd_brick(GridGeo g, RaySrc src, Mlp
     }
   }
   if (cur >= 0) flush_brick(g, cur, gacc, vb, d_dens, d_feat);
+  if (WG && cur >= 0) {
+    // d_mlp = [W1 [128][in_dim], b1 [128], W2 [128][128], b2 [128], W3 [3][128], b3 [3]]
+    const int I = mlp.in_dim;
+    float* dW1 = d_mlp;
+    float* db1 = dW1 + kHidden * I;
+    float* dW2 = db1 + kHidden;
+    float* db2 = dW2 + kHidden * kHidden;
+    float* dW3 = db2 + kHidden;
+    float* db3 = dW3 + 3 * kHidden;
+#pragma unroll
+    for (int a = 0; a < 8; a++) {
+      const int o = tn + 16 * a;
+#pragma unroll
+      for (int bb = 0; bb < 8; bb++) atomicAdd(&dW2[o * kHidden + tm + 16 * bb], gw2[a][bb]);
+#pragma unroll
+      for (int bb = 0; bb < 3; bb++)
+        if (tm + 16 * bb < I) atomicAdd(&dW1[o * I + tm + 16 * bb], gw1[a][bb]);
+      if (tm == 0) atomicAdd(&db1[o], gb1[a]);
+    }
+#pragma unroll
+    for (int j = 0; j < 3; j++) atomicAdd(&dW3[j * kHidden + ro], gw3[j]);
+    atomicAdd(&db2[ro], gb2);
+    if (ro == 0)
+#pragma unroll
+      for (int j = 0; j < 3; j++) atomicAdd(&db3[j], gb3[j]);
+  }
+}
+
+template <typename T, bool WG>
+static cudaError_t launch_bwd_brick(const RenderPlan& plan, const RaySrc& src, const MlpPtrs& mlp, const RenderWs& ws,
+                                    const void* feat, const float* d_rgb, float* d_dens, float* d_feat, float* d_mlp,
+                                    int smem, cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(k_bwd_brick<T, WG>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  k_bwd_brick<T, WG><<<num_sms(), 256, smem, st>>>(plan.geo, src, mlp, ws, (const T*)feat, d_rgb, d_dens, d_feat,
+                                                   d_mlp);
+  return cudaGetLastError();
 }
 
 cicero_status run_backward(const cicero_grid* grid, const MlpPtrs& mlp, const RenderPlan& plan, const RaySrc& src,
-                           const RenderWs& ws, const float* d_rgb, float* d_dens, float* d_feat, cudaStream_t st) {
+                           const RenderWs& ws, const float* d_rgb, float* d_dens, float* d_feat, float* d_mlp,
+                           cudaStream_t st) {
   OutBufs none;
   memset(&none, 0, sizeof none);
   cicero_status s = run_render(grid, mlp, plan, src, ws, none, false, st);
@@ -367,19 +489,16 @@ cicero_status run_backward(const cicero_grid* grid, const MlpPtrs& mlp, const Re
   const int vb = plan.geo.brick + 1;
   const int smem = BwdSmem::gacc + vb * vb * vb * (plan.geo.C + 1) * 4;
   if (smem > 227 * 1024) return fail(CICERO_ERR_UNSUPPORTED, "brick too large for the backward kernel");
+  const bool f16 = grid->dtype == CICERO_F16;
   cudaError_t e;
-  if (grid->dtype == CICERO_F16) {
-    e = cudaFuncSetAttribute(k_bwd_brick<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_bwd_brick)");
-    k_bwd_brick<__half><<<num_sms(), 256, smem, st>>>(plan.geo, src, mlp, ws, (const __half*)grid->features, d_rgb,
-                                                      d_dens, d_feat);
-  } else {
-    e = cudaFuncSetAttribute(k_bwd_brick<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_bwd_brick)");
-    k_bwd_brick<float><<<num_sms(), 256, smem, st>>>(plan.geo, src, mlp, ws, (const float*)grid->features, d_rgb,
-                                                     d_dens, d_feat);
-  }
-  e = cudaGetLastError();
+  if (d_mlp)
+    e = f16 ? launch_bwd_brick<__half, true>(plan, src, mlp, ws, grid->features, d_rgb, d_dens, d_feat, d_mlp, smem, st)
+            : launch_bwd_brick<float, true>(plan, src, mlp, ws, grid->features, d_rgb, d_dens, d_feat, d_mlp, smem, st);
+  else
+    e = f16 ? launch_bwd_brick<__half, false>(plan, src, mlp, ws, grid->features, d_rgb, d_dens, d_feat, nullptr, smem,
+                                              st)
+            : launch_bwd_brick<float, false>(plan, src, mlp, ws, grid->features, d_rgb, d_dens, d_feat, nullptr, smem,
+                                             st);
   return e == cudaSuccess ? CICERO_OK : cuda_fail(e, "backward kernels");
 }
 

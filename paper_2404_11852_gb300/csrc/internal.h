@@ -213,7 +213,8 @@ void carve_warp_ws(WarpBatch& B, void* ws);
 cicero_status run_warp(const WarpBatch& B, const VoidTest& vt, const float* ref_rgb, const float* ref_depth,
                        cudaStream_t st);
 cicero_status run_backward(const cicero_grid* grid, const MlpPtrs& mlp, const RenderPlan& plan, const RaySrc& src,
-                           const RenderWs& ws, const float* d_rgb, float* d_dens, float* d_feat, cudaStream_t st);
+                           const RenderWs& ws, const float* d_rgb, float* d_dens, float* d_feat, float* d_mlp,
+                           cudaStream_t st);
 cicero_status launch_mlp_eval_f32(const MlpPtrs& mlp, const float* x, int M, float* c, cudaStream_t st);
 
 }  // namespace cicero

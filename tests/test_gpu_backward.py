@@ -16,7 +16,7 @@ def cc():
     return cicero
 
 
-def gpu_grads(cc, g32, m, o, d, sp, grad):
+def gpu_grads(cc, g32, m, o, d, sp, grad, with_mlp=False):
     import torch
     gd, md = cc.DeviceGrid.from_host(g32), cc.DeviceMlp.from_host(m)
     sd = cc.sampling_from(sp)
@@ -24,10 +24,21 @@ def gpu_grads(cc, g32, m, o, d, sp, grad):
     gr = torch.from_numpy(grad.astype(np.float32)).cuda()
     dd = torch.zeros(g32.density.shape, device="cuda")
     df = torch.zeros(g32.features.shape, device="cuda")
+    dm = torch.zeros(m.flat().size, device="cuda") if with_mlp else None
     ws = cc.workspace(cc.cicero_backward_workspace_size(gd.desc, o.shape[0], sd))
-    cc.cicero_render_backward(gd.desc, md.desc, ot, dt, sd, gr, dd, df, None, ws)
+    cc.cicero_render_backward(gd.desc, md.desc, ot, dt, sd, gr, dd, df, dm, ws)
     cc.cicero_workspace_status(ws)
-    return dd.cpu().double().numpy(), df.cpu().double().numpy()
+    out = dd.cpu().double().numpy(), df.cpu().double().numpy()
+    return out + (dm.cpu().double().numpy(),) if with_mlp else out
+
+
+def mlp_parts(m, flat):
+    """Split a flat [W1, b1, W2, b2, W3, b3] vector into its six pieces."""
+    parts, k = [], 0
+    for a in (m.w1, m.b1, m.w2, m.b2, m.w3, m.b3):
+        parts.append(flat[k:k + a.size])
+        k += a.size
+    return parts
 
 
 def rel_inf(a, b):
@@ -89,3 +100,55 @@ def test_autograd_function_matches_backward(cc, orc):
     wd, wf, _ = orc.backward(g, m, sp, grad, rays=(o, d))
     assert rel_inf(dens.grad.cpu().double().numpy(), wd) <= 1e-3
     assert rel_inf(feat.grad.cpu().double().numpy(), wf) <= 1e-3
+
+
+@pytest.mark.parametrize("case", ["fd", "occ"])
+def test_backward_mlp_weights(cc, orc, case):
+    """dL/d(W1, b1, W2, b2, W3, b3) against the oracle, per tensor (relative inf-norm <= 1e-3),
+    together with the grid gradients of the same call (which must not change with d_mlp)."""
+    if case == "fd":
+        g = scenes.scene_fd().astype(np.float32)
+        m = scenes.make_mlp(4, random_bias=True)
+        o, d = scenes.random_rays(64, seed=5)
+        sp = scenes.Sampling(near=0.5, far=2.5, n_samples=48, t_stop=0.0)
+    else:
+        g = scenes.make_grid(64, 12, 8, seed=32, dtype=np.float16, occ_res=16, occ_frac=0.3)
+        m = scenes.make_mlp(12, seed=33, random_bias=True)
+        o, d = scenes.random_rays(400, seed=36)
+        sp = scenes.sampling_march(64, 128)
+    R = o.shape[0]
+    out = orc.render(g, m, sp, rays=(o, d))
+    tgt = scenes.random_targets(R, seed=37).astype(np.float64)
+    grad = 2.0 * (out["rgb"] - tgt) / tgt.size
+    grad[out["amb"]] = 0.0  # ambiguous early stops contribute nothing on either side
+    wd, wf, wm = orc.backward(g, m, sp, grad, rays=(o, d), with_mlp=True)
+    dd, df, dm = gpu_grads(cc, g, m, o, d, sp, grad, with_mlp=True)
+    assert rel_inf(dd, wd) <= 1e-3, rel_inf(dd, wd)
+    assert rel_inf(df, wf) <= 1e-3, rel_inf(df, wf)
+    names = ("w1", "b1", "w2", "b2", "w3", "b3")
+    for name, a, b in zip(names, mlp_parts(m, dm), mlp_parts(m, wm)):
+        assert np.abs(b).max() > 0.0, name
+        assert rel_inf(a, b) <= 1e-3, (name, rel_inf(a, b))
+
+
+def test_autograd_mlp_weights(cc, orc):
+    """The autograd wrapper's MLP gradients (tensors with requires_grad) against the oracle."""
+    import torch
+    from paper_2404_11852_gb300.autograd import render_rays
+    g = scenes.scene_fd().astype(np.float32)
+    m = scenes.make_mlp(4, random_bias=True)
+    o, d = scenes.random_rays(64, seed=6)
+    sp = scenes.Sampling(near=0.5, far=2.5, n_samples=48, t_stop=0.0)
+    dens = torch.from_numpy(g.density).cuda()
+    feat = torch.from_numpy(g.features).cuda()
+    params = [torch.from_numpy(a).cuda().float().requires_grad_(True) for a in (m.w1, m.b1, m.w2, m.b2, m.w3, m.b3)]
+    md = cc.DeviceMlp(*params, n_freq=m.n_freq)
+    rgb = render_rays(dens, feat, md, torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda(), sp)
+    tgt = torch.from_numpy(scenes.random_targets(64, seed=7)).cuda()
+    ((rgb - tgt) ** 2).mean().backward()
+    ref = orc.render(g, m, sp, rays=(o, d))
+    grad = 2.0 * (ref["rgb"] - tgt.cpu().double().numpy()) / (64 * 3)
+    _, _, wm = orc.backward(g, m, sp, grad, rays=(o, d), with_mlp=True)
+    for p, b in zip(params, mlp_parts(m, wm)):
+        assert p.grad is not None and p.grad.shape == p.shape
+        assert rel_inf(p.grad.cpu().double().numpy().ravel(), b) <= 1e-3
