@@ -656,9 +656,34 @@ def backward_workload(cc, torch, dev):
     t_bm = event_ms(torch, lambda: bwd(dm), 5)
     cc.cicero_workspace_status(ws_f)
     cc.cicero_workspace_status(ws_b)
+    samples = int(ws_b[:16].view(torch.int32).cpu().numpy()[2])  # composited samples of the recompute
+    # per-stage device time of one backward call without and with the MLP weight gradients
+    stage = {}
+    for name, arg in (("grid", None), ("grid_and_mlp", dm)):
+        torch.cuda.synchronize()
+        cc.cicero_profile_begin()
+        for _ in range(5):
+            bwd(arg)
+        torch.cuda.synchronize()
+        p = cc.cicero_profile_end()
+        stage[name] = {k: p[k][0] / 5 for k in ("march", "bucket", "gather_mlp", "composite", "bwd_ray", "bwd_brick")}
+    # B2's algorithmic FP32 work per composited sample: recomputed layers 1-2, dL/dh2, dL/dh1,
+    # dL/dfeatures (+ dW3, dW2, dW1 with the weight gradients), against the FP32 FFMA peak
+    # derived from the SM count, 128 FP32 lanes per SM, 2 FLOP per FMA and the 2070 MHz maximum clock
+    C, H, I = 12, 128, m.w1.shape[1]
+    flop = 2 * (I * H + H * H + 3 * H + H * H + C * H)
+    flop_w = flop + 2 * (3 * H + H * H + I * H)
+    peak = torch.cuda.get_device_properties(0).multi_processor_count * 128 * 2 * 2.07e9 / 1e12
+    roof = {}
+    for name, f in (("grid", flop), ("grid_and_mlp", flop_w)):
+        t = stage[name]["bwd_brick"] / 1e3
+        ach = f * samples / t / 1e12 if t > 0 else 0.0
+        roof[name] = {"bound": "alu", "flop_per_sample": f, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                      "frac": ach / peak, "peak_src": "derived: SMs x 128 FP32 lanes x 2 x 2070 MHz"}
     return {"workload": "8192 rays x 256 samples, 160^3 x 12 FP32 grid, MSE loss", "forward_ms": t_f,
             "backward_ms": t_b, "backward_with_mlp_weights_ms": t_bm,
-            "rays_per_s_fwd_bwd": R / ((t_f + t_b) / 1e3),
+            "rays_per_s_fwd_bwd": R / ((t_f + t_b) / 1e3), "composited_samples": samples,
+            "stage_ms": stage, "k_bwd_brick_roofline": roof,
             "grad_bytes": int(dd.numel() * 4 + df.numel() * 4)}
 
 

@@ -112,19 +112,27 @@ __device__ __forceinline__ void gemm64(const float* A, const float* Bw, int K, i
   }
 }
 
-// same with B read transposed from Bt [128][128]: B[k][n] = Bt[n][k]
+__device__ __forceinline__ int col8(int tn, int j) { return j < 4 ? tn * 4 + j : 64 + tn * 4 + (j - 4); }
+
+// same with B read transposed from Bt [128][128]: B[k][n] = Bt[n][k], four k at a time (one
+// float4 of Bt per column); K is a multiple of 4
 __device__ __forceinline__ void gemm64_bt(const float* A, const float* Bt, int K, int tm, int tn, float acc[4][8]) {
-#pragma unroll 2
-  for (int k = 0; k < K; k++) {
-    const float4 a = *reinterpret_cast<const float4*>(&A[k * kLD + tm * 4]);
-    const float av[4] = {a.x, a.y, a.z, a.w};
-    float bv[8];
+#pragma unroll 1
+  for (int k = 0; k < K; k += 4) {
+    float4 bq[8];
 #pragma unroll
-    for (int j = 0; j < 8; j++) bv[j] = Bt[(j < 4 ? tn * 4 + j : 64 + tn * 4 + (j - 4)) * kHidden + k];
+    for (int j = 0; j < 8; j++) bq[j] = *reinterpret_cast<const float4*>(&Bt[col8(tn, j) * kHidden + k]);
 #pragma unroll
-    for (int i = 0; i < 4; i++)
+    for (int kk = 0; kk < 4; kk++) {
+      const float4 a = *reinterpret_cast<const float4*>(&A[(k + kk) * kLD + tm * 4]);
+      const float av[4] = {a.x, a.y, a.z, a.w};
 #pragma unroll
-      for (int j = 0; j < 8; j++) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+      for (int j = 0; j < 8; j++) {
+        const float b = kk == 0 ? bq[j].x : kk == 1 ? bq[j].y : kk == 2 ? bq[j].z : bq[j].w;
+#pragma unroll
+        for (int i = 0; i < 4; i++) acc[i][j] = fmaf(av[i], b, acc[i][j]);
+      }
+    }
   }
 }
 
@@ -132,15 +140,15 @@ __device__ __forceinline__ float dot4(float4 a, float4 b) {
   return fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, a.w * b.w)));
 }
 
-__device__ __forceinline__ int col8(int tn, int j) { return j < 4 ? tn * 4 + j : 64 + tn * 4 + (j - 4); }
-
+// corners q0 and q0 + 1 of the trilinear interpolation of the features at (i0, f), weighted,
+// into out[0, C) (the caller sums the four corner pairs)
 template <typename T>
-__device__ __forceinline__ void feat_trilinear_global(const GridGeo& g, const T* feat, const int i0[3], const float f[3],
-                                                      float* out) {
+__device__ __forceinline__ void feat_corner_pair(const GridGeo& g, const T* feat, const int i0[3], const float f[3],
+                                                 int q0, float* out) {
   const int C = g.C;
-  for (int c = 0; c < C; c++) out[c] = 0.0f;
 #pragma unroll
-  for (int q = 0; q < 8; q++) {
+  for (int u = 0; u < 2; u++) {
+    const int q = q0 + u;
     const int x = i0[0] + (q & 1), y = i0[1] + ((q >> 1) & 1), z = i0[2] + (q >> 2);
     const float wq = ((q & 1) ? f[0] : 1.f - f[0]) * (((q >> 1) & 1) ? f[1] : 1.f - f[1]) * ((q >> 2) ? f[2] : 1.f - f[2]);
     const T* v = feat + (((size_t)z * g.n[1] + y) * g.n[0] + x) * C;
@@ -239,48 +247,54 @@ __global__ void __launch_bounds__(256, 1) k_bwd_brick(GridGeo g, RaySrc src, Mlp
     }
     for (uint32_t start = start0; start < end; start += kBT) {
       const int mcnt = (int)min((uint32_t)kBT, end - start);
-      // gather: thread m < 64 features + meta, 64 <= t < 128 encoding.  Samples past mcnt and
+      // gather: four threads per sample (m = tid / 4), each interpolating two of the eight corners;
+      // the quad's partial sums are added with shuffles, then the first thread writes the features
+      // and the per-sample data and the second the direction encoding.  Samples past mcnt and
       // rejected samples get x = 0 and dL/dz = 0, so they add nothing to any gradient.
-      const int m = threadIdx.x & (kBT - 1), part = threadIdx.x >> 6;
-      if (part < 2) {
+      {
+        const int m = threadIdx.x >> 2, qp = threadIdx.x & 3;
         const bool valid = m < mcnt;
         const float4 qd = valid ? w.srt_qd[start + m] : make_float4(0.f, 0.f, 0.f, 1.f);
         const uint32_t sid = __float_as_uint(qd.x);
-        const int r = valid ? (int)w.rec_ray[sid] : 0;
-        const float d[3] = {qd.y, qd.z, qd.w};
-        if (part == 0) {
-          int ok = 0;
-          if (valid) {
-            const float4 pw = w.srt_pw[start + m];
-            const float p[3] = {pw.x, pw.y, pw.z};
-            float f[3], fv[24];
-            int i0[3];
-            const bool in = index_sample(g, p, i0, f);
-            const int l[3] = {i0[0] - bx * B, i0[1] - by * B, i0[2] - bz * B};
-            if (!in || l[0] < 0 || l[0] >= B || l[1] < 0 || l[1] >= B || l[2] < 0 || l[2] >= B) {
-              set_err(&w.hdr[0], kErrInternal);
-            } else {
-              ok = 1;
-              feat_trilinear_global<T>(g, feat, i0, f, fv);
-              for (int c = 0; c < C; c++) X[c * kLD + m] = fv[c];
-              for (int a = 0; a < 3; a++) {
-                ml[a * kBT + m] = l[a];
-                mf[a * kBT + m] = f[a];
-              }
-              mdraw[m] = w.rec_raw[sid];
-              const float4 cw = w.rec_c[sid];
-              const float cc[3] = {cw.x, cw.y, cw.z};
-              for (int j = 0; j < 3; j++) DZ[j * kLD + m] = cw.w * d_rgb[3 * r + j] * cc[j] * (1.0f - cc[j]);
+        float f[3] = {0.f, 0.f, 0.f}, fv[24];
+        int i0[3] = {0, 0, 0}, l[3] = {0, 0, 0};
+        bool ok = false;
+        if (valid) {
+          const float4 pw = w.srt_pw[start + m];
+          const float p[3] = {pw.x, pw.y, pw.z};
+          const bool in = index_sample(g, p, i0, f);
+          l[0] = i0[0] - bx * B;
+          l[1] = i0[1] - by * B;
+          l[2] = i0[2] - bz * B;
+          ok = in && l[0] >= 0 && l[0] < B && l[1] >= 0 && l[1] < B && l[2] >= 0 && l[2] < B;
+          if (!ok && qp == 0) set_err(&w.hdr[0], kErrInternal);
+        }
+        for (int c = 0; c < C; c++) fv[c] = 0.0f;
+        if (ok) feat_corner_pair<T>(g, feat, i0, f, 2 * qp, fv);
+        for (int c = 0; c < C; c++) {
+          fv[c] += __shfl_xor_sync(0xffffffffu, fv[c], 1);
+          fv[c] += __shfl_xor_sync(0xffffffffu, fv[c], 2);
+        }
+        if (qp == 0) {
+          for (int c = 0; c < C; c++) X[c * kLD + m] = fv[c];
+          if (ok) {
+            for (int a = 0; a < 3; a++) {
+              ml[a * kBT + m] = l[a];
+              mf[a * kBT + m] = f[a];
             }
-          }
-          if (!ok) {
-            for (int c = 0; c < C; c++) X[c * kLD + m] = 0.0f;
+            const int r = (int)w.rec_ray[sid];
+            mdraw[m] = w.rec_raw[sid];
+            const float4 cw = w.rec_c[sid];
+            const float cc[3] = {cw.x, cw.y, cw.z};
+            for (int j = 0; j < 3; j++) DZ[j * kLD + m] = cw.w * d_rgb[3 * r + j] * cc[j] * (1.0f - cc[j]);
+          } else {
             for (int j = 0; j < 3; j++) DZ[j * kLD + m] = 0.0f;
           }
-          mval[m] = ok;
-        } else {
+          mval[m] = ok ? 1 : 0;
+        } else if (qp == 1) {
           float e[3 + 6 * 7];
           const int ne = 3 + 6 * mlp.n_freq;
+          const float d[3] = {qd.y, qd.z, qd.w};
           if (valid) encode_dir(d, mlp.n_freq, e);
           for (int j = 0; j < ne; j++) X[(C + j) * kLD + m] = valid ? e[j] : 0.0f;
           for (int j = C + ne; j < kMaxIn; j++) X[j * kLD + m] = 0.0f;
@@ -400,13 +414,26 @@ __global__ void __launch_bounds__(256, 1) k_bwd_brick(GridGeo g, RaySrc src, Mlp
           }
         }
       }
-      // dL/dfeatures = W1[:, :C]^T dh1, into H2 (dL/dh2 is no longer read)
-      for (int e = threadIdx.x; e < C * kBT; e += blockDim.x) {
-        const int c = e / kBT, mm = e % kBT;
-        float s = 0.0f;
-#pragma unroll 8
-        for (int n = 0; n < kHidden; n++) s = fmaf(w1t[c * kHidden + n], H1[n * kLD + mm], s);
-        H2[c * kLD + mm] = s;
+      // dL/dfeatures = W1[:, :C]^T dh1, into H2 (dL/dh2 is no longer read): thread (mm = tid mod 64,
+      // cg = tid / 64) takes channels cg, cg + 4, cg + 8 (then + 12, ...) of sample mm, four hidden
+      // units at a time
+      {
+        const int mm = threadIdx.x & (kBT - 1), cg = threadIdx.x >> 6;
+        for (int c0 = cg; c0 < C; c0 += 12) {
+          const bool v1 = c0 + 4 < C, v2 = c0 + 8 < C;
+          float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f;
+#pragma unroll 2
+          for (int n = 0; n < kHidden; n += 4) {
+            const float4 h = make_float4(H1[n * kLD + mm], H1[(n + 1) * kLD + mm], H1[(n + 2) * kLD + mm],
+                                         H1[(n + 3) * kLD + mm]);
+            s0 += dot4(*reinterpret_cast<const float4*>(&w1t[c0 * kHidden + n]), h);
+            if (v1) s1 += dot4(*reinterpret_cast<const float4*>(&w1t[(c0 + 4) * kHidden + n]), h);
+            if (v2) s2 += dot4(*reinterpret_cast<const float4*>(&w1t[(c0 + 8) * kHidden + n]), h);
+          }
+          H2[c0 * kLD + mm] = s0;
+          if (v1) H2[(c0 + 4) * kLD + mm] = s1;
+          if (v2) H2[(c0 + 8) * kLD + mm] = s2;
+        }
       }
       __syncthreads();
       // trilinear adjoint into the brick accumulator: 4 threads per sample, 2 corners each
