@@ -252,6 +252,23 @@ def oracle_window(res: int, rank: int = 0, frames: list | None = None):
     return dt, oracle.max_threads(), holes / (N_TARGETS * res * res)
 
 
+def oracle_threads(g, m, cam, R, n_pix=2048):
+    """The oracle's full-render throughput on one host thread and on all of them (OpenMP over rays),
+    on the same seeded sample of the reference frame's rays (rays/s)."""
+    import oracle
+    import scenes
+    pix = (scenes.splitmix64(4242, n_pix) % np.uint64(R)).astype(np.int32)
+    out = {}
+    for name, th in (("single", 1), ("all", 0)):
+        t0 = time.perf_counter()
+        oracle.render(g, m, cam.sampling, cam=cam, pix=pix, threads=th)
+        out[name + "_rays_per_s"] = n_pix / (time.perf_counter() - t0)
+    out["all_cores"] = oracle.max_threads()
+    out["speedup"] = out["all_rays_per_s"] / out["single_rays_per_s"]
+    out["sample"] = f"{n_pix} seeded reference-frame rays (FP64, 256 slots)"
+    return out
+
+
 def run_reference(args, rank, world, window=None):
     """The oracle arm: rank 0 alone times the oracle; the other ranks exit without work."""
     if rank != 0:
@@ -872,7 +889,8 @@ def main():
         scale = R / (args.cpu_res ** 2)
         cpu = {"value": N_TARGETS / (dt * scale), "unit": "frames/s", "cores": cores, "kind": "oracle",
                "sample": f"whole SpaRW window at {args.cpu_res}x{args.cpu_res} ({args.cpu_res**2} of {R} pixels "
-                         f"per frame, FP64), time x {scale:.0f}"}
+                         f"per frame, FP64), time x {scale:.0f}",
+               "threads": oracle_threads(g_h, m_h, cam, R)}
 
     others = {}
     if rank == 0 and not args.no_extra:

@@ -444,8 +444,8 @@ int or_render(const or_grid *g, const or_mlp *m, const or_rays *rays, const or_s
     int R = n_rays_of(rays);
     if (m->in_dim != g->C + 3 + 6 * m->n_freq || m->hidden > OR_MAX_HIDDEN || m->in_dim > OR_MAX_IN) return -1;
 #ifdef _OPENMP
-    if (nthreads > 0) omp_set_num_threads(nthreads);
-#pragma omp parallel for schedule(dynamic, 16)
+    const int nt = nthreads > 0 ? nthreads : omp_get_max_threads();  /* this call only */
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nt)
 #endif
     for (int r = 0; r < R; r++) {
         ray_out a, b;
