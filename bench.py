@@ -49,8 +49,9 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-extra", action="store_true", help="skip the backward and small-scene SpaRW reports")
     p.add_argument("--cpu-res", type=int, default=100, help="oracle sample resolution (square)")
-    p.add_argument("--case", default="full", choices=["full", "small"],
-                   help="small: one 320x320 reference frame (BF16 and FP32) and two targets, for profilers")
+    p.add_argument("--case", default="full", choices=["full", "small", "backward"],
+                   help="small: one 320x320 reference frame (BF16 and FP32) and two targets, for profilers; "
+                        "backward: the differentiation workload alone")
     p.add_argument("--brick", type=int, default=4, help="brick size of the small case")
     return p.parse_args()
 
@@ -752,6 +753,13 @@ def main():
         return run_reference(args, rank, world)
     if args.case == "small":
         return small_case(args.brick)
+    if args.case == "backward":
+        import torch
+        from paper_2404_11852_gb300 import build, cicero as cc
+        build.build()
+        cc.lib()
+        print(json.dumps({"case": "backward", **backward_workload(cc, torch, "cuda")}), flush=True)
+        return None
 
     import torch
     import torch.distributed as dist
