@@ -606,21 +606,31 @@ struct F32Smem {
   static_assert(tile % 128 == 0, "TMA destination must be 128-byte aligned");
 };
 
-// acc[i][j]: rows {tm*4+i, 64+tm*4+(i-4)}, cols {tn*4+j, 64+tn*4+(j-4)}; A, B k-major [K][128]
+// acc[i][j]: rows {tm*4+i, 64+tm*4+(i-4)}, cols {tn*4+j, 64+tn*4+(j-4)}; A, B k-major [K][128].
+// The operands of step k + 1 are loaded before the 64 FMAs of step k.
 __device__ __forceinline__ void simt_gemm(const float* __restrict__ A, const float* __restrict__ Bw, int K, int tm,
                                           int tn, float acc[8][8]) {
+  float4 a0 = *reinterpret_cast<const float4*>(&A[tm * 4]);
+  float4 a1 = *reinterpret_cast<const float4*>(&A[64 + tm * 4]);
+  float4 b0 = *reinterpret_cast<const float4*>(&Bw[tn * 4]);
+  float4 b1 = *reinterpret_cast<const float4*>(&Bw[64 + tn * 4]);
 #pragma unroll 2
   for (int k = 0; k < K; k++) {
-    const float4 a0 = *reinterpret_cast<const float4*>(&A[k * kTile + tm * 4]);
-    const float4 a1 = *reinterpret_cast<const float4*>(&A[k * kTile + 64 + tm * 4]);
-    const float4 b0 = *reinterpret_cast<const float4*>(&Bw[k * kHidden + tn * 4]);
-    const float4 b1 = *reinterpret_cast<const float4*>(&Bw[k * kHidden + 64 + tn * 4]);
+    const int kn = k + 1 < K ? k + 1 : k;
+    const float4 na0 = *reinterpret_cast<const float4*>(&A[kn * kTile + tm * 4]);
+    const float4 na1 = *reinterpret_cast<const float4*>(&A[kn * kTile + 64 + tm * 4]);
+    const float4 nb0 = *reinterpret_cast<const float4*>(&Bw[kn * kHidden + tn * 4]);
+    const float4 nb1 = *reinterpret_cast<const float4*>(&Bw[kn * kHidden + 64 + tn * 4]);
     const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
     const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
     for (int i = 0; i < 8; i++)
 #pragma unroll
       for (int j = 0; j < 8; j++) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    a0 = na0;
+    a1 = na1;
+    b0 = nb0;
+    b1 = nb1;
   }
 }
 
@@ -694,18 +704,41 @@ __device__ __forceinline__ void mlp_f32_tile(char* sm, float c[3]) {
 #pragma unroll
     for (int j = 0; j < 8; j++) acc[i][j] = 0.0f;
   simt_gemm(H, w2t, kHidden, tm, tn, acc);
-  __syncthreads();
-  simt_epilogue(acc, b2, H, tm, tn);
+  // layer-2 epilogue fused with layer 3: h2 = relu(acc + b2) stays in registers; this thread's 8
+  // hidden units give partial sums z[i][o] = sum_j w3[o][n_j] h2[i][j] for its 8 samples, and the
+  // 16 threads that share the samples add theirs through shared memory (P [16][3][128], over H)
+  float z[8][3];
+#pragma unroll
+  for (int i = 0; i < 8; i++) z[i][0] = z[i][1] = z[i][2] = 0.0f;
+#pragma unroll
+  for (int j = 0; j < 8; j++) {
+    const int n = gemm_row(tn, j);
+    const float bj = b2[n], u0 = w3[n], u1 = w3[kHidden + n], u2 = w3[2 * kHidden + n];
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+      const float h = fmaxf(acc[i][j] + bj, 0.f);
+      z[i][0] = fmaf(u0, h, z[i][0]);
+      z[i][1] = fmaf(u1, h, z[i][1]);
+      z[i][2] = fmaf(u2, h, z[i][2]);
+    }
+  }
+  __syncthreads();  // every thread is done reading H (h1)
+  float* P = H;
+#pragma unroll
+  for (int i = 0; i < 8; i++) {
+    const int m = gemm_row(tm, i);
+#pragma unroll
+    for (int o = 0; o < 3; o++) P[(tn * 3 + o) * kTile + m] = z[i][o];
+  }
   __syncthreads();
   if (threadIdx.x < kTile) {
     const int m = threadIdx.x;
     float z0 = b3[0], z1 = b3[1], z2 = b3[2];
-#pragma unroll 8
-    for (int k = 0; k < kHidden; k++) {
-      const float h = H[k * kTile + m];
-      z0 = fmaf(w3[k], h, z0);
-      z1 = fmaf(w3[kHidden + k], h, z1);
-      z2 = fmaf(w3[2 * kHidden + k], h, z2);
+#pragma unroll
+    for (int t = 0; t < 16; t++) {
+      z0 += P[(t * 3 + 0) * kTile + m];
+      z1 += P[(t * 3 + 1) * kTile + m];
+      z2 += P[(t * 3 + 2) * kTile + m];
     }
     c[0] = sigmoid_f(z0);
     c[1] = sigmoid_f(z1);
