@@ -599,11 +599,14 @@ struct F32Smem {
   static constexpr int b1 = w3 + 3 * kHidden * 4;                // [128]
   static constexpr int b2 = b1 + kHidden * 4;                    // [128]
   static constexpr int b3 = b2 + kHidden * 4;                    // [4]
-  static constexpr int x = b3 + 16;                              // [48][128]
+  static constexpr int x = b3 + 16;                              // [48][128] inputs, buffer 0
   static constexpr int h = x + kK1 * kTile * 4;                  // [128][128]
   static constexpr int bar = ((h + kHidden * kTile * 4 + 127) / 128) * 128;  // mbarrier (8 B, pad 128)
-  static constexpr int tile = bar + 128;                         // brick tile (TMA destination, 128-B aligned)
-  static_assert(tile % 128 == 0, "TMA destination must be 128-byte aligned");
+  static constexpr int x2 = bar + 128;                           // [48][128] inputs, buffer 1
+  // brick tile (TMA destination, 128-B aligned): after buffer 1, or in its place with one buffer
+  static constexpr int tile = x2 + kK1 * kTile * 4;
+  static constexpr int tile1 = x2;
+  static_assert(tile % 128 == 0 && tile1 % 128 == 0, "TMA destination must be 128-byte aligned");
 };
 
 // acc[i][j]: rows {tm*4+i, 64+tm*4+(i-4)}, cols {tn*4+j, 64+tn*4+(j-4)}; A, B k-major [K][128].
@@ -679,16 +682,40 @@ __device__ void load_mlp_f32_smem(char* sm, const MlpPtrs& m) {
   if (threadIdx.x < 4) b3[threadIdx.x] = threadIdx.x < 3 ? m.b3[threadIdx.x] : 0.0f;
 }
 
+// Named barriers of the FP32 kernels: the 256 MLP threads among themselves, and the hand-off of
+// the two input buffers between the producer warps and the MLP threads (full: the producers
+// arrive, the MLP threads wait; empty: the reverse).
+constexpr int kBarMlp = 1, kBarProd = 2, kBarFull0 = 3, kBarEmpty0 = 5;
+constexpr int kMlpThreads = 256, kProdThreads = 128;
+__device__ __forceinline__ void nbar_sync(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
+__device__ __forceinline__ bool nbar_sync_and(int id, int n, bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 p, %1, 0;\n\t"
+      "bar.red.and.pred q, %2, %3, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"((uint32_t)v), "r"(id), "r"(n)
+      : "memory");
+  return r != 0;
+}
+__device__ __forceinline__ void nbar_arrive(int id, int n) {
+  __threadfence_block();  // this thread's shared-memory accesses before the arrival
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
 // Three-layer MLP of the 128 samples whose inputs are in X [48][128]; threads < 128 return c of
-// sample m = threadIdx.x.  Needs 256 threads.
-__device__ __forceinline__ void mlp_f32_tile(char* sm, float c[3]) {
+// sample m = threadIdx.x.  Run by the 256 MLP threads (threadIdx.x < 256), which synchronise on
+// their own named barrier; with empty_id > 0 they also arrive on that barrier (with the producers,
+// kMlpThreads + kProdThreads) once layer 1 has read X.
+__device__ __forceinline__ void mlp_f32_tile(char* sm, const float* X, float c[3], int empty_id = 0) {
   const float* w1t = (const float*)(sm + F32Smem::w1t);
   const float* w2t = (const float*)(sm + F32Smem::w2t);
   const float* w3 = (const float*)(sm + F32Smem::w3);
   const float* b1 = (const float*)(sm + F32Smem::b1);
   const float* b2 = (const float*)(sm + F32Smem::b2);
   const float* b3 = (const float*)(sm + F32Smem::b3);
-  const float* X = (const float*)(sm + F32Smem::x);
   float* H = (float*)(sm + F32Smem::h);
   const int tm = threadIdx.x & 15, tn = threadIdx.x >> 4;
   float acc[8][8];
@@ -698,7 +725,8 @@ __device__ __forceinline__ void mlp_f32_tile(char* sm, float c[3]) {
     for (int j = 0; j < 8; j++) acc[i][j] = 0.0f;
   simt_gemm(X, w1t, kK1, tm, tn, acc);
   simt_epilogue(acc, b1, H, tm, tn);
-  __syncthreads();
+  nbar_sync(kBarMlp, kMlpThreads);
+  if (empty_id) nbar_arrive(empty_id, kMlpThreads + kProdThreads);  // X may be refilled
 #pragma unroll
   for (int i = 0; i < 8; i++)
 #pragma unroll
@@ -722,7 +750,7 @@ __device__ __forceinline__ void mlp_f32_tile(char* sm, float c[3]) {
       z[i][2] = fmaf(u2, h, z[i][2]);
     }
   }
-  __syncthreads();  // every thread is done reading H (h1)
+  nbar_sync(kBarMlp, kMlpThreads);  // every thread is done reading H (h1)
   float* P = H;
 #pragma unroll
   for (int i = 0; i < 8; i++) {
@@ -730,7 +758,7 @@ __device__ __forceinline__ void mlp_f32_tile(char* sm, float c[3]) {
 #pragma unroll
     for (int o = 0; o < 3; o++) P[(tn * 3 + o) * kTile + m] = z[i][o];
   }
-  __syncthreads();
+  nbar_sync(kBarMlp, kMlpThreads);
   if (threadIdx.x < kTile) {
     const int m = threadIdx.x;
     float z0 = b3[0], z1 = b3[1], z2 = b3[2];
@@ -746,14 +774,21 @@ __device__ __forceinline__ void mlp_f32_tile(char* sm, float c[3]) {
   }
 }
 
+// K5f: FP32 Feature Gathering + Computation.  Warps 0-7 run the MLP of tile t while warps 8-11
+// (producers, one thread per sample row) gather tile t + 1 into the other input buffer: staged
+// brick (TMA, reloaded when the brick changes) -> trilinear features + direction encoding.  With
+// nbuf = 1 (a brick too large for two buffers) the producers wait until layer 1 of tile t has read
+// the single buffer.  The buffers are handed over with named barriers (full / empty, alternating
+// between two ids per tile so that consecutive generations never mix); a producer that runs into
+// a timeout keeps taking part in them (with zero inputs), so the MLP threads never wait on a
+// barrier that cannot complete.
 template <typename T>
-__global__ void __launch_bounds__(256, 1) k_gather_mlp_f32(GridGeo g, int S, MlpPtrs mlp, RenderWs w,
-                                                           const __grid_constant__ CUtensorMap fmap, int vb, int vx,
-                                                           int box_bytes) {
+__global__ void __launch_bounds__(kMlpThreads + kProdThreads, 1)
+    k_gather_mlp_f32(GridGeo g, int S, MlpPtrs mlp, RenderWs w, const __grid_constant__ CUtensorMap fmap, int vb,
+                     int vx, int box_bytes, int nbuf) {
   extern __shared__ __align__(128) char sm[];
-  float* X = (float*)(sm + F32Smem::x);
   uint64_t* bar = (uint64_t*)(sm + F32Smem::bar);
-  T* tile = (T*)(sm + F32Smem::tile);
+  T* tile = (T*)(sm + (nbuf == 2 ? F32Smem::tile : F32Smem::tile1));
   load_mlp_f32_smem(sm, mlp);
   if (threadIdx.x == 0) {
     mbar_init(bar, 1);
@@ -763,33 +798,38 @@ __global__ void __launch_bounds__(256, 1) k_gather_mlp_f32(GridGeo g, int S, Mlp
   const uint32_t n_tiles = w.hdr[1];
   const uint32_t per = (n_tiles + gridDim.x - 1) / gridDim.x;
   const uint32_t t_begin = blockIdx.x * per, t_end = min(n_tiles, t_begin + per);
-  const int B = g.brick, C = g.C;
-  const int m = threadIdx.x & (kTile - 1), part = threadIdx.x >> 7;
-  int loaded = -1;
-  uint32_t phase = 0;
-  bool alive = true;
-  for (uint32_t ti = t_begin; ti < t_end && alive; ti++) {
-    const uint4 td = w.tile[ti];
-    const int b = (int)td.z;
-    const uint32_t start = td.x;
-    const int mcnt = (int)(td.y & 0xFFu);
-    const int bx = (int)(td.w & 0xFFFFu), by = (int)(td.w >> 16), bz = (int)((td.y >> 8) & 0x1FFFu);
-    if (b != loaded) {
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        mbar_expect_tx(bar, (uint32_t)box_bytes);
-        tma_load_3d(tile, &fmap, bx * B * C, by * B, bz * B, bar);
+  const uint32_t n = t_end > t_begin ? t_end - t_begin : 0;
+  if (threadIdx.x >= kMlpThreads) {
+    // ------------------------------------------------------------------ producers
+    const int m = threadIdx.x - kMlpThreads;
+    const int B = g.brick, C = g.C;
+    int loaded = -1;
+    uint32_t phase = 0;
+    bool alive = true;
+    for (uint32_t i = 0; i < n; i++) {
+      const int b = i & 1;
+      float* X = (float*)(sm + ((i % nbuf) ? F32Smem::x2 : F32Smem::x));
+      // layer 1 of tile i - nbuf, the buffer's last user, is done with it
+      if (i >= (uint32_t)nbuf) nbar_sync(kBarEmpty0 + ((i - nbuf) & 1), kMlpThreads + kProdThreads);
+      const uint4 td = w.tile[t_begin + i];
+      const uint32_t start = td.x;
+      const int mcnt = (int)(td.y & 0xFFu);
+      const int bx = (int)(td.w & 0xFFFFu), by = (int)(td.w >> 16), bz = (int)((td.y >> 8) & 0x1FFFu);
+      if (alive && (int)td.z != loaded) {
+        nbar_sync(kBarProd, kProdThreads);  // every producer is done with the staged brick
+        if (m == 0) {
+          mbar_expect_tx(bar, (uint32_t)box_bytes);
+          tma_load_3d(tile, &fmap, bx * B * C, by * B, bz * B, bar);
+        }
+        alive = nbar_sync_and(kBarProd, kProdThreads, mbar_wait(bar, phase, &w.hdr[0]));
+        if (alive) phase ^= 1u;
+        loaded = (int)td.z;
       }
-      if (!mbar_wait(bar, phase, &w.hdr[0])) alive = false;
-      phase ^= 1u;
-      loaded = b;
-    }
-    if (!__syncthreads_and(alive)) break;
-    if (m < mcnt) {
-      if (part == 0) {
+      if (alive && m < mcnt) {
         const float4 pw = w.srt_pw[start + m];
-        const float p[3] = {pw.x, pw.y, pw.z};
-        float f[3], feat[24];
+        const float4 dd = w.srt_qd[start + m];
+        const float p[3] = {pw.x, pw.y, pw.z}, d[3] = {dd.y, dd.z, dd.w};
+        float f[3], feat[24], e[3 + 6 * 7];
         int i0[3];
         const bool ok = index_sample(g, p, i0, f);
         const int l[3] = {i0[0] - bx * B, i0[1] - by * B, i0[2] - bz * B};
@@ -800,25 +840,32 @@ __global__ void __launch_bounds__(256, 1) k_gather_mlp_f32(GridGeo g, int S, Mlp
           tri_smem<T>(tile, vb, vx, C, l, f, feat);
           for (int c = 0; c < C; c++) X[c * kTile + m] = feat[c];
         }
-      } else {
-        const float4 dd = w.srt_qd[start + m];
-        const float d[3] = {dd.y, dd.z, dd.w};
-        float e[3 + 6 * 7];
         encode_dir(d, mlp.n_freq, e);
         const int ne = 3 + 6 * mlp.n_freq;
         for (int j = 0; j < ne; j++) X[(C + j) * kTile + m] = e[j];
         for (int j = C + ne; j < kK1; j++) X[j * kTile + m] = 0.0f;
+      } else {
+        for (int j = 0; j < kK1; j++) X[j * kTile + m] = 0.0f;
       }
-    } else {
-      if (part == 0)
-        for (int c = 0; c < C; c++) X[c * kTile + m] = 0.0f;
-      else
-        for (int j = C; j < kK1; j++) X[j * kTile + m] = 0.0f;
+      nbar_arrive(kBarFull0 + b, kMlpThreads + kProdThreads);
     }
-    __syncthreads();
+    // the MLP threads' last releases of each buffer, so that every barrier is left balanced
+    for (uint32_t i = n >= (uint32_t)nbuf ? n - nbuf : 0; i < n; i++)
+      nbar_sync(kBarEmpty0 + (i & 1), kMlpThreads + kProdThreads);
+    return;
+  }
+  // -------------------------------------------------------------------- MLP threads
+  for (uint32_t i = 0; i < n; i++) {
+    const int b = i & 1;
+    const float* X = (const float*)(sm + ((i % nbuf) ? F32Smem::x2 : F32Smem::x));
+    const uint4 td = w.tile[t_begin + i];
+    const uint32_t start = td.x;
+    const int mcnt = (int)(td.y & 0xFFu);
+    nbar_sync(kBarFull0 + b, kMlpThreads + kProdThreads);  // the producers have filled X
     float c[3];
-    mlp_f32_tile(sm, c);
-    if (threadIdx.x < kTile && m < mcnt)
+    mlp_f32_tile(sm, X, c, kBarEmpty0 + b);
+    const int m = threadIdx.x;
+    if (m < kTile && m < mcnt)
       w.rec_c[__float_as_uint(w.srt_qd[start + m].x)] = make_float4(c[0], c[1], c[2], w.srt_pw[start + m].w);
   }
 }
@@ -995,14 +1042,16 @@ static int blocks_for_warps(long long warps, int per_sm) {
 template <typename T>
 static cicero_status launch_f32(const GridGeo& geo, const RaySrc& src, int S, const MlpPtrs& mlp, const RenderWs& ws,
                                 const CUtensorMap& map, const BrickBox& box, cudaStream_t st) {
-  const int smem = F32Smem::tile + box.box_bytes;
+  const int nbuf = F32Smem::tile + box.box_bytes <= 227 * 1024 ? 2 : 1;  // two input buffers when they fit
+  const int smem = (nbuf == 2 ? F32Smem::tile : F32Smem::tile1) + box.box_bytes;
   if (smem > 227 * 1024) return fail(CICERO_ERR_UNSUPPORTED, "brick too large for the FP32 feature-computation kernel");
   auto kern = k_gather_mlp_f32<T>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_gather_mlp_f32)");
   {
     ProfScope ps(kStGatherMlp, st);
-    kern<<<num_sms(), 256, smem, st>>>(geo, S, mlp, ws, map, box.vb, box.vx, box.box_bytes);
+    kern<<<num_sms(), kMlpThreads + kProdThreads, smem, st>>>(geo, S, mlp, ws, map, box.vb, box.vx, box.box_bytes,
+                                                                   nbuf);
   }
   count_launches(1);
   e = cudaGetLastError();
@@ -1124,7 +1173,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_eval_f32(MlpPtrs mlp, const floa
     }
     __syncthreads();
     float cc[3];
-    mlp_f32_tile(sm, cc);
+    mlp_f32_tile(sm, X, cc);
     const int row = t * kTile + threadIdx.x;
     if (threadIdx.x < kTile && row < M) {
       c[3 * row + 0] = cc[0];
