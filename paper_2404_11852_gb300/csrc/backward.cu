@@ -307,7 +307,7 @@ __global__ void __launch_bounds__(256, 1) k_bwd_brick(GridGeo g, RaySrc src, Mlp
       for (int i = 0; i < 4; i++)
 #pragma unroll
         for (int j = 0; j < 8; j++) acc[i][j] = 0.0f;
-      gemm64(X, w1t, kMaxIn, tm, tn, acc);
+      gemm64(X, w1t, (mlp.in_dim + 3) & ~3, tm, tn, acc);  // rows in_dim.. of X and W1^T are zero
 #pragma unroll
       for (int j = 0; j < 8; j++) {
         const int n = col8(tn, j);

@@ -705,11 +705,11 @@ __device__ __forceinline__ void nbar_arrive(int id, int n) {
   asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
 }
 
-// Three-layer MLP of the 128 samples whose inputs are in X [48][128]; threads < 128 return c of
-// sample m = threadIdx.x.  Run by the 256 MLP threads (threadIdx.x < 256), which synchronise on
+// Three-layer MLP of the 128 samples whose inputs are in X [48][128] (rows in_dim.. zero);
+// threads < 128 return c of sample m = threadIdx.x.  Run by the 256 MLP threads (threadIdx.x < 256), which synchronise on
 // their own named barrier; with empty_id > 0 they also arrive on that barrier (with the producers,
 // kMlpThreads + kProdThreads) once layer 1 has read X.
-__device__ __forceinline__ void mlp_f32_tile(char* sm, const float* X, float c[3], int empty_id = 0) {
+__device__ __forceinline__ void mlp_f32_tile(char* sm, const float* X, float c[3], int in_dim, int empty_id = 0) {
   const float* w1t = (const float*)(sm + F32Smem::w1t);
   const float* w2t = (const float*)(sm + F32Smem::w2t);
   const float* w3 = (const float*)(sm + F32Smem::w3);
@@ -723,7 +723,7 @@ __device__ __forceinline__ void mlp_f32_tile(char* sm, const float* X, float c[3
   for (int i = 0; i < 8; i++)
 #pragma unroll
     for (int j = 0; j < 8; j++) acc[i][j] = 0.0f;
-  simt_gemm(X, w1t, kK1, tm, tn, acc);
+  simt_gemm(X, w1t, (in_dim + 3) & ~3, tm, tn, acc);  // rows in_dim.. of X and W1^T are zero
   simt_epilogue(acc, b1, H, tm, tn);
   nbar_sync(kBarMlp, kMlpThreads);
   if (empty_id) nbar_arrive(empty_id, kMlpThreads + kProdThreads);  // X may be refilled
@@ -863,7 +863,7 @@ __global__ void __launch_bounds__(kMlpThreads + kProdThreads, 1)
     const int mcnt = (int)(td.y & 0xFFu);
     nbar_sync(kBarFull0 + b, kMlpThreads + kProdThreads);  // the producers have filled X
     float c[3];
-    mlp_f32_tile(sm, X, c, kBarEmpty0 + b);
+    mlp_f32_tile(sm, X, c, mlp.in_dim, kBarEmpty0 + b);
     const int m = threadIdx.x;
     if (m < kTile && m < mcnt)
       w.rec_c[__float_as_uint(w.srt_qd[start + m].x)] = make_float4(c[0], c[1], c[2], w.srt_pw[start + m].w);
@@ -1173,7 +1173,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_eval_f32(MlpPtrs mlp, const floa
     }
     __syncthreads();
     float cc[3];
-    mlp_f32_tile(sm, X, cc);
+    mlp_f32_tile(sm, X, cc, mlp.in_dim);
     const int row = t * kTile + threadIdx.x;
     if (threadIdx.x < kTile && row < M) {
       c[3 * row + 0] = cc[0];
