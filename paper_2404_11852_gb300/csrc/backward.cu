@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(256, 1) k_bwd_brick(GridGeo g, RaySrc src, Mlp
   float* mdraw = mf + 3 * kBT;                        // [64]
   int* mval = (int*)(mdraw + kBT);                    // [64]
   float* gacc = (float*)(sm + BwdSmem::gacc);
-  const int C = g.C, B = g.brick, vb = B + 1, S = w.S;
+  const int C = g.C, B = g.brick, vb = B + 1;
   for (int i = threadIdx.x; i < kMaxIn * kHidden; i += blockDim.x) {
     const int k = i / kHidden, n = i % kHidden;
     w1t[i] = k < mlp.in_dim ? mlp.w1[n * mlp.in_dim + k] : 0.0f;
