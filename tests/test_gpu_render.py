@@ -199,15 +199,15 @@ def large():
     return scenes.scene_large(), scenes.make_mlp(12)
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_large_frame_sampled(cc, orc, large, precision):
+@pytest.mark.parametrize("precision,brick", [(0, 8), (1, 4), (1, 8)])  # the benchmark's bricks: FP32 8, BF16 4
+def test_large_frame_sampled(cc, orc, large, precision, brick):
     g, m = large
     cam = scenes.orbit_camera(800, 800, sampling=scenes.sampling_march(256, 256))
-    out = gpu_render(cc, g, m, cam, cam.sampling, precision, 8)
+    out = gpu_render(cc, g, m, cam, cam.sampling, precision, brick)
     pix = (scenes.splitmix64(4242, 400) % np.uint64(800 * 800)).astype(np.int32)
     ref = orc.render(g, m, cam.sampling, cam=cam, pix=pix)
     sub = {k: v[pix] for k, v in out.items()}
     tol = TOL32 if precision == 0 else TOL16
     err, p = check_render(sub, ref, tol, psnr_min=None if precision == 0 else PSNR16)
     assert (ref["acc"] > 0.5).mean() > 0.05
-    print(f"800x800 precision {precision}: max|drgb| {err:.3g} PSNR {p}")
+    print(f"800x800 precision {precision} brick {brick}: max|drgb| {err:.3g} PSNR {p}")

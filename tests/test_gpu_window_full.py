@@ -1,0 +1,87 @@
+"""The SpaRW window at full size, in the launch configuration the benchmark times: an 800x800
+reference frame of the 256^3 FP16 scene with its 32^3 occupancy mask (BF16 MLP, brick 4), the 16
+targets of the window warped in one batch (Eq. 1-3, void test), and every target's holes rendered
+in one batch with a capped record capacity (Eq. 4).  Against the oracle fed the GPU's reference
+frame: the hole masks, hole lists, warped colours and depths bit-exact at every pixel of every
+target, and the rendered hole colours on seeded samples of each target's holes within the BF16
+tolerance."""
+import numpy as np
+import pytest
+
+import scenes
+from helpers import check_render
+
+pytestmark = pytest.mark.gpu
+
+TOL16, PSNR16 = 2e-2, 45.0
+HOLE_RECORDS = 128_000_000  # the benchmark's capacity for one window's holes (below rays x slots)
+
+
+@pytest.fixture(scope="module")
+def cc():
+    from paper_2404_11852_gb300 import cicero
+    cicero.lib()
+    return cicero
+
+
+def test_full_window_against_oracle(cc, orc):
+    import torch
+    g, m = scenes.scene_large(), scenes.make_mlp(12)
+    grid, mlp = cc.DeviceGrid.from_host(g), cc.DeviceMlp.from_host(m)
+    cam = scenes.orbit_camera(800, 800, sampling=scenes.sampling_march(256, 256))
+    targets = [scenes.offset_camera(cam, k) for k in scenes.SPARW_OFFSETS]
+    R, n = cam.width * cam.height, len(targets)
+    sd, cd = cc.sampling_from(cam.sampling), cc.camera_from(cam)
+    tds = [cc.camera_from(t) for t in targets]
+    o16 = cc.options(cc.MLP_BF16, 4)
+    oh = cc.options(cc.MLP_BF16, 4, max_records=HOLE_RECORDS)
+    assert HOLE_RECORDS < n * R * cam.sampling.n_samples  # the exact-reservation path runs
+
+    ref_rgb, ref_depth = torch.empty(R, 3, device="cuda"), torch.empty(R, device="cuda")
+    ws_r = cc.workspace(cc.cicero_render_workspace_size(grid.desc, R, sd, o16))
+    cc.cicero_render(grid.desc, mlp.desc, cd, sd, o16, ref_rgb, ref_depth, None, None, ws_r)
+    cc.cicero_workspace_status(ws_r)
+    del ws_r
+
+    t_rgb, t_dep = torch.empty(n, R, 3, device="cuda"), torch.empty(n, R, device="cuda")
+    mask = torch.empty(n, R, dtype=torch.uint8, device="cuda")
+    hidx = torch.empty(n, R, dtype=torch.int32, device="cuda")
+    nh = torch.zeros(n, dtype=torch.int32, device="cuda")
+    L = [[x[i] for i in range(n)] for x in (t_rgb, t_dep, mask, hidx)]
+    ws_w = cc.workspace(cc.cicero_warp_batch_workspace_size(tds))
+    cc.cicero_warp_batch(ref_rgb, ref_depth, cd, tds, 180.0, grid.desc, sd, L[0], L[1], L[2], L[3], nh, ws_w)
+    warped_rgb, warped_dep = t_rgb.cpu().numpy(), t_dep.cpu().numpy()
+    masks, lists, counts = mask.cpu().numpy(), hidx.cpu().numpy(), nh.cpu().numpy()
+
+    ws_h = cc.workspace(cc.cicero_render_workspace_size(grid.desc, n * R, sd, oh))
+    cc.cicero_render_holes_batch(grid.desc, mlp.desc, tds, sd, oh, L[3], nh, n * R, L[0], L[1], ws_h)
+    cc.cicero_workspace_status(ws_h)
+    out_rgb, out_dep = t_rgb.cpu().double().numpy(), t_dep.cpu().double().numpy()
+
+    rr, rd = ref_rgb.cpu().numpy(), ref_depth.cpu().numpy()
+    total_holes, sampled = 0, []
+    for i, tgt in enumerate(targets):
+        want = orc.warp(rr, rd, cam, tgt, void_grid=g, void_sampling=cam.sampling)
+        np.testing.assert_array_equal(masks[i], want["mask"])
+        assert int(counts[i]) == want["n_holes"]
+        np.testing.assert_array_equal(lists[i][:counts[i]], want["hole_idx"])
+        np.testing.assert_array_equal(warped_rgb[i], want["rgb"])
+        np.testing.assert_array_equal(warped_dep[i], want["depth"])
+        holes = want["hole_idx"]
+        total_holes += len(holes)
+        keep = np.ones(R, bool)
+        keep[holes] = False
+        np.testing.assert_array_equal(out_rgb[i][keep], want["rgb"][keep].astype(np.float64))
+        if len(holes):
+            pick = holes[(scenes.splitmix64(900 + i, 48) % np.uint64(len(holes))).astype(np.int64)]
+            sampled.append((i, np.unique(pick)))
+    assert total_holes > 0.02 * n * R  # the window has real holes to render
+    got_rgb, got_dep, ref = [], [], []
+    for i, pix in sampled:
+        ref.append(orc.render(g, m, cam.sampling, cam=targets[i], pix=pix.astype(np.int32)))
+        got_rgb.append(out_rgb[i][pix])
+        got_dep.append(out_dep[i][pix])
+    want = {k: np.concatenate([r[k] for r in ref]) for k in ("rgb", "rgb_alt", "amb", "acc", "depth")}
+    # the hole render writes colour and depth; opacity is not an output of it
+    sub = {"rgb": np.concatenate(got_rgb), "depth": np.concatenate(got_dep), "acc": want["acc"]}
+    check_render(sub, want, TOL16, psnr_min=PSNR16)
