@@ -152,7 +152,9 @@ __device__ __forceinline__ void count_bricks(const RenderWs& w, uint32_t n, KeyA
 // emit at most kStage records (and no backward / RIT extras) stages them in the warp's shared
 // buffers st_pw/st_key and reserves exactly its count at the end, so the capacity follows the
 // samples actually composited; otherwise rays reserve their upper bound up front (faster).
-template <typename T>
+// EXTRA: the records also carry their slot, ray, transmittance and raw density (the backward and
+// the Ray Index Table export); a compile-time flag, so that the forward march tests nothing for them.
+template <typename T, bool EXTRA>
 __device__ __forceinline__ void march_ray(const GridGeo& g, const Samp& s, const T* __restrict__ dens,
                                           const RenderWs& w, int r, const float o[3], const float d[3],
                                           uint32_t key_base, float* dep, float* acc_out, int32_t* steps_out,
@@ -165,7 +167,7 @@ __device__ __forceinline__ void march_ray(const GridGeo& g, const Samp& s, const
   const int bound = record_bound(g, sl, o, d);
   // exact reservation pays only when the caller capped the capacity below the worst case
   const bool capped = (unsigned long long)w.Q < (unsigned long long)w.R * (unsigned long long)w.S;
-  const bool staged = capped && bound <= kStage && !w.rec_k && !w.rec_ray && !w.rec_T;
+  const bool staged = capped && bound <= kStage && !EXTRA;
   uint32_t base = 0;
   if (!staged) {
     if (lane == 0 && bound > 0) base = atomicAdd(&w.hdr[3], (uint32_t)bound);
@@ -234,11 +236,13 @@ __device__ __forceinline__ void march_ray(const GridGeo& g, const Samp& s, const
       const size_t q = (size_t)base + cnt + __popc(cmask & lt_mask);
       w.rec_pw[q] = make_float4(p[0], p[1], p[2], wk);
       w.rec_key[q] = key;
-      if (w.rec_k) w.rec_k[q] = (uint16_t)k;
-      if (w.rec_ray) w.rec_ray[q] = (uint32_t)r;
-      if (w.rec_T) {
-        w.rec_T[q] = Tk;
-        w.rec_raw[q] = raw;
+      if constexpr (EXTRA) {
+        if (w.rec_k) w.rec_k[q] = (uint16_t)k;
+        if (w.rec_ray) w.rec_ray[q] = (uint32_t)r;
+        if (w.rec_T) {
+          w.rec_T[q] = Tk;
+          w.rec_raw[q] = raw;
+        }
       }
     }
     // brick histogram: one atomic per run of consecutive lanes with the same brick
@@ -298,7 +302,7 @@ __device__ __forceinline__ void march_ray(const GridGeo& g, const Samp& s, const
 }
 
 // K1: one warp per ray.
-template <typename T>
+template <typename T, bool EXTRA>
 __global__ void __launch_bounds__(256) k_march(GridGeo g, Samp s, RaySrc src, const T* __restrict__ dens,
                                                RenderWs w, OutBufs out) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -312,7 +316,7 @@ __global__ void __launch_bounds__(256) k_march(GridGeo g, Samp s, RaySrc src, co
     float o[3], d[3];
     ray_gen(src, rr, o, d);
     float* dep = out.depth[rr.view];
-    march_ray<T>(g, s, dens, w, r, o, d, 0u, dep ? dep + rr.pix : nullptr, out.acc ? out.acc + rr.pix : nullptr,
+    march_ray<T, EXTRA>(g, s, dens, w, r, o, d, 0u, dep ? dep + rr.pix : nullptr, out.acc ? out.acc + rr.pix : nullptr,
                  out.n_steps ? out.n_steps + rr.pix : nullptr, st_pw[wb], st_key[wb]);
   }
 }
@@ -953,7 +957,8 @@ __global__ void __launch_bounds__(256) k_march_batch(const JobDesc* __restrict__
     const int pix = r - J.ray_base;
     float o[3], d[3];
     ray_gen_cam(J.cam, pix, o, d);
-    march_ray<T>(C.g, C.s, (const T*)J.density, w, r, o, d, (uint32_t)J.brick_base, J.depth ? J.depth + pix : nullptr,
+    // a batch's records carry no extras (no backward, no export)
+    march_ray<T, false>(C.g, C.s, (const T*)J.density, w, r, o, d, (uint32_t)J.brick_base, J.depth ? J.depth + pix : nullptr,
                  nullptr, nullptr, st_pw[wb], st_key[wb], j);
   }
 }
@@ -1067,10 +1072,15 @@ cicero_status run_render(const cicero_grid* grid, const MlpPtrs& mlp, const Rend
   {
     ProfScope ps(kStMarch, st);
     k_clear<<<std::min(num_sms() * 4, (plan.nb + 255) / 256 + 1), 256, 0, st>>>(ws.hdr, 16, ws.brick_cnt, plan.nb);
-    if (f16)
-      k_march<__half><<<mb, 256, 0, st>>>(geo, plan.samp, src, (const __half*)grid->density, ws, out);
+    const bool extra = ws.rec_k || ws.rec_ray || ws.rec_T;
+    if (f16 && extra)
+      k_march<__half, true><<<mb, 256, 0, st>>>(geo, plan.samp, src, (const __half*)grid->density, ws, out);
+    else if (f16)
+      k_march<__half, false><<<mb, 256, 0, st>>>(geo, plan.samp, src, (const __half*)grid->density, ws, out);
+    else if (extra)
+      k_march<float, true><<<mb, 256, 0, st>>>(geo, plan.samp, src, (const float*)grid->density, ws, out);
     else
-      k_march<float><<<mb, 256, 0, st>>>(geo, plan.samp, src, (const float*)grid->density, ws, out);
+      k_march<float, false><<<mb, 256, 0, st>>>(geo, plan.samp, src, (const float*)grid->density, ws, out);
   }
   {
     ProfScope ps(kStBucket, st);
