@@ -94,6 +94,12 @@ __device__ __forceinline__ float warp_sum(float v) {
 // (the slab test in FP32; the inside test that decides may differ from it only by rounding).
 __device__ __forceinline__ int record_bound(const GridGeo& g, const Slots& sl, const float o[3], const float d[3]) {
   if (sl.n <= 0) return 0;
+  if (sl.march) {
+    // box-march slots run from the box entry t0 while t_k < tout: fewer than (tout - t0) / dt + 1 of
+    // them (two slots of margin cover the fast division)
+    const float span = __fdividef(sl.tout - sl.t0, sl.dt) + 2.0f;
+    return span >= (float)sl.n ? sl.n : max(0, (int)span);
+  }
   float lo = -3.0e38f, hi = 3.0e38f;
 #pragma unroll
   for (int a = 0; a < 3; a++) {
