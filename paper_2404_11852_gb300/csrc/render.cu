@@ -160,17 +160,17 @@ __device__ __forceinline__ void count_bricks(const RenderWs& w, uint32_t n, KeyA
 // samples actually composited; otherwise rays reserve their upper bound up front (faster).
 // EXTRA: the records also carry their slot, ray, transmittance and raw density (the backward and
 // the Ray Index Table export); a compile-time flag, so that the forward march tests nothing for them.
+// The march of one ray by one warp, given its slots and record bound.
 template <typename T, bool EXTRA>
-__device__ __forceinline__ void march_ray(const GridGeo& g, const Samp& s, const T* __restrict__ dens,
-                                          const RenderWs& w, int r, const float o[3], const float d[3],
-                                          uint32_t key_base, float* dep, float* acc_out, int32_t* steps_out,
-                                          float4* st_pw, uint32_t* st_key, int tag = 0) {
+__device__ __forceinline__ void march_ray_core(const GridGeo& g, const Samp& s, const T* __restrict__ dens,
+                                               const RenderWs& w, int r, const float o[3], const float d[3],
+                                               const Slots& sl, int bound, uint32_t key_base, float* dep,
+                                               float* acc_out, int32_t* steps_out, float4* st_pw, uint32_t* st_key,
+                                               int tag = 0) {
   const int lane = threadIdx.x & 31;
   const unsigned full = 0xffffffffu;
   const unsigned lt_mask = (1u << lane) - 1u;
   const unsigned le_mask = (2u << lane) - 1u;  // lanes <= this one (all ones for lane 31)
-  const Slots sl = place_slots(g, s, o, d);
-  const int bound = record_bound(g, sl, o, d);
   // exact reservation pays only when the caller capped the capacity below the worst case
   const bool capped = (unsigned long long)w.Q < (unsigned long long)w.R * (unsigned long long)w.S;
   const bool staged = capped && bound <= kStage && !EXTRA;
@@ -307,23 +307,78 @@ __device__ __forceinline__ void march_ray(const GridGeo& g, const Samp& s, const
   }
 }
 
-// K1: one warp per ray.
 template <typename T, bool EXTRA>
-__global__ void __launch_bounds__(256) k_march(GridGeo g, Samp s, RaySrc src, const T* __restrict__ dens,
+__device__ __forceinline__ void march_ray(const GridGeo& g, const Samp& s, const T* __restrict__ dens,
+                                          const RenderWs& w, int r, const float o[3], const float d[3],
+                                          uint32_t key_base, float* dep, float* acc_out, int32_t* steps_out,
+                                          float4* st_pw, uint32_t* st_key, int tag = 0) {
+  const Slots sl = place_slots(g, s, o, d);
+  march_ray_core<T, EXTRA>(g, s, dens, w, r, o, d, sl, record_bound(g, sl, o, d), key_base, dep, acc_out, steps_out,
+                           st_pw, st_key, tag);
+}
+
+// Per-ray setup shared by a warp: ray, slots, record bound and output pixel.
+struct RaySetup {
+  float o[3], d[3];
+  float t0, dt, tout;
+  int n, march, bound, view, pix;
+};
+
+// K1: one warp per ray.  A warp's rays are r = warp + i nwarps; lane j prepares the setup of the
+// j-th of each group of 32 of them (ray generation, slot placement, record bound: the divisions
+// and the square root), which the whole warp then reads from shared memory ray by ray.
+template <typename T, bool EXTRA>
+__global__ void __launch_bounds__(256, 4) k_march(GridGeo g, Samp s, RaySrc src, const T* __restrict__ dens,
                                                RenderWs w, OutBufs out) {
+  const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   const int R = ray_count(src);
   __shared__ float4 st_pw[8][kStage];
   __shared__ uint32_t st_key[8][kStage];
+  __shared__ RaySetup setup[8][32];
   const int wb = threadIdx.x >> 5;
-  for (int r = warp; r < R; r += nwarps) {
-    const RayRef rr = ray_ref(src, r);
-    float o[3], d[3];
-    ray_gen(src, rr, o, d);
-    float* dep = out.depth[rr.view];
-    march_ray<T, EXTRA>(g, s, dens, w, r, o, d, 0u, dep ? dep + rr.pix : nullptr, out.acc ? out.acc + rr.pix : nullptr,
-                 out.n_steps ? out.n_steps + rr.pix : nullptr, st_pw[wb], st_key[wb]);
+  for (long long i0 = 0;; i0 += 32) {
+    const long long rl = (long long)warp + (i0 + lane) * nwarps;
+    const unsigned have = __ballot_sync(0xffffffffu, rl < R);
+    if (!have) break;
+    if (rl < R) {
+      const RayRef rr = ray_ref(src, (int)rl);
+      RaySetup& q = setup[wb][lane];
+      float o[3], d[3];
+      ray_gen(src, rr, o, d);
+      const Slots sl = place_slots(g, s, o, d);
+#pragma unroll
+      for (int a = 0; a < 3; a++) {
+        q.o[a] = o[a];
+        q.d[a] = d[a];
+      }
+      q.t0 = sl.t0;
+      q.dt = sl.dt;
+      q.tout = sl.tout;
+      q.n = sl.n;
+      q.march = sl.march ? 1 : 0;
+      q.bound = record_bound(g, sl, o, d);
+      q.view = rr.view;
+      q.pix = rr.pix;
+    }
+    __syncwarp();
+    const int nq = __popc(have);  // rl grows with the lane: the rays present are lanes 0 .. nq-1
+    for (int j = 0; j < nq; j++) {
+      const RaySetup& q = setup[wb][j];
+      const float o[3] = {q.o[0], q.o[1], q.o[2]}, d[3] = {q.d[0], q.d[1], q.d[2]};
+      Slots sl;
+      sl.t0 = q.t0;
+      sl.dt = q.dt;
+      sl.tout = q.tout;
+      sl.n = q.n;
+      sl.march = q.march != 0;
+      float* dep = out.depth[q.view];
+      march_ray_core<T, EXTRA>(g, s, dens, w, (int)((long long)warp + (i0 + j) * nwarps), o, d, sl, q.bound, 0u,
+                               dep ? dep + q.pix : nullptr, out.acc ? out.acc + q.pix : nullptr,
+                               out.n_steps ? out.n_steps + q.pix : nullptr, st_pw[wb], st_key[wb]);
+    }
+    __syncwarp();  // the setup slots are free for the next group
   }
 }
 
