@@ -97,14 +97,9 @@ __global__ void __launch_bounds__(256) k_splat(const __grid_constant__ WarpBatch
 // Void depth test of pixel p of view v by a whole warp: 32 slots per step, stop at the first slot
 // that is inside the box (and in an occupied cell).  Same FP32 slot placement and indexing as
 // rendering.
-__device__ __forceinline__ bool warp_ray_has_sample(const VoidTest& vt, int v, int p) {
+__device__ __forceinline__ bool warp_ray_has_sample(const VoidTest& vt, const float o[3], const float d[3],
+                                                    const Slots& sl) {
   const int lane = threadIdx.x & 31;
-  float o[3], d[3];
-  RayRef rr;
-  rr.view = v;
-  rr.pix = p;
-  ray_gen(vt.src, rr, o, d);
-  const Slots sl = place_slots(vt.g, vt.s, o, d);
   for (int k0 = 0; k0 < sl.n; k0 += 32) {
     const int k = k0 + lane;
     const float t = slot_t(sl, k);
@@ -155,28 +150,76 @@ __global__ void __launch_bounds__(256) k_resolve(const __grid_constant__ WarpBat
   }
 }
 
+// Per-candidate setup shared by a warp: the target ray and its slots.
+struct VoidSetup {
+  float o[3], d[3];
+  float t0, dt, tout;
+  int n, march, p;
+};
+
 // Void depth test of the listed candidates, one warp each (candidates cluster in the image, so
-// testing them where they lie would serialise a warp's worth of marches).
+// testing them where they lie would serialise a warp's worth of marches).  A warp's candidates are
+// i = warp + k nwarps; lane j prepares the ray and slots of the j-th of each group of 32 of them,
+// which the whole warp then reads from shared memory candidate by candidate.
 __global__ void __launch_bounds__(256) k_void(const __grid_constant__ WarpBatch B, const __grid_constant__ VoidTest vt) {
   const int v = blockIdx.y;
   const WarpView& V = B.v[v];
   const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   const int n = *V.n_holes;
-  for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nwarps) {
-    const int p = V.hole_idx[i];
-    const bool is_void = !warp_ray_has_sample(vt, v, p);
-    if (lane == 0) {
-      if (is_void) {
-        V.wrgb[3 * p + 0] = vt.s.bg[0];
-        V.wrgb[3 * p + 1] = vt.s.bg[1];
-        V.wrgb[3 * p + 2] = vt.s.bg[2];
-        if (V.wdepth) V.wdepth[p] = __int_as_float(0x7f800000);
-        V.mask[p] = 2;
-      } else {
-        V.mask[p] = 1;
+  __shared__ VoidSetup setup[8][32];
+  const int wb = threadIdx.x >> 5;
+  for (long long i0 = 0;; i0 += 32) {
+    const long long il = (long long)warp + (i0 + lane) * nwarps;
+    const unsigned have = __ballot_sync(0xffffffffu, il < n);
+    if (!have) break;
+    if (il < n) {
+      VoidSetup& q = setup[wb][lane];
+      RayRef rr;
+      rr.view = v;
+      rr.pix = V.hole_idx[il];
+      float o[3], d[3];
+      ray_gen(vt.src, rr, o, d);
+      const Slots sl = place_slots(vt.g, vt.s, o, d);
+#pragma unroll
+      for (int a = 0; a < 3; a++) {
+        q.o[a] = o[a];
+        q.d[a] = d[a];
+      }
+      q.t0 = sl.t0;
+      q.dt = sl.dt;
+      q.tout = sl.tout;
+      q.n = sl.n;
+      q.march = sl.march ? 1 : 0;
+      q.p = rr.pix;
+    }
+    __syncwarp();
+    const int nq = __popc(have);  // il grows with the lane: the candidates present are lanes 0 .. nq-1
+    for (int j = 0; j < nq; j++) {
+      const VoidSetup& q = setup[wb][j];
+      const float o[3] = {q.o[0], q.o[1], q.o[2]}, d[3] = {q.d[0], q.d[1], q.d[2]};
+      Slots sl;
+      sl.t0 = q.t0;
+      sl.dt = q.dt;
+      sl.tout = q.tout;
+      sl.n = q.n;
+      sl.march = q.march != 0;
+      const int p = q.p;
+      const bool is_void = !warp_ray_has_sample(vt, o, d, sl);
+      if (lane == 0) {
+        if (is_void) {
+          V.wrgb[3 * p + 0] = vt.s.bg[0];
+          V.wrgb[3 * p + 1] = vt.s.bg[1];
+          V.wrgb[3 * p + 2] = vt.s.bg[2];
+          if (V.wdepth) V.wdepth[p] = __int_as_float(0x7f800000);
+          V.mask[p] = 2;
+        } else {
+          V.mask[p] = 1;
+        }
       }
     }
+    __syncwarp();  // the setup slots are free for the next group
   }
 }
 
