@@ -989,38 +989,77 @@ struct JobCache {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_march_batch(const JobDesc* __restrict__ jobs, const int* __restrict__ bases,
-                                                     int n_jobs, int R, RenderWs w) {
+__global__ void __launch_bounds__(256, 4) k_march_batch(const JobDesc* __restrict__ jobs, const int* __restrict__ bases,
+                                                        int n_jobs, int R, RenderWs w) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   const int lane = threadIdx.x & 31;
   __shared__ float4 st_pw[8][kStage];
   __shared__ uint32_t st_key[8][kStage];
   __shared__ JobCache cache[8];
+  __shared__ RaySetup setup[8][32];
   const int wb = threadIdx.x >> 5;
   JobCache& C = cache[wb];
   if (lane == 0) C.job = -1;
   __syncwarp();
-  for (int r = warp; r < R; r += nwarps) {
-    const int j = job_of(bases, n_jobs, r);
-    const JobDesc& J = jobs[j];
-    if (C.job != j) {
-      __syncwarp();
-      constexpr int kWords = (int)((sizeof(GridGeo) + sizeof(Samp)) / 4);
-      static_assert(offsetof(JobCache, s) == sizeof(GridGeo), "cache layout");
-      static_assert(offsetof(JobDesc, samp) == offsetof(JobDesc, geo) + sizeof(GridGeo), "job layout");
-      const uint32_t* src = (const uint32_t*)&J.geo;
-      uint32_t* dst = (uint32_t*)&C.g;
-      for (int k = lane; k < kWords; k += 32) dst[k] = src[k];
-      if (lane == 0) C.job = j;
-      __syncwarp();
+  // as in k_march: lane j prepares the j-th of each group of 32 of the warp's rays (its job, ray,
+  // slots and record bound, from the job's own geometry and sampling)
+  for (long long i0 = 0;; i0 += 32) {
+    const long long rl = (long long)warp + (i0 + lane) * nwarps;
+    const unsigned have = __ballot_sync(0xffffffffu, rl < R);
+    if (!have) break;
+    if (rl < R) {
+      const int j = job_of(bases, n_jobs, (int)rl);
+      const JobDesc& J = jobs[j];
+      RaySetup& q = setup[wb][lane];
+      const int pix = (int)rl - J.ray_base;
+      float o[3], d[3];
+      ray_gen_cam(J.cam, pix, o, d);
+      const Slots sl = place_slots(J.geo, J.samp, o, d);
+#pragma unroll
+      for (int a = 0; a < 3; a++) {
+        q.o[a] = o[a];
+        q.d[a] = d[a];
+      }
+      q.t0 = sl.t0;
+      q.dt = sl.dt;
+      q.tout = sl.tout;
+      q.n = sl.n;
+      q.march = sl.march ? 1 : 0;
+      q.bound = record_bound(J.geo, sl, o, d);
+      q.view = j;
+      q.pix = pix;
     }
-    const int pix = r - J.ray_base;
-    float o[3], d[3];
-    ray_gen_cam(J.cam, pix, o, d);
-    // a batch's records carry no extras (no backward, no export)
-    march_ray<T, false>(C.g, C.s, (const T*)J.density, w, r, o, d, (uint32_t)J.brick_base, J.depth ? J.depth + pix : nullptr,
-                 nullptr, nullptr, st_pw[wb], st_key[wb], j);
+    __syncwarp();
+    const int nq = __popc(have);
+    for (int jj = 0; jj < nq; jj++) {
+      const RaySetup& q = setup[wb][jj];
+      const int j = q.view;
+      const JobDesc& J = jobs[j];
+      if (C.job != j) {
+        __syncwarp();
+        constexpr int kWords = (int)((sizeof(GridGeo) + sizeof(Samp)) / 4);
+        static_assert(offsetof(JobCache, s) == sizeof(GridGeo), "cache layout");
+        static_assert(offsetof(JobDesc, samp) == offsetof(JobDesc, geo) + sizeof(GridGeo), "job layout");
+        const uint32_t* src = (const uint32_t*)&J.geo;
+        uint32_t* dst = (uint32_t*)&C.g;
+        for (int k = lane; k < kWords; k += 32) dst[k] = src[k];
+        if (lane == 0) C.job = j;
+        __syncwarp();
+      }
+      const float o[3] = {q.o[0], q.o[1], q.o[2]}, d[3] = {q.d[0], q.d[1], q.d[2]};
+      Slots sl;
+      sl.t0 = q.t0;
+      sl.dt = q.dt;
+      sl.tout = q.tout;
+      sl.n = q.n;
+      sl.march = q.march != 0;
+      // a batch's records carry no extras (no backward, no export)
+      march_ray_core<T, false>(C.g, C.s, (const T*)J.density, w, (int)((long long)warp + (i0 + jj) * nwarps), o, d, sl,
+                               q.bound, (uint32_t)J.brick_base, J.depth ? J.depth + q.pix : nullptr, nullptr, nullptr,
+                               st_pw[wb], st_key[wb], j);
+    }
+    __syncwarp();  // the setup slots are free for the next group
   }
 }
 
