@@ -941,25 +941,45 @@ __global__ void __launch_bounds__(256) k_composite(RaySrc src, Samp s, RenderWs 
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   const int R = ray_count(src);
-  for (int r = warp; r < R; r += nwarps) {
-    const uint32_t n = w.ray_n[r], start = w.ray_start[r];
-    float a0 = 0.f, a1 = 0.f, a2 = 0.f;
-    for (uint32_t j = lane; j < n; j += 32) {
-      const float4 v = w.rec_c[start + j];
-      a0 += v.w * v.x;
-      a1 += v.w * v.y;
-      a2 += v.w * v.z;
+  const unsigned full = 0xffffffffu;
+  // lane j reads the header and output pixel of the j-th of each group of 32 of the warp's rays
+  // (r = warp + i nwarps); the warp then composites them one by one
+  for (long long i0 = 0;; i0 += 32) {
+    const long long rl = (long long)warp + (i0 + lane) * nwarps;
+    const unsigned have = __ballot_sync(full, rl < R);
+    if (!have) break;
+    uint32_t n_l = 0, start_l = 0;
+    float T_l = 0.0f;
+    RayRef rr;
+    rr.view = 0;
+    rr.pix = 0;
+    if (rl < R) {
+      n_l = w.ray_n[rl];
+      start_l = w.ray_start[rl];
+      T_l = w.ray_T[rl];
+      rr = ray_ref(src, (int)rl);
     }
-    a0 = warp_sum(a0);
-    a1 = warp_sum(a1);
-    a2 = warp_sum(a2);
-    if (lane == 0) {
-      const float T = w.ray_T[r];
-      const RayRef rr = ray_ref(src, r);
-      float* rgb = out.rgb[rr.view];
-      rgb[3 * rr.pix + 0] = a0 + T * s.bg[0];
-      rgb[3 * rr.pix + 1] = a1 + T * s.bg[1];
-      rgb[3 * rr.pix + 2] = a2 + T * s.bg[2];
+    const int nq = __popc(have);
+    for (int jj = 0; jj < nq; jj++) {
+      const uint32_t n = __shfl_sync(full, n_l, jj), start = __shfl_sync(full, start_l, jj);
+      const float T = __shfl_sync(full, T_l, jj);
+      const int view = __shfl_sync(full, rr.view, jj), pix = __shfl_sync(full, rr.pix, jj);
+      float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+      for (uint32_t j = lane; j < n; j += 32) {
+        const float4 v = w.rec_c[start + j];
+        a0 += v.w * v.x;
+        a1 += v.w * v.y;
+        a2 += v.w * v.z;
+      }
+      a0 = warp_sum(a0);
+      a1 = warp_sum(a1);
+      a2 = warp_sum(a2);
+      if (lane == 0) {
+        float* rgb = out.rgb[view];
+        rgb[3 * pix + 0] = a0 + T * s.bg[0];
+        rgb[3 * pix + 1] = a1 + T * s.bg[1];
+        rgb[3 * pix + 2] = a2 + T * s.bg[2];
+      }
     }
   }
 }
