@@ -283,21 +283,23 @@ __device__ __forceinline__ bool run_layer(char* sm, Group& G, int layer, uint32_
   if (G.m == 0) {
     fence_after();
     if (layer < 2) {
-      const uint32_t a_base = smem_u32(G.act);
-      const uint32_t b_base = smem_u32(sm + (layer == 0 ? Smem::w1 : Smem::w2));
-      const int steps = layer == 0 ? kK1 / 16 : kK2 / 16;
+      // descriptors built once; the next K step of 16 is 256 bytes on, +16 in the address field
       const uint32_t sbo = (uint32_t)(layer == 0 ? kK1 : kK2) * 16;
+      const uint64_t da = smem_desc(smem_u32(G.act), 128u, sbo);
+      const uint64_t db = smem_desc(smem_u32(sm + (layer == 0 ? Smem::w1 : Smem::w2)), 128u, sbo);
       const uint32_t idesc = idesc_bf16(kHidden);
-#pragma unroll 1
-      for (int s = 0; s < steps; s++)
-        mma_bf16(G.tmem, smem_desc(a_base + 256u * s, 128u, sbo), smem_desc(b_base + 256u * s, 128u, sbo), idesc,
-                 s > 0 ? 1u : 0u);
+      if (layer == 0) {
+#pragma unroll
+        for (int s = 0; s < kK1 / 16; s++) mma_bf16(G.tmem, da + 16u * s, db + 16u * s, idesc, s > 0 ? 1u : 0u);
+      } else {
+#pragma unroll
+        for (int s = 0; s < kK2 / 16; s++) mma_bf16(G.tmem, da + 16u * s, db + 16u * s, idesc, s > 0 ? 1u : 0u);
+      }
     } else {
-      const uint32_t b_base = smem_u32(sm + Smem::w3);
-#pragma unroll 1
+      const uint64_t db = smem_desc(smem_u32(sm + Smem::w3), 128u, kHidden * 16);
+#pragma unroll
       for (int s = 0; s < kHidden / 16; s++)
-        mma_bf16_ta(G.tmem + kL3Col, G.tmem + 8u * s, smem_desc(b_base + 256u * s, 128u, kHidden * 16),
-                    idesc_bf16(kN3), s > 0 ? 1u : 0u);
+        mma_bf16_ta(G.tmem + kL3Col, G.tmem + 8u * s, db + 16u * s, idesc_bf16(kN3), s > 0 ? 1u : 0u);
     }
     mma_commit(G.bar_mma);
   }
@@ -623,11 +625,11 @@ __device__ __forceinline__ bool gather_tiles(char* sm, tc::Group& G, const GridG
       gsync(G.g);
       if (m == 0) {
         fence_after();
-        const uint32_t a_base = smem_u32(G.act), b_base = smem_u32(sm + Smem::w1);
-#pragma unroll 1
+        const uint64_t da = smem_desc(smem_u32(G.act), 128u, kK1 * 16);
+        const uint64_t db = smem_desc(smem_u32(sm + Smem::w1), 128u, kK1 * 16);
+#pragma unroll
         for (int s2 = 0; s2 < kK1 / 16; s2++)
-          mma_bf16(G.tmem, smem_desc(a_base + 256u * s2, 128u, kK1 * 16),
-                   smem_desc(b_base + 256u * s2, 128u, kK1 * 16), idesc_bf16(kHidden), s2 > 0 ? 1u : 0u);
+          mma_bf16(G.tmem, da + 16u * s2, db + 16u * s2, idesc_bf16(kHidden), s2 > 0 ? 1u : 0u);
         mma_commit(G.bar_mma);
       }
       mma_pending = true;
@@ -652,11 +654,10 @@ __device__ __forceinline__ bool gather_tiles(char* sm, tc::Group& G, const GridG
       gsync(G.g);
       if (m == 0) {
         fence_after();
-        const uint32_t b_base = smem_u32(sm + Smem::w3);
-#pragma unroll 1
+        const uint64_t db = smem_desc(smem_u32(sm + Smem::w3), 128u, kHidden * 16);
+#pragma unroll
         for (int s2 = 0; s2 < kHidden / 16; s2++)
-          mma_bf16_ta(G.tmem + kL3Col, G.tmem + 8u * s2, smem_desc(b_base + 256u * s2, 128u, kHidden * 16),
-                      idesc_bf16(kN3), s2 > 0 ? 1u : 0u);
+          mma_bf16_ta(G.tmem + kL3Col, G.tmem + 8u * s2, db + 16u * s2, idesc_bf16(kN3), s2 > 0 ? 1u : 0u);
         mma_commit(G.bar_mma);
       }
       mma_pending = true;
