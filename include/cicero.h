@@ -397,8 +397,9 @@ size_t cicero_backward_workspace_size(const cicero_grid *grid, int n_rays, const
 /* The Ray Index Table (Sec. IV-A) of a camera: the samples that reach Feature Gathering, grouped
  * by brick of opt->brick^3 voxels, brick id (bz * nby + by) * nbx + bx with nb = ceil((n-1)/brick).
  * brick_offsets [n_bricks + 1]: samples of brick b are samples[brick_offsets[b] .. brick_offsets[b+1]).
- * samples [H*W*n_samples]: sample id = ray * n_samples + slot.  The order inside one brick is
- * not specified.  n_bricks is returned through *n_bricks_out (host).  Size the workspace with
+ * samples [H*W*n_samples]: sample id = ray * n_samples + slot.  Inside one brick the samples
+ * are grouped by octant of the brick (x half, then y, then z as bits 0, 1, 2); their order inside
+ * an octant is not specified.  n_bricks is returned through *n_bricks_out (host).  Size the workspace with
  * cicero_build_rit_workspace_size. */
 cicero_status cicero_build_rit(const cicero_grid *grid, const cicero_camera *cam, const cicero_sampling *sampling,
                                const cicero_options *opt, int32_t *brick_offsets, int32_t *samples,

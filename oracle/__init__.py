@@ -74,7 +74,7 @@ def lib():
         P = C.c_void_p
         L.or_render.argtypes = [P] * 13 + [C.c_int]
         L.or_render.restype = C.c_int
-        L.or_active_samples.argtypes = [P, P, P, C.c_int, P, P, P, C.c_long, P, P]
+        L.or_active_samples.argtypes = [P, P, P, C.c_int, P, P, P, P, C.c_long, P, P]
         L.or_active_samples.restype = C.c_long
         L.or_sample_grid.argtypes = [P, P, C.c_int, P, P]
         L.or_hash_features.argtypes = [P, P, C.c_int, P]
@@ -219,7 +219,7 @@ def render(grid, mlp, sampling, cam=None, pix=None, rays=None, threads: int = 0)
 
 
 def active_samples(grid, sampling, brick: int, cam=None, pix=None, rays=None, cap: int | None = None) -> dict:
-    """The samples that reach Feature Gathering with their brick id (FP32 decisions)."""
+    """The samples that reach Feature Gathering with their brick id and voxel (FP32 decisions)."""
     keep = _Keep()
     g, s = _grid(grid, keep), _sampling(sampling)
     r = _rays(keep, cam, pix, rays)
@@ -228,14 +228,15 @@ def active_samples(grid, sampling, brick: int, cam=None, pix=None, rays=None, ca
     ray_of = np.zeros(cap, dtype=np.int32)
     slot_of = np.zeros(cap, dtype=np.int32)
     brick_of = np.zeros(cap, dtype=np.int32)
+    voxel_of = np.zeros(cap, dtype=np.int32)
     n_steps = np.zeros(R, dtype=np.int32)
     amb = np.zeros(R, dtype=np.int32)
     n = lib().or_active_samples(C.byref(g), C.byref(r), C.byref(s), brick, _ptr(ray_of), _ptr(slot_of),
-                                _ptr(brick_of), cap, _ptr(n_steps), _ptr(amb))
+                                _ptr(brick_of), _ptr(voxel_of), cap, _ptr(n_steps), _ptr(amb))
     if n < 0:
         raise ValueError("capacity too small")
-    return {"ray": ray_of[:n], "slot": slot_of[:n], "brick": brick_of[:n], "n_steps": n_steps,
-            "amb": amb.astype(bool)}
+    return {"ray": ray_of[:n], "slot": slot_of[:n], "brick": brick_of[:n], "voxel": voxel_of[:n],
+            "n_steps": n_steps, "amb": amb.astype(bool)}
 
 
 def sample_grid(grid, points):

@@ -468,10 +468,11 @@ int or_render(const or_grid *g, const or_mlp *m, const or_rays *rays, const or_s
 /* The samples that reach Feature Gathering, in ray order then slot order, with the brick
  * ("MVoxel", Sec. IV-A) of B^3 voxels that holds each one: brick (bx, by, bz) = i0 / B and
  * id = (bz * nby + by) * nbx + bx with nb = ceil((N - 1) / B).  This is the content of the
- * Ray Index Table before it is grouped by brick.  Returns the number of samples (or -1 if
- * `cap` is too small); n_steps/amb as in or_render. */
+ * Ray Index Table before it is grouped by brick.  voxel_of (may be NULL) receives the voxel i0 of
+ * each sample as (i0z * Ny + i0y) * Nx + i0x.  Returns the number of samples (or -1 if `cap` is
+ * too small); n_steps/amb as in or_render. */
 long or_active_samples(const or_grid *g, const or_rays *rays, const or_sampling *s, int B,
-                       int32_t *ray_of, int32_t *slot_of, int32_t *brick_of, long cap,
+                       int32_t *ray_of, int32_t *slot_of, int32_t *brick_of, int32_t *voxel_of, long cap,
                        int32_t *n_steps, int32_t *amb) {
     int R = n_rays_of(rays);
     int nb[3];
@@ -511,6 +512,7 @@ long or_active_samples(const or_grid *g, const or_rays *rays, const or_sampling 
             ray_of[cnt] = r;
             slot_of[cnt] = k;
             brick_of[cnt] = ((ix.i0[2] / B) * nb[1] + ix.i0[1] / B) * nb[0] + ix.i0[0] / B;
+            if (voxel_of) voxel_of[cnt] = (ix.i0[2] * g->n[1] + ix.i0[1]) * g->n[0] + ix.i0[0];
             cnt++;
             T *= 1.0 - alpha;
         }

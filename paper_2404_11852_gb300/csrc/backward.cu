@@ -254,13 +254,13 @@ __global__ void __launch_bounds__(256, 1) k_bwd_brick(GridGeo g, RaySrc src, Mlp
       {
         const int m = threadIdx.x >> 2, qp = threadIdx.x & 3;
         const bool valid = m < mcnt;
-        const float4 qd = valid ? w.srt_qd[start + m] : make_float4(0.f, 0.f, 0.f, 1.f);
+        const float4 qd = valid ? w.srt[start + m].qd : make_float4(0.f, 0.f, 0.f, 1.f);
         const uint32_t sid = __float_as_uint(qd.x);
         float f[3] = {0.f, 0.f, 0.f}, fv[24];
         int i0[3] = {0, 0, 0}, l[3] = {0, 0, 0};
         bool ok = false;
         if (valid) {
-          const float4 pw = w.srt_pw[start + m];
+          const float4 pw = w.srt[start + m].pw;
           const float p[3] = {pw.x, pw.y, pw.z};
           const bool in = index_sample(g, p, i0, f);
           l[0] = i0[0] - bx * B;

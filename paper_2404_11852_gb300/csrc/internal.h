@@ -35,26 +35,32 @@ struct ProfScope {
 // Workspace of one rendering call (all device pointers, carved from the caller's buffer).
 // Records (one per composited sample) are allocated per ray from a capacity of Q records: each ray
 // reserves an upper bound of its sample count (from the slab test) and fills a prefix of it.
+// One record of the sorted Ray Index Table payload: (position, weight) and (record index as
+// bits, ray direction).  32 bytes, so that every record the scatter writes is one whole DRAM
+// sector (no partial-sector writes when neighbouring records land from different rays).
+struct __align__(32) SrtRec {
+  float4 pw, qd;
+};
+
 struct RenderWs {
   uint32_t* hdr;        // [0] error bits, [1] tile count, [2] composited samples, [3] records reserved
   uint32_t* ray_n;      // [R] composited samples of each ray
   uint32_t* ray_start;  // [R] first record of each ray
   float* ray_T;         // [R] transmittance after the last composited slot
   float4* ray_dir;      // [R] unit direction of each ray
-  uint32_t* rec_key;    // [Q] brick id
+  uint32_t* rec_key;    // [Q] RIT key: brick id * kOctants + octant
   float4* rec_pw;       // [Q] sample position (FP32, bit-identical to the march) and weight T_k alpha_k
   uint16_t* rec_k;      // [Q] slot index (only for Ray Index Table export; may be null)
   float4* rec_c;        // [Q] (c_r, c_g, c_b, w) of each record
   float* rec_T;         // [Q] transmittance before the slot (backward only; may be null)
   float* rec_raw;       // [Q] interpolated raw density, then dL/draw (backward only; may be null)
-  uint32_t* brick_cnt;  // [nb]
-  uint32_t* brick_off;  // [nb + 1]
-  uint32_t* brick_cur;  // [nb]
+  uint32_t* brick_cnt;  // [nb * kOctants] records per RIT key
+  uint32_t* brick_off;  // [nb * kOctants + 1] first record of each key (brick b starts at key b * kOctants)
+  uint32_t* brick_cur;  // [nb * kOctants] scatter cursors
   uint32_t* tile_off;   // [nb + 1] first tile of each brick
   uint32_t* blk_sums;   // [2 * scan blocks] per-block sums of the brick scan
   uint4* tile;          // [max_tiles] (first record, count | bz << 8 | job << 21, brick id, bx | by << 16)
-  float4* srt_pw;       // [Q] records' (position, weight) in brick order (the Ray Index Table payload)
-  float4* srt_qd;       // [Q] records' (record index as bits, ray direction) in brick order
+  SrtRec* srt;          // [Q] the Ray Index Table payload in brick order
   uint32_t* rec_ray;    // [Q] ray of each record (backward and RIT export only; may be null)
   int R, S, nb, max_tiles;
   uint32_t Q;

@@ -16,7 +16,9 @@
 // thread of a group issues the MMAs and commits them to the group's mbarrier.
 // Operands use the canonical K-major, no-swizzle layout: 8-row x 16-byte core matrices stored as
 // 128 contiguous bytes, K-adjacent core matrices 128 B apart (leading byte offset) and 8-row groups
-// K*16 bytes apart (stride byte offset).
+// K*16 bytes apart (stride byte offset).  A group's activation buffer keeps the K = 144 stride for
+// both layers that read it, so layer 1's 48 input columns and the constant columns 128..143 of
+// layer 2 never overlap and the constants are written once per CTA.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -283,10 +285,11 @@ __device__ __forceinline__ bool run_layer(char* sm, Group& G, int layer, uint32_
   if (G.m == 0) {
     fence_after();
     if (layer < 2) {
-      // descriptors built once; the next K step of 16 is 256 bytes on, +16 in the address field
-      const uint32_t sbo = (uint32_t)(layer == 0 ? kK1 : kK2) * 16;
-      const uint64_t da = smem_desc(smem_u32(G.act), 128u, sbo);
-      const uint64_t db = smem_desc(smem_u32(sm + (layer == 0 ? Smem::w1 : Smem::w2)), 128u, sbo);
+      // descriptors built once; the next K step of 16 is 256 bytes on, +16 in the address field.
+      // A always has the K = 144 row-group stride (layer 1's A fills its first 48 columns).
+      const uint64_t da = smem_desc(smem_u32(G.act), 128u, kK2 * 16);
+      const uint64_t db = smem_desc(smem_u32(sm + (layer == 0 ? Smem::w1 : Smem::w2)), 128u,
+                                    (uint32_t)(layer == 0 ? kK1 : kK2) * 16);
       const uint32_t idesc = idesc_bf16(kHidden);
       if (layer == 0) {
 #pragma unroll
@@ -310,7 +313,8 @@ __device__ __forceinline__ bool run_layer(char* sm, Group& G, int layer, uint32_
 }
 
 // ReLU of the 128 accumulator columns (+ bias when it could not be folded into the MMA) -> BF16
-// K-major rows of A (K = 144: column 128 is the constant 1 that multiplies b2, 129..143 zero).
+// K-major rows of A (K = 144: column 128 is the constant 1 that multiplies b2 and 129..143 are
+// zero; the CTA prologue writes those once, and no other store reaches them).
 __device__ __forceinline__ void epilogue_hidden(const Group& G, const float* bias) {
   const uint32_t taddr = G.tmem + ((uint32_t)((G.m >> 5) * 32) << 16);
 #pragma unroll 1
@@ -337,8 +341,6 @@ __device__ __forceinline__ void epilogue_hidden(const Group& G, const float* bia
       *reinterpret_cast<uint4*>(G.act + kmaj_off(G.m, cc * 64 + q * 8, kK2)) = o;
     }
   }
-  *reinterpret_cast<uint4*>(G.act + kmaj_off(G.m, kHidden, kK2)) = make_uint4(0x3f80u, 0u, 0u, 0u);  // bf16 1.0
-  *reinterpret_cast<uint4*>(G.act + kmaj_off(G.m, kHidden + 8, kK2)) = make_uint4(0u, 0u, 0u, 0u);
   fence_proxy_async();
   fence_before();
 }
@@ -511,6 +513,10 @@ __device__ __forceinline__ Group setup(char* sm, const MlpPtrs* mlp, int groups,
   G.tmem = *tslot + (uint32_t)(G.g * 128);
   G.ph_tma = 0;
   G.ph_mma = 0;
+  // the constant columns 128..143 of this row of A: 1 (times b2), then zeros
+  *reinterpret_cast<uint4*>(G.act + kmaj_off(G.m, kHidden, kK2)) = make_uint4(0x3f80u, 0u, 0u, 0u);  // bf16 1.0
+  *reinterpret_cast<uint4*>(G.act + kmaj_off(G.m, kHidden + 8, kK2)) = make_uint4(0u, 0u, 0u, 0u);
+  fence_proxy_async();
   return G;
 }
 
@@ -585,8 +591,8 @@ __device__ __forceinline__ bool gather_tiles(char* sm, tc::Group& G, const GridG
   const uint4 none = make_uint4(0u, 0u, 0u, 0u);
   auto payload = [&](const uint4& d, float4& a, float4& q) {
     const uint32_t row = d.x + min((uint32_t)m, (d.y & 0xFFu) - 1u);  // every listed tile has >= 1 record
-    a = w.srt_pw[row];
-    q = w.srt_qd[row];
+    a = w.srt[row].pw;
+    q = w.srt[row].qd;
   };
   auto tma_brick = [&](const uint4& d) {
     mbar_expect_tx(G.bar_tma, (uint32_t)box_bytes);
@@ -625,7 +631,7 @@ __device__ __forceinline__ bool gather_tiles(char* sm, tc::Group& G, const GridG
       gsync(G.g);
       if (m == 0) {
         fence_after();
-        const uint64_t da = smem_desc(smem_u32(G.act), 128u, kK1 * 16);
+        const uint64_t da = smem_desc(smem_u32(G.act), 128u, kK2 * 16);
         const uint64_t db = smem_desc(smem_u32(sm + Smem::w1), 128u, kK1 * 16);
 #pragma unroll
         for (int s2 = 0; s2 < kK1 / 16; s2++)
@@ -708,7 +714,7 @@ __device__ __forceinline__ bool gather_tiles(char* sm, tc::Group& G, const GridG
         if (in_dim < kK1) x[CC && NF ? (CC + 3 + 6 * NF) % kK1 : in_dim % kK1] = 1.0f;  // folded layer-1 bias
       }
 #pragma unroll
-      for (int k0 = 0; k0 < kK1; k0 += 8) store_chunk(G.act, m, k0, kK1, x + k0);
+      for (int k0 = 0; k0 < kK1; k0 += 8) store_chunk(G.act, m, k0, kK2, x + k0);
       fence_proxy_async();
     }
     if (run) {
@@ -834,7 +840,7 @@ __global__ void __launch_bounds__(512, 1) k_mlp_eval_bf16(MlpPtrs mlp, const flo
     for (int j = 0; j < kK1; j++)
       v[j] = (row < M && j < mlp.in_dim) ? x[(size_t)row * mlp.in_dim + j] : (j == mlp.in_dim ? 1.0f : 0.0f);
 #pragma unroll
-    for (int k0 = 0; k0 < kK1; k0 += 8) store_chunk(G.act, G.m, k0, kK1, v + k0);
+    for (int k0 = 0; k0 < kK1; k0 += 8) store_chunk(G.act, G.m, k0, kK2, v + k0);
     fence_proxy_async();
     float cc[3];
     alive = mlp_tile(sm, G, err, cc, mlp.in_dim < kK1);

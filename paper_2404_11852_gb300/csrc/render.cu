@@ -24,6 +24,8 @@ namespace cicero {
 
 static size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 
+constexpr int kScanChunk = 1024;  // bricks per block of the RIT offset scan (one per thread)
+
 size_t render_ws_bytes(const RenderPlan& p) {
   const size_t Q = p.Q, R = (size_t)p.R;
   size_t b = al256(64);
@@ -32,10 +34,11 @@ size_t render_ws_bytes(const RenderPlan& p) {
   if (p.want_k) b += al256(2 * Q);
   if (p.want_bwd) b += 2 * al256(4 * Q);
   if (p.want_k || p.want_bwd) b += al256(4 * Q);
-  b += 2 * al256(4 * (size_t)p.nb) + 2 * al256(4 * ((size_t)p.nb + 1));
-  b += al256(8 * ((size_t)p.nb / 4096 + 2));
+  const size_t nk = (size_t)p.nb * kOctants;  // RIT keys: (brick, octant)
+  b += 2 * al256(4 * nk) + al256(4 * (nk + 1)) + al256(4 * ((size_t)p.nb + 1));
+  b += al256(8 * ((size_t)p.nb / kScanChunk + 2));
   b += al256(16 * (size_t)p.max_tiles);
-  b += 2 * al256(16 * Q);
+  b += al256(32 * Q);
   return b;
 }
 
@@ -60,14 +63,14 @@ bool carve_render_ws(void* ws, size_t bytes, const RenderPlan& p, RenderWs* w) {
   w->rec_T = p.want_bwd ? (float*)take(4 * Q) : nullptr;
   w->rec_raw = p.want_bwd ? (float*)take(4 * Q) : nullptr;
   w->rec_ray = (p.want_k || p.want_bwd) ? (uint32_t*)take(4 * Q) : nullptr;
-  w->brick_cnt = (uint32_t*)take(4 * (size_t)p.nb);
-  w->brick_cur = (uint32_t*)take(4 * (size_t)p.nb);
-  w->brick_off = (uint32_t*)take(4 * ((size_t)p.nb + 1));
+  const size_t nk = (size_t)p.nb * kOctants;
+  w->brick_cnt = (uint32_t*)take(4 * nk);
+  w->brick_cur = (uint32_t*)take(4 * nk);
+  w->brick_off = (uint32_t*)take(4 * (nk + 1));
   w->tile_off = (uint32_t*)take(4 * ((size_t)p.nb + 1));
-  w->blk_sums = (uint32_t*)take(8 * ((size_t)p.nb / 4096 + 2));
+  w->blk_sums = (uint32_t*)take(8 * ((size_t)p.nb / kScanChunk + 2));
   w->tile = (uint4*)take(16 * (size_t)p.max_tiles);
-  w->srt_pw = (float4*)take(16 * Q);
-  w->srt_qd = (float4*)take(16 * Q);
+  w->srt = (SrtRec*)take(32 * Q);
   w->R = p.R;
   w->S = p.S;
   w->nb = p.nb;
@@ -231,7 +234,7 @@ __device__ __forceinline__ void march_ray_core(const GridGeo& g, const Samp& s, 
     const bool contrib = act && lane < first && room;
     const float wk = (act && lane < first) ? Tk * one_minus_exp_neg(sd) : 0.0f;
     const unsigned cmask = __ballot_sync(full, contrib);
-    const uint32_t key = contrib ? key_base + brick_id(g, i0) : 0xffffffffu;
+    const uint32_t key = contrib ? brick_key(g, i0, key_base) : 0xffffffffu;
     if (staged) {
       if (contrib) {
         const uint32_t j = cnt + __popc(cmask & lt_mask);
@@ -422,19 +425,25 @@ __device__ __forceinline__ void block_exscan2(uint32_t a, uint32_t b, uint32_t* 
   __syncthreads();
 }
 
-// K2a: per block of kScanChunk bricks, the sums of sample counts and tile counts.
-constexpr int kScanChunk = 4096;  // bricks per scan block (1024 threads x 4)
+// The kOctants counters of brick b (zeros past the last brick).
+__device__ __forceinline__ uint32_t brick_counts(const RenderWs& w, int b, uint32_t v[kOctants]) {
+  static_assert(kOctants == 8, "two 16-byte loads per brick");
+  uint4 a = make_uint4(0u, 0u, 0u, 0u), c = a;
+  if (b < w.nb) {
+    const uint4* p = reinterpret_cast<const uint4*>(w.brick_cnt + (size_t)b * kOctants);
+    a = p[0];
+    c = p[1];
+  }
+  v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w, v[4] = c.x, v[5] = c.y, v[6] = c.z, v[7] = c.w;
+  return a.x + a.y + a.z + a.w + c.x + c.y + c.z + c.w;
+}
 
+// K2a: per block of kScanChunk bricks (one per thread), the sums of sample counts and tile counts.
 __global__ void __launch_bounds__(1024) k_brick_sums(RenderWs w) {
   __shared__ uint32_t sh[64];
-  const int base = blockIdx.x * kScanChunk + threadIdx.x * 4;
-  uint32_t c = 0, t = 0;
-#pragma unroll
-  for (int k = 0; k < 4; k++) {
-    const uint32_t v = base + k < w.nb ? w.brick_cnt[base + k] : 0;
-    c += v;
-    t += (v + kTile - 1) / kTile;
-  }
+  uint32_t v[kOctants];
+  const uint32_t c = brick_counts(w, blockIdx.x * kScanChunk + threadIdx.x, v);
+  const uint32_t t = (c + kTile - 1) / kTile;
   uint32_t ec, et, tc, tt;
   block_exscan2(c, t, &ec, &et, &tc, &tt, sh);
   if (threadIdx.x == 0) {
@@ -460,7 +469,7 @@ __global__ void __launch_bounds__(1024) k_brick_blocks(RenderWs w, int nblk) {
     run_t += tt;
   }
   if (threadIdx.x == 0) {
-    w.brick_off[w.nb] = run_c;
+    w.brick_off[(size_t)w.nb * kOctants] = run_c;
     w.tile_off[w.nb] = run_t;
     if (run_t > (uint32_t)w.max_tiles) {
       set_err(&w.hdr[0], kErrInternal);
@@ -471,29 +480,30 @@ __global__ void __launch_bounds__(1024) k_brick_blocks(RenderWs w, int nblk) {
   }
 }
 
-// K2c: brick and tile offsets of every brick; cursors reset for the scatter.
+// K2c: the offset of every (brick, octant) key and of every brick's first tile; cursors reset for
+// the scatter.
 __global__ void __launch_bounds__(1024) k_brick_offsets(RenderWs w) {
   __shared__ uint32_t sh[64];
-  const int base = blockIdx.x * kScanChunk + threadIdx.x * 4;
-  uint32_t v[4], c = 0, t = 0;
-#pragma unroll
-  for (int k = 0; k < 4; k++) {
-    v[k] = base + k < w.nb ? w.brick_cnt[base + k] : 0;
-    c += v[k];
-    t += (v[k] + kTile - 1) / kTile;
-  }
+  const int b = blockIdx.x * kScanChunk + threadIdx.x;
+  uint32_t v[kOctants];
+  const uint32_t c = brick_counts(w, b, v);
+  const uint32_t t = (c + kTile - 1) / kTile;
   uint32_t ec, et, tc, tt;
   block_exscan2(c, t, &ec, &et, &tc, &tt, sh);
-  uint32_t oc = w.blk_sums[2 * blockIdx.x] + ec, ot = w.blk_sums[2 * blockIdx.x + 1] + et;
+  if (b < w.nb) {
+    uint32_t o[kOctants], run = w.blk_sums[2 * blockIdx.x] + ec;
 #pragma unroll
-  for (int k = 0; k < 4; k++) {
-    if (base + k < w.nb) {
-      w.brick_off[base + k] = oc;
-      w.tile_off[base + k] = ot;
-      w.brick_cur[base + k] = 0;
+    for (int k = 0; k < kOctants; k++) {
+      o[k] = run;
+      run += v[k];
     }
-    oc += v[k];
-    ot += (v[k] + kTile - 1) / kTile;
+    uint4* off = reinterpret_cast<uint4*>(w.brick_off + (size_t)b * kOctants);
+    off[0] = make_uint4(o[0], o[1], o[2], o[3]);
+    off[1] = make_uint4(o[4], o[5], o[6], o[7]);
+    uint4* cur = reinterpret_cast<uint4*>(w.brick_cur + (size_t)b * kOctants);
+    cur[0] = make_uint4(0u, 0u, 0u, 0u);
+    cur[1] = make_uint4(0u, 0u, 0u, 0u);
+    w.tile_off[b] = w.blk_sums[2 * blockIdx.x + 1] + et;
   }
 }
 
@@ -507,15 +517,16 @@ __global__ void __launch_bounds__(256) k_tiles(GridGeo g, RenderWs w) {
       if (w.tile_off[mid] <= t) lo = mid;
       else hi = mid;
     }
-    const uint32_t start = w.brick_off[lo] + (t - w.tile_off[lo]) * kTile;
-    const uint32_t cnt = min(start + (uint32_t)kTile, w.brick_off[lo + 1]) - start;
+    const uint32_t start = w.brick_off[(size_t)lo * kOctants] + (t - w.tile_off[lo]) * kTile;
+    const uint32_t cnt = min(start + (uint32_t)kTile, w.brick_off[(size_t)(lo + 1) * kOctants]) - start;
     const uint32_t bx = lo % g.nb[0], by = (lo / g.nb[0]) % g.nb[1], bz = lo / (g.nb[0] * g.nb[1]);
     w.tile[t] = make_uint4(start, cnt | (bz << 8), (uint32_t)lo, bx | (by << 16));
   }
 }
 
-// K3: counting sort of the records by brick; the payload moves into brick order so that the
-// gather kernels stream it (order inside a brick is unspecified).  A warp takes one ray at a time
+// K3: counting sort of the records by (brick, octant) key; the payload moves into brick order so
+// that the gather kernels stream it, octant by octant inside a brick (order inside an octant is
+// unspecified).  A warp takes one ray at a time
 // in chunks of 32 records; each chunk's records and their bricks' offsets load together, and the
 // next ray's header and first chunk are loaded while the current ray's atomics are in flight.
 __global__ void __launch_bounds__(256) k_scatter(RaySrc src, RenderWs w) {
@@ -583,8 +594,8 @@ __global__ void __launch_bounds__(256) k_scatter(RaySrc src, RenderWs w) {
       off = __shfl_sync(full, off, hl < 0 ? 0 : hl);
       if (valid) {
         const uint32_t dst = c.boff + off + (uint32_t)(lane - hl);
-        w.srt_pw[dst] = c.pw;
-        w.srt_qd[dst] = make_float4(__uint_as_float(q), dir.x, dir.y, dir.z);
+        w.srt[dst].pw = c.pw;
+        w.srt[dst].qd = make_float4(__uint_as_float(q), dir.x, dir.y, dir.z);
       }
     }
     if (n == 0 && rn < R) load_chunk(nstart, nn, 0, nxt);
@@ -891,8 +902,8 @@ __global__ void __launch_bounds__(kMlpThreads + kProdThreads, 1)
         loaded = (int)td.z;
       }
       if (alive && m < mcnt) {
-        const float4 pw = w.srt_pw[start + m];
-        const float4 dd = w.srt_qd[start + m];
+        const float4 pw = w.srt[start + m].pw;
+        const float4 dd = w.srt[start + m].qd;
         const float p[3] = {pw.x, pw.y, pw.z}, d[3] = {dd.y, dd.z, dd.w};
         float f[3], feat[24], e[3 + 6 * 7];
         int i0[3];
@@ -931,7 +942,7 @@ __global__ void __launch_bounds__(kMlpThreads + kProdThreads, 1)
     mlp_f32_tile(sm, X, c, mlp.in_dim, kBarEmpty0 + b);
     const int m = threadIdx.x;
     if (m < kTile && m < mcnt)
-      w.rec_c[__float_as_uint(w.srt_qd[start + m].x)] = make_float4(c[0], c[1], c[2], w.srt_pw[start + m].w);
+      w.rec_c[__float_as_uint(w.srt[start + m].qd.x)] = make_float4(c[0], c[1], c[2], w.srt[start + m].pw.w);
   }
 }
 
@@ -1093,8 +1104,8 @@ __global__ void __launch_bounds__(256) k_tiles_batch(const JobDesc* __restrict__
       if (w.tile_off[mid] <= t) lo = mid;
       else hi = mid;
     }
-    const uint32_t start = w.brick_off[lo] + (t - w.tile_off[lo]) * kTile;
-    const uint32_t cnt = min(start + (uint32_t)kTile, w.brick_off[lo + 1]) - start;
+    const uint32_t start = w.brick_off[(size_t)lo * kOctants] + (t - w.tile_off[lo]) * kTile;
+    const uint32_t cnt = min(start + (uint32_t)kTile, w.brick_off[(size_t)(lo + 1) * kOctants]) - start;
     const int j = job_of(bases + n_jobs, n_jobs, lo);
     const int* nb = jobs[j].geo.nb;
     const uint32_t b = (uint32_t)(lo - jobs[j].brick_base);
@@ -1135,9 +1146,9 @@ __global__ void __launch_bounds__(256) k_composite_batch(const JobDesc* __restri
 __global__ void k_rit_export(RenderWs w, int n_bricks, int32_t* offs, int32_t* samples) {
   const uint32_t total = w.hdr[2];
   const size_t i0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x, st = (size_t)gridDim.x * blockDim.x;
-  for (size_t i = i0; i <= (size_t)n_bricks; i += st) offs[i] = (int32_t)w.brick_off[i];
+  for (size_t i = i0; i <= (size_t)n_bricks; i += st) offs[i] = (int32_t)w.brick_off[i * kOctants];
   for (size_t i = i0; i < total; i += st) {
-    const uint32_t q = __float_as_uint(w.srt_qd[i].x);
+    const uint32_t q = __float_as_uint(w.srt[i].qd.x);
     samples[i] = (int32_t)(w.rec_ray[q] * (uint32_t)w.S + w.rec_k[q]);
   }
 }
@@ -1191,7 +1202,8 @@ cicero_status run_render(const cicero_grid* grid, const MlpPtrs& mlp, const Rend
   const int mb = blocks_for_warps(src.n_max, 16);
   {
     ProfScope ps(kStMarch, st);
-    k_clear<<<std::min(num_sms() * 4, (plan.nb + 255) / 256 + 1), 256, 0, st>>>(ws.hdr, 16, ws.brick_cnt, plan.nb);
+    k_clear<<<std::min(num_sms() * 4, (plan.nb * kOctants + 255) / 256 + 1), 256, 0, st>>>(ws.hdr, 16, ws.brick_cnt,
+                                                                                  (size_t)plan.nb * kOctants);
     const bool extra = ws.rec_k || ws.rec_ray || ws.rec_T;
     if (f16 && extra)
       k_march<__half, true><<<mb, 256, 0, st>>>(geo, plan.samp, src, (const __half*)grid->density, ws, out);
@@ -1251,7 +1263,8 @@ cicero_status run_render_batch(const BatchPlan& b, cudaStream_t st) {
   const int mb = blocks_for_warps(R, 16);
   {
     ProfScope ps(kStMarch, st);
-    k_clear<<<std::min(num_sms() * 4, (plan.nb + 255) / 256 + 1), 256, 0, st>>>(ws.hdr, 16, ws.brick_cnt, plan.nb);
+    k_clear<<<std::min(num_sms() * 4, (plan.nb * kOctants + 255) / 256 + 1), 256, 0, st>>>(ws.hdr, 16, ws.brick_cnt,
+                                                                                  (size_t)plan.nb * kOctants);
     if (b.f16)
       k_march_batch<__half><<<mb, 256, 0, st>>>(b.jobs, b.bases, b.n_jobs, R, ws);
     else

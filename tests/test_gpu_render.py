@@ -167,6 +167,16 @@ def test_ray_index_table_bit_exact(cc, orc, small, occ_scene, which, brick):
     exp = exp[np.lexsort((exp[:, 1], exp[:, 0]))]
     np.testing.assert_array_equal(got, exp)
     assert amb.sum() <= max(2, 1e-3 * R)
+    # inside each brick the samples come octant by octant (x, y, z halves of the brick as bits
+    # 0, 1, 2), in the order the library exports them
+    vox = dict(zip((want["ray"].astype(np.int64) * S + want["slot"]).tolist(), want["voxel"].tolist()))
+    nx, ny = g.n[0], g.n[1]
+    v = np.array([vox[i] for i in smp[keep_g].tolist()], dtype=np.int64)
+    i0 = np.stack([v % nx, (v // nx) % ny, v // (nx * ny)], 1)
+    octant = (((i0 % brick) >= brick // 2) * np.array([1, 2, 4])).sum(1)
+    b_of = brick_of[keep_g]
+    same = b_of[1:] == b_of[:-1]
+    assert (octant[1:][same] >= octant[:-1][same]).all()
 
 
 # ---------------------------------------------------------------------------------------------

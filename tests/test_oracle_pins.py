@@ -271,6 +271,9 @@ def test_active_samples_axis_ray(orc):
     want = (int(gz) // B * nb + int(gy) // B) * nb + np.floor(gx).astype(int) // B
     safe = np.abs(gx - np.round(gx)) > 1e-4
     np.testing.assert_array_equal(a["brick"][safe], want[safe])
+    # the voxel of each sample: floor of the vertex coordinate along x, fixed y and z
+    want_v = (int(gz) * N + int(gy)) * N + np.floor(gx).astype(int)
+    np.testing.assert_array_equal(a["voxel"][safe], want_v[safe])
 
 
 def test_active_samples_respect_occupancy(orc):
