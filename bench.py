@@ -38,6 +38,9 @@ HOLE_RECORDS = 128_000_000  # record capacity of the batched hole render (6.7 GB
 # kernel sources it was taken on; the roofline reports it only while those sources are unchanged.
 GATHER_TRAFFIC = {"bytes": 2740489984 + 1355325440, "sources_sha1": "11ffd68d6a02626c07d18466d921362979b780f3"}
 GATHER_SOURCES = ("mlp_tc.cu", "common.cuh", "internal.h")
+# shared-memory wavefronts per composited sample of the BF16 gather (LSU loads + LSU stores +
+# tensor-core operand reads, ncu on the 320x320 case), valid for the sources hashed above
+GATHER_SMEM_WAVEFRONTS_PER_SAMPLE = (24398098 + 31850717 + 67379200) / 10312421
 
 
 def parse():
@@ -175,9 +178,11 @@ def peaks():
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             j = json.load(f)
         return {"hbm_gbs": j["hbm_gbs"], "bf16_tflops": j["bf16_tflops"],
-                "bf16_tflops_sustained": j.get("bf16_tflops_sustained", j["bf16_tflops"]), "src": "measured"}
+                "bf16_tflops_sustained": j.get("bf16_tflops_sustained", j["bf16_tflops"]),
+                "sm_max_mhz": j.get("sm_max_mhz", 2070.0), "src": "measured"}
     except Exception:
-        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "src": "fallback"}
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0,
+                "src": "fallback"}
 
 
 class ClockSampler:
@@ -917,6 +922,12 @@ def main():
             "peak": pk["bf16_tflops_sustained"], "unit": "TFLOP/s", "frac": achieved / pk["bf16_tflops_sustained"],
             "traffic": gather_traffic(), "peak_src": f"{pk['src']} (sustained bf16)",
             "flop_per_launch": FLOP_PER_SAMPLE * active}
+    if gather_traffic() is not None:
+        # the shared-memory bound: one 128-byte wavefront per clock per SM
+        n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+        t_smem = GATHER_SMEM_WAVEFRONTS_PER_SAMPLE * active / (n_sm * pk["sm_max_mhz"] * 1e6)
+        roof["shared_memory"] = {"wavefronts_per_sample": GATHER_SMEM_WAVEFRONTS_PER_SAMPLE,
+                                 "bound_ms": t_smem * 1e3, "frac": t_smem / t_launch}
     stages = {k: {"ms_per_step": v[0] / 2, "launches_per_step": v[1] / 2} for k, v in prof.items() if v[1]}
     stage_roof = stage_roofline(stages, pk, R, int(holes), active, int(hole_hdr[2]))
 
