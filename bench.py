@@ -332,10 +332,14 @@ class SparwWindow:
                               self.ref_depth, None, None, self.ws_r)
 
     def run(self):
+        # No separate void test (void_grid None): a void hole's march in the hole batch finds no
+        # occupied slot and writes the background with depth +inf, the frames the test would give
+        # (bit for bit; tests/test_gpu_window_full.py), without repeating the start of every real
+        # hole's march.
         cc, L = self.cc, self.lists
         self.render_reference()
-        cc.cicero_warp_batch(self.ref_rgb, self.ref_depth, self.cd, self.tds, self.max_angle, self.grid.desc,
-                             self.sd, L[0], L[1], L[2], L[3], self.nh.view(-1), self.ws_w)
+        cc.cicero_warp_batch(self.ref_rgb, self.ref_depth, self.cd, self.tds, self.max_angle, None, None,
+                             L[0], L[1], L[2], L[3], self.nh.view(-1), self.ws_w)
         cc.cicero_render_holes_batch(self.grid.desc, self.mlp.desc, self.tds, self.sd, self.opt_holes, L[3], self.nh,
                                      self.n * self.R, L[0], L[1], self.ws_h)
 

@@ -277,8 +277,10 @@ cicero_status cicero_extrapolate_pose(const cicero_camera *prev, const cicero_ca
 /* ---------------------------------------------------------------------------------------------
  * SpaRW over a trajectory with reference rendering overlapped (Sec. III-C, "Reference Frame
  * Rendering"): frames are taken in windows of `window` targets; window w is warped from
- * reference frame refs[w] (cicero_warp_batch, void test on the pipeline's grid) and its holes
- * rendered (cicero_render_holes_batch), while reference w + 1 is rendered on `stream_ref`.  With
+ * reference frame refs[w] (cicero_warp_batch) and its holes rendered (cicero_render_holes_batch),
+ * while reference w + 1 is rendered on `stream_ref`.  Void holes are not tested separately: their
+ * march in the hole render finds no occupied slot and writes the background with depth +inf,
+ * the same frames as with the void depth test of cicero_warp_batch.  With
  * stream_ref == stream_tgt the same work runs serialised (same results).  Reference poses are the
  * caller's (for example from cicero_extrapolate_pose); every frame, reference or target, has the
  * size and intrinsics of `cam`.

@@ -256,7 +256,10 @@ cicero_status cicero_pipeline_run(cicero_pipeline* p, const cicero_camera* targe
       whc[v] = wh[v];
     }
     int32_t* nh = (int32_t*)(ws + L.nh);
-    s = cicero_warp_batch(ref_rgb(b), ref_depth(b), &refs[w], &targets[f0], k, p->max_angle, &p->grid, &p->samp, wr,
+    // No separate void test: a void hole's march in the hole render finds no occupied slot and
+    // writes the background with depth +inf, the result the test would give, so the test would only
+    // repeat the start of every real hole's march.
+    s = cicero_warp_batch(ref_rgb(b), ref_depth(b), &refs[w], &targets[f0], k, p->max_angle, nullptr, nullptr, wr,
                           depth ? wd : nullptr, wm, wh, nh, ws + L.ws_warp, L.ws_warp_bytes, st);
     if (s != CICERO_OK) return s;
     s = cicero_render_holes_batch(&p->grid, &p->mlp, &targets[f0], k, &p->samp, &p->opt_holes, whc, nh,

@@ -85,3 +85,41 @@ def test_full_window_against_oracle(cc, orc):
     # the hole render writes colour and depth; opacity is not an output of it
     sub = {"rgb": np.concatenate(got_rgb), "depth": np.concatenate(got_dep), "acc": want["acc"]}
     check_render(sub, want, TOL16, psnr_min=PSNR16)
+
+
+def test_void_holes_rendered_equal_void_test(cc):
+    """The void depth test (Sec. III-B) decides nothing the hole render does not: a hole whose ray
+    meets no occupied cell composites no sample and gets the background with depth +inf.  The
+    window with the separate test and the window that leaves void holes to the hole batch give
+    the same frames bit for bit."""
+    import torch
+    g, m = scenes.scene_large(), scenes.make_mlp(12)
+    grid, mlp = cc.DeviceGrid.from_host(g), cc.DeviceMlp.from_host(m)
+    cam = scenes.orbit_camera(320, 320, sampling=scenes.sampling_march(256, 256))
+    targets = [scenes.offset_camera(cam, k) for k in scenes.SPARW_OFFSETS]
+    R, n = cam.width * cam.height, len(targets)
+    sd, cd = cc.sampling_from(cam.sampling), cc.camera_from(cam)
+    tds = [cc.camera_from(t) for t in targets]
+    o16 = cc.options(cc.MLP_BF16, 4)
+    oh = cc.options(cc.MLP_BF16, 4, max_records=n * R * 40)
+    ref_rgb, ref_depth = torch.empty(R, 3, device="cuda"), torch.empty(R, device="cuda")
+    ws_r = cc.workspace(cc.cicero_render_workspace_size(grid.desc, R, sd, o16))
+    cc.cicero_render(grid.desc, mlp.desc, cd, sd, o16, ref_rgb, ref_depth, None, None, ws_r)
+    ws_w = cc.workspace(cc.cicero_warp_batch_workspace_size(tds))
+    ws_h = cc.workspace(cc.cicero_render_workspace_size(grid.desc, n * R, sd, oh))
+    out = {}
+    for mode, vg, vs in (("test", grid.desc, sd), ("render", None, None)):
+        t_rgb, t_dep = torch.empty(n, R, 3, device="cuda"), torch.empty(n, R, device="cuda")
+        mask = torch.empty(n, R, dtype=torch.uint8, device="cuda")
+        hidx = torch.empty(n, R, dtype=torch.int32, device="cuda")
+        nh = torch.zeros(n, dtype=torch.int32, device="cuda")
+        L = [[x[i] for i in range(n)] for x in (t_rgb, t_dep, mask, hidx)]
+        cc.cicero_warp_batch(ref_rgb, ref_depth, cd, tds, 180.0, vg, vs, L[0], L[1], L[2], L[3], nh, ws_w)
+        cc.cicero_render_holes_batch(grid.desc, mlp.desc, tds, sd, oh, L[3], nh, n * R, L[0], L[1], ws_h)
+        cc.cicero_workspace_status(ws_h)
+        out[mode] = (t_rgb, t_dep, mask.cpu().numpy(), int(nh.sum().item()))
+    n_void = int((out["test"][2] == 2).sum())
+    assert n_void > 0  # the case has void holes
+    assert out["render"][3] == out["test"][3] + n_void
+    assert torch.equal(out["test"][0], out["render"][0])
+    assert torch.equal(out["test"][1], out["render"][1])
