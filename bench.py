@@ -343,6 +343,15 @@ class SparwWindow:
         cc.cicero_render_holes_batch(self.grid.desc, self.mlp.desc, self.tds, self.sd, self.opt_holes, L[3], self.nh,
                                      self.n * self.R, L[0], L[1], self.ws_h)
 
+    def classify(self):
+        """Per target, the holes the separate void test would mark as disocclusions (mask 1) and as
+        void (mask 2).  Overwrites the target frames."""
+        cc, L = self.cc, self.lists
+        cc.cicero_warp_batch(self.ref_rgb, self.ref_depth, self.cd, self.tds, self.max_angle, self.grid.desc,
+                             self.sd, L[0], L[1], L[2], L[3], self.nh.view(-1), self.ws_w)
+        m = self.mask.cpu().numpy()
+        return (m == 1).sum(axis=1), (m == 2).sum(axis=1)
+
     def set_frames(self, t_rgb):
         """Write the target frames into ``t_rgb`` [n, R, 3] from the next run on."""
         self.t_rgb = t_rgb
@@ -748,10 +757,14 @@ def sparw_small_scene(cc, torch, dev, n_pix=1024):
         mse = float(np.mean(e ** 2))
         per.append({"k": scenes.SPARW_OFFSETS[i], "fraction_marched": float(holes[i]) / R,
                     "psnr_db": 10 * math.log10(1.0 / max(mse, 1e-30)), "max_err": float(e.max())})
+    disocc, void = win.classify()
+    for i, p in enumerate(per):
+        p.update({"disocclusion_holes": int(disocc[i]), "void_holes": int(void[i]),
+                  "fraction_void": float(void[i]) / R})
     return {"workload": "64^3 x 12 FP32 scene, 800x800, 64 samples, 16 targets (1 deg yaw + 5 mm apart)",
             "window_ms": t_win, "target_fps": n_t / (t_win / 1e3), "psnr_pixels_per_target": n_pix,
             "psnr_db_min": min(p["psnr_db"] for p in per), "fraction_marched_mean": float(holes.sum()) / (n_t * R),
-            "targets": per}
+            "marched": "disocclusion and void holes (a void hole's march composites nothing)", "targets": per}
 
 
 # ---------------------------------------------------------------------------------------------
@@ -969,6 +982,8 @@ def main():
         others["sparw_phi_sweep"] = phi_sweep(cc, torch, dev, grid, o16, active)
         others["config_hash_grid"] = hash_workload(cc, torch, dev, grid, g_h)
 
+    # the holes the separate void test would classify (outside every timed region)
+    disocc, void = win.classify()
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
@@ -988,7 +1003,8 @@ def main():
             "active_samples_per_frame": active,
             "autotune_ms_by_brick": {"bf16": tune16, "fp32": tune32}, "brick": {"bf16": b16, "fp32": b32},
             "fraction_rays_marched_targets": holes / (N_TARGETS * R),
-            "hole_batch": {"rays": holes / 1, "composited_samples": int(hole_hdr[2]),
+            "hole_batch": {"rays": holes / 1, "disocclusion_rays": int(disocc.sum()), "void_rays": int(void.sum()),
+                           "composited_samples": int(hole_hdr[2]),
                            "records_reserved": int(np.uint32(hole_hdr[3])), "record_capacity": HOLE_RECORDS},
             "roofline": roof, "stages": stages, "stage_roofline": stage_roof, "quality": quality, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "frames/s", "h2d_bytes_per_step": int(pose_h.numel() * 4),
