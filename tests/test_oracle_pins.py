@@ -647,3 +647,19 @@ def test_hash_continuous_across_cell_faces(orc):
     p = np.array([[x_face - 1e-9, 0.13, -0.41], [x_face + 1e-9, 0.13, -0.41]])
     f = orc.hash_features(g, p)
     np.testing.assert_allclose(f[0], f[1], atol=1e-7)
+
+
+def test_extrapolate_paper_example_n4(orc):
+    """The Eq. 6 example of Sec. III-C (tests/golden/eq6_reference_pose_n4.txt): lead N/2 = 2."""
+    import os
+    rows = {}
+    with open(os.path.join(os.path.dirname(__file__), "golden", "eq6_reference_pose_n4.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                k, *v = line.split()
+                rows[k] = np.array([float(x) for x in v])
+    prev = np.concatenate([np.eye(3), rows["T1"][:, None]], 1)
+    cur = np.concatenate([np.eye(3), rows["T2"][:, None]], 1)
+    r = orc.extrapolate_pose(prev, cur, rows["N"][0] / 2)
+    np.testing.assert_array_equal(r[:, 3], rows["R1"])  # dyadic values: exact in FP64
+    np.testing.assert_array_equal(r[:, :3], np.eye(3))
