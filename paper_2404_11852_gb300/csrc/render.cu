@@ -2,11 +2,13 @@
 //
 //   K1 k_march        one warp per ray, 32 slots per step: Indexing, density gathering,
 //                     alpha, transmittance by a warp scan of sigma*delta, early stop; reserves an
-//                     upper bound of its records, emits one record (position, w, brick) per
-//                     composited sample and counts them into the brick histogram
-//   K2 k_brick_*      brick offsets (3-phase exclusive scan of the histogram) and the tile list
-//   K3 k_scatter      counting sort of the records by brick, moving their payload into brick
-//                     order: the Ray Index Table
+//                     upper bound of its records, emits one record (position, w, RIT key =
+//                     brick x 8 + octant) per composited sample and counts them into the key
+//                     histogram
+//   K2 k_brick_*      key offsets (3-phase exclusive scan of the histogram, one brick of 8 keys
+//                     per thread), tile offsets per brick and the tile list
+//   K3 k_scatter      counting sort of the records by key, moving their payload into (brick,
+//                     octant) order as 32-byte records: the Ray Index Table
 //   K5 k_gather_mlp_f32 / mlp_tc.cu
 //                     per brick: one TMA copy of the brick (+1 vertex halo) into shared memory,
 //                     trilinear feature gathering from there, view encoding and the MLP
@@ -155,8 +157,9 @@ __device__ __forceinline__ void count_bricks(const RenderWs& w, uint32_t n, KeyA
   }
 }
 
-// K1 per ray (one warp; lane = slot within a chunk of 32 slots).  Records carry the brick id
-// offset by key_base (the job's first brick in a batch); dep/acc/steps point at the ray's outputs
+// K1 per ray (one warp; lane = slot within a chunk of 32 slots).  Records carry the RIT key of
+// their brick, offset by key_base (the job's first brick in a batch), and octant; dep/acc/steps
+// point at the ray's outputs
 // (or are NULL).  When the caller capped the record capacity below rays x samples, a ray that can
 // emit at most kStage records (and no backward / RIT extras) stages them in the warp's shared
 // buffers st_pw/st_key and reserves exactly its count at the end, so the capacity follows the
