@@ -950,6 +950,30 @@ __global__ void __launch_bounds__(kMlpThreads + kProdThreads, 1)
 }
 
 // K6: per ray, in slot order.
+// Sum over one ray's n records of w c: lane l takes records l, l + 32, l + 64, ... in that order
+// (so every caller sums identically), with the loads of four of them issued before their sums.
+__device__ __forceinline__ void ray_color_sum(const RenderWs& w, uint32_t start, uint32_t n, float& a0, float& a1,
+                                              float& a2) {
+  const uint32_t lane = threadIdx.x & 31u;
+  a0 = a1 = a2 = 0.f;
+  for (uint32_t j0 = 0; j0 < n; j0 += 128) {
+    float4 v[4];
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      const uint32_t j = j0 + 32u * u + lane;
+      v[u] = j < n ? w.rec_c[start + j] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      if (j0 + 32u * u + lane < n) {
+        a0 += v[u].w * v[u].x;
+        a1 += v[u].w * v[u].y;
+        a2 += v[u].w * v[u].z;
+      }
+    }
+  }
+}
+
 __global__ void __launch_bounds__(256) k_composite(RaySrc src, Samp s, RenderWs w, OutBufs out) {
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -978,13 +1002,8 @@ __global__ void __launch_bounds__(256) k_composite(RaySrc src, Samp s, RenderWs 
       const uint32_t n = __shfl_sync(full, n_l, jj), start = __shfl_sync(full, start_l, jj);
       const float T = __shfl_sync(full, T_l, jj);
       const int view = __shfl_sync(full, rr.view, jj), pix = __shfl_sync(full, rr.pix, jj);
-      float a0 = 0.f, a1 = 0.f, a2 = 0.f;
-      for (uint32_t j = lane; j < n; j += 32) {
-        const float4 v = w.rec_c[start + j];
-        a0 += v.w * v.x;
-        a1 += v.w * v.y;
-        a2 += v.w * v.z;
-      }
+      float a0, a1, a2;
+      ray_color_sum(w, start, n, a0, a1, a2);
       a0 = warp_sum(a0);
       a1 = warp_sum(a1);
       a2 = warp_sum(a2);
@@ -1124,13 +1143,8 @@ __global__ void __launch_bounds__(256) k_composite_batch(const JobDesc* __restri
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   for (int r = warp; r < R; r += nwarps) {
     const uint32_t n = w.ray_n[r], start = w.ray_start[r];
-    float a0 = 0.f, a1 = 0.f, a2 = 0.f;
-    for (uint32_t j = lane; j < n; j += 32) {
-      const float4 v = w.rec_c[start + j];
-      a0 += v.w * v.x;
-      a1 += v.w * v.y;
-      a2 += v.w * v.z;
-    }
+    float a0, a1, a2;
+    ray_color_sum(w, start, n, a0, a1, a2);
     a0 = warp_sum(a0);
     a1 = warp_sum(a1);
     a2 = warp_sum(a2);
