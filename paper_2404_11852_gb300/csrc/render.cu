@@ -483,8 +483,8 @@ __global__ void __launch_bounds__(1024) k_brick_blocks(RenderWs w, int nblk) {
   }
 }
 
-// K2c: the offset of every (brick, octant) key and of every brick's first tile; cursors reset for
-// the scatter.
+// K2c: the offset of every (brick, octant) key and of every brick's first tile; the scatter's
+// cursors start at the keys' offsets.
 __global__ void __launch_bounds__(1024) k_brick_offsets(RenderWs w) {
   __shared__ uint32_t sh[64];
   const int b = blockIdx.x * kScanChunk + threadIdx.x;
@@ -503,9 +503,9 @@ __global__ void __launch_bounds__(1024) k_brick_offsets(RenderWs w) {
     uint4* off = reinterpret_cast<uint4*>(w.brick_off + (size_t)b * kOctants);
     off[0] = make_uint4(o[0], o[1], o[2], o[3]);
     off[1] = make_uint4(o[4], o[5], o[6], o[7]);
-    uint4* cur = reinterpret_cast<uint4*>(w.brick_cur + (size_t)b * kOctants);
-    cur[0] = make_uint4(0u, 0u, 0u, 0u);
-    cur[1] = make_uint4(0u, 0u, 0u, 0u);
+    uint4* cur = reinterpret_cast<uint4*>(w.brick_cur + (size_t)b * kOctants);  // cursors start at the offsets
+    cur[0] = make_uint4(o[0], o[1], o[2], o[3]);
+    cur[1] = make_uint4(o[4], o[5], o[6], o[7]);
     w.tile_off[b] = w.blk_sums[2 * blockIdx.x + 1] + et;
   }
 }
@@ -529,8 +529,8 @@ __global__ void __launch_bounds__(256) k_tiles(GridGeo g, RenderWs w) {
 
 // K3: counting sort of the records by (brick, octant) key; the payload moves into brick order so
 // that the gather kernels stream it, octant by octant inside a brick (order inside an octant is
-// unspecified).  A warp takes one ray at a time
-// in chunks of 32 records; each chunk's records and their bricks' offsets load together, and the
+// unspecified).  A warp takes one ray at a time in chunks of 32 records.  The cursors start at
+// their keys' offsets, so the atomic of a run of equal keys returns the run's destination; the
 // next ray's header and first chunk are loaded while the current ray's atomics are in flight.
 __global__ void __launch_bounds__(256) k_scatter(RaySrc src, RenderWs w) {
   const int lane = threadIdx.x & 31;
@@ -541,7 +541,7 @@ __global__ void __launch_bounds__(256) k_scatter(RaySrc src, RenderWs w) {
   const unsigned lt_mask = (1u << lane) - 1u;
   const unsigned le_mask = (2u << lane) - 1u;
   struct Chunk {
-    uint32_t key, boff;
+    uint32_t key;
     float4 pw;
   };
   auto load_chunk = [&](uint32_t start, uint32_t n, uint32_t j0, Chunk& c) {
@@ -549,7 +549,6 @@ __global__ void __launch_bounds__(256) k_scatter(RaySrc src, RenderWs w) {
     const bool valid = j < n;
     c.key = valid ? w.rec_key[start + j] : 0xffffffffu;
     c.pw = valid ? w.rec_pw[start + j] : make_float4(0.f, 0.f, 0.f, 0.f);
-    c.boff = valid ? w.brick_off[c.key] : 0u;
   };
   // the warp's current ray and its first chunk
   int r = warp;
@@ -596,7 +595,7 @@ __global__ void __launch_bounds__(256) k_scatter(RaySrc src, RenderWs w) {
       const int hl = 31 - __clz(heads & le_mask);
       off = __shfl_sync(full, off, hl < 0 ? 0 : hl);
       if (valid) {
-        const uint32_t dst = c.boff + off + (uint32_t)(lane - hl);
+        const uint32_t dst = off + (uint32_t)(lane - hl);
         w.srt[dst].pw = c.pw;
         w.srt[dst].qd = make_float4(__uint_as_float(q), dir.x, dir.y, dir.z);
       }
