@@ -340,10 +340,14 @@ __global__ void __launch_bounds__(256, 4) k_march(GridGeo g, Samp s, RaySrc src,
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   const int R = ray_count(src);
-  __shared__ float4 st_pw[8][kStage];
-  __shared__ uint32_t st_key[8][kStage];
+  // record staging: dynamic shared memory, present (kMarchStageBytes) only when the launch stages,
+  // i.e. the capacity is capped and the records carry no extras; otherwise the larger L1 serves
+  // the density loads
+  extern __shared__ __align__(16) unsigned char march_stage[];
   __shared__ RaySetup setup[8][32];
   const int wb = threadIdx.x >> 5;
+  float4* st_pw = reinterpret_cast<float4*>(march_stage) + wb * kStage;
+  uint32_t* st_key = reinterpret_cast<uint32_t*>(march_stage + 8 * kStage * sizeof(float4)) + wb * kStage;
   for (long long i0 = 0;; i0 += 32) {
     const long long rl = (long long)warp + (i0 + lane) * nwarps;
     const unsigned have = __ballot_sync(0xffffffffu, rl < R);
@@ -382,10 +386,18 @@ __global__ void __launch_bounds__(256, 4) k_march(GridGeo g, Samp s, RaySrc src,
       float* dep = out.depth[q.view];
       march_ray_core<T, EXTRA>(g, s, dens, w, (int)((long long)warp + (i0 + j) * nwarps), o, d, sl, q.bound, 0u,
                                dep ? dep + q.pix : nullptr, out.acc ? out.acc + q.pix : nullptr,
-                               out.n_steps ? out.n_steps + q.pix : nullptr, st_pw[wb], st_key[wb]);
+                               out.n_steps ? out.n_steps + q.pix : nullptr, st_pw, st_key);
     }
     __syncwarp();  // the setup slots are free for the next group
   }
+}
+
+// Dynamic shared memory of a k_march launch: the staging buffers exactly when march_ray_core
+// stages (capacity capped below rays x slots, no record extras).
+constexpr int kMarchStageBytes = 8 * kStage * (int)(sizeof(float4) + sizeof(uint32_t));
+static int march_stage_bytes(const RenderWs& w, bool extra) {
+  const bool capped = (unsigned long long)w.Q < (unsigned long long)w.R * (unsigned long long)w.S;
+  return capped && !extra ? kMarchStageBytes : 0;
 }
 
 // K2: exclusive scan of the brick histogram and the list of tiles (<= kTile samples of one brick).
@@ -1221,14 +1233,22 @@ cicero_status run_render(const cicero_grid* grid, const MlpPtrs& mlp, const Rend
     k_clear<<<std::min(num_sms() * 4, (plan.nb * kOctants + 255) / 256 + 1), 256, 0, st>>>(ws.hdr, 16, ws.brick_cnt,
                                                                                   (size_t)plan.nb * kOctants);
     const bool extra = ws.rec_k || ws.rec_ray || ws.rec_T;
+    const int dyn = march_stage_bytes(ws, extra);
+    static const bool attrs = [] {
+      // staging + the per-ray setup exceed the default 48 KB per block: opt in once per instance
+      cudaFuncSetAttribute(k_march<__half, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMarchStageBytes);
+      cudaFuncSetAttribute(k_march<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMarchStageBytes);
+      return true;
+    }();
+    (void)attrs;
     if (f16 && extra)
-      k_march<__half, true><<<mb, 256, 0, st>>>(geo, plan.samp, src, (const __half*)grid->density, ws, out);
+      k_march<__half, true><<<mb, 256, dyn, st>>>(geo, plan.samp, src, (const __half*)grid->density, ws, out);
     else if (f16)
-      k_march<__half, false><<<mb, 256, 0, st>>>(geo, plan.samp, src, (const __half*)grid->density, ws, out);
+      k_march<__half, false><<<mb, 256, dyn, st>>>(geo, plan.samp, src, (const __half*)grid->density, ws, out);
     else if (extra)
-      k_march<float, true><<<mb, 256, 0, st>>>(geo, plan.samp, src, (const float*)grid->density, ws, out);
+      k_march<float, true><<<mb, 256, dyn, st>>>(geo, plan.samp, src, (const float*)grid->density, ws, out);
     else
-      k_march<float, false><<<mb, 256, 0, st>>>(geo, plan.samp, src, (const float*)grid->density, ws, out);
+      k_march<float, false><<<mb, 256, dyn, st>>>(geo, plan.samp, src, (const float*)grid->density, ws, out);
   }
   {
     ProfScope ps(kStBucket, st);
