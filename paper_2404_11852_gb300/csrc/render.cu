@@ -542,8 +542,9 @@ __global__ void __launch_bounds__(256) k_tiles(GridGeo g, RenderWs w) {
 // K3: counting sort of the records by (brick, octant) key; the payload moves into brick order so
 // that the gather kernels stream it, octant by octant inside a brick (order inside an octant is
 // unspecified).  A warp takes one ray at a time in chunks of 32 records.  The cursors start at
-// their keys' offsets, so the atomic of a run of equal keys returns the run's destination; the
-// next ray's header and first chunk are loaded while the current ray's atomics are in flight.
+// their keys' offsets, so the atomic of a run of equal keys returns the run's destination.  A
+// chunk's records are written one step later, while the next chunk's atomics are in flight, and
+// the next ray's header and first chunk are loaded ahead too.
 __global__ void __launch_bounds__(256) k_scatter(RaySrc src, RenderWs w) {
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -561,6 +562,22 @@ __global__ void __launch_bounds__(256) k_scatter(RaySrc src, RenderWs w) {
     const bool valid = j < n;
     c.key = valid ? w.rec_key[start + j] : 0xffffffffu;
     c.pw = valid ? w.rec_pw[start + j] : make_float4(0.f, 0.f, 0.f, 0.f);
+  };
+  // the chunk whose atomics were issued in the previous step: written once their results are
+  // back (every lane takes the base of its run's head), one step later
+  bool p_any = false, p_valid = false;
+  uint32_t p_off = 0, p_q = 0;
+  int p_hl = 0;
+  float4 p_pw = make_float4(0.f, 0.f, 0.f, 0.f), p_dir = p_pw;
+  auto flush = [&]() {
+    if (!p_any) return;
+    const uint32_t base = __shfl_sync(full, p_off, p_hl < 0 ? 0 : p_hl);
+    if (p_valid) {
+      const uint32_t dst = base + (uint32_t)(lane - p_hl);
+      w.srt[dst].pw = p_pw;
+      w.srt[dst].qd = make_float4(__uint_as_float(p_q), p_dir.x, p_dir.y, p_dir.z);
+    }
+    p_any = false;
   };
   // the warp's current ray and its first chunk
   int r = warp;
@@ -603,14 +620,15 @@ __global__ void __launch_bounds__(256) k_scatter(RaySrc src, RenderWs w) {
         const unsigned run = vmask & ~lt_mask & (end == 32 ? full : ((1u << end) - 1u));
         off = atomicAdd(&w.brick_cur[c.key], (uint32_t)__popc(run));
       }
-      // every lane takes the base of its run's head
-      const int hl = 31 - __clz(heads & le_mask);
-      off = __shfl_sync(full, off, hl < 0 ? 0 : hl);
-      if (valid) {
-        const uint32_t dst = off + (uint32_t)(lane - hl);
-        w.srt[dst].pw = c.pw;
-        w.srt[dst].qd = make_float4(__uint_as_float(q), dir.x, dir.y, dir.z);
-      }
+      // the previous chunk is written while this chunk's atomics are in flight
+      flush();
+      p_any = true;
+      p_valid = valid;
+      p_off = off;
+      p_hl = 31 - __clz(heads & le_mask);  // this lane's run head
+      p_q = q;
+      p_pw = c.pw;
+      p_dir = dir;
     }
     if (n == 0 && rn < R) load_chunk(nstart, nn, 0, nxt);
     n = nn;
@@ -618,6 +636,7 @@ __global__ void __launch_bounds__(256) k_scatter(RaySrc src, RenderWs w) {
     dir = ndir;
     cur = nxt;
   }
+  flush();
 }
 
 // -------------------------------------------------------------------------------------------
