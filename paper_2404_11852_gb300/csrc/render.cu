@@ -1223,7 +1223,7 @@ static int blocks_for_warps(long long warps, int per_sm) {
 }
 
 template <typename T>
-static cicero_status launch_f32(const GridGeo& geo, const RaySrc& src, int S, const MlpPtrs& mlp, const RenderWs& ws,
+static cicero_status launch_f32(const GridGeo& geo, int S, const MlpPtrs& mlp, const RenderWs& ws,
                                 const CUtensorMap& map, const BrickBox& box, cudaStream_t st) {
   const int nbuf = F32Smem::tile + box.box_bytes <= 227 * 1024 ? 2 : 1;  // two input buffers when they fit
   const int smem = (nbuf == 2 ? F32Smem::tile : F32Smem::tile1) + box.box_bytes;
@@ -1293,8 +1293,8 @@ cicero_status run_render(const cicero_grid* grid, const MlpPtrs& mlp, const Rend
   } else if (plan.precision == CICERO_MLP_BF16) {
     s = launch_gather_mlp_bf16(grid, geo, plan.samp, src, mlp, ws, map, box, st);
   } else {
-    s = f16 ? launch_f32<__half>(geo, src, plan.S, mlp, ws, map, box, st)
-            : launch_f32<float>(geo, src, plan.S, mlp, ws, map, box, st);
+    s = f16 ? launch_f32<__half>(geo, plan.S, mlp, ws, map, box, st)
+            : launch_f32<float>(geo, plan.S, mlp, ws, map, box, st);
   }
   if (s != CICERO_OK) return s;
   if (!out.rgb[0]) return CICERO_OK;  // the backward only needs the per-sample records
