@@ -128,6 +128,7 @@ cicero_status make_geo(const cicero_grid* g, int brick, GridGeo* geo, bool with_
   geo->occ_res = g->occ ? g->occ_res : 0;
   geo->brick = brick;
   geo->brick_shift = brick == 4 ? 2 : brick == 8 ? 3 : 4;
+  geo->idx32 = (unsigned long long)g->n[0] * g->n[1] * g->n[2] <= 0x7FFFFFFFull ? 1 : 0;
   const size_t row = (size_t)g->n[0] * g->C * elem_bytes(g->dtype);
   if (with_features && (((uintptr_t)g->features & 15) || (row & 15)))
     return fail(CICERO_ERR_ALIGNMENT, "features must be 16-byte aligned with n0*C*elem a multiple of 16 (TMA)");

@@ -39,6 +39,7 @@ struct GridGeo {
   int brick;           // voxels per brick edge (a power of two)
   int brick_shift;     // log2(brick)
   int nb[3];           // bricks per axis
+  int idx32;           // 1 when every vertex index fits in 31 bits (32-bit address arithmetic)
 };
 
 struct Samp {
@@ -256,12 +257,26 @@ __device__ __forceinline__ float ldf<__half>(const __half* p) { return __half2fl
 // Trilinear density from the global grid (read through the read-only path).
 template <typename T>
 __device__ __forceinline__ float density_trilinear(const GridGeo& g, const T* dens, const int i0[3], const float f[3]) {
-  size_t nx = g.n[0], nxy = (size_t)g.n[0] * g.n[1];
-  size_t b = (size_t)i0[2] * nxy + (size_t)i0[1] * nx + i0[0];
-  float v000 = ldf(dens + b), v001 = ldf(dens + b + 1);
-  float v010 = ldf(dens + b + nx), v011 = ldf(dens + b + nx + 1);
-  float v100 = ldf(dens + b + nxy), v101 = ldf(dens + b + nxy + 1);
-  float v110 = ldf(dens + b + nxy + nx), v111 = ldf(dens + b + nxy + nx + 1);
+  const T *p00, *p01, *p10, *p11;  // the four x-pairs of corners: (y, z) = (0,0), (1,0), (0,1), (1,1)
+  if (g.idx32) {
+    const int nx = g.n[0], nxy = g.n[0] * g.n[1];
+    const int b = (i0[2] * g.n[1] + i0[1]) * nx + i0[0];
+    p00 = dens + b;
+    p01 = dens + (b + nx);
+    p10 = dens + (b + nxy);
+    p11 = dens + (b + nxy + nx);
+  } else {
+    const size_t nx = g.n[0], nxy = (size_t)g.n[0] * g.n[1];
+    const size_t b = (size_t)i0[2] * nxy + (size_t)i0[1] * nx + i0[0];
+    p00 = dens + b;
+    p01 = dens + b + nx;
+    p10 = dens + b + nxy;
+    p11 = dens + b + nxy + nx;
+  }
+  float v000 = ldf(p00), v001 = ldf(p00 + 1);
+  float v010 = ldf(p01), v011 = ldf(p01 + 1);
+  float v100 = ldf(p10), v101 = ldf(p10 + 1);
+  float v110 = ldf(p11), v111 = ldf(p11 + 1);
   float fx = f[0], fy = f[1], fz = f[2];
   float c00 = v000 + fx * (v001 - v000), c01 = v010 + fx * (v011 - v010);
   float c10 = v100 + fx * (v101 - v100), c11 = v110 + fx * (v111 - v110);
