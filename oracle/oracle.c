@@ -20,8 +20,8 @@
  * relative 1e-4 of the threshold are flagged and their other outcome is returned as well.
  *
  * Readings where the paper is silent (camera axes, sample placement, activation, positional
- * encoding, background, depth definition, void rule, splat footprint, tie-break) are the ones
- * listed in the design doc and are restated at each function below.
+ * encoding, background, depth definition, void rule, splat footprint, tie-break) are stated at
+ * each function below.
  */
 #include <math.h>
 #include <stdint.h>
