@@ -88,6 +88,7 @@ def lib():
         L.or_backward.restype = C.c_int
         L.or_relu_margin.argtypes = [P] * 5
         L.or_max_threads.restype = C.c_int
+        L.or_rays_of.argtypes = [P] * 5
         _lib = L
     return _lib
 
@@ -382,6 +383,18 @@ def hash_features(grid, points):
     p = keep(np.ascontiguousarray(points, dtype=np.float64))
     out = np.zeros((p.shape[0], grid.C))
     lib().or_hash_features(C.byref(g), _ptr(p), p.shape[0], _ptr(out))
+    return out
+
+
+def camera_rays(cam, pix=None) -> dict:
+    """The oracle's rays of camera ``cam`` (every pixel, or the list ``pix``): FP32 origin and
+    direction (``o32``, ``d32``, the rays of the integer decisions) and FP64 (``o64``, ``d64``)."""
+    keep = _Keep()
+    r = _rays(keep, cam=cam, pix=pix)
+    n = _nrays(cam=cam, pix=pix)
+    out = {"o32": np.zeros((n, 3), np.float32), "d32": np.zeros((n, 3), np.float32),
+           "o64": np.zeros((n, 3)), "d64": np.zeros((n, 3))}
+    lib().or_rays_of(C.byref(r), _ptr(out["o32"]), _ptr(out["d32"]), _ptr(out["o64"]), _ptr(out["d64"]))
     return out
 
 

@@ -864,6 +864,25 @@ void or_relu_margin(const or_grid *g, const or_mlp *m, const or_rays *rays, cons
     free(recs);
 }
 
+/* The rays of a ray set (Sec. II-B Indexing; pinhole of Eq. 1 / Eq. 3): origin and unit
+ * direction of every ray, both the FP32 rays that take the integer decisions and the FP64 rays
+ * that carry the values.  o32, d32, o64, d64: [n_rays][3]; any of them may be NULL. */
+void or_rays_of(const or_rays *rays, float *o32, float *d32, double *o64, double *d64) {
+    const int R = n_rays_of(rays);
+    for (int k = 0; k < R; k++) {
+        float of[3], df[3];
+        double od[3], dd[3];
+        ray_f32(rays, k, of, df);
+        ray_f64(rays, k, od, dd);
+        for (int a = 0; a < 3; a++) {
+            if (o32) o32[3 * k + a] = of[a];
+            if (d32) d32[3 * k + a] = df[a];
+            if (o64) o64[3 * k + a] = od[a];
+            if (d64) d64[3 * k + a] = dd[a];
+        }
+    }
+}
+
 /* Features of the hash encoding at n world positions p [n][3] -> feat [n][levels * feat]. */
 void or_hash_features(const or_grid *g, const double *p, int n, double *feat) {
     for (int i = 0; i < n; i++) hash_features(g, p + 3 * i, feat + (size_t)i * g->C);

@@ -41,6 +41,86 @@ def _softplus(x):
 
 
 # ---------------------------------------------------------------------------------------------
+# camera rays (Sec. II-B Indexing: one ray per pixel; the pinhole of Eq. 1 and Eq. 3)
+
+
+def _rotation(seed):
+    """A seeded proper rotation (QR of a Gaussian matrix), rounded to FP32 like every pose."""
+    rng = np.random.default_rng(seed)
+    q, r = np.linalg.qr(rng.standard_normal((3, 3)))
+    q = q * np.sign(np.diag(r))
+    if np.linalg.det(q) < 0:
+        q[:, 0] = -q[:, 0]
+    return q.astype(np.float32)
+
+
+def _posed_camera(W, H, f, cx, cy, seed):
+    c2w = np.concatenate([_rotation(seed), np.array([[0.3], [-1.2], [0.7]], np.float32)], axis=1)
+    f32 = lambda v: float(np.float32(v))  # intrinsics are FP32 in every camera descriptor
+    return scenes.Camera(W, H, f32(f), f32(cx), f32(cy), c2w)
+
+
+@pytest.mark.parametrize("W,H", [(5, 3), (9, 15), (801, 799)])
+def test_centre_pixel_looks_along_the_optical_axis(orc, W, H):
+    """With the principal point at the image centre and odd sizes, the centre pixel's ray is the
+    camera's z axis: column 2 of the rotation of c2w; every ray starts at column 3."""
+    cam = _posed_camera(W, H, 0.9 * W, W / 2.0, H / 2.0, seed=W)
+    p = (H // 2) * W + W // 2
+    r = orc.camera_rays(cam, pix=np.array([p, 0], np.int32))
+    R = cam.c2w.astype(np.float64)
+    axis = R[:, 2] / np.linalg.norm(R[:, 2])
+    np.testing.assert_allclose(r["d64"][0], axis, atol=1e-15)
+    np.testing.assert_allclose(r["d32"][0], axis, atol=1e-7)
+    np.testing.assert_array_equal(r["o64"], np.tile(R[:, 3], (2, 1)))
+    assert not np.allclose(r["d64"][1], axis, atol=1e-3)  # a corner pixel looks elsewhere
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_rays_project_back_to_their_pixel_centres(orc, seed):
+    """Eq. 3 inverts the ray generation: a point on the ray of pixel p = j W + i, taken to camera
+    space by the inverse of c2w and projected with u = f X / Z + cx, v = f Y / Z + cy, lands on
+    the pixel centre (i + 1/2, j + 1/2).  Non-square, off-centre intrinsics and a general
+    rotation, so a transposed rotation, swapped pixel axes or a missing half-pixel fail."""
+    W, H = 7, 4
+    cam = _posed_camera(W, H, 5.3 + seed, 2.9 - 0.4 * seed, 1.7 + 0.3 * seed, seed=10 + seed)
+    r = orc.camera_rays(cam)
+    M = cam.c2w.astype(np.float64)
+    for rays_o, rays_d, tol in ((r["o64"], r["d64"], 1e-11), (r["o32"], r["d32"], 2e-5)):
+        np.testing.assert_allclose(np.linalg.norm(rays_d, axis=1), 1.0, atol=1e-7)
+        P = rays_o.astype(np.float64) + 2.7 * rays_d.astype(np.float64)
+        Xc = np.linalg.solve(M[:, :3], (P - M[:, 3]).T).T
+        assert (Xc[:, 2] > 0).all()
+        u = cam.f * Xc[:, 0] / Xc[:, 2] + cam.cx
+        v = cam.f * Xc[:, 1] / Xc[:, 2] + cam.cy
+        i, j = np.arange(W * H) % W, np.arange(W * H) // W
+        np.testing.assert_allclose(u, i + 0.5, atol=tol)
+        np.testing.assert_allclose(v, j + 0.5, atol=tol)
+
+
+def test_camera_axes_are_opencv(orc):
+    """Identity pose: x to the right, y down, z forward; pixel lists select pixels p = j W + i."""
+    W, H = 6, 4
+    c2w = np.concatenate([np.eye(3), np.zeros((3, 1))], axis=1).astype(np.float32)
+    cam = scenes.Camera(W, H, 3.0, W / 2.0, H / 2.0, c2w)
+    d = orc.camera_rays(cam)["d64"]
+    i, j = np.arange(W * H) % W, np.arange(W * H) // W
+    assert (np.sign(d[:, 0]) == np.sign(i + 0.5 - W / 2.0)).all()
+    assert (np.sign(d[:, 1]) == np.sign(j + 0.5 - H / 2.0)).all()
+    assert (d[:, 2] > 0).all()
+    pick = np.array([13, 2, 23], np.int32)
+    np.testing.assert_array_equal(orc.camera_rays(cam, pix=pick)["d64"], d[pick])
+
+
+def test_orbit_camera_centre_ray_meets_the_look_at_point(orc):
+    """The benchmark's orbit camera looks at the origin: the centre ray of an odd-sized image
+    passes through it at distance |o|."""
+    cam = scenes.orbit_camera(801, 801)
+    r = orc.camera_rays(cam, pix=np.array([400 * 801 + 400], np.int32))
+    o, d = r["o64"][0], r["d64"][0]
+    np.testing.assert_allclose(o + np.linalg.norm(o) * d, 0.0, atol=1e-6)
+
+
+# ---------------------------------------------------------------------------------------------
 # accumulation (Sec. II-B) against the closed form of a homogeneous medium
 
 
