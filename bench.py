@@ -559,12 +559,11 @@ def window_sweep(cc, torch, dev, grid, mlp, o16):
         hole_records = N * R * 40  # ~16% of the window's slots
         ws = cc.workspace(cc.cicero_pipeline_workspace_size(grid.desc, cd, sd, o16, N, hole_records), dev)
         p = cc.Pipeline(grid.desc, mlp.desc, cd, sd, o16, N, hole_records, 180.0, ws)
-        refs = cc.reference_poses(targets, N, lead)
 
         def run(overlap):
             cur = torch.cuda.current_stream(dev)
             s_ref.wait_stream(cur)
-            p.run(targets, refs, frames, None, stream_tgt=cur, stream_ref=s_ref if overlap else cur)
+            p.run(targets, frames, None, lead=lead, stream_tgt=cur, stream_ref=s_ref if overlap else cur)
 
         t_ov = event_ms(torch, lambda: run(True), 2)
         t_se = event_ms(torch, lambda: run(False), 2)

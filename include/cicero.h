@@ -49,7 +49,7 @@ typedef enum { CICERO_F32 = 0, CICERO_F16 = 1 } cicero_dtype;
  * activations rounded to BF16) and FP32 accumulation in tensor memory. */
 typedef enum { CICERO_MLP_FP32 = 0, CICERO_MLP_BF16 = 1 } cicero_precision;
 
-/* Dense voxel grid (Sec. II-B: "each vertex carries a high-dimensional feature vector").
+/* Dense voxel grid (Sec. II-B: a feature vector is stored at every vertex of the grid).
  * Vertices sit on the corners of the box [aabb_min, aabb_max]; n[a] vertices along axis a.
  *   density  [n2][n1][n0]       raw density, sigma = softplus(raw + act_shift)
  *   features [n2][n1][n0][C]    feature vectors
@@ -69,7 +69,7 @@ typedef struct {
     int occ_res;
 } cicero_grid;
 
-/* Feature Computation MLP (Sec. II-B: "a lightweight MLP"), FP32 weights, row-major [out][in]:
+/* Feature Computation MLP (Sec. II-B, a small MLP of unstated shape), FP32 weights, row-major [out][in]:
  *   x  = [features (C), d (3), sin(2^k d), cos(2^k d) for k = 0..n_freq-1 (6 n_freq)]
  *   h1 = relu(w1 x + b1)  (hidden), h2 = relu(w2 h1 + b2)  (hidden), c = sigmoid(w3 h2 + b3)  (3)
  * where d is the unit ray direction and each sin/cos block is (x, y, z) of sin then of cos.
@@ -275,22 +275,41 @@ cicero_status cicero_extrapolate_pose(const cicero_camera *prev, const cicero_ca
                                       cicero_camera *out);
 
 /* ---------------------------------------------------------------------------------------------
+ * Reference poses of a trajectory (Sec. III-C, Eq. 5-6), for the overlapped pipeline below.
+ * Frames are taken in windows of `window` targets; window w is warped from reference w.
+ * Reference 0 is frame 0.  Reference w >= 1 is rendered while window w - 1 runs, so it can only
+ * use the poses known when window w - 1 starts: it is extrapolated (cicero_extrapolate_pose) from
+ * frames s - 1 and s, where s = max(1, (w - 1) window) is the first frame of window w - 1 (frame 1
+ * for the first window, which needs two poses), with
+ *   CICERO_LEAD_CENTRED: lead = w window + window / 2 - s, which carries the pose to the centre
+ *                        of the window the reference serves (the paper's intent: the reference
+ *                        sits in the middle of its targets);
+ *   CICERO_LEAD_PAPER:   lead = window / 2, Eq. 6 read literally (t_r = N/2 frame intervals
+ *                        after the latest pose).
+ * targets [n_frames] and refs [ceil(n_frames / window)] are host arrays; every reference has the
+ * intrinsics of its latest pose.  Host only, allocates nothing. */
+typedef enum { CICERO_LEAD_CENTRED = 0, CICERO_LEAD_PAPER = 1 } cicero_lead;
+
+cicero_status cicero_reference_poses(const cicero_camera *targets, int n_frames, int window, cicero_lead lead,
+                                     cicero_camera *refs);
+
+/* ---------------------------------------------------------------------------------------------
  * SpaRW over a trajectory with reference rendering overlapped (Sec. III-C, "Reference Frame
  * Rendering"): frames are taken in windows of `window` targets; window w is warped from
- * reference frame refs[w] (cicero_warp_batch) and its holes rendered (cicero_render_holes_batch),
- * while reference w + 1 is rendered on `stream_ref`.  Void holes are not tested separately: their
- * march in the hole render finds no occupied slot and writes the background with depth +inf,
- * the same frames as with the void depth test of cicero_warp_batch.  With
- * stream_ref == stream_tgt the same work runs serialised (same results).  Reference poses are the
- * caller's (for example from cicero_extrapolate_pose); every frame, reference or target, has the
- * size and intrinsics of `cam`.
+ * reference frame w (cicero_warp_batch) and its holes rendered (cicero_render_holes_batch),
+ * while reference w + 1 is rendered on `stream_ref`.  The reference poses are derived from the
+ * trajectory by cicero_reference_poses with the given lead.  Void holes are not tested
+ * separately: their march in the hole render finds no occupied slot and writes the background
+ * with depth +inf, the same frames as with the void depth test of cicero_warp_batch.  With
+ * stream_ref == stream_tgt the same work runs serialised (same results).  Every frame, reference
+ * or target, has the size and intrinsics of `cam`.
  *
  * The workspace holds two reference frames and their render workspaces (opt applies to them),
  * scratch for one window's hole masks and lists, and the hole-batch workspace of `hole_records`
  * records (opt's max_records for the hole batch).  The handle is host memory owned by the
  * caller; one run at a time per pipeline (the previous run's work is waited for on the streams,
- * not on the host).  targets [n_frames] and refs [ceil(n_frames / window)] are host arrays;
- * rgb / depth are host arrays of n_frames device pointers ([H*W][3] / [H*W]; depth may be NULL).
+ * not on the host).  targets [n_frames] is a host array; rgb / depth are host arrays of n_frames
+ * device pointers ([H*W][3] / [H*W]; depth may be NULL).
  * cicero_pipeline_status reads the error bits of the kernels (synchronises `stream`). */
 typedef struct cicero_pipeline cicero_pipeline;
 
@@ -302,7 +321,7 @@ cicero_status cicero_pipeline_create(const cicero_grid *grid, const cicero_mlp *
                                      long long hole_records, float max_angle_deg, void *workspace, size_t ws_bytes,
                                      cicero_pipeline **out);
 cicero_status cicero_pipeline_run(cicero_pipeline *pipeline, const cicero_camera *targets, int n_frames,
-                                  const cicero_camera *refs, float *const *rgb, float *const *depth,
+                                  cicero_lead lead, float *const *rgb, float *const *depth,
                                   void *stream_tgt, void *stream_ref);
 cicero_status cicero_pipeline_status(const cicero_pipeline *pipeline, void *stream);
 cicero_status cicero_pipeline_destroy(cicero_pipeline *pipeline);
@@ -352,16 +371,19 @@ cicero_status cicero_warp_batch(const float *ref_rgb, const float *ref_depth, co
 
 size_t cicero_warp_batch_workspace_size(const cicero_camera *tgt_cams, int n_views);
 
-/* cicero_warp without a workspace, for callers that cannot allocate device memory (for example
- * code that runs while a stream is captured into a CUDA graph, where cudaMalloc is not allowed,
- * or real-time loops that must not enter an allocator).  The paper has no counterpart: this is a
- * packaging variant of the warp above, with the same arguments and outputs minus the workspace.
+/* cicero_warp without a workspace, for callers that cannot allocate device memory: real-time
+ * loops that must not enter an allocator, host programs that link this library without a device
+ * allocator of their own, plugins whose host framework owns all device memory.  The paper has no
+ * counterpart: this is a packaging variant of the warp above, with the same arguments and outputs
+ * minus the workspace.
  *   - Scratch (the depth buffer and scan sums, ~8 MiB) is a static array in the library's device
  *     image, present on every device that loads the library until the process exits.  The target
  *     image may have at most 1048576 pixels (width * height); larger targets return
  *     CICERO_ERR_UNSUPPORTED.  The call allocates and frees nothing.
  *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
- *     that device current; make that first call before any stream capture.
+ *     that device current, and caches it for the life of the process; make that first call before
+ *     any stream capture.  After cudaDeviceReset on a device the cached address is stale: do not
+ *     call this entry point on that device again.
  *   - Every call shares the one array: calls that may overlap on the GPU (different streams, or
  *     different host threads on one device) race and must be serialised by the caller.  The call
  *     clears what must start empty (the depth buffer) itself. */

@@ -359,6 +359,23 @@ def extrapolate_pose(c2w_prev, c2w_cur, lead: float) -> np.ndarray:
     return np.concatenate([Rl @ Cm[:, :3], pos[:, None]], axis=1)
 
 
+def reference_schedule(n_frames: int, window: int, lead: str = "centred"):
+    """Which poses each reference frame of a trajectory is extrapolated from (Sec. III-C,
+    Eq. 5-6), for the overlapped pipeline: frames come in windows of ``window`` targets and window
+    w is warped from reference w.  Reference 0 is frame 0 itself (``None``).  Reference w >= 1 is
+    rendered while window w - 1 runs, so it uses the two latest poses known when window w - 1
+    starts: frames s - 1 and s with s the first frame of window w - 1 (at least 1, since two poses
+    are needed).  Its lead, in frame intervals after frame s: "centred" carries it to the centre of
+    the window it serves, frame w * window + window / 2; "paper" is Eq. 6 read literally,
+    t_r = N / 2 with N = window.  Returns one (prev, cur, lead) triple per window."""
+    out = [None]
+    for w in range(1, (n_frames + window - 1) // window):
+        s = max(1, (w - 1) * window)
+        centre = w * window + window / 2.0
+        out.append((s - 1, s, centre - s if lead == "centred" else window / 2.0))
+    return out
+
+
 def upsample_bilinear(img, W: int, H: int) -> np.ndarray:
     """Bilinear resampling of img [h, w, C] to [H, W, C] in FP64 (the DS-2 comparator: the frame is
     rendered at half resolution, then upsampled by bilinear interpolation).  Reading: pixel

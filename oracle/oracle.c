@@ -153,7 +153,7 @@ static void ray_f64(const or_rays *r, int k, double o[3], double d[3]) {
 }
 
 /* ------------------------------------------------------------------------------------------
- * Sample placement (Sec. II-B: "each ray samples a set of points along its direction").
+ * Sample placement (Sec. II-B: every ray takes a set of point samples along its direction).
  * step == 0: slot k sits at near + (k + 1/2) * (far - near) / S (midpoint rule), S slots.
  * step  > 0: the slab test gives the entry t_in and exit t_out of the box; slot k sits at
  *            t_in + (k + 1/2) * step while k < S and the slot is before t_out.
@@ -305,7 +305,7 @@ static double softplus(double x) { return x > 30.0 ? x + log1p(exp(-x)) : log1p(
 static double sigm(double x) { return 1.0 / (1.0 + exp(-x)); }
 
 /* ------------------------------------------------------------------------------------------
- * Feature Computation (Sec. II-B): the "lightweight MLP".  Input x = [features (C), d (3),
+ * Feature Computation (Sec. II-B, a small MLP whose shape the paper does not give).  Input x = [features (C), d (3),
  * then for k = 0..n_freq-1: sin(2^k d_x), sin(2^k d_y), sin(2^k d_z), cos(2^k d_x),
  * cos(2^k d_y), cos(2^k d_z)]; h1 = relu(W1 x + b1); h2 = relu(W2 h1 + b2);
  * c = sigmoid(W3 h2 + b3). */
@@ -344,8 +344,8 @@ static void mlp_fwd(const or_mlp *m, const double *x, mlp_state *st) {
 }
 
 /* ------------------------------------------------------------------------------------------
- * One ray, front to back (accumulation, Sec. II-B "accumulating all ray samples along the ray
- * direction", with the standard emission-absorption quadrature):
+ * One ray, front to back (accumulation, Sec. II-B: the samples of a ray are summed along it,
+ * here with the standard emission-absorption quadrature):
  *   sigma_k = softplus(trilinear(density) + shift),  alpha_k = 1 - exp(-sigma_k * delta),
  *   T_0 = 1; before slot k: stop if T_k < t_stop; w_k = T_k alpha_k; T_{k+1} = T_k (1 - alpha_k)
  *   rgb = sum w_k c_k + T_end bg,  acc = sum w_k,  depth = sum w_k t_k / acc  (+inf if acc < void_acc)
@@ -567,12 +567,12 @@ void or_encode(const or_mlp *m, int C, const double *feat, const double *d, int 
  * D = +inf (void) is a point at infinity: its direction is rotated and projected and it keeps
  * depth +inf.  Depth test: the smallest key (float bits of Z' << 32 | q) wins, i.e. the nearest
  * point, ties to the lower reference index.  With phi < 180 deg a point is kept only when the
- * angle between its reference ray and its target ray (theta, Fig. "intuition") is below phi;
+ * angle between its reference ray and its target ray (theta in the paper's figure on the warping intuition) is below phi;
  * points at infinity have theta = 0.
  * Target pixels: a winner copies its reference colour (mask 0).  A pixel with no winner is a
  * hole; with a void grid given, a hole whose ray has no sample inside the box (and in an
  * occupied cell) is void (mask 2: background colour, depth +inf, skipped - the paper's depth
- * test for "pixels whose depth is infinite"); the rest (mask 1) are listed in ascending pixel
+ * test: pixels at infinite depth are not rendered); the rest (mask 1) are listed in ascending pixel
  * order for sparse rendering (Eq. 4).  warped_depth (may be NULL) is |P'| for warped pixels. */
 
 typedef struct { int width, height; float f, cx, cy; float c2w[12]; } or_cam;

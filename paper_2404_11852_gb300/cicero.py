@@ -94,7 +94,8 @@ _SIGS = {
     "cicero_upsample_bilinear": ([_P, C.c_int, C.c_int, C.c_int, _P, C.c_int, C.c_int, _P], C.c_int),
     "cicero_pipeline_workspace_size": ([_P, _P, _P, _P, C.c_int, C.c_longlong], _Z),
     "cicero_pipeline_create": ([_P] * 5 + [C.c_int, C.c_longlong, C.c_float, _P, _Z, _P], C.c_int),
-    "cicero_pipeline_run": ([_P, _P, C.c_int, _P, _P, _P, _P, _P], C.c_int),
+    "cicero_pipeline_run": ([_P, _P, C.c_int, C.c_int, _P, _P, _P, _P], C.c_int),
+    "cicero_reference_poses": ([_P, C.c_int, C.c_int, C.c_int, _P], C.c_int),
     "cicero_pipeline_status": ([_P, _P], C.c_int),
     "cicero_pipeline_destroy": ([_P], C.c_int),
     "cicero_profile_begin": ([], C.c_int),
@@ -488,13 +489,12 @@ class Pipeline:
                                             int(window), int(hole_records), float(max_angle_deg), p, n, C.byref(h)))
         self.handle, self.ws, self.window = h, ws, window
 
-    def run(self, targets, refs, rgb, depth=None, stream_tgt=None, stream_ref=None):
-        """targets / refs: lists of Camera; rgb / depth: lists of device tensors (one per target)."""
+    def run(self, targets, rgb, depth=None, lead: str = "centred", stream_tgt=None, stream_ref=None):
+        """targets: list of Camera; rgb / depth: lists of device tensors (one per target)."""
         tg = (Camera * len(targets))(*targets)
-        rf = (Camera * len(refs))(*refs)
         pr = (C.c_void_p * len(rgb))(*[_ptr(t).value for t in rgb])
         pd = (C.c_void_p * len(depth))(*[_ptr(t).value for t in depth]) if depth is not None else None
-        _check(lib().cicero_pipeline_run(self.handle, tg, len(targets), rf, pr, pd, _stream(stream_tgt),
+        _check(lib().cicero_pipeline_run(self.handle, tg, len(targets), _LEADS[lead], pr, pd, _stream(stream_tgt),
                                          _stream(stream_ref)))
 
     def status(self, stream=None):
@@ -512,19 +512,18 @@ class Pipeline:
             pass
 
 
-def reference_poses(targets, window: int, lead: str = "centred"):
-    """Reference cameras of a trajectory for Pipeline.run (Sec. III-C, Eq. 5-6), causal for the
-    overlapped schedule: reference w is rendered while window w - 1 runs, so it is extrapolated
-    from the two poses known at the first frame s of window w - 1.  lead="centred" carries it to
-    frame w * window + window / 2 (the paper's centre of the window it serves); lead="paper"
-    applies Eq. 6 literally (window / 2 frame intervals from frame s).  Reference 0 is frame 0."""
-    refs = [targets[0]]
+LEAD_CENTRED, LEAD_PAPER = 0, 1
+_LEADS = {"centred": LEAD_CENTRED, "paper": LEAD_PAPER}
+
+
+def cicero_reference_poses(targets, window: int, lead: str = "centred"):
+    """Reference cameras the pipeline derives from a trajectory (list of Camera); lead is
+    "centred" or "paper"."""
+    tg = (Camera * len(targets))(*targets)
     n_win = (len(targets) + window - 1) // window
-    for w in range(1, n_win):
-        s = max(1, (w - 1) * window)
-        frames = (w * window + window / 2.0 - s) if lead == "centred" else window / 2.0
-        refs.append(cicero_extrapolate_pose(targets[s - 1], targets[s], frames))
-    return refs
+    out = (Camera * n_win)()
+    _check(lib().cicero_reference_poses(tg, len(targets), int(window), _LEADS[lead], out))
+    return list(out)
 
 
 def cicero_upsample_bilinear(src, w: int, h: int, dst, W: int, H: int, stream=None):

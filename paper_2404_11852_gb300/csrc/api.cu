@@ -382,7 +382,8 @@ static cicero_status warp_common(const float* ref_rgb, const float* ref_depth, c
     vt.src.kind = 0;
     vt.src.n_views = n_views;
   } else if (void_sampling) {
-    make_samp(void_sampling, &vt.s);
+    st = make_samp(void_sampling, &vt.s);  // unused without a grid, but validated like everywhere else
+    if (st != CICERO_OK) return st;
   }
   return run_warp(B, vt, ref_rgb, ref_depth, (cudaStream_t)stream);
 }

@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <new>
+#include <vector>
 
 #include "../../include/cicero.h"
 #include "internal.h"
@@ -158,6 +159,23 @@ cicero_status cicero_extrapolate_pose(const cicero_camera* prev, const cicero_ca
   return CICERO_OK;
 }
 
+cicero_status cicero_reference_poses(const cicero_camera* targets, int n_frames, int window, cicero_lead lead,
+                                     cicero_camera* refs) {
+  if (!targets || !refs) return fail(CICERO_ERR_INVALID_ARG, "targets/refs is NULL");
+  if (n_frames < 1 || window < 1) return fail(CICERO_ERR_INVALID_ARG, "n_frames and window must be >= 1");
+  if (lead != CICERO_LEAD_CENTRED && lead != CICERO_LEAD_PAPER) return fail(CICERO_ERR_INVALID_ARG, "unknown lead");
+  const int n_win = (n_frames + window - 1) / window;
+  refs[0] = targets[0];
+  for (int w = 1; w < n_win; w++) {
+    // the first frame of window w - 1 (frame 1 for the first window: two poses are needed)
+    const int s = (w - 1) * window > 1 ? (w - 1) * window : 1;
+    const double frames = lead == CICERO_LEAD_CENTRED ? (double)w * window + window / 2.0 - s : window / 2.0;
+    const cicero_status st = cicero_extrapolate_pose(&targets[s - 1], &targets[s], (float)frames, &refs[w]);
+    if (st != CICERO_OK) return st;
+  }
+  return CICERO_OK;
+}
+
 size_t cicero_pipeline_workspace_size(const cicero_grid* grid, const cicero_camera* cam,
                                       const cicero_sampling* sampling, const cicero_options* opt, int window,
                                       long long hole_records) {
@@ -202,12 +220,20 @@ cicero_status cicero_pipeline_create(const cicero_grid* grid, const cicero_mlp* 
   return CICERO_OK;
 }
 
-cicero_status cicero_pipeline_run(cicero_pipeline* p, const cicero_camera* targets, int n_frames,
-                                  const cicero_camera* refs, float* const* rgb, float* const* depth, void* stream_tgt,
-                                  void* stream_ref) {
-  if (!p || !targets || !refs || !rgb) return fail(CICERO_ERR_INVALID_ARG, "a pipeline argument is NULL");
+cicero_status cicero_pipeline_run(cicero_pipeline* p, const cicero_camera* targets, int n_frames, cicero_lead lead,
+                                  float* const* rgb, float* const* depth, void* stream_tgt, void* stream_ref) {
+  if (!p || !targets || !rgb) return fail(CICERO_ERR_INVALID_ARG, "a pipeline argument is NULL");
   if (n_frames < 1) return fail(CICERO_ERR_INVALID_ARG, "n_frames must be >= 1");
   const int N = p->window, n_win = (n_frames + N - 1) / N;
+  std::vector<cicero_camera> ref_poses;
+  try {
+    ref_poses.resize((size_t)n_win);
+  } catch (...) {
+    return fail(CICERO_ERR_INTERNAL, "out of host memory");
+  }
+  const cicero_camera* refs = ref_poses.data();
+  if (cicero_status s0 = cicero_reference_poses(targets, n_frames, N, lead, ref_poses.data()); s0 != CICERO_OK)
+    return s0;
   for (int i = 0; i < n_frames; i++)
     if (targets[i].width != p->cam.width || targets[i].height != p->cam.height || !rgb[i])
       return fail(CICERO_ERR_INVALID_ARG, "every target frame must have the pipeline's size and an rgb buffer");

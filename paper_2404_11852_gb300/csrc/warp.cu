@@ -10,6 +10,8 @@
 // All decision arithmetic uses explicit round-to-nearest intrinsics (no FMA contraction).
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include <algorithm>
 
 #include "common.cuh"
@@ -398,11 +400,11 @@ cicero_status run_warp(const WarpBatch& B, const VoidTest& vt, const float* ref_
 }
 
 // -------------------------------------------------------------------------------------------
-// Allocation-free warp.  Some callers cannot allocate device memory: code running while a stream
-// is being captured into a CUDA graph (cudaMalloc is not allowed there), real-time loops that must
-// not enter the allocator, or host programs linking this library without a device allocator of
-// their own.  For them cicero_warp_noalloc uses a scratch array that is part of the library's
-// device image instead of a caller-provided workspace.
+// Allocation-free warp.  Some callers cannot allocate device memory: real-time loops that must
+// not enter an allocator (an allocation can block for an unbounded time), host programs that link
+// this library without any device allocator of their own, and plugins whose host framework owns
+// every byte of device memory.  For them cicero_warp_noalloc uses a scratch array that is part of
+// the library's device image instead of a caller-provided workspace.
 
 namespace {
 
@@ -416,7 +418,11 @@ constexpr size_t kNoAllocBytes = 256 + ((8 * (size_t)kNoAllocMaxPixels + 255) & 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 constexpr int kMaxDevices = 64;
-void* g_noalloc_ptr[kMaxDevices] = {nullptr};
+// Per-device address of the scratch array, looked up on the first call on that device.  Atomic
+// entries: host threads driving different devices may make their first calls at the same time
+// (two threads on one device both look it up and store the same address).  The cache lives as
+// long as the process; after cudaDeviceReset on a device its entry is stale.
+std::atomic<void*> g_noalloc_ptr[kMaxDevices];
 
 // Device address of the scratch array on the current device (looked up once per device).
 cicero_status noalloc_scratch(void** out) {
@@ -424,13 +430,13 @@ cicero_status noalloc_scratch(void** out) {
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
   if (dev < 0 || dev >= kMaxDevices) return fail(CICERO_ERR_UNSUPPORTED, "device index out of range");
-  if (!g_noalloc_ptr[dev]) {
-    void* p = nullptr;
+  void* p = g_noalloc_ptr[dev].load(std::memory_order_relaxed);
+  if (!p) {
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(scratch)");
-    g_noalloc_ptr[dev] = p;
+    g_noalloc_ptr[dev].store(p, std::memory_order_relaxed);
   }
-  *out = g_noalloc_ptr[dev];
+  *out = p;
   return CICERO_OK;
 }
 

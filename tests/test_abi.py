@@ -155,3 +155,25 @@ def test_extrapolate_pose_matches_oracle(cc):
             assert (got.width, got.height, got.f) == (b.width, b.height, np.float32(b.f))
     with pytest.raises(cc.CiceroError):
         cc.cicero_extrapolate_pose(cc.camera_from(cam), cc.camera_from(cam), float("nan"))
+
+
+@pytest.mark.parametrize("lead", ["centred", "paper"])
+@pytest.mark.parametrize("window,n_frames", [(4, 10), (3, 3), (16, 120), (6, 1)])
+def test_reference_poses_follow_the_oracle_schedule(cc, orc, lead, window, n_frames):
+    """cicero_reference_poses (host code of the library) against the oracle's schedule and FP64
+    extrapolation.  The FP32 poses are orthonormal to ~1e-7 only, and the two sides take the
+    rotation between them differently (the library by quaternion, the oracle by the trace and the
+    skew part, whose angle is ill-conditioned for the small per-frame rotations), so the angle
+    differs by a few 1e-7 rad and that difference is carried `lead` times: the tolerance grows with
+    the lead (1e-5 rad at a lead of 24 frames is 0.01 pixel at f = 1100)."""
+    import scenes
+    cam = scenes.orbit_camera(64, 48)
+    traj = [scenes.offset_camera(cam, k, yaw_deg=1.5, shift=0.01) for k in range(n_frames)]
+    refs = cc.cicero_reference_poses([cc.camera_from(t) for t in traj], window, lead)
+    sched = orc.reference_schedule(n_frames, window, lead)
+    assert len(refs) == len(sched)
+    for r, e in zip(refs, sched):
+        got = np.array(r.c2w[:], np.float64).reshape(3, 4)
+        want = traj[0].c2w.astype(np.float64) if e is None else orc.extrapolate_pose(traj[e[0]].c2w, traj[e[1]].c2w, e[2])
+        np.testing.assert_allclose(got, want, atol=1e-6 + 5e-7 * (0.0 if e is None else e[2]))
+        assert (r.width, r.height, r.f, r.cx, r.cy) == (cam.width, cam.height, np.float32(cam.f), cam.cx, cam.cy)

@@ -123,22 +123,22 @@ def test_render_holes(cc, orc, ref_frame, precision, tol):
 
 
 def test_sparw_chain_against_oracle_chain(cc, orc):
-    """Reference render -> warp -> hole render on the GPU (BF16) vs the same chain in the
-    oracle: the two chains agree to within the BF16 tolerance band (reported PSNR)."""
-    import torch
+    """Reference render -> warp -> hole render on the GPU (BF16 MLP) against the oracle running the
+    same chain fed the GPU's reference frame, so that both sides warp the same points.  The GPU
+    reference is within the BF16 tolerance of the oracle's; the hole mask, the hole list and the
+    warped pixels are bit-exact; the rendered holes, and so the whole target frame, are within the
+    BF16 tolerance (max |rgb err| <= 2e-2, PSNR >= 45 dB) of the oracle's chain."""
+    from helpers import gpu_render, rgb_errors
+    tol, psnr_min = 2e-2, 45.0
     g, m = scenes.scene_small(), scenes.make_mlp(12)
     cam = scenes.orbit_camera(96, 96, sampling=scenes.sampling_uniform(64))
-    from helpers import gpu_render
     gref = gpu_render(cc, g, m, cam, cam.sampling, 1, 8)
-    oref = orc.render(g, m, cam.sampling, cam=cam)
+    check_render(gref, orc.render(g, m, cam.sampling, cam=cam), tol, psnr_min=psnr_min)
+    rr, rd = gref["rgb"].astype(np.float32), gref["depth"].astype(np.float32)  # exact: GPU FP32 values
     tgt = scenes.offset_camera(cam, 4)
-    o_w = orc.warp(oref["rgb"].astype(np.float32), oref["depth"].astype(np.float32), cam, tgt, void_grid=g,
-                   void_sampling=cam.sampling)
-    o_rgb = o_w["rgb"].astype(np.float64)
-    if o_w["n_holes"]:
-        o_rgb[o_w["hole_idx"]] = orc.render(g, m, cam.sampling, cam=tgt, pix=o_w["hole_idx"])["rgb"]
-    got = gpu_warp(cc, gref["rgb"].astype(np.float32), gref["depth"].astype(np.float32), cam, tgt, void_grid=g,
-                   void_sp=cam.sampling)
+    want = orc.warp(rr, rd, cam, tgt, void_grid=g, void_sampling=cam.sampling)
+    got = gpu_warp(cc, rr, rd, cam, tgt, void_grid=g, void_sp=cam.sampling)
+    assert_warp_equal(got, want)
     wr, wd, hidx, nh = got["_dev"]
     gd, md = cc.DeviceGrid.from_host(g), cc.DeviceMlp.from_host(m)
     NT = tgt.width * tgt.height
@@ -146,11 +146,24 @@ def test_sparw_chain_against_oracle_chain(cc, orc):
     ws = cc.workspace(cc.cicero_render_workspace_size(gd.desc, NT, sd, opt))
     cc.cicero_render_holes(gd.desc, md.desc, cd, sd, opt, hidx, nh, NT, wr, wd, ws)
     cc.cicero_workspace_status(ws)
-    p = psnr(wr.cpu().double().numpy(), o_rgb)
+    out_rgb, out_d = wr.cpu().double().numpy(), wd.cpu().double().numpy()
+    holes = want["hole_idx"]
+    assert len(holes) > 0
+    keep = np.ones(NT, bool)
+    keep[holes] = False
+    np.testing.assert_array_equal(out_rgb[keep], want["rgb"][keep].astype(np.float64))
+    ref = orc.render(g, m, cam.sampling, cam=tgt, pix=holes)
+    check_render({"rgb": out_rgb[holes], "depth": out_d[holes], "acc": ref["acc"]}, ref, tol, psnr_min=psnr_min)
+    # the whole target frame against the oracle's chain (warped pixels contribute no error)
+    err, _ = rgb_errors(out_rgb[holes], ref)
+    sq = np.where(err[:, None] == np.abs(out_rgb[holes] - ref["rgb"]).max(1, keepdims=True),
+                  (out_rgb[holes] - ref["rgb"]) ** 2, (out_rgb[holes] - ref["rgb_alt"]) ** 2)
+    frame_psnr = 10 * np.log10(1.0 / max(sq.sum() / (3 * NT), 1e-30))
     full = orc.render(g, m, cam.sampling, cam=tgt)["rgb"]
-    print(f"SpaRW chain GPU vs oracle chain: {p:.1f} dB; oracle SpaRW vs full render: {psnr(o_rgb, full):.1f} dB; "
-          f"holes {o_w['n_holes']} of {NT}")
-    assert p >= 40.0
+    print(f"SpaRW chain GPU vs oracle chain: max err {err.max():.2e}, {frame_psnr:.1f} dB; "
+          f"SpaRW frame vs the oracle's full render (approximation, not gated): {psnr(out_rgb, full):.1f} dB; "
+          f"holes {len(holes)} of {NT}")
+    assert err.max() <= tol and frame_psnr >= psnr_min
 
 
 @pytest.mark.parametrize("precision", [0, 1])

@@ -743,3 +743,39 @@ def test_extrapolate_paper_example_n4(orc):
     r = orc.extrapolate_pose(prev, cur, rows["N"][0] / 2)
     np.testing.assert_array_equal(r[:, 3], rows["R1"])  # dyadic values: exact in FP64
     np.testing.assert_array_equal(r[:, :3], np.eye(3))
+
+
+def test_reference_schedule_reproduces_the_paper_example(orc):
+    """The Eq. 6 example of Sec. III-C through the schedule: with Eq. 6 read literally and windows
+    of N = 4, the second reference is extrapolated from the first two frames (T1, T2) by N/2 = 2
+    intervals, which gives R1 of tests/golden/eq6_reference_pose_n4.txt."""
+    import os
+    rows = {}
+    with open(os.path.join(os.path.dirname(__file__), "golden", "eq6_reference_pose_n4.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                k, *v = line.split()
+                rows[k] = np.array([float(x) for x in v])
+    N = int(rows["N"][0])
+    sched = orc.reference_schedule(3 * N, N, lead="paper")
+    assert sched[0] is None and len(sched) == 3
+    prev, cur, lead = sched[1]
+    assert (prev, cur, lead) == (0, 1, N / 2)
+    poses = [np.concatenate([np.eye(3), rows[k][:, None]], 1) for k in ("T1", "T2")]
+    r = orc.extrapolate_pose(poses[prev], poses[cur], lead)
+    np.testing.assert_array_equal(r[:, 3], rows["R1"])
+
+
+def test_reference_schedule_centres_each_reference(orc):
+    """On a constant-velocity straight path the extrapolation is exact, so each reference lands on
+    the centre of the window it serves (centred lead), or N/2 frames after the latest known pose
+    (Eq. 6 literally), which is a window behind."""
+    N, n = 4, 14
+    pos = lambda t: np.array([0.1 * t, -0.05 * t, 0.02 * t])
+    poses = [np.concatenate([np.eye(3), pos(i)[:, None]], 1) for i in range(n)]
+    for lead, centre in (("centred", lambda w: w * N + N / 2.0), ("paper", lambda w: max(1, (w - 1) * N) + N / 2.0)):
+        for w, e in enumerate(orc.reference_schedule(n, N, lead)):
+            if e is None:
+                continue
+            r = orc.extrapolate_pose(poses[e[0]], poses[e[1]], e[2])
+            np.testing.assert_allclose(r[:, 3], pos(centre(w)), atol=1e-12)

@@ -1,8 +1,8 @@
 """The allocation-free warp entry point (cicero_warp_noalloc) against cicero_warp.
 
-cicero_warp_noalloc exists for callers that cannot allocate device memory (for example while a
-stream is being captured into a CUDA graph).  Its scratch is a fixed array inside the library, so
-this test checks, through the C ABI, that two calls in a row each give exactly what cicero_warp
+cicero_warp_noalloc exists for callers that cannot allocate device memory (real-time loops that
+must not enter an allocator, host programs without a device allocator of their own).  Its scratch
+is a fixed array inside the library, so this test checks, through the C ABI, that two calls in a row each give exactly what cicero_warp
 gives with a workspace (the warp is bit-exact, so the tolerance of the other warp tests is zero),
 and that a target larger than the built-in scratch is refused before any GPU work.
 """
