@@ -103,11 +103,11 @@ typedef struct {
 
 /* Options of the rendering calls (NULL = defaults: FP32 MLP, bricks of 8^3 voxels, full capacity).
  * max_records caps the per-sample records the workspace holds (0 = n_rays * n_samples, which can
- * never overflow; 52 bytes per record).  With a capacity below n_rays * n_samples, a ray that can
- * composite at most 256 samples reserves exactly the samples it composites (it stages them on chip
- * first); with the full capacity, and for every ray of cicero_render_backward and cicero_build_rit,
- * rays reserve an upper bound of their samples (their slots within two slots of the grid box).  If the reservations exceed max_records the rays that do not
- * fit composite nothing and cicero_workspace_status returns CICERO_ERR_WORKSPACE_TOO_SMALL. */
+ * never overflow; 52 bytes per record).  Each ray reserves records for its active slots, the slots
+ * inside the grid box and in an occupied cell, found exactly before its march (for slots past the
+ * 256th, every slot before the box exit); the samples it composites are a subset of those (early
+ * stop ends the rest).  If the reservations exceed max_records the rays that do not fit composite
+ * nothing and cicero_workspace_status returns CICERO_ERR_WORKSPACE_TOO_SMALL. */
 typedef struct {
     cicero_precision precision;
     int brick;          /* voxels per brick edge ("MVoxel", Sec. IV-A): 4, 8 or 16; 0 = 8 */

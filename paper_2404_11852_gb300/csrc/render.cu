@@ -95,31 +95,189 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
-// Upper bound of the samples a ray can composite: its slots within two slots of the box span
-// (the slab test in FP32; the inside test that decides may differ from it only by rounding).
-__device__ __forceinline__ int record_bound(const GridGeo& g, const Slots& sl, const float o[3], const float d[3]) {
-  if (sl.n <= 0) return 0;
-  if (sl.march) {
-    // box-march slots run from the box entry t0 while t_k < tout: fewer than (tout - t0) / dt + 1 of
-    // them (two slots of margin cover the fast division)
-    const float span = __fdividef(sl.tout - sl.t0, sl.dt) + 2.0f;
-    return span >= (float)sl.n ? sl.n : max(0, (int)span);
+// -------------------------------------------------------------------------------------------
+// Exact active-slot masks.  Along one axis, a slot's position p = o + t_k d, its vertex coordinate
+// g = (p - min) / h and its occupancy cell floor(g R / (n - 1)) are each a monotone function of
+// the slot index k (t_k grows with k and every FP32 operation on the way rounds monotonically), so
+// the slots of a ray fall into runs of constant (inside/outside, cell) per axis.  The setup lane of
+// a ray walks these runs: it estimates where the next cell boundary is crossed and then finds the
+// exact slot by evaluating the same FP32 expressions as index_sample at a few slots, so the mask it
+// builds holds exactly the slots index_sample accepts (inside the box, in an occupied cell), while
+// evaluating only ~2 slots per cell boundary instead of every slot.
+
+constexpr int kMaskWords = 8;                   // slots covered by the mask: 256
+constexpr int kMaskSlots = 32 * kMaskWords;
+constexpr int kStateHigh = 0x7fffffff;          // past the box along an axis
+constexpr uint32_t kNoRoom = 0xffffffffu;       // a ray whose records found no room
+
+// State of slot k along axis a: -1 before the box, kStateHigh past it, otherwise the occupancy cell
+// (0 when the grid has no mask).  The operations are those of index_sample, in the same order.
+__device__ __forceinline__ int axis_state(const GridGeo& g, const Slots& sl, float o, float d, int a, int k) {
+  const float t = slot_t(sl, k);
+  const float p = __fadd_rn(o, __fmul_rn(t, d));
+  const float ga = __fmul_rn(__fsub_rn(p, g.amin[a]), g.inv_h[a]);
+  if (!(ga >= 0.0f)) return -1;
+  if (!(ga <= (float)(g.n[a] - 1))) return kStateHigh;
+  if (!g.occ) return 0;
+  const int c = (int)floorf(__fmul_rn(ga, g.occ_scale[a]));
+  return c > g.occ_res - 1 ? g.occ_res - 1 : c;
+}
+
+// Smallest k in (lo, hi] with P(k), for a predicate that is false up to some slot and true after
+// it, given P(lo) false and P(hi) true (neither is evaluated).  `est` is a guess: the search walks
+// from it in doubling steps and bisects, so a guess off by one costs two or three evaluations.
+template <typename Pred>
+__device__ __forceinline__ int first_true(int lo, int hi, float est, Pred P) {
+  int e = !(est > (float)lo) ? lo + 1 : (!(est < (float)hi) ? hi : (int)est);
+  if (e == hi || P(e)) {
+    hi = e;
+    for (int step = 1;; step <<= 1) {
+      const int m = hi - step;
+      if (m <= lo) break;
+      if (P(m)) {
+        hi = m;
+      } else {
+        lo = m;
+        break;
+      }
+    }
+  } else {
+    lo = e;
+    for (int step = 1;; step <<= 1) {
+      const int m = lo + step;
+      if (m >= hi) break;
+      if (P(m)) {
+        hi = m;
+        break;
+      }
+      lo = m;
+    }
   }
-  float lo = -3.0e38f, hi = 3.0e38f;
+  while (hi - lo > 1) {
+    const int m = (lo + hi) >> 1;
+    if (P(m)) hi = m;
+    else lo = m;
+  }
+  return hi;
+}
+
+// First slot after k whose state along axis a differs from s = axis_state(k); kend if none before it.
+__device__ __forceinline__ int next_change(const GridGeo& g, const Slots& sl, float o, float d, float inv_d,
+                                           float inv_dt, int a, int k, int s, int kend) {
+  if (d == 0.0f) return kend;  // the coordinate does not change along the ray
+  const int R = g.occ ? g.occ_res : 1;
+  float B;  // the vertex coordinate where the state changes
+  if (d > 0.0f) {
+    if (s == kStateHigh) return kend;
+    B = s < 0 ? 0.0f : (s < R - 1 ? __fdividef((float)(s + 1), g.occ_scale[a]) : (float)(g.n[a] - 1));
+  } else {
+    if (s < 0) return kend;
+    B = s == kStateHigh ? (float)(g.n[a] - 1) : (s > 0 ? __fdividef((float)s, g.occ_scale[a]) : 0.0f);
+  }
+  const float tb = (g.amin[a] + __fdividef(B, g.inv_h[a]) - o) * inv_d;
+  const float est = ceilf((tb - sl.t0) * inv_dt - 0.5f);
+  return first_true(k, kend, est, [&](int kk) { return axis_state(g, sl, o, d, a, kk) != s; });
+}
+
+__device__ __forceinline__ void set_bits(uint32_t* mask, int k, int e) {
+  for (int w = k >> 5; w <= (e - 1) >> 5; w++) {
+    const int lo = max(k - 32 * w, 0), hi = min(e - 32 * w, 32);
+    const uint32_t upto = hi == 32 ? 0xffffffffu : ((1u << hi) - 1u);
+    mask[w] |= upto & ~((1u << lo) - 1u);
+  }
+}
+
+// Mask of the active slots among the first kend (<= kMaskSlots) slots of a ray; returns their count.
+__device__ __forceinline__ int active_mask(const GridGeo& g, const Slots& sl, const float o[3], const float d[3],
+                                           int kend, uint32_t* mask) {
+#pragma unroll
+  for (int w = 0; w < kMaskWords; w++) mask[w] = 0u;
+  if (kend <= 0) return 0;
+  const float inv_dt = __fdividef(1.0f, sl.dt);
+  float inv_d[3];
+  int st[3], nx[3];
 #pragma unroll
   for (int a = 0; a < 3; a++) {
-    if (d[a] == 0.0f) continue;
-    float t0 = __fdiv_rn(__fsub_rn(g.amin[a], o[a]), d[a]);
-    float t1 = __fdiv_rn(__fsub_rn(g.amax[a], o[a]), d[a]);
-    lo = fmaxf(lo, fminf(t0, t1));
-    hi = fminf(hi, fmaxf(t0, t1));
+    inv_d[a] = d[a] != 0.0f ? __fdividef(1.0f, d[a]) : 0.0f;
+    st[a] = axis_state(g, sl, o[a], d[a], a, 0);
+    nx[a] = next_change(g, sl, o[a], d[a], inv_d[a], inv_dt, a, 0, st[a], kend);
   }
-  if (lo > hi + 2.0f * sl.dt) return 0;
-  const float a = fminf(lo, hi), b = fmaxf(lo, hi);
-  const float klo = (a - sl.t0) / sl.dt - 2.5f, khi = (b - sl.t0) / sl.dt + 1.5f;
-  const int kmin = (int)floorf(fminf(fmaxf(klo, 0.0f), (float)sl.n));
-  const int kmax = (int)ceilf(fminf(fmaxf(khi, -1.0f), (float)(sl.n - 1)));
-  return kmax >= kmin ? kmax - kmin + 1 : 0;
+  int k = 0, count = 0;
+  for (;;) {  // every pass moves k forward by at least one slot
+    const int e = min(nx[0], min(nx[1], nx[2]));
+    bool on = true;
+#pragma unroll
+    for (int a = 0; a < 3; a++) on = on && st[a] >= 0 && st[a] != kStateHigh;
+    if (on && g.occ) {
+      const int R = g.occ_res;
+      on = __ldg(&g.occ[((size_t)st[2] * R + st[1]) * R + st[0]]) != 0;
+    }
+    if (on) {
+      set_bits(mask, k, e);
+      count += e - k;
+    }
+    if (e >= kend) break;
+    k = e;
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+      if (nx[a] == e) {
+        st[a] = axis_state(g, sl, o[a], d[a], a, e);
+        nx[a] = next_change(g, sl, o[a], d[a], inv_d[a], inv_dt, a, e, st[a], kend);
+      }
+  }
+  return count;
+}
+
+// Per-ray setup, prepared by one lane for the warp that marches the ray.
+struct RaySetup {
+  float o[3], d[3];
+  float t0, dt;
+  int nv;        // valid slots: before the box exit (box-march mode) and within the slot budget
+  int nact;      // slots that reach Feature Gathering at most: the mask's count plus every valid slot past it
+  uint32_t base; // first record reserved for the ray (nact of them), or kNoRoom
+  int view, pix;
+  uint32_t mask[kMaskWords];  // bit k: slot k is inside the box and in an occupied cell
+};
+
+__device__ __forceinline__ void prepare_ray(const GridGeo& g, const Samp& s, const float o[3], const float d[3],
+                                            RaySetup& q) {
+  const Slots sl = place_slots(g, s, o, d);
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    q.o[a] = o[a];
+    q.d[a] = d[a];
+  }
+  q.t0 = sl.t0;
+  q.dt = sl.dt;
+  int nv = sl.n;
+  if (sl.march && nv > 0) {  // slots run while t_k < t_out: the first slot past the exit, exactly
+    const float est = ceilf(__fdividef(sl.tout - sl.t0, sl.dt) - 0.5f);
+    nv = first_true(-1, nv, est, [&](int k) { return !(slot_t(sl, k) < sl.tout); });
+  }
+  q.nv = nv;
+  const int kend = min(nv, kMaskSlots);
+  q.nact = active_mask(g, sl, o, d, kend, q.mask) + (nv - kend);
+}
+
+// Reserves the records of the warp's (up to) 32 prepared rays with one atomic: lane j's ray gets
+// nact records from its base, or kNoRoom (and an error) when they pass the capacity.
+__device__ __forceinline__ void reserve_records(const RenderWs& w, RaySetup* q, bool have) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t n = have ? (uint32_t)q[lane].nact : 0u;
+  uint32_t incl = n;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const uint32_t v = __shfl_up_sync(0xffffffffu, incl, off);
+    if (lane >= off) incl += v;
+  }
+  uint32_t base = 0;
+  if (lane == 31 && incl) base = atomicAdd(&w.hdr[3], incl);
+  base = __shfl_sync(0xffffffffu, base, 31) + (incl - n);
+  if (have) {
+    const bool room = (unsigned long long)base + n <= (unsigned long long)w.Q;
+    if (!room) set_err(&w.hdr[0], kErrCapacity);
+    q[lane].base = room ? base : kNoRoom;
+  }
 }
 
 // 1 - e^{-x} for x >= 0 without cancellation: the Taylor series x (1 - x/2 (1 - x/3 (1 - x/4 (1 - x/5))))
@@ -130,89 +288,77 @@ __device__ __forceinline__ float one_minus_exp_neg(float x) {
   return x < 0.03125f ? series : 1.0f - __expf(-x);
 }
 
-constexpr int kStage = 256;  // records a warp stages in shared memory before reserving them
-
-// Brick histogram of n consecutive records with keys key(j), one atomic per run of equal keys,
-// adding `sign` per record (-1 takes back the counts of records that found no room).
-template <typename KeyAt>
-__device__ __forceinline__ void count_bricks(const RenderWs& w, uint32_t n, KeyAt key_at, int sign) {
-  const int lane = threadIdx.x & 31;
-  const unsigned full = 0xffffffffu;
-  const unsigned lt_mask = (1u << lane) - 1u;
-  const unsigned le_mask = (2u << lane) - 1u;
-  for (uint32_t j0 = 0; j0 < n; j0 += 32) {
-    const uint32_t j = j0 + lane;
-    const bool v = j < n;
-    const uint32_t key = v ? key_at(j) : 0xffffffffu;
-    const unsigned vmask = __ballot_sync(full, v);
-    const uint32_t prev = __shfl_up_sync(full, key, 1);
-    const bool head = v && (lane == 0 || prev != key);
-    const unsigned heads = __ballot_sync(full, head);
-    if (head) {
-      const unsigned after = heads & ~le_mask;
-      const int end = after ? __ffs(after) - 1 : 32;
-      const unsigned run = vmask & ~lt_mask & (end == 32 ? full : ((1u << end) - 1u));
-      atomicAdd(&w.brick_cnt[key], (uint32_t)(sign * __popc(run)));
-    }
+// Voxel and fraction of a sample that index_sample accepted (the same operations, without the tests).
+__device__ __forceinline__ void index_voxel(const GridGeo& g, const float p[3], int i0[3], float f[3]) {
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    const float ga = __fmul_rn(__fsub_rn(p[a], g.amin[a]), g.inv_h[a]);
+    int i = (int)floorf(ga);
+    if (i > g.n[a] - 2) i = g.n[a] - 2;
+    if (i < 0) i = 0;  // never taken for an accepted sample (g >= 0); keeps every load inside the grid
+    i0[a] = i;
+    f[a] = __fsub_rn(ga, (float)i);
   }
 }
 
-// K1 per ray (one warp; lane = slot within a chunk of 32 slots).  Records carry the RIT key of
-// their brick, offset by key_base (the job's first brick in a batch), and octant; dep/acc/steps
-// point at the ray's outputs
-// (or are NULL).  When the caller capped the record capacity below rays x samples, a ray that can
-// emit at most kStage records (and no backward / RIT extras) stages them in the warp's shared
-// buffers st_pw/st_key and reserves exactly its count at the end, so the capacity follows the
-// samples actually composited; otherwise rays reserve their upper bound up front (faster).
+// K1 per ray (one warp; lane = slot within a chunk of 32 slots), from the ray's prepared setup q.
+// Chunks inside the mask take their active slots from it: a chunk with none is skipped (only the
+// early-stop test runs, the transmittance being unchanged), and active lanes interpolate density
+// without testing their slot again; chunks past the mask (rays of more than kMaskSlots slots) test
+// every slot with index_sample.  Both give the slots index_sample accepts, in the same chunks as a
+// plain slot-by-slot march, so the sums and the records are the same bit for bit.  Records carry
+// the RIT key of their brick, offset by key_base (the job's first brick in a batch), and octant;
+// dep/acc/steps point at the ray's outputs (or are NULL).
 // EXTRA: the records also carry their slot, ray, transmittance and raw density (the backward and
 // the Ray Index Table export); a compile-time flag, so that the forward march tests nothing for them.
-// The march of one ray by one warp, given its slots and record bound.
 template <typename T, bool EXTRA>
 __device__ __forceinline__ void march_ray_core(const GridGeo& g, const Samp& s, const T* __restrict__ dens,
-                                               const RenderWs& w, int r, const float o[3], const float d[3],
-                                               const Slots& sl, int bound, uint32_t key_base, float* dep,
-                                               float* acc_out, int32_t* steps_out, float4* st_pw, uint32_t* st_key,
-                                               int tag = 0) {
+                                               const RenderWs& w, int r, const RaySetup& q, uint32_t key_base,
+                                               float* dep, float* acc_out, int32_t* steps_out, int tag = 0) {
   const int lane = threadIdx.x & 31;
   const unsigned full = 0xffffffffu;
   const unsigned lt_mask = (1u << lane) - 1u;
   const unsigned le_mask = (2u << lane) - 1u;  // lanes <= this one (all ones for lane 31)
-  // exact reservation pays only when the caller capped the capacity below the worst case
-  const bool capped = (unsigned long long)w.Q < (unsigned long long)w.R * (unsigned long long)w.S;
-  const bool staged = capped && bound <= kStage && !EXTRA;
-  uint32_t base = 0;
-  if (!staged) {
-    if (lane == 0 && bound > 0) base = atomicAdd(&w.hdr[3], (uint32_t)bound);
-    base = __shfl_sync(full, base, 0);
-  }
-  const bool room = staged || (unsigned long long)base + (unsigned)bound <= (unsigned long long)w.Q;
-  if (!room && lane == 0) set_err(&w.hdr[0], kErrCapacity);
+  const float o[3] = {q.o[0], q.o[1], q.o[2]}, d[3] = {q.d[0], q.d[1], q.d[2]};
+  Slots sl;
+  sl.t0 = q.t0;
+  sl.dt = q.dt;
+  sl.n = q.nv;
+  sl.tout = 0.0f;
+  sl.march = false;
+  const int nv = q.nv;
+  const bool room = q.base != kNoRoom;
+  const uint32_t base = room ? q.base : 0u;
   float Ssum = 0.0f, acc_l = 0.0f, dsum_l = 0.0f;
   uint32_t cnt = 0;
-  int steps = sl.n;
-  for (int k0 = 0; k0 < sl.n; k0 += 32) {
+  int steps = nv;
+  for (int k0 = 0; k0 < nv; k0 += 32) {
     const int k = k0 + lane;
+    const bool valid = k < nv;
+    const unsigned vmask = nv - k0 >= 32 ? full : ((1u << (nv - k0)) - 1u);
     const float t = slot_t(sl, k);
-    const bool valid = slot_valid(sl, k, t);
-    const unsigned vmask = __ballot_sync(full, valid);
-    if (!vmask) {
-      steps = k0;
-      break;
-    }
     int i0[3] = {0, 0, 0};
-    float f[3], p[3] = {0.0f, 0.0f, 0.0f};
-    bool act = false;
-    if (valid) {
-      sample_pos(o, d, t, p);
-      act = index_sample(g, p, i0, f);
+    float f[3] = {0.0f, 0.0f, 0.0f}, p[3] = {0.0f, 0.0f, 0.0f};
+    bool act;
+    unsigned amask;
+    if (k0 < kMaskSlots) {
+      amask = q.mask[k0 >> 5];
+      act = (amask >> lane) & 1u;
+      if (act) {
+        sample_pos(o, d, t, p);
+        index_voxel(g, p, i0, f);
+      }
+    } else {
+      act = false;
+      if (valid) {
+        sample_pos(o, d, t, p);
+        act = index_sample(g, p, i0, f);
+      }
+      amask = __ballot_sync(full, act);
     }
-    if (!__any_sync(full, act)) {  // nothing to composite in these slots: only the stop test
+    if (!amask) {  // nothing to composite in these slots: only the stop test
       if (s.t_stop > 0.0f && __expf(-(Ssum + 0.0f)) < s.t_stop) {
         steps = k0;
-        break;
-      }
-      if (vmask != full) {
-        steps = k0 + __popc(vmask);
         break;
       }
       continue;
@@ -238,22 +384,16 @@ __device__ __forceinline__ void march_ray_core(const GridGeo& g, const Samp& s, 
     const float wk = (act && lane < first) ? Tk * one_minus_exp_neg(sd) : 0.0f;
     const unsigned cmask = __ballot_sync(full, contrib);
     const uint32_t key = contrib ? brick_key(g, i0, key_base) : 0xffffffffu;
-    if (staged) {
-      if (contrib) {
-        const uint32_t j = cnt + __popc(cmask & lt_mask);
-        st_pw[j] = make_float4(p[0], p[1], p[2], wk);
-        st_key[j] = key;
-      }
-    } else if (contrib) {
-      const size_t q = (size_t)base + cnt + __popc(cmask & lt_mask);
-      w.rec_pw[q] = make_float4(p[0], p[1], p[2], wk);
-      w.rec_key[q] = key;
+    if (contrib) {
+      const size_t qi = (size_t)base + cnt + __popc(cmask & lt_mask);
+      w.rec_pw[qi] = make_float4(p[0], p[1], p[2], wk);
+      w.rec_key[qi] = key;
       if constexpr (EXTRA) {
-        if (w.rec_k) w.rec_k[q] = (uint16_t)k;
-        if (w.rec_ray) w.rec_ray[q] = (uint32_t)r;
+        if (w.rec_k) w.rec_k[qi] = (uint16_t)k;
+        if (w.rec_ray) w.rec_ray[qi] = (uint32_t)r;
         if (w.rec_T) {
-          w.rec_T[q] = Tk;
-          w.rec_raw[q] = raw;
+          w.rec_T[qi] = Tk;
+          w.rec_raw[qi] = raw;
         }
       }
     }
@@ -277,29 +417,7 @@ __device__ __forceinline__ void march_ray_core(const GridGeo& g, const Samp& s, 
       steps = k0 + first;
       break;
     }
-    if (vmask != full) {
-      steps = k0 + __popc(vmask);
-      break;
-    }
-  }
-  if (staged) {
-    // reserve exactly the composited records and copy them out
-    __syncwarp();
-    if (lane == 0 && cnt) base = atomicAdd(&w.hdr[3], cnt);
-    base = __shfl_sync(full, base, 0);
-    if ((unsigned long long)base + cnt <= (unsigned long long)w.Q) {
-      for (uint32_t j = lane; j < cnt; j += 32) {
-        w.rec_pw[(size_t)base + j] = st_pw[j];
-        w.rec_key[(size_t)base + j] = st_key[j];
-      }
-    } else {
-      // no room: take the records back out of the histogram; the ray composites nothing and the
-      // error is reported
-      if (lane == 0) set_err(&w.hdr[0], kErrCapacity);
-      count_bricks(w, cnt, [&](uint32_t j) { return st_key[j]; }, -1);
-      cnt = 0;
-    }
-    __syncwarp();  // the staging buffers are free for the warp's next ray
+    (void)vmask;
   }
   const float acc = warp_sum(acc_l), dsum = warp_sum(dsum_l);
   if (lane == 0) {
@@ -313,26 +431,9 @@ __device__ __forceinline__ void march_ray_core(const GridGeo& g, const Samp& s, 
   }
 }
 
-template <typename T, bool EXTRA>
-__device__ __forceinline__ void march_ray(const GridGeo& g, const Samp& s, const T* __restrict__ dens,
-                                          const RenderWs& w, int r, const float o[3], const float d[3],
-                                          uint32_t key_base, float* dep, float* acc_out, int32_t* steps_out,
-                                          float4* st_pw, uint32_t* st_key, int tag = 0) {
-  const Slots sl = place_slots(g, s, o, d);
-  march_ray_core<T, EXTRA>(g, s, dens, w, r, o, d, sl, record_bound(g, sl, o, d), key_base, dep, acc_out, steps_out,
-                           st_pw, st_key, tag);
-}
-
-// Per-ray setup shared by a warp: ray, slots, record bound and output pixel.
-struct RaySetup {
-  float o[3], d[3];
-  float t0, dt, tout;
-  int n, march, bound, view, pix;
-};
-
 // K1: one warp per ray.  A warp's rays are r = warp + i nwarps; lane j prepares the setup of the
-// j-th of each group of 32 of them (ray generation, slot placement, record bound: the divisions
-// and the square root), which the whole warp then reads from shared memory ray by ray.
+// j-th of each group of 32 of them (ray generation, slot placement, the active-slot mask), the
+// warp reserves their records with one atomic, and then marches them one by one from shared memory.
 template <typename T, bool EXTRA>
 __global__ void __launch_bounds__(256, 4) k_march(GridGeo g, Samp s, RaySrc src, const T* __restrict__ dens,
                                                RenderWs w, OutBufs out) {
@@ -340,14 +441,8 @@ __global__ void __launch_bounds__(256, 4) k_march(GridGeo g, Samp s, RaySrc src,
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   const int R = ray_count(src);
-  // record staging: dynamic shared memory, present (kMarchStageBytes) only when the launch stages,
-  // i.e. the capacity is capped and the records carry no extras; otherwise the larger L1 serves
-  // the density loads
-  extern __shared__ __align__(16) unsigned char march_stage[];
   __shared__ RaySetup setup[8][32];
   const int wb = threadIdx.x >> 5;
-  float4* st_pw = reinterpret_cast<float4*>(march_stage) + wb * kStage;
-  uint32_t* st_key = reinterpret_cast<uint32_t*>(march_stage + 8 * kStage * sizeof(float4)) + wb * kStage;
   for (long long i0 = 0;; i0 += 32) {
     const long long rl = (long long)warp + (i0 + lane) * nwarps;
     const unsigned have = __ballot_sync(0xffffffffu, rl < R);
@@ -357,47 +452,22 @@ __global__ void __launch_bounds__(256, 4) k_march(GridGeo g, Samp s, RaySrc src,
       RaySetup& q = setup[wb][lane];
       float o[3], d[3];
       ray_gen(src, rr, o, d);
-      const Slots sl = place_slots(g, s, o, d);
-#pragma unroll
-      for (int a = 0; a < 3; a++) {
-        q.o[a] = o[a];
-        q.d[a] = d[a];
-      }
-      q.t0 = sl.t0;
-      q.dt = sl.dt;
-      q.tout = sl.tout;
-      q.n = sl.n;
-      q.march = sl.march ? 1 : 0;
-      q.bound = record_bound(g, sl, o, d);
+      prepare_ray(g, s, o, d, q);
       q.view = rr.view;
       q.pix = rr.pix;
     }
+    reserve_records(w, setup[wb], rl < R);
     __syncwarp();
     const int nq = __popc(have);  // rl grows with the lane: the rays present are lanes 0 .. nq-1
     for (int j = 0; j < nq; j++) {
       const RaySetup& q = setup[wb][j];
-      const float o[3] = {q.o[0], q.o[1], q.o[2]}, d[3] = {q.d[0], q.d[1], q.d[2]};
-      Slots sl;
-      sl.t0 = q.t0;
-      sl.dt = q.dt;
-      sl.tout = q.tout;
-      sl.n = q.n;
-      sl.march = q.march != 0;
       float* dep = out.depth[q.view];
-      march_ray_core<T, EXTRA>(g, s, dens, w, (int)((long long)warp + (i0 + j) * nwarps), o, d, sl, q.bound, 0u,
+      march_ray_core<T, EXTRA>(g, s, dens, w, (int)((long long)warp + (i0 + j) * nwarps), q, 0u,
                                dep ? dep + q.pix : nullptr, out.acc ? out.acc + q.pix : nullptr,
-                               out.n_steps ? out.n_steps + q.pix : nullptr, st_pw, st_key);
+                               out.n_steps ? out.n_steps + q.pix : nullptr);
     }
     __syncwarp();  // the setup slots are free for the next group
   }
-}
-
-// Dynamic shared memory of a k_march launch: the staging buffers exactly when march_ray_core
-// stages (capacity capped below rays x slots, no record extras).
-constexpr int kMarchStageBytes = 8 * kStage * (int)(sizeof(float4) + sizeof(uint32_t));
-static int march_stage_bytes(const RenderWs& w, bool extra) {
-  const bool capped = (unsigned long long)w.Q < (unsigned long long)w.R * (unsigned long long)w.S;
-  return capped && !extra ? kMarchStageBytes : 0;
 }
 
 // K2: exclusive scan of the brick histogram and the list of tiles (<= kTile samples of one brick).
@@ -1077,8 +1147,6 @@ __global__ void __launch_bounds__(256, 4) k_march_batch(const JobDesc* __restric
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   const int lane = threadIdx.x & 31;
-  __shared__ float4 st_pw[8][kStage];
-  __shared__ uint32_t st_key[8][kStage];
   __shared__ JobCache cache[8];
   __shared__ RaySetup setup[8][32];
   const int wb = threadIdx.x >> 5;
@@ -1086,7 +1154,7 @@ __global__ void __launch_bounds__(256, 4) k_march_batch(const JobDesc* __restric
   if (lane == 0) C.job = -1;
   __syncwarp();
   // as in k_march: lane j prepares the j-th of each group of 32 of the warp's rays (its job, ray,
-  // slots and record bound, from the job's own geometry and sampling)
+  // slots and active-slot mask, from the job's own geometry and sampling)
   for (long long i0 = 0;; i0 += 32) {
     const long long rl = (long long)warp + (i0 + lane) * nwarps;
     const unsigned have = __ballot_sync(0xffffffffu, rl < R);
@@ -1098,21 +1166,11 @@ __global__ void __launch_bounds__(256, 4) k_march_batch(const JobDesc* __restric
       const int pix = (int)rl - J.ray_base;
       float o[3], d[3];
       ray_gen_cam(J.cam, pix, o, d);
-      const Slots sl = place_slots(J.geo, J.samp, o, d);
-#pragma unroll
-      for (int a = 0; a < 3; a++) {
-        q.o[a] = o[a];
-        q.d[a] = d[a];
-      }
-      q.t0 = sl.t0;
-      q.dt = sl.dt;
-      q.tout = sl.tout;
-      q.n = sl.n;
-      q.march = sl.march ? 1 : 0;
-      q.bound = record_bound(J.geo, sl, o, d);
+      prepare_ray(J.geo, J.samp, o, d, q);
       q.view = j;
       q.pix = pix;
     }
+    reserve_records(w, setup[wb], rl < R);
     __syncwarp();
     const int nq = __popc(have);
     for (int jj = 0; jj < nq; jj++) {
@@ -1130,17 +1188,9 @@ __global__ void __launch_bounds__(256, 4) k_march_batch(const JobDesc* __restric
         if (lane == 0) C.job = j;
         __syncwarp();
       }
-      const float o[3] = {q.o[0], q.o[1], q.o[2]}, d[3] = {q.d[0], q.d[1], q.d[2]};
-      Slots sl;
-      sl.t0 = q.t0;
-      sl.dt = q.dt;
-      sl.tout = q.tout;
-      sl.n = q.n;
-      sl.march = q.march != 0;
       // a batch's records carry no extras (no backward, no export)
-      march_ray_core<T, false>(C.g, C.s, (const T*)J.density, w, (int)((long long)warp + (i0 + jj) * nwarps), o, d, sl,
-                               q.bound, (uint32_t)J.brick_base, J.depth ? J.depth + q.pix : nullptr, nullptr, nullptr,
-                               st_pw[wb], st_key[wb], j);
+      march_ray_core<T, false>(C.g, C.s, (const T*)J.density, w, (int)((long long)warp + (i0 + jj) * nwarps), q,
+                               (uint32_t)J.brick_base, J.depth ? J.depth + q.pix : nullptr, nullptr, nullptr, j);
     }
     __syncwarp();  // the setup slots are free for the next group
   }
@@ -1252,22 +1302,14 @@ cicero_status run_render(const cicero_grid* grid, const MlpPtrs& mlp, const Rend
     k_clear<<<std::min(num_sms() * 4, (plan.nb * kOctants + 255) / 256 + 1), 256, 0, st>>>(ws.hdr, 16, ws.brick_cnt,
                                                                                   (size_t)plan.nb * kOctants);
     const bool extra = ws.rec_k || ws.rec_ray || ws.rec_T;
-    const int dyn = march_stage_bytes(ws, extra);
-    static const bool attrs = [] {
-      // staging + the per-ray setup exceed the default 48 KB per block: opt in once per instance
-      cudaFuncSetAttribute(k_march<__half, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMarchStageBytes);
-      cudaFuncSetAttribute(k_march<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMarchStageBytes);
-      return true;
-    }();
-    (void)attrs;
     if (f16 && extra)
-      k_march<__half, true><<<mb, 256, dyn, st>>>(geo, plan.samp, src, (const __half*)grid->density, ws, out);
+      k_march<__half, true><<<mb, 256, 0, st>>>(geo, plan.samp, src, (const __half*)grid->density, ws, out);
     else if (f16)
-      k_march<__half, false><<<mb, 256, dyn, st>>>(geo, plan.samp, src, (const __half*)grid->density, ws, out);
+      k_march<__half, false><<<mb, 256, 0, st>>>(geo, plan.samp, src, (const __half*)grid->density, ws, out);
     else if (extra)
-      k_march<float, true><<<mb, 256, dyn, st>>>(geo, plan.samp, src, (const float*)grid->density, ws, out);
+      k_march<float, true><<<mb, 256, 0, st>>>(geo, plan.samp, src, (const float*)grid->density, ws, out);
     else
-      k_march<float, false><<<mb, 256, dyn, st>>>(geo, plan.samp, src, (const float*)grid->density, ws, out);
+      k_march<float, false><<<mb, 256, 0, st>>>(geo, plan.samp, src, (const float*)grid->density, ws, out);
   }
   {
     ProfScope ps(kStBucket, st);

@@ -131,15 +131,33 @@ def test_explicit_rays_fp32(cc, orc, small):
 # Ray Index Table: bit-exact grouping of samples by brick
 
 
-@pytest.mark.parametrize("which,brick", [("small", 8), ("small", 4), ("occ", 8), ("occ", 16)])
+def _axis_camera(axis):
+    """A camera looking along +z (axis 2) or +x (axis 0) with a long focal length, so that its rays
+    are axis-parallel (the centre pixel exactly) or nearly so, its origin on occupancy cell
+    boundaries of the 96^3 scene (cells of 1/16 of the box)."""
+    R = np.eye(3) if axis == 2 else np.array([[0.0, 0.0, 1.0], [1.0, 0.0, 0.0], [0.0, 1.0, 0.0]])
+    pos = np.array([-0.6875, 0.0625, -1.5]) if axis == 2 else np.array([-1.5, 0.0, 0.125])
+    c2w = np.concatenate([R, pos[:, None]], 1).astype(np.float32)
+    return scenes.Camera(33, 33, 4000.0, 16.5, 16.5, c2w, scenes.sampling_march(96, 160))
+
+
+@pytest.mark.parametrize("which,brick", [("small", 8), ("small", 4), ("occ", 8), ("occ", 16), ("axis_z", 8),
+                                         ("axis_x", 4)])
 def test_ray_index_table_bit_exact(cc, orc, small, occ_scene, which, brick):
+    """The samples that reach Feature Gathering, grouped by brick, bit-exact against the oracle's
+    slot-by-slot classification.  The axis cases put rays parallel or nearly parallel to an axis
+    and start them on occupancy cell boundaries, where the march's per-ray mask of active slots
+    (found from cell boundary crossings) is most easily wrong."""
     import torch
     if which == "small":
         g, _ = small
         cam = scenes.orbit_camera(48, 40, sampling=scenes.sampling_uniform(64))
-    else:
+    elif which == "occ":
         g, _ = occ_scene
         cam = scenes.orbit_camera(40, 40, az_deg=120.0, sampling=scenes.sampling_march(96, 160))
+    else:
+        g, _ = occ_scene
+        cam = _axis_camera(2 if which == "axis_z" else 0)
     S = cam.sampling.n_samples
     R = cam.width * cam.height
     want = orc.active_samples(g, cam.sampling, brick, cam=cam)

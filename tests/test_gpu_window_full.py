@@ -35,7 +35,7 @@ def test_full_window_against_oracle(cc, orc):
     tds = [cc.camera_from(t) for t in targets]
     o16 = cc.options(cc.MLP_BF16, 4)
     oh = cc.options(cc.MLP_BF16, 4, max_records=HOLE_RECORDS)
-    assert HOLE_RECORDS < n * R * cam.sampling.n_samples  # the exact-reservation path runs
+    assert HOLE_RECORDS < n * R * cam.sampling.n_samples  # a capacity below the worst case
 
     ref_rgb, ref_depth = torch.empty(R, 3, device="cuda"), torch.empty(R, device="cuda")
     ws_r = cc.workspace(cc.cicero_render_workspace_size(grid.desc, R, sd, o16))
