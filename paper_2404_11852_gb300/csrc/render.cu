@@ -301,20 +301,21 @@ __device__ __forceinline__ void index_voxel(const GridGeo& g, const float p[3], 
   }
 }
 
-// K1 per ray (one warp; lane = slot within a chunk of 32 slots), from the ray's prepared setup q.
-// Chunks inside the mask take their active slots from it: a chunk with none is skipped (only the
-// early-stop test runs, the transmittance being unchanged), and active lanes interpolate density
-// without testing their slot again; chunks past the mask (rays of more than kMaskSlots slots) test
-// every slot with index_sample.  Both give the slots index_sample accepts, in the same chunks as a
-// plain slot-by-slot march, so the sums and the records are the same bit for bit.  Records carry
-// the RIT key of their brick, offset by key_base (the job's first brick in a batch), and octant;
-// dep/acc/steps point at the ray's outputs (or are NULL).
+// K1 per ray (one warp), from the ray's prepared setup q.  The ray's active slots inside the mask
+// are listed in slot order (list: the warp's kMaskSlots bytes of shared memory) and composited 32
+// at a time, lane j taking the j-th active slot of the chunk; slots past the mask (rays of more
+// than kMaskSlots slots) follow in chunks of 32 consecutive slots, each tested with index_sample.
+// Inactive slots add nothing to the transmittance, so the early stop falls on the slot after the
+// last active slot processed before the transmittance dropped below t_stop, as in a plain
+// slot-by-slot march.  Records carry the RIT key of their brick, offset by key_base (the job's first
+// brick in a batch), and octant; dep/acc/steps point at the ray's outputs (or are NULL).
 // EXTRA: the records also carry their slot, ray, transmittance and raw density (the backward and
 // the Ray Index Table export); a compile-time flag, so that the forward march tests nothing for them.
 template <typename T, bool EXTRA>
 __device__ __forceinline__ void march_ray_core(const GridGeo& g, const Samp& s, const T* __restrict__ dens,
                                                const RenderWs& w, int r, const RaySetup& q, uint32_t key_base,
-                                               float* dep, float* acc_out, int32_t* steps_out, int tag = 0) {
+                                               float* dep, float* acc_out, int32_t* steps_out, uint8_t* list,
+                                               int tag = 0) {
   const int lane = threadIdx.x & 31;
   const unsigned full = 0xffffffffu;
   const unsigned lt_mask = (1u << lane) - 1u;
@@ -331,38 +332,10 @@ __device__ __forceinline__ void march_ray_core(const GridGeo& g, const Samp& s, 
   const uint32_t base = room ? q.base : 0u;
   float Ssum = 0.0f, acc_l = 0.0f, dsum_l = 0.0f;
   uint32_t cnt = 0;
-  int steps = nv;
-  for (int k0 = 0; k0 < nv; k0 += 32) {
-    const int k = k0 + lane;
-    const bool valid = k < nv;
-    const unsigned vmask = nv - k0 >= 32 ? full : ((1u << (nv - k0)) - 1u);
-    const float t = slot_t(sl, k);
-    int i0[3] = {0, 0, 0};
-    float f[3] = {0.0f, 0.0f, 0.0f}, p[3] = {0.0f, 0.0f, 0.0f};
-    bool act;
-    unsigned amask;
-    if (k0 < kMaskSlots) {
-      amask = q.mask[k0 >> 5];
-      act = (amask >> lane) & 1u;
-      if (act) {
-        sample_pos(o, d, t, p);
-        index_voxel(g, p, i0, f);
-      }
-    } else {
-      act = false;
-      if (valid) {
-        sample_pos(o, d, t, p);
-        act = index_sample(g, p, i0, f);
-      }
-      amask = __ballot_sync(full, act);
-    }
-    if (!amask) {  // nothing to composite in these slots: only the stop test
-      if (s.t_stop > 0.0f && __expf(-(Ssum + 0.0f)) < s.t_stop) {
-        steps = k0;
-        break;
-      }
-      continue;
-    }
+  // One chunk of up to 32 samples, lane by lane in slot order: density, the scan of sigma delta,
+  // the stop test (lanes with `elig`), weights, records and the brick histogram.  Returns the first
+  // lane whose transmittance is below t_stop (32: none); Ssum then holds the sum up to that lane.
+  auto chunk = [&](bool act, bool elig, int k, float t, const float p[3], const int i0[3], const float f[3]) -> int {
     float sd = 0.0f, raw = 0.0f;
     if (act) {
       raw = density_trilinear(g, dens, i0, f);
@@ -377,7 +350,7 @@ __device__ __forceinline__ void march_ray_core(const GridGeo& g, const Samp& s, 
     float excl = __shfl_up_sync(full, incl, 1);
     if (lane == 0) excl = 0.0f;
     const float Tk = __expf(-(Ssum + excl));
-    const bool stop = valid && s.t_stop > 0.0f && Tk < s.t_stop;
+    const bool stop = elig && s.t_stop > 0.0f && Tk < s.t_stop;
     const unsigned smask = __ballot_sync(full, stop);
     const int first = smask ? __ffs(smask) - 1 : 32;
     const bool contrib = act && lane < first && room;
@@ -397,7 +370,7 @@ __device__ __forceinline__ void march_ray_core(const GridGeo& g, const Samp& s, 
         }
       }
     }
-    // brick histogram: one atomic per run of consecutive lanes with the same brick
+    // brick histogram: one atomic per run of consecutive lanes with the same key
     const uint32_t prev = __shfl_up_sync(full, key, 1);
     const bool head = contrib && (lane == 0 || prev != key);
     const unsigned heads = __ballot_sync(full, head);
@@ -413,11 +386,81 @@ __device__ __forceinline__ void march_ray_core(const GridGeo& g, const Samp& s, 
     const int last = first == 32 ? 31 : first - 1;
     const float tot = __shfl_sync(full, incl, last < 0 ? 0 : last);
     if (first > 0) Ssum += tot;
-    if (first < 32) {
-      steps = k0 + first;
+    return first;
+  };
+
+  // the active slots of the mask, in slot order: lane j lists those of slots 8 j .. 8 j + 7
+  int n_act;
+  {
+    uint32_t bits = (q.mask[lane >> 2] >> ((lane & 3) * 8)) & 0xffu;
+    const int c = __popc(bits);
+    int incl = c;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const int v = __shfl_up_sync(full, incl, off);
+      if (lane >= off) incl += v;
+    }
+    n_act = __shfl_sync(full, incl, 31);
+    int pos = incl - c;
+    while (bits) {
+      list[pos++] = (uint8_t)(8 * lane + __ffs(bits) - 1);
+      bits &= bits - 1u;
+    }
+    __syncwarp();
+  }
+  int steps = nv, last = -1;  // last: slot of the last active sample composited so far
+  bool stopped = false;
+  for (int j0 = 0; j0 < n_act; j0 += 32) {
+    const int j = j0 + lane;
+    const bool has = j < n_act;
+    const int k = has ? (int)list[j] : 0;
+    const float t = slot_t(sl, k);
+    int i0[3] = {0, 0, 0};
+    float f[3] = {0.0f, 0.0f, 0.0f}, p[3] = {0.0f, 0.0f, 0.0f};
+    if (has) {
+      sample_pos(o, d, t, p);
+      index_voxel(g, p, i0, f);
+    }
+    const int first = chunk(has, has, k, t, p, i0, f);
+    const int prev_k = __shfl_sync(full, k, first > 0 && first < 32 ? first - 1 : 0);
+    if (first < 32) {  // the stop falls right after the previous active slot
+      steps = (first > 0 ? prev_k : last) + 1;
+      stopped = true;
       break;
     }
-    (void)vmask;
+    last = __shfl_sync(full, k, min(n_act - j0, 32) - 1);
+  }
+  __syncwarp();  // the list is free for the warp's next ray
+  if (!stopped && s.t_stop > 0.0f && __expf(-(Ssum + 0.0f)) < s.t_stop) {
+    // the transmittance fell below the threshold at the last active slot: the next slot stops
+    steps = last + 1;
+    stopped = true;
+  }
+  if (!stopped) {
+    for (int k0 = kMaskSlots; k0 < nv; k0 += 32) {  // slots past the mask, tested one by one
+      const int k = k0 + lane;
+      const bool valid = k < nv;
+      const float t = slot_t(sl, k);
+      int i0[3] = {0, 0, 0};
+      float f[3] = {0.0f, 0.0f, 0.0f}, p[3] = {0.0f, 0.0f, 0.0f};
+      bool act = false;
+      if (valid) {
+        sample_pos(o, d, t, p);
+        act = index_sample(g, p, i0, f);
+      }
+      if (!__any_sync(full, act)) {  // nothing to composite in these slots: only the stop test
+        if (s.t_stop > 0.0f && __expf(-(Ssum + 0.0f)) < s.t_stop) {
+          steps = k0;
+          break;
+        }
+        continue;
+      }
+      const int first = chunk(act, valid, k, t, p, i0, f);
+      if (first < 32) {
+        steps = k0 + first;
+        break;
+      }
+    }
   }
   const float acc = warp_sum(acc_l), dsum = warp_sum(dsum_l);
   if (lane == 0) {
@@ -442,6 +485,7 @@ __global__ void __launch_bounds__(256, 4) k_march(GridGeo g, Samp s, RaySrc src,
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   const int R = ray_count(src);
   __shared__ RaySetup setup[8][32];
+  __shared__ uint8_t slot_list[8][kMaskSlots];
   const int wb = threadIdx.x >> 5;
   for (long long i0 = 0;; i0 += 32) {
     const long long rl = (long long)warp + (i0 + lane) * nwarps;
@@ -464,7 +508,7 @@ __global__ void __launch_bounds__(256, 4) k_march(GridGeo g, Samp s, RaySrc src,
       float* dep = out.depth[q.view];
       march_ray_core<T, EXTRA>(g, s, dens, w, (int)((long long)warp + (i0 + j) * nwarps), q, 0u,
                                dep ? dep + q.pix : nullptr, out.acc ? out.acc + q.pix : nullptr,
-                               out.n_steps ? out.n_steps + q.pix : nullptr);
+                               out.n_steps ? out.n_steps + q.pix : nullptr, slot_list[wb]);
     }
     __syncwarp();  // the setup slots are free for the next group
   }
@@ -1149,6 +1193,7 @@ __global__ void __launch_bounds__(256, 4) k_march_batch(const JobDesc* __restric
   const int lane = threadIdx.x & 31;
   __shared__ JobCache cache[8];
   __shared__ RaySetup setup[8][32];
+  __shared__ uint8_t slot_list[8][kMaskSlots];
   const int wb = threadIdx.x >> 5;
   JobCache& C = cache[wb];
   if (lane == 0) C.job = -1;
@@ -1190,7 +1235,8 @@ __global__ void __launch_bounds__(256, 4) k_march_batch(const JobDesc* __restric
       }
       // a batch's records carry no extras (no backward, no export)
       march_ray_core<T, false>(C.g, C.s, (const T*)J.density, w, (int)((long long)warp + (i0 + jj) * nwarps), q,
-                               (uint32_t)J.brick_base, J.depth ? J.depth + q.pix : nullptr, nullptr, nullptr, j);
+                               (uint32_t)J.brick_base, J.depth ? J.depth + q.pix : nullptr, nullptr, nullptr,
+                               slot_list[wb], j);
     }
     __syncwarp();  // the setup slots are free for the next group
   }
