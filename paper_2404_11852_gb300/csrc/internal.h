@@ -62,6 +62,7 @@ struct RenderWs {
   uint4* tile;          // [max_tiles] (first record, count | bz << 8 | job << 21, brick id, bx | by << 16)
   SrtRec* srt;          // [Q] the Ray Index Table payload in brick order
   uint32_t* rec_ray;    // [Q] ray of each record (backward and RIT export only; may be null)
+  struct RaySetup* setup;  // [R] per-ray setup of the march (ray, slots, active-slot mask, records)
   int R, S, nb, max_tiles;
   uint32_t Q;
 };

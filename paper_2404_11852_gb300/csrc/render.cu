@@ -27,6 +27,7 @@ namespace cicero {
 static size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 
 constexpr int kScanChunk = 1024;  // bricks per block of the RIT offset scan (one per thread)
+constexpr size_t kRaySetupBytes = 84;  // sizeof(RaySetup), checked where it is defined
 
 size_t render_ws_bytes(const RenderPlan& p) {
   const size_t Q = p.Q, R = (size_t)p.R;
@@ -41,6 +42,7 @@ size_t render_ws_bytes(const RenderPlan& p) {
   b += al256(8 * ((size_t)p.nb / kScanChunk + 2));
   b += al256(16 * (size_t)p.max_tiles);
   b += al256(32 * Q);
+  b += al256(kRaySetupBytes * R);
   return b;
 }
 
@@ -73,6 +75,7 @@ bool carve_render_ws(void* ws, size_t bytes, const RenderPlan& p, RenderWs* w) {
   w->blk_sums = (uint32_t*)take(8 * ((size_t)p.nb / kScanChunk + 2));
   w->tile = (uint4*)take(16 * (size_t)p.max_tiles);
   w->srt = (SrtRec*)take(32 * Q);
+  w->setup = (RaySetup*)take(kRaySetupBytes * R);
   w->R = p.R;
   w->S = p.S;
   w->nb = p.nb;
@@ -238,6 +241,8 @@ struct RaySetup {
   int view, pix;
   uint32_t mask[kMaskWords];  // bit k: slot k is inside the box and in an occupied cell
 };
+static_assert(sizeof(RaySetup) == kRaySetupBytes, "RaySetup layout");
+constexpr int kSetupWords = (int)(sizeof(RaySetup) / 4);
 
 __device__ __forceinline__ void prepare_ray(const GridGeo& g, const Samp& s, const float o[3], const float d[3],
                                             RaySetup& q) {
@@ -474,9 +479,66 @@ __device__ __forceinline__ void march_ray_core(const GridGeo& g, const Samp& s, 
   }
 }
 
-// K1: one warp per ray.  A warp's rays are r = warp + i nwarps; lane j prepares the setup of the
-// j-th of each group of 32 of them (ray generation, slot placement, the active-slot mask), the
-// warp reserves their records with one atomic, and then marches them one by one from shared memory.
+// The job whose first ray (or first brick) is the largest one <= x, from the contiguous array of
+// the jobs' first rays (or bricks).
+__device__ __forceinline__ int job_of(const int* __restrict__ base, int n_jobs, int x) {
+  int lo = 0, hi = n_jobs;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(&base[mid]) <= x) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// K0: the setup of every ray, one thread per ray (ray generation, slot placement, the exact mask
+// of active slots), with the records reserved by one atomic per 32 rays.  A separate kernel keeps
+// all 32 lanes of a warp busy on the mask walk however many rays a launch has, while the march
+// keeps one warp per ray.  With BATCH, ray r belongs to the job found among the jobs' first rays.
+template <bool BATCH>
+__global__ void __launch_bounds__(256) k_ray_setup(GridGeo g, Samp s, RaySrc src, const JobDesc* __restrict__ jobs,
+                                                   const int* __restrict__ bases, int n_jobs, int R_batch, RenderWs w) {
+  __shared__ RaySetup sq[256];
+  const int R = BATCH ? R_batch : ray_count(src);
+  for (long long r0 = (long long)blockIdx.x * 256; r0 < R; r0 += (long long)gridDim.x * 256) {
+    const long long r = r0 + threadIdx.x;
+    const bool have = r < R;
+    if (have) {
+      RaySetup& q = sq[threadIdx.x];
+      float o[3], d[3];
+      if constexpr (BATCH) {
+        const int j = job_of(bases, n_jobs, (int)r);
+        const JobDesc& J = jobs[j];
+        const int pix = (int)r - J.ray_base;
+        ray_gen_cam(J.cam, pix, o, d);
+        prepare_ray(J.geo, J.samp, o, d, q);
+        q.view = j;
+        q.pix = pix;
+      } else {
+        const RayRef rr = ray_ref(src, (int)r);
+        ray_gen(src, rr, o, d);
+        prepare_ray(g, s, o, d, q);
+        q.view = rr.view;
+        q.pix = rr.pix;
+      }
+    }
+    reserve_records(w, sq + (threadIdx.x & ~31), have);
+    __syncthreads();
+    const int n = (int)min((long long)256, (long long)R - r0);
+    const uint32_t* from = reinterpret_cast<const uint32_t*>(sq);
+    uint32_t* to = reinterpret_cast<uint32_t*>(w.setup + r0);
+    for (int i = threadIdx.x; i < n * kSetupWords; i += 256) to[i] = from[i];
+    __syncthreads();
+  }
+}
+
+// The warp's copy of ray r's setup: lane i < kSetupWords holds word i (loaded ahead of time).
+__device__ __forceinline__ uint32_t setup_word(const RenderWs& w, long long r, int lane) {
+  return lane < kSetupWords ? __ldg(reinterpret_cast<const uint32_t*>(w.setup + r) + lane) : 0u;
+}
+
+// K1: one warp per ray, rays r = warp + i nwarps; each ray's setup (from K0) is staged in shared
+// memory, the next ray's loaded while the current one marches.
 template <typename T, bool EXTRA>
 __global__ void __launch_bounds__(256, 4) k_march(GridGeo g, Samp s, RaySrc src, const T* __restrict__ dens,
                                                RenderWs w, OutBufs out) {
@@ -484,33 +546,20 @@ __global__ void __launch_bounds__(256, 4) k_march(GridGeo g, Samp s, RaySrc src,
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   const int R = ray_count(src);
-  __shared__ RaySetup setup[8][32];
+  __shared__ RaySetup setup[8];
   __shared__ uint8_t slot_list[8][kMaskSlots];
   const int wb = threadIdx.x >> 5;
-  for (long long i0 = 0;; i0 += 32) {
-    const long long rl = (long long)warp + (i0 + lane) * nwarps;
-    const unsigned have = __ballot_sync(0xffffffffu, rl < R);
-    if (!have) break;
-    if (rl < R) {
-      const RayRef rr = ray_ref(src, (int)rl);
-      RaySetup& q = setup[wb][lane];
-      float o[3], d[3];
-      ray_gen(src, rr, o, d);
-      prepare_ray(g, s, o, d, q);
-      q.view = rr.view;
-      q.pix = rr.pix;
-    }
-    reserve_records(w, setup[wb], rl < R);
+  uint32_t next = warp < R ? setup_word(w, warp, lane) : 0u;
+  for (long long r = warp; r < R; r += nwarps) {
+    if (lane < kSetupWords) reinterpret_cast<uint32_t*>(&setup[wb])[lane] = next;
     __syncwarp();
-    const int nq = __popc(have);  // rl grows with the lane: the rays present are lanes 0 .. nq-1
-    for (int j = 0; j < nq; j++) {
-      const RaySetup& q = setup[wb][j];
-      float* dep = out.depth[q.view];
-      march_ray_core<T, EXTRA>(g, s, dens, w, (int)((long long)warp + (i0 + j) * nwarps), q, 0u,
-                               dep ? dep + q.pix : nullptr, out.acc ? out.acc + q.pix : nullptr,
-                               out.n_steps ? out.n_steps + q.pix : nullptr, slot_list[wb]);
-    }
-    __syncwarp();  // the setup slots are free for the next group
+    if (r + nwarps < R) next = setup_word(w, r + nwarps, lane);
+    const RaySetup& q = setup[wb];
+    float* dep = out.depth[q.view];
+    march_ray_core<T, EXTRA>(g, s, dens, w, (int)r, q, 0u, dep ? dep + q.pix : nullptr,
+                             out.acc ? out.acc + q.pix : nullptr, out.n_steps ? out.n_steps + q.pix : nullptr,
+                             slot_list[wb]);
+    __syncwarp();  // the setup slot is free for the next ray
   }
 }
 
@@ -1165,18 +1214,6 @@ __global__ void __launch_bounds__(256) k_composite(RaySrc src, Samp s, RenderWs 
 // Batched render: every ray of every job in one launch per stage.  Rays are numbered job after
 // job, and so are bricks, so bucketing, scan and scatter run unchanged on the batch.
 
-// The job whose first ray (or first brick) is the largest one <= x, from the contiguous array of
-// the jobs' first rays (or bricks).
-__device__ __forceinline__ int job_of(const int* __restrict__ base, int n_jobs, int x) {
-  int lo = 0, hi = n_jobs;
-  while (hi - lo > 1) {
-    const int mid = (lo + hi) >> 1;
-    if (__ldg(&base[mid]) <= x) lo = mid;
-    else hi = mid;
-  }
-  return lo;
-}
-
 // Per-warp copy of the current job's geometry and sampling in shared memory, refreshed when the
 // warp's ray belongs to another job (the march reads them there, not from registers).
 struct JobCache {
@@ -1186,59 +1223,40 @@ struct JobCache {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(256, 4) k_march_batch(const JobDesc* __restrict__ jobs, const int* __restrict__ bases,
-                                                        int n_jobs, int R, RenderWs w) {
+__global__ void __launch_bounds__(256, 4) k_march_batch(const JobDesc* __restrict__ jobs, int R, RenderWs w) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   const int lane = threadIdx.x & 31;
   __shared__ JobCache cache[8];
-  __shared__ RaySetup setup[8][32];
+  __shared__ RaySetup setup[8];
   __shared__ uint8_t slot_list[8][kMaskSlots];
   const int wb = threadIdx.x >> 5;
   JobCache& C = cache[wb];
   if (lane == 0) C.job = -1;
   __syncwarp();
-  // as in k_march: lane j prepares the j-th of each group of 32 of the warp's rays (its job, ray,
-  // slots and active-slot mask, from the job's own geometry and sampling)
-  for (long long i0 = 0;; i0 += 32) {
-    const long long rl = (long long)warp + (i0 + lane) * nwarps;
-    const unsigned have = __ballot_sync(0xffffffffu, rl < R);
-    if (!have) break;
-    if (rl < R) {
-      const int j = job_of(bases, n_jobs, (int)rl);
-      const JobDesc& J = jobs[j];
-      RaySetup& q = setup[wb][lane];
-      const int pix = (int)rl - J.ray_base;
-      float o[3], d[3];
-      ray_gen_cam(J.cam, pix, o, d);
-      prepare_ray(J.geo, J.samp, o, d, q);
-      q.view = j;
-      q.pix = pix;
-    }
-    reserve_records(w, setup[wb], rl < R);
+  // as in k_march: the rays' setups (with their jobs) come from K0
+  uint32_t next = warp < R ? setup_word(w, warp, lane) : 0u;
+  for (long long r = warp; r < R; r += nwarps) {
+    if (lane < kSetupWords) reinterpret_cast<uint32_t*>(&setup[wb])[lane] = next;
     __syncwarp();
-    const int nq = __popc(have);
-    for (int jj = 0; jj < nq; jj++) {
-      const RaySetup& q = setup[wb][jj];
-      const int j = q.view;
-      const JobDesc& J = jobs[j];
-      if (C.job != j) {
-        __syncwarp();
-        constexpr int kWords = (int)((sizeof(GridGeo) + sizeof(Samp)) / 4);
-        static_assert(offsetof(JobCache, s) == sizeof(GridGeo), "cache layout");
-        static_assert(offsetof(JobDesc, samp) == offsetof(JobDesc, geo) + sizeof(GridGeo), "job layout");
-        const uint32_t* src = (const uint32_t*)&J.geo;
-        uint32_t* dst = (uint32_t*)&C.g;
-        for (int k = lane; k < kWords; k += 32) dst[k] = src[k];
-        if (lane == 0) C.job = j;
-        __syncwarp();
-      }
-      // a batch's records carry no extras (no backward, no export)
-      march_ray_core<T, false>(C.g, C.s, (const T*)J.density, w, (int)((long long)warp + (i0 + jj) * nwarps), q,
-                               (uint32_t)J.brick_base, J.depth ? J.depth + q.pix : nullptr, nullptr, nullptr,
-                               slot_list[wb], j);
+    if (r + nwarps < R) next = setup_word(w, r + nwarps, lane);
+    const RaySetup& q = setup[wb];
+    const int j = q.view;
+    const JobDesc& J = jobs[j];
+    if (C.job != j) {
+      constexpr int kWords = (int)((sizeof(GridGeo) + sizeof(Samp)) / 4);
+      static_assert(offsetof(JobCache, s) == sizeof(GridGeo), "cache layout");
+      static_assert(offsetof(JobDesc, samp) == offsetof(JobDesc, geo) + sizeof(GridGeo), "job layout");
+      const uint32_t* src = (const uint32_t*)&J.geo;
+      uint32_t* dst = (uint32_t*)&C.g;
+      for (int k = lane; k < kWords; k += 32) dst[k] = src[k];
+      if (lane == 0) C.job = j;
+      __syncwarp();
     }
-    __syncwarp();  // the setup slots are free for the next group
+    // a batch's records carry no extras (no backward, no export)
+    march_ray_core<T, false>(C.g, C.s, (const T*)J.density, w, (int)r, q, (uint32_t)J.brick_base,
+                             J.depth ? J.depth + q.pix : nullptr, nullptr, nullptr, slot_list[wb], j);
+    __syncwarp();  // the setup slot is free for the next ray
   }
 }
 
@@ -1310,6 +1328,11 @@ BrickBox brick_box(const GridGeo& geo, int elem) {
   return b;
 }
 
+// blocks of K0 (256 rays each, grid-stride beyond 8 blocks per SM)
+static int setup_blocks(long long rays) {
+  return (int)std::max(1ll, std::min((rays + 255) / 256, (long long)num_sms() * 8));
+}
+
 static int blocks_for_warps(long long warps, int per_sm) {
   long long blocks = (warps + 7) / 8;
   long long cap = (long long)num_sms() * per_sm;
@@ -1348,6 +1371,7 @@ cicero_status run_render(const cicero_grid* grid, const MlpPtrs& mlp, const Rend
     k_clear<<<std::min(num_sms() * 4, (plan.nb * kOctants + 255) / 256 + 1), 256, 0, st>>>(ws.hdr, 16, ws.brick_cnt,
                                                                                   (size_t)plan.nb * kOctants);
     const bool extra = ws.rec_k || ws.rec_ray || ws.rec_T;
+    k_ray_setup<false><<<setup_blocks(src.n_max), 256, 0, st>>>(geo, plan.samp, src, nullptr, nullptr, 0, 0, ws);
     if (f16 && extra)
       k_march<__half, true><<<mb, 256, 0, st>>>(geo, plan.samp, src, (const __half*)grid->density, ws, out);
     else if (f16)
@@ -1366,7 +1390,7 @@ cicero_status run_render(const cicero_grid* grid, const MlpPtrs& mlp, const Rend
     k_tiles<<<num_sms() * 4, 256, 0, st>>>(geo, ws);
     k_scatter<<<mb, 256, 0, st>>>(src, ws);
   }
-  count_launches(7);
+  count_launches(8);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "march/bucket kernels");
   if (stop_after_bucketing) return CICERO_OK;
@@ -1408,10 +1432,11 @@ cicero_status run_render_batch(const BatchPlan& b, cudaStream_t st) {
     ProfScope ps(kStMarch, st);
     k_clear<<<std::min(num_sms() * 4, (plan.nb * kOctants + 255) / 256 + 1), 256, 0, st>>>(ws.hdr, 16, ws.brick_cnt,
                                                                                   (size_t)plan.nb * kOctants);
+    k_ray_setup<true><<<setup_blocks(R), 256, 0, st>>>(plan.geo, plan.samp, src, b.jobs, b.bases, b.n_jobs, R, ws);
     if (b.f16)
-      k_march_batch<__half><<<mb, 256, 0, st>>>(b.jobs, b.bases, b.n_jobs, R, ws);
+      k_march_batch<__half><<<mb, 256, 0, st>>>(b.jobs, R, ws);
     else
-      k_march_batch<float><<<mb, 256, 0, st>>>(b.jobs, b.bases, b.n_jobs, R, ws);
+      k_march_batch<float><<<mb, 256, 0, st>>>(b.jobs, R, ws);
   }
   {
     ProfScope ps(kStBucket, st);
@@ -1422,7 +1447,7 @@ cicero_status run_render_batch(const BatchPlan& b, cudaStream_t st) {
     k_tiles_batch<<<num_sms() * 4, 256, 0, st>>>(b.jobs, b.bases, b.n_jobs, ws);
     k_scatter<<<mb, 256, 0, st>>>(src, ws);
   }
-  count_launches(7);
+  count_launches(8);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "batched march/bucket kernels");
   cicero_status s = launch_gather_mlp_bf16_batch(b, st);
