@@ -113,17 +113,39 @@ constexpr int kMaskSlots = 32 * kMaskWords;
 constexpr int kStateHigh = 0x7fffffff;          // past the box along an axis
 constexpr uint32_t kNoRoom = 0xffffffffu;       // a ray whose records found no room
 
-// State of slot k along axis a: -1 before the box, kStateHigh past it, otherwise the occupancy cell
-// (0 when the grid has no mask).  The operations are those of index_sample, in the same order.
-__device__ __forceinline__ int axis_state(const GridGeo& g, const Slots& sl, float o, float d, int a, int k) {
+// One axis of a ray and of the grid, as the index test sees it.
+struct AxisP {
+  float o, d, inv_d;       // ray origin and direction along the axis, 1/d (0 when d = 0)
+  float amin, inv_h, top;  // box minimum, vertices per unit length, n - 1
+  float occ_scale;         // occupancy cells per vertex step
+};
+
+__device__ __forceinline__ AxisP axis_p(const GridGeo& g, const float o[3], const float d[3], const float inv_d[3],
+                                        int a) {
+  auto pick = [a](float x0, float x1, float x2) { return a == 0 ? x0 : (a == 1 ? x1 : x2); };
+  AxisP A;
+  A.o = pick(o[0], o[1], o[2]);
+  A.d = pick(d[0], d[1], d[2]);
+  A.inv_d = pick(inv_d[0], inv_d[1], inv_d[2]);
+  A.amin = pick(g.amin[0], g.amin[1], g.amin[2]);
+  A.inv_h = pick(g.inv_h[0], g.inv_h[1], g.inv_h[2]);
+  A.top = pick((float)(g.n[0] - 1), (float)(g.n[1] - 1), (float)(g.n[2] - 1));
+  A.occ_scale = pick(g.occ_scale[0], g.occ_scale[1], g.occ_scale[2]);
+  return A;
+}
+
+// State of slot k along an axis: -1 before the box, kStateHigh past it, otherwise the occupancy
+// cell (0 when the grid has no mask, R = 0).  The operations are those of index_sample, in the
+// same order.
+__device__ __forceinline__ int axis_state(const AxisP& A, int R, const Slots& sl, int k) {
   const float t = slot_t(sl, k);
-  const float p = __fadd_rn(o, __fmul_rn(t, d));
-  const float ga = __fmul_rn(__fsub_rn(p, g.amin[a]), g.inv_h[a]);
+  const float p = __fadd_rn(A.o, __fmul_rn(t, A.d));
+  const float ga = __fmul_rn(__fsub_rn(p, A.amin), A.inv_h);
   if (!(ga >= 0.0f)) return -1;
-  if (!(ga <= (float)(g.n[a] - 1))) return kStateHigh;
-  if (!g.occ) return 0;
-  const int c = (int)floorf(__fmul_rn(ga, g.occ_scale[a]));
-  return c > g.occ_res - 1 ? g.occ_res - 1 : c;
+  if (!(ga <= A.top)) return kStateHigh;
+  if (!R) return 0;
+  const int c = (int)floorf(__fmul_rn(ga, A.occ_scale));
+  return c > R - 1 ? R - 1 : c;
 }
 
 // Smallest k in (lo, hi] with P(k), for a predicate that is false up to some slot and true after
@@ -164,22 +186,22 @@ __device__ __forceinline__ int first_true(int lo, int hi, float est, Pred P) {
   return hi;
 }
 
-// First slot after k whose state along axis a differs from s = axis_state(k); kend if none before it.
-__device__ __forceinline__ int next_change(const GridGeo& g, const Slots& sl, float o, float d, float inv_d,
-                                           float inv_dt, int a, int k, int s, int kend) {
-  if (d == 0.0f) return kend;  // the coordinate does not change along the ray
-  const int R = g.occ ? g.occ_res : 1;
+// First slot after k whose state along the axis differs from s = axis_state(k); kend if none before it.
+__device__ __forceinline__ int next_change(const AxisP& A, int R, const Slots& sl, float inv_dt, int k, int s,
+                                           int kend) {
+  if (A.d == 0.0f) return kend;  // the coordinate does not change along the ray
+  const int Rc = R ? R : 1;
   float B;  // the vertex coordinate where the state changes
-  if (d > 0.0f) {
+  if (A.d > 0.0f) {
     if (s == kStateHigh) return kend;
-    B = s < 0 ? 0.0f : (s < R - 1 ? __fdividef((float)(s + 1), g.occ_scale[a]) : (float)(g.n[a] - 1));
+    B = s < 0 ? 0.0f : (s < Rc - 1 ? __fdividef((float)(s + 1), A.occ_scale) : A.top);
   } else {
     if (s < 0) return kend;
-    B = s == kStateHigh ? (float)(g.n[a] - 1) : (s > 0 ? __fdividef((float)s, g.occ_scale[a]) : 0.0f);
+    B = s == kStateHigh ? A.top : (s > 0 ? __fdividef((float)s, A.occ_scale) : 0.0f);
   }
-  const float tb = (g.amin[a] + __fdividef(B, g.inv_h[a]) - o) * inv_d;
+  const float tb = (A.amin + __fdividef(B, A.inv_h) - A.o) * A.inv_d;
   const float est = ceilf((tb - sl.t0) * inv_dt - 0.5f);
-  return first_true(k, kend, est, [&](int kk) { return axis_state(g, sl, o, d, a, kk) != s; });
+  return first_true(k, kend, est, [&](int kk) { return axis_state(A, R, sl, kk) != s; });
 }
 
 __device__ __forceinline__ void set_bits(uint32_t* mask, int k, int e) {
@@ -190,43 +212,50 @@ __device__ __forceinline__ void set_bits(uint32_t* mask, int k, int e) {
   }
 }
 
-// Mask of the active slots among the first kend (<= kMaskSlots) slots of a ray; returns their count.
+// Mask of the active slots among the first kend (<= kMaskSlots) slots of a ray; returns their
+// count.  Each pass takes the segment of slots up to the next state change on any axis, then moves
+// the one axis that changes there (ties take one pass each, the later ones with empty segments), so
+// every lane of a warp runs the same instructions whichever axis its ray crosses.
 __device__ __forceinline__ int active_mask(const GridGeo& g, const Slots& sl, const float o[3], const float d[3],
                                            int kend, uint32_t* mask) {
 #pragma unroll
   for (int w = 0; w < kMaskWords; w++) mask[w] = 0u;
   if (kend <= 0) return 0;
+  const int R = g.occ ? g.occ_res : 0;
   const float inv_dt = __fdividef(1.0f, sl.dt);
   float inv_d[3];
+#pragma unroll
+  for (int a = 0; a < 3; a++) inv_d[a] = d[a] != 0.0f ? __fdividef(1.0f, d[a]) : 0.0f;
   int st[3], nx[3];
 #pragma unroll
   for (int a = 0; a < 3; a++) {
-    inv_d[a] = d[a] != 0.0f ? __fdividef(1.0f, d[a]) : 0.0f;
-    st[a] = axis_state(g, sl, o[a], d[a], a, 0);
-    nx[a] = next_change(g, sl, o[a], d[a], inv_d[a], inv_dt, a, 0, st[a], kend);
+    const AxisP A = axis_p(g, o, d, inv_d, a);
+    st[a] = axis_state(A, R, sl, 0);
+    nx[a] = next_change(A, R, sl, inv_dt, 0, st[a], kend);
   }
   int k = 0, count = 0;
-  for (;;) {  // every pass moves k forward by at least one slot
+  for (;;) {  // every pass moves k forward or settles one of the axes that change at k
     const int e = min(nx[0], min(nx[1], nx[2]));
-    bool on = true;
+    bool on = e > k;
 #pragma unroll
     for (int a = 0; a < 3; a++) on = on && st[a] >= 0 && st[a] != kStateHigh;
-    if (on && g.occ) {
-      const int R = g.occ_res;
-      on = __ldg(&g.occ[((size_t)st[2] * R + st[1]) * R + st[0]]) != 0;
-    }
+    if (on && R) on = __ldg(&g.occ[((size_t)st[2] * R + st[1]) * R + st[0]]) != 0;
     if (on) {
       set_bits(mask, k, e);
       count += e - k;
     }
     if (e >= kend) break;
     k = e;
-#pragma unroll
-    for (int a = 0; a < 3; a++)
-      if (nx[a] == e) {
-        st[a] = axis_state(g, sl, o[a], d[a], a, e);
-        nx[a] = next_change(g, sl, o[a], d[a], inv_d[a], inv_dt, a, e, st[a], kend);
-      }
+    const int a = nx[0] == e ? 0 : (nx[1] == e ? 1 : 2);
+    const AxisP A = axis_p(g, o, d, inv_d, a);
+    const int sa = axis_state(A, R, sl, e);
+    const int na = next_change(A, R, sl, inv_dt, e, sa, kend);
+    st[0] = a == 0 ? sa : st[0];
+    st[1] = a == 1 ? sa : st[1];
+    st[2] = a == 2 ? sa : st[2];
+    nx[0] = a == 0 ? na : nx[0];
+    nx[1] = a == 1 ? na : nx[1];
+    nx[2] = a == 2 ? na : nx[2];
   }
   return count;
 }
