@@ -52,6 +52,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-extra", action="store_true", help="skip the backward and small-scene SpaRW reports")
     p.add_argument("--cpu-res", type=int, default=100, help="oracle sample resolution (square)")
+    p.add_argument("--oracle-full-window", action="store_true",
+                   help="reference arm: also time one full-resolution oracle window (minutes on the host)")
     p.add_argument("--case", default="full", choices=["full", "small", "backward"],
                    help="small: one 320x320 reference frame (BF16 and FP32) and two targets, for profilers; "
                         "backward: the differentiation workload alone")
@@ -276,25 +278,40 @@ def oracle_threads(g, m, cam, R, n_pix=2048):
 
 
 def run_reference(args, rank, world, window=None):
-    """The oracle arm: rank 0 alone times the oracle; the other ranks exit without work."""
+    """The oracle arm: rank 0 alone times the oracle; the other ranks exit without work.  A step is
+    the oracle's whole SpaRW window at a reduced resolution (a bounded sample of the workload);
+    `ms_per_step` is the time of that sample, `value` the 800x800 rate it extrapolates to by the
+    pixel ratio (stated in `sample`).  With --oracle-full-window one full-resolution window is timed
+    as well."""
     if rank != 0:
         return None
     window = window or oracle_window
+    res = args.cpu_res
+    for _ in range(max(0, args.warmup)):
+        window(res)
     dts = []
     for _ in range(max(1, args.steps)):
-        dt, cores, _ = window(args.cpu_res)
+        dt, cores, _ = window(res)
         dts.append(dt)
-    scale = (W * H) / (args.cpu_res * args.cpu_res)
-    t_step = float(np.mean(dts)) * scale
-    fps = N_TARGETS / t_step
+    scale = (W * H) / (res * res)
+    t_sample = float(np.mean(dts))
+    t_full = t_sample * scale
+    fps = N_TARGETS / t_full
+    sample = {"resolution": f"{res}x{res}", "pixels_per_frame": res * res, "full_pixels_per_frame": W * H,
+              "scale": scale, "ms_per_full_window_extrapolated": t_full * 1e3,
+              "what": "whole SpaRW window (reference render, 16 warps, 16 hole renders), FP64"}
     line = {"impl": "reference", "metric": METRIC, "value": fps, "unit": "frames/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": 0, "ms_per_step": t_step * 1e3, "higher_is_better": True,
+            "steps": len(dts), "warmup": max(0, args.warmup), "ms_per_step": t_sample * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
+            "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"}, "sample": sample,
             "cpu_baseline": {"value": fps, "unit": "frames/s", "cores": cores, "kind": "oracle",
-                             "sample": f"whole SpaRW window at {args.cpu_res}x{args.cpu_res} "
-                                       f"({args.cpu_res**2} of {W*H} pixels per frame), time x {scale:.0f}"},
+                             "sample": f"whole SpaRW window at {res}x{res} ({res * res} of {W * H} pixels per "
+                                       f"frame), time x {scale:.0f}"},
             "e2e": {"value": fps, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    if getattr(args, "oracle_full_window", False):
+        dt, _, _ = window(W)
+        line["full_window"] = {"resolution": f"{W}x{H}", "ms": dt * 1e3, "frames_per_s": N_TARGETS / dt,
+                               "extrapolation_error": t_full / dt - 1.0}
     print(json.dumps(line), flush=True)
     return line
 
@@ -508,7 +525,7 @@ SWEEP_WINDOWS = (6, 16, 21, 26, 30)
 SWEEP_FRAMES = 120
 
 
-def window_sweep(cc, torch, dev, grid, mlp, o16):
+def window_sweep(cc, torch, dev, grid, mlp, o16, sampling=None, label=None):
     """SpaRW over a 120-frame trajectory on the 800x800 scene (the camera orbits the object at
     0.5 deg of azimuth per frame, looking at it: a 60 deg arc) with the reference of each window
     rendered on a second stream (cicero_pipeline, Sec. III-C), for windows of 6 .. 30 targets (the
@@ -516,7 +533,7 @@ def window_sweep(cc, torch, dev, grid, mlp, o16):
     rendering every frame in full (BF16), and PSNR of the frames against those full renders (every
     pixel; a frame identical to its full render counts as 100 dB in the mean)."""
     import scenes
-    cam = scenes.orbit_camera(W, H, sampling=scenes.sampling_march(256, 256))
+    cam = scenes.orbit_camera(W, H, sampling=sampling or scenes.sampling_march(256, 256))
     traj = [scenes.orbit_camera(W, H, az_deg=30.0 + 0.5 * k, sampling=cam.sampling) for k in range(SWEEP_FRAMES)]
     targets = [cc.camera_from(t) for t in traj]
     R = W * H
@@ -555,6 +572,8 @@ def window_sweep(cc, torch, dev, grid, mlp, o16):
     frames = [torch.empty(R, 3, device=dev) for _ in traj]
     s_ref = torch.cuda.Stream(dev)
     res = {"frames": SWEEP_FRAMES, "full_render_fps": SWEEP_FRAMES / (t_full / 1e3), "ds2": ds2_res, "windows": []}
+    if label:
+        res["scene"] = label
     for N, lead in [(n, "centred") for n in SWEEP_WINDOWS] + [(16, "paper")]:
         hole_records = N * R * 40  # ~16% of the window's slots
         ws = cc.workspace(cc.cicero_pipeline_workspace_size(grid.desc, cd, sd, o16, N, hole_records), dev)
@@ -727,13 +746,47 @@ def backward_workload(cc, torch, dev):
             "grad_bytes": int(dd.numel() * 4 + df.numel() * 4)}
 
 
-def sparw_small_scene(cc, torch, dev, n_pix=1024):
-    """SpaRW on the 64^3 scene: reference 800x800 at the orbit pose (64 uniform samples), 16 targets
-    warped and hole-rendered (BF16 MLP).  Per target: fraction of rays marched and PSNR against
-    the FP64 oracle on n_pix sampled pixels; the window's device time."""
+def plain_small(cc, torch, dev):
+    """Config 1: a plain render of the 64^3 scene, 64x64 pixels, 64 uniform samples, FP32 and BF16
+    MLP; device ms per frame (CUDA events, 20 renders) and the error of every pixel against the FP64
+    oracle (the better outcome on the rays whose early stop is ambiguous)."""
     import oracle
     import scenes
     g, m = scenes.scene_small(), scenes.make_mlp(12)
+    cam = scenes.orbit_camera(64, 64, sampling=scenes.sampling_uniform(64))
+    gd, md = cc.DeviceGrid.from_host(g, dev), cc.DeviceMlp.from_host(m, dev)
+    sd, cd = cc.sampling_from(cam.sampling), cc.camera_from(cam)
+    R = 64 * 64
+    ref = oracle.render(g, m, cam.sampling, cam=cam)
+    out = {"workload": "64^3 x 12 FP32 scene (8 blobs), 64x64, 64 uniform samples in [0.5, 2.5], t_stop 1e-3",
+           "ambiguous_rays": int(ref["amb"].sum())}
+    for name, prec in (("fp32", cc.MLP_FP32), ("bf16", cc.MLP_BF16)):
+        opt = cc.options(prec, 8)
+        ws = cc.workspace(cc.cicero_render_workspace_size(gd.desc, R, sd, opt), dev)
+        rgb, depth = torch.empty(R, 3, device=dev), torch.empty(R, device=dev)
+
+        def render():
+            cc.cicero_render(gd.desc, md.desc, cd, sd, opt, rgb, depth, None, None, ws)
+
+        ms = event_ms(torch, render, 20)
+        cc.cicero_workspace_status(ws)
+        got = rgb.cpu().double().numpy()
+        e = np.where(ref["amb"][:, None], np.minimum(np.abs(got - ref["rgb"]), np.abs(got - ref["rgb_alt"])),
+                     np.abs(got - ref["rgb"]))
+        out[name] = {"ms": ms, "max_err": float(e.max()),
+                     "psnr_db": 10 * math.log10(1.0 / max(float(np.mean(e ** 2)), 1e-30))}
+    return out
+
+
+def sparw_small_scene(cc, torch, dev, n_pix=1024, opaque=False):
+    """SpaRW on the 64^3 scene: reference 800x800 at the orbit pose (64 uniform samples), 16 targets
+    warped and hole-rendered (BF16 MLP).  Per target: fraction of rays marched and PSNR against
+    the FP64 oracle's full render of the target on n_pix sampled pixels (SpaRW's approximation
+    error, not gated); the window's device time.  opaque: the blobs scaled to opaque surfaces."""
+    import oracle
+    import scenes
+    g = scenes.scene_small_opaque() if opaque else scenes.scene_small()
+    m = scenes.make_mlp(12)
     cam = scenes.orbit_camera(W, H, sampling=scenes.sampling_uniform(64))
     targets = [scenes.offset_camera(cam, k) for k in scenes.SPARW_OFFSETS]
     R, n_t = W * H, len(targets)
@@ -760,7 +813,11 @@ def sparw_small_scene(cc, torch, dev, n_pix=1024):
     for i, p in enumerate(per):
         p.update({"disocclusion_holes": int(disocc[i]), "void_holes": int(void[i]),
                   "fraction_void": float(void[i]) / R})
+    scene = (f"opaque surfaces (blob amplitudes x {scenes.OPAQUE_AMP_SCALE:g}: rays stop within a sample or two "
+             f"of a blob, the expected depth is a surface)" if opaque
+             else "fog-like blobs (amplitudes U[10, 40]: ~50 composited samples per ray)")
     return {"workload": "64^3 x 12 FP32 scene, 800x800, 64 samples, 16 targets (1 deg yaw + 5 mm apart)",
+            "scene": scene,
             "window_ms": t_win, "target_fps": n_t / (t_win / 1e3), "psnr_pixels_per_target": n_pix,
             "psnr_db_min": min(p["psnr_db"] for p in per), "fraction_marched_mean": float(holes.sum()) / (n_t * R),
             "marched": "disocclusion and void holes (a void hole's march composites nothing)", "targets": per}
@@ -962,6 +1019,11 @@ def main():
         quality = {"ref_bf16_max_err": float(e.max()),
                    "ref_bf16_psnr_db": float(10 * math.log10(1.0 / max(float(np.mean(e ** 2)), 1e-30))),
                    "sample_pixels": int(len(pix))}
+        full(o32)
+        got = win.ref_rgb.cpu().double().numpy()[pix]
+        e = np.where(ref["amb"][:, None], np.minimum(np.abs(got - ref["rgb"]), np.abs(got - ref["rgb_alt"])),
+                     np.abs(got - ref["rgb"]))
+        quality["ref_fp32_max_err"] = float(e.max())
         frames = []
         dt, cores, _ = oracle_window(args.cpu_res, rank, frames)
         quality["sparw_bf16_vs_oracle_sparw"] = sparw_parity(cc, torch, dev, grid, mlp, args.cpu_res, rank, frames,
@@ -975,9 +1037,16 @@ def main():
     others = {}
     if rank == 0 and not args.no_extra:
         others["config_backward"] = backward_workload(cc, torch, dev)
+        others["config_plain_64"] = plain_small(cc, torch, dev)
         others["config_sparw_small_scene"] = sparw_small_scene(cc, torch, dev)
+        others["config_sparw_opaque_scene"] = sparw_small_scene(cc, torch, dev, opaque=True)
         others["config_batched"] = batched_workload(cc, torch, dev)
         others["sparw_window_sweep"] = window_sweep(cc, torch, dev, grid, mlp, o16)
+        g_op = cc.DeviceGrid.from_host(scenes.scene_small_opaque(), dev)
+        others["sparw_window_sweep_opaque_scene"] = window_sweep(
+            cc, torch, dev, g_op, cc.DeviceMlp.from_host(scenes.make_mlp(12), dev), cc.options(cc.MLP_BF16, 8),
+            sampling=scenes.sampling_uniform(64), label="64^3 opaque-surface scene, 64 uniform samples")
+        del g_op
         others["sparw_phi_sweep"] = phi_sweep(cc, torch, dev, grid, o16, active)
         others["config_hash_grid"] = hash_workload(cc, torch, dev, grid, g_h)
 

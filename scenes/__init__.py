@@ -163,11 +163,11 @@ class Camera:
 # grids
 
 
-def blob_density(N: int, n_blobs: int, seed: int, aabb=(-1.0, 1.0)) -> np.ndarray:
+def blob_density(N: int, n_blobs: int, seed: int, aabb=(-1.0, 1.0), amp_scale: float = 1.0) -> np.ndarray:
     """Sum of isotropic Gaussian blobs sampled at the vertices, float64 [N][N][N].
 
     Per blob, in draw order: centre (x, y, z) ~ U[-0.6, 0.6], width s ~ U[0.06, 0.2],
-    amplitude A ~ U[10, 40]; the value at vertex p is A * exp(-|p - mu|^2 / (2 s^2)).
+    amplitude A ~ amp_scale U[10, 40]; the value at vertex p is A * exp(-|p - mu|^2 / (2 s^2)).
     """
     d = uniform(stream_seed(seed, 1), 5 * n_blobs)
     lo, hi = aabb
@@ -176,7 +176,7 @@ def blob_density(N: int, n_blobs: int, seed: int, aabb=(-1.0, 1.0)) -> np.ndarra
     for b in range(n_blobs):
         mu = -0.6 + 1.2 * d[5 * b: 5 * b + 3]
         s = 0.06 + 0.14 * d[5 * b + 3]
-        amp = 10.0 + 30.0 * d[5 * b + 4]
+        amp = amp_scale * (10.0 + 30.0 * d[5 * b + 4])
         gx = np.exp(-((x - mu[0]) ** 2) / (2 * s * s))
         gy = np.exp(-((x - mu[1]) ** 2) / (2 * s * s))
         gz = np.exp(-((x - mu[2]) ** 2) / (2 * s * s))
@@ -224,8 +224,8 @@ def occupancy_mask(raw: np.ndarray, R: int, frac: float) -> np.ndarray:
 
 
 def make_grid(N: int, C: int, n_blobs: int, seed: int = SEED_SCENE, dtype=np.float32,
-              occ_res: int = 0, occ_frac: float = 0.15) -> Grid:
-    raw = blob_density(N, n_blobs, seed)
+              occ_res: int = 0, occ_frac: float = 0.15, amp_scale: float = 1.0) -> Grid:
+    raw = blob_density(N, n_blobs, seed, amp_scale=amp_scale)
     feat = smoothed_features(N, C, seed)
     occ = occupancy_mask(raw, occ_res, occ_frac) if occ_res else None
     return Grid((N, N, N), C, raw.astype(dtype), feat.astype(dtype), occ=occ)
@@ -355,6 +355,16 @@ def with_hash(g: Grid, h: HashGrid) -> Grid:
 def scene_small(dtype=np.float32) -> Grid:
     """64^3 grid, 8 blobs, 12 feature channels (the small single-view scene)."""
     return make_grid(64, 12, 8, SEED_SCENE, dtype)
+
+
+OPAQUE_AMP_SCALE = 25.0
+
+
+def scene_small_opaque(dtype=np.float32) -> Grid:
+    """The small scene with every blob amplitude x 25 (A ~ U[250, 1000]): a ray stops within a
+    sample or two of entering a blob, so the expected depth is the blob's surface, as with the
+    solid objects of the paper's scenes (the fog-like default blobs composite ~100 samples)."""
+    return make_grid(64, 12, 8, SEED_SCENE, dtype, amp_scale=OPAQUE_AMP_SCALE)
 
 
 def scene_large() -> Grid:

@@ -33,7 +33,7 @@ def _worker(rank, world, port, out_dir):
     res["azimuth"] = bench.rank_azimuth(rank)
 
     class Args:
-        steps, cpu_res, gpus = 2, 8, world
+        steps, warmup, cpu_res, gpus = 2, 1, 8, world
 
     calls = []
 
@@ -61,12 +61,17 @@ def test_two_gloo_ranks(tmp_path, capfd):
     # weak scaling: the ranks render different windows
     assert res[0]["azimuth"] != res[1]["azimuth"]
     # reference arm: rank 0 times the oracle and prints one line, rank 1 does no work
-    assert res[0]["reference_calls"] == 2 and res[1]["reference_calls"] == 0
+    assert res[0]["reference_calls"] == 3 and res[1]["reference_calls"] == 0  # 1 warm-up + 2 timed
+
     assert res[1]["reference"] is None
     line = res[0]["reference"]
     assert line["impl"] == "reference" and line["cpu_baseline"]["kind"] == "oracle"
     scale = (800 * 800) / (8 * 8)
     assert line["value"] == pytest.approx(16 / (0.25 * scale))
+    # the steps and their time are what ran (the sample); the extrapolation is stated beside them
+    assert line["steps"] == 2 and line["warmup"] == 1 and line["ms_per_step"] == pytest.approx(250.0)
+    assert line["sample"]["scale"] == pytest.approx(scale) and line["sample"]["resolution"] == "8x8"
+    assert line["sample"]["ms_per_full_window_extrapolated"] == pytest.approx(250.0 * scale)
     assert line["e2e"]["h2d_bytes_per_step"] == 0
     printed = [l for l in capfd.readouterr().out.splitlines() if l.startswith("{")]
     assert len(printed) == 1 and json.loads(printed[0])["impl"] == "reference"
