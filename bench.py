@@ -461,8 +461,9 @@ def batched_workload(cc, torch, dev, n_check=8, reps=5):
     cap = int(0.45 * rs)  # composited samples are ~35% of the slots here; a shortfall is reported
     opt4 = cc.options(cc.MLP_BF16, 4, max_records=cap)
     ws = cc.workspace(cc.cicero_batch_workspace_size(jobs, opt4), dev)
-    brick, tune = cc.cicero_batch_autotune_brick(jobs, opt4, ws)
-    opt = cc.options(cc.MLP_BF16, brick, max_records=cap)
+    tuned, tune = cc.cicero_batch_autotune(jobs, opt4, ws)
+    brick, groups = tuned.brick, tuned.mlp_groups
+    opt = cc.options(cc.MLP_BF16, brick, max_records=cap, mlp_groups=groups)
     b = cc.Batch(jobs, opt, ws)
     b.launch()  # outside the capture: kernel attributes
     torch.cuda.synchronize()
@@ -476,7 +477,7 @@ def batched_workload(cc, torch, dev, n_check=8, reps=5):
     t_batch = event_ms(torch, graph.replay, reps)
     b.status()
     # the same jobs one cicero_render at a time (one workspace, sized for the largest job)
-    o1 = cc.options(cc.MLP_BF16, brick)
+    o1 = cc.options(cc.MLP_BF16, brick, mlp_groups=groups)
     big = max(cc.cicero_render_workspace_size(sc[si][2].desc, c.width * c.height, keep[j][1], o1)
               for j, (si, c, _) in enumerate(specs))
     ws1 = cc.workspace(big, dev)
@@ -514,10 +515,12 @@ def batched_workload(cc, torch, dev, n_check=8, reps=5):
     b.close()
     return {"workload": f"{BATCH_JOBS} jobs: grids 96^3..256^3 x 12 FP16 (6 scenes, own MLPs), images 256^2..1024^2, "
                         "64..256 samples per ray", "rays": rays, "composited_samples": samples,
-            "brick": brick, "autotune_ms_by_brick": tune, "batch_ms": t_batch,
+            "brick": brick, "mlp_groups": groups,
+            "autotune_ms": {f"brick{k[0]}_groups{k[1]}": v for k, v in tune.items() if v > 0},
+            "batch_ms": t_batch,
             "jobs_per_s": BATCH_JOBS / (t_batch / 1e3), "msamples_per_s": samples / (t_batch / 1e3) / 1e6,
             "one_call_per_job_ms": t_single, "speedup_vs_one_call_per_job": t_single / t_batch,
-            "launch": "one CUDA graph (9 kernels for all jobs)", "record_capacity": cap, "stage_ms": stage_ms,
+            "launch": "one CUDA graph (10 kernels for all jobs)", "record_capacity": cap, "stage_ms": stage_ms,
             "oracle_check": {"pixels": n // 3, "max_err": worst, "psnr_db": 10 * math.log10(1.0 / max(sq / n, 1e-30))}}
 
 

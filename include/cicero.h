@@ -112,6 +112,8 @@ typedef struct {
     cicero_precision precision;
     int brick;          /* voxels per brick edge ("MVoxel", Sec. IV-A): 4, 8 or 16; 0 = 8 */
     long long max_records;
+    int mlp_groups;     /* BF16 tensor-core MLP: 128-sample tiles in flight per SM (each tile runs its
+                           own gather -> layer 1 -> 2 -> 3 chain), 1..4; 0 = as many as fit */
 } cicero_options;
 
 /* ---------------------------------------------------------------------------------------------
@@ -217,13 +219,15 @@ cicero_status cicero_batch_create(const cicero_job *jobs, int n_jobs, const cice
 cicero_status cicero_batch_launch(const cicero_batch *batch, void *stream);
 cicero_status cicero_batch_destroy(cicero_batch *batch);
 
-/* Brick-size autotuner of a batch: creates, launches once untimed and once timed with bricks of
- * 4, 8 and 16 voxels (each that fits ws_bytes) and returns the fastest in *best_brick; ms[3]
- * (may be NULL) the timed milliseconds (-1 = not tried).  Size the workspace with brick 4.
- * Synchronises `stream`; leaves no handle behind (create one with the chosen brick). */
-cicero_status cicero_batch_autotune_brick(const cicero_job *jobs, int n_jobs, const cicero_options *opt,
-                                          void *workspace, size_t ws_bytes, void *stream,
-                                          int *best_brick, float *ms);
+/* Autotuner of a batch: creates the batch and launches it once untimed and once timed for every
+ * brick of 4, 8 and 16 voxels and every count of MLP tiles in flight per SM (mlp_groups 1..4) that
+ * fit ws_bytes and the kernels' shared memory, and writes the fastest into *best (a copy of opt with
+ * brick and mlp_groups set).  ms [3][4] (may be NULL) receives the timed milliseconds, row = brick
+ * 4 / 8 / 16, column = mlp_groups 1..4 (-1 = not tried).  Size the workspace with brick 4.
+ * Synchronises `stream`; leaves no handle behind (create one with *best). */
+cicero_status cicero_batch_autotune(const cicero_job *jobs, int n_jobs, const cicero_options *opt,
+                                    void *workspace, size_t ws_bytes, void *stream, cicero_options *best,
+                                    float *ms);
 
 /* ---------------------------------------------------------------------------------------------
  * Hash-encoded rendering (the hierarchical-encoding workload of Sec. IV-A "Accommodating

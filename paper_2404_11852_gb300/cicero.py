@@ -48,7 +48,7 @@ class Camera(C.Structure):
 
 
 class Options(C.Structure):
-    _fields_ = [("precision", C.c_int), ("brick", C.c_int), ("max_records", C.c_longlong)]
+    _fields_ = [("precision", C.c_int), ("brick", C.c_int), ("max_records", C.c_longlong), ("mlp_groups", C.c_int)]
 
 
 class HashGridDesc(C.Structure):
@@ -87,7 +87,7 @@ _SIGS = {
     "cicero_batch_create": ([_P, C.c_int, _P, _P, _Z, _P], C.c_int),
     "cicero_batch_launch": ([_P, _P], C.c_int),
     "cicero_batch_destroy": ([_P], C.c_int),
-    "cicero_batch_autotune_brick": ([_P, C.c_int, _P, _P, _Z, _P, _P, _P], C.c_int),
+    "cicero_batch_autotune": ([_P, C.c_int, _P, _P, _Z, _P, _P, _P], C.c_int),
     "cicero_extrapolate_pose": ([_P, _P, C.c_float, _P], C.c_int),
     "cicero_render_hash": ([_P] * 8 + [_P, _Z, _P], C.c_int),
     "cicero_render_hash_workspace_size": ([_P, _P, C.c_int, _P, _P], _Z),
@@ -223,9 +223,9 @@ def camera_from(cam) -> Camera:
     return camera(cam.width, cam.height, cam.f, cam.cx, cam.cy, cam.c2w)
 
 
-def options(precision: int = MLP_FP32, brick: int = 8, max_records: int = 0) -> Options:
+def options(precision: int = MLP_FP32, brick: int = 8, max_records: int = 0, mlp_groups: int = 0) -> Options:
     o = Options()
-    o.precision, o.brick, o.max_records = precision, brick, max_records
+    o.precision, o.brick, o.max_records, o.mlp_groups = precision, brick, max_records, mlp_groups
     return o
 
 
@@ -454,12 +454,13 @@ class Batch:
             pass
 
 
-def cicero_batch_autotune_brick(jobs, opt: Options, ws: torch.Tensor, stream=None):
+def cicero_batch_autotune(jobs, opt: Options, ws: torch.Tensor, stream=None):
+    """Returns the fastest Options (brick and mlp_groups set) and the timed ms per (brick, mlp_groups)."""
     p, n = _ws(ws)
-    best = C.c_int(0)
-    ms = (C.c_float * 3)()
-    _check(lib().cicero_batch_autotune_brick(jobs, len(jobs), C.byref(opt), p, n, _stream(stream), C.byref(best), ms))
-    return int(best.value), {b: float(ms[i]) for i, b in enumerate((4, 8, 16))}
+    best = Options()
+    ms = (C.c_float * 12)()
+    _check(lib().cicero_batch_autotune(jobs, len(jobs), C.byref(opt), p, n, _stream(stream), C.byref(best), ms))
+    return best, {(b, g): float(ms[4 * i + g - 1]) for i, b in enumerate((4, 8, 16)) for g in range(1, 5)}
 
 
 def cicero_extrapolate_pose(prev: Camera, cur: Camera, lead: float) -> Camera:

@@ -236,6 +236,8 @@ static cicero_status plan_render(const cicero_grid* grid, const cicero_mlp* mlp,
   p->precision = opt ? opt->precision : CICERO_MLP_FP32;
   if (p->precision != CICERO_MLP_FP32 && p->precision != CICERO_MLP_BF16)
     return fail(CICERO_ERR_INVALID_ARG, "precision");
+  p->mlp_groups = opt ? opt->mlp_groups : 0;
+  if (p->mlp_groups < 0 || p->mlp_groups > 4) return fail(CICERO_ERR_INVALID_ARG, "mlp_groups must be 0..4");
   return CICERO_OK;
 }
 
@@ -405,10 +407,30 @@ static cicero_status plan_batch(const cicero_job* jobs, int n_jobs, const cicero
   if (!opt || opt->precision != CICERO_MLP_BF16)
     return fail(CICERO_ERR_UNSUPPORTED, "batched rendering runs the BF16 tensor-core MLP only");
   const int brick = opt->brick ? opt->brick : 8;
+  if (opt->mlp_groups < 0 || opt->mlp_groups > 4) return fail(CICERO_ERR_INVALID_ARG, "mlp_groups must be 0..4");
   memset(b, 0, sizeof *b);
+  b->mlp_groups = opt->mlp_groups;
   unsigned long long R = 0, Q = 0, nb = 0;
   int S = 0;
-  for (int j = 0; j < n_jobs; j++) {
+  // table order: jobs that share MLP weights side by side (in the caller's order otherwise), so the
+  // persistent gather loads each set of weights once per CTA range; every job still writes its own
+  // outputs, so the order is not visible to the caller
+  std::vector<int> order((size_t)n_jobs);
+  {
+    std::vector<char> taken((size_t)n_jobs, 0);
+    int k = 0;
+    for (int j = 0; j < n_jobs; j++) {
+      if (taken[j]) continue;
+      if (!jobs[j].mlp) return fail(CICERO_ERR_INVALID_ARG, "a job field is NULL");
+      for (int i = j; i < n_jobs; i++)
+        if (!taken[i] && jobs[i].mlp && same_mlp(mlp_ptrs(jobs[i].mlp), mlp_ptrs(jobs[j].mlp))) {
+          order[k++] = i;
+          taken[i] = 1;
+        }
+    }
+  }
+  for (int jt = 0; jt < n_jobs; jt++) {
+    const int j = order[jt];
     const cicero_job& J = jobs[j];
     if (!J.grid || !J.mlp || !J.cam || !J.sampling || !J.rgb) return fail(CICERO_ERR_INVALID_ARG, "a job field is NULL");
     GridGeo geo;
@@ -418,7 +440,7 @@ static cicero_status plan_batch(const cicero_job* jobs, int n_jobs, const cicero
     if (st == CICERO_OK) st = check_cam(J.cam);
     if (st == CICERO_OK) st = check_mlp(J.mlp, J.grid);
     if (st != CICERO_OK) return st;
-    if (j == 0) {
+    if (jt == 0) {
       b->f16 = J.grid->dtype == CICERO_F16;
       b->C = J.grid->C;
       b->n_freq = J.mlp->n_freq;
@@ -428,7 +450,7 @@ static cicero_status plan_batch(const cicero_job* jobs, int n_jobs, const cicero
     const unsigned long long rj = (unsigned long long)J.cam->width * J.cam->height;
     const unsigned long long nbj = (unsigned long long)geo.nb[0] * geo.nb[1] * geo.nb[2];
     if (table) {
-      JobDesc& D = table[j];
+      JobDesc& D = table[jt];
       memset(&D, 0, sizeof D);
       D.geo = geo;
       D.samp = samp;
@@ -448,8 +470,8 @@ static cicero_status plan_batch(const cicero_job* jobs, int n_jobs, const cicero
     Q += rj * (unsigned long long)J.sampling->n_samples;
     nb += nbj;
     S = std::max(S, J.sampling->n_samples);
-    if (j == 0) b->box = brick_box(geo, elem_bytes(J.grid->dtype));
-    if (j == 0) b->plan.geo = geo;
+    if (jt == 0) b->box = brick_box(geo, elem_bytes(J.grid->dtype));
+    if (jt == 0) b->plan.geo = geo;
   }
   if (R >= (1ull << 31) || nb >= (1ull << 31)) return fail(CICERO_ERR_UNSUPPORTED, "batch has too many rays or bricks");
   if (opt->max_records > 0 && (unsigned long long)opt->max_records < Q) Q = (unsigned long long)opt->max_records;
@@ -901,49 +923,53 @@ cicero_status cicero_batch_destroy(cicero_batch* batch) {
   return CICERO_OK;
 }
 
-cicero_status cicero_batch_autotune_brick(const cicero_job* jobs, int n_jobs, const cicero_options* opt,
-                                          void* workspace, size_t ws_bytes, void* stream, int* best_brick,
-                                          float* ms) {
-  if (!best_brick || !opt) return fail(CICERO_ERR_INVALID_ARG, "best_brick/opt is NULL");
+cicero_status cicero_batch_autotune(const cicero_job* jobs, int n_jobs, const cicero_options* opt, void* workspace,
+                                    size_t ws_bytes, void* stream, cicero_options* best_opt, float* ms) {
+  if (!best_opt || !opt) return fail(CICERO_ERR_INVALID_ARG, "best/opt is NULL");
   cudaStream_t st = (cudaStream_t)stream;
-  const int cand[3] = {4, 8, 16};
+  const int bricks[3] = {4, 8, 16};
   float best = 1e30f;
-  *best_brick = 0;
+  bool found = false;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaError_t e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
   if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
-  for (int i = 0; i < 3; i++) {
-    if (ms) ms[i] = -1.0f;
-    cicero_options o = *opt;
-    o.brick = cand[i];
-    cicero_batch* b = nullptr;
-    if (cicero_batch_create(jobs, n_jobs, &o, workspace, ws_bytes, &b) != CICERO_OK) continue;
-    // one untimed launch (first use of the kernels), then one timed launch
-    if (cicero_batch_launch(b, stream) != CICERO_OK) {
+  if (ms)
+    for (int i = 0; i < 12; i++) ms[i] = -1.0f;
+  for (int i = 0; i < 3 && e == cudaSuccess; i++) {
+    for (int g = 1; g <= 4; g++) {
+      cicero_options o = *opt;
+      o.brick = bricks[i];
+      o.mlp_groups = g;
+      cicero_batch* b = nullptr;
+      if (cicero_batch_create(jobs, n_jobs, &o, workspace, ws_bytes, &b) != CICERO_OK) break;  // brick does not fit
+      // one untimed launch (first use of the kernels), then one timed launch
+      if (cicero_batch_launch(b, stream) != CICERO_OK) {
+        cicero_batch_destroy(b);
+        break;  // this brick size is not supported for these grids
+      }
+      cudaEventRecord(e0, st);
+      cicero_batch_launch(b, stream);
+      cudaEventRecord(e1, st);
+      e = cudaEventSynchronize(e1);
+      const cicero_status ws_st = cicero_workspace_status((char*)workspace + batch_table_bytes(n_jobs), stream);
       cicero_batch_destroy(b);
-      continue;  // this brick size is not supported for these grids
-    }
-    cudaEventRecord(e0, st);
-    cicero_batch_launch(b, stream);
-    cudaEventRecord(e1, st);
-    e = cudaEventSynchronize(e1);
-    const cicero_status ws_st = cicero_workspace_status((char*)workspace + batch_table_bytes(n_jobs), stream);
-    cicero_batch_destroy(b);
-    if (e != cudaSuccess) break;
-    if (ws_st != CICERO_OK) continue;
-    float t = 0.0f;
-    cudaEventElapsedTime(&t, e0, e1);
-    if (ms) ms[i] = t;
-    if (t < best) {
-      best = t;
-      *best_brick = cand[i];
+      if (e != cudaSuccess) break;
+      if (ws_st != CICERO_OK) continue;
+      float t = 0.0f;
+      cudaEventElapsedTime(&t, e0, e1);
+      if (ms) ms[4 * i + (g - 1)] = t;
+      if (t < best) {
+        best = t;
+        *best_opt = o;
+        found = true;
+      }
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (e != cudaSuccess) return cuda_fail(e, "batch autotune");
-  if (!*best_brick) return fail(CICERO_ERR_UNSUPPORTED, "no brick size could render this batch");
+  if (!found) return fail(CICERO_ERR_UNSUPPORTED, "no brick size could render this batch");
   return CICERO_OK;
 }
 

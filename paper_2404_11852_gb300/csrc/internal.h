@@ -76,6 +76,7 @@ struct RenderPlan {
   bool want_k;
   bool want_bwd;
   cicero_precision precision;
+  int mlp_groups;  // BF16 tensor-core MLP tiles in flight per SM (0 = as many as fit)
 };
 
 // Output buffers of a rendering call, per view (rgb/depth indexed by pixel, or by ray for explicit
@@ -100,6 +101,12 @@ struct MlpPtrs {
   const float *w1, *b1, *w2, *b2, *w3, *b3;
   int in_dim, n_freq;
 };
+
+// Two jobs whose MLPs are the same tensors (so their weights need loading once).
+__host__ __device__ inline bool same_mlp(const MlpPtrs& a, const MlpPtrs& b) {
+  return a.w1 == b.w1 && a.b1 == b.b1 && a.w2 == b.w2 && a.b2 == b.b2 && a.w3 == b.w3 && a.b3 == b.b3 &&
+         a.in_dim == b.in_dim && a.n_freq == b.n_freq;
+}
 
 struct HashGeo;
 cicero_status run_render(const cicero_grid* grid, const MlpPtrs& mlp, const RenderPlan& plan, const RaySrc& src,
@@ -146,6 +153,7 @@ struct BatchPlan {
   BrickBox box;
   bool f16;
   int C, n_freq;
+  int mlp_groups;       // tiles in flight per SM requested (0 = as many as fit)
   void* workspace;
   size_t ws_bytes;
 };
@@ -170,7 +178,7 @@ cicero_status launch_gather_mlp_bf16_hash(const GridGeo& geo, const MlpPtrs& mlp
                                           const HashGeo& hg, cudaStream_t st);
 
 // BF16 tensor-core Feature Computation (mlp_tc.cu)
-cicero_status launch_gather_mlp_bf16(const cicero_grid* grid, const GridGeo& geo, const Samp& samp, const RaySrc& src,
+cicero_status launch_gather_mlp_bf16(const cicero_grid* grid, const GridGeo& geo, int mlp_groups,
                                      const MlpPtrs& mlp, const RenderWs& ws, const CUtensorMap& map, const BrickBox& box,
                                      cudaStream_t st);
 cicero_status launch_mlp_eval_bf16(const MlpPtrs& mlp, const float* x, int M, float* c, uint32_t* err,

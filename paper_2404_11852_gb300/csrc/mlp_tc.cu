@@ -786,10 +786,11 @@ __global__ void __launch_bounds__(512, 1) k_gather_mlp_bf16_hash(GridGeo g, MlpP
   tmem_free_all(tmem_base);
 }
 
-// The batched version: like the kernel above, each CTA takes a contiguous range of the tile list
-// (ordered job after job), split into pieces at job boundaries; at the start of each piece the
-// CTA stages the job's geometry in shared memory and loads its MLP weights if they differ from
-// the ones there, and the piece is split evenly among the groups.
+// The batched version, job-major: the jobs are taken one after the other (in table order, where
+// jobs that share MLP weights are adjacent), and every CTA takes its contiguous share of each job's
+// tiles, split evenly among its groups, as a launch per job would; so at any moment the GPU works on
+// one or two jobs' grids, which keeps their bricks in L2.  The CTA stages each job's geometry in
+// shared memory and loads the job's MLP weights when they differ from the ones there.
 template <typename T, int CC, int NF>
 __global__ void __launch_bounds__(512, 1) k_gather_mlp_bf16_batch(const JobDesc* __restrict__ jobs, int n_jobs,
                                                                   RenderWs w, int vb, int vx, int box_bytes,
@@ -798,29 +799,28 @@ __global__ void __launch_bounds__(512, 1) k_gather_mlp_bf16_batch(const JobDesc*
   extern __shared__ __align__(1024) char sm[];
   Group G = setup(sm, nullptr, groups, box_bytes);
   const uint32_t tmem_base = G.tmem - (uint32_t)(G.g * 128);
-  const uint32_t n_tiles = w.hdr[1];
-  const uint32_t per = (n_tiles + gridDim.x - 1) / gridDim.x;
-  const long long c0 = (long long)blockIdx.x * per, c1 = min((long long)n_tiles, c0 + per);
   GridGeo& geo = *(GridGeo*)(sm + Smem::geo);  // the current job's geometry, read by every group
-  const float* cur_w1 = nullptr;
+  const MlpPtrs* cur = nullptr;
   int loaded = -1;
   bool alive = true;
-  for (long long a = c0; a < c1;) {
-    const JobDesc& J = jobs[(w.tile[a].y >> 21) & 0x7FFu];
-    const long long b = min(c1, (long long)w.tile_off[J.brick_base + J.nb]);
+  for (int j = 0; j < n_jobs; j++) {
+    const JobDesc& J = jobs[j];
+    const long long j0 = w.tile_off[J.brick_base], j1 = w.tile_off[J.brick_base + J.nb];
+    const long long per = (j1 - j0 + gridDim.x - 1) / gridDim.x;
+    const long long a = min(j1, j0 + (long long)blockIdx.x * per), b = min(j1, a + per);
+    if (b <= a) continue;
     __syncthreads();  // every group is done with the previous job's geometry (and weights)
     if (threadIdx.x == 0) geo = J.geo;
-    if (J.mlp.w1 != cur_w1) {
+    if (!cur || !same_mlp(*cur, J.mlp)) {
       load_weights(sm, J.mlp);
       fence_proxy_async();
-      cur_w1 = J.mlp.w1;
+      cur = &J.mlp;
     }
     __syncthreads();
     const long long span = b - a;
     const long long t0 = a + (span * G.g) / groups, t1 = a + (span * (G.g + 1)) / groups;
     alive = gather_tiles<T, CC, NF>(sm, G, geo, &J.map, J.mlp.in_dim, J.mlp.n_freq, vb, vx, box_bytes, w, t0, t1,
                                     loaded, alive);
-    a = b;
   }
   tmem_free_all(tmem_base);
 }
@@ -856,12 +856,19 @@ __global__ void __launch_bounds__(512, 1) k_mlp_eval_bf16(MlpPtrs mlp, const flo
 
 // -------------------------------------------------------------------------------------------
 
-template <typename T, int CC, int NF>
-static cicero_status launch_tc(const GridGeo& geo, int S, const MlpPtrs& mlp, const RenderWs& ws,
-                               const CUtensorMap& map, const BrickBox& box, cudaStream_t st) {
+// Tile pipelines per CTA: as many as fit the shared memory, at most `requested` (0 = no limit).
+static int tc_groups(int box_bytes, int requested) {
   using namespace tc;
   int groups = kMaxGroups;
-  while (groups > 1 && Smem::groups + groups * group_bytes(box.box_bytes) > 227 * 1024) groups--;
+  while (groups > 1 && Smem::groups + groups * group_bytes(box_bytes) > 227 * 1024) groups--;
+  return requested > 0 && requested < groups ? requested : groups;
+}
+
+template <typename T, int CC, int NF>
+static cicero_status launch_tc(const GridGeo& geo, int S, const MlpPtrs& mlp, const RenderWs& ws,
+                               const CUtensorMap& map, const BrickBox& box, int mlp_groups, cudaStream_t st) {
+  using namespace tc;
+  const int groups = tc_groups(box.box_bytes, mlp_groups);
   int smem = Smem::groups + groups * group_bytes(box.box_bytes);
   if (smem > 227 * 1024) return fail(CICERO_ERR_UNSUPPORTED, "brick too large for the tensor-core kernel");
   smem = std::max(smem, 120 * 1024);  // one CTA per SM: it owns all 512 TMEM columns
@@ -877,17 +884,15 @@ static cicero_status launch_tc(const GridGeo& geo, int S, const MlpPtrs& mlp, co
   return e == cudaSuccess ? CICERO_OK : cuda_fail(e, "k_gather_mlp_bf16");
 }
 
-cicero_status launch_gather_mlp_bf16(const cicero_grid* grid, const GridGeo& geo, const Samp& samp, const RaySrc& src,
+cicero_status launch_gather_mlp_bf16(const cicero_grid* grid, const GridGeo& geo, int mlp_groups,
                                      const MlpPtrs& mlp, const RenderWs& ws, const CUtensorMap& map,
                                      const BrickBox& box, cudaStream_t st) {
-  (void)samp;
-  (void)src;
   const bool f16 = grid->dtype == CICERO_F16;
   if (geo.C == 12 && mlp.n_freq == 4)
-    return f16 ? launch_tc<__half, 12, 4>(geo, ws.S, mlp, ws, map, box, st)
-               : launch_tc<float, 12, 4>(geo, ws.S, mlp, ws, map, box, st);
-  return f16 ? launch_tc<__half, 0, 0>(geo, ws.S, mlp, ws, map, box, st)
-             : launch_tc<float, 0, 0>(geo, ws.S, mlp, ws, map, box, st);
+    return f16 ? launch_tc<__half, 12, 4>(geo, ws.S, mlp, ws, map, box, mlp_groups, st)
+               : launch_tc<float, 12, 4>(geo, ws.S, mlp, ws, map, box, mlp_groups, st);
+  return f16 ? launch_tc<__half, 0, 0>(geo, ws.S, mlp, ws, map, box, mlp_groups, st)
+             : launch_tc<float, 0, 0>(geo, ws.S, mlp, ws, map, box, mlp_groups, st);
 }
 
 template <typename T, int CC, int NF>
@@ -919,8 +924,7 @@ cicero_status launch_gather_mlp_bf16_hash(const GridGeo& geo, const MlpPtrs& mlp
 template <typename T, int CC, int NF>
 static cicero_status launch_tc_batch(const BatchPlan& b, cudaStream_t st) {
   using namespace tc;
-  int groups = kMaxGroups;
-  while (groups > 1 && Smem::groups + groups * group_bytes(b.box.box_bytes) > 227 * 1024) groups--;
+  const int groups = tc_groups(b.box.box_bytes, b.mlp_groups);
   int smem = Smem::groups + groups * group_bytes(b.box.box_bytes);
   if (smem > 227 * 1024) return fail(CICERO_ERR_UNSUPPORTED, "brick too large for the tensor-core kernel");
   smem = std::max(smem, 120 * 1024);  // one CTA per SM: it owns all 512 TMEM columns

@@ -1314,22 +1314,44 @@ __global__ void __launch_bounds__(256) k_composite_batch(const JobDesc* __restri
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  for (int r = warp; r < R; r += nwarps) {
-    const uint32_t n = w.ray_n[r], start = w.ray_start[r];
-    float a0, a1, a2;
-    ray_color_sum(w, start, n, a0, a1, a2);
-    a0 = warp_sum(a0);
-    a1 = warp_sum(a1);
-    a2 = warp_sum(a2);
-    if (lane == 0) {
-      const JobDesc& J = jobs[__float_as_int(w.ray_dir[r].w)];  // the job the march tagged the ray with
-      const int pix = r - J.ray_base;
-      const float T = w.ray_T[r];
-      J.rgb[3 * pix + 0] = a0 + T * J.samp.bg[0];
-      J.rgb[3 * pix + 1] = a1 + T * J.samp.bg[1];
-      J.rgb[3 * pix + 2] = a2 + T * J.samp.bg[2];
+  const unsigned full = 0xffffffffu;
+  // as in k_composite: lane j reads the header of the j-th of each group of 32 of the warp's rays,
+  // with its job (the tag the march left), output pixel and background; the warp then composites
+  // them one by one
+  for (long long i0 = 0;; i0 += 32) {
+    const long long rl = (long long)warp + (i0 + lane) * nwarps;
+    const unsigned have = __ballot_sync(full, rl < R);
+    if (!have) break;
+    uint32_t n_l = 0, start_l = 0;
+    float T_l = 0.0f, bg0 = 0.0f, bg1 = 0.0f, bg2 = 0.0f;
+    float* px_l = nullptr;
+    if (rl < R) {
+      n_l = w.ray_n[rl];
+      start_l = w.ray_start[rl];
+      T_l = w.ray_T[rl];
+      const JobDesc& J = jobs[__float_as_int(w.ray_dir[rl].w)];
+      px_l = J.rgb + 3 * ((int)rl - J.ray_base);
+      bg0 = J.samp.bg[0];
+      bg1 = J.samp.bg[1];
+      bg2 = J.samp.bg[2];
+    }
+    const int nq = __popc(have);
+    for (int jj = 0; jj < nq; jj++) {
+      const uint32_t n = __shfl_sync(full, n_l, jj), start = __shfl_sync(full, start_l, jj);
+      const float T = __shfl_sync(full, T_l, jj);
+      float a0, a1, a2;
+      ray_color_sum(w, start, n, a0, a1, a2);
+      a0 = warp_sum(a0);
+      a1 = warp_sum(a1);
+      a2 = warp_sum(a2);
+      if (lane == jj) {  // the lane that holds the ray's pixel writes it
+        px_l[0] = a0 + T * bg0;
+        px_l[1] = a1 + T * bg1;
+        px_l[2] = a2 + T * bg2;
+      }
     }
   }
+  (void)n_jobs;
 }
 
 // Ray Index Table export: sample id = ray * S + slot.
@@ -1432,7 +1454,7 @@ cicero_status run_render(const cicero_grid* grid, const MlpPtrs& mlp, const Rend
   } else if ((s = encode_brick_map(grid, geo, box, &map)) != CICERO_OK) {
     return s;
   } else if (plan.precision == CICERO_MLP_BF16) {
-    s = launch_gather_mlp_bf16(grid, geo, plan.samp, src, mlp, ws, map, box, st);
+    s = launch_gather_mlp_bf16(grid, geo, plan.mlp_groups, mlp, ws, map, box, st);
   } else {
     s = f16 ? launch_f32<__half>(geo, plan.S, mlp, ws, map, box, st)
             : launch_f32<float>(geo, plan.S, mlp, ws, map, box, st);

@@ -130,9 +130,10 @@ def test_batch_autotune(cc, batch):
     specs, dev, outs, jobs = batch
     opt = cc.options(cc.MLP_BF16, 4)
     ws = cc.workspace(cc.cicero_batch_workspace_size(jobs, opt))
-    best, ms = cc.cicero_batch_autotune_brick(jobs, opt, ws)
-    assert best in (4, 8, 16)
-    assert ms[best] > 0 and all(v == -1.0 or v > 0 for v in ms.values())
+    best, ms = cc.cicero_batch_autotune(jobs, opt, ws)
+    assert best.brick in (4, 8, 16) and 1 <= best.mlp_groups <= 4
+    assert ms[(best.brick, best.mlp_groups)] > 0 and all(v == -1.0 or v > 0 for v in ms.values())
+    assert min(v for v in ms.values() if v > 0) == ms[(best.brick, best.mlp_groups)]
 
 
 def test_batch_record_capacity_overflow_reported(cc, batch):
