@@ -760,9 +760,12 @@ def plain_small(cc, torch, dev):
     gd, md = cc.DeviceGrid.from_host(g, dev), cc.DeviceMlp.from_host(m, dev)
     sd, cd = cc.sampling_from(cam.sampling), cc.camera_from(cam)
     R = 64 * 64
+    t0 = time.perf_counter()
     ref = oracle.render(g, m, cam.sampling, cam=cam)
+    t_oracle = time.perf_counter() - t0
     out = {"workload": "64^3 x 12 FP32 scene (8 blobs), 64x64, 64 uniform samples in [0.5, 2.5], t_stop 1e-3",
-           "ambiguous_rays": int(ref["amb"].sum())}
+           "ambiguous_rays": int(ref["amb"].sum()),
+           "oracle": {"ms": t_oracle * 1e3, "cores": oracle.max_threads(), "kind": "FP64, every pixel"}}
     for name, prec in (("fp32", cc.MLP_FP32), ("bf16", cc.MLP_BF16)):
         opt = cc.options(prec, 8)
         ws = cc.workspace(cc.cicero_render_workspace_size(gd.desc, R, sd, opt), dev)
