@@ -204,6 +204,21 @@ __device__ __forceinline__ void sample_pos(const float o[3], const float d[3], f
   for (int a = 0; a < 3; a++) p[a] = __fadd_rn(o[a], __fmul_rn(t, d[a]));
 }
 
+// Position p and ray direction d of slot k of a ray whose geometry is ot = (origin, t0) and
+// dd = (direction, dt): the march's own operations (slot_t, sample_pos), so the bits are the
+// march's.
+__device__ __forceinline__ void sample_of(const float4& ot, const float4& dd, uint32_t k, float p[3], float d[3]) {
+  Slots sl;
+  sl.t0 = ot.w;
+  sl.dt = dd.w;
+  const float t = slot_t(sl, (int)k);
+  const float o[3] = {ot.x, ot.y, ot.z};
+  d[0] = dd.x;
+  d[1] = dd.y;
+  d[2] = dd.z;
+  sample_pos(o, d, t, p);
+}
+
 // Indexing (Sec. II-B): continuous vertex coordinate g, voxel i0 = min(floor g, n - 2) and the
 // fraction inside the voxel; false when the sample is outside the box or in an empty cell.
 __device__ __forceinline__ bool index_sample(const GridGeo& g, const float p[3], int i0[3], float f[3]) {

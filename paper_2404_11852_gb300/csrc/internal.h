@@ -42,6 +42,12 @@ struct __align__(32) SrtRec {
   float4 pw, qd;
 };
 
+// Per-ray geometry of the samples: (origin, first slot's t0) and (unit direction, slot step dt);
+// slot k sits at o + (t0 + (k + 1/2) dt) d.
+struct __align__(16) RayGeo {
+  float4 ot, dd;
+};
+
 struct RenderWs {
   uint32_t* hdr;        // [0] error bits, [1] tile count, [2] composited samples, [3] records reserved
   uint32_t* ray_n;      // [R] composited samples of each ray
@@ -49,11 +55,12 @@ struct RenderWs {
   float* ray_T;         // [R] transmittance after the last composited slot
   float4* ray_dir;      // [R] unit direction of each ray
   uint32_t* rec_key;    // [Q] RIT key: brick id * kOctants + octant
-  float4* rec_pw;       // [Q] sample position (FP32, bit-identical to the march) and weight T_k alpha_k
-  uint16_t* rec_k;      // [Q] slot index (only for Ray Index Table export; may be null)
-  float4* rec_c;        // [Q] (c_r, c_g, c_b, w) of each record
+  float* rec_w;         // [Q] weight T_k alpha_k
+  uint16_t* rec_slot;   // [Q] slot index
+  float4* rec_c;        // [Q] (c_r, c_g, c_b, w) of each record (written by the gather, in record order)
   float* rec_T;         // [Q] transmittance before the slot (backward only; may be null)
   float* rec_raw;       // [Q] interpolated raw density, then dL/draw (backward only; may be null)
+  uint32_t* rec_ray;    // [Q] ray of each record (backward and RIT export only; may be null)
   uint32_t* brick_cnt;  // [nb * kOctants] records per RIT key
   uint32_t* brick_off;  // [nb * kOctants + 1] first record of each key (brick b starts at key b * kOctants)
   uint32_t* brick_cur;  // [nb * kOctants] scatter cursors
@@ -61,7 +68,7 @@ struct RenderWs {
   uint32_t* blk_sums;   // [2 * scan blocks] per-block sums of the brick scan
   uint4* tile;          // [max_tiles] (first record, count | bz << 8 | job << 21, brick id, bx | by << 16)
   SrtRec* srt;          // [Q] the Ray Index Table payload in brick order
-  uint32_t* rec_ray;    // [Q] ray of each record (backward and RIT export only; may be null)
+  RayGeo* ray_geo;      // [R] geometry of each ray's samples
   struct RaySetup* setup;  // [R] per-ray setup of the march (ray, slots, active-slot mask, records)
   int R, S, nb, max_tiles;
   uint32_t Q;

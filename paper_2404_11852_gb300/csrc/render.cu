@@ -32,9 +32,8 @@ constexpr size_t kRaySetupBytes = 84;  // sizeof(RaySetup), checked where it is 
 size_t render_ws_bytes(const RenderPlan& p) {
   const size_t Q = p.Q, R = (size_t)p.R;
   size_t b = al256(64);
-  b += 3 * al256(4 * R) + al256(16 * R);
-  b += al256(4 * Q) + al256(16 * Q);  // rec_c shares rec_pw's storage (rec_pw is dead after the sort)
-  if (p.want_k) b += al256(2 * Q);
+  b += 3 * al256(4 * R) + al256(16 * R) + al256(32 * R);
+  b += 2 * al256(4 * Q) + al256(2 * Q) + al256(16 * Q);
   if (p.want_bwd) b += 2 * al256(4 * Q);
   if (p.want_k || p.want_bwd) b += al256(4 * Q);
   const size_t nk = (size_t)p.nb * kOctants;  // RIT keys: (brick, octant)
@@ -60,10 +59,11 @@ bool carve_render_ws(void* ws, size_t bytes, const RenderPlan& p, RenderWs* w) {
   w->ray_start = (uint32_t*)take(4 * R);
   w->ray_T = (float*)take(4 * R);
   w->ray_dir = (float4*)take(16 * R);
+  w->ray_geo = (RayGeo*)take(32 * R);
   w->rec_key = (uint32_t*)take(4 * Q);
-  w->rec_pw = (float4*)take(16 * Q);
-  w->rec_c = w->rec_pw;
-  w->rec_k = p.want_k ? (uint16_t*)take(2 * Q) : nullptr;
+  w->rec_w = (float*)take(4 * Q);
+  w->rec_slot = (uint16_t*)take(2 * Q);
+  w->rec_c = (float4*)take(16 * Q);
   w->rec_T = p.want_bwd ? (float*)take(4 * Q) : nullptr;
   w->rec_raw = p.want_bwd ? (float*)take(4 * Q) : nullptr;
   w->rec_ray = (p.want_k || p.want_bwd) ? (uint32_t*)take(4 * Q) : nullptr;
@@ -343,8 +343,10 @@ __device__ __forceinline__ void index_voxel(const GridGeo& g, const float p[3], 
 // last active slot processed before the transmittance dropped below t_stop, as in a plain
 // slot-by-slot march.  Records carry the RIT key of their brick, offset by key_base (the job's first
 // brick in a batch), and octant; dep/acc/steps point at the ray's outputs (or are NULL).
-// EXTRA: the records also carry their slot, ray, transmittance and raw density (the backward and
-// the Ray Index Table export); a compile-time flag, so that the forward march tests nothing for them.
+// A record is the sample's RIT key, weight and slot (the scatter recomputes its position from the
+// ray's geometry).  EXTRA: the records also carry their ray, transmittance and raw density (the
+// backward and the Ray Index Table export); a compile-time flag, so that the forward march tests
+// nothing for them.
 template <typename T, bool EXTRA>
 __device__ __forceinline__ void march_ray_core(const GridGeo& g, const Samp& s, const T* __restrict__ dens,
                                                const RenderWs& w, int r, const RaySetup& q, uint32_t key_base,
@@ -393,10 +395,10 @@ __device__ __forceinline__ void march_ray_core(const GridGeo& g, const Samp& s, 
     const uint32_t key = contrib ? brick_key(g, i0, key_base) : 0xffffffffu;
     if (contrib) {
       const size_t qi = (size_t)base + cnt + __popc(cmask & lt_mask);
-      w.rec_pw[qi] = make_float4(p[0], p[1], p[2], wk);
       w.rec_key[qi] = key;
+      w.rec_w[qi] = wk;
+      w.rec_slot[qi] = (uint16_t)k;
       if constexpr (EXTRA) {
-        if (w.rec_k) w.rec_k[qi] = (uint16_t)k;
         if (w.rec_ray) w.rec_ray[qi] = (uint32_t)r;
         if (w.rec_T) {
           w.rec_T[qi] = Tk;
@@ -552,6 +554,13 @@ __global__ void __launch_bounds__(256) k_ray_setup(GridGeo g, Samp s, RaySrc src
       }
     }
     reserve_records(w, sq + (threadIdx.x & ~31), have);
+    if (have) {
+      const RaySetup& q = sq[threadIdx.x];
+      RayGeo rg;
+      rg.ot = make_float4(q.o[0], q.o[1], q.o[2], q.t0);
+      rg.dd = make_float4(q.d[0], q.d[1], q.d[2], q.dt);
+      w.ray_geo[r] = rg;
+    }
     __syncthreads();
     const int n = (int)min((long long)256, (long long)R - r0);
     const uint32_t* from = reinterpret_cast<const uint32_t*>(sq);
@@ -737,7 +746,7 @@ __global__ void __launch_bounds__(256) k_tiles(GridGeo g, RenderWs w) {
 // their keys' offsets, so the atomic of a run of equal keys returns the run's destination.  A
 // chunk's records are written one step later, while the next chunk's atomics are in flight, and
 // the next ray's header and first chunk are loaded ahead too.
-__global__ void __launch_bounds__(256) k_scatter(RaySrc src, RenderWs w) {
+__global__ void __launch_bounds__(256, 4) k_scatter(RaySrc src, RenderWs w) {
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -746,14 +755,15 @@ __global__ void __launch_bounds__(256) k_scatter(RaySrc src, RenderWs w) {
   const unsigned lt_mask = (1u << lane) - 1u;
   const unsigned le_mask = (2u << lane) - 1u;
   struct Chunk {
-    uint32_t key;
-    float4 pw;
+    uint32_t key, slot;
+    float wk;
   };
   auto load_chunk = [&](uint32_t start, uint32_t n, uint32_t j0, Chunk& c) {
     const uint32_t j = j0 + lane;
     const bool valid = j < n;
     c.key = valid ? w.rec_key[start + j] : 0xffffffffu;
-    c.pw = valid ? w.rec_pw[start + j] : make_float4(0.f, 0.f, 0.f, 0.f);
+    c.slot = valid ? w.rec_slot[start + j] : 0u;
+    c.wk = valid ? w.rec_w[start + j] : 0.0f;
   };
   // the chunk whose atomics were issued in the previous step: written once their results are
   // back (every lane takes the base of its run's head), one step later
@@ -771,28 +781,31 @@ __global__ void __launch_bounds__(256) k_scatter(RaySrc src, RenderWs w) {
     }
     p_any = false;
   };
-  // the warp's current ray and its first chunk
+  // the warp's current ray (its header and geometry) and its first chunk
   int r = warp;
   uint32_t n = 0, start = 0;
-  float4 dir = make_float4(0.f, 0.f, 0.f, 0.f);
+  RayGeo geo;
+  geo.ot = geo.dd = make_float4(0.f, 0.f, 0.f, 0.f);
   Chunk cur;
   if (r < R) {
     n = w.ray_n[r];
     start = w.ray_start[r];
-    dir = w.ray_dir[r];
+    geo = w.ray_geo[r];
     load_chunk(start, n, 0, cur);
   }
   for (; r < R; r += nwarps) {
-    // the next ray's header and first chunk
+    // the next ray's header, geometry and first chunk
     const int rn = r + nwarps;
     uint32_t nn = 0, nstart = 0;
-    float4 ndir = make_float4(0.f, 0.f, 0.f, 0.f);
+    RayGeo ngeo = geo;
     Chunk nxt;
     nxt.key = 0xffffffffu;
+    nxt.slot = 0u;
+    nxt.wk = 0.0f;
     if (rn < R) {
       nn = w.ray_n[rn];
       nstart = w.ray_start[rn];
-      ndir = w.ray_dir[rn];
+      ngeo = w.ray_geo[rn];
     }
     for (uint32_t j0 = 0; j0 < n; j0 += 32) {
       Chunk c = cur;
@@ -814,18 +827,21 @@ __global__ void __launch_bounds__(256) k_scatter(RaySrc src, RenderWs w) {
       }
       // the previous chunk is written while this chunk's atomics are in flight
       flush();
+      // the sample's position, recomputed from its ray and slot as the march computed it
+      float p[3], d[3];
+      sample_of(geo.ot, geo.dd, c.slot, p, d);
       p_any = true;
       p_valid = valid;
       p_off = off;
       p_hl = 31 - __clz(heads & le_mask);  // this lane's run head
       p_q = q;
-      p_pw = c.pw;
-      p_dir = dir;
+      p_pw = make_float4(p[0], p[1], p[2], c.wk);
+      p_dir = make_float4(d[0], d[1], d[2], 0.0f);
     }
     if (n == 0 && rn < R) load_chunk(nstart, nn, 0, nxt);
     n = nn;
     start = nstart;
-    dir = ndir;
+    geo = ngeo;
     cur = nxt;
   }
   flush();
@@ -1361,7 +1377,7 @@ __global__ void k_rit_export(RenderWs w, int n_bricks, int32_t* offs, int32_t* s
   for (size_t i = i0; i <= (size_t)n_bricks; i += st) offs[i] = (int32_t)w.brick_off[i * kOctants];
   for (size_t i = i0; i < total; i += st) {
     const uint32_t q = __float_as_uint(w.srt[i].qd.x);
-    samples[i] = (int32_t)(w.rec_ray[q] * (uint32_t)w.S + w.rec_k[q]);
+    samples[i] = (int32_t)(w.rec_ray[q] * (uint32_t)w.S + w.rec_slot[q]);
   }
 }
 
@@ -1421,7 +1437,7 @@ cicero_status run_render(const cicero_grid* grid, const MlpPtrs& mlp, const Rend
     ProfScope ps(kStMarch, st);
     k_clear<<<std::min(num_sms() * 4, (plan.nb * kOctants + 255) / 256 + 1), 256, 0, st>>>(ws.hdr, 16, ws.brick_cnt,
                                                                                   (size_t)plan.nb * kOctants);
-    const bool extra = ws.rec_k || ws.rec_ray || ws.rec_T;
+    const bool extra = ws.rec_ray || ws.rec_T;
     k_ray_setup<false><<<setup_blocks(src.n_max), 256, 0, st>>>(geo, plan.samp, src, nullptr, nullptr, 0, 0, ws);
     if (f16 && extra)
       k_march<__half, true><<<mb, 256, 0, st>>>(geo, plan.samp, src, (const __half*)grid->density, ws, out);
