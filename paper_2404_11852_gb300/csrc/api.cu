@@ -701,6 +701,7 @@ size_t cicero_warp_workspace_size(const cicero_camera* tgt_cam) {
   return warp_ws_bytes(tgt_cam->width, tgt_cam->height);
 }
 
+
 cicero_status cicero_render_backward(const cicero_grid* grid, const cicero_mlp* mlp, const float* ray_o,
                                      const float* ray_d, int n_rays, const cicero_sampling* sampling,
                                      const float* d_rgb, float* d_density, float* d_features, float* d_mlp,

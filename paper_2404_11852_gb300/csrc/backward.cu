@@ -6,12 +6,16 @@
 //   B1 k_bwd_ray       per ray (warp), in slot order: R_k = sum_{j>k} w_j c_j + T_end bg by a
 //                      warp scan, dL/dsigma_k = delta (T_{k+1} g.c_k - g.R_k) and
 //                      dL/draw_k = dL/dsigma_k * sigmoid(raw_k + shift)
-//   B2 k_bwd_brick     per brick (Ray Index Table order), 64 samples at a time: MLP forward and
-//                      backward on CUDA cores down to dL/dfeatures, then the trilinear adjoint
-//                      accumulated in a shared-memory copy of the brick's vertices; when the CTA
-//                      leaves the brick, one global atomicAdd per touched vertex entry.  With
-//                      d_mlp, the weight gradients are summed over the CTA's tiles in registers
-//                      and added to d_mlp once per CTA.
+//   B2 k_bwd_brick_tc  grid gradients: per brick (Ray Index Table order), 128 samples at a time,
+//                      the MLP backward down to dL/dfeatures on the tensor cores, with the ReLU
+//                      masks the FP32 forward recorded (nothing of the forward is recomputed), then
+//                      the trilinear adjoint accumulated in a shared-memory copy of the brick's
+//                      vertices; when the CTA leaves the brick, one global atomicAdd per touched
+//                      vertex entry.
+//   B2 k_bwd_brick     with d_mlp (the weight gradients need h1 and x): the same per brick, 64
+//                      samples at a time, MLP forward and backward on CUDA cores, the weight
+//                      gradients summed over the CTA's tiles in registers and added to d_mlp once
+//                      per CTA.
 #include <cuda_runtime.h>
 
 #include <string.h>
@@ -20,6 +24,7 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "tc_ptx.cuh"
 
 namespace cicero {
 
@@ -184,7 +189,7 @@ template <typename T, bool WG>
 __global__ void __launch_bounds__(256, 1) k_bwd_brick(GridGeo g, RaySrc src, MlpPtrs mlp, RenderWs w,
                                                       const T* __restrict__ feat, const float* __restrict__ d_rgb,
                                                       float* d_dens, float* d_feat, float* d_mlp) {
-  extern __shared__ __align__(128) char sm[];
+  extern __shared__ __align__(1024) char sm[];
   float* w1t = (float*)(sm + BwdSmem::w1t);
   float* w2t = (float*)(sm + BwdSmem::w2t);
   float* w3 = (float*)(sm + BwdSmem::w3);
@@ -486,6 +491,248 @@ __global__ void __launch_bounds__(256, 1) k_bwd_brick(GridGeo g, RaySrc src, Mlp
   }
 }
 
+// ---------------------------------------------------------------------------------------------
+// B2 on the tensor cores (grid gradients).  Per tile of <= 128 samples of one brick, one thread per
+// sample:
+//   dh2 = (dz3 W3) masked by relu'(z2)           CUDA cores (K = 3)
+//   dh1 = (dh2 W2) masked by relu'(z1)           tcgen05 kind::f16, M = 128, N = 128, K = 128
+//   dL/dfeatures = dh1 W1[:, :C]                 tcgen05, N = 16 (channels padded), K = 128
+// FP32 accuracy from BF16 operands: every operand x is split into hi = bf16(x) and lo = bf16(x - hi)
+// and each product is hi hi' + hi lo' + lo hi' (the "bf16x3" scheme of Henry, Tang and Heinecke,
+// ARITH 2019: ~16 significant bits per product, the lo lo' term below FP32 rounding of the result),
+// accumulated in FP32 in tensor memory.  The ReLU masks are the FP32 forward's (rec_mask).
+
+namespace bt {
+constexpr int kThreads = 256;  // two threads per sample of a 128-sample tile
+constexpr int kN1 = 16;        // channels of dL/dfeatures, padded to the smallest MMA width
+struct Smem {
+  static constexpr int w2t_hi = 0;                                  // [128][128] bf16: row i, K = o: W2[o][i]
+  static constexpr int w2t_lo = w2t_hi + kHidden * kHidden * 2;
+  static constexpr int w1t_hi = w2t_lo + kHidden * kHidden * 2;     // [16][128] bf16: row c, K = i: W1[i][c]
+  static constexpr int w1t_lo = w1t_hi + kN1 * kHidden * 2;
+  static constexpr int a_hi = w1t_lo + kN1 * kHidden * 2;           // [128][128] bf16: dh2, then dh1
+  static constexpr int a_lo = a_hi + kTile * kHidden * 2;
+  static constexpr int w3 = a_lo + kTile * kHidden * 2;             // [3][128] f32
+  static constexpr int bars = w3 + 3 * kHidden * 4;                 // mbarrier; TMEM address at +8
+  static constexpr int gacc = bars + 128;                           // [vb^3][C + 1] f32
+  static_assert(a_hi % 16 == 0 && w1t_hi % 16 == 0 && bars % 16 == 0, "operand alignment");
+};
+constexpr uint32_t kTmemCols = 128;
+}  // namespace bt
+
+// 8 consecutive K values of one row, split into the hi and lo operands (hi exactly representable in
+// BF16, so its packing rounds nothing)
+__device__ __forceinline__ void store_chunk_split(char* hi_base, char* lo_base, int row, int k0, int K,
+                                                  const float* v) {
+  float h[8], l[8];
+#pragma unroll
+  for (int j = 0; j < 8; j++) {
+    h[j] = __bfloat162float(__float2bfloat16_rn(v[j]));
+    l[j] = v[j] - h[j];
+  }
+  tc::store_chunk(hi_base, row, k0, K, h);
+  tc::store_chunk(lo_base, row, k0, K, l);
+}
+
+// ReLU mask bit of hidden unit n (the layout the FP32 forward writes)
+__device__ __forceinline__ bool mask_bit(const uint4& mk, int n) {
+  const int bi = n < 64 ? n >> 2 : (n - 64) >> 2;
+  const int sh = (bi & 3) * 8 + (n < 64 ? (n & 3) : 4 + ((n - 64) & 3));
+  const uint32_t wd = (bi >> 2) == 0 ? mk.x : (bi >> 2) == 1 ? mk.y : (bi >> 2) == 2 ? mk.z : mk.w;
+  return (wd >> sh) & 1u;
+}
+
+// dh A (hi, lo) x B (hi, lo) over K = 128 into the accumulator at d: 8 K steps of three products
+__device__ __forceinline__ void mma_split(uint32_t d, uint64_t ah, uint64_t al, uint64_t bh, uint64_t bl,
+                                          uint32_t idesc) {
+#pragma unroll
+  for (int s = 0; s < kHidden / 16; s++) {
+    tc::mma_bf16(d, ah + 16u * s, bh + 16u * s, idesc, s > 0 ? 1u : 0u);
+    tc::mma_bf16(d, ah + 16u * s, bl + 16u * s, idesc, 1u);
+    tc::mma_bf16(d, al + 16u * s, bh + 16u * s, idesc, 1u);
+  }
+}
+
+// Two threads per sample (m = tid mod 128, half h = tid / 128): each computes half of dh2's and of
+// dh1's 128 hidden units (TMEM columns [64 h, 64 h + 64) of the sample's lane) and scatters half of
+// the trilinear corners, so a tile's CUDA-core work is spread over 8 warps.
+__global__ void __launch_bounds__(bt::kThreads, 1) k_bwd_brick_tc(GridGeo g, MlpPtrs mlp, RenderWs w,
+                                                                  const float* __restrict__ d_rgb, float* d_dens,
+                                                                  float* d_feat) {
+  using namespace tc;
+  extern __shared__ __align__(1024) char sm[];
+  const int C = g.C, B = g.brick, vb = B + 1;
+  const int m = threadIdx.x & (kTile - 1), h = threadIdx.x / kTile;
+  char* a_hi = sm + bt::Smem::a_hi;
+  char* a_lo = sm + bt::Smem::a_lo;
+  float* w3s = (float*)(sm + bt::Smem::w3);
+  float* gacc = (float*)(sm + bt::Smem::gacc);
+  uint64_t* bar = (uint64_t*)(sm + bt::Smem::bars);
+  uint32_t* tslot = (uint32_t*)(sm + bt::Smem::bars + 8);
+  // the weights, transposed into the B operands and split
+  for (int i = threadIdx.x; i < kHidden * (kHidden / 8); i += bt::kThreads) {
+    const int n = i / (kHidden / 8), k0 = (i % (kHidden / 8)) * 8;
+    float v[8];
+#pragma unroll
+    for (int j = 0; j < 8; j++) v[j] = mlp.w2[(k0 + j) * kHidden + n];
+    store_chunk_split(sm + bt::Smem::w2t_hi, sm + bt::Smem::w2t_lo, n, k0, kHidden, v);
+  }
+  for (int i = threadIdx.x; i < bt::kN1 * (kHidden / 8); i += bt::kThreads) {
+    const int n = i / (kHidden / 8), k0 = (i % (kHidden / 8)) * 8;
+    float v[8];
+#pragma unroll
+    for (int j = 0; j < 8; j++) v[j] = n < C ? mlp.w1[(k0 + j) * mlp.in_dim + n] : 0.0f;
+    store_chunk_split(sm + bt::Smem::w1t_hi, sm + bt::Smem::w1t_lo, n, k0, kHidden, v);
+  }
+  for (int i = threadIdx.x; i < 3 * kHidden; i += bt::kThreads) w3s[i] = mlp.w3[i];
+  for (int i = threadIdx.x; i < vb * vb * vb * (C + 1); i += bt::kThreads) gacc[i] = 0.0f;
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  fence_proxy_async();
+  if (threadIdx.x < 32) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(bt::kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tslot;
+  const uint32_t taddr = tmem + ((uint32_t)(((threadIdx.x >> 5) & 3) * 32) << 16);  // this warp's lanes
+  const uint64_t ah = smem_desc(smem_u32(a_hi), 128u, kHidden * 16), al = smem_desc(smem_u32(a_lo), 128u, kHidden * 16);
+  const uint64_t b2h = smem_desc(smem_u32(sm + bt::Smem::w2t_hi), 128u, kHidden * 16);
+  const uint64_t b2l = smem_desc(smem_u32(sm + bt::Smem::w2t_lo), 128u, kHidden * 16);
+  const uint64_t b1h = smem_desc(smem_u32(sm + bt::Smem::w1t_hi), 128u, kHidden * 16);
+  const uint64_t b1l = smem_desc(smem_u32(sm + bt::Smem::w1t_lo), 128u, kHidden * 16);
+  uint32_t phase = 0;
+  bool alive = true;
+
+  const uint32_t n_tiles = w.hdr[1];
+  const uint32_t per = (n_tiles + gridDim.x - 1) / gridDim.x;
+  const uint32_t t_begin = blockIdx.x * per, t_end = min(n_tiles, t_begin + per);
+  int cur = -1;
+  for (uint32_t ti = t_begin; ti < t_end && alive; ti++) {
+    const uint4 td = w.tile[ti];
+    const int b = (int)td.z;
+    const uint32_t start = td.x;
+    const int mcnt = (int)(td.y & 0xFFu);
+    const int bx = (int)(td.w & 0xFFFFu), by = (int)(td.w >> 16), bz = (int)((td.y >> 8) & 0x1FFFu);
+    if (b != cur) {
+      if (cur >= 0) {
+        flush_brick(g, cur, gacc, vb, d_dens, d_feat);
+        __syncthreads();
+      }
+      cur = b;
+    }
+    // this thread's sample: its brick-local voxel, weights of the colour gradient, ReLU masks
+    bool ok = false;
+    float dz0 = 0.f, dz1 = 0.f, dz2 = 0.f, draw = 0.f, f[3] = {0.f, 0.f, 0.f};
+    int l[3] = {0, 0, 0};
+    uint4 m1 = make_uint4(0u, 0u, 0u, 0u), m2 = m1;
+    if (m < mcnt) {
+      const float4 pw = w.srt[start + m].pw;
+      const uint32_t rid = __float_as_uint(w.srt[start + m].qd.x);
+      const float p[3] = {pw.x, pw.y, pw.z};
+      int i0[3];
+      const bool in = index_sample(g, p, i0, f);
+      l[0] = i0[0] - bx * B;
+      l[1] = i0[1] - by * B;
+      l[2] = i0[2] - bz * B;
+      ok = in && l[0] >= 0 && l[0] < B && l[1] >= 0 && l[1] < B && l[2] >= 0 && l[2] < B;
+      if (!ok) {
+        if (h == 0) set_err(&w.hdr[0], kErrInternal);
+      } else {
+        const int r = (int)w.rec_ray[rid];
+        const float4 cw = w.rec_c[rid];
+        draw = w.rec_raw[rid];
+        m1 = w.rec_mask[2 * (size_t)rid];
+        m2 = w.rec_mask[2 * (size_t)rid + 1];
+        dz0 = cw.w * d_rgb[3 * r] * cw.x * (1.0f - cw.x);
+        dz1 = cw.w * d_rgb[3 * r + 1] * cw.y * (1.0f - cw.y);
+        dz2 = cw.w * d_rgb[3 * r + 2] * cw.z * (1.0f - cw.z);
+      }
+    }
+    // dh2 = (dz3 W3) masked by relu'(z2): this thread's half of row m of A
+#pragma unroll
+    for (int k0 = 0; k0 < kHidden / 2; k0 += 8) {
+      float v[8];
+#pragma unroll
+      for (int j = 0; j < 8; j++) {
+        const int o = 64 * h + k0 + j;
+        v[j] = mask_bit(m2, o) ? w3s[o] * dz0 + w3s[kHidden + o] * dz1 + w3s[2 * kHidden + o] * dz2 : 0.0f;
+      }
+      store_chunk_split(a_hi, a_lo, m, 64 * h + k0, kHidden, v);
+    }
+    fence_proxy_async();
+    __syncthreads();
+    // dh1 = dh2 W2 into columns [0, 128)
+    if (threadIdx.x == 0) {
+      fence_after();
+      mma_split(tmem, ah, al, b2h, b2l, idesc_bf16(kHidden));
+      mma_commit(bar);
+    }
+    alive = __syncthreads_and(mbar_wait(bar, phase, &w.hdr[0]));
+    fence_after();
+    if (!alive) break;
+    phase ^= 1u;
+    // dh1 masked by relu'(z1) -> this thread's half of row m of A (dh2 is no longer read)
+    {
+      float v[64];
+      tmem_ld<64>(taddr + 64 * h, v);
+#pragma unroll
+      for (int q = 0; q < 8; q++) {
+        float x[8];
+#pragma unroll
+        for (int j = 0; j < 8; j++) x[j] = mask_bit(m1, 64 * h + q * 8 + j) ? v[q * 8 + j] : 0.0f;
+        store_chunk_split(a_hi, a_lo, m, 64 * h + q * 8, kHidden, x);
+      }
+    }
+    fence_proxy_async();
+    fence_before();
+    __syncthreads();
+    // dL/dfeatures = dh1 W1[:, :C] into columns [0, 16)
+    if (threadIdx.x == 0) {
+      fence_after();
+      mma_split(tmem, ah, al, b1h, b1l, idesc_bf16(bt::kN1));
+      mma_commit(bar);
+    }
+    alive = __syncthreads_and(mbar_wait(bar, phase, &w.hdr[0]));
+    fence_after();
+    if (!alive) break;
+    phase ^= 1u;
+    float dft[16];
+    tmem_ld<16>(taddr, dft);
+    fence_before();
+    // trilinear adjoint into the brick accumulator: corners 4 h .. 4 h + 3
+    if (ok) {
+#pragma unroll
+      for (int u = 0; u < 4; u++) {
+        const int q = 4 * h + u;
+        const float wq = ((q & 1) ? f[0] : 1.f - f[0]) * (((q >> 1) & 1) ? f[1] : 1.f - f[1]) *
+                         ((q >> 2) ? f[2] : 1.f - f[2]);
+        const int lv = ((l[2] + (q >> 2)) * vb + (l[1] + ((q >> 1) & 1))) * vb + (l[0] + (q & 1));
+        float* ga = gacc + lv * (C + 1);
+#pragma unroll
+        for (int c = 0; c < bt::kN1; c++)
+          if (c < C) atomicAdd(&ga[c], wq * dft[c]);
+        atomicAdd(&ga[C], wq * draw);
+      }
+    }
+    __syncthreads();
+  }
+  if (alive && cur >= 0) flush_brick(g, cur, gacc, vb, d_dens, d_feat);
+  if (!alive) mbar_wait(bar, phase, &w.hdr[0]);  // MMAs may still be running (bounded)
+  fence_before();
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(bt::kTmemCols) : "memory");
+  }
+}
+
 template <typename T, bool WG>
 static cudaError_t launch_bwd_brick(const RenderPlan& plan, const RaySrc& src, const MlpPtrs& mlp, const RenderWs& ws,
                                     const void* feat, const float* d_rgb, float* d_dens, float* d_feat, float* d_mlp,
@@ -518,6 +765,16 @@ cicero_status run_backward(const cicero_grid* grid, const MlpPtrs& mlp, const Re
   if (smem > 227 * 1024) return fail(CICERO_ERR_UNSUPPORTED, "brick too large for the backward kernel");
   const bool f16 = grid->dtype == CICERO_F16;
   cudaError_t e;
+  const int smem_tc = bt::Smem::gacc + vb * vb * vb * (plan.geo.C + 1) * 4;
+  if (!d_mlp && ws.rec_mask && plan.geo.C <= bt::kN1 && smem_tc <= 227 * 1024) {
+    // grid gradients on the tensor cores, with the forward's ReLU masks
+    e = cudaFuncSetAttribute(k_bwd_brick_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_tc);
+    if (e == cudaSuccess) {
+      k_bwd_brick_tc<<<num_sms(), bt::kThreads, smem_tc, st>>>(plan.geo, mlp, ws, d_rgb, d_dens, d_feat);
+      e = cudaGetLastError();
+    }
+    return e == cudaSuccess ? CICERO_OK : cuda_fail(e, "backward kernels");
+  }
   if (d_mlp)
     e = f16 ? launch_bwd_brick<__half, true>(plan, src, mlp, ws, grid->features, d_rgb, d_dens, d_feat, d_mlp, smem, st)
             : launch_bwd_brick<float, true>(plan, src, mlp, ws, grid->features, d_rgb, d_dens, d_feat, d_mlp, smem, st);

@@ -61,6 +61,8 @@ struct RenderWs {
   float* rec_T;         // [Q] transmittance before the slot (backward only; may be null)
   float* rec_raw;       // [Q] interpolated raw density, then dL/draw (backward only; may be null)
   uint32_t* rec_ray;    // [Q] ray of each record (backward and RIT export only; may be null)
+  uint4* rec_mask;      // [Q][2] ReLU masks of MLP layers 1 and 2 from the FP32 forward (backward only; may be
+                        // null): hidden unit n < 64 is bit n % 4 of byte n / 4, unit 64 + n is bit 4 + n % 4
   uint32_t* brick_cnt;  // [nb * kOctants] records per RIT key
   uint32_t* brick_off;  // [nb * kOctants + 1] first record of each key (brick b starts at key b * kOctants)
   uint32_t* brick_cur;  // [nb * kOctants] scatter cursors

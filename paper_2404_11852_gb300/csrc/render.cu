@@ -34,7 +34,7 @@ size_t render_ws_bytes(const RenderPlan& p) {
   size_t b = al256(64);
   b += 3 * al256(4 * R) + al256(16 * R) + al256(32 * R);
   b += 2 * al256(4 * Q) + al256(2 * Q) + al256(16 * Q);
-  if (p.want_bwd) b += 2 * al256(4 * Q);
+  if (p.want_bwd) b += 2 * al256(4 * Q) + al256(32 * Q);
   if (p.want_k || p.want_bwd) b += al256(4 * Q);
   const size_t nk = (size_t)p.nb * kOctants;  // RIT keys: (brick, octant)
   b += 2 * al256(4 * nk) + al256(4 * (nk + 1)) + al256(4 * ((size_t)p.nb + 1));
@@ -67,6 +67,7 @@ bool carve_render_ws(void* ws, size_t bytes, const RenderPlan& p, RenderWs* w) {
   w->rec_T = p.want_bwd ? (float*)take(4 * Q) : nullptr;
   w->rec_raw = p.want_bwd ? (float*)take(4 * Q) : nullptr;
   w->rec_ray = (p.want_k || p.want_bwd) ? (uint32_t*)take(4 * Q) : nullptr;
+  w->rec_mask = p.want_bwd ? (uint4*)take(32 * Q) : nullptr;
   const size_t nk = (size_t)p.nb * kOctants;
   w->brick_cnt = (uint32_t*)take(4 * nk);
   w->brick_cur = (uint32_t*)take(4 * nk);
@@ -1026,7 +1027,22 @@ __device__ __forceinline__ void nbar_arrive(int id, int n) {
 // threads < 128 return c of sample m = threadIdx.x.  Run by the 256 MLP threads (threadIdx.x < 256), which synchronise on
 // their own named barrier; with empty_id > 0 they also arrive on that barrier (with the producers,
 // kMlpThreads + kProdThreads) once layer 1 has read X.
-__device__ __forceinline__ void mlp_f32_tile(char* sm, const float* X, float c[3], int in_dim, int empty_id = 0) {
+// This thread's ReLU bits of one layer into msk [16][128] bytes: byte (tn, m) holds units
+// tn * 4 + j (bit j) and 64 + tn * 4 + j (bit 4 + j) of sample m, as relu(acc + bias) > 0 decides.
+__device__ __forceinline__ void store_relu_bits(const float acc[8][8], const float* bias, uint8_t* msk, int tm,
+                                                int tn) {
+#pragma unroll
+  for (int i = 0; i < 8; i++) {
+    uint32_t byte = 0;
+#pragma unroll
+    for (int j = 0; j < 8; j++) byte |= (acc[i][j] + bias[gemm_row(tn, j)] > 0.f ? 1u : 0u) << j;
+    msk[tn * kTile + gemm_row(tm, i)] = (uint8_t)byte;
+  }
+}
+
+// msk (may be NULL): [2][16][128] bytes receiving the ReLU masks of layers 1 and 2 (store_relu_bits).
+__device__ __forceinline__ void mlp_f32_tile(char* sm, const float* X, float c[3], int in_dim, int empty_id = 0,
+                                             uint8_t* msk = nullptr) {
   const float* w1t = (const float*)(sm + F32Smem::w1t);
   const float* w2t = (const float*)(sm + F32Smem::w2t);
   const float* w3 = (const float*)(sm + F32Smem::w3);
@@ -1041,6 +1057,7 @@ __device__ __forceinline__ void mlp_f32_tile(char* sm, const float* X, float c[3
 #pragma unroll
     for (int j = 0; j < 8; j++) acc[i][j] = 0.0f;
   simt_gemm(X, w1t, (in_dim + 3) & ~3, tm, tn, acc);  // rows in_dim.. of X and W1^T are zero
+  if (msk) store_relu_bits(acc, b1, msk, tm, tn);
   simt_epilogue(acc, b1, H, tm, tn);
   nbar_sync(kBarMlp, kMlpThreads);
   if (empty_id) nbar_arrive(empty_id, kMlpThreads + kProdThreads);  // X may be refilled
@@ -1049,6 +1066,7 @@ __device__ __forceinline__ void mlp_f32_tile(char* sm, const float* X, float c[3
 #pragma unroll
     for (int j = 0; j < 8; j++) acc[i][j] = 0.0f;
   simt_gemm(H, w2t, kHidden, tm, tn, acc);
+  if (msk) store_relu_bits(acc, b2, msk + 16 * kTile, tm, tn);
   // layer-2 epilogue fused with layer 3: h2 = relu(acc + b2) stays in registers; this thread's 8
   // hidden units give partial sums z[i][o] = sum_j w3[o][n_j] h2[i][j] for its 8 samples, and the
   // 16 threads that share the samples add theirs through shared memory (P [16][3][128], over H)
@@ -1106,6 +1124,8 @@ __global__ void __launch_bounds__(kMlpThreads + kProdThreads, 1)
   extern __shared__ __align__(128) char sm[];
   uint64_t* bar = (uint64_t*)(sm + F32Smem::bar);
   T* tile = (T*)(sm + (nbuf == 2 ? F32Smem::tile : F32Smem::tile1));
+  // the ReLU masks of two tiles, after the brick tile (present only when the launch records masks)
+  uint8_t* mask_smem = (uint8_t*)tile + ((box_bytes + 127) & ~127);
   load_mlp_f32_smem(sm, mlp);
   if (threadIdx.x == 0) {
     mbar_init(bar, 1);
@@ -1180,10 +1200,27 @@ __global__ void __launch_bounds__(kMlpThreads + kProdThreads, 1)
     const int mcnt = (int)(td.y & 0xFFu);
     nbar_sync(kBarFull0 + b, kMlpThreads + kProdThreads);  // the producers have filled X
     float c[3];
-    mlp_f32_tile(sm, X, c, mlp.in_dim, kBarEmpty0 + b);
+    // with a backward to follow, the layers' ReLU masks too (two buffers by tile parity: a thread
+    // cannot write tile i + 2's masks before every thread has passed tile i + 1's first barrier,
+    // which follows its reads of tile i's)
+    uint8_t* msk = w.rec_mask ? mask_smem + (i & 1) * 32 * kTile : nullptr;
+    mlp_f32_tile(sm, X, c, mlp.in_dim, kBarEmpty0 + b, msk);
     const int m = threadIdx.x;
-    if (m < kTile && m < mcnt)
-      w.rec_c[__float_as_uint(w.srt[start + m].qd.x)] = make_float4(c[0], c[1], c[2], w.srt[start + m].pw.w);
+    if (m < kTile && m < mcnt) {
+      const uint32_t rid = __float_as_uint(w.srt[start + m].qd.x);
+      w.rec_c[rid] = make_float4(c[0], c[1], c[2], w.srt[start + m].pw.w);
+      if (msk) {
+        uint32_t v[8];
+#pragma unroll
+        for (int q = 0; q < 8; q++) {  // word q: bytes tn = 4 q' .. of layer q / 4
+          const uint8_t* src = msk + (q >> 2) * 16 * kTile + (q & 3) * 4 * kTile + m;
+          v[q] = (uint32_t)src[0] | ((uint32_t)src[kTile] << 8) | ((uint32_t)src[2 * kTile] << 16) |
+                 ((uint32_t)src[3 * kTile] << 24);
+        }
+        w.rec_mask[2 * (size_t)rid] = make_uint4(v[0], v[1], v[2], v[3]);
+        w.rec_mask[2 * (size_t)rid + 1] = make_uint4(v[4], v[5], v[6], v[7]);
+      }
+    }
   }
 }
 
@@ -1411,8 +1448,10 @@ static int blocks_for_warps(long long warps, int per_sm) {
 template <typename T>
 static cicero_status launch_f32(const GridGeo& geo, int S, const MlpPtrs& mlp, const RenderWs& ws,
                                 const CUtensorMap& map, const BrickBox& box, cudaStream_t st) {
-  const int nbuf = F32Smem::tile + box.box_bytes <= 227 * 1024 ? 2 : 1;  // two input buffers when they fit
-  const int smem = (nbuf == 2 ? F32Smem::tile : F32Smem::tile1) + box.box_bytes;
+  const int masks = ws.rec_mask ? 2 * 32 * kTile : 0;  // ReLU masks of two tiles for the backward
+  const int boxa = (box.box_bytes + 127) & ~127;
+  const int nbuf = F32Smem::tile + boxa + masks <= 227 * 1024 ? 2 : 1;  // two input buffers when they fit
+  const int smem = (nbuf == 2 ? F32Smem::tile : F32Smem::tile1) + boxa + masks;
   if (smem > 227 * 1024) return fail(CICERO_ERR_UNSUPPORTED, "brick too large for the FP32 feature-computation kernel");
   auto kern = k_gather_mlp_f32<T>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
