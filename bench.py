@@ -729,19 +729,31 @@ def backward_workload(cc, torch, dev):
         torch.cuda.synchronize()
         p = cc.cicero_profile_end()
         stage[name] = {k: p[k][0] / 5 for k in ("march", "bucket", "gather_mlp", "composite", "bwd_ray", "bwd_brick")}
-    # B2's algorithmic FP32 work per composited sample: recomputed layers 1-2, dL/dh2, dL/dh1,
-    # dL/dfeatures (+ dW3, dW2, dW1 with the weight gradients), against the FP32 FFMA peak
-    # derived from the SM count, 128 FP32 lanes per SM, 2 FLOP per FMA and the 2070 MHz maximum clock
+    # B2 without the weight gradients (k_bwd_brick_tc): the tensor-core GEMMs dL/dh1 = dL/dh2 W2 and
+    # dL/dfeatures = dL/dh1 W1[:, :C] per composited sample, algorithmic 2 (H H + C H) FLOP, executed
+    # as three split-BF16 products with the feature channels padded to N = 16, against the measured
+    # sustained BF16 peak.  With the weight gradients (k_bwd_brick, CUDA cores): recomputed layers
+    # 1-2, dL/dh2, dL/dh1, dL/dfeatures, dW3, dW2, dW1 against the FP32 FFMA peak derived from the
+    # SM count, 128 FP32 lanes per SM, 2 FLOP per FMA and the 2070 MHz maximum clock
     C, H, I = 12, 128, m.w1.shape[1]
-    flop = 2 * (I * H + H * H + 3 * H + H * H + C * H)
-    flop_w = flop + 2 * (3 * H + H * H + I * H)
-    peak = torch.cuda.get_device_properties(0).multi_processor_count * 128 * 2 * 2.07e9 / 1e12
+    pk = peaks()
+    flop_tc = 2 * (H * H + C * H)
+    flop_tc_exec = 3 * 2 * H * (H + 16)
+    flop_w = 2 * (I * H + H * H + 3 * H + H * H + C * H) + 2 * (3 * H + H * H + I * H)
+    fp32_peak = torch.cuda.get_device_properties(0).multi_processor_count * 128 * 2 * 2.07e9 / 1e12
     roof = {}
-    for name, f in (("grid", flop), ("grid_and_mlp", flop_w)):
-        t = stage[name]["bwd_brick"] / 1e3
-        ach = f * samples / t / 1e12 if t > 0 else 0.0
-        roof[name] = {"bound": "alu", "flop_per_sample": f, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                      "frac": ach / peak, "peak_src": "derived: SMs x 128 FP32 lanes x 2 x 2070 MHz"}
+    t = stage["grid"]["bwd_brick"] / 1e3
+    ach = flop_tc * samples / t / 1e12 if t > 0 else 0.0
+    roof["grid"] = {"kernel": "k_bwd_brick_tc", "bound": "tensor", "flop_per_sample": flop_tc,
+                    "executed_mma_flop_per_sample": flop_tc_exec, "achieved": ach,
+                    "peak": pk["bf16_tflops_sustained"], "unit": "TFLOP/s", "frac": ach / pk["bf16_tflops_sustained"],
+                    "executed_tflops": flop_tc_exec * samples / t / 1e12 if t > 0 else 0.0,
+                    "peak_src": "measured (sustained bf16)"}
+    t = stage["grid_and_mlp"]["bwd_brick"] / 1e3
+    ach = flop_w * samples / t / 1e12 if t > 0 else 0.0
+    roof["grid_and_mlp"] = {"kernel": "k_bwd_brick (weight gradients)", "bound": "alu", "flop_per_sample": flop_w,
+                            "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach / fp32_peak,
+                            "peak_src": "derived: SMs x 128 FP32 lanes x 2 x 2070 MHz"}
     return {"workload": "8192 rays x 256 samples, 160^3 x 12 FP32 grid, MSE loss", "forward_ms": t_f,
             "backward_ms": t_b, "backward_with_mlp_weights_ms": t_bm,
             "rays_per_s_fwd_bwd": R / ((t_f + t_b) / 1e3), "composited_samples": samples,

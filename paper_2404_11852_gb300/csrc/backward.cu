@@ -534,13 +534,22 @@ __device__ __forceinline__ void store_chunk_split(char* hi_base, char* lo_base, 
   tc::store_chunk(lo_base, row, k0, K, l);
 }
 
-// ReLU mask bit of hidden unit n (the layout the FP32 forward writes)
-__device__ __forceinline__ bool mask_bit(const uint4& mk, int n) {
-  const int bi = n < 64 ? n >> 2 : (n - 64) >> 2;
-  const int sh = (bi & 3) * 8 + (n < 64 ? (n & 3) : 4 + ((n - 64) & 3));
-  const uint32_t wd = (bi >> 2) == 0 ? mk.x : (bi >> 2) == 1 ? mk.y : (bi >> 2) == 2 ? mk.z : mk.w;
-  return (wd >> sh) & 1u;
-}
+// ReLU mask of the half h of the hidden units (h = 0: units 0..63, 1: 64..127), in the layout the
+// FP32 forward writes (unit n < 64 is bit n % 4 of byte n / 4, unit 64 + n bit 4 + n % 4): the
+// words shifted so that unit 64 h + i is bit (i / 4 % 4) * 8 + i % 4 of word i / 16.
+struct HalfMask {
+  uint32_t w[4];
+  __device__ __forceinline__ HalfMask(const uint4& mk, int h) {
+    const uint32_t sh = 4u * (uint32_t)h;
+    w[0] = mk.x >> sh;
+    w[1] = mk.y >> sh;
+    w[2] = mk.z >> sh;
+    w[3] = mk.w >> sh;
+  }
+  __device__ __forceinline__ bool operator[](int i) const {  // i = 0..63, a compile-time constant in use
+    return (w[i >> 4] >> (((i >> 2) & 3) * 8 + (i & 3))) & 1u;
+  }
+};
 
 // dh A (hi, lo) x B (hi, lo) over K = 128 into the accumulator at d: 8 K steps of three products
 __device__ __forceinline__ void mma_split(uint32_t d, uint64_t ah, uint64_t al, uint64_t bh, uint64_t bl,
@@ -656,15 +665,24 @@ __global__ void __launch_bounds__(bt::kThreads, 1) k_bwd_brick_tc(GridGeo g, Mlp
       }
     }
     // dh2 = (dz3 W3) masked by relu'(z2): this thread's half of row m of A
+    {
+      const HalfMask mk(m2, h);
+      const float4* w30 = reinterpret_cast<const float4*>(w3s + 64 * h);
+      const float4* w31 = reinterpret_cast<const float4*>(w3s + kHidden + 64 * h);
+      const float4* w32 = reinterpret_cast<const float4*>(w3s + 2 * kHidden + 64 * h);
 #pragma unroll
-    for (int k0 = 0; k0 < kHidden / 2; k0 += 8) {
-      float v[8];
+      for (int k0 = 0; k0 < kHidden / 2; k0 += 8) {
+        float v[8];
 #pragma unroll
-      for (int j = 0; j < 8; j++) {
-        const int o = 64 * h + k0 + j;
-        v[j] = mask_bit(m2, o) ? w3s[o] * dz0 + w3s[kHidden + o] * dz1 + w3s[2 * kHidden + o] * dz2 : 0.0f;
+        for (int q = 0; q < 2; q++) {
+          const float4 a = w30[(k0 >> 2) + q], b = w31[(k0 >> 2) + q], c = w32[(k0 >> 2) + q];
+          const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w}, cv[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+          for (int j = 0; j < 4; j++)
+            v[4 * q + j] = mk[k0 + 4 * q + j] ? av[j] * dz0 + bv[j] * dz1 + cv[j] * dz2 : 0.0f;
+        }
+        store_chunk_split(a_hi, a_lo, m, 64 * h + k0, kHidden, v);
       }
-      store_chunk_split(a_hi, a_lo, m, 64 * h + k0, kHidden, v);
     }
     fence_proxy_async();
     __syncthreads();
@@ -680,13 +698,14 @@ __global__ void __launch_bounds__(bt::kThreads, 1) k_bwd_brick_tc(GridGeo g, Mlp
     phase ^= 1u;
     // dh1 masked by relu'(z1) -> this thread's half of row m of A (dh2 is no longer read)
     {
+      const HalfMask mk(m1, h);
       float v[64];
       tmem_ld<64>(taddr + 64 * h, v);
 #pragma unroll
       for (int q = 0; q < 8; q++) {
         float x[8];
 #pragma unroll
-        for (int j = 0; j < 8; j++) x[j] = mask_bit(m1, 64 * h + q * 8 + j) ? v[q * 8 + j] : 0.0f;
+        for (int j = 0; j < 8; j++) x[j] = mk[q * 8 + j] ? v[q * 8 + j] : 0.0f;
         store_chunk_split(a_hi, a_lo, m, 64 * h + q * 8, kHidden, x);
       }
     }
