@@ -16,14 +16,16 @@ def cc():
     return cicero
 
 
-def gpu_grads(cc, g32, m, o, d, sp, grad, with_mlp=False):
+def gpu_grads(cc, g32, m, o, d, sp, grad, with_mlp=False, feat_offset=0):
+    """feat_offset > 0 places d_features that many floats into a larger buffer (an address that
+    is not 16-byte aligned when feat_offset % 4 != 0)."""
     import torch
     gd, md = cc.DeviceGrid.from_host(g32), cc.DeviceMlp.from_host(m)
     sd = cc.sampling_from(sp)
     ot, dt = torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda()
     gr = torch.from_numpy(grad.astype(np.float32)).cuda()
     dd = torch.zeros(g32.density.shape, device="cuda")
-    df = torch.zeros(g32.features.shape, device="cuda")
+    df = torch.zeros(g32.features.size + feat_offset, device="cuda")[feat_offset:].view(g32.features.shape)
     dm = torch.zeros(m.flat().size, device="cuda") if with_mlp else None
     ws = cc.workspace(cc.cicero_backward_workspace_size(gd.desc, o.shape[0], sd))
     cc.cicero_render_backward(gd.desc, md.desc, ot, dt, sd, gr, dd, df, dm, ws)
@@ -76,6 +78,24 @@ def test_backward_larger_scene(cc, orc, brick_scene):
     grad[~keep] = 0.0  # ambiguous early stops contribute nothing on either side
     wd, wf, _ = orc.backward(g, m, sp, grad, rays=(o, d))
     dd, df = gpu_grads(cc, g, m, o, d, sp, grad)
+    assert rel_inf(dd, wd) <= 1e-3, rel_inf(dd, wd)
+    assert rel_inf(df, wf) <= 1e-3, rel_inf(df, wf)
+
+
+@pytest.mark.parametrize("C, feat_offset", [(6, 0), (12, 1), (12, 4)])
+def test_backward_channel_layouts(cc, orc, C, feat_offset):
+    """The trilinear adjoint adds four channels per 16-byte atomic when C % 4 == 0 and d_features
+    is 16-byte aligned, one channel per atomic otherwise: both paths against the oracle."""
+    g = scenes.make_grid(40, C, 6, seed=41)
+    m = scenes.make_mlp(C, seed=42, random_bias=True)
+    o, d = scenes.random_rays(200, seed=43)
+    sp = scenes.Sampling(near=0.5, far=2.5, n_samples=64, t_stop=1e-3)
+    out = orc.render(g, m, sp, rays=(o, d))
+    tgt = scenes.random_targets(200, seed=44).astype(np.float64)
+    grad = 2.0 * (out["rgb"] - tgt) / tgt.size
+    grad[out["amb"]] = 0.0
+    wd, wf, _ = orc.backward(g, m, sp, grad, rays=(o, d))
+    dd, df = gpu_grads(cc, g, m, o, d, sp, grad, feat_offset=feat_offset)
     assert rel_inf(dd, wd) <= 1e-3, rel_inf(dd, wd)
     assert rel_inf(df, wf) <= 1e-3, rel_inf(df, wf)
 
