@@ -718,7 +718,9 @@ def backward_workload(cc, torch, dev):
     t_bm = event_ms(torch, lambda: bwd(dm), 5)
     cc.cicero_workspace_status(ws_f)
     cc.cicero_workspace_status(ws_b)
-    samples = int(ws_b[:16].view(torch.int32).cpu().numpy()[2])  # composited samples of the recompute
+    hdr = ws_b[:32].view(torch.int32).cpu().numpy()
+    samples = int(hdr[2])  # composited samples of the recompute
+    fixed = int(hdr[4])    # of which recomputed in FP32 (uncertain split-BF16 ReLU decisions)
     # per-stage device time of one backward call without and with the MLP weight gradients
     stage = {}
     for name, arg in (("grid", None), ("grid_and_mlp", dm)):
@@ -757,6 +759,7 @@ def backward_workload(cc, torch, dev):
     return {"workload": "8192 rays x 256 samples, 160^3 x 12 FP32 grid, MSE loss", "forward_ms": t_f,
             "backward_ms": t_b, "backward_with_mlp_weights_ms": t_bm,
             "rays_per_s_fwd_bwd": R / ((t_f + t_b) / 1e3), "composited_samples": samples,
+            "fp32_recomputed_samples": fixed,
             "stage_ms": stage, "k_bwd_brick_roofline": roof,
             "grad_bytes": int(dd.numel() * 4 + df.numel() * 4)}
 

@@ -1,8 +1,10 @@
 // Backward of the FP32 renderer: gradient of a loss L(rgb) with respect to the density and
 // feature grids.  Nothing is stored by the forward pass; the backward recomputes it:
 //
-//   forward recompute  K1-K5 of render.cu (march, Ray Index Table, per-brick gather + MLP),
-//                      which leaves per composited sample (c, w, T, raw density)
+//   forward recompute  K1-K4 of render.cu (march, Ray Index Table), then per brick the features
+//                      and the MLP: k_fwd_x3 (tensor cores, split-BF16 products) and k_fwd_fix
+//                      (FP32, the samples whose ReLU decisions k_fwd_x3 cannot certify); this
+//                      leaves per composited sample (c, w, T, raw density) and the ReLU masks
 //   B1 k_bwd_ray       per ray (warp), in slot order: R_k = sum_{j>k} w_j c_j + T_end bg by a
 //                      warp scan, dL/dsigma_k = delta (T_{k+1} g.c_k - g.R_k) and
 //                      dL/draw_k = dL/dsigma_k * sigmoid(raw_k + shift)
@@ -561,11 +563,12 @@ struct HalfMask {
   }
 };
 
-// dh A (hi, lo) x B (hi, lo) over K = 128 into the accumulator at d: 8 K steps of three products
+// A (hi, lo) x B (hi, lo) over K = 16 KSTEPS into the accumulator at d: three products per K step
+template <int KSTEPS = kHidden / 16>
 __device__ __forceinline__ void mma_split(uint32_t d, uint64_t ah, uint64_t al, uint64_t bh, uint64_t bl,
                                           uint32_t idesc) {
 #pragma unroll
-  for (int s = 0; s < kHidden / 16; s++) {
+  for (int s = 0; s < KSTEPS; s++) {
     tc::mma_bf16(d, ah + 16u * s, bh + 16u * s, idesc, s > 0 ? 1u : 0u);
     tc::mma_bf16(d, ah + 16u * s, bl + 16u * s, idesc, 1u);
     tc::mma_bf16(d, al + 16u * s, bh + 16u * s, idesc, 1u);
@@ -740,6 +743,361 @@ __global__ void __launch_bounds__(bt::kThreads, 1) k_bwd_brick_tc(GridGeo g, Mlp
     fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(bt::kTmemCols) : "memory");
   }
+}
+
+
+// ------------------------------------------------------------------------------------------------
+// The backward's forward recompute on the tensor cores.  Per tile of 128 samples of one brick:
+// x -> h1 = relu(W1 x + b1) -> h2 = relu(W2 h1 + b2) -> c = sigmoid(W3 h2 + b3), layers 1 and 2 as
+// tcgen05 MMAs on split-BF16 operands (hi + lo, three products per K step as in k_bwd_brick_tc,
+// FP32 accumulation in TMEM), the biases, layer 3 and the sigmoid in FP32 on the CUDA cores.  It
+// writes what the backward reads: (c, w) into rec_c and the ReLU masks of layers 1 and 2 into
+// rec_mask.  Two threads per sample: thread (m, h) interpolates the four corners at z offset h,
+// converts half of row m of x (K values 24 h .. 24 h + 23) and takes hidden units 64 h .. 64 h + 63
+// in the epilogues; the h = 1 threads hand their partial sums to the h = 0 threads through
+// shared memory.
+//
+// A ReLU decision taken on a split-BF16 pre-activation can differ from the FP32 one where the
+// pre-activation is within the products' error of zero, and one flipped mask moves that sample's
+// whole gradient through the unit.  So each decision is checked against an estimate of that
+// error: unit n of layer 1 is uncertain when |z1_n| <= eps ||W1_n|| ||x||, unit n of layer 2 when
+// |z2_n| <= eps ||W2_n|| (||h1|| + ||x|| ||W1||_F) (its own products plus layer 1's errors carried
+// through W2).  Each split product drops terms of at most ~3 2^-18 |w x|, and the rounding errors
+// of a K-term sum add up like a random walk, to ~2^-17 ||w o x||_2, while ||w|| ||x|| is about
+// sqrt(K) ||w o x||_2: eps = 2^-17 leaves a margin of 7 to 11 times the typical error (K = 48,
+// 128).  The samples with an uncertain decision are listed (their sorted record index, in rec_key,
+// which the Ray Index Table no longer needs; count in hdr[4]) and recomputed by the FP32 MLP
+// afterwards (k_fwd_fix), so their masks are the FP32 path's.  On the 8192-ray workload 8.6% of
+// the samples are listed (16.5% with eps = 2^-16, 4.4% with 2^-18; the gradients of the three
+// parity scenes agree with the FP64 oracle to ~5e-6 in all three cases, and to 2e-3 without the
+// fix-up).
+namespace xt {
+constexpr int kThreads = 256;
+constexpr int kK1 = 48;    // layer-1 K: in_dim padded to a multiple of 16
+constexpr int kMaxC = 16;  // feature channels
+constexpr int kXS = kK1 + 1;  // FP32 row stride of the staged inputs (odd: rows in distinct banks)
+constexpr float kEps = 7.62939453125e-06f;  // 2^-17
+struct Smem {
+  static constexpr int w1_hi = 0;                             // [128][48] bf16: row n, K = k: W1[n][k]
+  static constexpr int w1_lo = w1_hi + kHidden * kK1 * 2;
+  static constexpr int w2_hi = w1_lo + kHidden * kK1 * 2;     // [128][128] bf16: row n, K = k: W2[n][k]
+  static constexpr int w2_lo = w2_hi + kHidden * kHidden * 2;
+  static constexpr int a_hi = w2_lo + kHidden * kHidden * 2;  // [128][48] x, then [128][128] h1
+  static constexpr int a_lo = a_hi + kTile * kHidden * 2;
+  static constexpr int prm = a_lo + kTile * kHidden * 2;      // b1 [128], b2 [128], w3 [3][128], b3 [4] f32
+  static constexpr int xs = prm + (5 * kHidden + 4) * 4;      // [128][kXS] f32: partial features, encoding
+  static constexpr int zpart = xs + kTile * kXS * 4;          // [128][4] f32: layer 3 over units 64..127
+  static constexpr int mpart = zpart + kTile * 4 * 4;         // [128][8] u32: ReLU bits of units 64..127
+  static constexpr int nrm = mpart + kTile * 8 * 4;           // ||W1_n|| [128], ||W2_n|| [128], ||W1||_F f32
+  static constexpr int nxp = nrm + (2 * kHidden + 4) * 4;     // [2][128] f32: ||x||^2 over each thread's K half
+  static constexpr int hp = nxp + 2 * kTile * 4;              // [2][128] f32: ||h1||^2 over each half
+  static constexpr int flg = hp + 2 * kTile * 4;              // [128] u32: uncertain decision among units 64..127
+  static constexpr int bars = flg + kTile * 4;                // mbarrier; TMEM address at +8
+  static constexpr int bytes = bars + 128;
+  static_assert(a_hi % 16 == 0 && w2_hi % 16 == 0 && xs % 16 == 0 && bars % 16 == 0, "alignment");
+};
+constexpr uint32_t kTmemCols = 128;
+}  // namespace xt
+
+bool fwd_x3_supported(const GridGeo& g, const MlpPtrs& mlp) {
+  return g.C <= xt::kMaxC && mlp.in_dim <= xt::kK1 && mlp.in_dim == g.C + 3 + 6 * mlp.n_freq;
+}
+
+// Bits of this thread's ReLU decisions: unit 64 h + n (n < 64) is bit ((n / 4) % 4) * 8 + 4 h + n % 4
+// of word n / 16 (the rec_mask layout)
+__device__ __forceinline__ void relu_bit(uint32_t mw[4], int n, int h, bool on) {
+  mw[n >> 4] |= (on ? 1u : 0u) << (((n >> 2) & 3) * 8 + 4 * h + (n & 3));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(xt::kThreads, 1) k_fwd_x3(GridGeo g, MlpPtrs mlp, RenderWs w,
+                                                            const T* __restrict__ feat) {
+  using namespace tc;
+  extern __shared__ __align__(1024) char sm[];
+  const int C = g.C, B = g.brick;
+  const int m = threadIdx.x & (kTile - 1), h = threadIdx.x / kTile;
+  char* a_hi = sm + xt::Smem::a_hi;
+  char* a_lo = sm + xt::Smem::a_lo;
+  float* b1s = (float*)(sm + xt::Smem::prm);
+  float* b2s = b1s + kHidden;
+  float* w3s = b2s + kHidden;
+  float* b3s = w3s + 3 * kHidden;
+  float* xs = (float*)(sm + xt::Smem::xs) + m * xt::kXS;  // this sample's row
+  float* nw1 = (float*)(sm + xt::Smem::nrm);
+  float* nw2 = nw1 + kHidden;
+  float* fro1 = nw2 + kHidden;
+  float* nxp = (float*)(sm + xt::Smem::nxp);
+  float* hp = (float*)(sm + xt::Smem::hp);
+  uint32_t* flg = (uint32_t*)(sm + xt::Smem::flg);
+  float* zpart = (float*)(sm + xt::Smem::zpart) + 4 * m;
+  uint32_t* mpart = (uint32_t*)(sm + xt::Smem::mpart) + 8 * m;
+  uint64_t* bar = (uint64_t*)(sm + xt::Smem::bars);
+  uint32_t* tslot = (uint32_t*)(sm + xt::Smem::bars + 8);
+  // the weights, split into the hi and lo B operands; the other parameters in FP32
+  for (int i = threadIdx.x; i < kHidden * (xt::kK1 / 8); i += xt::kThreads) {
+    const int n = i / (xt::kK1 / 8), k0 = (i % (xt::kK1 / 8)) * 8;
+    float v[8];
+#pragma unroll
+    for (int j = 0; j < 8; j++) v[j] = k0 + j < mlp.in_dim ? mlp.w1[n * mlp.in_dim + k0 + j] : 0.0f;
+    store_chunk_split(sm + xt::Smem::w1_hi, sm + xt::Smem::w1_lo, n, k0, xt::kK1, v);
+  }
+  for (int i = threadIdx.x; i < kHidden * (kHidden / 8); i += xt::kThreads) {
+    const int n = i / (kHidden / 8), k0 = (i % (kHidden / 8)) * 8;
+    float v[8];
+#pragma unroll
+    for (int j = 0; j < 8; j++) v[j] = mlp.w2[n * kHidden + k0 + j];
+    store_chunk_split(sm + xt::Smem::w2_hi, sm + xt::Smem::w2_lo, n, k0, kHidden, v);
+  }
+  for (int i = threadIdx.x; i < kHidden; i += xt::kThreads) {
+    b1s[i] = mlp.b1[i];
+    b2s[i] = mlp.b2[i];
+  }
+  for (int i = threadIdx.x; i < 3 * kHidden; i += xt::kThreads) w3s[i] = mlp.w3[i];
+  if (threadIdx.x < 4) b3s[threadIdx.x] = threadIdx.x < 3 ? mlp.b3[threadIdx.x] : 0.0f;
+  {  // row norms of W1 (threads < 128) and W2 (the others)
+    const int n = threadIdx.x & (kHidden - 1);
+    float s2 = 0.0f;
+    if (threadIdx.x < kHidden)
+      for (int k = 0; k < mlp.in_dim; k++) s2 = fmaf(mlp.w1[n * mlp.in_dim + k], mlp.w1[n * mlp.in_dim + k], s2);
+    else
+      for (int k = 0; k < kHidden; k++) s2 = fmaf(mlp.w2[n * kHidden + k], mlp.w2[n * kHidden + k], s2);
+    (threadIdx.x < kHidden ? nw1 : nw2)[n] = sqrtf(s2);
+  }
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  fence_proxy_async();
+  if (threadIdx.x < 32) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(xt::kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (threadIdx.x == 0) {  // read after the first tile's first barrier
+    float f2 = 0.0f;
+    for (int n = 0; n < kHidden; n++) f2 = fmaf(nw1[n], nw1[n], f2);
+    *fro1 = sqrtf(f2);
+  }
+  const uint32_t tmem = *tslot;
+  const uint32_t taddr = tmem + ((uint32_t)(((threadIdx.x >> 5) & 3) * 32) << 16);  // this warp's lanes
+  const uint64_t ax_h = smem_desc(smem_u32(a_hi), 128u, xt::kK1 * 16), ax_l = smem_desc(smem_u32(a_lo), 128u, xt::kK1 * 16);
+  const uint64_t ah_h = smem_desc(smem_u32(a_hi), 128u, kHidden * 16), ah_l = smem_desc(smem_u32(a_lo), 128u, kHidden * 16);
+  const uint64_t b1h = smem_desc(smem_u32(sm + xt::Smem::w1_hi), 128u, xt::kK1 * 16);
+  const uint64_t b1l = smem_desc(smem_u32(sm + xt::Smem::w1_lo), 128u, xt::kK1 * 16);
+  const uint64_t b2h = smem_desc(smem_u32(sm + xt::Smem::w2_hi), 128u, kHidden * 16);
+  const uint64_t b2l = smem_desc(smem_u32(sm + xt::Smem::w2_lo), 128u, kHidden * 16);
+  const int ne = 3 + 6 * mlp.n_freq;
+  uint32_t phase = 0;
+  bool alive = true;
+
+  const uint32_t n_tiles = w.hdr[1];
+  const uint32_t per = (n_tiles + gridDim.x - 1) / gridDim.x;
+  const uint32_t t_begin = blockIdx.x * per, t_end = min(n_tiles, t_begin + per);
+  for (uint32_t ti = t_begin; ti < t_end && alive; ti++) {
+    const uint4 td = w.tile[ti];
+    const uint32_t start = td.x;
+    const int mcnt = (int)(td.y & 0xFFu);
+    const int bx = (int)(td.w & 0xFFFFu), by = (int)(td.w >> 16), bz = (int)((td.y >> 8) & 0x1FFFu);
+    const bool valid = m < mcnt;
+    uint32_t rid = 0;
+    float wgt = 0.0f, d[3] = {0.0f, 0.0f, 0.0f}, fx[xt::kMaxC];
+#pragma unroll
+    for (int c = 0; c < xt::kMaxC; c++) fx[c] = 0.0f;
+    if (valid) {
+      const float4 pw = w.srt[start + m].pw;
+      const float4 qd = w.srt[start + m].qd;
+      rid = __float_as_uint(qd.x);
+      wgt = pw.w;
+      d[0] = qd.y;
+      d[1] = qd.z;
+      d[2] = qd.w;
+      const float p[3] = {pw.x, pw.y, pw.z};
+      int i0[3];
+      float f[3];
+      const bool in = index_sample(g, p, i0, f);
+      const int l[3] = {i0[0] - bx * B, i0[1] - by * B, i0[2] - bz * B};
+      if (!(in && l[0] >= 0 && l[0] < B && l[1] >= 0 && l[1] < B && l[2] >= 0 && l[2] < B)) {
+        if (h == 0) set_err(&w.hdr[0], kErrInternal);
+      } else {
+        // this thread's four corners (z offset h), weighted
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+          const int q = 4 * h + u;
+          const float wq = corner_weight(f[0], f[1], f[2], q);
+          const T* v = feat + corner_vertex(g, i0[0], i0[1], i0[2], q) * (size_t)C;
+#pragma unroll
+          for (int c = 0; c < xt::kMaxC; c++)
+            if (c < C) fx[c] = fmaf(wq, ldf(v + c), fx[c]);
+        }
+      }
+    }
+    if (h == 1) {
+      // partial features and the direction encoding into the staged row
+#pragma unroll
+      for (int c = 0; c < xt::kMaxC; c++)
+        if (c < C) xs[c] = fx[c];
+      if (valid)
+        encode_dir(d, mlp.n_freq, xs + C);
+      else
+        for (int j = 0; j < ne; j++) xs[C + j] = 0.0f;
+      for (int k = C + ne; k < xt::kK1; k++) xs[k] = 0.0f;
+    }
+    __syncthreads();
+    // row m of x in BF16 hi + lo: K values 24 h .. 24 h + 23 (every feature channel is below 24)
+    {
+      float x2 = 0.0f;
+      if (h == 0) {
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+          float v[8];
+#pragma unroll
+          for (int t = 0; t < 8; t++) {
+            const int k = 8 * j + t;
+            v[t] = k < xt::kMaxC && k < C ? fx[k < xt::kMaxC ? k : 0] + xs[k] : xs[k];
+            x2 = fmaf(v[t], v[t], x2);
+          }
+          store_chunk_split(a_hi, a_lo, m, 8 * j, xt::kK1, v);
+        }
+      } else {
+#pragma unroll
+        for (int j = 3; j < 6; j++) {
+          float v[8];
+#pragma unroll
+          for (int t = 0; t < 8; t++) {
+            v[t] = xs[8 * j + t];
+            x2 = fmaf(v[t], v[t], x2);
+          }
+          store_chunk_split(a_hi, a_lo, m, 8 * j, xt::kK1, v);
+        }
+      }
+      nxp[h * kTile + m] = x2;
+    }
+    fence_proxy_async();
+    fence_before();
+    __syncthreads();
+    // layer 1: W1 x into columns [0, 128)
+    if (threadIdx.x == 0) {
+      fence_after();
+      mma_split<xt::kK1 / 16>(tmem, ax_h, ax_l, b1h, b1l, idesc_bf16(kHidden));
+      mma_commit(bar);
+    }
+    alive = __syncthreads_and(mbar_wait(bar, phase, &w.hdr[0]));
+    fence_after();
+    if (!alive) break;
+    phase ^= 1u;
+    uint32_t mw1[4] = {0u, 0u, 0u, 0u}, mw2[4] = {0u, 0u, 0u, 0u};
+    const float nx = sqrtf(nxp[m] + nxp[kTile + m]);
+    bool unsure = false;
+    {
+      float v[64], h2s = 0.0f;
+      tmem_ld<64>(taddr + 64 * h, v);
+      const float tx = xt::kEps * nx;
+#pragma unroll
+      for (int q = 0; q < 8; q++) {
+        float x[8];
+#pragma unroll
+        for (int t = 0; t < 8; t++) {
+          const int n = 8 * q + t;
+          const float z = v[n] + b1s[64 * h + n];
+          relu_bit(mw1, n, h, z > 0.0f);
+          unsure |= fabsf(z) <= tx * nw1[64 * h + n];
+          x[t] = fmaxf(z, 0.0f);
+          h2s = fmaf(x[t], x[t], h2s);
+        }
+        store_chunk_split(a_hi, a_lo, m, 64 * h + 8 * q, kHidden, x);
+      }
+      hp[h * kTile + m] = h2s;
+    }
+    fence_proxy_async();
+    fence_before();
+    __syncthreads();
+    // layer 2: W2 h1 into columns [0, 128)
+    if (threadIdx.x == 0) {
+      fence_after();
+      mma_split(tmem, ah_h, ah_l, b2h, b2l, idesc_bf16(kHidden));
+      mma_commit(bar);
+    }
+    alive = __syncthreads_and(mbar_wait(bar, phase, &w.hdr[0]));
+    fence_after();
+    if (!alive) break;
+    phase ^= 1u;
+    float z0 = 0.0f, z1 = 0.0f, z2 = 0.0f;
+    {
+      float v[64];
+      tmem_ld<64>(taddr + 64 * h, v);
+      const float th = xt::kEps * (sqrtf(hp[m] + hp[kTile + m]) + nx * *fro1);
+#pragma unroll
+      for (int n = 0; n < 64; n++) {
+        const int u = 64 * h + n;
+        const float z = v[n] + b2s[u];
+        relu_bit(mw2, n, h, z > 0.0f);
+        unsure |= fabsf(z) <= th * nw2[u];
+        const float h2 = fmaxf(z, 0.0f);
+        z0 = fmaf(w3s[u], h2, z0);
+        z1 = fmaf(w3s[kHidden + u], h2, z1);
+        z2 = fmaf(w3s[2 * kHidden + u], h2, z2);
+      }
+    }
+    fence_before();
+    if (h == 1) {
+      zpart[0] = z0;
+      zpart[1] = z1;
+      zpart[2] = z2;
+#pragma unroll
+      for (int j = 0; j < 4; j++) {
+        mpart[j] = mw1[j];
+        mpart[4 + j] = mw2[j];
+      }
+      flg[m] = unsure ? 1u : 0u;
+    }
+    __syncthreads();
+    if (h == 0) {  // warps 0-3: list the uncertain samples (one atomic per warp)
+      const bool fix = valid && (unsure || flg[m] != 0u);
+      const uint32_t bal = __ballot_sync(0xffffffffu, fix);
+      uint32_t base = 0;
+      if ((threadIdx.x & 31) == 0 && bal) base = atomicAdd(&w.hdr[4], (uint32_t)__popc(bal));
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (fix) w.rec_key[base + __popc(bal & ((1u << (threadIdx.x & 31)) - 1u))] = start + m;
+    }
+    if (h == 0 && valid) {
+      const float c0 = sigmoid_f(z0 + zpart[0] + b3s[0]);
+      const float c1 = sigmoid_f(z1 + zpart[1] + b3s[1]);
+      const float c2 = sigmoid_f(z2 + zpart[2] + b3s[2]);
+      w.rec_c[rid] = make_float4(c0, c1, c2, wgt);
+      w.rec_mask[2 * (size_t)rid] = make_uint4(mw1[0] | mpart[0], mw1[1] | mpart[1], mw1[2] | mpart[2], mw1[3] | mpart[3]);
+      w.rec_mask[2 * (size_t)rid + 1] =
+          make_uint4(mw2[0] | mpart[4], mw2[1] | mpart[5], mw2[2] | mpart[6], mw2[3] | mpart[7]);
+    }
+  }
+  if (!alive) mbar_wait(bar, phase, &w.hdr[0]);  // MMAs may still be running (bounded)
+  fence_before();
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(xt::kTmemCols) : "memory");
+  }
+}
+
+cicero_status launch_fwd_x3(const cicero_grid* grid, const GridGeo& geo, const MlpPtrs& mlp, const RenderWs& ws,
+                            cudaStream_t st) {
+  const bool f16 = grid->dtype == CICERO_F16;
+  cudaError_t e = f16 ? cudaFuncSetAttribute(k_fwd_x3<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, xt::Smem::bytes)
+                      : cudaFuncSetAttribute(k_fwd_x3<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, xt::Smem::bytes);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_fwd_x3)");
+  {
+    ProfScope ps(kStGatherMlp, st);
+    if (f16)
+      k_fwd_x3<__half><<<num_sms(), xt::kThreads, xt::Smem::bytes, st>>>(geo, mlp, ws, (const __half*)grid->features);
+    else
+      k_fwd_x3<float><<<num_sms(), xt::kThreads, xt::Smem::bytes, st>>>(geo, mlp, ws, (const float*)grid->features);
+  }
+  count_launches(1);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? CICERO_OK : cuda_fail(e, "k_fwd_x3");
 }
 
 template <typename T, bool WG>

@@ -49,12 +49,14 @@ struct __align__(16) RayGeo {
 };
 
 struct RenderWs {
-  uint32_t* hdr;        // [0] error bits, [1] tile count, [2] composited samples, [3] records reserved
+  uint32_t* hdr;        // [0] error bits, [1] tile count, [2] composited samples, [3] records reserved,
+                        // [4] samples listed for the FP32 fix-up of the backward's forward recompute
   uint32_t* ray_n;      // [R] composited samples of each ray
   uint32_t* ray_start;  // [R] first record of each ray
   float* ray_T;         // [R] transmittance after the last composited slot
   float4* ray_dir;      // [R] unit direction of each ray
-  uint32_t* rec_key;    // [Q] RIT key: brick id * kOctants + octant
+  uint32_t* rec_key;    // [Q] RIT key: brick id * kOctants + octant; once the RIT is built, the backward's
+                        // forward recompute lists its uncertain samples here (sorted record indices)
   float* rec_w;         // [Q] weight T_k alpha_k
   uint16_t* rec_slot;   // [Q] slot index
   float4* rec_c;        // [Q] (c_r, c_g, c_b, w) of each record (written by the gather, in record order)
@@ -240,5 +242,11 @@ cicero_status run_backward(const cicero_grid* grid, const MlpPtrs& mlp, const Re
                            const RenderWs& ws, const float* d_rgb, float* d_dens, float* d_feat, float* d_mlp,
                            cudaStream_t st);
 cicero_status launch_mlp_eval_f32(const MlpPtrs& mlp, const float* x, int M, float* c, cudaStream_t st);
+
+// The backward's forward recompute on the tensor cores (split-BF16 products, FP32 accumulation):
+// (c, w) into rec_c and the ReLU masks into rec_mask for every composited sample (backward.cu)
+bool fwd_x3_supported(const GridGeo& g, const MlpPtrs& mlp);
+cicero_status launch_fwd_x3(const cicero_grid* grid, const GridGeo& geo, const MlpPtrs& mlp, const RenderWs& ws,
+                            cudaStream_t st);
 
 }  // namespace cicero

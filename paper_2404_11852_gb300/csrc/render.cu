@@ -1224,6 +1224,87 @@ __global__ void __launch_bounds__(kMlpThreads + kProdThreads, 1)
   }
 }
 
+// The samples that the backward's tensor-core forward recompute (k_fwd_x3) could not certify (a
+// ReLU pre-activation within the error bound of its split-BF16 products), recomputed with the FP32
+// MLP of K5f: (c, w) and both ReLU masks overwritten.  The list holds sorted record indices
+// (rec_key, count in hdr[4]); 128 samples per step, features interpolated from global memory.
+template <typename T>
+__global__ void __launch_bounds__(kMlpThreads, 1) k_fwd_fix(GridGeo g, MlpPtrs mlp, RenderWs w,
+                                                           const T* __restrict__ feat) {
+  extern __shared__ __align__(128) char sm[];
+  float* X = (float*)(sm + F32Smem::x);
+  uint8_t* msk = (uint8_t*)(sm + F32Smem::x2);  // [2][16][128] ReLU bytes (store_relu_bits)
+  load_mlp_f32_smem(sm, mlp);
+  const uint32_t n = w.hdr[4];
+  const int C = g.C, m = threadIdx.x;
+  const int ne = 3 + 6 * mlp.n_freq;
+  for (uint32_t base = blockIdx.x * kTile; base < n; base += gridDim.x * kTile) {
+    const bool valid = m < kTile && base + m < n;
+    uint32_t si = 0;
+    __syncthreads();  // the weights, or the previous step's reads of X and the masks
+    if (m < kTile) {
+      if (valid) {
+        si = w.rec_key[base + m];
+        const float4 pw = w.srt[si].pw, qd = w.srt[si].qd;
+        const float p[3] = {pw.x, pw.y, pw.z}, d[3] = {qd.y, qd.z, qd.w};
+        int i0[3];
+        float f[3], e[3 + 6 * 7];
+        const bool ok = index_sample(g, p, i0, f);
+        for (int c = 0; c < C; c++) {
+          float v = 0.0f;
+          if (ok) {
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+              const float wq = ((q & 1) ? f[0] : 1.f - f[0]) * (((q >> 1) & 1) ? f[1] : 1.f - f[1]) *
+                               ((q >> 2) ? f[2] : 1.f - f[2]);
+              const size_t vx = ((size_t)(i0[2] + (q >> 2)) * g.n[1] + (i0[1] + ((q >> 1) & 1))) * g.n[0] +
+                                (i0[0] + (q & 1));
+              v = fmaf(wq, ldf(feat + vx * C + c), v);
+            }
+          }
+          X[c * kTile + m] = v;
+        }
+        encode_dir(d, mlp.n_freq, e);
+        for (int j = 0; j < ne; j++) X[(C + j) * kTile + m] = e[j];
+        for (int j = C + ne; j < kK1; j++) X[j * kTile + m] = 0.0f;
+      } else {
+        for (int j = 0; j < kK1; j++) X[j * kTile + m] = 0.0f;
+      }
+    }
+    __syncthreads();
+    float c[3];
+    mlp_f32_tile(sm, X, c, mlp.in_dim, 0, msk);
+    if (valid) {
+      const uint32_t rid = __float_as_uint(w.srt[si].qd.x);
+      w.rec_c[rid] = make_float4(c[0], c[1], c[2], w.srt[si].pw.w);
+      uint32_t v[8];
+#pragma unroll
+      for (int q = 0; q < 8; q++) {
+        const uint8_t* src = msk + (q >> 2) * 16 * kTile + (q & 3) * 4 * kTile + m;
+        v[q] = (uint32_t)src[0] | ((uint32_t)src[kTile] << 8) | ((uint32_t)src[2 * kTile] << 16) |
+               ((uint32_t)src[3 * kTile] << 24);
+      }
+      w.rec_mask[2 * (size_t)rid] = make_uint4(v[0], v[1], v[2], v[3]);
+      w.rec_mask[2 * (size_t)rid + 1] = make_uint4(v[4], v[5], v[6], v[7]);
+    }
+  }
+}
+
+template <typename T>
+static cicero_status launch_fwd_fix(const GridGeo& geo, const MlpPtrs& mlp, const RenderWs& ws, const void* feat,
+                                    cudaStream_t st) {
+  const int smem = F32Smem::x2 + 2 * 16 * kTile;
+  cudaError_t e = cudaFuncSetAttribute(k_fwd_fix<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_fwd_fix)");
+  {
+    ProfScope ps(kStGatherMlp, st);
+    k_fwd_fix<T><<<num_sms(), kMlpThreads, smem, st>>>(geo, mlp, ws, (const T*)feat);
+  }
+  count_launches(1);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? CICERO_OK : cuda_fail(e, "k_fwd_fix");
+}
+
 // K6: per ray, in slot order.
 // Sum over one ray's n records of w c: lane l takes records l, l + 32, l + 64, ... in that order
 // (so every caller sums identically), with the loads of four of them issued before their sums.
@@ -1510,6 +1591,13 @@ cicero_status run_render(const cicero_grid* grid, const MlpPtrs& mlp, const Rend
     return s;
   } else if (plan.precision == CICERO_MLP_BF16) {
     s = launch_gather_mlp_bf16(grid, geo, plan.mlp_groups, mlp, ws, map, box, st);
+  } else if (ws.rec_mask && fwd_x3_supported(geo, mlp)) {
+    // a backward follows: colours and ReLU masks only, on the tensor cores, then the uncertain
+    // samples again in FP32
+    s = launch_fwd_x3(grid, geo, mlp, ws, st);
+    if (s == CICERO_OK)
+      s = f16 ? launch_fwd_fix<__half>(geo, mlp, ws, grid->features, st)
+              : launch_fwd_fix<float>(geo, mlp, ws, grid->features, st);
   } else {
     s = f16 ? launch_f32<__half>(geo, plan.S, mlp, ws, map, box, st)
             : launch_f32<float>(geo, plan.S, mlp, ws, map, box, st);
