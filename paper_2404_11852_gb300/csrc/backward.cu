@@ -634,19 +634,56 @@ __global__ void __launch_bounds__(bt::kThreads, 1) k_bwd_brick_tc(GridGeo g, Mlp
   const uint32_t n_tiles = w.hdr[1];
   const uint32_t per = (n_tiles + gridDim.x - 1) / gridDim.x;
   const uint32_t t_begin = blockIdx.x * per, t_end = min(n_tiles, t_begin + per);
+  // This thread's sample of the next tile, loaded in three dependent levels: the sorted record
+  // (position, record index), then the record's ray, colour, dL/draw and ReLU masks, then the ray's
+  // dL/drgb.  The first level of tile t + 1 is issued when tile t starts, the others after its
+  // MMA waits, so the chain of loads runs behind tile t's work.
+  uint4 n_td = make_uint4(0u, 0u, 0u, 0u), n_m1 = n_td, n_m2 = n_td;
+  float4 n_pw = make_float4(0.f, 0.f, 0.f, 0.f), n_cw = n_pw;
+  uint32_t n_rid = 0, n_r = 0;
+  float n_draw = 0.f, n_g0 = 0.f, n_g1 = 0.f, n_g2 = 0.f;
+  auto level_a = [&](uint32_t t) {
+    n_td = w.tile[t];
+    if (m < (int)(n_td.y & 0xFFu)) {
+      n_pw = w.srt[n_td.x + m].pw;
+      n_rid = __float_as_uint(w.srt[n_td.x + m].qd.x);
+    }
+  };
+  auto level_b = [&]() {
+    if (m < (int)(n_td.y & 0xFFu)) {
+      n_r = w.rec_ray[n_rid];
+      n_cw = w.rec_c[n_rid];
+      n_draw = w.rec_raw[n_rid];
+      n_m1 = w.rec_mask[2 * (size_t)n_rid];
+      n_m2 = w.rec_mask[2 * (size_t)n_rid + 1];
+    }
+  };
+  auto level_c = [&]() {
+    if (m < (int)(n_td.y & 0xFFu)) {
+      n_g0 = d_rgb[3 * n_r];
+      n_g1 = d_rgb[3 * n_r + 1];
+      n_g2 = d_rgb[3 * n_r + 2];
+    }
+  };
+  if (t_begin < t_end) {
+    level_a(t_begin);
+    level_b();
+    level_c();
+  }
   for (uint32_t ti = t_begin; ti < t_end && alive; ti++) {
-    const uint4 td = w.tile[ti];
-    const uint32_t start = td.x;
+    const uint4 td = n_td;
+    const float4 pw = n_pw, cw = n_cw;
+    const uint4 m1 = n_m1, m2 = n_m2;
+    const float draw = n_draw, g0 = n_g0, g1 = n_g1, g2 = n_g2;
+    const bool more = ti + 1 < t_end;
+    if (more) level_a(ti + 1);
     const int mcnt = (int)(td.y & 0xFFu);
     const int bx = (int)(td.w & 0xFFFFu), by = (int)(td.w >> 16), bz = (int)((td.y >> 8) & 0x1FFFu);
-    // this thread's sample: its brick-local voxel, weights of the colour gradient, ReLU masks
+    // this thread's sample: its voxel, weights of the colour gradient
     bool ok = false;
-    float dz0 = 0.f, dz1 = 0.f, dz2 = 0.f, draw = 0.f, f[3] = {0.f, 0.f, 0.f};
+    float dz0 = 0.f, dz1 = 0.f, dz2 = 0.f, f[3] = {0.f, 0.f, 0.f};
     int i0[3] = {0, 0, 0};
-    uint4 m1 = make_uint4(0u, 0u, 0u, 0u), m2 = m1;
     if (m < mcnt) {
-      const float4 pw = w.srt[start + m].pw;
-      const uint32_t rid = __float_as_uint(w.srt[start + m].qd.x);
       const float p[3] = {pw.x, pw.y, pw.z};
       const bool in = index_sample(g, p, i0, f);
       const int l[3] = {i0[0] - bx * B, i0[1] - by * B, i0[2] - bz * B};
@@ -654,14 +691,9 @@ __global__ void __launch_bounds__(bt::kThreads, 1) k_bwd_brick_tc(GridGeo g, Mlp
       if (!ok) {
         if (h == 0) set_err(&w.hdr[0], kErrInternal);
       } else {
-        const int r = (int)w.rec_ray[rid];
-        const float4 cw = w.rec_c[rid];
-        draw = w.rec_raw[rid];
-        m1 = w.rec_mask[2 * (size_t)rid];
-        m2 = w.rec_mask[2 * (size_t)rid + 1];
-        dz0 = cw.w * d_rgb[3 * r] * cw.x * (1.0f - cw.x);
-        dz1 = cw.w * d_rgb[3 * r + 1] * cw.y * (1.0f - cw.y);
-        dz2 = cw.w * d_rgb[3 * r + 2] * cw.z * (1.0f - cw.z);
+        dz0 = cw.w * g0 * cw.x * (1.0f - cw.x);
+        dz1 = cw.w * g1 * cw.y * (1.0f - cw.y);
+        dz2 = cw.w * g2 * cw.z * (1.0f - cw.z);
       }
     }
     // dh2 = (dz3 W3) masked by relu'(z2): this thread's half of row m of A
@@ -696,6 +728,7 @@ __global__ void __launch_bounds__(bt::kThreads, 1) k_bwd_brick_tc(GridGeo g, Mlp
     fence_after();
     if (!alive) break;
     phase ^= 1u;
+    if (more) level_b();
     // dh1 masked by relu'(z1) -> this thread's half of row m of A (dh2 is no longer read)
     {
       const HalfMask mk(m1, h);
@@ -722,6 +755,7 @@ __global__ void __launch_bounds__(bt::kThreads, 1) k_bwd_brick_tc(GridGeo g, Mlp
     fence_after();
     if (!alive) break;
     phase ^= 1u;
+    if (more) level_c();
     float dft[16];
     tmem_ld<16>(taddr, dft);
     fence_before();
@@ -897,8 +931,21 @@ __global__ void __launch_bounds__(xt::kThreads, 1) k_fwd_x3(GridGeo g, MlpPtrs m
   const uint32_t n_tiles = w.hdr[1];
   const uint32_t per = (n_tiles + gridDim.x - 1) / gridDim.x;
   const uint32_t t_begin = blockIdx.x * per, t_end = min(n_tiles, t_begin + per);
+  // this thread's sorted record of the next tile, loaded when the current tile starts
+  uint4 n_td = make_uint4(0u, 0u, 0u, 0u);
+  float4 n_pw = make_float4(0.f, 0.f, 0.f, 0.f), n_qd = n_pw;
+  auto prefetch = [&](uint32_t t) {
+    n_td = w.tile[t];
+    if (m < (int)(n_td.y & 0xFFu)) {
+      n_pw = w.srt[n_td.x + m].pw;
+      n_qd = w.srt[n_td.x + m].qd;
+    }
+  };
+  if (t_begin < t_end) prefetch(t_begin);
   for (uint32_t ti = t_begin; ti < t_end && alive; ti++) {
-    const uint4 td = w.tile[ti];
+    const uint4 td = n_td;
+    const float4 pw = n_pw, qd = n_qd;
+    if (ti + 1 < t_end) prefetch(ti + 1);
     const uint32_t start = td.x;
     const int mcnt = (int)(td.y & 0xFFu);
     const int bx = (int)(td.w & 0xFFFFu), by = (int)(td.w >> 16), bz = (int)((td.y >> 8) & 0x1FFFu);
@@ -908,8 +955,6 @@ __global__ void __launch_bounds__(xt::kThreads, 1) k_fwd_x3(GridGeo g, MlpPtrs m
 #pragma unroll
     for (int c = 0; c < xt::kMaxC; c++) fx[c] = 0.0f;
     if (valid) {
-      const float4 pw = w.srt[start + m].pw;
-      const float4 qd = w.srt[start + m].qd;
       rid = __float_as_uint(qd.x);
       wgt = pw.w;
       d[0] = qd.y;
