@@ -59,10 +59,11 @@ struct RenderWs {
                         // forward recompute lists its uncertain samples here (sorted record indices)
   float* rec_w;         // [Q] weight T_k alpha_k
   uint16_t* rec_slot;   // [Q] slot index
-  float4* rec_c;        // [Q] (c_r, c_g, c_b, w) of each record (written by the gather, in record order)
+  float4* rec_c;        // [Q] (c_r, c_g, c_b, w) of each record (written by the gather, in record order); in
+                        // the backward, B1 replaces it by (dL/dz3 [3], dL/draw)
   float* rec_T;         // [Q] transmittance before the slot (backward only; may be null)
-  float* rec_raw;       // [Q] interpolated raw density, then dL/draw (backward only; may be null)
-  uint32_t* rec_ray;    // [Q] ray of each record (backward and RIT export only; may be null)
+  float* rec_raw;       // [Q] interpolated raw density (backward only; may be null)
+  uint32_t* rec_ray;    // [Q] ray of each record (RIT export only; may be null)
   uint4* rec_mask;      // [Q][2] ReLU masks of MLP layers 1 and 2 from the FP32 forward (backward only; may be
                         // null): hidden unit n < 64 is bit n % 4 of byte n / 4, unit 64 + n is bit 4 + n % 4
   uint32_t* brick_cnt;  // [nb * kOctants] records per RIT key

@@ -35,7 +35,7 @@ size_t render_ws_bytes(const RenderPlan& p) {
   b += 3 * al256(4 * R) + al256(16 * R) + al256(32 * R);
   b += 2 * al256(4 * Q) + al256(2 * Q) + al256(16 * Q);
   if (p.want_bwd) b += 2 * al256(4 * Q) + al256(32 * Q);
-  if (p.want_k || p.want_bwd) b += al256(4 * Q);
+  if (p.want_k) b += al256(4 * Q);
   const size_t nk = (size_t)p.nb * kOctants;  // RIT keys: (brick, octant)
   b += 2 * al256(4 * nk) + al256(4 * (nk + 1)) + al256(4 * ((size_t)p.nb + 1));
   b += al256(8 * ((size_t)p.nb / kScanChunk + 2));
@@ -66,7 +66,7 @@ bool carve_render_ws(void* ws, size_t bytes, const RenderPlan& p, RenderWs* w) {
   w->rec_c = (float4*)take(16 * Q);
   w->rec_T = p.want_bwd ? (float*)take(4 * Q) : nullptr;
   w->rec_raw = p.want_bwd ? (float*)take(4 * Q) : nullptr;
-  w->rec_ray = (p.want_k || p.want_bwd) ? (uint32_t*)take(4 * Q) : nullptr;
+  w->rec_ray = p.want_k ? (uint32_t*)take(4 * Q) : nullptr;
   w->rec_mask = p.want_bwd ? (uint4*)take(32 * Q) : nullptr;
   const size_t nk = (size_t)p.nb * kOctants;
   w->brick_cnt = (uint32_t*)take(4 * nk);
