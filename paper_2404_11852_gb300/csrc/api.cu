@@ -702,6 +702,17 @@ size_t cicero_warp_workspace_size(const cicero_camera* tgt_cam) {
 }
 
 
+// The backward's plan: FP32, bricks of 8 (fewer, fuller tiles for the tensor-core kernels, which
+// take up to 16 channels); bricks of 4 above that, where the FP32 recompute stages each brick in
+// shared memory beside its two input buffers.
+static cicero_options backward_options(const cicero_grid* grid) {
+  cicero_options o;
+  memset(&o, 0, sizeof o);
+  o.precision = CICERO_MLP_FP32;
+  o.brick = (grid && grid->C > 16) ? 4 : 8;
+  return o;
+}
+
 cicero_status cicero_render_backward(const cicero_grid* grid, const cicero_mlp* mlp, const float* ray_o,
                                      const float* ray_d, int n_rays, const cicero_sampling* sampling,
                                      const float* d_rgb, float* d_density, float* d_features, float* d_mlp,
@@ -709,7 +720,8 @@ cicero_status cicero_render_backward(const cicero_grid* grid, const cicero_mlp* 
   if (n_rays > 0 && (!ray_o || !ray_d || !d_rgb)) return fail(CICERO_ERR_INVALID_ARG, "ray_o/ray_d/d_rgb is NULL");
   if (!d_density || !d_features) return fail(CICERO_ERR_INVALID_ARG, "d_density/d_features is NULL");
   RenderPlan plan;
-  cicero_status st = plan_render(grid, mlp, n_rays, sampling, nullptr, &plan, true);
+  const cicero_options opt = backward_options(grid);
+  cicero_status st = plan_render(grid, mlp, n_rays, sampling, &opt, &plan, true);
   if (st != CICERO_OK) return st;
   plan.want_bwd = true;
   if (!ws_ok(workspace)) return fail(CICERO_ERR_INVALID_ARG, "workspace must be non-NULL and 256-byte aligned");
@@ -728,7 +740,8 @@ cicero_status cicero_render_backward(const cicero_grid* grid, const cicero_mlp* 
 
 size_t cicero_backward_workspace_size(const cicero_grid* grid, int n_rays, const cicero_sampling* sampling) {
   RenderPlan plan;
-  if (plan_render(grid, nullptr, n_rays, sampling, nullptr, &plan, false) != CICERO_OK) return 0;
+  const cicero_options opt = backward_options(grid);
+  if (plan_render(grid, nullptr, n_rays, sampling, &opt, &plan, false) != CICERO_OK) return 0;
   plan.want_bwd = true;
   return render_ws_bytes(plan);
 }

@@ -82,10 +82,12 @@ def test_backward_larger_scene(cc, orc, brick_scene):
     assert rel_inf(df, wf) <= 1e-3, rel_inf(df, wf)
 
 
-@pytest.mark.parametrize("C, feat_offset", [(6, 0), (12, 1), (12, 4)])
+@pytest.mark.parametrize("C, feat_offset", [(6, 0), (12, 1), (12, 4), (20, 0)])
 def test_backward_channel_layouts(cc, orc, C, feat_offset):
     """The trilinear adjoint adds four channels per 16-byte atomic when C % 4 == 0 and d_features
-    is 16-byte aligned, one channel per atomic otherwise: both paths against the oracle."""
+    is 16-byte aligned, one channel per atomic otherwise: both paths against the oracle.  C = 20
+    is beyond the tensor-core kernels (at most 16 channels): the FP32 recompute and the CUDA-core
+    grid-gradient kernel run instead."""
     g = scenes.make_grid(40, C, 6, seed=41)
     m = scenes.make_mlp(C, seed=42, random_bias=True)
     o, d = scenes.random_rays(200, seed=43)
