@@ -703,8 +703,8 @@ def backward_workload(cc, torch, dev):
     ws_f = cc.workspace(cc.cicero_render_workspace_size(gd.desc, R, sd, opt), dev)
     ws_b = cc.workspace(cc.cicero_backward_workspace_size(gd.desc, R, sd), dev)
 
-    def fwd():
-        cc.cicero_render_rays(gd.desc, md.desc, ot, dt, sd, opt, rgb, depth, None, None, ws_f)
+    def fwd(o=opt):
+        cc.cicero_render_rays(gd.desc, md.desc, ot, dt, sd, o, rgb, depth, None, None, ws_f)
 
     dm = torch.zeros(m.flat().size, device=dev)
 
@@ -714,6 +714,10 @@ def backward_workload(cc, torch, dev):
 
     fwd()
     t_f = event_ms(torch, fwd, 5)
+    # the same forward with the FP32-class tensor-core MLP (split BF16), then the FP32 one again,
+    # whose colours feed the loss gradient
+    t_fs = event_ms(torch, lambda: fwd(cc.options(cc.MLP_FP32_SPLIT, 8)), 5)
+    fwd()
     t_b = event_ms(torch, bwd, 5)
     t_bm = event_ms(torch, lambda: bwd(dm), 5)
     cc.cicero_workspace_status(ws_f)
@@ -757,8 +761,9 @@ def backward_workload(cc, torch, dev):
                             "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach / fp32_peak,
                             "peak_src": "derived: SMs x 128 FP32 lanes x 2 x 2070 MHz"}
     return {"workload": "8192 rays x 256 samples, 160^3 x 12 FP32 grid, MSE loss", "forward_ms": t_f,
-            "backward_ms": t_b, "backward_with_mlp_weights_ms": t_bm,
-            "rays_per_s_fwd_bwd": R / ((t_f + t_b) / 1e3), "composited_samples": samples,
+            "forward_split_bf16_ms": t_fs, "backward_ms": t_b, "backward_with_mlp_weights_ms": t_bm,
+            "rays_per_s_fwd_bwd": R / ((t_f + t_b) / 1e3),
+            "rays_per_s_fwd_bwd_split_forward": R / ((t_fs + t_b) / 1e3), "composited_samples": samples,
             "fp32_recomputed_samples": fixed,
             "stage_ms": stage, "k_bwd_brick_roofline": roof,
             "grad_bytes": int(dd.numel() * 4 + df.numel() * 4)}
@@ -891,6 +896,7 @@ def main():
     b32, tune32 = cc.cicero_autotune_brick(grid.desc, mlp.desc, cd, sd, cc.MLP_FP32, ref_rgb, ref_depth, ws_t)
     del ws_t, ref_rgb, ref_depth
     o16, o32 = cc.options(cc.MLP_BF16, b16), cc.options(cc.MLP_FP32, b32)
+    o_split = cc.options(cc.MLP_FP32_SPLIT, b32)  # FP32-class MLP on the tensor cores (split BF16)
     # all targets' holes are rendered in one batched pass; records are capped well above need
     ob = cc.options(cc.MLP_BF16, b16, max_records=HOLE_RECORDS)
     win = SparwWindow(cc, torch, dev, grid, mlp, cam, targets, o16, ob,
@@ -995,6 +1001,7 @@ def main():
     hdr = win.header(win.ws_r)
     active = int(hdr[2])
     t_bf16 = timed(lambda: full(o16), n_fp, 1)
+    t_split = timed(lambda: full(o_split), n_fp, 1)
 
     # per-stage device time (CUDA events on the launching stream) over two profiled windows
     cc.cicero_profile_begin()
@@ -1045,6 +1052,11 @@ def main():
         e = np.where(ref["amb"][:, None], np.minimum(np.abs(got - ref["rgb"]), np.abs(got - ref["rgb_alt"])),
                      np.abs(got - ref["rgb"]))
         quality["ref_fp32_max_err"] = float(e.max())
+        full(o_split)
+        got = win.ref_rgb.cpu().double().numpy()[pix]
+        e = np.where(ref["amb"][:, None], np.minimum(np.abs(got - ref["rgb"]), np.abs(got - ref["rgb_alt"])),
+                     np.abs(got - ref["rgb"]))
+        quality["ref_fp32_split_max_err"] = float(e.max())
         frames = []
         dt, cores, _ = oracle_window(args.cpu_res, rank, frames)
         quality["sparw_bf16_vs_oracle_sparw"] = sparw_parity(cc, torch, dev, grid, mlp, args.cpu_res, rank, frames,
@@ -1089,6 +1101,8 @@ def main():
             "bf16_full_fps": n_fp * world / t_bf16,
             "msamples_per_s_bf16_full": active * n_fp * world / t_bf16 / 1e6,
             "msamples_per_s_fp32_full": active * n_fp * world / t_fp32 / 1e6,
+            "fp32_split_full_fps": n_fp * world / t_split,
+            "msamples_per_s_fp32_split_full": active * n_fp * world / t_split / 1e6,
             "active_samples_per_frame": active,
             "autotune_ms_by_brick": {"bf16": tune16, "fp32": tune32}, "brick": {"bf16": b16, "fp32": b32},
             "fraction_rays_marched_targets": holes / (N_TARGETS * R),

@@ -46,8 +46,13 @@ typedef enum { CICERO_F32 = 0, CICERO_F16 = 1 } cicero_dtype;
 
 /* Arithmetic of Feature Computation (the MLP):
  * FP32: FP32 FFMA on CUDA cores.  BF16: tcgen05 tensor-core MMAs with BF16 operands (weights and
- * activations rounded to BF16) and FP32 accumulation in tensor memory. */
-typedef enum { CICERO_MLP_FP32 = 0, CICERO_MLP_BF16 = 1 } cicero_precision;
+ * activations rounded to BF16) and FP32 accumulation in tensor memory.  FP32_SPLIT: FP32-class
+ * accuracy on the tensor cores: every FP32 operand v of layers 1 and 2 is split into
+ * hi = bf16(v) and lo = bf16(v - hi), each product taken as hi.hi + hi.lo + lo.hi (the method of
+ * Henry, Tang and Heinecke, ARITH 2019) with FP32 accumulation in tensor memory, so a product keeps
+ * ~16 of FP32's 24 significand bits; biases, layer 3 and the sigmoid in FP32.  It needs C <= 16
+ * and is taken by cicero_render and cicero_render_rays only. */
+typedef enum { CICERO_MLP_FP32 = 0, CICERO_MLP_BF16 = 1, CICERO_MLP_FP32_SPLIT = 2 } cicero_precision;
 
 /* Dense voxel grid (Sec. II-B: a feature vector is stored at every vertex of the grid).
  * Vertices sit on the corners of the box [aabb_min, aabb_max]; n[a] vertices along axis a.

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libcicero.so")
 
 OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_ALIGNMENT, ERR_WORKSPACE, ERR_CUDA, ERR_TIMEOUT, ERR_INTERNAL = range(8)
 F32, F16 = 0, 1
-MLP_FP32, MLP_BF16 = 0, 1
+MLP_FP32, MLP_BF16, MLP_FP32_SPLIT = 0, 1, 2
 
 
 class CiceroError(RuntimeError):

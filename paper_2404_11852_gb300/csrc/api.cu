@@ -234,7 +234,7 @@ static cicero_status plan_render(const cicero_grid* grid, const cicero_mlp* mlp,
   p->want_k = false;
   p->want_bwd = false;
   p->precision = opt ? opt->precision : CICERO_MLP_FP32;
-  if (p->precision != CICERO_MLP_FP32 && p->precision != CICERO_MLP_BF16)
+  if (p->precision != CICERO_MLP_FP32 && p->precision != CICERO_MLP_BF16 && p->precision != CICERO_MLP_FP32_SPLIT)
     return fail(CICERO_ERR_INVALID_ARG, "precision");
   p->mlp_groups = opt ? opt->mlp_groups : 0;
   if (p->mlp_groups < 0 || p->mlp_groups > 4) return fail(CICERO_ERR_INVALID_ARG, "mlp_groups must be 0..4");
@@ -758,6 +758,7 @@ cicero_status cicero_mlp_eval(const cicero_mlp* mlp, const float* x, int M, cice
   const MlpPtrs p = mlp_ptrs(mlp);
   if (precision == CICERO_MLP_BF16) return launch_mlp_eval_bf16(p, x, M, c, (uint32_t*)workspace, (cudaStream_t)stream);
   if (precision == CICERO_MLP_FP32) return launch_mlp_eval_f32(p, x, M, c, (cudaStream_t)stream);
+  if (precision == CICERO_MLP_FP32_SPLIT) return fail(CICERO_ERR_UNSUPPORTED, "the split-BF16 MLP runs inside the renders only");
   return fail(CICERO_ERR_INVALID_ARG, "precision");
 }
 

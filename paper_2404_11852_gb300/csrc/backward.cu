@@ -836,7 +836,9 @@ __device__ __forceinline__ void relu_bit(uint32_t mw[4], int n, int h, bool on) 
   mw[n >> 4] |= (on ? 1u : 0u) << (((n >> 2) & 3) * 8 + 4 * h + (n & 3));
 }
 
-template <typename T>
+// BWD: the backward's recompute (masks, uncertain samples listed); otherwise a forward render's
+// Feature Computation (colours only).
+template <typename T, bool BWD>
 __global__ void __launch_bounds__(xt::kThreads, 1) k_fwd_x3(GridGeo g, MlpPtrs mlp, RenderWs w,
                                                             const T* __restrict__ feat) {
   using namespace tc;
@@ -1041,8 +1043,10 @@ __global__ void __launch_bounds__(xt::kThreads, 1) k_fwd_x3(GridGeo g, MlpPtrs m
         for (int t = 0; t < 8; t++) {
           const int n = 8 * q + t;
           const float z = v[n] + b1s[64 * h + n];
-          relu_bit(mw1, n, h, z > 0.0f);
-          unsure |= fabsf(z) <= tx * nw1[64 * h + n];
+          if constexpr (BWD) {
+            relu_bit(mw1, n, h, z > 0.0f);
+            unsure |= fabsf(z) <= tx * nw1[64 * h + n];
+          }
           x[t] = fmaxf(z, 0.0f);
           h2s = fmaf(x[t], x[t], h2s);
         }
@@ -1072,8 +1076,10 @@ __global__ void __launch_bounds__(xt::kThreads, 1) k_fwd_x3(GridGeo g, MlpPtrs m
       for (int n = 0; n < 64; n++) {
         const int u = 64 * h + n;
         const float z = v[n] + b2s[u];
-        relu_bit(mw2, n, h, z > 0.0f);
-        unsure |= fabsf(z) <= th * nw2[u];
+        if constexpr (BWD) {
+          relu_bit(mw2, n, h, z > 0.0f);
+          unsure |= fabsf(z) <= th * nw2[u];
+        }
         const float h2 = fmaxf(z, 0.0f);
         z0 = fmaf(w3s[u], h2, z0);
         z1 = fmaf(w3s[kHidden + u], h2, z1);
@@ -1093,7 +1099,7 @@ __global__ void __launch_bounds__(xt::kThreads, 1) k_fwd_x3(GridGeo g, MlpPtrs m
       flg[m] = unsure ? 1u : 0u;
     }
     __syncthreads();
-    if (h == 0) {  // warps 0-3: list the uncertain samples (one atomic per warp)
+    if (BWD && h == 0) {  // warps 0-3: list the uncertain samples (one atomic per warp)
       const bool fix = valid && (unsure || flg[m] != 0u);
       const uint32_t bal = __ballot_sync(0xffffffffu, fix);
       uint32_t base = 0;
@@ -1106,9 +1112,12 @@ __global__ void __launch_bounds__(xt::kThreads, 1) k_fwd_x3(GridGeo g, MlpPtrs m
       const float c1 = sigmoid_f(z1 + zpart[1] + b3s[1]);
       const float c2 = sigmoid_f(z2 + zpart[2] + b3s[2]);
       w.rec_c[rid] = make_float4(c0, c1, c2, wgt);
-      w.rec_mask[2 * (size_t)rid] = make_uint4(mw1[0] | mpart[0], mw1[1] | mpart[1], mw1[2] | mpart[2], mw1[3] | mpart[3]);
-      w.rec_mask[2 * (size_t)rid + 1] =
-          make_uint4(mw2[0] | mpart[4], mw2[1] | mpart[5], mw2[2] | mpart[6], mw2[3] | mpart[7]);
+      if constexpr (BWD) {
+        w.rec_mask[2 * (size_t)rid] =
+            make_uint4(mw1[0] | mpart[0], mw1[1] | mpart[1], mw1[2] | mpart[2], mw1[3] | mpart[3]);
+        w.rec_mask[2 * (size_t)rid + 1] =
+            make_uint4(mw2[0] | mpart[4], mw2[1] | mpart[5], mw2[2] | mpart[6], mw2[3] | mpart[7]);
+      }
     }
   }
   if (!alive) mbar_wait(bar, phase, &w.hdr[0]);  // MMAs may still be running (bounded)
@@ -1122,17 +1131,33 @@ __global__ void __launch_bounds__(xt::kThreads, 1) k_fwd_x3(GridGeo g, MlpPtrs m
 
 cicero_status launch_fwd_x3(const cicero_grid* grid, const GridGeo& geo, const MlpPtrs& mlp, const RenderWs& ws,
                             cudaStream_t st) {
-  const bool f16 = grid->dtype == CICERO_F16;
-  cudaError_t e = f16 ? cudaFuncSetAttribute(k_fwd_x3<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, xt::Smem::bytes)
-                      : cudaFuncSetAttribute(k_fwd_x3<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, xt::Smem::bytes);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_fwd_x3)");
+  const bool f16 = grid->dtype == CICERO_F16, bwd = ws.rec_mask != nullptr;
+  cudaError_t e = cudaSuccess;
+  const int sb = xt::Smem::bytes;
+  const dim3 grid_dim(num_sms()), block(xt::kThreads);
   {
     ProfScope ps(kStGatherMlp, st);
-    if (f16)
-      k_fwd_x3<__half><<<num_sms(), xt::kThreads, xt::Smem::bytes, st>>>(geo, mlp, ws, (const __half*)grid->features);
-    else
-      k_fwd_x3<float><<<num_sms(), xt::kThreads, xt::Smem::bytes, st>>>(geo, mlp, ws, (const float*)grid->features);
+    if (f16) {
+      const __half* feat = (const __half*)grid->features;
+      if (bwd) {
+        e = cudaFuncSetAttribute(k_fwd_x3<__half, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sb);
+        if (e == cudaSuccess) k_fwd_x3<__half, true><<<grid_dim, block, sb, st>>>(geo, mlp, ws, feat);
+      } else {
+        e = cudaFuncSetAttribute(k_fwd_x3<__half, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sb);
+        if (e == cudaSuccess) k_fwd_x3<__half, false><<<grid_dim, block, sb, st>>>(geo, mlp, ws, feat);
+      }
+    } else {
+      const float* feat = (const float*)grid->features;
+      if (bwd) {
+        e = cudaFuncSetAttribute(k_fwd_x3<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sb);
+        if (e == cudaSuccess) k_fwd_x3<float, true><<<grid_dim, block, sb, st>>>(geo, mlp, ws, feat);
+      } else {
+        e = cudaFuncSetAttribute(k_fwd_x3<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sb);
+        if (e == cudaSuccess) k_fwd_x3<float, false><<<grid_dim, block, sb, st>>>(geo, mlp, ws, feat);
+      }
+    }
   }
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_fwd_x3)");
   count_launches(1);
   e = cudaGetLastError();
   return e == cudaSuccess ? CICERO_OK : cuda_fail(e, "k_fwd_x3");

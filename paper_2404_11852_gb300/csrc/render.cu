@@ -1587,10 +1587,11 @@ cicero_status run_render(const cicero_grid* grid, const MlpPtrs& mlp, const Rend
   CUtensorMap map;
   if (hash) {
     s = launch_gather_mlp_bf16_hash(geo, mlp, ws, *hash, st);  // features from the hash encoding
-  } else if ((s = encode_brick_map(grid, geo, box, &map)) != CICERO_OK) {
-    return s;
-  } else if (plan.precision == CICERO_MLP_BF16) {
-    s = launch_gather_mlp_bf16(grid, geo, plan.mlp_groups, mlp, ws, map, box, st);
+  } else if (plan.precision == CICERO_MLP_FP32_SPLIT) {
+    // split-BF16 tensor-core MLP, features read from global memory (no staged brick)
+    if (!fwd_x3_supported(geo, mlp))
+      return fail(CICERO_ERR_UNSUPPORTED, "the split-BF16 MLP takes at most 16 feature channels");
+    s = launch_fwd_x3(grid, geo, mlp, ws, st);  // colours only (no masks: rec_mask is NULL)
   } else if (ws.rec_mask && fwd_x3_supported(geo, mlp)) {
     // a backward follows: colours and ReLU masks only, on the tensor cores, then the uncertain
     // samples again in FP32
@@ -1598,6 +1599,10 @@ cicero_status run_render(const cicero_grid* grid, const MlpPtrs& mlp, const Rend
     if (s == CICERO_OK)
       s = f16 ? launch_fwd_fix<__half>(geo, mlp, ws, grid->features, st)
               : launch_fwd_fix<float>(geo, mlp, ws, grid->features, st);
+  } else if ((s = encode_brick_map(grid, geo, box, &map)) != CICERO_OK) {
+    return s;
+  } else if (plan.precision == CICERO_MLP_BF16) {
+    s = launch_gather_mlp_bf16(grid, geo, plan.mlp_groups, mlp, ws, map, box, st);
   } else {
     s = f16 ? launch_f32<__half>(geo, plan.S, mlp, ws, map, box, st)
             : launch_f32<float>(geo, plan.S, mlp, ws, map, box, st);

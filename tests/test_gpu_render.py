@@ -70,6 +70,35 @@ def test_fp16_grid_occupancy_march_fp32(cc, orc, occ_scene):
     assert (ref["acc"] > 0.5).mean() > 0.05  # the view hits the occupied cells
 
 
+@pytest.mark.parametrize("brick", [4, 8, 16])
+def test_fp32_split_small_scene(cc, orc, small, brick):
+    """The FP32-class tensor-core MLP (split-BF16 products) at the FP32 tolerance."""
+    g, m = small
+    cam = scenes.orbit_camera(64, 64, az_deg=60.0, sampling=scenes.sampling_uniform(64))
+    ref = orc.render(g, m, cam.sampling, cam=cam)
+    out = gpu_render(cc, g, m, cam, cam.sampling, cc.MLP_FP32_SPLIT, brick)
+    err, _ = check_render(out, ref, TOL32)
+    print(f"split-BF16 small scene, brick {brick}: max|drgb| {err:.3g}")
+
+
+def test_fp32_split_fp16_grid_occupancy(cc, orc, occ_scene):
+    g, m = occ_scene
+    cam = scenes.orbit_camera(48, 48, az_deg=120.0, sampling=scenes.sampling_march(96, 160))
+    ref = orc.render(g, m, cam.sampling, cam=cam)
+    out = gpu_render(cc, g, m, cam, cam.sampling, cc.MLP_FP32_SPLIT, 8)
+    check_render(out, ref, TOL32)
+
+
+def test_fp32_split_channel_limit(cc):
+    """More than 16 feature channels: the split-BF16 MLP refuses (CICERO_ERR_UNSUPPORTED)."""
+    g = scenes.make_grid(16, 20, 2, seed=5)
+    m = scenes.make_mlp(20, seed=6)
+    cam = scenes.orbit_camera(8, 8, sampling=scenes.sampling_uniform(16))
+    with pytest.raises(cc.CiceroError) as ei:
+        gpu_render(cc, g, m, cam, cam.sampling, cc.MLP_FP32_SPLIT, 8)
+    assert ei.value.status == 2
+
+
 def test_bf16_small_scene(cc, orc, small):
     g, m = small
     cam = scenes.orbit_camera(64, 64, sampling=scenes.sampling_uniform(64))
@@ -227,7 +256,7 @@ def large():
     return scenes.scene_large(), scenes.make_mlp(12)
 
 
-@pytest.mark.parametrize("precision,brick", [(0, 8), (1, 4), (1, 8)])  # the benchmark's bricks: FP32 8, BF16 4
+@pytest.mark.parametrize("precision,brick", [(0, 8), (1, 4), (1, 8), (2, 8)])  # the benchmark's bricks: FP32 8, BF16 4
 def test_large_frame_sampled(cc, orc, large, precision, brick):
     g, m = large
     cam = scenes.orbit_camera(800, 800, sampling=scenes.sampling_march(256, 256))
@@ -235,7 +264,7 @@ def test_large_frame_sampled(cc, orc, large, precision, brick):
     pix = (scenes.splitmix64(4242, 400) % np.uint64(800 * 800)).astype(np.int32)
     ref = orc.render(g, m, cam.sampling, cam=cam, pix=pix)
     sub = {k: v[pix] for k, v in out.items()}
-    tol = TOL32 if precision == 0 else TOL16
-    err, p = check_render(sub, ref, tol, psnr_min=None if precision == 0 else PSNR16)
+    tol = TOL16 if precision == 1 else TOL32
+    err, p = check_render(sub, ref, tol, psnr_min=PSNR16 if precision == 1 else None)
     assert (ref["acc"] > 0.5).mean() > 0.05
     print(f"800x800 precision {precision} brick {brick}: max|drgb| {err:.3g} PSNR {p}")
