@@ -12,7 +12,7 @@
 //                      the sigmoid's input, w_k g c_k (1 - c_k)) and dL/draw_k
 //   B2 k_bwd_brick_tc  grid gradients: per brick (Ray Index Table order), 128 samples at a time,
 //                      the MLP backward down to dL/dfeatures on the tensor cores, with the ReLU
-//                      masks the FP32 forward recorded (nothing of the forward is recomputed), then
+//                      masks the recompute recorded (no forward layer is evaluated again), then
 //                      the trilinear adjoint added straight into d_features and d_density with
 //                      global atomics, 16-byte vector atomics where the channels allow.
 //   B2 k_bwd_brick     with d_mlp (the weight gradients need h1 and x): the same per brick, 64
@@ -510,15 +510,17 @@ __global__ void __launch_bounds__(256, 1) k_bwd_brick(GridGeo g, RaySrc src, Mlp
 }
 
 // ---------------------------------------------------------------------------------------------
-// B2 on the tensor cores (grid gradients).  Per tile of <= 128 samples of one brick, one thread per
-// sample:
+// B2 on the tensor cores (grid gradients).  Per tile of <= 128 samples of one brick, two threads
+// per sample (each a half of the hidden units):
 //   dh2 = (dz3 W3) masked by relu'(z2)           CUDA cores (K = 3)
 //   dh1 = (dh2 W2) masked by relu'(z1)           tcgen05 kind::f16, M = 128, N = 128, K = 128
 //   dL/dfeatures = dh1 W1[:, :C]                 tcgen05, N = 16 (channels padded), K = 128
-// FP32 accuracy from BF16 operands: every operand x is split into hi = bf16(x) and lo = bf16(x - hi)
-// and each product is hi hi' + hi lo' + lo hi' (the "bf16x3" scheme of Henry, Tang and Heinecke,
-// ARITH 2019: ~16 significant bits per product, the lo lo' term below FP32 rounding of the result),
-// accumulated in FP32 in tensor memory.  The ReLU masks are the FP32 forward's (rec_mask).
+// Near-FP32 accuracy from BF16 operands: every operand x is split into hi = bf16(x) and
+// lo = bf16(x - hi) and each product is hi hi' + hi lo' + lo hi' (the bf16x3 scheme of Henry, Tang
+// and Heinecke, ARITH 2019: the dropped lo lo' term and the residuals of the split are each ~2^-18
+// of the product, so a product keeps ~16 significant bits), accumulated in FP32 in tensor memory.
+// The ReLU masks are the recompute's (rec_mask): every decision the split-BF16 recompute could not
+// certify was taken again by the FP32 MLP.
 
 namespace bt {
 constexpr int kThreads = 256;  // two threads per sample of a 128-sample tile
@@ -553,7 +555,7 @@ __device__ __forceinline__ void store_chunk_split(char* hi_base, char* lo_base, 
 }
 
 // ReLU mask of the half h of the hidden units (h = 0: units 0..63, 1: 64..127), in the layout the
-// FP32 forward writes (unit n < 64 is bit n % 4 of byte n / 4, unit 64 + n bit 4 + n % 4): the
+// recompute writes (unit n < 64 is bit n % 4 of byte n / 4, unit 64 + n bit 4 + n % 4): the
 // words shifted so that unit 64 h + i is bit (i / 4 % 4) * 8 + i % 4 of word i / 16.
 struct HalfMask {
   uint32_t w[4];
