@@ -102,6 +102,31 @@ def test_backward_channel_layouts(cc, orc, C, feat_offset):
     assert rel_inf(df, wf) <= 1e-3, rel_inf(df, wf)
 
 
+@pytest.mark.parametrize("with_mlp", [False, True])
+def test_backward_config4_grid(cc, orc, with_mlp):
+    """The differentiation workload's configuration (160^3 x 12 FP32 grid, 256 slots in [0.5, 2.5],
+    t_stop 1e-3, bricks of 8, the MSE loss against seeded targets) on every 16th of its 8192 rays:
+    grid (and MLP weight) gradients against the oracle.  Gradients are sums over rays, so the rays
+    are subset rather than the outputs sampled."""
+    g = scenes.scene_backward()
+    m = scenes.make_mlp(12)
+    o, d = scenes.random_rays(8192)
+    sel = np.arange(0, 8192, 16)
+    o, d = o[sel], d[sel]
+    sp = scenes.Sampling(near=0.5, far=2.5, n_samples=256, t_stop=1e-3)
+    out = orc.render(g, m, sp, rays=(o, d))
+    tgt = scenes.random_targets(8192)[sel].astype(np.float64)
+    grad = 2.0 * (out["rgb"] - tgt) / (8192 * 3)
+    grad[out["amb"]] = 0.0
+    wd, wf, wm = orc.backward(g, m, sp, grad, rays=(o, d), with_mlp=with_mlp)
+    res = gpu_grads(cc, g, m, o, d, sp, grad, with_mlp=with_mlp)
+    assert rel_inf(res[0], wd) <= 1e-3, rel_inf(res[0], wd)
+    assert rel_inf(res[1], wf) <= 1e-3, rel_inf(res[1], wf)
+    if with_mlp:
+        for name, a, b in zip(("w1", "b1", "w2", "b2", "w3", "b3"), mlp_parts(m, res[2]), mlp_parts(m, wm)):
+            assert rel_inf(a, b) <= 1e-3, (name, rel_inf(a, b))
+
+
 def test_autograd_function_matches_backward(cc, orc):
     import torch
     from paper_2404_11852_gb300.autograd import render_rays
