@@ -510,8 +510,10 @@ __global__ void __launch_bounds__(256, 1) k_bwd_brick(GridGeo g, RaySrc src, Mlp
 }
 
 // ---------------------------------------------------------------------------------------------
-// B2 on the tensor cores (grid gradients).  Per tile of <= 128 samples of one brick, two threads
-// per sample (each a half of the hidden units):
+// B2 on the tensor cores (grid gradients).  Two independent groups of 128 threads per CTA, each
+// with its own tiles (alternate tiles of the CTA's range), operand buffers, TMEM columns and
+// mbarrier, so that one group's MMA waits and loads overlap the other's CUDA-core work.  Per tile
+// of <= 128 samples of one brick, one thread per sample:
 //   dh2 = (dz3 W3) masked by relu'(z2)           CUDA cores (K = 3)
 //   dh1 = (dh2 W2) masked by relu'(z1)           tcgen05 kind::f16, M = 128, N = 128, K = 128
 //   dL/dfeatures = dh1 W1[:, :C]                 tcgen05, N = 16 (channels padded), K = 128
@@ -523,22 +525,40 @@ __global__ void __launch_bounds__(256, 1) k_bwd_brick(GridGeo g, RaySrc src, Mlp
 // certify was taken again by the FP32 MLP.
 
 namespace bt {
-constexpr int kThreads = 256;  // two threads per sample of a 128-sample tile
-constexpr int kN1 = 16;        // channels of dL/dfeatures, padded to the smallest MMA width
+constexpr int kGroups = 2;
+constexpr int kThreads = kGroups * kTile;  // one thread per sample of each group's 128-sample tile
+constexpr int kN1 = 16;                    // channels of dL/dfeatures, padded to the smallest MMA width
 struct Smem {
   static constexpr int w2t_hi = 0;                                  // [128][128] bf16: row i, K = o: W2[o][i]
   static constexpr int w2t_lo = w2t_hi + kHidden * kHidden * 2;
   static constexpr int w1t_hi = w2t_lo + kHidden * kHidden * 2;     // [16][128] bf16: row c, K = i: W1[i][c]
   static constexpr int w1t_lo = w1t_hi + kN1 * kHidden * 2;
-  static constexpr int a_hi = w1t_lo + kN1 * kHidden * 2;           // [128][128] bf16: dh2, then dh1
-  static constexpr int a_lo = a_hi + kTile * kHidden * 2;
-  static constexpr int w3 = a_lo + kTile * kHidden * 2;             // [3][128] f32
-  static constexpr int bars = w3 + 3 * kHidden * 4;                 // mbarrier; TMEM address at +8
+  static constexpr int a = w1t_lo + kN1 * kHidden * 2;              // per group: [128][128] bf16 hi, then lo:
+  static constexpr int a_group = 2 * kTile * kHidden * 2;           // dh2, then dh1
+  static constexpr int w3 = a + kGroups * a_group;                  // [3][128] f32
+  static constexpr int bars = w3 + 3 * kHidden * 4;                 // one mbarrier per group; TMEM address at +16
   static constexpr int bytes = bars + 128;
-  static_assert(a_hi % 16 == 0 && w1t_hi % 16 == 0 && bars % 16 == 0, "operand alignment");
+  static_assert(a % 16 == 0 && w1t_hi % 16 == 0 && bars % 16 == 0, "operand alignment");
 };
-constexpr uint32_t kTmemCols = 128;
+constexpr uint32_t kTmemCols = kGroups * 128;  // 128 columns per group
 }  // namespace bt
+
+// Barriers of one group of 128 threads (named barriers 1 and 2; 0 is __syncthreads)
+__device__ __forceinline__ void group_sync(int grp) {
+  asm volatile("bar.sync %0, %1;" ::"r"(1 + grp), "r"(kTile) : "memory");
+}
+__device__ __forceinline__ bool group_sync_and(int grp, bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 p, %1, 0;\n\t"
+      "bar.red.and.pred q, %2, %3, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"((uint32_t)v), "r"(1 + grp), "r"(kTile)
+      : "memory");
+  return r != 0;
+}
 
 // 8 consecutive K values of one row, split into the hi and lo operands (hi exactly representable in
 // BF16, so its packing rounds nothing)
@@ -592,12 +612,12 @@ __global__ void __launch_bounds__(bt::kThreads, 1) k_bwd_brick_tc(GridGeo g, Mlp
   extern __shared__ __align__(1024) char sm[];
   const int C = g.C, B = g.brick;
   const bool vec = (C & 3) == 0 && (reinterpret_cast<uintptr_t>(d_feat) & 15u) == 0;
-  const int m = threadIdx.x & (kTile - 1), h = threadIdx.x / kTile;
-  char* a_hi = sm + bt::Smem::a_hi;
-  char* a_lo = sm + bt::Smem::a_lo;
+  const int m = threadIdx.x & (kTile - 1), grp = threadIdx.x / kTile;
+  char* a_hi = sm + bt::Smem::a + grp * bt::Smem::a_group;
+  char* a_lo = a_hi + kTile * kHidden * 2;
   float* w3s = (float*)(sm + bt::Smem::w3);
-  uint64_t* bar = (uint64_t*)(sm + bt::Smem::bars);
-  uint32_t* tslot = (uint32_t*)(sm + bt::Smem::bars + 8);
+  uint64_t* bar = (uint64_t*)(sm + bt::Smem::bars) + grp;
+  uint32_t* tslot = (uint32_t*)(sm + bt::Smem::bars + 16);
   // the weights, transposed into the B operands and split
   for (int i = threadIdx.x; i < kHidden * (kHidden / 8); i += bt::kThreads) {
     const int n = i / (kHidden / 8), k0 = (i % (kHidden / 8)) * 8;
@@ -615,7 +635,7 @@ __global__ void __launch_bounds__(bt::kThreads, 1) k_bwd_brick_tc(GridGeo g, Mlp
   }
   for (int i = threadIdx.x; i < 3 * kHidden; i += bt::kThreads) w3s[i] = mlp.w3[i];
   if (threadIdx.x == 0) {
-    mbar_init(bar, 1);
+    for (int j = 0; j < bt::kGroups; j++) mbar_init((uint64_t*)(sm + bt::Smem::bars) + j, 1);
     fence_mbar_init();
   }
   fence_proxy_async();
@@ -628,7 +648,8 @@ __global__ void __launch_bounds__(bt::kThreads, 1) k_bwd_brick_tc(GridGeo g, Mlp
   fence_before();
   __syncthreads();
   fence_after();
-  const uint32_t tmem = *tslot;
+  const uint32_t tmem_base = *tslot;
+  const uint32_t tmem = tmem_base + 128u * (uint32_t)grp;                             // this group's columns
   const uint32_t taddr = tmem + ((uint32_t)(((threadIdx.x >> 5) & 3) * 32) << 16);  // this warp's lanes
   const uint64_t ah = smem_desc(smem_u32(a_hi), 128u, kHidden * 16), al = smem_desc(smem_u32(a_lo), 128u, kHidden * 16);
   const uint64_t b2h = smem_desc(smem_u32(sm + bt::Smem::w2t_hi), 128u, kHidden * 16);
@@ -662,17 +683,17 @@ __global__ void __launch_bounds__(bt::kThreads, 1) k_bwd_brick_tc(GridGeo g, Mlp
       n_m2 = w.rec_mask[2 * (size_t)n_rid + 1];
     }
   };
-  if (t_begin < t_end) {
-    level_a(t_begin);
+  if (t_begin + grp < t_end) {
+    level_a(t_begin + grp);
     level_b();
   }
-  for (uint32_t ti = t_begin; ti < t_end && alive; ti++) {
+  for (uint32_t ti = t_begin + grp; ti < t_end && alive; ti += bt::kGroups) {
     const uint4 td = n_td;
     const float4 pw = n_pw, dzw = n_dz;
     const uint4 m1 = n_m1, m2 = n_m2;
     const float draw = dzw.w;
-    const bool more = ti + 1 < t_end;
-    if (more) level_a(ti + 1);
+    const bool more = ti + bt::kGroups < t_end;
+    if (more) level_a(ti + bt::kGroups);
     const int mcnt = (int)(td.y & 0xFFu);
     const int bx = (int)(td.w & 0xFFFFu), by = (int)(td.w >> 16), bz = (int)((td.y >> 8) & 0x1FFFu);
     // this thread's sample: its voxel, weights of the colour gradient
@@ -685,15 +706,16 @@ __global__ void __launch_bounds__(bt::kThreads, 1) k_bwd_brick_tc(GridGeo g, Mlp
       const int l[3] = {i0[0] - bx * B, i0[1] - by * B, i0[2] - bz * B};
       ok = in && l[0] >= 0 && l[0] < B && l[1] >= 0 && l[1] < B && l[2] >= 0 && l[2] < B;
       if (!ok) {
-        if (h == 0) set_err(&w.hdr[0], kErrInternal);
+        set_err(&w.hdr[0], kErrInternal);
       } else {
         dz0 = dzw.x;
         dz1 = dzw.y;
         dz2 = dzw.z;
       }
     }
-    // dh2 = (dz3 W3) masked by relu'(z2): this thread's half of row m of A
-    {
+    // dh2 = (dz3 W3) masked by relu'(z2): row m of A, one half of the hidden units at a time
+#pragma unroll 1
+    for (int h = 0; h < 2; h++) {
       const HalfMask mk(m2, h);
       const float4* w30 = reinterpret_cast<const float4*>(w3s + 64 * h);
       const float4* w31 = reinterpret_cast<const float4*>(w3s + kHidden + 64 * h);
@@ -713,20 +735,22 @@ __global__ void __launch_bounds__(bt::kThreads, 1) k_bwd_brick_tc(GridGeo g, Mlp
       }
     }
     fence_proxy_async();
-    __syncthreads();
-    // dh1 = dh2 W2 into columns [0, 128)
-    if (threadIdx.x == 0) {
+    fence_before();
+    group_sync(grp);
+    // dh1 = dh2 W2 into the group's columns [0, 128)
+    if (m == 0) {
       fence_after();
       mma_split(tmem, ah, al, b2h, b2l, idesc_bf16(kHidden));
       mma_commit(bar);
     }
-    alive = __syncthreads_and(mbar_wait(bar, phase, &w.hdr[0]));
+    alive = group_sync_and(grp, mbar_wait(bar, phase, &w.hdr[0]));
     fence_after();
     if (!alive) break;
     phase ^= 1u;
     if (more) level_b();
-    // dh1 masked by relu'(z1) -> this thread's half of row m of A (dh2 is no longer read)
-    {
+    // dh1 masked by relu'(z1) -> row m of A (dh2 is no longer read), one half at a time
+#pragma unroll 1
+    for (int h = 0; h < 2; h++) {
       const HalfMask mk(m1, h);
       float v[64];
       tmem_ld<64>(taddr + 64 * h, v);
@@ -740,37 +764,36 @@ __global__ void __launch_bounds__(bt::kThreads, 1) k_bwd_brick_tc(GridGeo g, Mlp
     }
     fence_proxy_async();
     fence_before();
-    __syncthreads();
-    // dL/dfeatures = dh1 W1[:, :C] into columns [0, 16)
-    if (threadIdx.x == 0) {
+    group_sync(grp);
+    // dL/dfeatures = dh1 W1[:, :C] into the group's columns [0, 16)
+    if (m == 0) {
       fence_after();
       mma_split(tmem, ah, al, b1h, b1l, idesc_bf16(bt::kN1));
       mma_commit(bar);
     }
-    alive = __syncthreads_and(mbar_wait(bar, phase, &w.hdr[0]));
+    alive = group_sync_and(grp, mbar_wait(bar, phase, &w.hdr[0]));
     fence_after();
     if (!alive) break;
     phase ^= 1u;
     float dft[16];
     tmem_ld<16>(taddr, dft);
     fence_before();
-    // trilinear adjoint: corners 4 h .. 4 h + 3
+    // trilinear adjoint, the eight corners (the next tile's first group barrier also orders these
+    // TMEM reads before the next MMA into the same columns)
     if (ok) {
 #pragma unroll
-      for (int u = 0; u < 4; u++) {
-        const int q = 4 * h + u;
+      for (int q = 0; q < 8; q++)
         scatter_corner<bt::kN1>(C, vec, corner_vertex(g, i0[0], i0[1], i0[2], q), corner_weight(f[0], f[1], f[2], q),
-                       [&](int c) { return dft[c]; }, draw, d_dens, d_feat);
-      }
+                                [&](int c) { return dft[c]; }, draw, d_dens, d_feat);
     }
-    __syncthreads();
   }
   if (!alive) mbar_wait(bar, phase, &w.hdr[0]);  // MMAs may still be running (bounded)
   fence_before();
   __syncthreads();
   if (threadIdx.x < 32) {
     fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(bt::kTmemCols) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(bt::kTmemCols)
+                 : "memory");
   }
 }
 
