@@ -804,10 +804,10 @@ __global__ void __launch_bounds__(bt::kThreads, 1) k_bwd_brick_tc(GridGeo g, Mlp
 // tcgen05 MMAs on split-BF16 operands (hi + lo, three products per K step as in k_bwd_brick_tc,
 // FP32 accumulation in TMEM), the biases, layer 3 and the sigmoid in FP32 on the CUDA cores.  It
 // writes what the backward reads: (c, w) into rec_c and the ReLU masks of layers 1 and 2 into
-// rec_mask.  Two threads per sample: thread (m, h) interpolates the four corners at z offset h,
-// converts half of row m of x (K values 24 h .. 24 h + 23) and takes hidden units 64 h .. 64 h + 63
-// in the epilogues; the h = 1 threads hand their partial sums to the h = 0 threads through
-// shared memory.
+// rec_mask.  Two independent groups of 128 threads per CTA (alternate tiles, each its own operand
+// region, TMEM columns and mbarrier), one thread per sample: the thread interpolates its sample's
+// eight corners, stages its FP32 input row in shared memory (the row then read back in chunks), and
+// takes all 128 hidden units in the epilogues, 64 at a time.
 //
 // A ReLU decision taken on a split-BF16 pre-activation can differ from the FP32 one where the
 // pre-activation is within the products' error of zero, and one flipped mask moves that sample's
@@ -824,31 +824,37 @@ __global__ void __launch_bounds__(bt::kThreads, 1) k_bwd_brick_tc(GridGeo g, Mlp
 // parity scenes agree with the FP64 oracle to ~5e-6 in all three cases, and to 2e-3 without the
 // fix-up).
 namespace xt {
-constexpr int kThreads = 256;
-constexpr int kK1 = 48;    // layer-1 K: in_dim padded to a multiple of 16
-constexpr int kMaxC = 16;  // feature channels
-constexpr int kXS = kK1 + 1;  // FP32 row stride of the staged inputs (odd: rows in distinct banks)
+constexpr int kGroups = 2;
+constexpr int kThreads = kGroups * kTile;  // one thread per sample of each group's 128-sample tile
+constexpr int kK1 = 48;                    // layer-1 K: in_dim padded to a multiple of 16
+constexpr int kMaxC = 16;                  // feature channels
+constexpr int kXS = kK1 + 1;               // FP32 row stride of the staged inputs (odd: rows in distinct banks)
 constexpr float kEps = 7.62939453125e-06f;  // 2^-17
+// A group's operand region (64 KB).  While x is built: the FP32 rows at [0, 128 kXS 4) and the
+// layer-1 operand x (hi, lo; K = 48) at [40 KB, 64 KB).  From layer 1's epilogue on: h1 hi at
+// [0, 32 KB), lo at [32 KB, 64 KB), written once layer 1's MMA has read x and every row was read.
+struct Region {
+  static constexpr int xs = 0;
+  static constexpr int x_hi = 40 * 1024;
+  static constexpr int x_lo = x_hi + kTile * kK1 * 2;
+  static constexpr int h_hi = 0;
+  static constexpr int h_lo = kTile * kHidden * 2;
+  static constexpr int bytes = 2 * kTile * kHidden * 2;
+  static_assert(xs + kTile * kXS * 4 <= x_hi && x_lo + kTile * kK1 * 2 == bytes, "region layout");
+};
 struct Smem {
   static constexpr int w1_hi = 0;                             // [128][48] bf16: row n, K = k: W1[n][k]
   static constexpr int w1_lo = w1_hi + kHidden * kK1 * 2;
   static constexpr int w2_hi = w1_lo + kHidden * kK1 * 2;     // [128][128] bf16: row n, K = k: W2[n][k]
   static constexpr int w2_lo = w2_hi + kHidden * kHidden * 2;
-  static constexpr int a_hi = w2_lo + kHidden * kHidden * 2;  // [128][48] x, then [128][128] h1
-  static constexpr int a_lo = a_hi + kTile * kHidden * 2;
-  static constexpr int prm = a_lo + kTile * kHidden * 2;      // b1 [128], b2 [128], w3 [3][128], b3 [4] f32
-  static constexpr int xs = prm + (5 * kHidden + 4) * 4;      // [128][kXS] f32: partial features, encoding
-  static constexpr int zpart = xs + kTile * kXS * 4;          // [128][4] f32: layer 3 over units 64..127
-  static constexpr int mpart = zpart + kTile * 4 * 4;         // [128][8] u32: ReLU bits of units 64..127
-  static constexpr int nrm = mpart + kTile * 8 * 4;           // ||W1_n|| [128], ||W2_n|| [128], ||W1||_F f32
-  static constexpr int nxp = nrm + (2 * kHidden + 4) * 4;     // [2][128] f32: ||x||^2 over each thread's K half
-  static constexpr int hp = nxp + 2 * kTile * 4;              // [2][128] f32: ||h1||^2 over each half
-  static constexpr int flg = hp + 2 * kTile * 4;              // [128] u32: uncertain decision among units 64..127
-  static constexpr int bars = flg + kTile * 4;                // mbarrier; TMEM address at +8
+  static constexpr int region = w2_lo + kHidden * kHidden * 2;  // kGroups operand regions
+  static constexpr int prm = region + kGroups * Region::bytes;  // b1 [128], b2 [128], w3 [3][128], b3 [4] f32
+  static constexpr int nrm = prm + (5 * kHidden + 4) * 4;     // ||W1_n|| [128], ||W2_n|| [128], ||W1||_F f32
+  static constexpr int bars = nrm + (2 * kHidden + 4) * 4;    // one mbarrier per group; TMEM address at +16
   static constexpr int bytes = bars + 128;
-  static_assert(a_hi % 16 == 0 && w2_hi % 16 == 0 && xs % 16 == 0 && bars % 16 == 0, "alignment");
+  static_assert(region % 16 == 0 && w2_hi % 16 == 0 && bars % 16 == 0, "alignment");
 };
-constexpr uint32_t kTmemCols = 128;
+constexpr uint32_t kTmemCols = kGroups * 128;  // 128 columns per group
 }  // namespace xt
 
 bool fwd_x3_supported(const GridGeo& g, const MlpPtrs& mlp) {
@@ -869,24 +875,20 @@ __global__ void __launch_bounds__(xt::kThreads, 1) k_fwd_x3(GridGeo g, MlpPtrs m
   using namespace tc;
   extern __shared__ __align__(1024) char sm[];
   const int C = g.C, B = g.brick;
-  const int m = threadIdx.x & (kTile - 1), h = threadIdx.x / kTile;
-  char* a_hi = sm + xt::Smem::a_hi;
-  char* a_lo = sm + xt::Smem::a_lo;
+  const int m = threadIdx.x & (kTile - 1), grp = threadIdx.x / kTile;
+  char* region = sm + xt::Smem::region + grp * xt::Region::bytes;
+  char* h_hi = region + xt::Region::h_hi;
+  char* h_lo = region + xt::Region::h_lo;
+  float* xs = (float*)(region + xt::Region::xs) + m * xt::kXS;  // this sample's FP32 row
   float* b1s = (float*)(sm + xt::Smem::prm);
   float* b2s = b1s + kHidden;
   float* w3s = b2s + kHidden;
   float* b3s = w3s + 3 * kHidden;
-  float* xs = (float*)(sm + xt::Smem::xs) + m * xt::kXS;  // this sample's row
   float* nw1 = (float*)(sm + xt::Smem::nrm);
   float* nw2 = nw1 + kHidden;
   float* fro1 = nw2 + kHidden;
-  float* nxp = (float*)(sm + xt::Smem::nxp);
-  float* hp = (float*)(sm + xt::Smem::hp);
-  uint32_t* flg = (uint32_t*)(sm + xt::Smem::flg);
-  float* zpart = (float*)(sm + xt::Smem::zpart) + 4 * m;
-  uint32_t* mpart = (uint32_t*)(sm + xt::Smem::mpart) + 8 * m;
-  uint64_t* bar = (uint64_t*)(sm + xt::Smem::bars);
-  uint32_t* tslot = (uint32_t*)(sm + xt::Smem::bars + 8);
+  uint64_t* bar = (uint64_t*)(sm + xt::Smem::bars) + grp;
+  uint32_t* tslot = (uint32_t*)(sm + xt::Smem::bars + 16);
   // the weights, split into the hi and lo B operands; the other parameters in FP32
   for (int i = threadIdx.x; i < kHidden * (xt::kK1 / 8); i += xt::kThreads) {
     const int n = i / (xt::kK1 / 8), k0 = (i % (xt::kK1 / 8)) * 8;
@@ -908,7 +910,7 @@ __global__ void __launch_bounds__(xt::kThreads, 1) k_fwd_x3(GridGeo g, MlpPtrs m
   }
   for (int i = threadIdx.x; i < 3 * kHidden; i += xt::kThreads) w3s[i] = mlp.w3[i];
   if (threadIdx.x < 4) b3s[threadIdx.x] = threadIdx.x < 3 ? mlp.b3[threadIdx.x] : 0.0f;
-  {  // row norms of W1 (threads < 128) and W2 (the others)
+  if constexpr (BWD) {  // row norms of W1 (threads < 128) and W2 (the others)
     const int n = threadIdx.x & (kHidden - 1);
     float s2 = 0.0f;
     if (threadIdx.x < kHidden)
@@ -918,7 +920,7 @@ __global__ void __launch_bounds__(xt::kThreads, 1) k_fwd_x3(GridGeo g, MlpPtrs m
     (threadIdx.x < kHidden ? nw1 : nw2)[n] = sqrtf(s2);
   }
   if (threadIdx.x == 0) {
-    mbar_init(bar, 1);
+    for (int j = 0; j < xt::kGroups; j++) mbar_init((uint64_t*)(sm + xt::Smem::bars) + j, 1);
     fence_mbar_init();
   }
   fence_proxy_async();
@@ -931,15 +933,18 @@ __global__ void __launch_bounds__(xt::kThreads, 1) k_fwd_x3(GridGeo g, MlpPtrs m
   fence_before();
   __syncthreads();
   fence_after();
-  if (threadIdx.x == 0) {  // read after the first tile's first barrier
+  if (BWD && threadIdx.x == 0) {  // read after the first tile's first group barrier
     float f2 = 0.0f;
     for (int n = 0; n < kHidden; n++) f2 = fmaf(nw1[n], nw1[n], f2);
     *fro1 = sqrtf(f2);
   }
-  const uint32_t tmem = *tslot;
+  __syncthreads();
+  const uint32_t tmem_base = *tslot;
+  const uint32_t tmem = tmem_base + 128u * (uint32_t)grp;                             // this group's columns
   const uint32_t taddr = tmem + ((uint32_t)(((threadIdx.x >> 5) & 3) * 32) << 16);  // this warp's lanes
-  const uint64_t ax_h = smem_desc(smem_u32(a_hi), 128u, xt::kK1 * 16), ax_l = smem_desc(smem_u32(a_lo), 128u, xt::kK1 * 16);
-  const uint64_t ah_h = smem_desc(smem_u32(a_hi), 128u, kHidden * 16), ah_l = smem_desc(smem_u32(a_lo), 128u, kHidden * 16);
+  const uint64_t ax_h = smem_desc(smem_u32(region + xt::Region::x_hi), 128u, xt::kK1 * 16);
+  const uint64_t ax_l = smem_desc(smem_u32(region + xt::Region::x_lo), 128u, xt::kK1 * 16);
+  const uint64_t ah_h = smem_desc(smem_u32(h_hi), 128u, kHidden * 16), ah_l = smem_desc(smem_u32(h_lo), 128u, kHidden * 16);
   const uint64_t b1h = smem_desc(smem_u32(sm + xt::Smem::w1_hi), 128u, xt::kK1 * 16);
   const uint64_t b1l = smem_desc(smem_u32(sm + xt::Smem::w1_lo), 128u, xt::kK1 * 16);
   const uint64_t b2h = smem_desc(smem_u32(sm + xt::Smem::w2_hi), 128u, kHidden * 16);
@@ -951,7 +956,7 @@ __global__ void __launch_bounds__(xt::kThreads, 1) k_fwd_x3(GridGeo g, MlpPtrs m
   const uint32_t n_tiles = w.hdr[1];
   const uint32_t per = (n_tiles + gridDim.x - 1) / gridDim.x;
   const uint32_t t_begin = blockIdx.x * per, t_end = min(n_tiles, t_begin + per);
-  // this thread's sorted record of the next tile, loaded when the current tile starts
+  // this thread's sorted record of the group's next tile, loaded when the current tile starts
   uint4 n_td = make_uint4(0u, 0u, 0u, 0u);
   float4 n_pw = make_float4(0.f, 0.f, 0.f, 0.f), n_qd = n_pw;
   auto prefetch = [&](uint32_t t) {
@@ -961,37 +966,32 @@ __global__ void __launch_bounds__(xt::kThreads, 1) k_fwd_x3(GridGeo g, MlpPtrs m
       n_qd = w.srt[n_td.x + m].qd;
     }
   };
-  if (t_begin < t_end) prefetch(t_begin);
-  for (uint32_t ti = t_begin; ti < t_end && alive; ti++) {
+  if (t_begin + grp < t_end) prefetch(t_begin + grp);
+  for (uint32_t ti = t_begin + grp; ti < t_end && alive; ti += xt::kGroups) {
     const uint4 td = n_td;
     const float4 pw = n_pw, qd = n_qd;
-    if (ti + 1 < t_end) prefetch(ti + 1);
+    if (ti + xt::kGroups < t_end) prefetch(ti + xt::kGroups);
     const uint32_t start = td.x;
     const int mcnt = (int)(td.y & 0xFFu);
     const int bx = (int)(td.w & 0xFFFFu), by = (int)(td.w >> 16), bz = (int)((td.y >> 8) & 0x1FFFu);
     const bool valid = m < mcnt;
     uint32_t rid = 0;
-    float wgt = 0.0f, d[3] = {0.0f, 0.0f, 0.0f}, fx[xt::kMaxC];
+    float wgt = 0.0f, fx[xt::kMaxC];
 #pragma unroll
     for (int c = 0; c < xt::kMaxC; c++) fx[c] = 0.0f;
     if (valid) {
       rid = __float_as_uint(qd.x);
       wgt = pw.w;
-      d[0] = qd.y;
-      d[1] = qd.z;
-      d[2] = qd.w;
       const float p[3] = {pw.x, pw.y, pw.z};
       int i0[3];
       float f[3];
       const bool in = index_sample(g, p, i0, f);
       const int l[3] = {i0[0] - bx * B, i0[1] - by * B, i0[2] - bz * B};
       if (!(in && l[0] >= 0 && l[0] < B && l[1] >= 0 && l[1] < B && l[2] >= 0 && l[2] < B)) {
-        if (h == 0) set_err(&w.hdr[0], kErrInternal);
+        set_err(&w.hdr[0], kErrInternal);
       } else {
-        // this thread's four corners (z offset h), weighted
 #pragma unroll
-        for (int u = 0; u < 4; u++) {
-          const int q = 4 * h + u;
+        for (int q = 0; q < 8; q++) {
           const float wq = corner_weight(f[0], f[1], f[2], q);
           const T* v = feat + corner_vertex(g, i0[0], i0[1], i0[2], q) * (size_t)C;
 #pragma unroll
@@ -1000,67 +1000,50 @@ __global__ void __launch_bounds__(xt::kThreads, 1) k_fwd_x3(GridGeo g, MlpPtrs m
         }
       }
     }
-    if (h == 1) {
-      // partial features and the direction encoding into the staged row
+    // this sample's FP32 row of x (features, direction encoding, zeros), staged, then split into
+    // the layer-1 operand 8 K values at a time
 #pragma unroll
-      for (int c = 0; c < xt::kMaxC; c++)
-        if (c < C) xs[c] = fx[c];
-      if (valid)
-        encode_dir(d, mlp.n_freq, xs + C);
-      else
-        for (int j = 0; j < ne; j++) xs[C + j] = 0.0f;
-      for (int k = C + ne; k < xt::kK1; k++) xs[k] = 0.0f;
+    for (int c = 0; c < xt::kMaxC; c++)
+      if (c < C) xs[c] = fx[c];
+    if (valid) {
+      const float d[3] = {qd.y, qd.z, qd.w};
+      encode_dir(d, mlp.n_freq, xs + C);
+    } else {
+      for (int j = 0; j < ne; j++) xs[C + j] = 0.0f;
     }
-    __syncthreads();
-    // row m of x in BF16 hi + lo: K values 24 h .. 24 h + 23 (every feature channel is below 24)
-    {
-      float x2 = 0.0f;
-      if (h == 0) {
+    for (int k = C + ne; k < xt::kK1; k++) xs[k] = 0.0f;
+    float x2 = 0.0f;
 #pragma unroll
-        for (int j = 0; j < 3; j++) {
-          float v[8];
+    for (int j = 0; j < xt::kK1 / 8; j++) {
+      float v[8];
 #pragma unroll
-          for (int t = 0; t < 8; t++) {
-            const int k = 8 * j + t;
-            v[t] = k < xt::kMaxC && k < C ? fx[k < xt::kMaxC ? k : 0] + xs[k] : xs[k];
-            x2 = fmaf(v[t], v[t], x2);
-          }
-          store_chunk_split(a_hi, a_lo, m, 8 * j, xt::kK1, v);
-        }
-      } else {
-#pragma unroll
-        for (int j = 3; j < 6; j++) {
-          float v[8];
-#pragma unroll
-          for (int t = 0; t < 8; t++) {
-            v[t] = xs[8 * j + t];
-            x2 = fmaf(v[t], v[t], x2);
-          }
-          store_chunk_split(a_hi, a_lo, m, 8 * j, xt::kK1, v);
-        }
+      for (int t = 0; t < 8; t++) {
+        v[t] = xs[8 * j + t];
+        x2 = fmaf(v[t], v[t], x2);
       }
-      nxp[h * kTile + m] = x2;
+      store_chunk_split(region + xt::Region::x_hi, region + xt::Region::x_lo, m, 8 * j, xt::kK1, v);
     }
     fence_proxy_async();
     fence_before();
-    __syncthreads();
-    // layer 1: W1 x into columns [0, 128)
-    if (threadIdx.x == 0) {
+    group_sync(grp);
+    // layer 1: W1 x into the group's columns [0, 128)
+    if (m == 0) {
       fence_after();
       mma_split<xt::kK1 / 16>(tmem, ax_h, ax_l, b1h, b1l, idesc_bf16(kHidden));
       mma_commit(bar);
     }
-    alive = __syncthreads_and(mbar_wait(bar, phase, &w.hdr[0]));
+    alive = group_sync_and(grp, mbar_wait(bar, phase, &w.hdr[0]));
     fence_after();
     if (!alive) break;
     phase ^= 1u;
     uint32_t mw1[4] = {0u, 0u, 0u, 0u}, mw2[4] = {0u, 0u, 0u, 0u};
-    const float nx = sqrtf(nxp[m] + nxp[kTile + m]);
+    const float tx = xt::kEps * sqrtf(x2);
     bool unsure = false;
-    {
-      float v[64], h2s = 0.0f;
+    float h2s = 0.0f;  // ||h1||^2
+#pragma unroll 1
+    for (int h = 0; h < 2; h++) {
+      float v[64];
       tmem_ld<64>(taddr + 64 * h, v);
-      const float tx = xt::kEps * nx;
 #pragma unroll
       for (int q = 0; q < 8; q++) {
         float x[8];
@@ -1075,28 +1058,28 @@ __global__ void __launch_bounds__(xt::kThreads, 1) k_fwd_x3(GridGeo g, MlpPtrs m
           x[t] = fmaxf(z, 0.0f);
           h2s = fmaf(x[t], x[t], h2s);
         }
-        store_chunk_split(a_hi, a_lo, m, 64 * h + 8 * q, kHidden, x);
+        store_chunk_split(h_hi, h_lo, m, 64 * h + 8 * q, kHidden, x);
       }
-      hp[h * kTile + m] = h2s;
     }
     fence_proxy_async();
     fence_before();
-    __syncthreads();
-    // layer 2: W2 h1 into columns [0, 128)
-    if (threadIdx.x == 0) {
+    group_sync(grp);
+    // layer 2: W2 h1 into the group's columns [0, 128)
+    if (m == 0) {
       fence_after();
       mma_split(tmem, ah_h, ah_l, b2h, b2l, idesc_bf16(kHidden));
       mma_commit(bar);
     }
-    alive = __syncthreads_and(mbar_wait(bar, phase, &w.hdr[0]));
+    alive = group_sync_and(grp, mbar_wait(bar, phase, &w.hdr[0]));
     fence_after();
     if (!alive) break;
     phase ^= 1u;
     float z0 = 0.0f, z1 = 0.0f, z2 = 0.0f;
-    {
+    const float th = BWD ? xt::kEps * (sqrtf(h2s) + sqrtf(x2) * *fro1) : 0.0f;
+#pragma unroll 1
+    for (int h = 0; h < 2; h++) {
       float v[64];
       tmem_ld<64>(taddr + 64 * h, v);
-      const float th = xt::kEps * (sqrtf(hp[m] + hp[kTile + m]) + nx * *fro1);
 #pragma unroll
       for (int n = 0; n < 64; n++) {
         const int u = 64 * h + n;
@@ -1105,43 +1088,26 @@ __global__ void __launch_bounds__(xt::kThreads, 1) k_fwd_x3(GridGeo g, MlpPtrs m
           relu_bit(mw2, n, h, z > 0.0f);
           unsure |= fabsf(z) <= th * nw2[u];
         }
-        const float h2 = fmaxf(z, 0.0f);
-        z0 = fmaf(w3s[u], h2, z0);
-        z1 = fmaf(w3s[kHidden + u], h2, z1);
-        z2 = fmaf(w3s[2 * kHidden + u], h2, z2);
+        const float a2 = fmaxf(z, 0.0f);
+        z0 = fmaf(w3s[u], a2, z0);
+        z1 = fmaf(w3s[kHidden + u], a2, z1);
+        z2 = fmaf(w3s[2 * kHidden + u], a2, z2);
       }
     }
     fence_before();
-    if (h == 1) {
-      zpart[0] = z0;
-      zpart[1] = z1;
-      zpart[2] = z2;
-#pragma unroll
-      for (int j = 0; j < 4; j++) {
-        mpart[j] = mw1[j];
-        mpart[4 + j] = mw2[j];
-      }
-      flg[m] = unsure ? 1u : 0u;
-    }
-    __syncthreads();
-    if (BWD && h == 0) {  // warps 0-3: list the uncertain samples (one atomic per warp)
-      const bool fix = valid && (unsure || flg[m] != 0u);
+    if constexpr (BWD) {  // list the uncertain samples (one atomic per warp)
+      const bool fix = valid && unsure;
       const uint32_t bal = __ballot_sync(0xffffffffu, fix);
       uint32_t base = 0;
       if ((threadIdx.x & 31) == 0 && bal) base = atomicAdd(&w.hdr[4], (uint32_t)__popc(bal));
       base = __shfl_sync(0xffffffffu, base, 0);
       if (fix) w.rec_key[base + __popc(bal & ((1u << (threadIdx.x & 31)) - 1u))] = start + m;
     }
-    if (h == 0 && valid) {
-      const float c0 = sigmoid_f(z0 + zpart[0] + b3s[0]);
-      const float c1 = sigmoid_f(z1 + zpart[1] + b3s[1]);
-      const float c2 = sigmoid_f(z2 + zpart[2] + b3s[2]);
-      w.rec_c[rid] = make_float4(c0, c1, c2, wgt);
+    if (valid) {
+      w.rec_c[rid] = make_float4(sigmoid_f(z0 + b3s[0]), sigmoid_f(z1 + b3s[1]), sigmoid_f(z2 + b3s[2]), wgt);
       if constexpr (BWD) {
-        w.rec_mask[2 * (size_t)rid] =
-            make_uint4(mw1[0] | mpart[0], mw1[1] | mpart[1], mw1[2] | mpart[2], mw1[3] | mpart[3]);
-        w.rec_mask[2 * (size_t)rid + 1] =
-            make_uint4(mw2[0] | mpart[4], mw2[1] | mpart[5], mw2[2] | mpart[6], mw2[3] | mpart[7]);
+        w.rec_mask[2 * (size_t)rid] = make_uint4(mw1[0], mw1[1], mw1[2], mw1[3]);
+        w.rec_mask[2 * (size_t)rid + 1] = make_uint4(mw2[0], mw2[1], mw2[2], mw2[3]);
       }
     }
   }
@@ -1150,7 +1116,8 @@ __global__ void __launch_bounds__(xt::kThreads, 1) k_fwd_x3(GridGeo g, MlpPtrs m
   __syncthreads();
   if (threadIdx.x < 32) {
     fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(xt::kTmemCols) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(xt::kTmemCols)
+                 : "memory");
   }
 }
 
