@@ -603,9 +603,10 @@ __device__ __forceinline__ void mma_split(uint32_t d, uint64_t ah, uint64_t al, 
   }
 }
 
-// Two threads per sample (m = tid mod 128, half h = tid / 128): each computes half of dh2's and of
-// dh1's 128 hidden units (TMEM columns [64 h, 64 h + 64) of the sample's lane) and scatters half of
-// the trilinear corners, so a tile's CUDA-core work is spread over 8 warps.
+// Group grp = tid / 128 takes tiles t_begin + grp, t_begin + grp + 2, ...; thread m = tid mod 128
+// takes sample m of each (TMEM lane m of the group's columns [128 grp, 128 grp + 128)), its 128
+// hidden units 64 at a time and its eight trilinear corners.  The group's barriers are named
+// barriers of 128 threads, so the two groups never wait for each other until the kernel ends.
 __global__ void __launch_bounds__(bt::kThreads, 1) k_bwd_brick_tc(GridGeo g, MlpPtrs mlp, RenderWs w, float* d_dens,
                                                                   float* d_feat) {
   using namespace tc;
