@@ -1045,19 +1045,34 @@ __global__ void __launch_bounds__(xt::kThreads, 1) k_fwd_x3(GridGeo g, MlpPtrs m
     for (int h = 0; h < 2; h++) {
       float v[64];
       tmem_ld<64>(taddr + 64 * h, v);
+      const float4* b4 = reinterpret_cast<const float4*>(b1s + 64 * h);  // per-unit constants, 4 at a time
+      const float4* n4 = reinterpret_cast<const float4*>(nw1 + 64 * h);
 #pragma unroll
       for (int q = 0; q < 8; q++) {
         float x[8];
 #pragma unroll
-        for (int t = 0; t < 8; t++) {
-          const int n = 8 * q + t;
-          const float z = v[n] + b1s[64 * h + n];
+        for (int t4 = 0; t4 < 2; t4++) {
+          const float4 bq = b4[2 * q + t4];
+          const float bv[4] = {bq.x, bq.y, bq.z, bq.w};
+          float nv[4] = {0.f, 0.f, 0.f, 0.f};
           if constexpr (BWD) {
-            relu_bit(mw1, n, h, z > 0.0f);
-            unsure |= fabsf(z) <= tx * nw1[64 * h + n];
+            const float4 nq = n4[2 * q + t4];
+            nv[0] = nq.x;
+            nv[1] = nq.y;
+            nv[2] = nq.z;
+            nv[3] = nq.w;
           }
-          x[t] = fmaxf(z, 0.0f);
-          h2s = fmaf(x[t], x[t], h2s);
+#pragma unroll
+          for (int j = 0; j < 4; j++) {
+            const int t = 4 * t4 + j, n = 8 * q + t;
+            const float z = v[n] + bv[j];
+            if constexpr (BWD) {
+              relu_bit(mw1, n, h, z > 0.0f);
+              unsure |= fabsf(z) <= tx * nv[j];
+            }
+            x[t] = fmaxf(z, 0.0f);
+            h2s = fmaf(x[t], x[t], h2s);
+          }
         }
         store_chunk_split(h_hi, h_lo, m, 64 * h + 8 * q, kHidden, x);
       }
@@ -1081,18 +1096,37 @@ __global__ void __launch_bounds__(xt::kThreads, 1) k_fwd_x3(GridGeo g, MlpPtrs m
     for (int h = 0; h < 2; h++) {
       float v[64];
       tmem_ld<64>(taddr + 64 * h, v);
+      const float4* b4 = reinterpret_cast<const float4*>(b2s + 64 * h);  // per-unit constants, 4 at a time
+      const float4* n4 = reinterpret_cast<const float4*>(nw2 + 64 * h);
+      const float4* w0 = reinterpret_cast<const float4*>(w3s + 64 * h);
+      const float4* w1 = reinterpret_cast<const float4*>(w3s + kHidden + 64 * h);
+      const float4* w2 = reinterpret_cast<const float4*>(w3s + 2 * kHidden + 64 * h);
 #pragma unroll
-      for (int n = 0; n < 64; n++) {
-        const int u = 64 * h + n;
-        const float z = v[n] + b2s[u];
+      for (int n4i = 0; n4i < 16; n4i++) {
+        const float4 bq = b4[n4i], c0 = w0[n4i], c1 = w1[n4i], c2 = w2[n4i];
+        const float bv[4] = {bq.x, bq.y, bq.z, bq.w};
+        const float u0[4] = {c0.x, c0.y, c0.z, c0.w}, u1[4] = {c1.x, c1.y, c1.z, c1.w}, u2[4] = {c2.x, c2.y, c2.z, c2.w};
+        float nv[4] = {0.f, 0.f, 0.f, 0.f};
         if constexpr (BWD) {
-          relu_bit(mw2, n, h, z > 0.0f);
-          unsure |= fabsf(z) <= th * nw2[u];
+          const float4 nq = n4[n4i];
+          nv[0] = nq.x;
+          nv[1] = nq.y;
+          nv[2] = nq.z;
+          nv[3] = nq.w;
         }
-        const float a2 = fmaxf(z, 0.0f);
-        z0 = fmaf(w3s[u], a2, z0);
-        z1 = fmaf(w3s[kHidden + u], a2, z1);
-        z2 = fmaf(w3s[2 * kHidden + u], a2, z2);
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+          const int n = 4 * n4i + j;
+          const float z = v[n] + bv[j];
+          if constexpr (BWD) {
+            relu_bit(mw2, n, h, z > 0.0f);
+            unsure |= fabsf(z) <= th * nv[j];
+          }
+          const float a2 = fmaxf(z, 0.0f);
+          z0 = fmaf(u0[j], a2, z0);
+          z1 = fmaf(u1[j], a2, z1);
+          z2 = fmaf(u2[j], a2, z2);
+        }
       }
     }
     fence_before();
