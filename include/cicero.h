@@ -451,7 +451,8 @@ size_t cicero_mlp_eval_workspace_size(int M);
 
 /* Reads the error word of a workspace after the work queued on `stream` has finished (this call
  * synchronises `stream`).  Returns CICERO_OK, CICERO_ERR_TIMEOUT or CICERO_ERR_INTERNAL; the
- * word is cleared. */
+ * word is cleared.  A rendering or backward call with no rays still clears the word (on its
+ * stream), so the status after it is CICERO_OK whatever the workspace held. */
 cicero_status cicero_workspace_status(void *workspace, void *stream);
 
 /* Stage timing for measurement tools.  Between cicero_profile_begin and cicero_profile_end the

@@ -281,6 +281,14 @@ static cicero_status check_cam(const cicero_camera* c) {
   return CICERO_OK;
 }
 
+// A call with no rays queues no kernel; it still clears the workspace's status word (on the
+// caller's stream), so that cicero_workspace_status after it reports CICERO_OK whatever the
+// workspace held before.
+static cicero_status no_rays(const RenderWs& w, void* stream) {
+  const cudaError_t e = cudaMemsetAsync(w.hdr, 0, 4, (cudaStream_t)stream);
+  return e == cudaSuccess ? CICERO_OK : cuda_fail(e, "cudaMemsetAsync(status word)");
+}
+
 static cicero_status render_common(const cicero_grid* grid, const cicero_mlp* mlp, const cicero_sampling* s,
                                    const cicero_options* opt, const RaySrc& src, int n_rays, float* rgb, float* depth,
                                    float* acc, int32_t* n_steps, void* ws, size_t ws_bytes, void* stream) {
@@ -291,7 +299,7 @@ static cicero_status render_common(const cicero_grid* grid, const cicero_mlp* ml
   if (!ws_ok(ws)) return fail(CICERO_ERR_INVALID_ARG, "workspace must be non-NULL and 256-byte aligned");
   RenderWs w;
   if (!carve_render_ws(ws, ws_bytes, plan, &w)) return fail(CICERO_ERR_WORKSPACE_TOO_SMALL, "workspace too small");
-  if (n_rays == 0) return CICERO_OK;
+  if (n_rays == 0) return no_rays(w, stream);
   return run_render(grid, mlp_ptrs(mlp), plan, src, w, single_out(rgb, depth, acc, n_steps), false,
                     (cudaStream_t)stream);
 }
@@ -578,7 +586,7 @@ cicero_status cicero_render_holes_batch(const cicero_grid* grid, const cicero_ml
   if (!ws_ok(workspace)) return fail(CICERO_ERR_INVALID_ARG, "workspace must be non-NULL and 256-byte aligned");
   RenderWs w;
   if (!carve_render_ws(workspace, ws_bytes, plan, &w)) return fail(CICERO_ERR_WORKSPACE_TOO_SMALL, "workspace too small");
-  if (max_rays == 0) return CICERO_OK;
+  if (max_rays == 0) return no_rays(w, stream);
   return run_render(grid, mlp_ptrs(mlp), plan, src, w, out, false, (cudaStream_t)stream);
 }
 
@@ -727,7 +735,7 @@ cicero_status cicero_render_backward(const cicero_grid* grid, const cicero_mlp* 
   if (!ws_ok(workspace)) return fail(CICERO_ERR_INVALID_ARG, "workspace must be non-NULL and 256-byte aligned");
   RenderWs w;
   if (!carve_render_ws(workspace, ws_bytes, plan, &w)) return fail(CICERO_ERR_WORKSPACE_TOO_SMALL, "workspace too small");
-  if (n_rays == 0) return CICERO_OK;
+  if (n_rays == 0) return no_rays(w, stream);
   RaySrc src;
   memset(&src, 0, sizeof src);
   src.kind = 1;

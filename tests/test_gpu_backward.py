@@ -127,6 +127,37 @@ def test_backward_config4_grid(cc, orc, with_mlp):
             assert rel_inf(a, b) <= 1e-3, (name, rel_inf(a, b))
 
 
+def test_backward_degenerate(cc, orc):
+    """No rays: a valid call that adds nothing.  Rays that miss the box, or whose loss gradient is
+    zero, add nothing either, and rays beside them keep their oracle gradient."""
+    import torch
+    g = scenes.scene_fd().astype(np.float32)
+    m = scenes.make_mlp(4, random_bias=True)
+    gd, md = cc.DeviceGrid.from_host(g), cc.DeviceMlp.from_host(m)
+    sp = scenes.Sampling(near=0.5, far=2.5, n_samples=32, t_stop=0.0)
+    sd = cc.sampling_from(sp)
+    z = torch.zeros(0, 3, device="cuda")
+    dd = torch.zeros(g.density.shape, device="cuda")
+    df = torch.zeros(g.features.shape, device="cuda")
+    ws = cc.workspace(cc.cicero_backward_workspace_size(gd.desc, 0, sd))
+    ws.fill_(0xFF)  # whatever the workspace held, the call leaves a clear status word
+    cc.cicero_render_backward(gd.desc, md.desc, z, z, sd, z, dd, df, None, ws)
+    cc.cicero_workspace_status(ws)
+    assert float(dd.abs().max()) == 0.0 and float(df.abs().max()) == 0.0
+    # 16 rays: 4 miss the box (origin far away, pointing away), 4 have a zero loss gradient
+    o, d = scenes.random_rays(16, seed=9)
+    o[:4] = np.array([5.0, 5.0, 5.0], dtype=o.dtype)
+    d[:4] = np.array([1.0, 0.0, 0.0], dtype=d.dtype)
+    tgt = scenes.random_targets(16, seed=10).astype(np.float64)
+    out = orc.render(g, m, sp, rays=(o, d))
+    grad = 2.0 * (out["rgb"] - tgt) / tgt.size
+    grad[4:8] = 0.0
+    wd, wf, _ = orc.backward(g, m, sp, grad, rays=(o, d))
+    gd_, gf_ = gpu_grads(cc, g, m, o, d, sp, grad)
+    assert rel_inf(gd_, wd) <= 1e-3, rel_inf(gd_, wd)
+    assert rel_inf(gf_, wf) <= 1e-3, rel_inf(gf_, wf)
+
+
 def test_autograd_function_matches_backward(cc, orc):
     import torch
     from paper_2404_11852_gb300.autograd import render_rays

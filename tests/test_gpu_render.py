@@ -117,21 +117,25 @@ def test_bf16_fp16_grid_occupancy(cc, orc, occ_scene, brick):
     check_render(out, ref, TOL16, psnr_min=PSNR16)
 
 
-def test_degenerate_sizes(cc, orc, small):
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_degenerate_sizes(cc, orc, small, precision):
     import torch
     g, m = small
+    tol = TOL16 if precision == 1 else TOL32
     cam = scenes.orbit_camera(1, 1, sampling=scenes.sampling_uniform(64))
-    check_render(gpu_render(cc, g, m, cam, cam.sampling), orc.render(g, m, cam.sampling, cam=cam), TOL32)
+    check_render(gpu_render(cc, g, m, cam, cam.sampling, precision), orc.render(g, m, cam.sampling, cam=cam), tol)
     # zero rays: a valid call that writes nothing
     gd, md = cc.DeviceGrid.from_host(g), cc.DeviceMlp.from_host(m)
     sd = cc.sampling_from(cam.sampling)
     o = torch.zeros(0, 3, device="cuda")
     ws = cc.workspace(cc.cicero_render_workspace_size(gd.desc, 0, sd))
+    ws.fill_(0xFF)  # whatever the workspace held, the call leaves a clear status word
     cc.cicero_render_rays(gd.desc, md.desc, o, o, sd, None, o, None, None, None, ws)
+    cc.cicero_workspace_status(ws)
     # a camera that misses the box entirely renders the background
     far = scenes.Camera(8, 8, 10.0, 4.0, 4.0, scenes.look_at_c2w([5.0, 5.0, 5.0], target=[10.0, 10.0, 10.0]).astype(np.float32),
                         scenes.Sampling(bg=(0.3, 0.2, 0.1)))
-    out = gpu_render(cc, g, m, far, far.sampling)
+    out = gpu_render(cc, g, m, far, far.sampling, precision)
     np.testing.assert_allclose(out["rgb"], np.tile([0.3, 0.2, 0.1], (64, 1)), atol=1e-7)
     assert np.isinf(out["depth"]).all() and (out["acc"] == 0).all()
 
