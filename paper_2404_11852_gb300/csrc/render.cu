@@ -1228,6 +1228,7 @@ __global__ void __launch_bounds__(kMlpThreads + kProdThreads, 1)
 // ReLU pre-activation within the error bound of its split-BF16 products), recomputed with the FP32
 // MLP of K5f: (c, w) and both ReLU masks overwritten.  The list holds sorted record indices
 // (rec_key, count in hdr[4]); 128 samples per step, features interpolated from global memory.
+// Launched only after k_fwd_x3, so C <= 16.
 template <typename T>
 __global__ void __launch_bounds__(kMlpThreads, 1) k_fwd_fix(GridGeo g, MlpPtrs mlp, RenderWs w,
                                                            const T* __restrict__ feat) {
@@ -1238,38 +1239,51 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_fwd_fix(GridGeo g, MlpPtrs m
   const uint32_t n = w.hdr[4];
   const int C = g.C, m = threadIdx.x;
   const int ne = 3 + 6 * mlp.n_freq;
+  const int ms = m & (kTile - 1);  // the step's sample of this thread: threads < 128 interpolate its
+                                   // features, the others encode its direction, side by side
   for (uint32_t base = blockIdx.x * kTile; base < n; base += gridDim.x * kTile) {
     const bool valid = m < kTile && base + m < n;
+    const bool has = base + ms < n;
     uint32_t si = 0;
     __syncthreads();  // the weights, or the previous step's reads of X and the masks
+    if (has) si = w.rec_key[base + ms];
     if (m < kTile) {
-      if (valid) {
-        si = w.rec_key[base + m];
-        const float4 pw = w.srt[si].pw, qd = w.srt[si].qd;
-        const float p[3] = {pw.x, pw.y, pw.z}, d[3] = {qd.y, qd.z, qd.w};
-        int i0[3];
-        float f[3], e[3 + 6 * 7];
-        const bool ok = index_sample(g, p, i0, f);
-        for (int c = 0; c < C; c++) {
-          float v = 0.0f;
-          if (ok) {
+      float fx[16];
 #pragma unroll
-            for (int q = 0; q < 8; q++) {
-              const float wq = ((q & 1) ? f[0] : 1.f - f[0]) * (((q >> 1) & 1) ? f[1] : 1.f - f[1]) *
-                               ((q >> 2) ? f[2] : 1.f - f[2]);
-              const size_t vx = ((size_t)(i0[2] + (q >> 2)) * g.n[1] + (i0[1] + ((q >> 1) & 1))) * g.n[0] +
-                                (i0[0] + (q & 1));
-              v = fmaf(wq, ldf(feat + vx * C + c), v);
-            }
+      for (int c = 0; c < 16; c++) fx[c] = 0.0f;
+      if (has) {
+        const float4 pw = w.srt[si].pw;
+        const float p[3] = {pw.x, pw.y, pw.z};
+        int i0[3];
+        float f[3];
+        if (index_sample(g, p, i0, f)) {
+#pragma unroll
+          for (int q = 0; q < 8; q++) {  // corners outer, channels inner: every load in flight at once
+            const float wq = ((q & 1) ? f[0] : 1.f - f[0]) * (((q >> 1) & 1) ? f[1] : 1.f - f[1]) *
+                             ((q >> 2) ? f[2] : 1.f - f[2]);
+            const size_t vx = ((size_t)(i0[2] + (q >> 2)) * g.n[1] + (i0[1] + ((q >> 1) & 1))) * g.n[0] +
+                              (i0[0] + (q & 1));
+            const T* v = feat + vx * C;
+#pragma unroll
+            for (int c = 0; c < 16; c++)
+              if (c < C) fx[c] = fmaf(wq, ldf(v + c), fx[c]);
           }
-          X[c * kTile + m] = v;
         }
-        encode_dir(d, mlp.n_freq, e);
-        for (int j = 0; j < ne; j++) X[(C + j) * kTile + m] = e[j];
-        for (int j = C + ne; j < kK1; j++) X[j * kTile + m] = 0.0f;
-      } else {
-        for (int j = 0; j < kK1; j++) X[j * kTile + m] = 0.0f;
       }
+#pragma unroll
+      for (int c = 0; c < 16; c++)
+        if (c < C) X[c * kTile + m] = fx[c];
+    } else {
+      float e[3 + 6 * 7];
+      if (has) {
+        const float4 qd = w.srt[si].qd;
+        const float d[3] = {qd.y, qd.z, qd.w};
+        encode_dir(d, mlp.n_freq, e);
+        for (int j = 0; j < ne; j++) X[(C + j) * kTile + ms] = e[j];
+      } else {
+        for (int j = 0; j < ne; j++) X[(C + j) * kTile + ms] = 0.0f;
+      }
+      for (int j = C + ne; j < kK1; j++) X[j * kTile + ms] = 0.0f;
     }
     __syncthreads();
     float c[3];
