@@ -702,15 +702,18 @@ def backward_workload(cc, torch, dev):
     opt = cc.options(cc.MLP_FP32, 8)
     ws_f = cc.workspace(cc.cicero_render_workspace_size(gd.desc, R, sd, opt), dev)
     ws_b = cc.workspace(cc.cicero_backward_workspace_size(gd.desc, R, sd), dev)
+    # with the MLP weight gradients: the workspace that holds their staged operands (tensor-core
+    # GEMMs); the smaller one above takes them on the CUDA cores
+    ws_bm = cc.workspace(cc.cicero_backward_mlp_workspace_size(gd.desc, R, sd), dev)
 
     def fwd(o=opt):
         cc.cicero_render_rays(gd.desc, md.desc, ot, dt, sd, o, rgb, depth, None, None, ws_f)
 
     dm = torch.zeros(m.flat().size, device=dev)
 
-    def bwd(d_mlp=None):
+    def bwd(d_mlp=None, ws=None):
         torch.sub(rgb, tgt, out=d_rgb).mul_(2.0 / rgb.numel())  # dL/drgb of the MSE loss
-        cc.cicero_render_backward(gd.desc, md.desc, ot, dt, sd, d_rgb, dd, df, d_mlp, ws_b)
+        cc.cicero_render_backward(gd.desc, md.desc, ot, dt, sd, d_rgb, dd, df, d_mlp, ws_b if ws is None else ws)
 
     fwd()
     t_f = event_ms(torch, fwd, 5)
@@ -719,7 +722,8 @@ def backward_workload(cc, torch, dev):
     t_fs = event_ms(torch, lambda: fwd(cc.options(cc.MLP_FP32_SPLIT, 8)), 5)
     fwd()
     t_b = event_ms(torch, bwd, 5)
-    t_bm = event_ms(torch, lambda: bwd(dm), 5)
+    t_bm = event_ms(torch, lambda: bwd(dm, ws_bm), 5)
+    t_bm_simt = event_ms(torch, lambda: bwd(dm), 5)
     cc.cicero_workspace_status(ws_f)
     cc.cicero_workspace_status(ws_b)
     hdr = ws_b[:32].view(torch.int32).cpu().numpy()
@@ -727,18 +731,18 @@ def backward_workload(cc, torch, dev):
     fixed = int(hdr[4])    # of which recomputed in FP32 (uncertain split-BF16 ReLU decisions)
     # per-stage device time of one backward call without and with the MLP weight gradients
     stage = {}
-    for name, arg in (("grid", None), ("grid_and_mlp", dm)):
+    for name, arg, ws in (("grid", None, None), ("grid_and_mlp", dm, ws_bm), ("grid_and_mlp_cuda_cores", dm, None)):
         torch.cuda.synchronize()
         cc.cicero_profile_begin()
         for _ in range(5):
-            bwd(arg)
+            bwd(arg, ws)
         torch.cuda.synchronize()
         p = cc.cicero_profile_end()
         stage[name] = {k: p[k][0] / 5 for k in ("march", "bucket", "gather_mlp", "composite", "bwd_ray", "bwd_brick")}
     # B2 without the weight gradients (k_bwd_brick_tc): the tensor-core GEMMs dL/dh1 = dL/dh2 W2 and
     # dL/dfeatures = dL/dh1 W1[:, :C] per composited sample, algorithmic 2 (H H + C H) FLOP, executed
     # as three split-BF16 products with the feature channels padded to N = 16, against the measured
-    # sustained BF16 peak.  With the weight gradients (k_bwd_brick, CUDA cores): recomputed layers
+    # sustained BF16 peak.  With the weight gradients on the CUDA cores (k_bwd_brick): recomputed layers
     # 1-2, dL/dh2, dL/dh1, dL/dfeatures, dW3, dW2, dW1 against the FP32 FFMA peak derived from the
     # SM count, 128 FP32 lanes per SM, 2 FLOP per FMA and the 2070 MHz maximum clock
     C, H, I = 12, 128, m.w1.shape[1]
@@ -755,13 +759,25 @@ def backward_workload(cc, torch, dev):
                     "peak": pk["bf16_tflops_sustained"], "unit": "TFLOP/s", "frac": ach / pk["bf16_tflops_sustained"],
                     "executed_tflops": flop_tc_exec * samples / t / 1e12 if t > 0 else 0.0,
                     "peak_src": "measured (sustained bf16)"}
+    # with the weight gradients on the tensor cores (k_bwd_brick_tc staging the operands, then k_dw):
+    # the grid kernel's work plus the three weight-gradient outer products per sample (dW2 | db2,
+    # dW1 | db1, dW3), algorithmic; against the measured sustained BF16 peak
+    flop_dw = 2 * (H * (H + 1) + H * (I + 1) + 3 * H)
     t = stage["grid_and_mlp"]["bwd_brick"] / 1e3
+    ach = (flop_tc + flop_dw) * samples / t / 1e12 if t > 0 else 0.0
+    roof["grid_and_mlp"] = {"kernel": "k_bwd_brick_tc (staging) + k_dw", "bound": "tensor",
+                            "flop_per_sample": flop_tc + flop_dw, "achieved": ach,
+                            "peak": pk["bf16_tflops_sustained"], "unit": "TFLOP/s",
+                            "frac": ach / pk["bf16_tflops_sustained"], "peak_src": "measured (sustained bf16)"}
+    t = stage["grid_and_mlp_cuda_cores"]["bwd_brick"] / 1e3
     ach = flop_w * samples / t / 1e12 if t > 0 else 0.0
-    roof["grid_and_mlp"] = {"kernel": "k_bwd_brick (weight gradients)", "bound": "alu", "flop_per_sample": flop_w,
-                            "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach / fp32_peak,
-                            "peak_src": "derived: SMs x 128 FP32 lanes x 2 x 2070 MHz"}
+    roof["grid_and_mlp_cuda_cores"] = {"kernel": "k_bwd_brick (weight gradients, CUDA cores)", "bound": "alu",
+                                       "flop_per_sample": flop_w, "achieved": ach, "peak": fp32_peak,
+                                       "unit": "TFLOP/s", "frac": ach / fp32_peak,
+                                       "peak_src": "derived: SMs x 128 FP32 lanes x 2 x 2070 MHz"}
     return {"workload": "8192 rays x 256 samples, 160^3 x 12 FP32 grid, MSE loss", "forward_ms": t_f,
             "forward_split_bf16_ms": t_fs, "backward_ms": t_b, "backward_with_mlp_weights_ms": t_bm,
+            "backward_with_mlp_weights_cuda_cores_ms": t_bm_simt,
             "rays_per_s_fwd_bwd": R / ((t_f + t_b) / 1e3),
             "rays_per_s_fwd_bwd_split_forward": R / ((t_fs + t_b) / 1e3), "composited_samples": samples,
             "fp32_recomputed_samples": fixed,

@@ -425,6 +425,15 @@ cicero_status cicero_render_backward(const cicero_grid *grid, const cicero_mlp *
 
 size_t cicero_backward_workspace_size(const cicero_grid *grid, int n_rays, const cicero_sampling *sampling);
 
+/* Workspace of cicero_render_backward with d_mlp on the tensor cores: the above plus each
+ * composited sample's weight-gradient operands (x, h1, h2, dL/dh2, dL/dh1, dL/dz3: 564 FP32 rows of
+ * n_rays * n_samples columns rounded up to 64).  Given a workspace at least this large (and a grid
+ * of at most 16 channels), the backward stages those operands and forms dW1 | db1, dW2 | db2 and
+ * dW3 as split-BF16 tensor-core GEMMs over the samples; with a smaller one (at least
+ * cicero_backward_workspace_size) it takes the MLP weight gradients on the CUDA cores in FP32.
+ * Both agree with the oracle's gradients to 1e-3 relative. */
+size_t cicero_backward_mlp_workspace_size(const cicero_grid *grid, int n_rays, const cicero_sampling *sampling);
+
 /* ---------------------------------------------------------------------------------------------
  * Pieces of the path, exposed for testing and for callers that drive the stages themselves.
  */

@@ -37,7 +37,9 @@ class RenderRays(torch.autograd.Function):
         want_mlp = any(ctx.needs_input_grad[10:])
         n_mlp = sum(int(torch.Size(s).numel()) for s in ctx.mlp_shapes)
         dm = torch.zeros(n_mlp, device=density.device, dtype=torch.float32) if want_mlp else None
-        ws = cc.workspace(cc.cicero_backward_workspace_size(grid.desc, ray_o.shape[0], sd), ray_o.device)
+        # with MLP gradients, a workspace that holds their staged operands (tensor-core GEMMs)
+        size = cc.cicero_backward_mlp_workspace_size if want_mlp else cc.cicero_backward_workspace_size
+        ws = cc.workspace(size(grid.desc, ray_o.shape[0], sd), ray_o.device)
         cc.cicero_render_backward(grid.desc, ctx.mlp.desc, ray_o, ray_d, sd, d_rgb.contiguous().float(), dd, df,
                                   dm, ws)
         mlp_grads = [None] * len(ctx.mlp_shapes)

@@ -76,6 +76,7 @@ _SIGS = {
     "cicero_warp_noalloc": ([_P] * 4 + [C.c_float] + [_P] * 8, C.c_int),
     "cicero_render_backward": ([_P] * 4 + [C.c_int] + [_P] * 6 + [_Z, _P], C.c_int),
     "cicero_backward_workspace_size": ([_P, C.c_int, _P], _Z),
+    "cicero_backward_mlp_workspace_size": ([_P, C.c_int, _P], _Z),
     "cicero_build_rit": ([_P] * 8 + [_Z, _P], C.c_int),
     "cicero_build_rit_workspace_size": ([_P] * 4, _Z),
     "cicero_mlp_eval": ([_P, _P, C.c_int, C.c_int, _P, _P, _Z, _P], C.c_int),
@@ -332,6 +333,10 @@ def cicero_render_backward(grid: Grid, mlp: Mlp, ray_o, ray_d, samp: Sampling, d
 
 def cicero_backward_workspace_size(grid: Grid, n_rays: int, samp: Sampling) -> int:
     return int(lib().cicero_backward_workspace_size(C.byref(grid), int(n_rays), C.byref(samp)))
+
+
+def cicero_backward_mlp_workspace_size(grid: Grid, n_rays: int, samp: Sampling) -> int:
+    return int(lib().cicero_backward_mlp_workspace_size(C.byref(grid), int(n_rays), C.byref(samp)))
 
 
 def cicero_build_rit(grid: Grid, cam: Camera, samp: Sampling, opt: Options | None, brick_offsets, samples, ws,

@@ -233,6 +233,7 @@ static cicero_status plan_render(const cicero_grid* grid, const cicero_mlp* mlp,
   p->max_tiles = (int)((Q + kTile - 1) / kTile) + p->nb;
   p->want_k = false;
   p->want_bwd = false;
+  p->want_wg = false;
   p->precision = opt ? opt->precision : CICERO_MLP_FP32;
   if (p->precision != CICERO_MLP_FP32 && p->precision != CICERO_MLP_BF16 && p->precision != CICERO_MLP_FP32_SPLIT)
     return fail(CICERO_ERR_INVALID_ARG, "precision");
@@ -493,6 +494,7 @@ static cicero_status plan_batch(const cicero_job* jobs, int n_jobs, const cicero
   p.max_tiles = (int)((Q + kTile - 1) / kTile) + p.nb;
   p.want_k = false;
   p.want_bwd = false;
+  p.want_wg = false;
   p.precision = CICERO_MLP_BF16;
   return CICERO_OK;
 }
@@ -732,6 +734,11 @@ cicero_status cicero_render_backward(const cicero_grid* grid, const cicero_mlp* 
   cicero_status st = plan_render(grid, mlp, n_rays, sampling, &opt, &plan, true);
   if (st != CICERO_OK) return st;
   plan.want_bwd = true;
+  if (d_mlp && grid->C <= 16) {
+    // the weight gradients on the tensor cores when the workspace holds their staged operands
+    plan.want_wg = true;
+    if (render_ws_bytes(plan) > ws_bytes) plan.want_wg = false;
+  }
   if (!ws_ok(workspace)) return fail(CICERO_ERR_INVALID_ARG, "workspace must be non-NULL and 256-byte aligned");
   RenderWs w;
   if (!carve_render_ws(workspace, ws_bytes, plan, &w)) return fail(CICERO_ERR_WORKSPACE_TOO_SMALL, "workspace too small");
@@ -751,6 +758,15 @@ size_t cicero_backward_workspace_size(const cicero_grid* grid, int n_rays, const
   const cicero_options opt = backward_options(grid);
   if (plan_render(grid, nullptr, n_rays, sampling, &opt, &plan, false) != CICERO_OK) return 0;
   plan.want_bwd = true;
+  return render_ws_bytes(plan);
+}
+
+size_t cicero_backward_mlp_workspace_size(const cicero_grid* grid, int n_rays, const cicero_sampling* sampling) {
+  RenderPlan plan;
+  const cicero_options opt = backward_options(grid);
+  if (plan_render(grid, nullptr, n_rays, sampling, &opt, &plan, false) != CICERO_OK) return 0;
+  plan.want_bwd = true;
+  plan.want_wg = grid->C <= 16;
   return render_ws_bytes(plan);
 }
 

@@ -607,6 +607,7 @@ __device__ __forceinline__ void mma_split(uint32_t d, uint64_t ah, uint64_t al, 
 // takes sample m of each (TMEM lane m of the group's columns [128 grp, 128 grp + 128)), its 128
 // hidden units 64 at a time and its eight trilinear corners.  The group's barriers are named
 // barriers of 128 threads, so the two groups never wait for each other until the kernel ends.
+template <bool WG>
 __global__ void __launch_bounds__(bt::kThreads, 1) k_bwd_brick_tc(GridGeo g, MlpPtrs mlp, RenderWs w, float* d_dens,
                                                                   float* d_feat) {
   using namespace tc;
@@ -697,6 +698,9 @@ __global__ void __launch_bounds__(bt::kThreads, 1) k_bwd_brick_tc(GridGeo g, Mlp
     if (more) level_a(ti + bt::kGroups);
     const int mcnt = (int)(td.y & 0xFFu);
     const int bx = (int)(td.w & 0xFFFFu), by = (int)(td.w >> 16), bz = (int)((td.y >> 8) & 0x1FFFu);
+    // the weight gradients' operands of this sample (with d_mlp): column td.x + m of the staging
+    float* stg = (WG && m < mcnt) ? w.stage + stage_at(td.x + m) : nullptr;
+    constexpr size_t qs = kStageBlock;  // row stride inside a staged block
     // this thread's sample: its voxel, weights of the colour gradient
     bool ok = false;
     float dz0 = 0.f, dz1 = 0.f, dz2 = 0.f, f[3] = {0.f, 0.f, 0.f};
@@ -732,8 +736,17 @@ __global__ void __launch_bounds__(bt::kThreads, 1) k_bwd_brick_tc(GridGeo g, Mlp
           for (int j = 0; j < 4; j++)
             v[4 * q + j] = mk[k0 + 4 * q + j] ? av[j] * dz0 + bv[j] * dz1 + cv[j] * dz2 : 0.0f;
         }
+        if (WG && stg) {
+#pragma unroll
+          for (int j = 0; j < 8; j++) stg[(WgRows::dh2 + 64 * h + k0 + j) * qs] = v[j];
+        }
         store_chunk_split(a_hi, a_lo, m, 64 * h + k0, kHidden, v);
       }
+    }
+    if (WG && stg) {
+      stg[(WgRows::dz + 0) * qs] = dz0;
+      stg[(WgRows::dz + 1) * qs] = dz1;
+      stg[(WgRows::dz + 2) * qs] = dz2;
     }
     fence_proxy_async();
     fence_before();
@@ -760,6 +773,10 @@ __global__ void __launch_bounds__(bt::kThreads, 1) k_bwd_brick_tc(GridGeo g, Mlp
         float x[8];
 #pragma unroll
         for (int j = 0; j < 8; j++) x[j] = mk[q * 8 + j] ? v[q * 8 + j] : 0.0f;
+        if (WG && stg) {
+#pragma unroll
+          for (int j = 0; j < 8; j++) stg[(WgRows::dh1 + 64 * h + q * 8 + j) * qs] = x[j];
+        }
         store_chunk_split(a_hi, a_lo, m, 64 * h + q * 8, kHidden, x);
       }
     }
@@ -869,8 +886,8 @@ __device__ __forceinline__ void relu_bit(uint32_t mw[4], int n, int h, bool on) 
 }
 
 // BWD: the backward's recompute (masks, uncertain samples listed); otherwise a forward render's
-// Feature Computation (colours only).
-template <typename T, bool BWD>
+// Feature Computation (colours only).  WG (with BWD): also stage x, h1 and h2 for the weight gradients.
+template <typename T, bool BWD, bool WG = false>
 __global__ void __launch_bounds__(xt::kThreads, 1) k_fwd_x3(GridGeo g, MlpPtrs mlp, RenderWs w,
                                                             const T* __restrict__ feat) {
   using namespace tc;
@@ -976,6 +993,9 @@ __global__ void __launch_bounds__(xt::kThreads, 1) k_fwd_x3(GridGeo g, MlpPtrs m
     const int mcnt = (int)(td.y & 0xFFu);
     const int bx = (int)(td.w & 0xFFFFu), by = (int)(td.w >> 16), bz = (int)((td.y >> 8) & 0x1FFFu);
     const bool valid = m < mcnt;
+    // the weight gradients' operands of this sample (backward with d_mlp): column start + m
+    float* stg = (BWD && WG && valid) ? w.stage + stage_at(start + m) : nullptr;
+    constexpr size_t qs = kStageBlock;  // row stride inside a staged block
     uint32_t rid = 0;
     float wgt = 0.0f, fx[xt::kMaxC];
 #pragma unroll
@@ -1021,6 +1041,7 @@ __global__ void __launch_bounds__(xt::kThreads, 1) k_fwd_x3(GridGeo g, MlpPtrs m
       for (int t = 0; t < 8; t++) {
         v[t] = xs[8 * j + t];
         x2 = fmaf(v[t], v[t], x2);
+        if (WG && stg && 8 * j + t < mlp.in_dim) stg[(WgRows::x + 8 * j + t) * qs] = v[t];
       }
       store_chunk_split(region + xt::Region::x_hi, region + xt::Region::x_lo, m, 8 * j, xt::kK1, v);
     }
@@ -1072,6 +1093,7 @@ __global__ void __launch_bounds__(xt::kThreads, 1) k_fwd_x3(GridGeo g, MlpPtrs m
             }
             x[t] = fmaxf(z, 0.0f);
             h2s = fmaf(x[t], x[t], h2s);
+            if (WG && stg) stg[(WgRows::h1 + 64 * h + n) * qs] = x[t];
           }
         }
         store_chunk_split(h_hi, h_lo, m, 64 * h + 8 * q, kHidden, x);
@@ -1123,6 +1145,7 @@ __global__ void __launch_bounds__(xt::kThreads, 1) k_fwd_x3(GridGeo g, MlpPtrs m
             unsure |= fabsf(z) <= th * nv[j];
           }
           const float a2 = fmaxf(z, 0.0f);
+          if (WG && stg) stg[(WgRows::h2 + 64 * h + n) * qs] = a2;
           z0 = fmaf(u0[j], a2, z0);
           z1 = fmaf(u1[j], a2, z1);
           z2 = fmaf(u2[j], a2, z2);
@@ -1164,7 +1187,17 @@ cicero_status launch_fwd_x3(const cicero_grid* grid, const GridGeo& geo, const M
   const dim3 grid_dim(num_sms()), block(xt::kThreads);
   {
     ProfScope ps(kStGatherMlp, st);
-    if (f16) {
+    if (bwd && ws.stage) {  // the backward with the weight gradients' staging
+      if (f16) {
+        e = cudaFuncSetAttribute(k_fwd_x3<__half, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sb);
+        if (e == cudaSuccess)
+          k_fwd_x3<__half, true, true><<<grid_dim, block, sb, st>>>(geo, mlp, ws, (const __half*)grid->features);
+      } else {
+        e = cudaFuncSetAttribute(k_fwd_x3<float, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sb);
+        if (e == cudaSuccess)
+          k_fwd_x3<float, true, true><<<grid_dim, block, sb, st>>>(geo, mlp, ws, (const float*)grid->features);
+      }
+    } else if (f16) {
       const __half* feat = (const __half*)grid->features;
       if (bwd) {
         e = cudaFuncSetAttribute(k_fwd_x3<__half, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sb);
@@ -1188,6 +1221,334 @@ cicero_status launch_fwd_x3(const cicero_grid* grid, const GridGeo& geo, const M
   count_launches(1);
   e = cudaGetLastError();
   return e == cudaSuccess ? CICERO_OK : cuda_fail(e, "k_fwd_x3");
+}
+
+// ------------------------------------------------------------------------------------------------
+// The MLP weight gradients on the tensor cores, from the operands that the recompute (x, h1, h2)
+// and B2 (dL/dh2, dL/dh1, dL/dz3) staged per composited sample (feature-major FP32 rows, column =
+// sorted sample index).  They are sums over the samples s of outer products,
+//   [dW2 | db2]  = sum_s dh2_s [h1_s, 1]^T     M = 128, N = 144 (h1, then a block whose first row is 1)
+//   [dW1 | db1]  = sum_s dh1_s [x_s, 1]^T      M = 128, N = 48 (x, then row in_dim = 1, then zeros)
+//   dW3^T        = sum_s h2_s dz3_s^T          M = 128, N = 16 (3 rows used)
+// taken as tcgen05 MMAs with K = the samples, 16 per step, on split-BF16 operands (three products
+// as in k_bwd_brick_tc), each CTA accumulating its range of samples in TMEM and adding the sums to
+// d_mlp once; db3 = sum_s dz3_s on the CUDA cores.  Staged blocks of 16 samples (36 KB each) stream
+// in by bulk copies into a ring of kRing buffers, kRing - 1 of them in flight, while the current
+// block is split into the operands and multiplied.
+namespace dw {
+constexpr int kThreads = 256;
+constexpr int kKB = kStageBlock;                      // samples per step (K of the MMAs: one K16 step)
+constexpr int kMaxRows = WgRows::rows;                // a staged block: all rows of kKB samples
+constexpr int kRing = 4;                              // staged blocks in shared memory (3 in flight)
+constexpr int kUsedMax = 4 * kHidden + kMaxIn + 3;    // operand rows: dh2, h1, dh1, h2, x (in_dim), dz (3)
+constexpr int kItems = (kUsedMax * (kKB / 4) + kThreads - 1) / kThreads;  // float4 items per thread per step
+__host__ __device__ constexpr int op_bytes(int rows) { return 2 * rows * kKB * 2; }  // hi, then lo
+// one set of operands (the MMAs of one step read it; two sets alternate)
+struct Ops {
+  static constexpr int a_dh2 = 0;                                 // [128][kKB] bf16 hi, lo
+  static constexpr int b_h1 = a_dh2 + op_bytes(kHidden);          // [144][kKB]
+  static constexpr int a_dh1 = b_h1 + op_bytes(kHidden + 16);     // [128][kKB]
+  static constexpr int b_x = a_dh1 + op_bytes(kHidden);           // [48][kKB]
+  static constexpr int a_h2 = b_x + op_bytes(kMaxIn);             // [128][kKB]
+  static constexpr int b_dz = a_h2 + op_bytes(kHidden);           // [16][kKB]
+  static constexpr int bytes = b_dz + op_bytes(16);
+};
+struct Smem {
+  static constexpr int f32 = 0;                                   // [kRing][kMaxRows][kKB] f32 staged blocks
+  static constexpr int ops = f32 + kRing * kMaxRows * kKB * 4;    // [2] Ops
+  static constexpr int red = ops + 2 * Ops::bytes;                // [8 warps][4] f32: db3 partial sums
+  static constexpr int bars = red + 8 * 4 * 4;                    // loads [kRing], MMAs [2]; TMEM address after
+  static constexpr int bytes = bars + 128;
+  static_assert(ops % 16 == 0 && Ops::bytes % 16 == 0 && bars % 16 == 0, "alignment");
+};
+constexpr uint32_t kTmemCols = 256;  // [dW2 | db2] in [0, 144), [dW1 | db1] in [160, 208), dW3^T in [224, 240)
+constexpr uint32_t kColW1 = 160, kColW3 = 224;
+}  // namespace dw
+
+// 1-D bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16), completing on bar
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+// 4 consecutive K values of one row of a K-major (K = kKB) operand of `rows` rows, split into its
+// hi and lo halves
+__device__ __forceinline__ void store4_split(char* op, int rows, int row, int k, const float v[4]) {
+  float h[4], l[4];
+#pragma unroll
+  for (int j = 0; j < 4; j++) {
+    h[j] = __bfloat162float(__float2bfloat16_rn(v[j]));
+    l[j] = v[j] - h[j];
+  }
+  const uint32_t off = tc::kmaj_off(row, k, dw::kKB);
+  *reinterpret_cast<uint2*>(op + off) = make_uint2(tc::pack_bf16(h[0], h[1]), tc::pack_bf16(h[2], h[3]));
+  *reinterpret_cast<uint2*>(op + rows * dw::kKB * 2 + off) = make_uint2(tc::pack_bf16(l[0], l[1]), tc::pack_bf16(l[2], l[3]));
+}
+
+__global__ void __launch_bounds__(dw::kThreads, 1) k_dw(MlpPtrs mlp, RenderWs w, float* d_mlp) {
+  using namespace tc;
+  extern __shared__ __align__(1024) char sm[];
+  const int I = mlp.in_dim, nrows = 4 * kHidden + I + 3;  // the operand rows: dh2, h1, dh1, h2, x, dz
+  const uint32_t n = w.hdr[2];  // composited samples: staged columns [0, n)
+  const uint32_t nblk = (n + dw::kKB - 1) / dw::kKB;
+  const uint32_t per = (nblk + gridDim.x - 1) / gridDim.x;
+  const uint32_t b0 = blockIdx.x * per, b1 = min(nblk, b0 + per);
+  if (b0 >= b1) return;  // nothing to add (uniform per CTA, before any barrier or TMEM use)
+  float* f32 = (float*)(sm + dw::Smem::f32);
+  uint64_t* lbar = (uint64_t*)(sm + dw::Smem::bars);  // [kRing]
+  uint64_t* mbar = lbar + dw::kRing;                  // [2]
+  uint32_t* tslot = (uint32_t*)(mbar + 2);
+  // constant rows of both operand sets: h1's block (row 128 = 1, 129..143 = 0), x's rows from
+  // in_dim (row in_dim = 1), dz's rows 3..15 (0)
+  for (int i = threadIdx.x; i < 2 * (16 + (kMaxIn - I) + 13) * (dw::kKB / 4); i += dw::kThreads) {
+    const int set = i / ((16 + (kMaxIn - I) + 13) * (dw::kKB / 4));
+    const int ii = i % ((16 + (kMaxIn - I) + 13) * (dw::kKB / 4));
+    const int r = ii / (dw::kKB / 4), k = (ii % (dw::kKB / 4)) * 4;
+    char* ops = sm + dw::Smem::ops + set * dw::Ops::bytes;
+    float v[4] = {0.f, 0.f, 0.f, 0.f};
+    if (r < 16) {
+      if (r == 0) v[0] = v[1] = v[2] = v[3] = 1.0f;
+      store4_split(ops + dw::Ops::b_h1, kHidden + 16, kHidden + r, k, v);
+    } else if (r < 16 + (kMaxIn - I)) {
+      const int row = I + (r - 16);
+      if (row == I) v[0] = v[1] = v[2] = v[3] = 1.0f;
+      store4_split(ops + dw::Ops::b_x, kMaxIn, row, k, v);
+    } else {
+      store4_split(ops + dw::Ops::b_dz, 16, 3 + (r - 16 - (kMaxIn - I)), k, v);
+    }
+  }
+  // this thread's items: item i = threadIdx.x + 256 j is operand row i / 4 (dh2, h1, dh1, h2, x, dz in
+  // that order), samples 4 (i % 4) .. + 3; its staged row and its place in an operand set
+  uint32_t src[dw::kItems], dst[dw::kItems], lo[dw::kItems];
+  int dzrow[dw::kItems];
+#pragma unroll
+  for (int j = 0; j < dw::kItems; j++) {
+    const int i = threadIdx.x + dw::kThreads * j, r = i / (dw::kKB / 4), k = (i % (dw::kKB / 4)) * 4;
+    int srow = 0, orow = 0, rows = 1, obase = 0;
+    dzrow[j] = -1;
+    if (r < kHidden) {
+      srow = WgRows::dh2 + r, orow = r, rows = kHidden, obase = dw::Ops::a_dh2;
+    } else if (r < 2 * kHidden) {
+      srow = WgRows::h1 + r - kHidden, orow = r - kHidden, rows = kHidden + 16, obase = dw::Ops::b_h1;
+    } else if (r < 3 * kHidden) {
+      srow = WgRows::dh1 + r - 2 * kHidden, orow = r - 2 * kHidden, rows = kHidden, obase = dw::Ops::a_dh1;
+    } else if (r < 4 * kHidden) {
+      srow = WgRows::h2 + r - 3 * kHidden, orow = r - 3 * kHidden, rows = kHidden, obase = dw::Ops::a_h2;
+    } else if (r < 4 * kHidden + I) {
+      srow = WgRows::x + r - 4 * kHidden, orow = r - 4 * kHidden, rows = kMaxIn, obase = dw::Ops::b_x;
+    } else if (r < nrows) {
+      srow = WgRows::dz + r - 4 * kHidden - I, orow = r - 4 * kHidden - I, rows = 16, obase = dw::Ops::b_dz;
+      dzrow[j] = orow;
+    } else {
+      srow = -1;  // no item
+    }
+    src[j] = srow < 0 ? 0xffffffffu : (uint32_t)(srow * dw::kKB + k);
+    dst[j] = (uint32_t)obase + kmaj_off(orow, k, dw::kKB);
+    lo[j] = (uint32_t)(rows * dw::kKB * 2);
+  }
+  if (threadIdx.x == 0) {
+    for (int j = 0; j < dw::kRing; j++) mbar_init(lbar + j, 1);
+    mbar_init(mbar, 1);
+    mbar_init(mbar + 1, 1);
+    fence_mbar_init();
+  }
+  fence_proxy_async();
+  if (threadIdx.x < 32) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(dw::kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tslot;
+  // staged block b (all rows of its kKB samples, one contiguous array) into ring buffer p, by
+  // thread 0: the byte count expected, then one bulk copy
+  auto issue = [&](uint32_t b, int p) {
+    constexpr uint32_t kBytes = dw::kMaxRows * dw::kKB * 4;
+    static_assert(kBytes % 16 == 0, "bulk copy sizes must be multiples of 16 bytes");
+    mbar_expect_tx(lbar + p, kBytes);
+    bulk_load(f32 + (size_t)p * dw::kMaxRows * dw::kKB, w.stage + (size_t)b * dw::kMaxRows * dw::kKB, kBytes,
+              lbar + p);
+  };
+  // descriptors of operand set 0; set 1 lies Ops::bytes further (the address field counts 16 bytes)
+  const uint32_t ops0 = smem_u32(sm + dw::Smem::ops);
+  auto desc = [&](int off, int rows, int half) {
+    return smem_desc(ops0 + (uint32_t)off + (uint32_t)(half * rows * dw::kKB * 2), 128u, dw::kKB * 16);
+  };
+  const uint64_t d_dh2h = desc(dw::Ops::a_dh2, kHidden, 0), d_dh2l = desc(dw::Ops::a_dh2, kHidden, 1);
+  const uint64_t d_h1h = desc(dw::Ops::b_h1, kHidden + 16, 0), d_h1l = desc(dw::Ops::b_h1, kHidden + 16, 1);
+  const uint64_t d_dh1h = desc(dw::Ops::a_dh1, kHidden, 0), d_dh1l = desc(dw::Ops::a_dh1, kHidden, 1);
+  const uint64_t d_xh = desc(dw::Ops::b_x, kMaxIn, 0), d_xl = desc(dw::Ops::b_x, kMaxIn, 1);
+  const uint64_t d_h2h = desc(dw::Ops::a_h2, kHidden, 0), d_h2l = desc(dw::Ops::a_h2, kHidden, 1);
+  const uint64_t d_dzh = desc(dw::Ops::b_dz, 16, 0), d_dzl = desc(dw::Ops::b_dz, 16, 1);
+  uint32_t lphase = 0u, mphase = 0u;  // parity of each ring buffer's next fill, of each MMA barrier's next phase
+  uint32_t mma_pending = 0u;          // bit q: operand set q's MMAs not yet waited for
+  bool alive = true;
+  float db3_0 = 0.f, db3_1 = 0.f, db3_2 = 0.f;
+  uint32_t issued_end = min(b1, b0 + (uint32_t)dw::kRing - 1), waited_end = b0;  // [b0, issued_end) issued
+  if (threadIdx.x == 0)
+    for (uint32_t j = b0; j < issued_end; j++) issue(j, (int)(j - b0));
+  for (uint32_t b = b0; b < b1 && alive; b++) {
+    const int p = (int)((b - b0) % dw::kRing), q = (int)((b - b0) & 1u);
+    // the ring's next block goes into the buffer block b - 1 used, whose reads ended before the
+    // previous step's barrier
+    if (b + dw::kRing - 1 < b1) {
+      if (threadIdx.x == 0) issue(b + dw::kRing - 1, (int)((b - b0 + dw::kRing - 1) % dw::kRing));
+      issued_end = b + dw::kRing;
+    }
+    alive = __syncthreads_and(mbar_wait(lbar + p, (lphase >> p) & 1u, &w.hdr[0]));
+    if (!alive) break;
+    lphase ^= 1u << p;
+    waited_end = b + 1;
+    if (mma_pending & (1u << q)) {  // operand set q is still being read by the MMAs of step b - 2
+      alive = __syncthreads_and(mbar_wait(mbar + q, (mphase >> q) & 1u, &w.hdr[0]));
+      fence_after();
+      if (!alive) break;
+      mphase ^= 1u << q;
+      mma_pending &= ~(1u << q);
+    }
+    // the block's rows, split into operand set q; columns at or past n (only in the last block) are zero
+    const float* fb = f32 + (size_t)p * dw::kMaxRows * dw::kKB;
+    char* ops = sm + dw::Smem::ops + q * dw::Ops::bytes;
+    const bool tail = (b + 1) * dw::kKB > n;
+#pragma unroll
+    for (int j = 0; j < dw::kItems; j++) {
+      if (src[j] == 0xffffffffu) continue;
+      const float4 v4 = *reinterpret_cast<const float4*>(fb + src[j]);
+      float v[4] = {v4.x, v4.y, v4.z, v4.w};
+      if (tail) {
+        const uint32_t c0 = b * dw::kKB + (src[j] % dw::kKB);
+#pragma unroll
+        for (int t = 0; t < 4; t++)
+          if (c0 + t >= n) v[t] = 0.0f;
+      }
+      if (dzrow[j] >= 0) {
+        const float sum = (v[0] + v[1]) + (v[2] + v[3]);
+        db3_0 += dzrow[j] == 0 ? sum : 0.0f;
+        db3_1 += dzrow[j] == 1 ? sum : 0.0f;
+        db3_2 += dzrow[j] == 2 ? sum : 0.0f;
+      }
+      float h[4], l[4];
+#pragma unroll
+      for (int t = 0; t < 4; t++) {
+        h[t] = __bfloat162float(__float2bfloat16_rn(v[t]));
+        l[t] = v[t] - h[t];
+      }
+      *reinterpret_cast<uint2*>(ops + dst[j]) = make_uint2(pack_bf16(h[0], h[1]), pack_bf16(h[2], h[3]));
+      *reinterpret_cast<uint2*>(ops + dst[j] + lo[j]) = make_uint2(pack_bf16(l[0], l[1]), pack_bf16(l[2], l[3]));
+    }
+    fence_proxy_async();
+    fence_before();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      fence_after();
+      const uint64_t o = (uint64_t)(q * dw::Ops::bytes) >> 4;  // operand set q
+      const uint32_t acc = b == b0 ? 0u : 1u;
+      mma_bf16(tmem, d_dh2h + o, d_h1h + o, idesc_bf16(kHidden + 16), acc);
+      mma_bf16(tmem, d_dh2h + o, d_h1l + o, idesc_bf16(kHidden + 16), 1u);
+      mma_bf16(tmem, d_dh2l + o, d_h1h + o, idesc_bf16(kHidden + 16), 1u);
+      mma_bf16(tmem + dw::kColW1, d_dh1h + o, d_xh + o, idesc_bf16(kMaxIn), acc);
+      mma_bf16(tmem + dw::kColW1, d_dh1h + o, d_xl + o, idesc_bf16(kMaxIn), 1u);
+      mma_bf16(tmem + dw::kColW1, d_dh1l + o, d_xh + o, idesc_bf16(kMaxIn), 1u);
+      mma_bf16(tmem + dw::kColW3, d_h2h + o, d_dzh + o, idesc_bf16(16), acc);
+      mma_bf16(tmem + dw::kColW3, d_h2h + o, d_dzl + o, idesc_bf16(16), 1u);
+      mma_bf16(tmem + dw::kColW3, d_h2l + o, d_dzh + o, idesc_bf16(16), 1u);
+      mma_commit(mbar + q);
+    }
+    mma_pending |= 1u << q;
+  }
+  // the last MMAs (their commits arrive in order, so the later set's barrier covers both)
+  for (int q = 0; q < 2 && alive; q++) {
+    if (mma_pending & (1u << q)) {
+      alive = __syncthreads_and(mbar_wait(mbar + q, (mphase >> q) & 1u, &w.hdr[0]));
+      fence_after();
+      if (alive) {
+        mphase ^= 1u << q;
+        mma_pending &= ~(1u << q);
+      }
+    }
+  }
+  if (alive) {
+    // d_mlp = [W1 [128][I], b1 [128], W2 [128][128], b2 [128], W3 [3][128], b3 [3]]
+    float* dW1 = d_mlp;
+    float* db1 = dW1 + kHidden * I;
+    float* dW2 = db1 + kHidden;
+    float* db2 = dW2 + kHidden * kHidden;
+    float* dW3 = db2 + kHidden;
+    float* db3 = dW3 + 3 * kHidden;
+    const int wq = (threadIdx.x >> 5) & 3, un = wq * 32 + (threadIdx.x & 31);  // this thread's unit (lane)
+    const uint32_t taddr = tmem + ((uint32_t)(wq * 32) << 16);
+    if (threadIdx.x < 128) {  // [dW2 | db2]
+      float v[64];
+      tmem_ld<64>(taddr, v);
+#pragma unroll
+      for (int k = 0; k < 64; k++) atomicAdd(&dW2[un * kHidden + k], v[k]);
+      tmem_ld<64>(taddr + 64, v);
+#pragma unroll
+      for (int k = 0; k < 64; k++) atomicAdd(&dW2[un * kHidden + 64 + k], v[k]);
+      tmem_ld<16>(taddr + 128, v);
+      atomicAdd(&db2[un], v[0]);
+    } else {  // [dW1 | db1], dW3^T
+      float v[32];
+      tmem_ld<32>(taddr + dw::kColW1, v);
+#pragma unroll
+      for (int k = 0; k < 32; k++) {
+        if (k < I) atomicAdd(&dW1[un * I + k], v[k]);
+        else if (k == I) atomicAdd(&db1[un], v[k]);
+      }
+      tmem_ld<16>(taddr + dw::kColW1 + 32, v);
+#pragma unroll
+      for (int k = 0; k < 16; k++) {
+        if (32 + k < I) atomicAdd(&dW1[un * I + 32 + k], v[k]);
+        else if (32 + k == I) atomicAdd(&db1[un], v[k]);
+      }
+      tmem_ld<16>(taddr + dw::kColW3, v);
+      for (int j = 0; j < 3; j++) atomicAdd(&dW3[j * kHidden + un], v[j]);
+    }
+    // db3: the CTA's sum of dz3 over its samples
+    float* red = (float*)(sm + dw::Smem::red);
+    const float part[3] = {db3_0, db3_1, db3_2};
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+      float t = part[j];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if ((threadIdx.x & 31) == 0) red[(threadIdx.x >> 5) * 4 + j] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+      float t = 0.0f;
+      for (int wi = 0; wi < dw::kThreads / 32; wi++) t += red[wi * 4 + threadIdx.x];
+      atomicAdd(&db3[threadIdx.x], t);
+    }
+  }
+  for (int q = 0; q < 2; q++)  // after a timeout: MMAs may still be running (bounded)
+    if (mma_pending & (1u << q)) mbar_wait(mbar + q, (mphase >> q) & 1u, &w.hdr[0]);
+  for (uint32_t bb = waited_end; bb < issued_end; bb++) {  // after a timeout: bulk copies still in flight
+    const int pp = (int)((bb - b0) % dw::kRing);
+    mbar_wait(lbar + pp, (lphase >> pp) & 1u, &w.hdr[0]);
+    lphase ^= 1u << pp;
+  }
+  fence_before();
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(dw::kTmemCols) : "memory");
+  }
+}
+
+cicero_status launch_dw(const MlpPtrs& mlp, const RenderWs& ws, float* d_mlp, cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(k_dw, cudaFuncAttributeMaxDynamicSharedMemorySize, dw::Smem::bytes);
+  if (e == cudaSuccess) {
+    k_dw<<<num_sms(), dw::kThreads, dw::Smem::bytes, st>>>(mlp, ws, d_mlp);
+    e = cudaGetLastError();
+  }
+  count_launches(1);
+  return e == cudaSuccess ? CICERO_OK : cuda_fail(e, "k_dw");
 }
 
 template <typename T, bool WG>
@@ -1220,14 +1581,19 @@ cicero_status run_backward(const cicero_grid* grid, const MlpPtrs& mlp, const Re
   const bool f16 = grid->dtype == CICERO_F16;
   cudaError_t e;
   const int smem_tc = bt::Smem::bytes;
-  if (!d_mlp && ws.rec_mask && plan.geo.C <= bt::kN1) {
-    // grid gradients on the tensor cores, with the forward's ReLU masks
-    e = cudaFuncSetAttribute(k_bwd_brick_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_tc);
-    if (e == cudaSuccess) {
-      k_bwd_brick_tc<<<num_sms(), bt::kThreads, smem_tc, st>>>(plan.geo, mlp, ws, d_dens, d_feat);
-      e = cudaGetLastError();
+  if (ws.rec_mask && plan.geo.C <= bt::kN1 && (!d_mlp || ws.stage)) {
+    // grid gradients on the tensor cores, with the recompute's ReLU masks; with d_mlp, the weight
+    // gradients' operands staged on the way and the weight gradients as tensor-core GEMMs after
+    if (ws.stage) {
+      e = cudaFuncSetAttribute(k_bwd_brick_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_tc);
+      if (e == cudaSuccess) k_bwd_brick_tc<true><<<num_sms(), bt::kThreads, smem_tc, st>>>(plan.geo, mlp, ws, d_dens, d_feat);
+    } else {
+      e = cudaFuncSetAttribute(k_bwd_brick_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_tc);
+      if (e == cudaSuccess) k_bwd_brick_tc<false><<<num_sms(), bt::kThreads, smem_tc, st>>>(plan.geo, mlp, ws, d_dens, d_feat);
     }
-    return e == cudaSuccess ? CICERO_OK : cuda_fail(e, "backward kernels");
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "backward kernels");
+    return d_mlp ? launch_dw(mlp, ws, d_mlp, st) : CICERO_OK;
   }
   if (d_mlp)
     e = f16 ? launch_bwd_brick<__half, true>(plan, src, mlp, ws, grid->features, d_dens, d_feat, d_mlp, smem, st)

@@ -75,9 +75,26 @@ struct RenderWs {
   SrtRec* srt;          // [Q] the Ray Index Table payload in brick order
   RayGeo* ray_geo;      // [R] geometry of each ray's samples
   struct RaySetup* setup;  // [R] per-ray setup of the march (ray, slots, active-slot mask, records)
+  float* stage;         // per-sample operands of the MLP weight gradients (backward with d_mlp only; may be
+                        // null): blocks of 16 sorted samples, each [WgRows::rows][16] FP32 (stage_at)
   int R, S, nb, max_tiles;
   uint32_t Q;
 };
+
+// Rows of the weight-gradient staging: x (input, in_dim rows used), h1, h2 (layers 1 and 2 after
+// ReLU), dL/dh2 and dL/dh1 (masked), dL/dz3 (3 rows used)
+struct WgRows {
+  static constexpr int x = 0, h1 = 48, h2 = 176, dh2 = 304, dh1 = 432, dz = 560, rows = 564;
+};
+// floats of the staging for a capacity of Q samples, and the column of sorted sample s (row r of it
+// is at stage_at(s) + kStageBlock r): a block of kStageBlock samples is one contiguous array
+constexpr int kStageBlock = 16;
+__host__ __device__ inline size_t stage_floats(uint32_t Q) {
+  return (((size_t)Q + kStageBlock - 1) / kStageBlock) * WgRows::rows * kStageBlock;
+}
+__host__ __device__ inline size_t stage_at(uint32_t s) {
+  return (size_t)(s / kStageBlock) * WgRows::rows * kStageBlock + (s % kStageBlock);
+}
 
 struct RenderPlan {
   GridGeo geo;
@@ -87,6 +104,7 @@ struct RenderPlan {
   uint32_t Q;
   bool want_k;
   bool want_bwd;
+  bool want_wg;  // the backward stages the MLP weight gradients' operands (RenderWs::stage)
   cicero_precision precision;
   int mlp_groups;  // BF16 tensor-core MLP tiles in flight per SM (0 = as many as fit)
 };
@@ -247,6 +265,8 @@ cicero_status launch_mlp_eval_f32(const MlpPtrs& mlp, const float* x, int M, flo
 // The backward's forward recompute on the tensor cores (split-BF16 products, FP32 accumulation):
 // (c, w) into rec_c and the ReLU masks into rec_mask for every composited sample (backward.cu)
 bool fwd_x3_supported(const GridGeo& g, const MlpPtrs& mlp);
+// dW1 | db1, dW2 | db2, dW3 (and db3) from the staged operands, added to d_mlp (backward.cu)
+cicero_status launch_dw(const MlpPtrs& mlp, const RenderWs& ws, float* d_mlp, cudaStream_t st);
 cicero_status launch_fwd_x3(const cicero_grid* grid, const GridGeo& geo, const MlpPtrs& mlp, const RenderWs& ws,
                             cudaStream_t st);
 

@@ -60,7 +60,10 @@ def test_workspace_size_queries(cc):
     # at least the per-sample records (t, w, brick, sorted id: 4 B each; colour 16 B) of R*S slots
     assert ws >= R * 64 * 32
     assert cc.cicero_render_workspace_size(_grid(), R, sp, cc.options(1, 4)) > 0
-    assert cc.cicero_backward_workspace_size(_grid(), R, sp) > ws
+    wb = cc.cicero_backward_workspace_size(_grid(), R, sp)
+    assert wb > ws
+    # with the weight gradients' operands: 564 FP32 rows of R * S columns (rounded up to 64)
+    assert cc.cicero_backward_mlp_workspace_size(_grid(), R, sp) >= wb + 564 * 4 * R * 64
     cam = cc.camera(800, 800, 1000.0, 400.0, 400.0, np.eye(3, 4))
     assert cc.cicero_warp_workspace_size(cam) >= 800 * 800 * 8
     assert cc.cicero_mlp_eval_workspace_size(1000) >= 256

@@ -16,9 +16,10 @@ def cc():
     return cicero
 
 
-def gpu_grads(cc, g32, m, o, d, sp, grad, with_mlp=False, feat_offset=0):
+def gpu_grads(cc, g32, m, o, d, sp, grad, with_mlp=False, feat_offset=0, mlp_path="tc"):
     """feat_offset > 0 places d_features that many floats into a larger buffer (an address that
-    is not 16-byte aligned when feat_offset % 4 != 0)."""
+    is not 16-byte aligned when feat_offset % 4 != 0).  With the MLP weight gradients, mlp_path
+    "tc" sizes the workspace for their tensor-core GEMMs, "simt" for the CUDA-core path."""
     import torch
     gd, md = cc.DeviceGrid.from_host(g32), cc.DeviceMlp.from_host(m)
     sd = cc.sampling_from(sp)
@@ -27,7 +28,8 @@ def gpu_grads(cc, g32, m, o, d, sp, grad, with_mlp=False, feat_offset=0):
     dd = torch.zeros(g32.density.shape, device="cuda")
     df = torch.zeros(g32.features.size + feat_offset, device="cuda")[feat_offset:].view(g32.features.shape)
     dm = torch.zeros(m.flat().size, device="cuda") if with_mlp else None
-    ws = cc.workspace(cc.cicero_backward_workspace_size(gd.desc, o.shape[0], sd))
+    size = cc.cicero_backward_mlp_workspace_size if with_mlp and mlp_path == "tc" else cc.cicero_backward_workspace_size
+    ws = cc.workspace(size(gd.desc, o.shape[0], sd))
     cc.cicero_render_backward(gd.desc, md.desc, ot, dt, sd, gr, dd, df, dm, ws)
     cc.cicero_workspace_status(ws)
     out = dd.cpu().double().numpy(), df.cpu().double().numpy()
@@ -180,8 +182,9 @@ def test_autograd_function_matches_backward(cc, orc):
     assert rel_inf(feat.grad.cpu().double().numpy(), wf) <= 1e-3
 
 
+@pytest.mark.parametrize("path", ["tc", "simt"])
 @pytest.mark.parametrize("case", ["fd", "occ"])
-def test_backward_mlp_weights(cc, orc, case):
+def test_backward_mlp_weights(cc, orc, case, path):
     """dL/d(W1, b1, W2, b2, W3, b3) against the oracle, per tensor (relative inf-norm <= 1e-3),
     together with the grid gradients of the same call (which must not change with d_mlp)."""
     if case == "fd":
@@ -200,7 +203,7 @@ def test_backward_mlp_weights(cc, orc, case):
     grad = 2.0 * (out["rgb"] - tgt) / tgt.size
     grad[out["amb"]] = 0.0  # ambiguous early stops contribute nothing on either side
     wd, wf, wm = orc.backward(g, m, sp, grad, rays=(o, d), with_mlp=True)
-    dd, df, dm = gpu_grads(cc, g, m, o, d, sp, grad, with_mlp=True)
+    dd, df, dm = gpu_grads(cc, g, m, o, d, sp, grad, with_mlp=True, mlp_path=path)
     assert rel_inf(dd, wd) <= 1e-3, rel_inf(dd, wd)
     assert rel_inf(df, wf) <= 1e-3, rel_inf(df, wf)
     names = ("w1", "b1", "w2", "b2", "w3", "b3")
