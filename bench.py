@@ -738,7 +738,8 @@ def backward_workload(cc, torch, dev):
             bwd(arg, ws)
         torch.cuda.synchronize()
         p = cc.cicero_profile_end()
-        stage[name] = {k: p[k][0] / 5 for k in ("march", "bucket", "gather_mlp", "composite", "bwd_ray", "bwd_brick")}
+        stage[name] = {k: p[k][0] / 5 for k in ("march", "bucket", "gather_mlp", "composite", "bwd_ray", "bwd_brick",
+                                                "bwd_weights")}
     # B2 without the weight gradients (k_bwd_brick_tc): the tensor-core GEMMs dL/dh1 = dL/dh2 W2 and
     # dL/dfeatures = dL/dh1 W1[:, :C] per composited sample, algorithmic 2 (H H + C H) FLOP, executed
     # as three split-BF16 products with the feature channels padded to N = 16, against the measured
@@ -759,16 +760,26 @@ def backward_workload(cc, torch, dev):
                     "peak": pk["bf16_tflops_sustained"], "unit": "TFLOP/s", "frac": ach / pk["bf16_tflops_sustained"],
                     "executed_tflops": flop_tc_exec * samples / t / 1e12 if t > 0 else 0.0,
                     "peak_src": "measured (sustained bf16)"}
-    # with the weight gradients on the tensor cores (k_bwd_brick_tc staging the operands, then k_dw):
-    # the grid kernel's work plus the three weight-gradient outer products per sample (dW2 | db2,
-    # dW1 | db1, dW3), algorithmic; against the measured sustained BF16 peak
-    flop_dw = 2 * (H * (H + 1) + H * (I + 1) + 3 * H)
+    # with the weight gradients on the tensor cores: k_bwd_brick_tc also stages dL/dh2, dL/dh1 and dL/dz3
+    # (same FLOPs, tensor roofline), then k_dw reads every staged block once (per 16 samples 36,352
+    # bytes of split-BF16 operand rows: x, h1, h2 written by the recompute, the three gradients by the
+    # grid kernel) and forms the weight gradients (dW2 | db2, dW1 | db1, dW3 | db3) as tensor-core GEMMs
+    # over the samples: HBM roofline on the staged bytes against the measured copy bandwidth, the
+    # GEMMs' algorithmic rate beside it
     t = stage["grid_and_mlp"]["bwd_brick"] / 1e3
-    ach = (flop_tc + flop_dw) * samples / t / 1e12 if t > 0 else 0.0
-    roof["grid_and_mlp"] = {"kernel": "k_bwd_brick_tc (staging) + k_dw", "bound": "tensor",
-                            "flop_per_sample": flop_tc + flop_dw, "achieved": ach,
-                            "peak": pk["bf16_tflops_sustained"], "unit": "TFLOP/s",
-                            "frac": ach / pk["bf16_tflops_sustained"], "peak_src": "measured (sustained bf16)"}
+    ach = flop_tc * samples / t / 1e12 if t > 0 else 0.0
+    roof["grid_staging"] = {"kernel": "k_bwd_brick_tc (staging the weight-gradient operands)", "bound": "tensor",
+                            "flop_per_sample": flop_tc, "achieved": ach, "peak": pk["bf16_tflops_sustained"],
+                            "unit": "TFLOP/s", "frac": ach / pk["bf16_tflops_sustained"],
+                            "peak_src": "measured (sustained bf16)"}
+    flop_dw = 2 * (H * (H + 1) + H * (I + 1) + 3 * H)
+    stage_bytes = 36352 / 16
+    t = stage["grid_and_mlp"]["bwd_weights"] / 1e3
+    ach = stage_bytes * samples / t / 1e9 if t > 0 else 0.0
+    roof["weights"] = {"kernel": "k_dw", "bound": "hbm", "bytes_per_sample": stage_bytes, "achieved": ach,
+                       "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": ach / pk["hbm_gbs"],
+                       "peak_src": "measured (copy)", "flop_per_sample": flop_dw,
+                       "tflops": flop_dw * samples / t / 1e12 if t > 0 else 0.0}
     t = stage["grid_and_mlp_cuda_cores"]["bwd_brick"] / 1e3
     ach = flop_w * samples / t / 1e12 if t > 0 else 0.0
     roof["grid_and_mlp_cuda_cores"] = {"kernel": "k_bwd_brick (weight gradients, CUDA cores)", "bound": "alu",

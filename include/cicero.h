@@ -426,10 +426,11 @@ cicero_status cicero_render_backward(const cicero_grid *grid, const cicero_mlp *
 size_t cicero_backward_workspace_size(const cicero_grid *grid, int n_rays, const cicero_sampling *sampling);
 
 /* Workspace of cicero_render_backward with d_mlp on the tensor cores: the above plus each
- * composited sample's weight-gradient operands (x, h1, h2, dL/dh2, dL/dh1, dL/dz3: 564 FP32 rows of
- * n_rays * n_samples columns rounded up to 64).  Given a workspace at least this large (and a grid
- * of at most 16 channels), the backward stages those operands and forms dW1 | db1, dW2 | db2 and
- * dW3 as split-BF16 tensor-core GEMMs over the samples; with a smaller one (at least
+ * composited sample's weight-gradient operands (x, h1, h2, dL/dh2, dL/dh1, dL/dz3, each value split
+ * into two BF16 halves: 2,272 bytes per sample slot, n_rays * n_samples slots rounded up to 64).
+ * Given a workspace at least this large (and a grid of at most 16 channels), the backward stages
+ * those operands and forms dW1 | db1, dW2 | db2 and dW3 | db3 as split-BF16 tensor-core GEMMs over
+ * the samples; with a smaller one (at least
  * cicero_backward_workspace_size) it takes the MLP weight gradients on the CUDA cores in FP32.
  * Both agree with the oracle's gradients to 1e-3 relative. */
 size_t cicero_backward_mlp_workspace_size(const cicero_grid *grid, int n_rays, const cicero_sampling *sampling);
@@ -470,7 +471,8 @@ cicero_status cicero_workspace_status(void *workspace, void *stream);
  * the number of timed launches.  Stages: 0 march (Indexing + density + transmittance),
  * 1 brick bucketing (Ray Index Table), 2 brick gather + MLP, 3 compositing, 4 warp splat
  * (Eq. 1-3 + depth test), 5 warp resolve + hole listing, 6 backward per ray, 7 backward per
- * brick, 8 MLP alone.  Profiling state is process-wide; do not profile from several threads. */
+ * brick (grid gradients; with the weight gradients on CUDA cores, those too), 8 MLP alone,
+ * 9 MLP weight gradients from the staged operands.  Profiling state is process-wide; do not profile from several threads. */
 cicero_status cicero_profile_begin(void);
 cicero_status cicero_profile_end(double *total_ms, long long *launches, int n_stages);
 

@@ -377,7 +377,7 @@ def cicero_workspace_status(ws, stream=None):
 
 
 STAGES = ("march", "bucket", "gather_mlp", "composite", "warp_splat", "warp_resolve", "bwd_ray", "bwd_brick",
-          "mlp_eval")
+          "mlp_eval", "bwd_weights")
 
 
 def cicero_profile_begin():

@@ -574,6 +574,34 @@ __device__ __forceinline__ void store_chunk_split(char* hi_base, char* lo_base, 
   tc::store_chunk(lo_base, row, k0, K, l);
 }
 
+// the same split of 8 values, packed as the two 16-byte rows (hi, lo) of a BF16 operand
+__device__ __forceinline__ void split8(const float* v, uint4& hi, uint4& lo) {
+  float h[8], l[8];
+#pragma unroll
+  for (int j = 0; j < 8; j++) {
+    h[j] = __bfloat162float(__float2bfloat16_rn(v[j]));
+    l[j] = v[j] - h[j];
+  }
+  hi = make_uint4(tc::pack_bf16(h[0], h[1]), tc::pack_bf16(h[2], h[3]), tc::pack_bf16(h[4], h[5]),
+                  tc::pack_bf16(h[6], h[7]));
+  lo = make_uint4(tc::pack_bf16(l[0], l[1]), tc::pack_bf16(l[2], l[3]), tc::pack_bf16(l[4], l[5]),
+                  tc::pack_bf16(l[6], l[7]));
+}
+
+// row (k0 .. k0 + 7) of a K-major operand in shared memory, from packed hi and lo rows
+__device__ __forceinline__ void store_rows(char* hi_base, char* lo_base, int row, int k0, int K, const uint4& hi,
+                                           const uint4& lo) {
+  *reinterpret_cast<uint4*>(hi_base + tc::kmaj_off(row, k0, K)) = hi;
+  *reinterpret_cast<uint4*>(lo_base + tc::kmaj_off(row, k0, K)) = lo;
+}
+
+// row group g of the staged operand at offset op (R rows) of one sample, whose rows start at col
+// (stage_col of the sample)
+__device__ __forceinline__ void stage_put(char* col, int op, int R, int g, const uint4& hi, const uint4& lo) {
+  *reinterpret_cast<uint4*>(col + op + 256 * g) = hi;
+  *reinterpret_cast<uint4*>(col + op + 32 * R + 256 * g) = lo;
+}
+
 // ReLU mask of the half h of the hidden units (h = 0: units 0..63, 1: 64..127), in the layout the
 // recompute writes (unit n < 64 is bit n % 4 of byte n / 4, unit 64 + n bit 4 + n % 4): the
 // words shifted so that unit 64 h + i is bit (i / 4 % 4) * 8 + i % 4 of word i / 16.
@@ -699,8 +727,7 @@ __global__ void __launch_bounds__(bt::kThreads, 1) k_bwd_brick_tc(GridGeo g, Mlp
     const int mcnt = (int)(td.y & 0xFFu);
     const int bx = (int)(td.w & 0xFFFFu), by = (int)(td.w >> 16), bz = (int)((td.y >> 8) & 0x1FFFu);
     // the weight gradients' operands of this sample (with d_mlp): column td.x + m of the staging
-    float* stg = (WG && m < mcnt) ? w.stage + stage_at(td.x + m) : nullptr;
-    constexpr size_t qs = kStageBlock;  // row stride inside a staged block
+    char* stg = (WG && m < mcnt) ? w.stage + stage_col(td.x + m) : nullptr;
     // this thread's sample: its voxel, weights of the colour gradient
     bool ok = false;
     float dz0 = 0.f, dz1 = 0.f, dz2 = 0.f, f[3] = {0.f, 0.f, 0.f};
@@ -736,17 +763,17 @@ __global__ void __launch_bounds__(bt::kThreads, 1) k_bwd_brick_tc(GridGeo g, Mlp
           for (int j = 0; j < 4; j++)
             v[4 * q + j] = mk[k0 + 4 * q + j] ? av[j] * dz0 + bv[j] * dz1 + cv[j] * dz2 : 0.0f;
         }
-        if (WG && stg) {
-#pragma unroll
-          for (int j = 0; j < 8; j++) stg[(WgRows::dh2 + 64 * h + k0 + j) * qs] = v[j];
-        }
-        store_chunk_split(a_hi, a_lo, m, 64 * h + k0, kHidden, v);
+        uint4 hi, lo;
+        split8(v, hi, lo);
+        store_rows(a_hi, a_lo, m, 64 * h + k0, kHidden, hi, lo);
+        if (WG && stg) stage_put(stg, WgStage::dh2, kHidden, (64 * h + k0) / 8, hi, lo);
       }
     }
     if (WG && stg) {
-      stg[(WgRows::dz + 0) * qs] = dz0;
-      stg[(WgRows::dz + 1) * qs] = dz1;
-      stg[(WgRows::dz + 2) * qs] = dz2;
+      const float v[8] = {dz0, dz1, dz2, 0.f, 0.f, 0.f, 0.f, 0.f};
+      uint4 hi, lo;
+      split8(v, hi, lo);
+      stage_put(stg, WgStage::dz, 8, 0, hi, lo);
     }
     fence_proxy_async();
     fence_before();
@@ -773,11 +800,10 @@ __global__ void __launch_bounds__(bt::kThreads, 1) k_bwd_brick_tc(GridGeo g, Mlp
         float x[8];
 #pragma unroll
         for (int j = 0; j < 8; j++) x[j] = mk[q * 8 + j] ? v[q * 8 + j] : 0.0f;
-        if (WG && stg) {
-#pragma unroll
-          for (int j = 0; j < 8; j++) stg[(WgRows::dh1 + 64 * h + q * 8 + j) * qs] = x[j];
-        }
-        store_chunk_split(a_hi, a_lo, m, 64 * h + q * 8, kHidden, x);
+        uint4 hi, lo;
+        split8(x, hi, lo);
+        store_rows(a_hi, a_lo, m, 64 * h + q * 8, kHidden, hi, lo);
+        if (WG && stg) stage_put(stg, WgStage::dh1, kHidden, 8 * h + q, hi, lo);
       }
     }
     fence_proxy_async();
@@ -994,8 +1020,7 @@ __global__ void __launch_bounds__(xt::kThreads, 1) k_fwd_x3(GridGeo g, MlpPtrs m
     const int bx = (int)(td.w & 0xFFFFu), by = (int)(td.w >> 16), bz = (int)((td.y >> 8) & 0x1FFFu);
     const bool valid = m < mcnt;
     // the weight gradients' operands of this sample (backward with d_mlp): column start + m
-    float* stg = (BWD && WG && valid) ? w.stage + stage_at(start + m) : nullptr;
-    constexpr size_t qs = kStageBlock;  // row stride inside a staged block
+    char* stg = (BWD && WG && valid) ? w.stage + stage_col(start + m) : nullptr;
     uint32_t rid = 0;
     float wgt = 0.0f, fx[xt::kMaxC];
 #pragma unroll
@@ -1041,9 +1066,11 @@ __global__ void __launch_bounds__(xt::kThreads, 1) k_fwd_x3(GridGeo g, MlpPtrs m
       for (int t = 0; t < 8; t++) {
         v[t] = xs[8 * j + t];
         x2 = fmaf(v[t], v[t], x2);
-        if (WG && stg && 8 * j + t < mlp.in_dim) stg[(WgRows::x + 8 * j + t) * qs] = v[t];
       }
-      store_chunk_split(region + xt::Region::x_hi, region + xt::Region::x_lo, m, 8 * j, xt::kK1, v);
+      uint4 hi, lo;
+      split8(v, hi, lo);
+      store_rows(region + xt::Region::x_hi, region + xt::Region::x_lo, m, 8 * j, xt::kK1, hi, lo);
+      if (WG && stg) stage_put(stg, WgStage::x, xt::kK1, j, hi, lo);
     }
     fence_proxy_async();
     fence_before();
@@ -1093,10 +1120,12 @@ __global__ void __launch_bounds__(xt::kThreads, 1) k_fwd_x3(GridGeo g, MlpPtrs m
             }
             x[t] = fmaxf(z, 0.0f);
             h2s = fmaf(x[t], x[t], h2s);
-            if (WG && stg) stg[(WgRows::h1 + 64 * h + n) * qs] = x[t];
           }
         }
-        store_chunk_split(h_hi, h_lo, m, 64 * h + 8 * q, kHidden, x);
+        uint4 hi, lo;
+        split8(x, hi, lo);
+        store_rows(h_hi, h_lo, m, 64 * h + 8 * q, kHidden, hi, lo);
+        if (WG && stg) stage_put(stg, WgStage::h1, kHidden, 8 * h + q, hi, lo);
       }
     }
     fence_proxy_async();
@@ -1113,6 +1142,7 @@ __global__ void __launch_bounds__(xt::kThreads, 1) k_fwd_x3(GridGeo g, MlpPtrs m
     if (!alive) break;
     phase ^= 1u;
     float z0 = 0.0f, z1 = 0.0f, z2 = 0.0f;
+    float h2v[8];  // h2 of 8 consecutive units, staged once complete (WG)
     const float th = BWD ? xt::kEps * (sqrtf(h2s) + sqrtf(x2) * *fro1) : 0.0f;
 #pragma unroll 1
     for (int h = 0; h < 2; h++) {
@@ -1145,10 +1175,15 @@ __global__ void __launch_bounds__(xt::kThreads, 1) k_fwd_x3(GridGeo g, MlpPtrs m
             unsure |= fabsf(z) <= th * nv[j];
           }
           const float a2 = fmaxf(z, 0.0f);
-          if (WG && stg) stg[(WgRows::h2 + 64 * h + n) * qs] = a2;
+          if constexpr (WG) h2v[4 * (n4i & 1) + j] = a2;
           z0 = fmaf(u0[j], a2, z0);
           z1 = fmaf(u1[j], a2, z1);
           z2 = fmaf(u2[j], a2, z2);
+        }
+        if (WG && stg && (n4i & 1)) {  // units 64 h + 8 (n4i / 2) .. + 7 complete
+          uint4 hi, lo;
+          split8(h2v, hi, lo);
+          stage_put(stg, WgStage::h2, kHidden, 8 * h + n4i / 2, hi, lo);
         }
       }
     }
@@ -1236,33 +1271,19 @@ cicero_status launch_fwd_x3(const cicero_grid* grid, const GridGeo& geo, const M
 // in by bulk copies into a ring of kRing buffers, kRing - 1 of them in flight, while the current
 // block is split into the operands and multiplied.
 namespace dw {
-constexpr int kThreads = 256;
-constexpr int kKB = kStageBlock;                      // samples per step (K of the MMAs: one K16 step)
-constexpr int kMaxRows = WgRows::rows;                // a staged block: all rows of kKB samples
-constexpr int kRing = 4;                              // staged blocks in shared memory (3 in flight)
-constexpr int kUsedMax = 4 * kHidden + kMaxIn + 3;    // operand rows: dh2, h1, dh1, h2, x (in_dim), dz (3)
-constexpr int kItems = (kUsedMax * (kKB / 4) + kThreads - 1) / kThreads;  // float4 items per thread per step
-__host__ __device__ constexpr int op_bytes(int rows) { return 2 * rows * kKB * 2; }  // hi, then lo
-// one set of operands (the MMAs of one step read it; two sets alternate)
-struct Ops {
-  static constexpr int a_dh2 = 0;                                 // [128][kKB] bf16 hi, lo
-  static constexpr int b_h1 = a_dh2 + op_bytes(kHidden);          // [144][kKB]
-  static constexpr int a_dh1 = b_h1 + op_bytes(kHidden + 16);     // [128][kKB]
-  static constexpr int b_x = a_dh1 + op_bytes(kHidden);           // [48][kKB]
-  static constexpr int a_h2 = b_x + op_bytes(kMaxIn);             // [128][kKB]
-  static constexpr int b_dz = a_h2 + op_bytes(kHidden);           // [16][kKB]
-  static constexpr int bytes = b_dz + op_bytes(16);
-};
+constexpr int kThreads = 128;                  // thread 0 runs the pipeline; all four warps read TMEM out
+constexpr int kRing = 6;                       // staged blocks in shared memory (copies in flight)
+constexpr int kBuf = WgStage::bytes + 256;     // a staged block and a zero row group (dL/dz3 rows 8..15)
 struct Smem {
-  static constexpr int f32 = 0;                                   // [kRing][kMaxRows][kKB] f32 staged blocks
-  static constexpr int ops = f32 + kRing * kMaxRows * kKB * 4;    // [2] Ops
-  static constexpr int red = ops + 2 * Ops::bytes;                // [8 warps][4] f32: db3 partial sums
-  static constexpr int bars = red + 8 * 4 * 4;                    // loads [kRing], MMAs [2]; TMEM address after
-  static constexpr int bytes = bars + 128;
-  static_assert(ops % 16 == 0 && Ops::bytes % 16 == 0 && bars % 16 == 0, "alignment");
+  static constexpr int ring = 0;                     // [kRing][kBuf]
+  static constexpr int ones = ring + kRing * kBuf;   // [128][16] BF16 ones: A of db3, B of db1 and db2
+  static constexpr int bars = ones + 4096;           // full [kRing], free [kRing]; TMEM address after
+  static constexpr int bytes = bars + 16 * kRing + 16;
+  static_assert(kBuf % 16 == 0 && ones % 16 == 0 && bars % 16 == 0, "alignment");
 };
-constexpr uint32_t kTmemCols = 256;  // [dW2 | db2] in [0, 144), [dW1 | db1] in [160, 208), dW3^T in [224, 240)
-constexpr uint32_t kColW1 = 160, kColW3 = 224;
+// tensor memory: dW2 [0, 128), db2 [128, 144), dW1 [160, 208), db1 [208, 224), dW3^T [224, 240), db3 [240, 256)
+constexpr uint32_t kTmemCols = 256;
+constexpr uint32_t kColB2 = 128, kColW1 = 160, kColB1 = 208, kColW3 = 224, kColB3 = 240;
 }  // namespace dw
 
 // 1-D bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16), completing on bar
@@ -1273,85 +1294,46 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
                : "memory");
 }
 
-// 4 consecutive K values of one row of a K-major (K = kKB) operand of `rows` rows, split into its
-// hi and lo halves
-__device__ __forceinline__ void store4_split(char* op, int rows, int row, int k, const float v[4]) {
-  float h[4], l[4];
-#pragma unroll
-  for (int j = 0; j < 4; j++) {
-    h[j] = __bfloat162float(__float2bfloat16_rn(v[j]));
-    l[j] = v[j] - h[j];
-  }
-  const uint32_t off = tc::kmaj_off(row, k, dw::kKB);
-  *reinterpret_cast<uint2*>(op + off) = make_uint2(tc::pack_bf16(h[0], h[1]), tc::pack_bf16(h[2], h[3]));
-  *reinterpret_cast<uint2*>(op + rows * dw::kKB * 2 + off) = make_uint2(tc::pack_bf16(l[0], l[1]), tc::pack_bf16(l[2], l[3]));
-}
-
+// MLP weight gradients over all composited samples, from the staged operands (WgStage): per block
+// of 16 samples, D += A B^T with K = the samples, split-BF16 products (hi hi + hi lo + lo hi):
+//   [dW2 | db2] = dL/dh2^T [h1 | 1],  [dW1 | db1] = dL/dh1^T [x | 1],  dW3^T = h2^T dL/dz3,
+//   db3 = 1^T dL/dz3,
+// both operands MN-major (the staged rows), accumulated in TMEM over the CTA's blocks and added to
+// d_mlp once per CTA.  Thread 0 streams the blocks through a ring of kRing buffers with bulk copies
+// (one mbarrier per buffer for the copy, one for the MMAs that read it) and issues the MMAs.
 __global__ void __launch_bounds__(dw::kThreads, 1) k_dw(MlpPtrs mlp, RenderWs w, float* d_mlp) {
   using namespace tc;
   extern __shared__ __align__(1024) char sm[];
-  const int I = mlp.in_dim, nrows = 4 * kHidden + I + 3;  // the operand rows: dh2, h1, dh1, h2, x, dz
+  const int I = mlp.in_dim;
   const uint32_t n = w.hdr[2];  // composited samples: staged columns [0, n)
-  const uint32_t nblk = (n + dw::kKB - 1) / dw::kKB;
+  const uint32_t nblk = (n + kStageBlock - 1) / kStageBlock;
   const uint32_t per = (nblk + gridDim.x - 1) / gridDim.x;
   const uint32_t b0 = blockIdx.x * per, b1 = min(nblk, b0 + per);
   if (b0 >= b1) return;  // nothing to add (uniform per CTA, before any barrier or TMEM use)
-  float* f32 = (float*)(sm + dw::Smem::f32);
-  uint64_t* lbar = (uint64_t*)(sm + dw::Smem::bars);  // [kRing]
-  uint64_t* mbar = lbar + dw::kRing;                  // [2]
-  uint32_t* tslot = (uint32_t*)(mbar + 2);
-  // constant rows of both operand sets: h1's block (row 128 = 1, 129..143 = 0), x's rows from
-  // in_dim (row in_dim = 1), dz's rows 3..15 (0)
-  for (int i = threadIdx.x; i < 2 * (16 + (kMaxIn - I) + 13) * (dw::kKB / 4); i += dw::kThreads) {
-    const int set = i / ((16 + (kMaxIn - I) + 13) * (dw::kKB / 4));
-    const int ii = i % ((16 + (kMaxIn - I) + 13) * (dw::kKB / 4));
-    const int r = ii / (dw::kKB / 4), k = (ii % (dw::kKB / 4)) * 4;
-    char* ops = sm + dw::Smem::ops + set * dw::Ops::bytes;
-    float v[4] = {0.f, 0.f, 0.f, 0.f};
-    if (r < 16) {
-      if (r == 0) v[0] = v[1] = v[2] = v[3] = 1.0f;
-      store4_split(ops + dw::Ops::b_h1, kHidden + 16, kHidden + r, k, v);
-    } else if (r < 16 + (kMaxIn - I)) {
-      const int row = I + (r - 16);
-      if (row == I) v[0] = v[1] = v[2] = v[3] = 1.0f;
-      store4_split(ops + dw::Ops::b_x, kMaxIn, row, k, v);
-    } else {
-      store4_split(ops + dw::Ops::b_dz, 16, 3 + (r - 16 - (kMaxIn - I)), k, v);
-    }
+  uint64_t* full = (uint64_t*)(sm + dw::Smem::bars);  // [kRing]: the buffer's copy landed
+  uint64_t* fre = full + dw::kRing;                   // [kRing]: the MMAs reading the buffer are done
+  uint32_t* tslot = (uint32_t*)(fre + dw::kRing);
+  // the last block's columns from n on are written by no producer: zero them in global memory
+  // (every row group of every operand) before a copy reads them
+  const uint32_t kt = n % kStageBlock;
+  if (b1 == nblk && kt != 0) {
+    char* blk = w.stage + (size_t)(nblk - 1) * WgStage::bytes;
+    const int nk = kStageBlock - (int)kt;
+    for (int i = threadIdx.x; i < (WgStage::bytes / 256) * nk; i += dw::kThreads)
+      *reinterpret_cast<uint4*>(blk + 256 * (i / nk) + 16 * ((int)kt + i % nk)) = make_uint4(0u, 0u, 0u, 0u);
+    asm volatile("fence.proxy.async.global;" ::: "memory");  // before the async proxy's copies
   }
-  // this thread's items: item i = threadIdx.x + 256 j is operand row i / 4 (dh2, h1, dh1, h2, x, dz in
-  // that order), samples 4 (i % 4) .. + 3; its staged row and its place in an operand set
-  uint32_t src[dw::kItems], dst[dw::kItems], lo[dw::kItems];
-  int dzrow[dw::kItems];
-#pragma unroll
-  for (int j = 0; j < dw::kItems; j++) {
-    const int i = threadIdx.x + dw::kThreads * j, r = i / (dw::kKB / 4), k = (i % (dw::kKB / 4)) * 4;
-    int srow = 0, orow = 0, rows = 1, obase = 0;
-    dzrow[j] = -1;
-    if (r < kHidden) {
-      srow = WgRows::dh2 + r, orow = r, rows = kHidden, obase = dw::Ops::a_dh2;
-    } else if (r < 2 * kHidden) {
-      srow = WgRows::h1 + r - kHidden, orow = r - kHidden, rows = kHidden + 16, obase = dw::Ops::b_h1;
-    } else if (r < 3 * kHidden) {
-      srow = WgRows::dh1 + r - 2 * kHidden, orow = r - 2 * kHidden, rows = kHidden, obase = dw::Ops::a_dh1;
-    } else if (r < 4 * kHidden) {
-      srow = WgRows::h2 + r - 3 * kHidden, orow = r - 3 * kHidden, rows = kHidden, obase = dw::Ops::a_h2;
-    } else if (r < 4 * kHidden + I) {
-      srow = WgRows::x + r - 4 * kHidden, orow = r - 4 * kHidden, rows = kMaxIn, obase = dw::Ops::b_x;
-    } else if (r < nrows) {
-      srow = WgRows::dz + r - 4 * kHidden - I, orow = r - 4 * kHidden - I, rows = 16, obase = dw::Ops::b_dz;
-      dzrow[j] = orow;
-    } else {
-      srow = -1;  // no item
-    }
-    src[j] = srow < 0 ? 0xffffffffu : (uint32_t)(srow * dw::kKB + k);
-    dst[j] = (uint32_t)obase + kmaj_off(orow, k, dw::kKB);
-    lo[j] = (uint32_t)(rows * dw::kKB * 2);
-  }
+  // constants: the ones operand, each buffer's zero row group
+  for (int i = threadIdx.x; i < 4096 / 16; i += dw::kThreads)
+    *reinterpret_cast<uint4*>(sm + dw::Smem::ones + 16 * i) = make_uint4(0x3F803F80u, 0x3F803F80u, 0x3F803F80u, 0x3F803F80u);
+  for (int i = threadIdx.x; i < dw::kRing * 16; i += dw::kThreads)
+    *reinterpret_cast<uint4*>(sm + dw::Smem::ring + (i / 16) * dw::kBuf + WgStage::bytes + 16 * (i % 16)) =
+        make_uint4(0u, 0u, 0u, 0u);
   if (threadIdx.x == 0) {
-    for (int j = 0; j < dw::kRing; j++) mbar_init(lbar + j, 1);
-    mbar_init(mbar, 1);
-    mbar_init(mbar + 1, 1);
+    for (int j = 0; j < dw::kRing; j++) {
+      mbar_init(full + j, 1);
+      mbar_init(fre + j, 1);
+    }
     fence_mbar_init();
   }
   fence_proxy_async();
@@ -1365,113 +1347,85 @@ __global__ void __launch_bounds__(dw::kThreads, 1) k_dw(MlpPtrs mlp, RenderWs w,
   __syncthreads();
   fence_after();
   const uint32_t tmem = *tslot;
-  // staged block b (all rows of its kKB samples, one contiguous array) into ring buffer p, by
-  // thread 0: the byte count expected, then one bulk copy
-  auto issue = [&](uint32_t b, int p) {
-    constexpr uint32_t kBytes = dw::kMaxRows * dw::kKB * 4;
-    static_assert(kBytes % 16 == 0, "bulk copy sizes must be multiples of 16 bytes");
-    mbar_expect_tx(lbar + p, kBytes);
-    bulk_load(f32 + (size_t)p * dw::kMaxRows * dw::kKB, w.stage + (size_t)b * dw::kMaxRows * dw::kKB, kBytes,
-              lbar + p);
-  };
-  // descriptors of operand set 0; set 1 lies Ops::bytes further (the address field counts 16 bytes)
-  const uint32_t ops0 = smem_u32(sm + dw::Smem::ops);
-  auto desc = [&](int off, int rows, int half) {
-    return smem_desc(ops0 + (uint32_t)off + (uint32_t)(half * rows * dw::kKB * 2), 128u, dw::kKB * 16);
-  };
-  const uint64_t d_dh2h = desc(dw::Ops::a_dh2, kHidden, 0), d_dh2l = desc(dw::Ops::a_dh2, kHidden, 1);
-  const uint64_t d_h1h = desc(dw::Ops::b_h1, kHidden + 16, 0), d_h1l = desc(dw::Ops::b_h1, kHidden + 16, 1);
-  const uint64_t d_dh1h = desc(dw::Ops::a_dh1, kHidden, 0), d_dh1l = desc(dw::Ops::a_dh1, kHidden, 1);
-  const uint64_t d_xh = desc(dw::Ops::b_x, kMaxIn, 0), d_xl = desc(dw::Ops::b_x, kMaxIn, 1);
-  const uint64_t d_h2h = desc(dw::Ops::a_h2, kHidden, 0), d_h2l = desc(dw::Ops::a_h2, kHidden, 1);
-  const uint64_t d_dzh = desc(dw::Ops::b_dz, 16, 0), d_dzl = desc(dw::Ops::b_dz, 16, 1);
-  uint32_t lphase = 0u, mphase = 0u;  // parity of each ring buffer's next fill, of each MMA barrier's next phase
-  uint32_t mma_pending = 0u;          // bit q: operand set q's MMAs not yet waited for
   bool alive = true;
-  float db3_0 = 0.f, db3_1 = 0.f, db3_2 = 0.f;
-  uint32_t issued_end = min(b1, b0 + (uint32_t)dw::kRing - 1), waited_end = b0;  // [b0, issued_end) issued
-  if (threadIdx.x == 0)
-    for (uint32_t j = b0; j < issued_end; j++) issue(j, (int)(j - b0));
-  for (uint32_t b = b0; b < b1 && alive; b++) {
-    const int p = (int)((b - b0) % dw::kRing), q = (int)((b - b0) & 1u);
-    // the ring's next block goes into the buffer block b - 1 used, whose reads ended before the
-    // previous step's barrier
-    if (b + dw::kRing - 1 < b1) {
-      if (threadIdx.x == 0) issue(b + dw::kRing - 1, (int)((b - b0 + dw::kRing - 1) % dw::kRing));
-      issued_end = b + dw::kRing;
-    }
-    alive = __syncthreads_and(mbar_wait(lbar + p, (lphase >> p) & 1u, &w.hdr[0]));
-    if (!alive) break;
-    lphase ^= 1u << p;
-    waited_end = b + 1;
-    if (mma_pending & (1u << q)) {  // operand set q is still being read by the MMAs of step b - 2
-      alive = __syncthreads_and(mbar_wait(mbar + q, (mphase >> q) & 1u, &w.hdr[0]));
-      fence_after();
+  if (threadIdx.x == 0) {
+    // block b into buffer p: the byte count expected, then one bulk copy
+    auto issue = [&](uint32_t b, int p) {
+      static_assert(WgStage::bytes % 16 == 0, "bulk copy sizes must be multiples of 16 bytes");
+      mbar_expect_tx(full + p, WgStage::bytes);
+      bulk_load(sm + dw::Smem::ring + p * dw::kBuf, w.stage + (size_t)b * WgStage::bytes, WgStage::bytes, full + p);
+    };
+    // descriptors of buffer 0 (buffer p lies p kBuf further; the address field counts 16 bytes):
+    // MN-major, K-adjacent core matrices (8 samples) 128 bytes apart, row groups 256 bytes apart;
+    // dL/dz3's hi half with its row groups 512 bytes apart, so that rows 8..15 are the zero group
+    const uint32_t r0 = smem_u32(sm + dw::Smem::ring);
+    auto op = [&](int off, int R, int half) { return smem_desc(r0 + off + half * 32 * R, 128u, 256u); };
+    const uint64_t dh2h = op(WgStage::dh2, kHidden, 0), dh2l = op(WgStage::dh2, kHidden, 1);
+    const uint64_t h1h = op(WgStage::h1, kHidden, 0), h1l = op(WgStage::h1, kHidden, 1);
+    const uint64_t dh1h = op(WgStage::dh1, kHidden, 0), dh1l = op(WgStage::dh1, kHidden, 1);
+    const uint64_t h2h = op(WgStage::h2, kHidden, 0), h2l = op(WgStage::h2, kHidden, 1);
+    const uint64_t xh = op(WgStage::x, kMaxIn, 0), xl = op(WgStage::x, kMaxIn, 1);
+    const uint64_t dzh = smem_desc(r0 + WgStage::dz, 128u, 512u), dzl = op(WgStage::dz, 8, 1);
+    const uint64_t one = smem_desc(smem_u32(sm + dw::Smem::ones), 128u, 256u);
+    constexpr uint32_t iw2 = idesc_bf16_mn(kHidden), ib = idesc_bf16_mn(16), iw1 = idesc_bf16_mn(kMaxIn);
+    uint32_t fph = 0u, eph = 0u;  // parity of each buffer's next copy and next MMA completion
+    uint32_t issued = b0, landed = b0, mma_from = b0, mma_to = b0;  // copies [landed, issued) and MMA
+                                                                     // commits [mma_from, mma_to) pending
+    for (; issued < min(b1, b0 + (uint32_t)dw::kRing); issued++) issue(issued, (int)(issued - b0));
+    for (uint32_t b = b0; b < b1 && alive; b++) {
+      const int p = (int)((b - b0) % dw::kRing);
+      alive = mbar_wait(full + p, (fph >> p) & 1u, &w.hdr[0]);
       if (!alive) break;
-      mphase ^= 1u << q;
-      mma_pending &= ~(1u << q);
-    }
-    // the block's rows, split into operand set q; columns at or past n (only in the last block) are zero
-    const float* fb = f32 + (size_t)p * dw::kMaxRows * dw::kKB;
-    char* ops = sm + dw::Smem::ops + q * dw::Ops::bytes;
-    const bool tail = (b + 1) * dw::kKB > n;
-#pragma unroll
-    for (int j = 0; j < dw::kItems; j++) {
-      if (src[j] == 0xffffffffu) continue;
-      const float4 v4 = *reinterpret_cast<const float4*>(fb + src[j]);
-      float v[4] = {v4.x, v4.y, v4.z, v4.w};
-      if (tail) {
-        const uint32_t c0 = b * dw::kKB + (src[j] % dw::kKB);
-#pragma unroll
-        for (int t = 0; t < 4; t++)
-          if (c0 + t >= n) v[t] = 0.0f;
-      }
-      if (dzrow[j] >= 0) {
-        const float sum = (v[0] + v[1]) + (v[2] + v[3]);
-        db3_0 += dzrow[j] == 0 ? sum : 0.0f;
-        db3_1 += dzrow[j] == 1 ? sum : 0.0f;
-        db3_2 += dzrow[j] == 2 ? sum : 0.0f;
-      }
-      float h[4], l[4];
-#pragma unroll
-      for (int t = 0; t < 4; t++) {
-        h[t] = __bfloat162float(__float2bfloat16_rn(v[t]));
-        l[t] = v[t] - h[t];
-      }
-      *reinterpret_cast<uint2*>(ops + dst[j]) = make_uint2(pack_bf16(h[0], h[1]), pack_bf16(h[2], h[3]));
-      *reinterpret_cast<uint2*>(ops + dst[j] + lo[j]) = make_uint2(pack_bf16(l[0], l[1]), pack_bf16(l[2], l[3]));
-    }
-    fence_proxy_async();
-    fence_before();
-    __syncthreads();
-    if (threadIdx.x == 0) {
+      fph ^= 1u << p;
+      landed = b + 1;
       fence_after();
-      const uint64_t o = (uint64_t)(q * dw::Ops::bytes) >> 4;  // operand set q
+      const uint64_t o = (uint64_t)(p * dw::kBuf) >> 4;
       const uint32_t acc = b == b0 ? 0u : 1u;
-      mma_bf16(tmem, d_dh2h + o, d_h1h + o, idesc_bf16(kHidden + 16), acc);
-      mma_bf16(tmem, d_dh2h + o, d_h1l + o, idesc_bf16(kHidden + 16), 1u);
-      mma_bf16(tmem, d_dh2l + o, d_h1h + o, idesc_bf16(kHidden + 16), 1u);
-      mma_bf16(tmem + dw::kColW1, d_dh1h + o, d_xh + o, idesc_bf16(kMaxIn), acc);
-      mma_bf16(tmem + dw::kColW1, d_dh1h + o, d_xl + o, idesc_bf16(kMaxIn), 1u);
-      mma_bf16(tmem + dw::kColW1, d_dh1l + o, d_xh + o, idesc_bf16(kMaxIn), 1u);
-      mma_bf16(tmem + dw::kColW3, d_h2h + o, d_dzh + o, idesc_bf16(16), acc);
-      mma_bf16(tmem + dw::kColW3, d_h2h + o, d_dzl + o, idesc_bf16(16), 1u);
-      mma_bf16(tmem + dw::kColW3, d_h2l + o, d_dzh + o, idesc_bf16(16), 1u);
-      mma_commit(mbar + q);
-    }
-    mma_pending |= 1u << q;
-  }
-  // the last MMAs (their commits arrive in order, so the later set's barrier covers both)
-  for (int q = 0; q < 2 && alive; q++) {
-    if (mma_pending & (1u << q)) {
-      alive = __syncthreads_and(mbar_wait(mbar + q, (mphase >> q) & 1u, &w.hdr[0]));
-      fence_after();
-      if (alive) {
-        mphase ^= 1u << q;
-        mma_pending &= ~(1u << q);
+      mma_bf16(tmem, dh2h + o, h1h + o, iw2, acc);
+      mma_bf16(tmem, dh2h + o, h1l + o, iw2, 1u);
+      mma_bf16(tmem, dh2l + o, h1h + o, iw2, 1u);
+      mma_bf16(tmem + dw::kColB2, dh2h + o, one, ib, acc);
+      mma_bf16(tmem + dw::kColB2, dh2l + o, one, ib, 1u);
+      mma_bf16(tmem + dw::kColW1, dh1h + o, xh + o, iw1, acc);
+      mma_bf16(tmem + dw::kColW1, dh1h + o, xl + o, iw1, 1u);
+      mma_bf16(tmem + dw::kColW1, dh1l + o, xh + o, iw1, 1u);
+      mma_bf16(tmem + dw::kColB1, dh1h + o, one, ib, acc);
+      mma_bf16(tmem + dw::kColB1, dh1l + o, one, ib, 1u);
+      mma_bf16(tmem + dw::kColW3, h2h + o, dzh + o, ib, acc);
+      mma_bf16(tmem + dw::kColW3, h2h + o, dzl + o, ib, 1u);
+      mma_bf16(tmem + dw::kColW3, h2l + o, dzh + o, ib, 1u);
+      mma_bf16(tmem + dw::kColB3, one, dzh + o, ib, acc);
+      mma_bf16(tmem + dw::kColB3, one, dzl + o, ib, 1u);
+      mma_commit(fre + p);
+      mma_to = b + 1;
+      // block b - 1's MMAs done: its buffer takes the next copy
+      if (b > b0) {
+        const int pp = (int)((b - 1 - b0) % dw::kRing);
+        alive = mbar_wait(fre + pp, (eph >> pp) & 1u, &w.hdr[0]);
+        if (!alive) break;
+        eph ^= 1u << pp;
+        mma_from = b;
+        if (issued < b1) {
+          issue(issued, pp);
+          issued++;
+        }
       }
     }
+    // the last MMAs; after a timeout, also the MMAs and the copies still in flight (bounded waits)
+    for (uint32_t b = mma_from; b < mma_to; b++) {
+      const int pp = (int)((b - b0) % dw::kRing);
+      if (mbar_wait(fre + pp, (eph >> pp) & 1u, &w.hdr[0])) eph ^= 1u << pp;
+      else alive = false;
+    }
+    for (uint32_t b = landed; b < issued; b++) {
+      const int pp = (int)((b - b0) % dw::kRing);
+      if (mbar_wait(full + pp, (fph >> pp) & 1u, &w.hdr[0])) fph ^= 1u << pp;
+      alive = false;
+    }
   }
+  fence_before();
+  alive = __syncthreads_and(alive);
+  fence_after();
   if (alive) {
     // d_mlp = [W1 [128][I], b1 [128], W2 [128][128], b2 [128], W3 [3][128], b3 [3]]
     float* dW1 = d_mlp;
@@ -1480,58 +1434,34 @@ __global__ void __launch_bounds__(dw::kThreads, 1) k_dw(MlpPtrs mlp, RenderWs w,
     float* db2 = dW2 + kHidden * kHidden;
     float* dW3 = db2 + kHidden;
     float* db3 = dW3 + 3 * kHidden;
-    const int wq = (threadIdx.x >> 5) & 3, un = wq * 32 + (threadIdx.x & 31);  // this thread's unit (lane)
-    const uint32_t taddr = tmem + ((uint32_t)(wq * 32) << 16);
-    if (threadIdx.x < 128) {  // [dW2 | db2]
-      float v[64];
-      tmem_ld<64>(taddr, v);
+    const int un = threadIdx.x;  // this thread's hidden unit: TMEM lane (warp w reads lanes 32 w ..)
+    const uint32_t taddr = tmem + ((uint32_t)((threadIdx.x >> 5) * 32) << 16);
+    float v[64];
+    tmem_ld<64>(taddr, v);
 #pragma unroll
-      for (int k = 0; k < 64; k++) atomicAdd(&dW2[un * kHidden + k], v[k]);
-      tmem_ld<64>(taddr + 64, v);
+    for (int k = 0; k < 64; k++) atomicAdd(&dW2[un * kHidden + k], v[k]);
+    tmem_ld<64>(taddr + 64, v);
 #pragma unroll
-      for (int k = 0; k < 64; k++) atomicAdd(&dW2[un * kHidden + 64 + k], v[k]);
-      tmem_ld<16>(taddr + 128, v);
-      atomicAdd(&db2[un], v[0]);
-    } else {  // [dW1 | db1], dW3^T
-      float v[32];
-      tmem_ld<32>(taddr + dw::kColW1, v);
+    for (int k = 0; k < 64; k++) atomicAdd(&dW2[un * kHidden + 64 + k], v[k]);
+    tmem_ld<32>(taddr + dw::kColW1, v);
 #pragma unroll
-      for (int k = 0; k < 32; k++) {
-        if (k < I) atomicAdd(&dW1[un * I + k], v[k]);
-        else if (k == I) atomicAdd(&db1[un], v[k]);
-      }
-      tmem_ld<16>(taddr + dw::kColW1 + 32, v);
+    for (int k = 0; k < 32; k++)
+      if (k < I) atomicAdd(&dW1[un * I + k], v[k]);
+    tmem_ld<16>(taddr + dw::kColW1 + 32, v);
 #pragma unroll
-      for (int k = 0; k < 16; k++) {
-        if (32 + k < I) atomicAdd(&dW1[un * I + 32 + k], v[k]);
-        else if (32 + k == I) atomicAdd(&db1[un], v[k]);
-      }
-      tmem_ld<16>(taddr + dw::kColW3, v);
-      for (int j = 0; j < 3; j++) atomicAdd(&dW3[j * kHidden + un], v[j]);
-    }
-    // db3: the CTA's sum of dz3 over its samples
-    float* red = (float*)(sm + dw::Smem::red);
-    const float part[3] = {db3_0, db3_1, db3_2};
+    for (int k = 0; k < 16; k++)
+      if (32 + k < I) atomicAdd(&dW1[un * I + 32 + k], v[k]);
+    tmem_ld<16>(taddr + dw::kColB2, v);
+    atomicAdd(&db2[un], v[0]);
+    tmem_ld<16>(taddr + dw::kColB1, v);
+    atomicAdd(&db1[un], v[0]);
+    tmem_ld<16>(taddr + dw::kColW3, v);
 #pragma unroll
-    for (int j = 0; j < 3; j++) {
-      float t = part[j];
+    for (int j = 0; j < 3; j++) atomicAdd(&dW3[j * kHidden + un], v[j]);
+    tmem_ld<16>(taddr + dw::kColB3, v);  // every lane holds db3
+    if (un == 0)
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-      if ((threadIdx.x & 31) == 0) red[(threadIdx.x >> 5) * 4 + j] = t;
-    }
-    __syncthreads();
-    if (threadIdx.x < 3) {
-      float t = 0.0f;
-      for (int wi = 0; wi < dw::kThreads / 32; wi++) t += red[wi * 4 + threadIdx.x];
-      atomicAdd(&db3[threadIdx.x], t);
-    }
-  }
-  for (int q = 0; q < 2; q++)  // after a timeout: MMAs may still be running (bounded)
-    if (mma_pending & (1u << q)) mbar_wait(mbar + q, (mphase >> q) & 1u, &w.hdr[0]);
-  for (uint32_t bb = waited_end; bb < issued_end; bb++) {  // after a timeout: bulk copies still in flight
-    const int pp = (int)((bb - b0) % dw::kRing);
-    mbar_wait(lbar + pp, (lphase >> pp) & 1u, &w.hdr[0]);
-    lphase ^= 1u << pp;
+      for (int j = 0; j < 3; j++) atomicAdd(&db3[j], v[j]);
   }
   fence_before();
   __syncthreads();
@@ -1576,7 +1506,6 @@ cicero_status run_backward(const cicero_grid* grid, const MlpPtrs& mlp, const Re
     k_bwd_ray<<<blocks, 256, 0, st>>>(src, plan.samp, ws, d_rgb, plan.geo.act_shift);
   }
   count_launches(2);
-  ProfScope ps(kStBwdBrick, st);
   const int smem = BwdSmem::bytes;
   const bool f16 = grid->dtype == CICERO_F16;
   cudaError_t e;
@@ -1584,17 +1513,25 @@ cicero_status run_backward(const cicero_grid* grid, const MlpPtrs& mlp, const Re
   if (ws.rec_mask && plan.geo.C <= bt::kN1 && (!d_mlp || ws.stage)) {
     // grid gradients on the tensor cores, with the recompute's ReLU masks; with d_mlp, the weight
     // gradients' operands staged on the way and the weight gradients as tensor-core GEMMs after
-    if (ws.stage) {
-      e = cudaFuncSetAttribute(k_bwd_brick_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_tc);
-      if (e == cudaSuccess) k_bwd_brick_tc<true><<<num_sms(), bt::kThreads, smem_tc, st>>>(plan.geo, mlp, ws, d_dens, d_feat);
-    } else {
-      e = cudaFuncSetAttribute(k_bwd_brick_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_tc);
-      if (e == cudaSuccess) k_bwd_brick_tc<false><<<num_sms(), bt::kThreads, smem_tc, st>>>(plan.geo, mlp, ws, d_dens, d_feat);
+    {
+      ProfScope ps(kStBwdBrick, st);
+      if (ws.stage) {
+        e = cudaFuncSetAttribute(k_bwd_brick_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_tc);
+        if (e == cudaSuccess)
+          k_bwd_brick_tc<true><<<num_sms(), bt::kThreads, smem_tc, st>>>(plan.geo, mlp, ws, d_dens, d_feat);
+      } else {
+        e = cudaFuncSetAttribute(k_bwd_brick_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_tc);
+        if (e == cudaSuccess)
+          k_bwd_brick_tc<false><<<num_sms(), bt::kThreads, smem_tc, st>>>(plan.geo, mlp, ws, d_dens, d_feat);
+      }
+      if (e == cudaSuccess) e = cudaGetLastError();
+      if (e != cudaSuccess) return cuda_fail(e, "backward kernels");
     }
-    if (e == cudaSuccess) e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "backward kernels");
-    return d_mlp ? launch_dw(mlp, ws, d_mlp, st) : CICERO_OK;
+    if (!d_mlp) return CICERO_OK;
+    ProfScope ps(kStBwdWeights, st);
+    return launch_dw(mlp, ws, d_mlp, st);
   }
+  ProfScope ps(kStBwdBrick, st);
   if (d_mlp)
     e = f16 ? launch_bwd_brick<__half, true>(plan, src, mlp, ws, grid->features, d_dens, d_feat, d_mlp, smem, st)
             : launch_bwd_brick<float, true>(plan, src, mlp, ws, grid->features, d_dens, d_feat, d_mlp, smem, st);

@@ -21,7 +21,7 @@ int num_sms();
 // Stage timing with CUDA events on the launching stream (off unless cicero_profile_begin was
 // called) and a count of the kernels the library launches.
 enum Stage { kStMarch = 0, kStBucket, kStGatherMlp, kStComposite, kStWarpSplat, kStWarpResolve, kStBwdRay,
-             kStBwdBrick, kStMlpEval, kNumStages };
+             kStBwdBrick, kStMlpEval, kStBwdWeights, kNumStages };
 void count_launches(int n);
 struct ProfScope {
   ProfScope(int stage, cudaStream_t st);
@@ -75,25 +75,30 @@ struct RenderWs {
   SrtRec* srt;          // [Q] the Ray Index Table payload in brick order
   RayGeo* ray_geo;      // [R] geometry of each ray's samples
   struct RaySetup* setup;  // [R] per-ray setup of the march (ray, slots, active-slot mask, records)
-  float* stage;         // per-sample operands of the MLP weight gradients (backward with d_mlp only; may be
-                        // null): blocks of 16 sorted samples, each [WgRows::rows][16] FP32 (stage_at)
+  char* stage;          // per-sample operands of the MLP weight gradients (backward with d_mlp only; may be
+                        // null): blocks of kStageBlock sorted samples, WgStage::bytes each (stage_col)
   int R, S, nb, max_tiles;
   uint32_t Q;
 };
 
-// Rows of the weight-gradient staging: x (input, in_dim rows used), h1, h2 (layers 1 and 2 after
-// ReLU), dL/dh2 and dL/dh1 (masked), dL/dz3 (3 rows used)
-struct WgRows {
-  static constexpr int x = 0, h1 = 48, h2 = 176, dh2 = 304, dh1 = 432, dz = 560, rows = 564;
-};
-// floats of the staging for a capacity of Q samples, and the column of sorted sample s (row r of it
-// is at stage_at(s) + kStageBlock r): a block of kStageBlock samples is one contiguous array
+// Weight-gradient staging: per block of kStageBlock sorted samples, the split-BF16 operands of the
+// weight-gradient GEMMs over the samples, in the MN-major no-swizzle layout that the tensor cores
+// read (K = the block's samples): an operand of R rows (hidden units, inputs or outputs) is R / 8
+// row groups of 256 bytes for the hi halves, then as many for the lo halves; in row group g, the
+// 16 bytes at 16 k hold rows 8 g .. 8 g + 7 of sample k (two 128-byte core matrices of 8 samples).
+// Operands: dL/dh2, h1, dL/dh1, h2 (128 rows each), x (48 rows: the input, zero from in_dim),
+// dL/dz3 (8 rows: 3 used).
 constexpr int kStageBlock = 16;
-__host__ __device__ inline size_t stage_floats(uint32_t Q) {
-  return (((size_t)Q + kStageBlock - 1) / kStageBlock) * WgRows::rows * kStageBlock;
+struct WgStage {
+  static constexpr int dh2 = 0, h1 = 8192, dh1 = 16384, h2 = 24576, x = 32768, dz = 35840, bytes = 36352;
+};
+// bytes of the staging for a capacity of Q samples, and where sample s's 16-byte rows start (row
+// group g of an operand of R rows at offset op: + op + 256 g for hi, + op + 32 R + 256 g for lo)
+__host__ __device__ inline size_t stage_bytes(uint32_t Q) {
+  return (((size_t)Q + kStageBlock - 1) / kStageBlock) * WgStage::bytes;
 }
-__host__ __device__ inline size_t stage_at(uint32_t s) {
-  return (size_t)(s / kStageBlock) * WgRows::rows * kStageBlock + (s % kStageBlock);
+__host__ __device__ inline size_t stage_col(uint32_t s) {
+  return (size_t)(s / kStageBlock) * WgStage::bytes + (size_t)(s % kStageBlock) * 16;
 }
 
 struct RenderPlan {

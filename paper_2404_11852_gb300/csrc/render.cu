@@ -36,7 +36,7 @@ size_t render_ws_bytes(const RenderPlan& p) {
   b += 2 * al256(4 * Q) + al256(2 * Q) + al256(16 * Q);
   if (p.want_bwd) b += 2 * al256(4 * Q) + al256(32 * Q);
   if (p.want_k) b += al256(4 * Q);
-  if (p.want_wg) b += al256(4 * stage_floats(p.Q));
+  if (p.want_wg) b += al256(stage_bytes(p.Q));
   const size_t nk = (size_t)p.nb * kOctants;  // RIT keys: (brick, octant)
   b += 2 * al256(4 * nk) + al256(4 * (nk + 1)) + al256(4 * ((size_t)p.nb + 1));
   b += al256(8 * ((size_t)p.nb / kScanChunk + 2));
@@ -68,7 +68,7 @@ bool carve_render_ws(void* ws, size_t bytes, const RenderPlan& p, RenderWs* w) {
   w->rec_T = p.want_bwd ? (float*)take(4 * Q) : nullptr;
   w->rec_raw = p.want_bwd ? (float*)take(4 * Q) : nullptr;
   w->rec_ray = p.want_k ? (uint32_t*)take(4 * Q) : nullptr;
-  w->stage = p.want_wg ? (float*)take(4 * stage_floats(p.Q)) : nullptr;
+  w->stage = p.want_wg ? (char*)take(stage_bytes(p.Q)) : nullptr;
   w->rec_mask = p.want_bwd ? (uint4*)take(32 * Q) : nullptr;
   const size_t nk = (size_t)p.nb * kOctants;
   w->brick_cnt = (uint32_t*)take(4 * nk);

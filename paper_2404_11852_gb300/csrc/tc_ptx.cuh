@@ -4,7 +4,8 @@
 //
 // Operands use the canonical K-major, no-swizzle layout: 8-row x 16-byte core matrices stored as
 // 128 contiguous bytes, K-adjacent core matrices 128 B apart (leading byte offset) and 8-row groups
-// K*16 bytes apart (stride byte offset).
+// K*16 bytes apart (stride byte offset).  The weight-gradient GEMMs read MN-major operands
+// (idesc_bf16_mn).
 #pragma once
 #include <cuda_bf16.h>
 #include <stdint.h>
@@ -32,6 +33,11 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
 __host__ __device__ constexpr uint32_t idesc_bf16(int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
 }
+
+// the same with both operands MN-major (transpose bits 15 and 16): 8 consecutive M (or N) values of
+// one K index form a 16-byte row, 8 K rows a 128-byte core matrix; core matrices adjacent in K lie
+// the leading byte offset apart, those adjacent in M (or N) the stride byte offset apart
+__host__ __device__ constexpr uint32_t idesc_bf16_mn(int N) { return idesc_bf16(N) | (1u << 15) | (1u << 16); }
 
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
   asm volatile(

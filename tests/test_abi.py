@@ -62,8 +62,8 @@ def test_workspace_size_queries(cc):
     assert cc.cicero_render_workspace_size(_grid(), R, sp, cc.options(1, 4)) > 0
     wb = cc.cicero_backward_workspace_size(_grid(), R, sp)
     assert wb > ws
-    # with the weight gradients' operands: 564 FP32 rows of R * S columns (rounded up to 64)
-    assert cc.cicero_backward_mlp_workspace_size(_grid(), R, sp) >= wb + 564 * 4 * R * 64
+    # with the weight gradients' operands: 2,272 bytes of split-BF16 rows per sample slot (R * 64 here)
+    assert cc.cicero_backward_mlp_workspace_size(_grid(), R, sp) >= wb + 2272 * R * 64
     cam = cc.camera(800, 800, 1000.0, 400.0, 400.0, np.eye(3, 4))
     assert cc.cicero_warp_workspace_size(cam) >= 800 * 800 * 8
     assert cc.cicero_mlp_eval_workspace_size(1000) >= 256

@@ -16,10 +16,11 @@ def cc():
     return cicero
 
 
-def gpu_grads(cc, g32, m, o, d, sp, grad, with_mlp=False, feat_offset=0, mlp_path="tc"):
+def gpu_grads(cc, g32, m, o, d, sp, grad, with_mlp=False, feat_offset=0, mlp_path="tc", fill=None):
     """feat_offset > 0 places d_features that many floats into a larger buffer (an address that
     is not 16-byte aligned when feat_offset % 4 != 0).  With the MLP weight gradients, mlp_path
-    "tc" sizes the workspace for their tensor-core GEMMs, "simt" for the CUDA-core path."""
+    "tc" sizes the workspace for their tensor-core GEMMs, "simt" for the CUDA-core path.  fill:
+    a byte written over the whole workspace first (0xFF makes every unwritten BF16 value a NaN)."""
     import torch
     gd, md = cc.DeviceGrid.from_host(g32), cc.DeviceMlp.from_host(m)
     sd = cc.sampling_from(sp)
@@ -30,6 +31,8 @@ def gpu_grads(cc, g32, m, o, d, sp, grad, with_mlp=False, feat_offset=0, mlp_pat
     dm = torch.zeros(m.flat().size, device="cuda") if with_mlp else None
     size = cc.cicero_backward_mlp_workspace_size if with_mlp and mlp_path == "tc" else cc.cicero_backward_workspace_size
     ws = cc.workspace(size(gd.desc, o.shape[0], sd))
+    if fill is not None:
+        ws.fill_(fill)
     cc.cicero_render_backward(gd.desc, md.desc, ot, dt, sd, gr, dd, df, dm, ws)
     cc.cicero_workspace_status(ws)
     out = dd.cpu().double().numpy(), df.cpu().double().numpy()
@@ -183,11 +186,20 @@ def test_autograd_function_matches_backward(cc, orc):
 
 
 @pytest.mark.parametrize("path", ["tc", "simt"])
-@pytest.mark.parametrize("case", ["fd", "occ"])
+@pytest.mark.parametrize("case", ["fd", "occ", "few"])
 def test_backward_mlp_weights(cc, orc, case, path):
     """dL/d(W1, b1, W2, b2, W3, b3) against the oracle, per tensor (relative inf-norm <= 1e-3),
-    together with the grid gradients of the same call (which must not change with d_mlp)."""
-    if case == "fd":
+    together with the grid gradients of the same call (which must not change with d_mlp).  "few":
+    two rays, under 16 composited samples (one partial block of the staged operands, every other
+    CTA of the weight-gradient kernel idle), in a workspace of NaN bytes."""
+    fill = None
+    if case == "few":
+        g = scenes.scene_fd().astype(np.float32)
+        m = scenes.make_mlp(4, random_bias=True)
+        o, d = scenes.random_rays(2, seed=5)
+        sp = scenes.Sampling(near=0.5, far=2.5, n_samples=6, t_stop=0.0)
+        fill = 0xFF
+    elif case == "fd":
         g = scenes.scene_fd().astype(np.float32)
         m = scenes.make_mlp(4, random_bias=True)
         o, d = scenes.random_rays(64, seed=5)
@@ -203,13 +215,30 @@ def test_backward_mlp_weights(cc, orc, case, path):
     grad = 2.0 * (out["rgb"] - tgt) / tgt.size
     grad[out["amb"]] = 0.0  # ambiguous early stops contribute nothing on either side
     wd, wf, wm = orc.backward(g, m, sp, grad, rays=(o, d), with_mlp=True)
-    dd, df, dm = gpu_grads(cc, g, m, o, d, sp, grad, with_mlp=True, mlp_path=path)
+    dd, df, dm = gpu_grads(cc, g, m, o, d, sp, grad, with_mlp=True, mlp_path=path, fill=fill)
     assert rel_inf(dd, wd) <= 1e-3, rel_inf(dd, wd)
     assert rel_inf(df, wf) <= 1e-3, rel_inf(df, wf)
     names = ("w1", "b1", "w2", "b2", "w3", "b3")
     for name, a, b in zip(names, mlp_parts(m, dm), mlp_parts(m, wm)):
         assert np.abs(b).max() > 0.0, name
         assert rel_inf(a, b) <= 1e-3, (name, rel_inf(a, b))
+
+
+def test_backward_mlp_weights_degenerate(cc, orc):
+    """With d_mlp and the tensor-core workspace: no rays, and rays that all miss the box, add
+    nothing to any gradient and leave a clear status word (workspace of NaN bytes)."""
+    import torch
+    g = scenes.scene_fd().astype(np.float32)
+    m = scenes.make_mlp(4, random_bias=True)
+    sp = scenes.Sampling(near=0.5, far=2.5, n_samples=32, t_stop=0.0)
+    for R in (0, 8):
+        o, d = scenes.random_rays(max(R, 1), seed=9)
+        o, d = o[:R].copy(), d[:R].copy()
+        o[:] = np.array([5.0, 5.0, 5.0], dtype=o.dtype)
+        d[:] = np.array([1.0, 0.0, 0.0], dtype=d.dtype)
+        grad = np.ones((R, 3))
+        dd, df, dm = gpu_grads(cc, g, m, o, d, sp, grad, with_mlp=True, mlp_path="tc", fill=0xFF)
+        assert np.abs(dd).max() == 0.0 and np.abs(df).max() == 0.0 and np.abs(dm).max() == 0.0, R
 
 
 def test_autograd_mlp_weights(cc, orc):
