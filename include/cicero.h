@@ -390,9 +390,8 @@ size_t cicero_warp_batch_workspace_size(const cicero_camera *tgt_cams, int n_vie
  *     image may have at most 1048576 pixels (width * height); larger targets return
  *     CICERO_ERR_UNSUPPORTED.  The call allocates and frees nothing.
  *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
- *     that device current, and caches it for the life of the process; make that first call before
- *     any stream capture.  After cudaDeviceReset on a device the cached address is stale: do not
- *     call this entry point on that device again.
+ *     that device current, and caches it for the life of the process.  After cudaDeviceReset on a
+ *     device the cached address is stale: do not call this entry point on that device again.
  *   - Every call shares the one array: calls that may overlap on the GPU (different streams, or
  *     different host threads on one device) race and must be serialised by the caller.  The call
  *     clears what must start empty (the depth buffer) itself. */
