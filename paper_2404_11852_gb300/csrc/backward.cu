@@ -3,7 +3,8 @@
 //
 //   forward recompute  K1-K4 of render.cu (march, Ray Index Table), then per brick the features
 //                      and the MLP: k_fwd_x3 (tensor cores, split-BF16 products) and k_fwd_fix
-//                      (FP32, the samples whose ReLU decisions k_fwd_x3 cannot certify); this
+//                      (FP32, the samples with a ReLU pre-activation within k_fwd_x3's error
+//                      estimate of zero); this
 //                      leaves per composited sample (c, w, T, raw density) and the ReLU masks
 //   B1 k_bwd_ray       per ray (warp), in slot order: R_k = sum_{j>k} w_j c_j + T_end bg by a
 //                      warp scan, dL/dsigma_k = delta (T_{k+1} g.c_k - g.R_k) and
@@ -521,8 +522,8 @@ __global__ void __launch_bounds__(256, 1) k_bwd_brick(GridGeo g, RaySrc src, Mlp
 // lo = bf16(x - hi) and each product is hi hi' + hi lo' + lo hi' (the bf16x3 scheme of Henry, Tang
 // and Heinecke, ARITH 2019: the dropped lo lo' term and the residuals of the split are each ~2^-18
 // of the product, so a product keeps ~16 significant bits), accumulated in FP32 in tensor memory.
-// The ReLU masks are the recompute's (rec_mask): every decision the split-BF16 recompute could not
-// certify was taken again by the FP32 MLP.
+// The ReLU masks are the recompute's (rec_mask): every decision whose pre-activation the split-BF16
+// recompute found within its error estimate of zero was taken again by the FP32 MLP.
 
 namespace bt {
 constexpr int kGroups = 2;

@@ -1226,8 +1226,8 @@ __global__ void __launch_bounds__(kMlpThreads + kProdThreads, 1)
   }
 }
 
-// The samples that the backward's tensor-core forward recompute (k_fwd_x3) could not certify (a
-// ReLU pre-activation within the error bound of its split-BF16 products), recomputed with the FP32
+// The samples that the backward's tensor-core forward recompute (k_fwd_x3) listed (a ReLU
+// pre-activation within its error estimate of zero for the split-BF16 products), recomputed with the FP32
 // MLP of K5f: (c, w) and both ReLU masks overwritten.  The list holds sorted record indices
 // (rec_key, count in hdr[4]); 128 samples per step, features interpolated from global memory.
 // Launched only after k_fwd_x3, so C <= 16.
