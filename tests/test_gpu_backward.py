@@ -241,6 +241,30 @@ def test_backward_mlp_weights_degenerate(cc, orc):
         assert np.abs(dd).max() == 0.0 and np.abs(df).max() == 0.0 and np.abs(dm).max() == 0.0, R
 
 
+def test_backward_weight_path_dispatch(cc, orc):
+    """The weight gradients run as the staged tensor-core GEMMs (one weight-gradient launch per
+    call) when the workspace is cicero_backward_mlp_workspace_size, and on the CUDA cores (no such
+    launch) when it is only cicero_backward_workspace_size; both give the same gradients (each path
+    is within 1e-3 of the oracle elsewhere, so within 2e-3 of the other)."""
+    import torch
+    g = scenes.scene_fd().astype(np.float32)
+    m = scenes.make_mlp(4, random_bias=True)
+    o, d = scenes.random_rays(64, seed=5)
+    sp = scenes.Sampling(near=0.5, far=2.5, n_samples=48, t_stop=0.0)
+    grad = np.random.default_rng(3).standard_normal((64, 3)) * 1e-2
+    out = {}
+    for path in ("tc", "simt"):
+        torch.cuda.synchronize()
+        cc.cicero_profile_begin()
+        out[path] = gpu_grads(cc, g, m, o, d, sp, grad, with_mlp=True, mlp_path=path)
+        torch.cuda.synchronize()
+        prof = cc.cicero_profile_end()
+        assert prof["bwd_weights"][1] == (1 if path == "tc" else 0), (path, prof["bwd_weights"])
+        assert prof["bwd_brick"][1] == 1, (path, prof["bwd_brick"])
+    for a, b in zip(out["tc"], out["simt"]):
+        assert rel_inf(a, b) <= 2e-3, rel_inf(a, b)
+
+
 def test_autograd_mlp_weights(cc, orc):
     """The autograd wrapper's MLP gradients (tensors with requires_grad) against the oracle."""
     import torch
