@@ -831,6 +831,18 @@ def plain_small(cc, torch, dev):
     return out
 
 
+def tuned_bf16_brick(cc, torch, dev, gd, md, cam):
+    """The BF16 brick the library's autotuner picks for this scene's reference frame (timed renders),
+    with the times it measured per brick."""
+    R = cam.width * cam.height
+    sd, cd = cc.sampling_from(cam.sampling), cc.camera_from(cam)
+    ws = cc.workspace(cc.cicero_render_workspace_size(gd.desc, R, sd, cc.options(cc.MLP_BF16, 4)), dev)
+    rgb, depth = torch.empty(R, 3, device=dev), torch.empty(R, device=dev)
+    b, tune = cc.cicero_autotune_brick(gd.desc, md.desc, cd, sd, cc.MLP_BF16, rgb, depth, ws)
+    del ws, rgb, depth
+    return b, tune
+
+
 def sparw_small_scene(cc, torch, dev, n_pix=1024, opaque=False):
     """SpaRW on the 64^3 scene: reference 800x800 at the orbit pose (64 uniform samples), 16 targets
     warped and hole-rendered (BF16 MLP).  Per target: fraction of rays marched and PSNR against
@@ -844,8 +856,9 @@ def sparw_small_scene(cc, torch, dev, n_pix=1024, opaque=False):
     targets = [scenes.offset_camera(cam, k) for k in scenes.SPARW_OFFSETS]
     R, n_t = W * H, len(targets)
     gd, md = cc.DeviceGrid.from_host(g, dev), cc.DeviceMlp.from_host(m, dev)
-    opt = cc.options(cc.MLP_BF16, 8)
-    opt_h = cc.options(cc.MLP_BF16, 8, max_records=120_000_000)  # holes are ~10% of the pixels
+    brick, tune = tuned_bf16_brick(cc, torch, dev, gd, md, cam)
+    opt = cc.options(cc.MLP_BF16, brick)
+    opt_h = cc.options(cc.MLP_BF16, brick, max_records=120_000_000)  # holes are ~10% of the pixels
     win = SparwWindow(cc, torch, dev, gd, md, cam, targets, opt, opt_h)
     t_win = event_ms(torch, win.run, 5)
     win.check()
@@ -870,7 +883,7 @@ def sparw_small_scene(cc, torch, dev, n_pix=1024, opaque=False):
              f"of a blob, the expected depth is a surface)" if opaque
              else "fog-like blobs (amplitudes U[10, 40]: ~50 composited samples per ray)")
     return {"workload": "64^3 x 12 FP32 scene, 800x800, 64 samples, 16 targets (1 deg yaw + 5 mm apart)",
-            "scene": scene,
+            "scene": scene, "brick": brick, "autotune_ms": tune,
             "window_ms": t_win, "target_fps": n_t / (t_win / 1e3), "psnr_pixels_per_target": n_pix,
             "psnr_db_min": min(p["psnr_db"] for p in per), "fraction_marched_mean": float(holes.sum()) / (n_t * R),
             "marched": "disocclusion and void holes (a void hole's march composites nothing)", "targets": per}
@@ -1103,10 +1116,13 @@ def main():
         others["config_batched"] = batched_workload(cc, torch, dev)
         others["sparw_window_sweep"] = window_sweep(cc, torch, dev, grid, mlp, o16)
         g_op = cc.DeviceGrid.from_host(scenes.scene_small_opaque(), dev)
+        m_op = cc.DeviceMlp.from_host(scenes.make_mlp(12), dev)
+        b_op, _ = tuned_bf16_brick(cc, torch, dev, g_op, m_op,
+                                   scenes.orbit_camera(W, H, sampling=scenes.sampling_uniform(64)))
         others["sparw_window_sweep_opaque_scene"] = window_sweep(
-            cc, torch, dev, g_op, cc.DeviceMlp.from_host(scenes.make_mlp(12), dev), cc.options(cc.MLP_BF16, 8),
-            sampling=scenes.sampling_uniform(64), label="64^3 opaque-surface scene, 64 uniform samples")
-        del g_op
+            cc, torch, dev, g_op, m_op, cc.options(cc.MLP_BF16, b_op),
+            sampling=scenes.sampling_uniform(64), label=f"64^3 opaque-surface scene, 64 uniform samples, brick {b_op}")
+        del g_op, m_op
         others["sparw_phi_sweep"] = phi_sweep(cc, torch, dev, grid, o16, active)
         others["config_hash_grid"] = hash_workload(cc, torch, dev, grid, g_h)
 

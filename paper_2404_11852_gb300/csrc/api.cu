@@ -197,6 +197,7 @@ cicero_status encode_brick_map(const cicero_grid* grid, const GridGeo& geo, cons
   if (!fn) return fail(CICERO_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
   const int es = elem_bytes(grid->dtype);
   if (box.vx * geo.C > 256 || box.vb > 256) return fail(CICERO_ERR_UNSUPPORTED, "brick box exceeds 256 elements");
+  if (box.box_bytes > 227 * 1024) return fail(CICERO_ERR_UNSUPPORTED, "brick box does not fit in shared memory");
   cuuint64_t dims[3] = {(cuuint64_t)geo.n[0] * geo.C, (cuuint64_t)geo.n[1], (cuuint64_t)geo.n[2]};
   cuuint64_t strides[2] = {(cuuint64_t)geo.n[0] * geo.C * es, (cuuint64_t)geo.n[0] * geo.n[1] * geo.C * es};
   cuuint32_t boxd[3] = {(cuuint32_t)(box.vx * geo.C), (cuuint32_t)box.vb, (cuuint32_t)box.vb};
