@@ -713,14 +713,15 @@ size_t cicero_warp_workspace_size(const cicero_camera* tgt_cam) {
 }
 
 
-// The backward's plan: FP32, bricks of 8 (fewer, fuller tiles for the tensor-core kernels, which
-// take up to 16 channels); bricks of 4 above that, where the FP32 recompute stages each brick in
-// shared memory beside its two input buffers.
+// The backward's plan: FP32, bricks of 16 up to 16 channels (the tensor-core kernels and the
+// CUDA-core weight-gradient kernel read features from global memory, so a brick only groups the
+// samples: larger bricks give fewer, fuller 128-sample tiles); bricks of 4 above that, where the
+// FP32 recompute stages each brick in shared memory beside its two input buffers.
 static cicero_options backward_options(const cicero_grid* grid) {
   cicero_options o;
   memset(&o, 0, sizeof o);
   o.precision = CICERO_MLP_FP32;
-  o.brick = (grid && grid->C > 16) ? 4 : 8;
+  o.brick = (grid && grid->C > 16) ? 4 : 16;
   return o;
 }
 
