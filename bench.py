@@ -717,9 +717,10 @@ def backward_workload(cc, torch, dev):
 
     fwd()
     t_f = event_ms(torch, fwd, 5)
-    # the same forward with the FP32-class tensor-core MLP (split BF16), then the FP32 one again,
-    # whose colours feed the loss gradient
-    t_fs = event_ms(torch, lambda: fwd(cc.options(cc.MLP_FP32_SPLIT, 8)), 5)
+    # the same forward with the FP32-class tensor-core MLP (split BF16; bricks of 16, as the
+    # backward's plan: its kernels read features from global memory, so bigger bricks only make
+    # fuller tiles), then the FP32 one again, whose colours feed the loss gradient
+    t_fs = event_ms(torch, lambda: fwd(cc.options(cc.MLP_FP32_SPLIT, 16)), 5)
     fwd()
     t_b = event_ms(torch, bwd, 5)
     t_bm = event_ms(torch, lambda: bwd(dm, ws_bm), 5)
@@ -934,9 +935,10 @@ def main():
     ref_rgb, ref_depth = torch.empty(R, 3, device=dev), torch.empty(R, device=dev)
     b16, tune16 = cc.cicero_autotune_brick(grid.desc, mlp.desc, cd, sd, cc.MLP_BF16, ref_rgb, ref_depth, ws_t)
     b32, tune32 = cc.cicero_autotune_brick(grid.desc, mlp.desc, cd, sd, cc.MLP_FP32, ref_rgb, ref_depth, ws_t)
+    bsp, tunesp = cc.cicero_autotune_brick(grid.desc, mlp.desc, cd, sd, cc.MLP_FP32_SPLIT, ref_rgb, ref_depth, ws_t)
     del ws_t, ref_rgb, ref_depth
     o16, o32 = cc.options(cc.MLP_BF16, b16), cc.options(cc.MLP_FP32, b32)
-    o_split = cc.options(cc.MLP_FP32_SPLIT, b32)  # FP32-class MLP on the tensor cores (split BF16)
+    o_split = cc.options(cc.MLP_FP32_SPLIT, bsp)  # FP32-class MLP on the tensor cores (split BF16)
     # all targets' holes are rendered in one batched pass; records are capped well above need
     ob = cc.options(cc.MLP_BF16, b16, max_records=HOLE_RECORDS)
     win = SparwWindow(cc, torch, dev, grid, mlp, cam, targets, o16, ob,
@@ -1147,7 +1149,8 @@ def main():
             "fp32_split_full_fps": n_fp * world / t_split,
             "msamples_per_s_fp32_split_full": active * n_fp * world / t_split / 1e6,
             "active_samples_per_frame": active,
-            "autotune_ms_by_brick": {"bf16": tune16, "fp32": tune32}, "brick": {"bf16": b16, "fp32": b32},
+            "autotune_ms_by_brick": {"bf16": tune16, "fp32": tune32, "fp32_split": tunesp},
+            "brick": {"bf16": b16, "fp32": b32, "fp32_split": bsp},
             "fraction_rays_marched_targets": holes / (N_TARGETS * R),
             "hole_batch": {"rays": holes / 1, "disocclusion_rays": int(disocc.sum()), "void_rays": int(void.sum()),
                            "composited_samples": int(hole_hdr[2]),
