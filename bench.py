@@ -1044,6 +1044,12 @@ def main():
     active = int(hdr[2])
     t_bf16 = timed(lambda: full(o16), n_fp, 1)
     t_split = timed(lambda: full(o_split), n_fp, 1)
+    # marched slots of the frame: per pixel, the slot where its march stopped (or its last valid
+    # slot), from one more render outside the timed regions
+    n_steps = torch.empty(R, dtype=torch.int32, device=dev)
+    cc.cicero_render(grid.desc, mlp.desc, cd, sd, o16, win.ref_rgb, win.ref_depth, None, n_steps, win.ws_r)
+    marched = int(n_steps.sum().item())
+    del n_steps
 
     # per-stage device time (CUDA events on the launching stream) over two profiled windows
     cc.cicero_profile_begin()
@@ -1145,6 +1151,9 @@ def main():
             "plain_fp32_fps": n_fp * world / t_fp32,
             "bf16_full_fps": n_fp * world / t_bf16,
             "msamples_per_s_bf16_full": active * n_fp * world / t_bf16 / 1e6,
+            "marched_slots_per_frame": marched,
+            "mslots_marched_per_s_bf16_full": marched * n_fp * world / t_bf16 / 1e6,
+            "mslots_marched_per_s_fp32_full": marched * n_fp * world / t_fp32 / 1e6,
             "msamples_per_s_fp32_full": active * n_fp * world / t_fp32 / 1e6,
             "fp32_split_full_fps": n_fp * world / t_split,
             "msamples_per_s_fp32_split_full": active * n_fp * world / t_split / 1e6,
