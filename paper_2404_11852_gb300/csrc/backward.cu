@@ -16,10 +16,15 @@
 //                      masks the recompute recorded (no forward layer is evaluated again), then
 //                      the trilinear adjoint added straight into d_features and d_density with
 //                      global atomics, 16-byte vector atomics where the channels allow.
-//   B2 k_bwd_brick     with d_mlp (the weight gradients need h1 and x): the same per brick, 64
-//                      samples at a time, MLP forward and backward on CUDA cores, the weight
-//                      gradients summed over the CTA's tiles in registers and added to d_mlp once
-//                      per CTA; the trilinear adjoint as in k_bwd_brick_tc.
+//                      With d_mlp and a workspace that holds the staging, B0 and B2 also store
+//                      each sample's weight-gradient operands (x, h1, h2; dL/dh2, dL/dh1, dL/dz3)
+//                      as split-BF16 rows in the layout the tensor cores read, and
+//   B3 k_dw            forms the MLP weight gradients from them as tensor-core GEMMs over the
+//                      samples (bulk copies straight into MMA operands).
+//   B2 k_bwd_brick     with d_mlp and no room for the staging, or above 16 channels: the same
+//                      per brick, 64 samples at a time, MLP forward and backward on CUDA cores, the
+//                      weight gradients summed over the CTA's tiles in registers and added to
+//                      d_mlp once per CTA; the trilinear adjoint as in k_bwd_brick_tc.
 #include <cuda_runtime.h>
 
 #include <string.h>
@@ -1261,16 +1266,17 @@ cicero_status launch_fwd_x3(const cicero_grid* grid, const GridGeo& geo, const M
 
 // ------------------------------------------------------------------------------------------------
 // The MLP weight gradients on the tensor cores, from the operands that the recompute (x, h1, h2)
-// and B2 (dL/dh2, dL/dh1, dL/dz3) staged per composited sample (feature-major FP32 rows, column =
-// sorted sample index).  They are sums over the samples s of outer products,
-//   [dW2 | db2]  = sum_s dh2_s [h1_s, 1]^T     M = 128, N = 144 (h1, then a block whose first row is 1)
-//   [dW1 | db1]  = sum_s dh1_s [x_s, 1]^T      M = 128, N = 48 (x, then row in_dim = 1, then zeros)
-//   dW3^T        = sum_s h2_s dz3_s^T          M = 128, N = 16 (3 rows used)
-// taken as tcgen05 MMAs with K = the samples, 16 per step, on split-BF16 operands (three products
-// as in k_bwd_brick_tc), each CTA accumulating its range of samples in TMEM and adding the sums to
-// d_mlp once; db3 = sum_s dz3_s on the CUDA cores.  Staged blocks of 16 samples (36 KB each) stream
-// in by bulk copies into a ring of kRing buffers, kRing - 1 of them in flight, while the current
-// block is split into the operands and multiplied.
+// and B2 (dL/dh2, dL/dh1, dL/dz3) staged per composited sample, already split into BF16 hi and lo
+// in the MN-major layout the MMAs read (WgStage; K = the block's 16 samples, in sorted order).
+// They are sums over the samples s of outer products,
+//   dW2 = sum_s dh2_s h1_s^T    M = 128, N = 128     db2 = sum_s dh2_s    (against a ones operand)
+//   dW1 = sum_s dh1_s x_s^T     M = 128, N = 48      db1 = sum_s dh1_s
+//   dW3^T = sum_s h2_s dz3_s^T  M = 128, N = 16 (3 used)   db3 = sum_s dz3_s (A = ones)
+// taken as tcgen05 MMAs with K = 16 samples per step on split-BF16 operands (three products as in
+// k_bwd_brick_tc; the biases two: hi and lo against exact ones), each CTA accumulating its range of
+// samples in TMEM and adding the sums to d_mlp once.  Staged blocks (36 KB each) stream in by bulk
+// copies into a ring of kRing buffers, kRing - 1 of them in flight, and feed the MMAs as they are:
+// the kernel converts nothing.
 namespace dw {
 constexpr int kThreads = 128;                  // thread 0 runs the pipeline; all four warps read TMEM out
 constexpr int kRing = 6;                       // staged blocks in shared memory (copies in flight)
