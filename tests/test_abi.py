@@ -97,6 +97,16 @@ def test_invalid_arguments_rejected_on_host(cc):
     # unsupported brick size
     st = L.cicero_render_workspace_size(C.byref(_grid()), 64, C.byref(sp), C.byref(cc.options(0, 5)))
     assert st == 0
+    # record capacity: 2^24 rays x 256 slots reach 2^32 records unless max_records caps them
+    sp256 = cc.sampling(n_samples=256)
+    assert L.cicero_render_workspace_size(C.byref(_grid()), 1 << 24, C.byref(sp256), None) == 0
+    assert b"2^32" in L.cicero_last_error()
+    capped = cc.options(0, 8, max_records=100_000_000)
+    assert L.cicero_render_workspace_size(C.byref(_grid()), 1 << 24, C.byref(sp256), C.byref(capped)) > 0
+    # MLP tiles in flight per SM: 0 (as many as fit) .. 4
+    for groups, ok in ((0, True), (4, True), (5, False), (-1, False)):
+        size = L.cicero_render_workspace_size(C.byref(_grid()), 64, C.byref(sp), C.byref(cc.options(1, 4, 0, groups)))
+        assert (size > 0) == ok, groups
 
 
 def _mlp_desc(cc, in_dim=39, n_freq=4):
