@@ -1077,6 +1077,9 @@ def main():
         t_smem = GATHER_SMEM_WAVEFRONTS_PER_SAMPLE * active / (n_sm * pk["sm_max_mhz"] * 1e6)
         roof["shared_memory"] = {"wavefronts_per_sample": GATHER_SMEM_WAVEFRONTS_PER_SAMPLE,
                                  "bound_ms": t_smem * 1e3, "frac": t_smem / t_launch}
+        # the same launch against the HBM roofline: its DRAM bytes (ncu, above) over its event time
+        hbm = gather_traffic() / t_launch / 1e9
+        roof["hbm"] = {"achieved": hbm, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": hbm / pk["hbm_gbs"]}
     stages = {k: {"ms_per_step": v[0] / 2, "launches_per_step": v[1] / 2} for k, v in prof.items() if v[1]}
     stage_roof = stage_roofline(stages, pk, R, int(holes), active, int(hole_hdr[2]))
 
