@@ -99,6 +99,20 @@ def test_fp32_split_channel_limit(cc):
     assert ei.value.status == 2
 
 
+def test_brick_box_beyond_shared_memory(cc):
+    """An FP32 feature grid at bricks of 16 needs a staged box of 17^3 vertices x 12 x 4 B (235 KB),
+    more than shared memory holds: the BF16 and FP32 renders refuse with CICERO_ERR_UNSUPPORTED,
+    while the split-BF16 MLP, which stages no brick, renders it."""
+    g = scenes.make_grid(32, 12, 2, seed=5)
+    m = scenes.make_mlp(12, seed=6)
+    cam = scenes.orbit_camera(8, 8, sampling=scenes.sampling_uniform(16))
+    for prec in (cc.MLP_BF16, cc.MLP_FP32):
+        with pytest.raises(cc.CiceroError) as ei:
+            gpu_render(cc, g, m, cam, cam.sampling, prec, 16)
+        assert ei.value.status == 2, prec
+    gpu_render(cc, g, m, cam, cam.sampling, cc.MLP_FP32_SPLIT, 16)
+
+
 def test_bf16_small_scene(cc, orc, small):
     g, m = small
     cam = scenes.orbit_camera(64, 64, sampling=scenes.sampling_uniform(64))
