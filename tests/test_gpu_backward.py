@@ -265,6 +265,28 @@ def test_backward_weight_path_dispatch(cc, orc):
         assert rel_inf(a, b) <= 2e-3, rel_inf(a, b)
 
 
+@pytest.mark.parametrize("path", ["tc", "simt"])
+def test_backward_sixteen_channels(cc, orc, path):
+    """C = 16, the widest grid the tensor-core kernels take (dL/dfeatures fills the N = 16 MMA, the
+    input row 16 + 27 = 43 of 48 columns): grid and all six MLP gradients against the oracle, with
+    the weight gradients on the tensor cores and on the CUDA cores."""
+    C = 16
+    g = scenes.make_grid(40, C, 6, seed=51)
+    m = scenes.make_mlp(C, seed=52, random_bias=True)
+    o, d = scenes.random_rays(200, seed=53)
+    sp = scenes.Sampling(near=0.5, far=2.5, n_samples=64, t_stop=1e-3)
+    out = orc.render(g, m, sp, rays=(o, d))
+    tgt = scenes.random_targets(200, seed=54).astype(np.float64)
+    grad = 2.0 * (out["rgb"] - tgt) / tgt.size
+    grad[out["amb"]] = 0.0
+    wd, wf, wm = orc.backward(g, m, sp, grad, rays=(o, d), with_mlp=True)
+    dd, df, dm = gpu_grads(cc, g, m, o, d, sp, grad, with_mlp=True, mlp_path=path)
+    assert rel_inf(dd, wd) <= 1e-3, rel_inf(dd, wd)
+    assert rel_inf(df, wf) <= 1e-3, rel_inf(df, wf)
+    for name, a, b in zip(("w1", "b1", "w2", "b2", "w3", "b3"), mlp_parts(m, dm), mlp_parts(m, wm)):
+        assert rel_inf(a, b) <= 1e-3, (name, rel_inf(a, b))
+
+
 def test_autograd_mlp_weights(cc, orc):
     """The autograd wrapper's MLP gradients (tensors with requires_grad) against the oracle."""
     import torch

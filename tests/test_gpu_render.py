@@ -99,6 +99,16 @@ def test_fp32_split_channel_limit(cc):
     assert ei.value.status == 2
 
 
+def test_fp32_split_sixteen_channels(cc, orc):
+    """C = 16, the widest grid the split-BF16 MLP takes (input row 43 of 48 columns): FP32 tolerance."""
+    g = scenes.make_grid(32, 16, 4, seed=61)
+    m = scenes.make_mlp(16, seed=62)
+    cam = scenes.orbit_camera(40, 40, sampling=scenes.sampling_uniform(48))
+    ref = orc.render(g, m, cam.sampling, cam=cam)
+    out = gpu_render(cc, g, m, cam, cam.sampling, cc.MLP_FP32_SPLIT, 8)
+    check_render(out, ref, TOL32)
+
+
 def test_brick_box_beyond_shared_memory(cc):
     """An FP32 feature grid at bricks of 16 needs a staged box of 17^3 vertices x 12 x 4 B (235 KB),
     more than shared memory holds: the BF16 and FP32 renders refuse with CICERO_ERR_UNSUPPORTED,
