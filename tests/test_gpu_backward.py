@@ -265,12 +265,12 @@ def test_backward_weight_path_dispatch(cc, orc):
         assert rel_inf(a, b) <= 2e-3, rel_inf(a, b)
 
 
-@pytest.mark.parametrize("path", ["tc", "simt"])
-def test_backward_sixteen_channels(cc, orc, path):
+@pytest.mark.parametrize("C, path", [(16, "tc"), (16, "simt"), (20, "tc")])
+def test_backward_sixteen_channels(cc, orc, C, path):
     """C = 16, the widest grid the tensor-core kernels take (dL/dfeatures fills the N = 16 MMA, the
     input row 16 + 27 = 43 of 48 columns): grid and all six MLP gradients against the oracle, with
-    the weight gradients on the tensor cores and on the CUDA cores."""
-    C = 16
+    the weight gradients on the tensor cores and on the CUDA cores.  C = 20 with the tensor-core
+    workspace: beyond that width the backward takes the FP32 recompute and the CUDA-core kernel."""
     g = scenes.make_grid(40, C, 6, seed=51)
     m = scenes.make_mlp(C, seed=52, random_bias=True)
     o, d = scenes.random_rays(200, seed=53)
