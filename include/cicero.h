@@ -410,11 +410,13 @@ cicero_status cicero_warp_noalloc(const float *ref_rgb, const float *ref_depth,
  * [w1 [hidden][in_dim], b1 [hidden], w2 [hidden][hidden], b2 [hidden], w3 [3][hidden], b3 [3]]
  * (FP32, the layout of cicero_mlp's tensors back to back).  Gradients are summed with atomic adds,
  * so the order of the sums, and the last bits of the result, vary between calls.  Each ray's
- * forward pass is recomputed (nothing is stored by the forward); the recompute and the grid
- * gradients run the MLP on the tensor cores with split-BF16 operands (hi + lo, three products,
- * FP32 accumulation), and the samples with a ReLU pre-activation within an estimate of that
- * precision's error of zero (~10 times the typical error) are recomputed in FP32, so a mask
- * differs from the FP32 MLP's only where the split products err by more than that.  Early stop is a fixed truncation.  For composited sample k:
+ * forward pass is recomputed (nothing is stored by the forward).  Up to 16 feature channels the
+ * recompute and the grid gradients run the MLP on the tensor cores with split-BF16 operands
+ * (hi + lo, three products, FP32 accumulation), and the samples with a ReLU pre-activation within
+ * an estimate of that precision's error of zero (~10 times the typical error) are recomputed in
+ * FP32, so a mask differs from the FP32 MLP's only where the split products err by more than
+ * that; wider grids recompute and differentiate in FP32 on the CUDA cores.  Early stop is a fixed
+ * truncation.  For composited sample k:
  *   dL/dc_k = w_k g;  dL/dsigma_k = delta (T_{k+1} g.c_k - g.R_k), R_k = sum_{j>k} w_j c_j + T_end bg;
  *   dL/draw_k = dL/dsigma_k sigmoid(raw_k + shift); MLP chain rule; trilinear adjoint. */
 cicero_status cicero_render_backward(const cicero_grid *grid, const cicero_mlp *mlp,
